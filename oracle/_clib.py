@@ -1,0 +1,97 @@
+"""Build and load the oracle's C loops (test infrastructure only).
+
+Compiled with gcc -O2 -fopenmp -ffp-contract=off so that the only fused
+multiply-adds are the explicit fma() calls of stencil.c.
+"""
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "stencil.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_OUT_DIR, "liboracle_stencil.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile stencil.c into oracle/_build/liboracle_stencil.so."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11",
+               _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB)
+            i64, p = ctypes.c_int64, ctypes.c_void_p
+            for name, extra in (("oracle_apply_prec", 2), ("oracle_apply", 1), ("oracle_residual", 2)):
+                fn = getattr(L, name)
+                fn.restype = None
+                fn.argtypes = [i64, i64, i64, p, ctypes.c_int, p] + [p] * (extra + 1)
+            L.oracle_jacobi_inverse.restype = None
+            L.oracle_jacobi_inverse.argtypes = [i64, p, p]
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c64(a):
+    a = np.asarray(a, dtype=np.float64)
+    return a if a.flags["C_CONTIGUOUS"] else np.ascontiguousarray(a)
+
+
+class Stencil:
+    """Banded operator on a grid, evaluated by the C loops."""
+
+    def __init__(self, grid, coef):
+        self.grid = grid
+        self.coef = _c64(coef)
+        self.S = int(self.coef.shape[0])
+        self.n = grid.n
+        assert self.coef.shape == (self.S, self.n)
+        self._per = np.array([1 if p else 0 for p in grid.periodic], dtype=np.uint8)
+        self.dinv = np.empty(self.n)
+        lib().oracle_jacobi_inverse(self.n, _ptr(self.coef), _ptr(self.dinv))
+
+    def _dims(self):
+        g = self.grid
+        return g.nx, g.ny, g.nz, _ptr(self._per), self.S, _ptr(self.coef)
+
+    def apply_prec(self, v):
+        v = _c64(v)
+        w = np.empty(self.n)
+        lib().oracle_apply_prec(*self._dims(), _ptr(self.dinv), _ptr(v), _ptr(w))
+        return w
+
+    def apply(self, x):
+        x = _c64(x)
+        w = np.empty(self.n)
+        lib().oracle_apply(*self._dims(), _ptr(x), _ptr(w))
+        return w
+
+    def residual(self, b, x):
+        b = _c64(b)
+        x = _c64(x)
+        r = np.empty(self.n)
+        lib().oracle_residual(*self._dims(), _ptr(b), _ptr(x), _ptr(r))
+        return r
+
+    def minv(self, v):
+        """M^{-1} v with M = diag(A): one rounding per element."""
+        return self.dinv * v

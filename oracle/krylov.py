@@ -1,0 +1,517 @@
+"""Oracle Krylov solvers: plain, slow, FP64, step by step (test infrastructure).
+
+Each solver follows one of the paper's algorithms in its order and notation,
+with N-length products evaluated by the C loops of stencil.c (through
+``Stencil``) and NumPy dot products / axpys, and the small dense problems by
+NumPy/SciPy LAPACK. Readings of the paper that this module takes:
+
+* Preconditioning is point Jacobi M = diag(A) applied from the right for
+  every solver, so every residual below is the true residual b - A x.
+* Convergence is tested relative to ||b||; GMRES(m) and rGCROT stop a cycle
+  at the first step whose least-squares residual estimate |g_{j+1}| meets the
+  tolerance (the in-cycle estimate of the note under Algorithm 1) and then
+  recompute b - A x (line 14); another cycle runs if that is still above.
+* Matrix-vector products are counted in the recurrences only (lines 6 and
+  the BiCGStab lines 7 and 12); b - A x and the A U of line 1a are not.
+* Algorithm 3, line 13a: the solution takes x <- x + U z with z = -B y, the
+  sign that the derivation of eq. (xm_UV_rm) gives (x_m = x_0 + V_m y + U z);
+  the listing's 'x - U(R^{-1} z)' contradicts it, and with U stored as U R^{-1}
+  (so that A U = C) no R appears.
+* Line 14a (recycle-space update) uses harmonic Ritz vectors (the GCRO-DR
+  selection named in the title of Algorithm 3), after every cycle; see
+  ``harmonic_ritz_update``.
+* The projection of line 1b (xi = C^T r, r <- r - C xi, x <- x + U xi) is
+  applied at the top of every cycle, not only the first. In exact arithmetic
+  the residual of line 14 is already orthogonal to the updated C (it is
+  W_hat times a vector orthogonal to range(G)), so the iterates are
+  unchanged; in floating point its C-component is amplified by every update
+  (by about 30x per cycle on the 5^3 convection-diffusion problem), which
+  breaks v_1 ⟂ C (eq. V_perp_C) within a few cycles.
+* BiCGStab's shadow residual is r~ = r_0 (the note under Algorithm 2), taken
+  after the projection of line 1c in Algorithm 4.
+"""
+import numpy as np
+import scipy.linalg as sla
+
+from ._clib import Stencil
+
+OK = 0
+NOT_CONVERGED = 1
+BREAKDOWN = 2
+
+
+def _info(status, matvecs, cycles, restarts, relres_true, relres_est, hist, kdim=0):
+    return dict(status=status, matvecs=matvecs, cycles=cycles, restarts=restarts,
+                relres_true=relres_true, relres_est=relres_est, history=hist, recycle_dim=kdim)
+
+
+def _givens(a, b):
+    if b == 0.0:
+        return 1.0, 0.0, a
+    r = np.hypot(a, b)
+    return a / r, b / r, r
+
+
+class _LS:
+    """Progressive Givens QR of the (j+1) x j Hessenberg matrix and rotated rhs
+    (Algorithm 1/3, line 12: y = argmin || e_1 rho - H y ||)."""
+
+    def __init__(self, m, rho):
+        self.R = np.zeros((m + 1, m))
+        self.g = np.zeros(m + 1)
+        self.g[0] = rho
+        self.cs = np.zeros(m)
+        self.sn = np.zeros(m)
+
+    def add_column(self, j, h):
+        """h = H[0:j+2, j]; returns |g_{j+1}| (the residual-norm estimate)."""
+        h = h.copy()
+        for i in range(j):
+            t = self.cs[i] * h[i] + self.sn[i] * h[i + 1]
+            h[i + 1] = -self.sn[i] * h[i] + self.cs[i] * h[i + 1]
+            h[i] = t
+        c, s, r = _givens(h[j], h[j + 1])
+        self.cs[j], self.sn[j] = c, s
+        h[j], h[j + 1] = r, 0.0
+        self.R[: j + 2, j] = h[: j + 2]
+        self.g[j + 1] = -s * self.g[j]
+        self.g[j] = c * self.g[j]
+        return abs(self.g[j + 1])
+
+    def solve(self, jj):
+        return sla.solve_triangular(self.R[:jj, :jj], self.g[:jj], lower=False)
+
+
+def _op(grid_or_op, coef=None):
+    if isinstance(grid_or_op, Stencil):
+        return grid_or_op
+    return Stencil(grid_or_op, coef)
+
+
+# --------------------------------------------------------------------------- GMRES(m)
+def gmres(op, b, x0=None, tol=1e-8, m=30, max_matvec=2000, keep_cycle=False):
+    """GMRES(m), Algorithm 1, right-preconditioned by M = diag(A).
+
+    Arnoldi with modified Gram-Schmidt (lines 7-9) on A M^{-1}; solution
+    update x <- x + M^{-1} V_j y (line 13); true residual (line 14)."""
+    n = op.n
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=float)
+    bnorm = float(np.linalg.norm(b))
+    if bnorm == 0.0:
+        return np.zeros(n), _info(OK, 0, 0, 0, 0.0, 0.0, [])
+    r = op.residual(b, x)
+    rho = float(np.linalg.norm(r))
+    matvecs = cycles = 0
+    hist = [rho / bnorm]
+    est = rho / bnorm
+    last = None
+    while rho > tol * bnorm and matvecs < max_matvec:
+        V = np.zeros((m + 1, n))
+        H = np.zeros((m + 1, m))
+        V[0] = r / rho
+        ls = _LS(m, rho)
+        jj = 0
+        for j in range(m):
+            w = op.apply_prec(V[j])
+            matvecs += 1
+            for l in range(j + 1):
+                H[l, j] = V[l] @ w
+                w = w - V[l] * H[l, j]
+            H[j + 1, j] = np.linalg.norm(w)
+            happy = H[j + 1, j] == 0.0
+            if not happy:
+                V[j + 1] = w / H[j + 1, j]
+            e = ls.add_column(j, H[: j + 2, j])
+            est = e / bnorm
+            jj = j + 1
+            if e <= tol * bnorm or happy or matvecs >= max_matvec:
+                break
+        y = ls.solve(jj)
+        x = x + op.minv(V[:jj].T @ y)
+        r = op.residual(b, x)
+        rho = float(np.linalg.norm(r))
+        cycles += 1
+        hist.append(rho / bnorm)
+        if keep_cycle:
+            last = dict(V=V[: jj + 1].copy(), H=H[: jj + 1, :jj].copy(), y=y)
+    st = OK if rho <= tol * bnorm else NOT_CONVERGED
+    info = _info(st, matvecs, cycles, 0, rho / bnorm, est, hist)
+    if keep_cycle:
+        info["last_cycle"] = last
+    return x, info
+
+
+# --------------------------------------------------------------------------- recycle space helpers
+def recycle_from_u(op, U):
+    """Line 1a: C~ = A U, thin QR C~ = C R; return (U R^{-1}, C) so A U = C."""
+    Ct = np.stack([op.apply(u) for u in U.T], axis=1)
+    Q, R = np.linalg.qr(Ct)
+    Unew = sla.solve_triangular(R, U.T, trans="T", lower=False).T  # U R^{-1}
+    return Unew, Q
+
+
+def harmonic_ritz_update(op, U, C, V, B, H, jj, k, return_theta=False):
+    """Line 14a: new recycle space from harmonic Ritz vectors.
+
+    W = [U, M^{-1} V_j] (x-space) and W_hat = [C, V_{j+1}] satisfy
+    A W = W_hat G with G = [[I, B], [0, H_j]] (the augmented Arnoldi relation,
+    eq. aug-arnoldi-rec). Harmonic Ritz pairs of A M^{-1} with respect to
+    range(M W) solve G^T G p = theta G^T F p, F = W_hat^T M W =
+    [[C^T M U, 0], [V_{j+1}^T M U, [I; 0]]]. The eigenvectors of the k
+    smallest |theta| (a complex pair enters as [Re p, Im p]; a pair split by
+    the cut is dropped; infinite theta never selected) form P; with
+    G P = Q R' (thin QR), C <- W_hat Q and U <- W P R'^{-1}, which keeps
+    A U = C and C^T C = I."""
+    n = op.n
+    kc = 0 if U is None else U.shape[1]
+    nn = kc + jj
+    G = np.zeros((nn + 1, nn))
+    F = np.zeros((nn + 1, nn))
+    if kc:
+        G[:kc, :kc] = np.eye(kc)
+        G[:kc, kc:] = B[:kc, :jj]
+        MU = U * op.coef[0][:, None]
+        F[:kc, :kc] = C.T @ MU
+        F[kc:, :kc] = V[: jj + 1] @ MU
+    G[kc:, kc:] = H[: jj + 1, :jj]
+    F[kc:kc + jj, kc:] = np.eye(jj)
+    A_ = G.T @ G
+    B_ = G.T @ F
+    ab, vr = sla.eig(A_, B_, right=True, left=False, homogeneous_eigvals=True)
+    alpha, beta = ab[0], ab[1]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        theta = alpha / beta
+    mag = np.abs(theta)
+    mag[~np.isfinite(mag)] = np.inf
+    order = np.lexsort((np.imag(theta) < 0, np.real(theta), mag))
+    kk = min(k, nn)
+    cols = []
+    used = set()
+    for idx in order:
+        if len(cols) >= kk or not np.isfinite(mag[idx]):
+            break
+        if idx in used:
+            continue
+        if abs(np.imag(theta[idx])) > 0:
+            if len(cols) + 2 > kk:
+                break
+            v = vr[:, idx]
+            cols.append(np.real(v))
+            cols.append(np.imag(v))
+            # the conjugate partner is the nearest remaining eigenvalue to conj(theta)
+            rest = [i for i in order if i != idx and i not in used]
+            partner = min(rest, key=lambda i: abs(theta[i] - np.conj(theta[idx])))
+            used.add(idx)
+            used.add(partner)
+        else:
+            cols.append(np.real(vr[:, idx]))
+            used.add(idx)
+    if not cols:
+        return (U, C, theta) if return_theta else (U, C)
+    P = np.stack(cols, axis=1)
+    Q, Rp = np.linalg.qr(G @ P)
+    What = np.concatenate([C, V[: jj + 1].T], axis=1) if kc else V[: jj + 1].T
+    Wx = (np.concatenate([U, (op.dinv[:, None] * V[:jj].T)], axis=1) if kc
+          else op.dinv[:, None] * V[:jj].T)
+    Cn = What @ Q
+    Un = Wx @ sla.solve_triangular(Rp, P.T, trans="T", lower=False).T  # W P R'^{-1}
+    return (Un, Cn, theta) if return_theta else (Un, Cn)
+
+
+# --------------------------------------------------------------------------- rGCROT(m,k)
+def rgcrot(op, b, x0=None, tol=1e-8, m=30, k=10, U=None, C=None, update=True, max_matvec=2000,
+           keep_cycle=False):
+    """rGCROT(m,k), Algorithm 3, right-preconditioned by M = diag(A).
+
+    U, C are N x k_cur arrays (or None) with A U = C, C^T C = I; if only U is
+    given, line 1a makes C. Returns (x, U, C, info)."""
+    n = op.n
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=float)
+    bnorm = float(np.linalg.norm(b))
+    if U is not None and U.shape[1] == 0:
+        U = C = None
+    if U is not None and C is None:
+        U, C = recycle_from_u(op, U)
+    kc = 0 if U is None else U.shape[1]
+    if bnorm == 0.0:
+        return np.zeros(n), U, C, _info(OK, 0, 0, 0, 0.0, 0.0, [], kc)
+    rhat = op.residual(b, x)                      # line 1
+    if kc:
+        xi = C.T @ rhat                           # line 1b
+        r = rhat - C @ xi
+        x = x + U @ xi
+    else:
+        r = rhat
+    rho = float(np.linalg.norm(r))
+    matvecs = cycles = 0
+    hist = [rho / bnorm]
+    est = rho / bnorm
+    last = None
+    first = True
+    while rho > tol * bnorm and matvecs < max_matvec:   # line 3
+        if kc and not first:
+            # line 1b again: v_1 must be orthogonal to the (updated) C for
+            # eq. V_perp_C; the residual of line 14 is only orthogonal to it
+            # up to rounding, and each update of line 14a amplifies the drift.
+            xi = C.T @ r
+            r = r - C @ xi
+            x = x + U @ xi
+            rho = float(np.linalg.norm(r))
+        first = False
+        V = np.zeros((m + 1, n))
+        H = np.zeros((m + 1, m))
+        Bm = np.zeros((max(kc, 1), m))
+        V[0] = r / rho                                  # line 4
+        ls = _LS(m, rho)
+        jj = 0
+        for j in range(m):                              # line 5
+            w = op.apply_prec(V[j])                     # line 6
+            matvecs += 1
+            for l in range(kc):                         # lines 6a-6c
+                Bm[l, j] = C[:, l] @ w
+                w = w - C[:, l] * Bm[l, j]
+            for l in range(j + 1):                      # lines 7-9
+                H[l, j] = V[l] @ w
+                w = w - V[l] * H[l, j]
+            H[j + 1, j] = np.linalg.norm(w)             # line 10
+            happy = H[j + 1, j] == 0.0
+            if not happy:
+                V[j + 1] = w / H[j + 1, j]
+            e = ls.add_column(j, H[: j + 2, j])
+            est = e / bnorm
+            jj = j + 1
+            if e <= tol * bnorm or happy or matvecs >= max_matvec:
+                break
+        y = ls.solve(jj)                                # line 12
+        x = x + op.minv(V[:jj].T @ y)                   # line 13
+        if kc:
+            z = -Bm[:kc, :jj] @ y                       # line 12a
+            x = x + U @ z                               # line 13a
+        r = op.residual(b, x)                           # line 14
+        rho = float(np.linalg.norm(r))
+        cycles += 1
+        hist.append(rho / bnorm)
+        if keep_cycle:
+            last = dict(V=V[: jj + 1].copy(), H=H[: jj + 1, :jj].copy(), B=Bm[:kc, :jj].copy(),
+                        C=None if C is None else C.copy(), U=None if U is None else U.copy(), y=y, jj=jj)
+        if update and k > 0:                            # line 14a
+            U, C = harmonic_ritz_update(op, U, C, V, Bm, H, jj, k)
+            kc = 0 if U is None else U.shape[1]
+    st = OK if rho <= tol * bnorm else NOT_CONVERGED
+    info = _info(st, matvecs, cycles, 0, rho / bnorm, est, hist, kc)
+    if keep_cycle:
+        info["last_cycle"] = last
+    return x, U, C, info
+
+
+# --------------------------------------------------------------------------- BiCGStab
+def bicgstab(op, b, x0=None, tol=1e-8, max_matvec=2000):
+    """BiCGStab, Algorithm 2, right-preconditioned: the iterates p, s live in
+    the preconditioned space and x = x_0 + M^{-1} (sum of alpha p + omega s)."""
+    n = op.n
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=float)
+    bnorm = float(np.linalg.norm(b))
+    if bnorm == 0.0:
+        return np.zeros(n), _info(OK, 0, 0, 0, 0.0, 0.0, [])
+    r = op.residual(b, x)                               # line 1
+    rt = r.copy()                                       # r~ = r_0
+    xt = np.zeros(n)
+    matvecs = it = 0
+    hist = [np.linalg.norm(r) / bnorm]
+    status = NOT_CONVERGED
+    p = v = None
+    alpha = omega = rho_old = 0.0
+    while np.linalg.norm(r) > tol * bnorm and matvecs < max_matvec:  # line 3
+        rho = rt @ r                                    # line 4
+        if rho == 0.0:                                  # line 5
+            status = BREAKDOWN
+            break
+        if it == 0:                                     # line 6
+            p = r.copy()
+        else:
+            beta = (rho / rho_old) * (alpha / omega)
+            p = r + beta * (p - omega * v)
+        v = op.apply_prec(p)                            # line 7
+        matvecs += 1
+        alpha = rho / (rt @ v)                          # line 8
+        s = r - alpha * v
+        if np.linalg.norm(s) <= tol * bnorm:            # lines 9-10
+            xt = xt + alpha * p
+            r = s
+            it += 1
+            hist.append(np.linalg.norm(r) / bnorm)
+            break
+        t = op.apply_prec(s)                            # line 12
+        matvecs += 1
+        tt = t @ t
+        if tt == 0.0:
+            status = BREAKDOWN
+            break
+        omega = (t @ s) / tt                            # line 13
+        xt = xt + alpha * p + omega * s                 # line 14
+        r = s - omega * t                               # line 15
+        rho_old = rho                                   # line 16
+        it += 1
+        hist.append(np.linalg.norm(r) / bnorm)
+        if omega == 0.0:
+            status = BREAKDOWN
+            break
+    x = x + op.minv(xt)
+    rtrue = op.residual(b, x)
+    rel = float(np.linalg.norm(rtrue)) / bnorm
+    if status != BREAKDOWN:
+        status = OK if rel <= tol else NOT_CONVERGED
+    return x, _info(status, matvecs, it, 0, rel, float(np.linalg.norm(r)) / bnorm, hist)
+
+
+# --------------------------------------------------------------------------- rBiCGStab
+def _rbicgstab_pass(op, b, x, tol, U, C, max_matvec, bnorm, callback=None):
+    """One run of Algorithm 4 from x_hat = x; returns (x, matvecs, its,
+    breakdown, updated-residual norm, history)."""
+    n = op.n
+    kc = 0 if C is None else C.shape[1]
+    rhat = op.residual(b, x)                            # line 1
+    if kc:
+        eta1 = C.T @ rhat                               # line 1c
+        r = rhat - C @ eta1
+        xi = -eta1
+    else:
+        r = rhat
+        xi = np.zeros(0)
+    rt = r.copy()                                       # line 2: r~ = r_0
+    xt = np.zeros(n)
+    matvecs = it = 0
+    hist = []
+    brk = False
+    p = v = None
+    alpha = omega = rho_old = 0.0
+    while np.linalg.norm(r) > tol * bnorm and matvecs < max_matvec:   # line 3
+        rho = rt @ r                                    # line 4
+        if abs(rho) <= 1e-14 * np.linalg.norm(rt) * np.linalg.norm(r):   # line 5
+            brk = True
+            break
+        if it == 0:                                     # line 6
+            p = r.copy()
+        else:
+            beta = (rho / rho_old) * (alpha / omega)
+            p = r + beta * (p - omega * v)
+        v = op.apply_prec(p)                            # line 7
+        matvecs += 1
+        if kc:
+            eta1 = C.T @ v                              # line 7a
+            v = v - C @ eta1
+        rtv = rt @ v
+        if rtv == 0.0:
+            brk = True
+            break
+        alpha = rho / rtv                               # line 8
+        s = r - alpha * v
+        if np.linalg.norm(s) <= tol * bnorm:            # line 9
+            xt = xt + alpha * p                         # line 10
+            r = s
+            if kc:
+                xi = xi + alpha * eta1                  # line 10a
+            it += 1
+            hist.append(np.linalg.norm(r) / bnorm)
+            break
+        t = op.apply_prec(s)                            # line 12
+        matvecs += 1
+        if kc:
+            eta2 = C.T @ t                              # line 12a
+            t = t - C @ eta2
+        tt = t @ t
+        if tt == 0.0:
+            brk = True
+            break
+        omega = (t @ s) / tt                            # line 13
+        if kc:
+            xi = xi + alpha * eta1 + omega * eta2       # line 13a
+        xt = xt + alpha * p + omega * s                 # line 14
+        r = s - omega * t                               # line 15
+        rho_old = rho                                   # line 16
+        it += 1
+        hist.append(np.linalg.norm(r) / bnorm)
+        if callback is not None:
+            callback(r)
+        if omega == 0.0:
+            brk = True
+            break
+    if callback is not None:
+        callback(r)
+    x = x + op.minv(xt)                                 # line 17a (and x = x_hat + M^{-1} x~)
+    if kc:
+        x = x - U @ xi
+    return x, matvecs, it, brk, float(np.linalg.norm(r)), hist
+
+
+def rbicgstab(op, b, x0=None, tol=1e-8, U=None, C=None, max_matvec=2000, max_restarts=3, callback=None):
+    """rBiCGStab with one recycle space, Algorithm 4, right-preconditioned.
+
+    When the updated residual meets the tolerance the postponed U update is
+    folded in (line 17a) and the true residual b - A x is checked; if it is
+    above the tolerance, or on breakdown, Algorithm 4 restarts from the
+    current x (at most ``max_restarts`` times)."""
+    n = op.n
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=float)
+    bnorm = float(np.linalg.norm(b))
+    if U is not None and U.shape[1] == 0:
+        U = C = None
+    if U is not None and C is None:
+        U, C = recycle_from_u(op, U)                    # line 1b
+    kc = 0 if U is None else U.shape[1]
+    if bnorm == 0.0:
+        return np.zeros(n), _info(OK, 0, 0, 0, 0.0, 0.0, [], kc)
+    matvecs = its = restarts = 0
+    hist = []
+    status = NOT_CONVERGED
+    upd = np.inf
+    while True:
+        x, mv, it, brk, upd, h = _rbicgstab_pass(op, b, x, tol, U, C, max_matvec - matvecs, bnorm, callback)
+        matvecs += mv
+        its += it
+        hist += h
+        rel = float(np.linalg.norm(op.residual(b, x))) / bnorm
+        if rel <= tol:
+            status = OK
+            break
+        if matvecs >= max_matvec:
+            status = NOT_CONVERGED
+            break
+        if restarts >= max_restarts:
+            status = BREAKDOWN if brk else NOT_CONVERGED
+            break
+        restarts += 1
+    return x, _info(status, matvecs, its, restarts, rel, upd / bnorm, hist, kc)
+
+
+# --------------------------------------------------------------------------- sequence drivers
+class RecyclingSequence:
+    """Solves a sequence A x_t = b_t carrying the recycle space (U, C) across
+    steps (Sec. 1, Sec. 2.3). mode: 'GMRES', 'rGCROT', 'BiCGStab',
+    'rBiCGStab' or 'hybrid' (rGCROT with recycle update for the first
+    ``hybrid_switch`` steps, then rBiCGStab with U, C frozen; Sec. 2.4)."""
+
+    def __init__(self, op, mode="rGCROT", m=30, k=10, tol=1e-8, hybrid_switch=5, max_matvec=2000):
+        self.op, self.mode, self.m, self.k, self.tol = op, mode, m, k, tol
+        self.hybrid_switch, self.max_matvec = hybrid_switch, max_matvec
+        self.U = self.C = None
+        self.t = 0
+
+    def solve(self, b, x0=None):
+        mode = self.mode
+        if mode == "hybrid":
+            mode = "rGCROT" if self.t < self.hybrid_switch else "rBiCGStab"
+        if mode == "GMRES":
+            x, info = gmres(self.op, b, x0, self.tol, self.m, self.max_matvec)
+        elif mode == "rGCROT":
+            x, self.U, self.C, info = rgcrot(self.op, b, x0, self.tol, self.m, self.k, self.U, self.C,
+                                             update=True, max_matvec=self.max_matvec)
+        elif mode == "BiCGStab":
+            x, info = bicgstab(self.op, b, x0, self.tol, self.max_matvec)
+        elif mode == "rBiCGStab":
+            x, info = rbicgstab(self.op, b, x0, self.tol, self.U, self.C, self.max_matvec)
+        else:
+            raise ValueError(mode)
+        info["mode"] = mode
+        self.t += 1
+        return x, info

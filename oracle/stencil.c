@@ -1,0 +1,91 @@
+/*
+ * Oracle (test infrastructure only; never linked into the product library).
+ *
+ * Plain C loops for the banded structured-grid operator of Sec. 2.1 ("Data
+ * Layout": 7 or 19 coefficients per cell in diagonal storage) and the right
+ * point-Jacobi preconditioner (Sec. 2.1, "Preconditioners"; applied from the
+ * right as for BiCGStab).
+ *
+ * Every output element is evaluated in a fixed order:
+ *   z_q   = v_q * dinv_q              (dinv_q = 1 / a_qq, IEEE divide)
+ *   w_p   = coef[0][p] * z_p
+ *   w_p   = fma(coef[s][p], z_nb(p,s), w_p)   for s = 1 .. S-1
+ * Bands that point out of a non-periodic face are skipped (their
+ * coefficients are zero by construction). Periodic axes wrap.
+ *
+ * Layout: coef is S contiguous bands of N = nx*ny*nz doubles, cell index
+ * i + nx*(j + ny*k). Band offsets (dx,dy,dz):
+ *   0 (0,0,0); 1 (-1,0,0) 2 (1,0,0) 3 (0,-1,0) 4 (0,1,0) 5 (0,0,-1) 6 (0,0,1);
+ *   7 (-1,-1,0) 8 (1,-1,0) 9 (-1,1,0) 10 (1,1,0);
+ *   11 (-1,0,-1) 12 (1,0,-1) 13 (-1,0,1) 14 (1,0,1);
+ *   15 (0,-1,-1) 16 (0,1,-1) 17 (0,-1,1) 18 (0,1,1).
+ */
+#include <math.h>
+#include <stdint.h>
+
+static const int OFF[19][3] = {
+    {0, 0, 0},
+    {-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1},
+    {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 1, 0},
+    {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1}, {1, 0, 1},
+    {0, -1, -1}, {0, 1, -1}, {0, -1, 1}, {0, 1, 1},
+};
+
+/* neighbour coordinate along one axis; -1 when outside a non-periodic axis */
+static int64_t wrap(int64_t c, int64_t n, int periodic) {
+  if (c >= 0 && c < n) return c;
+  if (!periodic) return -1;
+  return c < 0 ? c + n : c - n;
+}
+
+/* y = A * (scale .* v); scale == NULL means the identity */
+static void apply_core(int64_t nx, int64_t ny, int64_t nz, const uint8_t* per, int S,
+                       const double* coef, const double* scale, const double* v, double* y) {
+  const int64_t N = nx * ny * nz;
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < nz; ++k) {
+    for (int64_t j = 0; j < ny; ++j) {
+      for (int64_t i = 0; i < nx; ++i) {
+        const int64_t p = i + nx * (j + ny * k);
+        double zp = scale ? v[p] * scale[p] : v[p];
+        double w = coef[p] * zp;
+        for (int s = 1; s < S; ++s) {
+          int64_t ii = wrap(i + OFF[s][0], nx, per[0]);
+          int64_t jj = wrap(j + OFF[s][1], ny, per[1]);
+          int64_t kk = wrap(k + OFF[s][2], nz, per[2]);
+          if (ii < 0 || jj < 0 || kk < 0) continue;
+          const int64_t q = ii + nx * (jj + ny * kk);
+          double zq = scale ? v[q] * scale[q] : v[q];
+          w = fma(coef[(int64_t)s * N + p], zq, w);
+        }
+        y[p] = w;
+      }
+    }
+  }
+}
+
+/* dinv[p] = 1 / coef[0][p] */
+void oracle_jacobi_inverse(int64_t n, const double* coef, double* dinv) {
+  for (int64_t p = 0; p < n; ++p) dinv[p] = 1.0 / coef[p];
+}
+
+/* w = A * M^{-1} v  (right point-Jacobi) */
+void oracle_apply_prec(int64_t nx, int64_t ny, int64_t nz, const uint8_t* per, int S,
+                       const double* coef, const double* dinv, const double* v, double* w) {
+  apply_core(nx, ny, nz, per, S, coef, dinv, v, w);
+}
+
+/* w = A v */
+void oracle_apply(int64_t nx, int64_t ny, int64_t nz, const uint8_t* per, int S,
+                  const double* coef, const double* v, double* w) {
+  apply_core(nx, ny, nz, per, S, coef, 0, v, w);
+}
+
+/* r = b - A x, element by element: r_p = b_p - (A x)_p */
+void oracle_residual(int64_t nx, int64_t ny, int64_t nz, const uint8_t* per, int S,
+                     const double* coef, const double* b, const double* x, double* r) {
+  const int64_t N = nx * ny * nz;
+  apply_core(nx, ny, nz, per, S, coef, 0, x, r);
+#pragma omp parallel for schedule(static)
+  for (int64_t p = 0; p < N; ++p) r[p] = b[p] - r[p];
+}

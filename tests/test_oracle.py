@@ -1,0 +1,236 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by linear
+algebra, not by the oracle itself: brute-force dense operators, dense LU
+solutions, finite termination, monotone residuals (Table 1), the special
+cases of Algorithms 3 and 4 with an empty recycle space (their notes), the
+invariants of Sec. 2.3 (eqs. V_perp_C, aug-arnoldi-rec, aug-arnoldi-equiv),
+harmonic Ritz values computed from explicit dense matrices, and exact
+recycling."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from problems import Grid, make_config, random_operator, porous_skew_19pt
+from problems.operators import sphere_pack
+from problems.fields import rng_for
+import oracle
+from oracle import Stencil, dense_matrix, gmres, rgcrot, bicgstab, rbicgstab, harmonic_ritz_update
+
+
+def tiny_problems():
+    out = []
+    c1 = make_config(1, size=5)
+    out.append(("convdiff", c1.grid, c1.coef, c1.rhs(0)))
+    c2 = make_config(2, size=6)
+    out.append(("channel", c2.grid, c2.coef, c2.rhs(1)))
+    n = (7, 6, 5)
+    solid, _ = sphere_pack(n, 1.6, 0.3, rng_for(9, 3), max_attempts=3000)
+    grid, coef = porous_skew_19pt(n, np.where(solid, 1e-2, 1.0), 15.0)
+    b = np.random.default_rng(3).standard_normal(grid.n)
+    out.append(("porous", grid, coef, b))
+    g = Grid(4, 5, 3, (True, False, True))
+    out.append(("random19", g, random_operator(g, 19, np.random.default_rng(4), 1.2),
+                np.random.default_rng(5).standard_normal(g.n)))
+    return out
+
+
+PROBS = tiny_problems()
+
+
+@pytest.mark.parametrize("per", [(False, False, False), (True, False, True), (True, True, True)])
+@pytest.mark.parametrize("S", [7, 19])
+def test_stencil_matches_dense(per, S):
+    g = Grid(5, 4, 3, per)
+    coef = random_operator(g, S, np.random.default_rng(S))
+    op = Stencil(g, coef)
+    A = dense_matrix(g, coef)
+    rng = np.random.default_rng(1)
+    v = rng.standard_normal(g.n)
+    b = rng.standard_normal(g.n)
+    scale = np.abs(A) @ np.abs(v)
+    assert np.all(np.abs(op.apply(v) - A @ v) <= 1e-14 * scale)
+    z = v / coef[0]
+    assert np.all(np.abs(op.apply_prec(v) - A @ z) <= 1e-14 * (np.abs(A) @ np.abs(z)))
+    assert np.all(np.abs(op.residual(b, v) - (b - A @ v)) <= 1e-14 * (scale + np.abs(b)))
+    assert np.array_equal(op.dinv, 1.0 / coef[0])
+
+
+@pytest.mark.parametrize("name,grid,coef,b", PROBS, ids=[p[0] for p in PROBS])
+@pytest.mark.parametrize("mode", ["GMRES", "rGCROT", "BiCGStab", "rBiCGStab"])
+def test_solvers_reach_dense_lu(name, grid, coef, b, mode):
+    op = Stencil(grid, coef)
+    A = dense_matrix(grid, coef)
+    xs = sla.solve(A, b)
+    kappa = np.linalg.cond(A)
+    tol = 1e-12
+    if mode == "GMRES":
+        x, info = gmres(op, b, tol=tol, m=12, max_matvec=5000)
+    elif mode == "rGCROT":
+        x, U, C, info = rgcrot(op, b, tol=tol, m=12, k=6, max_matvec=5000)
+    elif mode == "BiCGStab":
+        x, info = bicgstab(op, b, tol=tol, max_matvec=5000)
+    else:
+        # recycle space from a preceding rGCROT solve of a neighbouring rhs
+        b0 = b + 0.1 * np.random.default_rng(7).standard_normal(b.size)
+        _, U, C, _ = rgcrot(op, b0, tol=1e-10, m=12, k=6)
+        x, info = rbicgstab(op, b, tol=tol, U=U, C=C, max_matvec=5000)
+    rel = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+    assert rel <= 10 * tol or (mode in ("BiCGStab", "rBiCGStab") and rel <= 1e-10)
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= max(1e-9, 10 * kappa * rel)
+
+
+def test_gmres_finite_termination():
+    """Full GMRES (m >= N) terminates within N matrix-vector products."""
+    g = Grid(3, 3, 3, (False, False, False))
+    coef = random_operator(g, 19, np.random.default_rng(11), dominance=0.6)
+    op = Stencil(g, coef)
+    b = np.random.default_rng(12).standard_normal(g.n)
+    x, info = gmres(op, b, tol=1e-11, m=g.n, max_matvec=g.n)
+    assert info["status"] == oracle.OK and info["matvecs"] <= g.n
+    assert info["cycles"] == 1
+
+
+@pytest.mark.parametrize("name,grid,coef,b", PROBS[:3], ids=[p[0] for p in PROBS[:3]])
+def test_monotone_true_residual(name, grid, coef, b):
+    """GMRES(m) and rGCROT residual norms do not increase (Table 1)."""
+    op = Stencil(grid, coef)
+    _, i1 = gmres(op, b, tol=1e-11, m=5, max_matvec=3000)
+    _, _, _, i2 = rgcrot(op, b, tol=1e-11, m=5, k=4, max_matvec=3000)
+    for h in (i1["history"], i2["history"]):
+        h = np.array(h)
+        assert np.all(h[1:] <= h[:-1] * (1 + 1e-10))
+        assert len(h) > 2
+
+
+@pytest.mark.parametrize("name,grid,coef,b", PROBS, ids=[p[0] for p in PROBS])
+def test_rgcrot_k0_is_gmres(name, grid, coef, b):
+    """Algorithm 3 without a recycle space is Algorithm 1 (note under Alg. 3)."""
+    op = Stencil(grid, coef)
+    x1, i1 = gmres(op, b, tol=1e-10, m=7)
+    x2, U, C, i2 = rgcrot(op, b, tol=1e-10, m=7, k=0)
+    assert np.array_equal(x1, x2) and i1["matvecs"] == i2["matvecs"] and U is None
+
+
+@pytest.mark.parametrize("name,grid,coef,b", PROBS, ids=[p[0] for p in PROBS])
+def test_rbicgstab_empty_is_bicgstab(name, grid, coef, b):
+    """Algorithm 4 with an empty recycle space is Algorithm 2 (note under Alg. 4)."""
+    op = Stencil(grid, coef)
+    x1, i1 = bicgstab(op, b, tol=1e-10)
+    x2, i2 = rbicgstab(op, b, tol=1e-10, max_restarts=0)
+    assert np.array_equal(x1, x2) and i1["matvecs"] == i2["matvecs"]
+
+
+@pytest.mark.parametrize("name,grid,coef,b", PROBS, ids=[p[0] for p in PROBS])
+def test_recycle_invariants(name, grid, coef, b):
+    """A U = C, C^T C = I (Sec. 2.3), V_{m+1} ⟂ C (eq. V_perp_C) and the
+    augmented Arnoldi relation A M^{-1} V_m = C B + V_{m+1} H (eq.
+    aug-arnoldi-rec), with dense matrices."""
+    op = Stencil(grid, coef)
+    A = dense_matrix(grid, coef)
+    Minv = np.diag(1.0 / coef[0])
+    nA = np.linalg.norm(A, 2)
+    _, U, C, _ = rgcrot(op, b, tol=1e-12, m=6, k=4, max_matvec=400)
+    b2 = b + 0.05 * np.random.default_rng(2).standard_normal(b.size)
+    x, U2, C2, info = rgcrot(op, b2, tol=1e-12, m=6, k=4, U=U, C=C, max_matvec=400, keep_cycle=True)
+    for UU, CC in ((U, C), (U2, C2)):
+        assert np.linalg.norm(A @ UU - CC) <= 1e-11 * nA * np.linalg.norm(UU)
+        assert np.linalg.norm(CC.T @ CC - np.eye(CC.shape[1])) <= 1e-12
+    lc = info["last_cycle"]
+    V, H, B, Cc = lc["V"].T, lc["H"], lc["B"], lc["C"]
+    jj = lc["jj"]
+    assert np.linalg.norm(V.T @ Cc) <= 1e-12
+    assert np.linalg.norm(V.T @ V - np.eye(jj + 1)) <= 1e-12
+    lhs = A @ Minv @ V[:, :jj]
+    rhs = Cc @ B + V @ H
+    assert np.linalg.norm(lhs - rhs) <= 1e-12 * np.linalg.norm(A @ Minv, 2)
+    # eq. aug-arnoldi-equiv: (I - C C^T) A M^{-1} V_m = V_{m+1} H
+    P = np.eye(A.shape[0]) - Cc @ Cc.T
+    assert np.linalg.norm(P @ lhs - V @ H) <= 1e-12 * np.linalg.norm(A @ Minv, 2)
+
+
+def test_harmonic_ritz_values_dense():
+    """The small pencil (G^T G, G^T F) gives the harmonic Ritz values of
+    A M^{-1} on range([M U, V_j]): eigenvalues of ((AY)^T AY, (AY)^T Y) with
+    Y = [M U, V_j] formed explicitly."""
+    name, grid, coef, b = PROBS[2]
+    op = Stencil(grid, coef)
+    A = dense_matrix(grid, coef)
+    M = np.diag(coef[0])
+    Ahat = A @ np.linalg.inv(M)
+    _, U, C, _ = rgcrot(op, b, tol=1e-12, m=6, k=4, max_matvec=60)
+    b2 = b + 0.05 * np.random.default_rng(2).standard_normal(b.size)
+    _, _, _, info = rgcrot(op, b2, tol=1e-14, m=6, k=4, U=U, C=C, max_matvec=6, keep_cycle=True, update=False)
+    lc = info["last_cycle"]
+    jj = lc["jj"]
+    Vr = lc["V"]
+    Hm = np.zeros((7, 6)); Hm[: jj + 1, :jj] = lc["H"]
+    Bm = np.zeros((4, 6)); Bm[:, :jj] = lc["B"]
+    Vfull = np.zeros((7, grid.n)); Vfull[: jj + 1] = Vr
+    _, _, theta = harmonic_ritz_update(op, lc["U"], lc["C"], Vfull, Bm, Hm, jj, 4, return_theta=True)
+    Y = np.concatenate([M @ lc["U"], Vr[:jj].T], axis=1)
+    AY = Ahat @ Y
+    ref = sla.eigvals(AY.T @ AY, AY.T @ Y)
+    got = np.sort_complex(np.asarray(theta))
+    ref = np.sort_complex(ref)
+    scale = np.abs(ref).max()
+    assert np.allclose(got, ref, atol=1e-9 * scale, rtol=1e-9)
+
+
+def test_exact_recycling():
+    """If b lies in range(C) the initial projection (line 1b / 1c) solves the
+    system: no matrix-vector products and x = U C^T b."""
+    name, grid, coef, b = PROBS[0]
+    op = Stencil(grid, coef)
+    _, U, C, _ = rgcrot(op, b, tol=1e-12, m=6, k=4, max_matvec=200)
+    bb = C @ np.array([1.0, -2.0, 0.5, 3.0][: C.shape[1]])
+    x, _, _, info = rgcrot(op, bb, tol=1e-10, m=6, k=4, U=U, C=C)
+    assert info["matvecs"] == 0
+    assert np.allclose(x, U @ (C.T @ bb), atol=1e-12 * np.linalg.norm(x))
+    x2, info2 = rbicgstab(op, bb, tol=1e-10, U=U, C=C)
+    assert info2["matvecs"] == 0
+    A = dense_matrix(grid, coef)
+    assert np.linalg.norm(bb - A @ x2) <= 1e-10 * np.linalg.norm(bb)
+
+
+def test_rbicgstab_residuals_orthogonal_to_c_and_solution_relation():
+    """Every updated rBiCGStab residual is ⟂ C (eq. rbicgstab-res: r lives in
+    the Krylov space of (I - C C^T) A), and after the postponed U update the
+    solution's true residual equals the updated one up to rounding
+    (eq. sol-update-from-res)."""
+    name, grid, coef, b = PROBS[2]
+    op = Stencil(grid, coef)
+    A = dense_matrix(grid, coef)
+    _, U, C, _ = rgcrot(op, b, tol=1e-11, m=8, k=5)
+    b2 = b + 0.1 * np.random.default_rng(4).standard_normal(b.size)
+    rs = []
+    x, info = rbicgstab(op, b2, tol=1e-9, U=U, C=C, max_restarts=0, callback=lambda r: rs.append(r.copy()))
+    assert len(rs) > 3
+    for r in rs:
+        assert np.linalg.norm(C.T @ r) <= 1e-10 * np.linalg.norm(b2)
+    rtrue = b2 - A @ x
+    assert np.linalg.norm(rtrue - rs[-1]) <= 1e-10 * np.linalg.norm(b2)
+
+
+def test_hybrid_sequence_reuses_space():
+    """Hybrid (Sec. 2.4): rGCROT builds U, C over the first steps, then
+    rBiCGStab reuses them frozen; every step converges."""
+    c = make_config(1, size=6)
+    op = Stencil(c.grid, c.coef)
+    seq = oracle.RecyclingSequence(op, mode="hybrid", m=8, k=6, tol=1e-9, hybrid_switch=2)
+    modes = []
+    for t in range(4):
+        x, info = seq.solve(c.rhs(t))
+        modes.append(info["mode"])
+        assert info["status"] == oracle.OK and info["relres_true"] <= 1e-9
+    assert modes == ["rGCROT", "rGCROT", "rBiCGStab", "rBiCGStab"]
+    assert seq.U.shape[1] == 6
+
+
+def test_zero_rhs():
+    name, grid, coef, b = PROBS[0]
+    op = Stencil(grid, coef)
+    z = np.zeros_like(b)
+    for f in (lambda: gmres(op, z), lambda: bicgstab(op, z), lambda: rbicgstab(op, z)):
+        x, info = f()
+        assert info["matvecs"] == 0 and np.all(x == 0)
+    x, U, C, info = rgcrot(op, z)
+    assert info["matvecs"] == 0 and np.all(x == 0)
