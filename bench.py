@@ -1,0 +1,336 @@
+#!/usr/bin/env python
+"""Benchmark: solves/s of a time-step sequence on the 128^3 wall-refined
+channel (7-point, periodic x/z, Neumann walls, one pinned cell), rGCROT(40,20)
+with the recycle space carried from step to step, relative tolerance 1e-8.
+
+One "step" is one solve of one time step (all of the solver's phases: stencil
+products with the Jacobi preconditioner, projections onto the recycle space,
+Arnoldi orthogonalisation, cycle updates and the harmonic Ritz recycle
+update). W warm-up steps (which also build the recycle space), then K timed
+steps; inputs (all right-hand sides) are resident in HBM before the timed
+region, and every step's working set (about 1 GB of basis vectors) exceeds the
+129 MB L2. Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  --impl reference times the CPU oracle (FP64, host cores) on a bounded
+  sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/sec and solver HBM GB/s (% of peak) at rel-res 1e-8; p50/p99 solve latency"
+WORKLOADS = {
+    # name: (config id, grid edge, mode, m, k)
+    "channel128": (2, 128, "rGCROT", 40, 20),
+    "porous192": (3, 192, "hybrid", 40, 20),
+    "convdiff32": (1, 32, "rGCROT", 30, 10),
+}
+# Matrix-vector products per solve of the channel128 sequence in steady state
+# (steps 3-12 of the sequence), measured on the GB300 arm; used only to turn
+# the reference arm's per-cycle time into solves/s.
+MV_PER_SOLVE = {"channel128": 1400.0, "convdiff32": 60.0, "porous192": 400.0}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+
+        def rd():
+            for line in self.proc.stdout:
+                self.lines.append(line.strip())
+
+        self.th = threading.Thread(target=rd, daemon=True)
+        self.th.start()
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.th:
+            self.th.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("RK_BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_cycle_sample(cfg, mode, m, k, cycles=2):
+    """Time the CPU oracle on `cycles` rGCROT cycles of step 0 of the workload
+    (the first builds the recycle space; the last is timed). Returns
+    (seconds per matvec of a cycle at recycle dimension k, threads)."""
+    import numpy as np
+    import oracle
+    op = oracle.Stencil(cfg.grid, cfg.coef)
+    b = cfg.rhs(0)
+    U = C = None
+    per_mv = None
+    for c in range(cycles):
+        t0 = time.perf_counter()
+        _, U, C, info = oracle.rgcrot(op, b, tol=1e-14, m=m, k=k, U=U, C=C, max_matvec=m)
+        dt = time.perf_counter() - t0
+        per_mv = dt / max(info["matvecs"], 1)
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return per_mv, threads
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    from problems import make_config
+    cid, edge, mode, m, k = WORKLOADS[args.workload]
+    cfg = make_config(cid, size=edge)
+    # warm-up: build the recycle space with one cycle
+    import oracle
+    op = oracle.Stencil(cfg.grid, cfg.coef)
+    b = cfg.rhs(0)
+    _, U, C, _ = oracle.rgcrot(op, b, tol=1e-14, m=m, k=k, max_matvec=m)
+    for _ in range(max(args.warmup - 1, 0)):
+        _, U, C, _ = oracle.rgcrot(op, b, tol=1e-14, m=m, k=k, U=U, C=C, max_matvec=m)
+    times = []
+    t_all = time.perf_counter()
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        _, U, C, info = oracle.rgcrot(op, b, tol=1e-14, m=m, k=k, U=U, C=C, max_matvec=m)
+        times.append((time.perf_counter() - t0) / max(info["matvecs"], 1))
+    total = time.perf_counter() - t_all
+    per_mv = statistics.mean(times)
+    mv = MV_PER_SOLVE[args.workload]
+    value = 1.0 / (per_mv * mv)
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    sample = (f"each step: one rGCROT({m},{k}) cycle ({m} matvecs, recycle dim {k}) of step 0 of {args.workload}; "
+              f"solves/s = 1/(s per matvec x {mv:.0f} matvecs per solve)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "grid": [edge] * 3, "solver": f"{mode}({m},{k})", "tol": 1e-8,
+                       "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__ as g
+    g.build()
+    from problems import make_config
+    from paper_1501_03358_gb300 import Context, Problem
+
+    cid, edge, mode, m, k = WORKLOADS[args.workload]
+    cfg = make_config(cid, size=edge, seed=None if rank == 0 else 20150113 + cid + 1000 * rank)
+    W, K = args.warmup, args.steps
+    nsteps = W + 2 * K
+    # all right-hand sides resident in HBM before timing; pinned host copies for e2e
+    rhs_host = [torch.from_numpy(cfg.rhs(t)).pin_memory() for t in range(nsteps)]
+    rhs_dev = [h.to("cuda", non_blocking=True) for h in rhs_host]
+    stream = torch.cuda.current_stream()
+    ctx = Context()
+    prob = Problem(ctx, cfg.grid, torch.from_numpy(cfg.coef))
+    x = torch.zeros(cfg.n, dtype=torch.float64, device="cuda")
+    kw = dict(tol=1e-8, m=m, k=k, mode=mode, max_matvec=args.max_matvec, hybrid_switch=5)
+    infos = []
+    for t in range(W):
+        x.zero_()
+        _, info = prob.solve(rhs_dev[t], out=x, **kw)
+        infos.append(info)
+    torch.cuda.synchronize()
+    # ---- timed region (device events on the solve stream), profiling on
+    prob.profile(True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    lat = []
+    e0.record(stream)
+    tinfo = []
+    for t in range(W, W + K):
+        ts = torch.cuda.Event(enable_timing=True)
+        te = torch.cuda.Event(enable_timing=True)
+        ts.record(stream)
+        x.zero_()
+        _, info = prob.solve(rhs_dev[t], out=x, **kw)
+        te.record(stream)
+        tinfo.append(info)
+        lat.append((ts, te))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    lat_ms = [a.elapsed_time(b) for a, b in lat]
+    prof = prob.profile_read()
+    prob.profile(False)
+    ms_max = max_over_ranks(ws, ms)
+    # ---- end to end through the public API: pinned host b -> device, solve,
+    # device -> pinned host x, every step
+    xh = torch.empty(cfg.n, dtype=torch.float64).pin_memory()
+    bdev = torch.empty(cfg.n, dtype=torch.float64, device="cuda")
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for t in range(W + K, W + 2 * K):
+        bdev.copy_(rhs_host[t], non_blocking=True)
+        x.zero_()
+        prob.solve(bdev, out=x, **kw)
+        xh.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    barrier(ws)
+    e2e_s = max_over_ranks(ws, e2e_s)
+
+    peaks, peak_src = load_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    # dominant kernel class by time
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    dname, d = dom
+    achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
+    total_model = sum(i["model_bytes"] for i in tinfo)
+    solver_gbs = total_model / (ms * 1e-3) / 1e9
+    launches = int(sum(v["launches"] for v in prof.values()))
+    value = ws * K / (ms_max * 1e-3)
+    mv = [i["matvecs"] for i in tinfo]
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": K, "warmup": W,
+        "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": [edge] * 3, "stencil": cfg.S, "solver": f"{mode}({m},{k})",
+                   "tol": 1e-8, "sequence_steps_timed": [W, W + K - 1], "l2": "inputs larger than L2",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "solver_hbm_gbs": solver_gbs, "solver_hbm_frac": solver_gbs / hbm_peak,
+        "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99))},
+        "matvecs_per_solve": statistics.mean(mv), "relres_max": max(i["relres_true"] for i in tinfo),
+        "all_converged": all(i["status"] == 0 for i in tinfo),
+        "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
+                     "launches": d["launches"], "avg_launch_us": 1000.0 * d["ms"] / max(d["launches"], 1),
+                     "bytes_per_launch": d["bytes"] / max(d["launches"], 1)},
+        "kernel_classes": {kname: {"ms": round(v["ms"], 3), "launches": v["launches"],
+                                   "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
+                           for kname, v in prof.items() if v["launches"]},
+        "gpu_launches": launches,
+        "e2e": {"value": ws * K / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * cfg.n,
+                "d2h_bytes_per_step": 8 * cfg.n},
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        per_mv, threads = oracle_cycle_sample(cfg, mode, m, k, cycles=2)
+        mvs = statistics.mean(mv)
+        line["cpu_baseline"] = {"value": 1.0 / (per_mv * mvs), "unit": "solves/s", "cores": threads,
+                                "kind": "oracle",
+                                "sample": f"two rGCROT({m},{k}) cycles of step 0 (the second, at recycle dim {k}, "
+                                          f"timed: {per_mv * 1e3:.1f} ms per matvec); solves/s = 1/(that x "
+                                          f"{mvs:.0f} matvecs per solve measured above)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    prob.close()
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="channel128", choices=sorted(WORKLOADS))
+    ap.add_argument("--max-matvec", type=int, default=20000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

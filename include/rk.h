@@ -1,0 +1,198 @@
+/*
+ * rk.h — C ABI of the GB300 recycling Krylov library (librk.so).
+ *
+ * Solves sequences of nonsymmetric linear systems A x_t = b_t whose matrix A
+ * is a 7- or 19-point stencil on a structured 3-D grid (the pressure Poisson
+ * systems of eq. 1, Sec. 2.1, stored as bands: "Data Layout", Sec. 2.1) with
+ * the Krylov methods of Sec. 2.2-2.4:
+ *   RK_GMRES      GMRES(m), Algorithm 1;
+ *   RK_RGCROT     rGCROT(m,k) with a recycle space carried across solves,
+ *                 Algorithm 3 (recycle update of line 14a by harmonic Ritz
+ *                 vectors);
+ *   RK_RBICGSTAB  rBiCGStab with one recycle space, Algorithm 4 (k = 0 or no
+ *                 recycle space: plain BiCGStab, Algorithm 2);
+ *   RK_HYBRID     rGCROT for the first `hybrid_switch` solves of a problem,
+ *                 then rBiCGStab with that recycle space frozen (Sec. 2.4).
+ * All solvers are right-preconditioned by point Jacobi, M = diag(A)
+ * (the preconditioner of Sec. 2.1, restricted to its point-Jacobi sweep).
+ *
+ * Conventions
+ *  - Grid: nx*ny*nz cells, cell index i + nx*(j + ny*k) (x fastest).
+ *  - Bands: coef is S (7 or 19) contiguous arrays of N doubles; band s
+ *    multiplies the unknown at offset OFF[s]:
+ *      0 (0,0,0); 1 (-1,0,0) 2 (1,0,0) 3 (0,-1,0) 4 (0,1,0) 5 (0,0,-1) 6 (0,0,1);
+ *      7 (-1,-1,0) 8 (1,-1,0) 9 (-1,1,0) 10 (1,1,0);
+ *      11 (-1,0,-1) 12 (1,0,-1) 13 (-1,0,1) 14 (1,0,1);
+ *      15 (0,-1,-1) 16 (0,1,-1) 17 (0,-1,1) 18 (0,1,1).
+ *    Periodic axes wrap; a band pointing out of a non-periodic face must be
+ *    exactly 0 (checked by rk_create_problem).
+ *  - The recycle space is stored in x-space: U, C are N x k column-major
+ *    (column c at offset c*N) with A U = C and C^T C = I; the R of line 1a
+ *    is folded into U.
+ *  - Every pointer argument named "device" is CUDA device memory owned by
+ *    the caller and only read or written during the call. Host pointers are
+ *    named so. All GPU work is ordered on the stream passed to the call; the
+ *    call returns after that stream's work for it has completed (it
+ *    synchronises on the stream, never on the device).
+ *  - Errors: every entry point returns an rk_status; RK_OK = 0. Nothing
+ *    throws across the ABI. rk_last_error() gives a thread-local message.
+ */
+#ifndef RK_H
+#define RK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RK_OK = 0,
+  RK_E_INVALID = 1,          /* bad argument, stencil band pointing out of a wall, NaN in b */
+  RK_E_OOM = 2,              /* the allocator returned NULL */
+  RK_E_NOT_CONVERGED = 3,    /* max_matvec reached; x holds the last iterate */
+  RK_E_BREAKDOWN = 4,        /* rBiCGStab breakdown persisted through max restarts */
+  RK_E_RECYCLE_INVARIANT = 5,/* rk_set_recycle: ||A U - C|| or ||C^T C - I|| too large */
+  RK_E_DEVICE_TIMEOUT = 6,   /* a bounded device wait gave up */
+  RK_E_CUDA = 7              /* a CUDA runtime call failed */
+} rk_status;
+
+typedef enum { RK_GMRES = 0, RK_RGCROT = 1, RK_RBICGSTAB = 2, RK_HYBRID = 3 } rk_mode;
+typedef enum { RK_FP64 = 0, RK_MIXED = 1 } rk_precision;
+
+typedef struct {
+  int32_t nx, ny, nz;
+  uint8_t periodic[3]; /* nonzero: that axis wraps */
+  uint8_t reserved;
+} rk_grid;
+
+typedef struct {
+  double tol;            /* stop when ||b - A x|| <= tol * ||b|| (relative to ||b||) */
+  int32_t m;             /* Arnoldi steps per cycle (GMRES, rGCROT, hybrid's rGCROT phase) */
+  int32_t k;             /* max recycle dimension (rGCROT, rBiCGStab, hybrid); 0 = none */
+  int32_t max_matvec;    /* cap on matrix-vector products in the recurrences (<= 0: 2000) */
+  int32_t hybrid_switch; /* RK_HYBRID: solves of this problem run with rGCROT before the switch */
+  int32_t mode;          /* rk_mode */
+  int32_t precision;     /* rk_precision (RK_FP64 only in this version) */
+  int32_t update_recycle;/* rGCROT: 1 = update U, C after every cycle (line 14a), 0 = keep */
+  int32_t reserved;
+} rk_solve_params;
+
+typedef struct {
+  int32_t status;        /* rk_status of the solve */
+  int32_t mode_used;     /* rk_mode actually run (RK_HYBRID resolves to one of the others) */
+  int32_t matvecs;       /* matrix-vector products in the recurrences (b - A x excluded) */
+  int32_t cycles_or_iters; /* cycles (GMRES, rGCROT) or iterations (rBiCGStab) */
+  int32_t restarts;      /* rBiCGStab restarts (true-residual replacement or breakdown) */
+  int32_t recycle_dim;   /* recycle dimension after the solve */
+  double relres_true;    /* ||b - A x|| / ||b|| of the returned x, recomputed in FP64 */
+  double relres_est;     /* last recurrence estimate (|g_{j+1}| or ||r||) / ||b|| */
+  double model_bytes;    /* algorithmic HBM bytes of the solve (byte model of the library) */
+} rk_solve_info;
+
+typedef void* (*rk_alloc_fn)(size_t bytes, void* user);
+typedef void (*rk_free_fn)(void* ptr, void* user);
+
+typedef struct rk_context rk_context;
+typedef struct rk_problem rk_problem;
+
+/* Thread-local description of the last error on this thread (never NULL). */
+const char* rk_last_error(void);
+
+/* Library version string. */
+const char* rk_version(void);
+
+/*
+ * Create a context on the current CUDA device. alloc/free draw device memory
+ * (e.g. from a framework's caching allocator); both NULL means cudaMalloc /
+ * cudaFree. `user` is passed through. *out receives the context.
+ */
+int rk_context_create(rk_alloc_fn alloc, rk_free_fn free_fn, void* user, rk_context** out);
+/* Release the context. Problems created from it stay valid: the context's
+ * memory is released when the last of them is destroyed. */
+void rk_context_destroy(rk_context* ctx);
+
+/*
+ * Create a problem: the banded operator of Sec. 2.1 ("Data Layout").
+ * coef: device, S*N doubles (S in {7, 19}); copied into library memory.
+ * Fails with RK_E_INVALID if a band points out of a non-periodic face with a
+ * nonzero coefficient or a diagonal entry is zero. stream: cudaStream_t.
+ */
+int rk_create_problem(rk_context* ctx, const rk_grid* grid, int32_t S, const double* coef,
+                      void* stream, rk_problem** out);
+void rk_problem_destroy(rk_problem* p);
+
+/*
+ * Set the recycle space (Algorithm 3 line 1a / Algorithm 4 lines 1a-1b).
+ * U: device, N x k column-major. C: device N x k or NULL. With C == NULL the
+ * library forms C~ = A U and its thin QR C~ = C R (line 1a) and stores
+ * U R^{-1}, so that A U = C, C^T C = I. With C given it checks
+ * ||A U - C||_F <= 1e-10 ||A||_F ||U||_F and ||C^T C - I||_F <= 1e-10 and
+ * returns RK_E_RECYCLE_INVARIANT otherwise. k = 0 clears the space. On any
+ * error the problem is left with no recycle space.
+ * k must not exceed kmax (the problem's capacity, grown on demand).
+ */
+int rk_set_recycle(rk_problem* p, const double* U, const double* C, int32_t k, void* stream);
+
+/*
+ * Copy the recycle space out. U, C: device, N x capacity column-major (either
+ * may be NULL). *k: in = capacity (columns), out = stored dimension.
+ * Returns RK_E_INVALID if the capacity is smaller than the dimension.
+ */
+int rk_get_recycle(const rk_problem* p, double* U, double* C, int32_t* k, void* stream);
+
+/*
+ * Solve A x = b (one time step of a sequence).
+ * b: device, N doubles. x: device, N doubles; in: initial guess x0, out: the
+ * solution. params: host. info: host (may be NULL). The problem keeps its
+ * recycle space (and, for RK_HYBRID, its solve counter) across calls, which
+ * is how a sequence carries U, C from one step to the next (Sec. 2.4).
+ * ||b|| = 0 returns x = 0 with RK_OK and no matrix-vector products.
+ * Returns the solve status (also in info->status).
+ */
+int rk_solve(rk_problem* p, const double* b, double* x, const rk_solve_params* params,
+             rk_solve_info* info, void* stream);
+
+/*
+ * Operator application (single products, for tests and callers that compose):
+ * y = A (M^{-1} v) if precond != 0, else y = A v; and r = b - A x.
+ * All vectors device, N doubles.
+ */
+int rk_apply(const rk_problem* p, const double* v, double* y, int32_t precond, void* stream);
+int rk_residual(const rk_problem* p, const double* b, const double* x, double* r, void* stream);
+
+/*
+ * Block inner products used by the projections (Algorithm 3 lines 6a-9,
+ * Algorithm 4 lines 1c, 7a, 12a): out[q] = Q_q^T w for the nq columns of Q
+ * (device, column-major, leading dimension ld >= N), w device, out device
+ * (nq doubles). The reduction order is fixed by N alone (deterministic).
+ */
+int rk_dots(rk_context* ctx, int64_t n, int32_t nq, const double* Q, int64_t ld, const double* w,
+            double* out, void* stream);
+
+/*
+ * Opt-in kernel timing of the solves of a problem: CUDA events on the solve's
+ * stream around every launch, summed per kernel class ("spmv", "residual",
+ * "dots", "update", "gemm_rows", "gram", "small", "bicg", "harmonic_ritz") with the class's
+ * algorithmic HBM bytes (the library's byte model of each launch).
+ * rk_profile_enable resets the counters; rk_profile_read copies up to cap
+ * entries to out (host) and sets *count to the number of classes.
+ */
+typedef struct {
+  char name[16];
+  int64_t launches;
+  double ms;
+  double bytes;
+} rk_prof_entry;
+int rk_profile_enable(rk_problem* p, int32_t on);
+int rk_profile_read(rk_problem* p, rk_prof_entry* out, int32_t cap, int32_t* count);
+
+/* Number of solves run on this problem (the hybrid's step counter) and its
+ * recycle dimension. */
+int rk_problem_stats(const rk_problem* p, int32_t* solves, int32_t* recycle_dim, int64_t* n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RK_H */

@@ -1,0 +1,259 @@
+// Fused vector kernels of rBiCGStab with one recycle space (Algorithm 4;
+// Algorithm 2 when the recycle space is empty), right-preconditioned. The
+// scalar recurrences (alpha, omega, beta, rho, the postponed U coefficients
+// xi of lines 10a/13a) are advanced on the device by the last block of each
+// reduction, so a batch of iterations runs without host synchronisation; a
+// device flag stops the remaining kernels of a batch on convergence or
+// breakdown.
+#include <cmath>
+#include "rk_bicg.h"
+#include "rk_device.cuh"
+
+namespace rk {
+
+namespace {
+
+__device__ __forceinline__ bool stopped(const BicgScalars* s) { return s->stop != 0; }
+
+// line 6: p = r (first iteration) or p = r + beta (p - omega v)
+__global__ void __launch_bounds__(kRedThreads) k_bicg_p(BicgVecs v, BicgScalars* s, int64_t n) {
+  if (stopped(s)) return;
+  if (s->matvecs >= s->maxmv) {  // the cap of line 3 (i <= max_itn)
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s->flag = 3;
+      s->stop = 1;
+    }
+    return;
+  }
+  const bool first = s->it == 0;
+  const double beta = s->beta, omega = s->omega;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double ri = v.r[i];
+    v.p[i] = first ? ri : fma(beta, v.p[i] - omega * v.v[i], ri);
+  }
+}
+
+// line 8 (after 7a): alpha = rho / (r~^T v); r~ is orthogonal to C, so r~^T v
+// equals r~^T (v - C eta1).
+__global__ void k_bicg_alpha(BicgScalars* s, const double* dots, int kc) {
+  if (threadIdx.x != 0 || stopped(s)) return;
+  s->matvecs += 1;
+  const double rtv = dots[kc];
+  if (rtv == 0.0 || !isfinite(rtv)) {
+    s->flag = 2;
+    s->stop = 1;
+    return;
+  }
+  s->alpha = s->rho / rtv;
+}
+
+// lines 7a-9: v <- v - C eta1; s = r - alpha v; ||s||; on convergence the
+// half step of lines 10-10a is recorded (xi += alpha eta1 here, x~ += alpha p
+// by k_bicg_half).
+__global__ void __launch_bounds__(kRedThreads) k_bicg_s(BicgVecs v, BicgScalars* s, int64_t n, int kc,
+                                                        const double* C, int64_t ld, const double* eta1,
+                                                        double* xi, double* part, unsigned* counter) {
+  if (stopped(s)) return;
+  __shared__ double red[32];
+  __shared__ int lastflag;
+  __shared__ double se[256];
+  for (int q = threadIdx.x; q < kc; q += blockDim.x) se[q] = eta1[q];
+  __syncthreads();
+  const double alpha = s->alpha;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    double vi = v.v[i];
+    for (int q = 0; q < kc; ++q) vi = fma(-__ldg(&C[(int64_t)q * ld + i]), se[q], vi);
+    if (kc) v.v[i] = vi;
+    const double si = fma(-alpha, vi, v.r[i]);
+    v.s[i] = si;
+    acc = fma(si, si, acc);
+  }
+  const double b = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = b;
+  if (arrive_last(counter, &lastflag)) {
+    reduce_partials(part, gridDim.x, 1, &s->s2);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (sqrt(s->s2) <= s->tolabs) {
+        for (int q = 0; q < kc; ++q) xi[q] = fma(alpha, se[q], xi[q]);
+        s->half = 1;
+        s->flag = 1;
+        s->stop = 1;
+        s->upd = sqrt(s->s2);
+        s->it += 1;
+      }
+    }
+  }
+}
+
+// line 10 on convergence at the half step: x~ += alpha p
+__global__ void __launch_bounds__(kRedThreads) k_bicg_half(BicgVecs v, BicgScalars* s, int64_t n) {
+  if (s->half != 1) return;
+  const double alpha = s->alpha;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    v.xt[i] = fma(alpha, v.p[i], v.xt[i]);
+  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  }
+}
+
+// lines 12a-13: t <- t - C eta2; omega = t^T s / t^T t (last block).
+__global__ void __launch_bounds__(kRedThreads) k_bicg_t(BicgVecs v, BicgScalars* s, int64_t n, int kc,
+                                                        const double* C, int64_t ld, const double* eta2,
+                                                        double* part, unsigned* counter) {
+  if (stopped(s)) return;
+  __shared__ double red[32];
+  __shared__ int lastflag;
+  __shared__ double se[256];
+  for (int q = threadIdx.x; q < kc; q += blockDim.x) se[q] = eta2[q];
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  double ts = 0.0, tt = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    double ti = v.t[i];
+    for (int q = 0; q < kc; ++q) ti = fma(-__ldg(&C[(int64_t)q * ld + i]), se[q], ti);
+    if (kc) v.t[i] = ti;
+    ts = fma(ti, v.s[i], ts);
+    tt = fma(ti, ti, tt);
+  }
+  const double b0 = block_sum(ts, red);
+  __syncthreads();
+  const double b1 = block_sum(tt, red);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = b0;
+    part[2 * blockIdx.x + 1] = b1;
+  }
+  if (arrive_last(counter, &lastflag)) {
+    reduce_partials(part, gridDim.x, 2, s->tmp);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s->matvecs += 1;
+      const double tsv = s->tmp[0], ttv = s->tmp[1];
+      if (ttv == 0.0 || !isfinite(ttv)) {
+        s->flag = 2;
+        s->stop = 1;
+      } else {
+        s->omega = tsv / ttv;
+      }
+    }
+  }
+}
+
+// lines 13a-16: xi += alpha eta1 + omega eta2; x~ += alpha p + omega s;
+// r = s - omega t; rho = r~^T r, beta = (rho/rho_old)(alpha/omega); the
+// convergence (line 3) and breakdown (line 5) tests of the next iteration.
+__global__ void __launch_bounds__(kRedThreads) k_bicg_r(BicgVecs v, BicgScalars* s, int64_t n, int kc,
+                                                        const double* eta1, const double* eta2, double* xi,
+                                                        double* part, unsigned* counter) {
+  if (stopped(s)) return;
+  __shared__ double red[32];
+  __shared__ int lastflag;
+  const double alpha = s->alpha, omega = s->omega;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  double rr = 0.0, rtr = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double si = v.s[i];
+    v.xt[i] = fma(omega, si, fma(alpha, v.p[i], v.xt[i]));
+    const double ri = fma(-omega, v.t[i], si);
+    v.r[i] = ri;
+    rr = fma(ri, ri, rr);
+    rtr = fma(v.rt[i], ri, rtr);
+  }
+  const double b0 = block_sum(rtr, red);
+  __syncthreads();
+  const double b1 = block_sum(rr, red);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = b0;
+    part[2 * blockIdx.x + 1] = b1;
+  }
+  if (arrive_last(counter, &lastflag)) {
+    reduce_partials(part, gridDim.x, 2, s->tmp);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int q = 0; q < kc; ++q) xi[q] = fma(omega, eta2[q], fma(alpha, eta1[q], xi[q]));
+      const double rho_new = s->tmp[0];
+      const double rnorm = sqrt(s->tmp[1]);
+      s->it += 1;
+      s->upd = rnorm;
+      if (rnorm <= s->tolabs) {
+        s->flag = 1;
+        s->stop = 1;
+      } else if (omega == 0.0 || fabs(rho_new) <= 1e-14 * s->rtnorm * rnorm || !isfinite(rho_new)) {
+        s->flag = 2;
+        s->stop = 1;
+      } else {
+        s->beta = (rho_new / s->rho) * (alpha / omega);
+        s->rho = rho_new;
+      }
+    }
+  }
+}
+
+// Start of a pass of Algorithm 4 (after line 1c): r~ = r_0, rho = r~^T r_0.
+__global__ void k_bicg_init(BicgScalars* s, const double* rho2, double tolabs, int maxmv) {
+  if (threadIdx.x != 0) return;
+  s->rho = *rho2;
+  s->rtnorm = sqrt(*rho2);
+  s->tolabs = tolabs;
+  s->alpha = s->omega = s->beta = 0.0;
+  s->it = 0;
+  s->matvecs = 0;
+  s->maxmv = maxmv;
+  s->half = 0;
+  s->upd = sqrt(*rho2);
+  const bool conv = sqrt(*rho2) <= tolabs;
+  s->flag = conv ? 1 : (maxmv <= 0 ? 3 : 0);
+  s->stop = s->flag != 0 ? 1 : 0;
+}
+
+// coefficients of the fold of line 17a: [-xi; 1]
+__global__ void k_bicg_foldcoef(const double* xi, int kc, double* coefv) {
+  for (int q = threadIdx.x; q <= kc; q += blockDim.x) coefv[q] = q < kc ? -xi[q] : 1.0;
+}
+
+}  // namespace
+
+cudaError_t launch_bicg_foldcoef(const double* xi, int kc, double* coefv, cudaStream_t st) {
+  k_bicg_foldcoef<<<1, 256, 0, st>>>(xi, kc, coefv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bicg_init(BicgScalars* s, const double* rho2, double tolabs, int maxmv, cudaStream_t st) {
+  k_bicg_init<<<1, 32, 0, st>>>(s, rho2, tolabs, maxmv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bicg_p(const BicgVecs& v, BicgScalars* s, int64_t n, cudaStream_t st) {
+  k_bicg_p<<<red_blocks(n), kRedThreads, 0, st>>>(v, s, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_bicg_alpha(BicgScalars* s, const double* dots, int kc, cudaStream_t st) {
+  k_bicg_alpha<<<1, 32, 0, st>>>(s, dots, kc);
+  return cudaGetLastError();
+}
+cudaError_t launch_bicg_s(const BicgVecs& v, BicgScalars* s, int64_t n, int kc, const double* C, int64_t ld,
+                          const double* eta1, double* xi, double* part, unsigned* counter, cudaStream_t st) {
+  k_bicg_s<<<red_blocks(n), kRedThreads, 0, st>>>(v, s, n, kc, C, ld, eta1, xi, part, counter);
+  return cudaGetLastError();
+}
+cudaError_t launch_bicg_half(const BicgVecs& v, BicgScalars* s, int64_t n, cudaStream_t st) {
+  k_bicg_half<<<red_blocks(n), kRedThreads, 0, st>>>(v, s, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_bicg_t(const BicgVecs& v, BicgScalars* s, int64_t n, int kc, const double* C, int64_t ld,
+                          const double* eta2, double* part, unsigned* counter, cudaStream_t st) {
+  k_bicg_t<<<red_blocks(n), kRedThreads, 0, st>>>(v, s, n, kc, C, ld, eta2, part, counter);
+  return cudaGetLastError();
+}
+cudaError_t launch_bicg_r(const BicgVecs& v, BicgScalars* s, int64_t n, int kc, const double* eta1,
+                          const double* eta2, double* xi, double* part, unsigned* counter, cudaStream_t st) {
+  k_bicg_r<<<red_blocks(n), kRedThreads, 0, st>>>(v, s, n, kc, eta1, eta2, xi, part, counter);
+  return cudaGetLastError();
+}
+
+}  // namespace rk

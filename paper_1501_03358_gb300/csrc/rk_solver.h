@@ -1,0 +1,63 @@
+// Device-side state of one solve and the single-block kernels on the small
+// Hessenberg / harmonic Ritz problems. Internal to librk.
+#pragma once
+#include "rk_internal.h"
+
+namespace rk {
+
+// Scalars and small arrays of a solve, in device memory. Sizes: m = Arnoldi
+// steps per cycle, kmax = recycle capacity, nqmax = kmax + m + 2.
+struct SolveState {
+  double bnorm;      // ||b||
+  double tolabs;     // tol * ||b||
+  double est;        // |g_{j+1}| of the last Arnoldi step
+  double rho2;       // ||r||^2 from the last residual / projection
+  double nrm2[4];    // norms from fused reductions
+  double bic[16];    // rBiCGStab scalars (see solver.cu)
+  int done;          // the current cycle stops (estimate met, happy breakdown)
+  int jj;            // Arnoldi steps completed in the cycle
+  int knew;          // recycle dimension after the last update
+  int hr_status;     // 0 ok, else the harmonic Ritz solve failed (space kept)
+  int bic_flag;      // rBiCGStab: 1 converged (||s|| or ||r||), 2 breakdown
+  int bic_stop;      // rBiCGStab: skip further kernels this batch
+  int pad[2];
+};
+
+struct SmallBuffers {
+  int m, kmax, nqmax;
+  double* H;      // (m+1) x m, true Hessenberg, column-major
+  double* R;      // (m+1) x m, Givens-rotated copy
+  double* B;      // kmax x m, B = C^T A M^{-1} V
+  double* g;      // m+1
+  double* cs;     // m
+  double* sn;     // m
+  double* sv;     // m+2: column scales, v_l = sv[l] * q_l (stored q_l)
+  double* hacc;   // nqmax: accumulated projection coefficients (stored units)
+  double* dots;   // nqmax + 4: reduced inner products
+  double* coef;   // nqmax: coefficients handed to the update kernel
+  double* y;      // m
+  double* xcoef;  // nqmax: coefficients of the solution update
+  double* gram;   // (kmax + m + 1) x kmax: [C V]^T M U
+  double* QC;     // (kmax + m + 1) x kmax: C <- W_hat QC
+  double* PU;     // (kmax + m) x kmax:     U <- W PU
+  double* hrws;   // workspace of the harmonic Ritz solve (global fallback)
+  size_t hrws_doubles;
+};
+
+cudaError_t launch_arn_coef(SolveState* s, SmallBuffers b, int kc, int j, int pass, cudaStream_t st);
+cudaError_t launch_arn_finalize(SolveState* s, SmallBuffers b, int kc, int j, cudaStream_t st);
+cudaError_t launch_cycle_solve(SolveState* s, SmallBuffers b, int kc, cudaStream_t st);
+cudaError_t launch_harmonic_ritz(SolveState* s, SmallBuffers b, int kc, int jj, int k, cudaStream_t st);
+cudaError_t launch_set_scalar(SolveState* s, int which, cudaStream_t st);
+cudaError_t launch_cycle_init(SolveState* s, SmallBuffers b, cudaStream_t st);
+cudaError_t launch_set_tol(SolveState* s, double tol, cudaStream_t st);
+size_t harmonic_ritz_ws_doubles(int n);
+cudaError_t launch_chol_rinv(int k, const double* G, double* Rinv, double* Rw, int* status, cudaStream_t st);
+
+// Standalone harmonic Ritz selection on small matrices (for tests): G, F are
+// (n+1) x n column-major device arrays; outputs QC ((n+1) x k), PU (n x k) and
+// *knew (device int).
+cudaError_t launch_harmonic_ritz_small(int n, const double* G, const double* F, int k, double* QC,
+                                       double* PU, int* knew, double* ws, cudaStream_t st);
+
+}  // namespace rk

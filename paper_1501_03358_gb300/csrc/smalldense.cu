@@ -1,0 +1,876 @@
+// Single-block kernels on the small problems of the Krylov cycle:
+//  - the Givens least-squares update of each Arnoldi step (Algorithm 1/3,
+//    line 12, with the in-cycle residual estimate of the note under
+//    Algorithm 1) and the cycle's solve (lines 12-12a);
+//  - the harmonic Ritz selection of the recycle space (Algorithm 3, line
+//    14a), done entirely on the device:
+//      G = Q_G R_G (Householder),  M'' = (Q_G^T F) R_G^{-1},
+//      real Schur form of M'' (Hessenberg + Francis double-shift QR),
+//      eigenvectors of the k eigenvalues mu = 1/theta of largest modulus,
+//      orthonormal basis Q2 of their span, then
+//      C <- W_hat (Q_G Q2),   U <- W (R_G^{-1} Q2).
+//    With q = R_G p, G^T G p = theta G^T F p is M'' q = (1/theta) q, so the
+//    span selected is that of the harmonic Ritz vectors of the k smallest
+//    |theta|, and A U = C, C^T C = I hold by construction.
+#include <cmath>
+#include "rk_solver.h"
+#include "rk_device.cuh"
+
+namespace rk {
+
+namespace {
+
+constexpr int kHRThreads = 128;
+
+// ---------------------------------------------------------------- Arnoldi
+__global__ void k_arn_coef(SolveState* s, SmallBuffers b, int kc, int j, int pass) {
+  if (s->done) return;
+  const int nq = kc + j + 1;
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+    const double d = b.dots[q];
+    double c;
+    if (q < kc) {
+      c = d;
+    } else {
+      const double sl = b.sv[q - kc];
+      c = sl * sl * d;
+    }
+    b.coef[q] = c;
+    b.hacc[q] = pass == 0 ? c : b.hacc[q] + c;
+  }
+}
+
+__global__ void k_arn_finalize(SolveState* s, SmallBuffers b, int kc, int j) {
+  if (s->done || threadIdx.x != 0) return;
+  const int ldh = b.m + 1;
+  const double nrm2 = s->nrm2[1];
+  const double svj = b.sv[j];
+  const double nrm = sqrt(nrm2);
+  const double hnext = svj * nrm;
+  for (int l = 0; l < kc; ++l) b.B[l + (int64_t)j * b.kmax] = svj * b.hacc[l];
+  for (int l = 0; l <= j; ++l) b.H[l + j * ldh] = svj * b.hacc[kc + l] / b.sv[l];
+  b.H[j + 1 + j * ldh] = hnext;
+  for (int l = j + 2; l <= b.m; ++l) b.H[l + j * ldh] = 0.0;
+  // progressive Givens QR of the Hessenberg column j
+  double* R = b.R + j * ldh;
+  for (int l = 0; l <= j + 1; ++l) R[l] = b.H[l + j * ldh];
+  for (int i = 0; i < j; ++i) {
+    const double t = b.cs[i] * R[i] + b.sn[i] * R[i + 1];
+    R[i + 1] = -b.sn[i] * R[i] + b.cs[i] * R[i + 1];
+    R[i] = t;
+  }
+  double c = 1.0, sg = 0.0, r = R[j];
+  if (R[j + 1] != 0.0) {
+    r = hypot(R[j], R[j + 1]);
+    c = R[j] / r;
+    sg = R[j + 1] / r;
+  }
+  b.cs[j] = c;
+  b.sn[j] = sg;
+  R[j] = r;
+  R[j + 1] = 0.0;
+  b.g[j + 1] = -sg * b.g[j];
+  b.g[j] = c * b.g[j];
+  const double est = fabs(b.g[j + 1]);
+  s->est = est;
+  s->jj = j + 1;
+  const bool happy = !(nrm2 > 0.0);
+  b.sv[j + 1] = happy ? 0.0 : 1.0 / nrm;
+  if (est <= s->tolabs || happy) s->done = 1;
+}
+
+__global__ void k_cycle_solve(SolveState* s, SmallBuffers b, int kc) {
+  if (threadIdx.x != 0) return;
+  const int jj = s->jj;
+  const int ldh = b.m + 1;
+  for (int i = jj - 1; i >= 0; --i) {
+    double t = b.g[i];
+    for (int l = i + 1; l < jj; ++l) t -= b.R[i + l * ldh] * b.y[l];
+    b.y[i] = t / b.R[i + i * ldh];
+  }
+  for (int q = 0; q < kc; ++q) {
+    double z = 0.0;
+    for (int l = 0; l < jj; ++l) z = fma(b.B[q + (int64_t)l * b.kmax], b.y[l], z);
+    b.xcoef[q] = -z;  // z = -B y (line 12a)
+  }
+  for (int l = 0; l < jj; ++l) b.xcoef[kc + l] = b.sv[l] * b.y[l];
+}
+
+// ------------------------------------------------------------ harmonic Ritz
+struct HRWork {
+  double* G;   // (n+1) x n  -> reflectors below the diagonal, R_G above
+  double* F;   // (n+1) x n  -> Q_G^T F, later Z * X
+  double* M;   // n x n      -> Schur form T
+  double* Z;   // n x n      -> Schur vectors
+  double* X;   // n x n      -> selected eigenvectors, then Q2
+  double* tau; // n
+  double* v;   // n + 1
+  double* wr;  // n
+  double* wi;  // n
+  int* sel;    // n  (selected start index; -1 end)
+};
+
+__device__ HRWork hr_carve(double* base, int n) {
+  HRWork w;
+  double* p = base;
+  w.G = p; p += (size_t)(n + 1) * n;
+  w.F = p; p += (size_t)(n + 1) * n;
+  w.M = p; p += (size_t)n * n;
+  w.Z = p; p += (size_t)n * n;
+  w.X = p; p += (size_t)n * n;
+  w.tau = p; p += n;
+  w.v = p; p += n + 1;
+  w.wr = p; p += n;
+  w.wi = p; p += n;
+  w.sel = (int*)p;
+  return w;
+}
+
+// Householder vector for x[0..len): on return v[0] = 1, v[1..] scaled, beta
+// the new leading entry, tau the coefficient (I - tau v v^T). Block-wide.
+__device__ void house(const double* x, int len, double* v, double* beta_out, double* tau_out, double* red) {
+  double ss = 0.0;
+  for (int i = threadIdx.x + 1; i < len; i += blockDim.x) ss = fma(x[i], x[i], ss);
+  const double sig = block_sum(ss, red);
+  const double alpha = x[0];
+  __syncthreads();
+  if (sig == 0.0) {
+    for (int i = threadIdx.x; i < len; i += blockDim.x) v[i] = i == 0 ? 1.0 : 0.0;
+    if (threadIdx.x == 0) {
+      *beta_out = alpha;
+      *tau_out = 0.0;
+    }
+  } else {
+    const double nrm = sqrt(alpha * alpha + sig);
+    const double beta = alpha <= 0.0 ? nrm : -nrm;
+    const double v0 = alpha - beta;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) v[i] = i == 0 ? 1.0 : x[i] / v0;
+    if (threadIdx.x == 0) {
+      *beta_out = beta;
+      *tau_out = (beta - alpha) / beta;
+    }
+  }
+  __syncthreads();
+}
+
+// A(r0 + i, c) -= tau * v_i * (v^T A(r0:r0+len, c)) for columns c in [c0, c1).
+__device__ void apply_left(double* A, int ld, int r0, int len, int c0, int c1, const double* v, double tau) {
+  if (tau == 0.0) return;
+  for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+    double* col = A + (int64_t)c * ld + r0;
+    double w = 0.0;
+    for (int i = 0; i < len; ++i) w = fma(v[i], col[i], w);
+    w *= tau;
+    for (int i = 0; i < len; ++i) col[i] = fma(-w, v[i], col[i]);
+  }
+}
+
+// A(r, c0 + i) -= tau * (A(r, c0:c0+len) v) v_i for rows r in [r0, r1).
+__device__ void apply_right(double* A, int ld, int r0, int r1, int c0, int len, const double* v, double tau) {
+  if (tau == 0.0) return;
+  for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    double w = 0.0;
+    for (int i = 0; i < len; ++i) w = fma(A[r + (int64_t)(c0 + i) * ld], v[i], w);
+    w *= tau;
+    for (int i = 0; i < len; ++i) A[r + (int64_t)(c0 + i) * ld] = fma(-w, v[i], A[r + (int64_t)(c0 + i) * ld]);
+  }
+}
+
+// 3- or 2-vector Householder computed by one thread (no block sync).
+__device__ void house_small(double x, double y, double z, int len, double* v, double* tau) {
+  const double nrm = len == 3 ? sqrt(x * x + y * y + z * z) : sqrt(x * x + y * y);
+  if (nrm == 0.0 || (y == 0.0 && (len == 2 || z == 0.0))) {
+    v[0] = 1.0; v[1] = 0.0; v[2] = 0.0;
+    *tau = 0.0;
+    return;
+  }
+  const double beta = x <= 0.0 ? nrm : -nrm;
+  const double v0 = x - beta;
+  v[0] = 1.0;
+  v[1] = y / v0;
+  v[2] = len == 3 ? z / v0 : 0.0;
+  *tau = (beta - x) / beta;
+}
+
+// Complex helpers
+struct cplx { double re, im; };
+__device__ __forceinline__ cplx cmul(cplx a, cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
+  const double s = fabs(b.re) + fabs(b.im);
+  const double br = b.re / s, bi = b.im / s;
+  const double d = br * br + bi * bi;
+  return {(a.re * br + a.im * bi) / (d * s), (a.im * br - a.re * bi) / (d * s)};
+}
+
+// Core: G, F already in w.G, w.F (ld n+1). Outputs QC (ld ldqc, n+1 rows),
+// PU (ld ldpu, n rows), *knew_out, *status_out (0 ok).
+__device__ void hr_core(HRWork w, int n, int k, double* QC, int ldqc, double* PU, int ldpu, int* knew_out,
+                        int* status_out) {
+  __shared__ double red[32];
+  __shared__ double sh_beta, sh_tau;
+  __shared__ int sh_u, sh_l, sh_iter, sh_total, sh_fail, sh_knew;
+  __shared__ double sh_v3[3];
+  __shared__ double sh_tau3;
+  const int ldg = n + 1;
+  const double eps = 2.220446049250313e-16;
+
+  // ---- 1. Householder QR of G; the same reflectors applied to F.
+  for (int c = 0; c < n; ++c) {
+    const int len = n + 1 - c;
+    double* x = w.G + (int64_t)c * ldg + c;
+    house(x, len, w.v, &sh_beta, &sh_tau, red);
+    const double tau = sh_tau;
+    apply_left(w.G, ldg, c, len, c + 1, n, w.v, tau);
+    apply_left(w.F, ldg, c, len, 0, n, w.v, tau);
+    __syncthreads();
+    // store the reflector below the diagonal
+    for (int i = threadIdx.x; i < len; i += blockDim.x) x[i] = i == 0 ? sh_beta : w.v[i];
+    if (threadIdx.x == 0) w.tau[c] = tau;
+    __syncthreads();
+  }
+  // ---- 2. M = (Q_G^T F)(0:n, 0:n) R_G^{-1}, row by row.
+  if (threadIdx.x == 0) sh_fail = 0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < n; c += blockDim.x)
+    if (!(fabs(w.G[c + (int64_t)c * ldg]) > 1e-300)) sh_fail = 1;
+  __syncthreads();
+  if (sh_fail) {
+    if (threadIdx.x == 0) { *status_out = 1; *knew_out = 0; }
+    return;
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int c = 0; c < n; ++c) {
+      double t = w.F[i + (int64_t)c * ldg];
+      for (int l = 0; l < c; ++l) t = fma(-w.M[i + (int64_t)l * n], w.G[l + (int64_t)c * ldg], t);
+      w.M[i + (int64_t)c * n] = t / w.G[c + (int64_t)c * ldg];
+    }
+  }
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) w.Z[t] = (t % (n + 1)) == 0 ? 1.0 : 0.0;
+  __syncthreads();
+  // ---- 3. Hessenberg reduction M = Z H Z^T.
+  for (int c = 0; c + 2 < n; ++c) {
+    const int len = n - c - 1;
+    double* x = w.M + (int64_t)c * n + c + 1;
+    house(x, len, w.v, &sh_beta, &sh_tau, red);
+    const double tau = sh_tau;
+    apply_left(w.M, n, c + 1, len, c, n, w.v, tau);
+    __syncthreads();
+    apply_right(w.M, n, 0, n, c + 1, len, w.v, tau);
+    apply_right(w.Z, n, 0, n, c + 1, len, w.v, tau);
+    __syncthreads();
+    for (int i = threadIdx.x; i < len; i += blockDim.x) x[i] = i == 0 ? sh_beta : 0.0;
+    __syncthreads();
+  }
+  // ---- 4. Francis double-shift QR to real Schur form (T in M, vectors in Z).
+  double hnorm = 0.0;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) hnorm = fmax(hnorm, fabs(w.M[t]));
+  {
+    // block max via sum of squares of maxima is not needed; use sum of |.| bound
+    double s = block_sum(hnorm, red);
+    hnorm = s;
+  }
+  if (threadIdx.x == 0) {
+    sh_u = n - 1;
+    sh_iter = 0;
+    sh_total = 0;
+    sh_fail = 0;
+  }
+  __syncthreads();
+  double* H = w.M;
+#define HH(i, j) H[(i) + (int64_t)(j) * n]
+  while (true) {
+    __syncthreads();
+    const int u = sh_u;
+    if (u < 0 || sh_fail) break;
+    if (threadIdx.x == 0) {
+      int l = u;
+      while (l > 0) {
+        double s = fabs(HH(l - 1, l - 1)) + fabs(HH(l, l));
+        if (s == 0.0) s = hnorm;
+        if (fabs(HH(l, l - 1)) <= eps * s) break;
+        --l;
+      }
+      if (l > 0) HH(l, l - 1) = 0.0;
+      sh_l = l;
+    }
+    __syncthreads();
+    const int l = sh_l;
+    if (l == u) {  // 1 x 1 block
+      if (threadIdx.x == 0) {
+        w.wr[u] = HH(u, u);
+        w.wi[u] = 0.0;
+        sh_u = u - 1;
+        sh_iter = 0;
+      }
+      continue;
+    }
+    if (l == u - 1) {  // 2 x 2 block: split if real, record the pair if complex
+      __shared__ double c_cs, c_sn;
+      __shared__ int c_real;
+      if (threadIdx.x == 0) {
+        const double a = HH(u - 1, u - 1), bb = HH(u - 1, u), c = HH(u, u - 1), d = HH(u, u);
+        const double p = 0.5 * (a - d);
+        const double disc = p * p + bb * c;
+        if (disc >= 0.0) {
+          const double sq = sqrt(disc);
+          const double zz = p + (p >= 0.0 ? sq : -sq);
+          double cs = 1.0, sn = 0.0;
+          if (zz != 0.0 || c != 0.0) {
+            const double r = hypot(zz, c);
+            cs = zz / r;
+            sn = c / r;
+          }
+          c_cs = cs;
+          c_sn = sn;
+          c_real = 1;
+        } else {
+          c_real = 0;
+          w.wr[u - 1] = 0.5 * (a + d);
+          w.wr[u] = 0.5 * (a + d);
+          w.wi[u - 1] = sqrt(-disc);
+          w.wi[u] = -sqrt(-disc);
+        }
+      }
+      __syncthreads();
+      if (c_real) {
+        const double cs = c_cs, sn = c_sn;
+        for (int j = u - 1 + threadIdx.x; j < n; j += blockDim.x) {
+          const double h1 = HH(u - 1, j), h2 = HH(u, j);
+          HH(u - 1, j) = cs * h1 + sn * h2;
+          HH(u, j) = -sn * h1 + cs * h2;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i <= u; i += blockDim.x) {
+          const double h1 = HH(i, u - 1), h2 = HH(i, u);
+          HH(i, u - 1) = cs * h1 + sn * h2;
+          HH(i, u) = -sn * h1 + cs * h2;
+        }
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+          const double z1 = w.Z[i + (int64_t)(u - 1) * n], z2 = w.Z[i + (int64_t)u * n];
+          w.Z[i + (int64_t)(u - 1) * n] = cs * z1 + sn * z2;
+          w.Z[i + (int64_t)u * n] = -sn * z1 + cs * z2;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          HH(u, u - 1) = 0.0;
+          w.wr[u - 1] = HH(u - 1, u - 1);
+          w.wr[u] = HH(u, u);
+          w.wi[u - 1] = 0.0;
+          w.wi[u] = 0.0;
+        }
+      }
+      if (threadIdx.x == 0) {
+        sh_u = u - 2;
+        sh_iter = 0;
+      }
+      continue;
+    }
+    // Francis double-shift step on the active window [l, u]
+    __shared__ double fx, fy, fz;
+    if (threadIdx.x == 0) {
+      sh_iter += 1;
+      sh_total += 1;
+      if (sh_total > 40 * n) sh_fail = 1;
+      double s, t;
+      if (sh_iter == 10 || sh_iter == 20) {
+        const double ww = fabs(HH(u, u - 1)) + (u >= 2 ? fabs(HH(u - 1, u - 2)) : 0.0);
+        s = 1.5 * ww;
+        t = ww * ww;
+      } else {
+        s = HH(u - 1, u - 1) + HH(u, u);
+        t = HH(u - 1, u - 1) * HH(u, u) - HH(u - 1, u) * HH(u, u - 1);
+      }
+      fx = HH(l, l) * HH(l, l) + HH(l, l + 1) * HH(l + 1, l) - s * HH(l, l) + t;
+      fy = HH(l + 1, l) * (HH(l, l) + HH(l + 1, l + 1) - s);
+      fz = (l + 2 <= u) ? HH(l + 1, l) * HH(l + 2, l + 1) : 0.0;
+    }
+    __syncthreads();
+    if (sh_fail) break;
+    for (int kk = l; kk <= u - 2; ++kk) {
+      if (threadIdx.x == 0) house_small(fx, fy, fz, 3, sh_v3, &sh_tau3);
+      __syncthreads();
+      const double tau = sh_tau3;
+      const double v1 = sh_v3[1], v2 = sh_v3[2];
+      if (tau != 0.0) {
+        const int q = kk > l ? kk - 1 : l;
+        for (int j = q + threadIdx.x; j < n; j += blockDim.x) {
+          const double h0 = HH(kk, j), h1 = HH(kk + 1, j), h2 = HH(kk + 2, j);
+          const double ww = tau * (h0 + v1 * h1 + v2 * h2);
+          HH(kk, j) = h0 - ww;
+          HH(kk + 1, j) = h1 - ww * v1;
+          HH(kk + 2, j) = h2 - ww * v2;
+        }
+        __syncthreads();
+        const int rmaxi = kk + 3 < u ? kk + 3 : u;
+        for (int i = threadIdx.x; i <= rmaxi; i += blockDim.x) {
+          const double h0 = HH(i, kk), h1 = HH(i, kk + 1), h2 = HH(i, kk + 2);
+          const double ww = tau * (h0 + v1 * h1 + v2 * h2);
+          HH(i, kk) = h0 - ww;
+          HH(i, kk + 1) = h1 - ww * v1;
+          HH(i, kk + 2) = h2 - ww * v2;
+        }
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+          double* z0 = w.Z + i + (int64_t)kk * n;
+          const double h0 = z0[0], h1 = z0[n], h2 = z0[2 * (int64_t)n];
+          const double ww = tau * (h0 + v1 * h1 + v2 * h2);
+          z0[0] = h0 - ww;
+          z0[n] = h1 - ww * v1;
+          z0[2 * (int64_t)n] = h2 - ww * v2;
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        fx = HH(kk + 1, kk);
+        fy = HH(kk + 2, kk);
+        fz = kk < u - 2 ? HH(kk + 3, kk) : 0.0;
+        if (kk > l) {
+          // entries below the bulge are zero by construction
+        }
+      }
+      __syncthreads();
+    }
+    // final 2-vector reflector on rows u-1, u
+    if (threadIdx.x == 0) house_small(fx, fy, 0.0, 2, sh_v3, &sh_tau3);
+    __syncthreads();
+    {
+      const double tau = sh_tau3;
+      const double v1 = sh_v3[1];
+      if (tau != 0.0) {
+        const int q = u - 2 >= l ? u - 2 : l;
+        for (int j = q + threadIdx.x; j < n; j += blockDim.x) {
+          const double h0 = HH(u - 1, j), h1 = HH(u, j);
+          const double ww = tau * (h0 + v1 * h1);
+          HH(u - 1, j) = h0 - ww;
+          HH(u, j) = h1 - ww * v1;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i <= u; i += blockDim.x) {
+          const double h0 = HH(i, u - 1), h1 = HH(i, u);
+          const double ww = tau * (h0 + v1 * h1);
+          HH(i, u - 1) = h0 - ww;
+          HH(i, u) = h1 - ww * v1;
+        }
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+          const double h0 = w.Z[i + (int64_t)(u - 1) * n], h1 = w.Z[i + (int64_t)u * n];
+          const double ww = tau * (h0 + v1 * h1);
+          w.Z[i + (int64_t)(u - 1) * n] = h0 - ww;
+          w.Z[i + (int64_t)u * n] = h1 - ww * v1;
+        }
+      }
+    }
+    __syncthreads();
+    // clean the entries below the subdiagonal created by rounding
+    if (threadIdx.x == 0) {
+      for (int i = l + 2; i <= u; ++i) {
+        HH(i, i - 2) = 0.0;
+        if (i >= l + 3) HH(i, i - 3) = 0.0;
+      }
+    }
+  }
+  __syncthreads();
+  if (sh_fail) {
+    if (threadIdx.x == 0) { *status_out = 2; *knew_out = 0; }
+    return;
+  }
+  // ---- 5. selection: eigenvalues mu of largest modulus (theta = 1/mu smallest).
+  if (threadIdx.x == 0) {
+    int taken = 0, ns = 0;
+    // mark: use wi to find blocks; sel holds the start index of each chosen entity
+    for (int pass = 0; pass < n; ++pass) {
+      int best = -1;
+      double bmag = -1.0, bre = 0.0;
+      for (int i = 0; i < n; ++i) {
+        if (w.wi[i] < 0.0) continue;  // second member of a pair is represented by the first
+        bool used = false;
+        for (int t = 0; t < ns; ++t)
+          if (w.sel[t] == i) used = true;
+        if (used) continue;
+        const double mag = hypot(w.wr[i], w.wi[i]);
+        if (!(mag > 0.0)) continue;
+        const double ret = w.wr[i] / (mag * mag);  // Re theta
+        const bool better = mag > bmag * (1.0 + 1e-12) ||
+                            (mag >= bmag * (1.0 - 1e-12) && ret < bre);
+        if (best < 0 || better) {
+          best = i;
+          bmag = mag;
+          bre = ret;
+        }
+      }
+      if (best < 0) break;
+      const int need = w.wi[best] > 0.0 ? 2 : 1;
+      if (taken + need > k) break;
+      w.sel[ns++] = best;
+      taken += need;
+      if (taken == k) break;
+    }
+    w.sel[ns] = -1;
+    sh_knew = taken;
+    sh_l = ns;
+  }
+  __syncthreads();
+  const int knew = sh_knew;
+  const int nsel = sh_l;
+  if (knew == 0) {
+    if (threadIdx.x == 0) { *status_out = 3; *knew_out = 0; }
+    return;
+  }
+  // ---- 6. eigenvectors of T by back substitution (one thread per entity).
+  for (int e = threadIdx.x; e < nsel; e += blockDim.x) {
+    int col = 0;
+    for (int t = 0; t < e; ++t) col += w.wi[w.sel[t]] > 0.0 ? 2 : 1;
+    const int i = w.sel[e];
+    double* xr = w.X + (int64_t)col * n;
+    const double small = eps * (hnorm > 0.0 ? hnorm : 1.0);
+    if (w.wi[i] == 0.0) {
+      const double lam = H[i + (int64_t)i * n];
+      for (int r = 0; r < n; ++r) xr[r] = 0.0;
+      xr[i] = 1.0;
+      int r = i - 1;
+      while (r >= 0) {
+        const bool blk = r > 0 && H[r + (int64_t)(r - 1) * n] != 0.0;
+        if (!blk) {
+          double s = 0.0;
+          for (int c = r + 1; c <= i; ++c) s = fma(H[r + (int64_t)c * n], xr[c], s);
+          double den = H[r + (int64_t)r * n] - lam;
+          if (fabs(den) < small) den = small;
+          xr[r] = -s / den;
+          r -= 1;
+        } else {
+          double s1 = 0.0, s2 = 0.0;
+          for (int c = r + 1; c <= i; ++c) {
+            s1 = fma(H[(r - 1) + (int64_t)c * n], xr[c], s1);
+            s2 = fma(H[r + (int64_t)c * n], xr[c], s2);
+          }
+          const double a = H[(r - 1) + (int64_t)(r - 1) * n] - lam, b = H[(r - 1) + (int64_t)r * n];
+          const double c = H[r + (int64_t)(r - 1) * n], d = H[r + (int64_t)r * n] - lam;
+          double det = a * d - b * c;
+          if (fabs(det) < small * small) det = small * small;
+          xr[r - 1] = (-s1 * d + b * s2) / det;
+          xr[r] = (-a * s2 + c * s1) / det;
+          r -= 2;
+        }
+      }
+    } else {
+      // complex pair at (i, i+1); eigenvalue lambda = wr + i*wi (wi > 0)
+      double* xi = xr + n;
+      const cplx lam = {w.wr[i], w.wi[i]};
+      for (int r = 0; r < n; ++r) { xr[r] = 0.0; xi[r] = 0.0; }
+      const double p = H[i + (int64_t)i * n], q = H[i + (int64_t)(i + 1) * n];
+      const double rr = H[(i + 1) + (int64_t)i * n], ss = H[(i + 1) + (int64_t)(i + 1) * n];
+      // null vector of [[p - lam, q], [rr, ss - lam]]
+      if (fabs(q) >= fabs(rr)) {
+        xr[i] = q; xi[i] = 0.0;
+        xr[i + 1] = lam.re - p; xi[i + 1] = lam.im;
+      } else {
+        xr[i] = lam.re - ss; xi[i] = lam.im;
+        xr[i + 1] = rr; xi[i + 1] = 0.0;
+      }
+      int r = i - 1;
+      while (r >= 0) {
+        const bool blk = r > 0 && H[r + (int64_t)(r - 1) * n] != 0.0;
+        if (!blk) {
+          cplx s = {0.0, 0.0};
+          for (int c = r + 1; c <= i + 1; ++c) {
+            s.re = fma(H[r + (int64_t)c * n], xr[c], s.re);
+            s.im = fma(H[r + (int64_t)c * n], xi[c], s.im);
+          }
+          cplx den = {H[r + (int64_t)r * n] - lam.re, -lam.im};
+          if (fabs(den.re) + fabs(den.im) < small) den.re = small;
+          const cplx val = cdiv({-s.re, -s.im}, den);
+          xr[r] = val.re;
+          xi[r] = val.im;
+          r -= 1;
+        } else {
+          cplx s1 = {0.0, 0.0}, s2 = {0.0, 0.0};
+          for (int c = r + 1; c <= i + 1; ++c) {
+            s1.re = fma(H[(r - 1) + (int64_t)c * n], xr[c], s1.re);
+            s1.im = fma(H[(r - 1) + (int64_t)c * n], xi[c], s1.im);
+            s2.re = fma(H[r + (int64_t)c * n], xr[c], s2.re);
+            s2.im = fma(H[r + (int64_t)c * n], xi[c], s2.im);
+          }
+          const cplx a = {H[(r - 1) + (int64_t)(r - 1) * n] - lam.re, -lam.im};
+          const cplx b = {H[(r - 1) + (int64_t)r * n], 0.0};
+          const cplx c = {H[r + (int64_t)(r - 1) * n], 0.0};
+          const cplx d = {H[r + (int64_t)r * n] - lam.re, -lam.im};
+          cplx det = cmul(a, d);
+          const cplx bc = cmul(b, c);
+          det.re -= bc.re;
+          det.im -= bc.im;
+          if (fabs(det.re) + fabs(det.im) < small * small) det.re = small * small;
+          const cplx ms1 = {-s1.re, -s1.im}, ms2 = {-s2.re, -s2.im};
+          cplx t1 = cmul(ms1, d), t2 = cmul(b, ms2);
+          const cplx x1 = cdiv({t1.re - t2.re, t1.im - t2.im}, det);
+          t1 = cmul(a, ms2);
+          t2 = cmul(c, ms1);
+          const cplx x2 = cdiv({t1.re - t2.re, t1.im - t2.im}, det);
+          xr[r - 1] = x1.re; xi[r - 1] = x1.im;
+          xr[r] = x2.re; xi[r] = x2.im;
+          r -= 2;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // ---- 7. back to M'' coordinates: Y = Z X (stored in F, ld n), then
+  //         orthonormalise the columns (two Gram-Schmidt passes) into X.
+  double* Y = w.F;
+  for (int t = threadIdx.x; t < n * knew; t += blockDim.x) {
+    const int r = t % n, c = t / n;
+    double s = 0.0;
+    for (int l2 = 0; l2 < n; ++l2) s = fma(w.Z[r + (int64_t)l2 * n], w.X[l2 + (int64_t)c * n], s);
+    Y[t] = s;
+  }
+  __syncthreads();
+  int kept = 0;
+  for (int c = 0; c < knew; ++c) {
+    double* yc = Y + (int64_t)c * n;
+    double s0 = 0.0;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) s0 = fma(yc[r], yc[r], s0);
+    const double n0 = sqrt(block_sum(s0, red));
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int c2 = 0; c2 < kept; ++c2) {
+        const double* qc = w.X + (int64_t)c2 * n;
+        double d = 0.0;
+        for (int r = threadIdx.x; r < n; r += blockDim.x) d = fma(qc[r], yc[r], d);
+        d = block_sum(d, red);
+        __syncthreads();
+        for (int r = threadIdx.x; r < n; r += blockDim.x) yc[r] = fma(-d, qc[r], yc[r]);
+        __syncthreads();
+      }
+    }
+    double s1 = 0.0;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) s1 = fma(yc[r], yc[r], s1);
+    const double n1 = sqrt(block_sum(s1, red));
+    __syncthreads();
+    if (n1 > 1e-10 * n0 && n1 > 0.0) {
+      double* qk = w.X + (int64_t)kept * n;
+      for (int r = threadIdx.x; r < n; r += blockDim.x) qk[r] = yc[r] / n1;
+      ++kept;
+    }
+    __syncthreads();
+  }
+  // ---- 8. QC = Q_G [Q2; 0] ((n+1) x kept), PU = R_G^{-1} Q2 (n x kept).
+  for (int t = threadIdx.x; t < (n + 1) * kept; t += blockDim.x) {
+    const int r = t % (n + 1), c = t / (n + 1);
+    QC[r + (int64_t)c * ldqc] = r < n ? w.X[r + (int64_t)c * n] : 0.0;
+  }
+  __syncthreads();
+  for (int c = n - 1; c >= 0; --c) {
+    const int len = n + 1 - c;
+    const double tau = w.tau[c];
+    for (int j = threadIdx.x; j < kept; j += blockDim.x) {
+      double* col = QC + (int64_t)j * ldqc + c;
+      const double* vv = w.G + (int64_t)c * ldg + c;  // vv[0] holds R_G(c,c); the reflector has v[0] = 1
+      double s = col[0];
+      for (int i = 1; i < len; ++i) s = fma(vv[i], col[i], s);
+      s *= tau;
+      col[0] -= s;
+      for (int i = 1; i < len; ++i) col[i] = fma(-s, vv[i], col[i]);
+    }
+    __syncthreads();
+  }
+  for (int j = threadIdx.x; j < kept; j += blockDim.x) {
+    const double* q2 = w.X + (int64_t)j * n;
+    double* pu = PU + (int64_t)j * ldpu;
+    for (int r = n - 1; r >= 0; --r) {
+      double t = q2[r];
+      for (int c = r + 1; c < n; ++c) t = fma(-w.G[r + (int64_t)c * ldg], pu[c], t);
+      pu[r] = t / w.G[r + (int64_t)r * ldg];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *knew_out = kept;
+    *status_out = 0;
+  }
+#undef HH
+}
+
+// Solver wrapper: builds G and F from the cycle's B, H and Gram, runs the
+// core, folds the column scales of the stored V into QC and PU.
+__global__ void __launch_bounds__(kHRThreads) k_harmonic_ritz(SolveState* s, SmallBuffers b, int kc, int jj, int k,
+                                                              int use_smem) {
+  extern __shared__ double dsm[];
+  const int n = kc + jj;
+  double* base = use_smem ? dsm : b.hrws;
+  HRWork w = hr_carve(base, n);
+  const int ldg = n + 1;
+  const int ldh = b.m + 1;
+  for (int t = threadIdx.x; t < (n + 1) * n; t += blockDim.x) {
+    const int r = t % (n + 1), c = t / (n + 1);
+    double gv = 0.0, fv = 0.0;
+    if (r < kc && c < kc) {
+      gv = r == c ? 1.0 : 0.0;
+      fv = b.gram[r + (int64_t)c * (kc + jj + 1)];
+    } else if (r < kc) {
+      gv = b.B[r + (int64_t)(c - kc) * b.kmax];
+    } else if (c < kc) {
+      fv = b.sv[r - kc] * b.gram[r + (int64_t)c * (kc + jj + 1)];
+    } else {
+      gv = b.H[(r - kc) + (int64_t)(c - kc) * ldh];
+      fv = (r - kc) == (c - kc) ? 1.0 : 0.0;
+    }
+    w.G[r + (int64_t)c * ldg] = gv;
+    w.F[r + (int64_t)c * ldg] = fv;
+  }
+  __syncthreads();
+  __shared__ int knew, st;
+  hr_core(w, n, k, b.QC, n + 1, b.PU, n, &knew, &st);
+  __syncthreads();
+  // fold the stored-column scales (v_l = sv[l] q_l) into the coefficients
+  for (int t = threadIdx.x; t < (n + 1) * knew; t += blockDim.x) {
+    const int r = t % (n + 1), c = t / (n + 1);
+    if (r >= kc) b.QC[r + (int64_t)c * (n + 1)] *= b.sv[r - kc];
+  }
+  for (int t = threadIdx.x; t < n * knew; t += blockDim.x) {
+    const int r = t % n, c = t / n;
+    if (r >= kc) b.PU[r + (int64_t)c * n] *= b.sv[r - kc];
+  }
+  if (threadIdx.x == 0) {
+    s->knew = st == 0 ? knew : kc;
+    s->hr_status = st;
+  }
+}
+
+__global__ void __launch_bounds__(kHRThreads) k_harmonic_ritz_small(int n, const double* G, const double* F, int k,
+                                                                    double* QC, double* PU, int* knew_out,
+                                                                    double* ws, int use_smem) {
+  extern __shared__ double dsm[];
+  double* base = use_smem ? dsm : ws;
+  HRWork w = hr_carve(base, n);
+  for (int t = threadIdx.x; t < (n + 1) * n; t += blockDim.x) {
+    w.G[t] = G[t];
+    w.F[t] = F[t];
+  }
+  __syncthreads();
+  __shared__ int knew, st;
+  hr_core(w, n, k, QC, n + 1, PU, n, &knew, &st);
+  __syncthreads();
+  if (threadIdx.x == 0) *knew_out = st == 0 ? knew : -st;
+}
+
+// Cholesky G = R^T R of a k x k Gram matrix and R^{-1} (upper), one thread;
+// used by the CholQR of line 1a (C~ = A U = C R). status: 0 ok, 1 not SPD.
+__global__ void k_chol_rinv(int k, const double* G, double* Rinv, double* Rw, int* status) {
+  if (threadIdx.x != 0) return;
+  for (int t = 0; t < k * k; ++t) Rw[t] = 0.0;
+  for (int j = 0; j < k; ++j) {
+    double d = G[j + j * k];
+    for (int l = 0; l < j; ++l) d -= Rw[l + j * k] * Rw[l + j * k];
+    if (!(d > 0.0)) {
+      *status = 1;
+      return;
+    }
+    const double rjj = sqrt(d);
+    Rw[j + j * k] = rjj;
+    for (int c = j + 1; c < k; ++c) {
+      double t = G[j + c * k];
+      for (int l = 0; l < j; ++l) t -= Rw[l + j * k] * Rw[l + c * k];
+      Rw[j + c * k] = t / rjj;
+    }
+  }
+  // Rinv = R^{-1}: solve R X = I column by column (X upper triangular)
+  for (int c = 0; c < k; ++c) {
+    for (int r = k - 1; r >= 0; --r) {
+      double t = r == c ? 1.0 : 0.0;
+      for (int l = r + 1; l <= c; ++l) t -= Rw[r + l * k] * Rinv[l + c * k];
+      Rinv[r + c * k] = r > c ? 0.0 : t / Rw[r + r * k];
+    }
+  }
+  *status = 0;
+}
+
+// Start of an Arnoldi cycle: g = rho e_1, v_1 = r / rho (column 0 stores r,
+// so its scale is 1/rho), no steps taken.
+__global__ void k_cycle_init(SolveState* s, SmallBuffers b) {
+  const double rho = sqrt(s->rho2);
+  for (int i = threadIdx.x; i <= b.m; i += blockDim.x) b.g[i] = i == 0 ? rho : 0.0;
+  if (threadIdx.x == 0) {
+    b.sv[0] = rho > 0.0 ? 1.0 / rho : 0.0;
+    s->done = rho > 0.0 ? 0 : 1;
+    s->jj = 0;
+  }
+}
+
+// ||b|| from the reduced sum of squares and the absolute tolerance.
+__global__ void k_set_tol(SolveState* s, double tol) {
+  if (threadIdx.x != 0) return;
+  s->bnorm = sqrt(s->nrm2[0]);
+  s->tolabs = tol * s->bnorm;
+}
+
+__global__ void k_set_scalar(SolveState* s, int which) {
+  if (threadIdx.x != 0) return;
+  if (which == 0) s->done = 0;
+}
+
+size_t hr_doubles_host(int n) { return (size_t)2 * (n + 1) * n + (size_t)3 * n * n + 5 * (size_t)n + 8; }
+
+}  // namespace
+
+size_t harmonic_ritz_ws_doubles(int n) { return hr_doubles_host(n); }
+
+cudaError_t launch_arn_coef(SolveState* s, SmallBuffers b, int kc, int j, int pass, cudaStream_t st) {
+  k_arn_coef<<<1, 128, 0, st>>>(s, b, kc, j, pass);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_arn_finalize(SolveState* s, SmallBuffers b, int kc, int j, cudaStream_t st) {
+  k_arn_finalize<<<1, 32, 0, st>>>(s, b, kc, j);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cycle_solve(SolveState* s, SmallBuffers b, int kc, cudaStream_t st) {
+  k_cycle_solve<<<1, 32, 0, st>>>(s, b, kc);
+  return cudaGetLastError();
+}
+
+static constexpr size_t kHRSmemMax = 200 * 1024;
+
+cudaError_t launch_harmonic_ritz(SolveState* s, SmallBuffers b, int kc, int jj, int k, cudaStream_t st) {
+  const int n = kc + jj;
+  const size_t bytes = hr_doubles_host(n) * sizeof(double);
+  const int use_smem = bytes <= kHRSmemMax ? 1 : 0;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_harmonic_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHRSmemMax);
+    attr = true;
+  }
+  k_harmonic_ritz<<<1, kHRThreads, use_smem ? bytes : 0, st>>>(s, b, kc, jj, k, use_smem);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_harmonic_ritz_small(int n, const double* G, const double* F, int k, double* QC, double* PU,
+                                       int* knew, double* ws, cudaStream_t st) {
+  const size_t bytes = hr_doubles_host(n) * sizeof(double);
+  const int use_smem = bytes <= kHRSmemMax ? 1 : 0;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_harmonic_ritz_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHRSmemMax);
+    attr = true;
+  }
+  k_harmonic_ritz_small<<<1, kHRThreads, use_smem ? bytes : 0, st>>>(n, G, F, k, QC, PU, knew, ws, use_smem);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chol_rinv(int k, const double* G, double* Rinv, double* Rw, int* status, cudaStream_t st) {
+  k_chol_rinv<<<1, 32, 0, st>>>(k, G, Rinv, Rw, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cycle_init(SolveState* s, SmallBuffers b, cudaStream_t st) {
+  k_cycle_init<<<1, 128, 0, st>>>(s, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_tol(SolveState* s, double tol, cudaStream_t st) {
+  k_set_tol<<<1, 32, 0, st>>>(s, tol);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_scalar(SolveState* s, int which, cudaStream_t st) {
+  k_set_scalar<<<1, 32, 0, st>>>(s, which);
+  return cudaGetLastError();
+}
+
+}  // namespace rk

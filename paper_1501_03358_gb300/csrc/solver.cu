@@ -1,0 +1,999 @@
+// Host driver and C ABI of librk: problems, recycle spaces, and the solvers
+// of Sec. 2.2-2.4 (GMRES(m), rGCROT(m,k), rBiCGStab, hybrid) run as
+// sequences of device kernels on the caller's stream.
+//
+// Device layout of a problem (N cells, ld = N rounded up to 32 doubles):
+//   coef  S x ld     banded operator (copied from the caller)
+//   dinv  ld         1 / a_pp (right point-Jacobi)
+//   QB    (kmax + mcap + 1) x ld   columns [kmax - kc, kmax) hold C, columns
+//                    kmax + j hold the Arnoldi vectors; so [C V_j] is one
+//                    contiguous block for the block projections
+//   Ub    kmax x ld  U, right-aligned the same way (A U = C)
+//   bicg  7 x ld     rBiCGStab vectors
+// The Arnoldi vectors are stored unnormalised (v_l = sv[l] q_l); the column
+// scales are folded into the small coefficient vectors, never into a pass
+// over N.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+#include <algorithm>
+
+#include "rk.h"
+#include "rk_internal.h"
+#include "rk_solver.h"
+#include "rk_bicg.h"
+
+using namespace rk;
+
+namespace {
+thread_local std::string g_err = "no error";
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define RK_CUDA(x)                                                                                \
+  do {                                                                                            \
+    cudaError_t e_ = (x);                                                                         \
+    if (e_ != cudaSuccess) return fail(RK_E_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define RK_TRY(x)              \
+  do {                         \
+    int r_ = (x);              \
+    if (r_ != RK_OK) return r_; \
+  } while (0)
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+}  // namespace
+
+struct rk_context {
+  rk_alloc_fn alloc = nullptr;
+  rk_free_fn free_fn = nullptr;
+  void* user = nullptr;
+  int device = 0;
+  double* part = nullptr;
+  size_t part_n = 0;
+  unsigned* counter = nullptr;
+  int refs = 0;            // live problems created from this context
+  bool destroyed = false;  // rk_context_destroy was called
+};
+
+namespace {
+
+void context_free(rk_context* c);
+
+void* dev_alloc(rk_context* c, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  bytes = (size_t)round_up((int64_t)bytes, 256);
+  if (c->alloc) return c->alloc(bytes, c->user);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(rk_context* c, void* p) {
+  if (!p) return;
+  if (c->free_fn)
+    c->free_fn(p, c->user);
+  else
+    cudaFree(p);
+}
+
+template <typename T>
+int alloc_into(rk_context* c, T** out, size_t count) {
+  *out = (T*)dev_alloc(c, count * sizeof(T));
+  if (!*out) return fail(RK_E_OOM, "device allocation of " + std::to_string(count * sizeof(T)) + " bytes failed");
+  return RK_OK;
+}
+
+}  // namespace
+
+// Opt-in per-kernel-class timing: CUDA events recorded on the solve's stream
+// around every launch, reduced at the solve's synchronisation points.
+enum ProfClass { PC_SPMV = 0, PC_RESID, PC_DOTS, PC_UPDATE, PC_GEMM, PC_GRAM, PC_SMALL, PC_BICG, PC_HRITZ, PC_COUNT };
+static const char* kProfNames[PC_COUNT] = {"spmv", "residual", "dots", "update", "gemm_rows", "gram", "small", "bicg", "harmonic_ritz"};
+
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  struct Pending { cudaEvent_t a, b; int cls; double bytes; };
+  std::vector<Pending> pending;
+  double ms[PC_COUNT] = {0};
+  double bytes[PC_COUNT] = {0};
+  int64_t launches[PC_COUNT] = {0};
+  cudaEvent_t get() {
+    if (pool.empty()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      return e;
+    }
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  void flush() {
+    for (auto& q : pending) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, q.a, q.b) == cudaSuccess) {
+        ms[q.cls] += t;
+        bytes[q.cls] += q.bytes;
+        launches[q.cls] += 1;
+      }
+      pool.push_back(q.a);
+      pool.push_back(q.b);
+    }
+    pending.clear();
+  }
+  void reset() {
+    flush();
+    for (int i = 0; i < PC_COUNT; ++i) ms[i] = bytes[i] = 0.0, launches[i] = 0;
+  }
+  ~Profiler() {
+    for (auto& q : pending) { cudaEventDestroy(q.a); cudaEventDestroy(q.b); }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+struct ProfScope {
+  Profiler* pr;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  int cls;
+  double bytes;
+  ProfScope(Profiler* p, int c, double b, cudaStream_t s) : pr(p), st(s), cls(c), bytes(b) {
+    if (pr->on) {
+      a = pr->get();
+      cudaEventRecord(a, st);
+    }
+  }
+  ~ProfScope() {
+    if (pr->on && a) {
+      cudaEvent_t bev = pr->get();
+      cudaEventRecord(bev, st);
+      pr->pending.push_back({a, bev, cls, bytes});
+    }
+  }
+};
+
+struct rk_problem {
+  rk_context* ctx = nullptr;
+  Profiler prof;
+  Dims d{};
+  int S = 7;
+  int64_t n = 0, ld = 0;
+  double* coef = nullptr;
+  double* dinv = nullptr;
+  double anorm_f = 0.0;  // ||A||_F
+  int kmax = 0, mcap = 0, kdim = 0;
+  double* QB = nullptr;
+  double* Ub = nullptr;
+  double* bicg = nullptr;
+  // small
+  double* small = nullptr;
+  SmallBuffers sb{};
+  SolveState* st = nullptr;       // device
+  SolveState* st_h = nullptr;     // pinned host mirror
+  BicgScalars* bs = nullptr;      // device
+  BicgScalars* bs_h = nullptr;    // pinned host mirror
+  double* eta = nullptr;          // 3 x (kmax + 4): eta1, eta2, xi
+  double* part = nullptr;
+  size_t part_n = 0;
+  unsigned* counter = nullptr;
+  int* istat = nullptr;           // device ints for small kernels
+  int solves = 0;
+
+  double* Vcol(int j) const { return QB + (int64_t)(kmax + j) * ld; }
+  double* Cblk(int kc) const { return QB + (int64_t)(kmax - kc) * ld; }
+  double* Ublk(int kc) const { return Ub + (int64_t)(kmax - kc) * ld; }
+};
+
+namespace {
+
+size_t partials_needed(const rk_problem* p, int kmax, int mcap) {
+  const int nq = kmax + mcap + 6;
+  size_t a = (size_t)red_blocks(p->n) * nq;
+  size_t b = (size_t)gram_blocks(p->n) * (size_t)(kmax + mcap + 1) * (size_t)std::max(kmax, 1);
+  size_t c = (size_t)stencil_blocks(p->d) + 4;
+  size_t e = (size_t)red_blocks(p->n) * 4;
+  return std::max(std::max(a, b), std::max(c, e));
+}
+
+void free_small(rk_problem* p) {
+  dev_free(p->ctx, p->small);
+  p->small = nullptr;
+  dev_free(p->ctx, p->eta);
+  p->eta = nullptr;
+  dev_free(p->ctx, p->part);
+  p->part = nullptr;
+}
+
+// (Re)allocate the recycle/Arnoldi storage for capacity (kmax, mcap), keeping
+// the stored recycle space.
+int ensure_capacity(rk_problem* p, int kneed, int mneed, cudaStream_t st) {
+  if (kneed <= p->kmax && mneed <= p->mcap && p->QB) return RK_OK;
+  const int kmax = std::max(kneed, p->kmax);
+  const int mcap = std::max(mneed, p->mcap);
+  if (kmax > 256) return fail(RK_E_INVALID, "recycle dimension above 256 is not supported");
+  if (kmax + mcap + 1 > 512) return fail(RK_E_INVALID, "k + m above 511 is not supported");
+  double* QB = nullptr;
+  double* Ub = nullptr;
+  RK_TRY(alloc_into(p->ctx, &QB, (size_t)(kmax + mcap + 1) * p->ld));
+  if (kmax > 0) {
+    int r = alloc_into(p->ctx, &Ub, (size_t)kmax * p->ld);
+    if (r != RK_OK) {
+      dev_free(p->ctx, QB);
+      return r;
+    }
+  }
+  if (p->kdim > 0) {
+    RK_CUDA(cudaMemcpyAsync(QB + (int64_t)(kmax - p->kdim) * p->ld, p->Cblk(p->kdim),
+                            sizeof(double) * p->ld * p->kdim, cudaMemcpyDeviceToDevice, st));
+    RK_CUDA(cudaMemcpyAsync(Ub + (int64_t)(kmax - p->kdim) * p->ld, p->Ublk(p->kdim),
+                            sizeof(double) * p->ld * p->kdim, cudaMemcpyDeviceToDevice, st));
+    RK_CUDA(cudaStreamSynchronize(st));
+  }
+  dev_free(p->ctx, p->QB);
+  dev_free(p->ctx, p->Ub);
+  p->QB = QB;
+  p->Ub = Ub;
+  p->kmax = kmax;
+  p->mcap = mcap;
+  // small buffers
+  free_small(p);
+  const int m = mcap, nq = kmax + mcap + 2;
+  SmallBuffers& b = p->sb;
+  b.m = m;
+  b.kmax = std::max(kmax, 1);
+  b.nqmax = nq;
+  const int nhr = kmax + mcap;
+  b.hrws_doubles = harmonic_ritz_ws_doubles(std::max(nhr, 1));
+  size_t total = 0;
+  auto take = [&](size_t cnt) {
+    size_t off = total;
+    total += (size_t)round_up((int64_t)cnt, 32);
+    return off;
+  };
+  const size_t oH = take((size_t)(m + 1) * m), oR = take((size_t)(m + 1) * m), oB = take((size_t)b.kmax * m),
+               og = take(m + 1), ocs = take(m), osn = take(m), osv = take(m + 2), ohacc = take(nq),
+               odots = take(nq + 4), ocoef = take(nq), oy = take(m), ox = take(nq),
+               ogram = take((size_t)(kmax + m + 1) * b.kmax), oQC = take((size_t)(kmax + m + 1) * b.kmax),
+               oPU = take((size_t)(kmax + m) * b.kmax), ows = take(b.hrws_doubles);
+  RK_TRY(alloc_into(p->ctx, &p->small, total));
+  b.H = p->small + oH;
+  b.R = p->small + oR;
+  b.B = p->small + oB;
+  b.g = p->small + og;
+  b.cs = p->small + ocs;
+  b.sn = p->small + osn;
+  b.sv = p->small + osv;
+  b.hacc = p->small + ohacc;
+  b.dots = p->small + odots;
+  b.coef = p->small + ocoef;
+  b.y = p->small + oy;
+  b.xcoef = p->small + ox;
+  b.gram = p->small + ogram;
+  b.QC = p->small + oQC;
+  b.PU = p->small + oPU;
+  b.hrws = p->small + ows;
+  RK_CUDA(cudaMemsetAsync(p->small, 0, total * sizeof(double), st));
+  RK_TRY(alloc_into(p->ctx, &p->eta, (size_t)3 * (kmax + 4) + (size_t)kmax * kmax * 2 + 16));
+  p->part_n = partials_needed(p, kmax, mcap);
+  RK_TRY(alloc_into(p->ctx, &p->part, p->part_n));
+  return RK_OK;
+}
+
+int sync_state(rk_problem* p, cudaStream_t st) {
+  RK_CUDA(cudaMemcpyAsync(p->st_h, p->st, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
+  RK_CUDA(cudaStreamSynchronize(st));
+  p->prof.flush();
+  return RK_OK;
+}
+
+// sum of squares of a device vector into st->nrm2[slot]
+int norm2_into(rk_problem* p, const double* v, int slot, cudaStream_t st) {
+  DotsArgs a{};
+  a.n = p->n;
+  a.nq = 0;
+  a.Q = v;
+  a.ld = p->ld;
+  a.ne = 0;
+  a.self = 1;
+  a.w = v;
+  a.part = p->part;
+  a.counter = p->counter;
+  a.out = &p->st->nrm2[slot];
+  ProfScope ps(&p->prof, PC_DOTS, 8.0 * (double)p->n, st);
+  RK_CUDA(launch_dots(a, st));
+  return RK_OK;
+}
+
+int dots_launch(rk_problem* p, const double* Q, int nq, const double* w, double* out, const int* skip,
+                cudaStream_t st, const double* extra0 = nullptr, int self = 0) {
+  DotsArgs a{};
+  a.n = p->n;
+  a.nq = nq;
+  a.Q = Q;
+  a.ld = p->ld;
+  a.extra[0] = extra0;
+  a.ne = extra0 ? 1 : 0;
+  a.self = self;
+  a.w = w;
+  a.part = p->part;
+  a.counter = p->counter;
+  a.out = out;
+  a.skip_flag = skip;
+  ProfScope ps(&p->prof, PC_DOTS, 8.0 * (nq + (extra0 ? 1 : 0) + 1) * (double)p->n, st);
+  RK_CUDA(launch_dots(a, st));
+  return RK_OK;
+}
+
+int update_launch(rk_problem* p, const double* Q, int nq, const double* c, double* y, double* nrm2, const int* skip,
+                  cudaStream_t st) {
+  UpdateArgs a{};
+  a.n = p->n;
+  a.nq = nq;
+  a.Q = Q;
+  a.ld = p->ld;
+  a.c = c;
+  a.y = y;
+  a.part = p->part;
+  a.counter = p->counter;
+  a.nrm2 = nrm2;
+  a.skip_flag = skip;
+  ProfScope ps(&p->prof, PC_UPDATE, 8.0 * (nq + 2) * (double)p->n, st);
+  RK_CUDA(launch_update(a, st));
+  return RK_OK;
+}
+
+// out (+)= [A cols | dinv .* B cols] P
+int gemm_launch(rk_problem* p, const double* A, int na, const double* Bm, int nb, const double* bscale,
+                const double* P, int nc, double* out, int accum, cudaStream_t st) {
+  GemmRowsArgs a{};
+  a.n = p->n;
+  a.na = na;
+  a.nb = nb;
+  a.nc = nc;
+  a.A = A;
+  a.lda = p->ld;
+  a.Bm = Bm;
+  a.ldb = p->ld;
+  a.bscale = bscale;
+  a.P = P;
+  a.out = out;
+  a.ldo = p->ld;
+  a.accum = accum;
+  ProfScope ps(&p->prof, PC_GEMM, 8.0 * (na + nb + nc * (accum ? 2 : 1) + (bscale ? 1 : 0)) * (double)p->n, st);
+  RK_CUDA(launch_gemm_rows(a, st));
+  return RK_OK;
+}
+
+// Structured-grid product on the solve stream, timed as one kernel class.
+int stencil_launch(rk_problem* p, int mode, const double* v, const double* b, double* y, double* part,
+                   unsigned* counter, double* nrm2, const int* skip, cudaStream_t st) {
+  const bool resid = mode == ST_RESID;
+  ProfScope ps(&p->prof, resid ? PC_RESID : PC_SPMV, 8.0 * (p->S + (resid ? 3 : 2)) * (double)p->n, st);
+  RK_CUDA(launch_stencil(p->d, p->S, mode, p->coef, mode == ST_PREC ? p->dinv : nullptr, v, b, y, part, counter,
+                         nrm2, skip, st));
+  return RK_OK;
+}
+
+// Line 1b at the start of a cycle: xi = C^T r, r <- r - C xi, x <- x + U xi;
+// ||r||^2 -> st->rho2.
+int project_residual(rk_problem* p, int kc, double* r, double* x, cudaStream_t st) {
+  if (kc == 0) return RK_OK;  // ||r||^2 already in st->rho2
+  double* xi = p->eta;  // kc
+  RK_TRY(dots_launch(p, p->Cblk(kc), kc, r, xi, nullptr, st));
+  RK_TRY(update_launch(p, p->Cblk(kc), kc, xi, r, &p->st->rho2, nullptr, st));
+  RK_TRY(gemm_launch(p, p->Ublk(kc), kc, nullptr, 0, nullptr, xi, 1, x, 1, st));
+  return RK_OK;
+}
+
+double model_words_cycle(int S, int kc, int jj, int m) {
+  double w = 0.0;
+  for (int j = 0; j < jj; ++j) w += S + 5 + 2.0 * (kc + j);
+  w += (jj + kc + 3) + (S + 3);
+  (void)m;
+  return w;
+}
+
+// ---------------------------------------------------------------- GMRES / rGCROT
+int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& prm, rk_solve_info& info,
+              bool recycle, bool update, cudaStream_t st) {
+  const int m = prm.m;
+  const int k = recycle ? prm.k : 0;
+  const int maxmv = prm.max_matvec > 0 ? prm.max_matvec : 2000;
+  RK_TRY(ensure_capacity(p, std::max(k, p->kdim), m, st));
+  int kc = recycle ? p->kdim : 0;
+  const double S = p->S;
+  double words = 0.0;
+  // ||b||
+  RK_TRY(norm2_into(p, b, 0, st));
+  { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_set_tol(p->st, prm.tol, st)); }
+  RK_TRY(sync_state(p, st));
+  const double bnorm = p->st_h->bnorm;
+  if (!std::isfinite(bnorm)) return fail(RK_E_INVALID, "b contains NaN or Inf");
+  if (bnorm == 0.0) {
+    RK_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * p->n, st));
+    RK_CUDA(cudaStreamSynchronize(st));
+    info.status = RK_OK;
+    info.recycle_dim = p->kdim;
+    return RK_OK;
+  }
+  const double tolabs = prm.tol * bnorm;
+  // line 1: r = b - A x into column 0 of V; line 1b
+  double* r = p->Vcol(0);
+  RK_TRY(stencil_launch(p, ST_RESID, x, b, r, p->part, p->counter,
+                         &p->st->rho2, nullptr, st));
+  RK_TRY(project_residual(p, kc, r, x, st));
+  words += (S + 3) + (kc ? 2.0 * kc + 3 : 0) + 1;
+  RK_TRY(sync_state(p, st));
+  double rho = std::sqrt(p->st_h->rho2);
+  int matvecs = 0, cycles = 0;
+  double est = rho / bnorm;
+  const int* done = &p->st->done;
+  while (rho > tolabs && matvecs < maxmv) {
+    const int steps = std::min(m, maxmv - matvecs);
+    { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_cycle_init(p->st, p->sb, st)); }
+    for (int j = 0; j < steps; ++j) {
+      RK_TRY(stencil_launch(p, ST_PREC, p->Vcol(j), nullptr, p->Vcol(j + 1), nullptr,
+                             nullptr, nullptr, done, st));
+      const int nq = kc + j + 1;
+      for (int pass = 0; pass < 2; ++pass) {
+        RK_TRY(dots_launch(p, p->Cblk(kc), nq, p->Vcol(j + 1), p->sb.dots, done, st));
+        { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_arn_coef(p->st, p->sb, kc, j, pass, st)); }
+        RK_TRY(update_launch(p, p->Cblk(kc), nq, p->sb.coef, p->Vcol(j + 1), &p->st->nrm2[1], done, st));
+      }
+      { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_arn_finalize(p->st, p->sb, kc, j, st)); }
+    }
+    RK_TRY(sync_state(p, st));
+    const int jj = p->st_h->jj;
+    if (jj == 0) break;
+    est = p->st_h->est / bnorm;
+    matvecs += jj;
+    cycles += 1;
+    // lines 12-13a: y, z = -B y, x <- x + M^{-1} V_j y + U z
+    { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_cycle_solve(p->st, p->sb, kc, st)); }
+    RK_TRY(gemm_launch(p, p->Ublk(kc), kc, p->Vcol(0), jj, p->dinv, p->sb.xcoef, 1, x, 1, st));
+    words += model_words_cycle(p->S, kc, jj, m);
+    // line 14a: recycle update (harmonic Ritz), before column 0 is reused
+    if (update && k > 0) {
+      if (kc > 0) {
+        GramArgs g{};
+        g.n = p->n;
+        g.na = kc;
+        g.nb = jj + 1;
+        g.nu = kc;
+        g.A = p->Cblk(kc);
+        g.lda = p->ld;
+        g.Bm = p->Vcol(0);
+        g.ldb = p->ld;
+        g.d = p->coef;  // diag(A) = band 0
+        g.U = p->Ublk(kc);
+        g.ldu = p->ld;
+        g.part = p->part;
+        g.counter = p->counter;
+        g.out = p->sb.gram;
+        { ProfScope ps_(&p->prof, PC_GRAM, 8.0 * (g.na + g.nb + g.nu + 1) * (double)p->n, st); RK_CUDA(launch_gram(g, st)); }
+      }
+      { ProfScope ps_(&p->prof, PC_HRITZ, 0.0, st); RK_CUDA(launch_harmonic_ritz(p->st, p->sb, kc, jj, k, st)); }
+      RK_TRY(sync_state(p, st));
+      const int knew = p->st_h->knew;
+      if (p->st_h->hr_status == 0 && knew > 0) {
+        // C <- [C V_{j+1}] QC, U <- [U, M^{-1} V_j] PU, both in place (row tiles)
+        RK_TRY(gemm_launch(p, p->Cblk(kc), kc, p->Vcol(0), jj + 1, nullptr, p->sb.QC, knew, p->Cblk(knew), 0, st));
+        RK_TRY(gemm_launch(p, p->Ublk(kc), kc, p->Vcol(0), jj, p->dinv, p->sb.PU, knew, p->Ublk(knew), 0, st));
+        kc = knew;
+        p->kdim = knew;
+        words += 6.0 * kc + 3.0 * jj + 4;
+      }
+    }
+    // line 14: r = b - A x (true residual) into column 0; next cycle's line 1b
+    RK_TRY(stencil_launch(p, ST_RESID, x, b, r, p->part, p->counter,
+                           &p->st->rho2, nullptr, st));
+    RK_TRY(project_residual(p, kc, r, x, st));
+    RK_TRY(sync_state(p, st));
+    rho = std::sqrt(p->st_h->rho2);
+  }
+  info.matvecs = matvecs;
+  info.cycles_or_iters = cycles;
+  info.relres_true = rho / bnorm;
+  info.relres_est = est;
+  info.recycle_dim = p->kdim;
+  info.model_bytes = 8.0 * words * (double)p->n;
+  info.status = rho <= tolabs ? RK_OK : RK_E_NOT_CONVERGED;
+  return info.status;
+}
+
+// ---------------------------------------------------------------- rBiCGStab
+int solve_bicg(rk_problem* p, const double* b, double* x, const rk_solve_params& prm, rk_solve_info& info,
+               bool recycle, cudaStream_t st) {
+  const int maxmv = prm.max_matvec > 0 ? prm.max_matvec : 2000;
+  RK_TRY(ensure_capacity(p, p->kdim, std::max(p->mcap, 1), st));
+  if (!p->bicg) RK_TRY(alloc_into(p->ctx, &p->bicg, (size_t)7 * p->ld));
+  const int kc = recycle ? p->kdim : 0;
+  BicgVecs v{};
+  v.r = p->bicg;
+  v.rt = p->bicg + p->ld;
+  v.p = p->bicg + 2 * p->ld;
+  v.v = p->bicg + 3 * p->ld;
+  v.s = p->bicg + 4 * p->ld;
+  v.t = p->bicg + 5 * p->ld;
+  v.xt = p->bicg + 6 * p->ld;
+  double* eta1 = p->eta;
+  double* eta2 = p->eta + (p->kmax + 4);
+  double* xi = p->eta + 2 * (p->kmax + 4);
+  RK_TRY(norm2_into(p, b, 0, st));
+  { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_set_tol(p->st, prm.tol, st)); }
+  RK_TRY(sync_state(p, st));
+  const double bnorm = p->st_h->bnorm;
+  if (!std::isfinite(bnorm)) return fail(RK_E_INVALID, "b contains NaN or Inf");
+  if (bnorm == 0.0) {
+    RK_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * p->n, st));
+    RK_CUDA(cudaStreamSynchronize(st));
+    info.status = RK_OK;
+    info.recycle_dim = p->kdim;
+    return RK_OK;
+  }
+  const double tolabs = prm.tol * bnorm;
+  const double S = p->S;
+  double words = 0.0;
+  int matvecs = 0, its = 0, restarts = 0;
+  double rel = 0.0, upd = 0.0;
+  int status = RK_E_NOT_CONVERGED;
+  const int NB = 8;
+  while (true) {
+    // line 1: r = b - A x; line 1c: eta1 = C^T r, r -= C eta1, xi = -eta1
+    RK_TRY(stencil_launch(p, ST_RESID, x, b, v.r, p->part, p->counter,
+                           &p->st->rho2, nullptr, st));
+    if (kc) {
+      RK_TRY(dots_launch(p, p->Cblk(kc), kc, v.r, xi, nullptr, st));
+      RK_TRY(update_launch(p, p->Cblk(kc), kc, xi, v.r, &p->st->rho2, nullptr, st));
+      // xi = -eta1 (applied as x <- x - U xi at the end)
+      RK_TRY(gemm_launch(p, p->Ublk(kc), kc, nullptr, 0, nullptr, xi, 1, x, 1, st));
+      RK_CUDA(cudaMemsetAsync(xi, 0, sizeof(double) * kc, st));
+    }
+    { ProfScope ps_(&p->prof, PC_BICG, 24.0 * p->n, st); RK_CUDA(launch_copy(p->n, v.r, v.rt, st)); RK_CUDA(launch_fill(p->n, 0.0, v.xt, st)); }
+    { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_bicg_init(p->bs, &p->st->rho2, tolabs, maxmv - matvecs, st)); }
+    words += (S + 3) + 2.0 * kc + 4;
+    bool running = true;
+    while (running) {
+      for (int it = 0; it < NB; ++it) {
+        { ProfScope ps_(&p->prof, PC_BICG, 32.0 * p->n, st); RK_CUDA(launch_bicg_p(v, p->bs, p->n, st)); }
+        RK_TRY(stencil_launch(p, ST_PREC, v.p, nullptr, v.v, nullptr, nullptr, nullptr,
+                               &p->bs->stop, st));
+        RK_TRY(dots_launch(p, p->Cblk(kc), kc, v.v, eta1, &p->bs->stop, st, v.rt));
+        { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_bicg_alpha(p->bs, eta1, kc, st)); }
+        { ProfScope ps_(&p->prof, PC_BICG, 8.0 * (kc + (kc ? 5 : 3)) * (double)p->n, st); RK_CUDA(launch_bicg_s(v, p->bs, p->n, kc, p->Cblk(kc), p->ld, eta1, xi, p->part, p->counter, st)); }
+        RK_TRY(stencil_launch(p, ST_PREC, v.s, nullptr, v.t, nullptr, nullptr, nullptr,
+                               &p->bs->stop, st));
+        if (kc) RK_TRY(dots_launch(p, p->Cblk(kc), kc, v.t, eta2, &p->bs->stop, st));
+        { ProfScope ps_(&p->prof, PC_BICG, 8.0 * (kc + (kc ? 3 : 2)) * (double)p->n, st); RK_CUDA(launch_bicg_t(v, p->bs, p->n, kc, p->Cblk(kc), p->ld, eta2, p->part, p->counter, st)); }
+        { ProfScope ps_(&p->prof, PC_BICG, 56.0 * p->n, st); RK_CUDA(launch_bicg_r(v, p->bs, p->n, kc, eta1, eta2, xi, p->part, p->counter, st)); }
+      }
+      RK_CUDA(cudaMemcpyAsync(p->bs_h, p->bs, sizeof(BicgScalars), cudaMemcpyDeviceToHost, st));
+      RK_CUDA(cudaStreamSynchronize(st));
+      p->prof.flush();
+      if (p->bs_h->stop) running = false;
+    }
+    if (p->bs_h->half == 1) { ProfScope ps_(&p->prof, PC_BICG, 24.0 * p->n, st); RK_CUDA(launch_bicg_half(v, p->bs, p->n, st)); }
+    matvecs += p->bs_h->matvecs;
+    its += p->bs_h->it;
+    upd = p->bs_h->upd;
+    words += (double)p->bs_h->it * (2 * S + 4.0 * kc + 22);
+    const int flag = p->bs_h->flag;
+    // line 17a: x <- x + M^{-1} x~ - U xi  (one row-tiled pass over U and x~)
+    {
+      double* coefv = p->eta + 3 * (p->kmax + 4);  // [-xi (kc); 1]
+      { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_bicg_foldcoef(xi, kc, coefv, st)); }
+      RK_TRY(gemm_launch(p, p->Ublk(kc), kc, v.xt, 1, p->dinv, coefv, 1, x, 1, st));
+      words += kc + 4;
+    }
+    // true residual (replacement, R12)
+    RK_TRY(stencil_launch(p, ST_RESID, x, b, v.r, p->part, p->counter,
+                           &p->st->rho2, nullptr, st));
+    RK_TRY(sync_state(p, st));
+    rel = std::sqrt(p->st_h->rho2) / bnorm;
+    if (rel <= prm.tol) {
+      status = RK_OK;
+      break;
+    }
+    if (matvecs >= maxmv || flag == 3) {
+      status = RK_E_NOT_CONVERGED;
+      break;
+    }
+    if (restarts >= 3) {
+      status = flag == 2 ? RK_E_BREAKDOWN : RK_E_NOT_CONVERGED;
+      break;
+    }
+    restarts += 1;
+  }
+  info.matvecs = matvecs;
+  info.cycles_or_iters = its;
+  info.restarts = restarts;
+  info.relres_true = rel;
+  info.relres_est = upd / bnorm;
+  info.recycle_dim = p->kdim;
+  info.model_bytes = 8.0 * words * (double)p->n;
+  info.status = status;
+  return status;
+}
+
+void context_free(rk_context* c) {
+  dev_free(c, c->part);
+  dev_free(c, c->counter);
+  delete c;
+}
+
+int check_grid(const rk_grid* g) {
+  if (!g || g->nx <= 0 || g->ny <= 0 || g->nz <= 0) return fail(RK_E_INVALID, "grid extents must be positive");
+  return RK_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* rk_last_error(void) { return g_err.c_str(); }
+
+const char* rk_version(void) { return "rk 0.1 (sm_103a)"; }
+
+int rk_context_create(rk_alloc_fn alloc, rk_free_fn free_fn, void* user, rk_context** out) {
+  if (!out) return fail(RK_E_INVALID, "out is NULL");
+  if ((alloc == nullptr) != (free_fn == nullptr)) return fail(RK_E_INVALID, "alloc and free must both be given");
+  rk_context* c = new rk_context();
+  c->alloc = alloc;
+  c->free_fn = free_fn;
+  c->user = user;
+  RK_CUDA(cudaGetDevice(&c->device));
+  c->counter = (unsigned*)dev_alloc(c, 64 * sizeof(unsigned));
+  if (!c->counter) {
+    delete c;
+    return fail(RK_E_OOM, "counter allocation failed");
+  }
+  RK_CUDA(cudaMemset(c->counter, 0, 64 * sizeof(unsigned)));
+  *out = c;
+  return RK_OK;
+}
+
+void rk_context_destroy(rk_context* c) {
+  if (!c) return;
+  c->destroyed = true;
+  if (c->refs == 0) context_free(c);
+}
+
+int rk_create_problem(rk_context* ctx, const rk_grid* grid, int32_t S, const double* coef, void* stream,
+                      rk_problem** out) {
+  if (!ctx || !out || !coef) return fail(RK_E_INVALID, "NULL argument");
+  RK_TRY(check_grid(grid));
+  if (S != 7 && S != 19) return fail(RK_E_INVALID, "S must be 7 or 19");
+  cudaStream_t st = (cudaStream_t)stream;
+  rk_problem* p = new rk_problem();
+  p->ctx = ctx;
+  ctx->refs += 1;
+  p->S = S;
+  p->d.nx = grid->nx;
+  p->d.ny = grid->ny;
+  p->d.nz = grid->nz;
+  p->d.px = grid->periodic[0] ? 1 : 0;
+  p->d.py = grid->periodic[1] ? 1 : 0;
+  p->d.pz = grid->periodic[2] ? 1 : 0;
+  p->n = (int64_t)grid->nx * grid->ny * grid->nz;
+  p->d.n = p->n;
+  p->ld = round_up(p->n, 32);
+  auto cleanup = [&](int code) {
+    rk_problem_destroy(p);
+    return code;
+  };
+  int r;
+  if ((r = alloc_into(ctx, &p->coef, (size_t)S * p->n)) != RK_OK) return cleanup(r);
+  if ((r = alloc_into(ctx, &p->dinv, (size_t)p->ld)) != RK_OK) return cleanup(r);
+  if ((r = alloc_into(ctx, &p->counter, 64)) != RK_OK) return cleanup(r);
+  if ((r = alloc_into(ctx, &p->st, 1)) != RK_OK) return cleanup(r);
+  if ((r = alloc_into(ctx, &p->bs, 1)) != RK_OK) return cleanup(r);
+  if ((r = alloc_into(ctx, &p->istat, 16)) != RK_OK) return cleanup(r);
+  if (cudaMallocHost(&p->st_h, sizeof(SolveState)) != cudaSuccess ||
+      cudaMallocHost(&p->bs_h, sizeof(BicgScalars)) != cudaSuccess) {
+    cudaGetLastError();
+    return cleanup(fail(RK_E_OOM, "pinned host allocation failed"));
+  }
+  if (cudaMemcpyAsync(p->coef, coef, sizeof(double) * S * p->n, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(p->counter, 0, 64 * sizeof(unsigned), st) != cudaSuccess ||
+      cudaMemsetAsync(p->st, 0, sizeof(SolveState), st) != cudaSuccess ||
+      cudaMemsetAsync(p->bs, 0, sizeof(BicgScalars), st) != cudaSuccess)
+    return cleanup(fail(RK_E_CUDA, "copying the coefficients failed"));
+  // validation on the host copy (structural zeros, nonzero diagonal)
+  {
+    std::vector<double> h((size_t)S * p->n);
+    if (cudaMemcpyAsync(h.data(), p->coef, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return cleanup(fail(RK_E_CUDA, "reading the coefficients back failed"));
+    static const int OFF[19][3] = {{0, 0, 0},   {-1, 0, 0},  {1, 0, 0},   {0, -1, 0}, {0, 1, 0},
+                                   {0, 0, -1},  {0, 0, 1},   {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0},
+                                   {1, 1, 0},   {-1, 0, -1}, {1, 0, -1},  {-1, 0, 1}, {1, 0, 1},
+                                   {0, -1, -1}, {0, 1, -1},  {0, -1, 1},  {0, 1, 1}};
+    double fro = 0.0;
+    std::vector<double> dinv(p->ld, 0.0);
+    for (int kk = 0; kk < grid->nz; ++kk)
+      for (int j = 0; j < grid->ny; ++j)
+        for (int i = 0; i < grid->nx; ++i) {
+          const int64_t q = i + (int64_t)grid->nx * (j + (int64_t)grid->ny * kk);
+          const double a0 = h[q];
+          if (!(a0 != 0.0) || !std::isfinite(a0))
+            return cleanup(fail(RK_E_INVALID, "zero or non-finite diagonal at cell " + std::to_string(q)));
+          dinv[q] = 1.0 / a0;
+          for (int s = 0; s < S; ++s) {
+            const double c = h[(size_t)s * p->n + q];
+            if (!std::isfinite(c)) return cleanup(fail(RK_E_INVALID, "non-finite coefficient"));
+            fro += c * c;
+            if (s == 0 || c == 0.0) continue;
+            const int ii = i + OFF[s][0], jj = j + OFF[s][1], k2 = kk + OFF[s][2];
+            const bool out_x = (ii < 0 || ii >= grid->nx) && !grid->periodic[0];
+            const bool out_y = (jj < 0 || jj >= grid->ny) && !grid->periodic[1];
+            const bool out_z = (k2 < 0 || k2 >= grid->nz) && !grid->periodic[2];
+            if (out_x || out_y || out_z)
+              return cleanup(fail(RK_E_INVALID, "band " + std::to_string(s) + " of cell " + std::to_string(q) +
+                                                    " points out of a non-periodic face with a nonzero coefficient"));
+          }
+        }
+    p->anorm_f = std::sqrt(fro);
+    if (cudaMemcpyAsync(p->dinv, dinv.data(), sizeof(double) * p->ld, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return cleanup(fail(RK_E_CUDA, "uploading the preconditioner failed"));
+  }
+  *out = p;
+  return RK_OK;
+}
+
+void rk_problem_destroy(rk_problem* p) {
+  if (!p) return;
+  rk_context* c = p->ctx;
+  dev_free(c, p->coef);
+  dev_free(c, p->dinv);
+  dev_free(c, p->QB);
+  dev_free(c, p->Ub);
+  dev_free(c, p->bicg);
+  dev_free(c, p->small);
+  dev_free(c, p->eta);
+  dev_free(c, p->part);
+  dev_free(c, p->counter);
+  dev_free(c, p->st);
+  dev_free(c, p->bs);
+  dev_free(c, p->istat);
+  if (p->st_h) cudaFreeHost(p->st_h);
+  if (p->bs_h) cudaFreeHost(p->bs_h);
+  delete p;
+  c->refs -= 1;
+  if (c->destroyed && c->refs == 0) context_free(c);
+}
+
+int rk_apply(const rk_problem* p, const double* v, double* y, int32_t precond, void* stream) {
+  if (!p || !v || !y) return fail(RK_E_INVALID, "NULL argument");
+  RK_CUDA(launch_stencil(p->d, p->S, precond ? ST_PREC : ST_PLAIN, p->coef, p->dinv, v, nullptr, y, nullptr,
+                         nullptr, nullptr, nullptr, (cudaStream_t)stream));
+  RK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  return RK_OK;
+}
+
+int rk_residual(const rk_problem* p, const double* b, const double* x, double* r, void* stream) {
+  if (!p || !b || !x || !r) return fail(RK_E_INVALID, "NULL argument");
+  RK_CUDA(launch_stencil(p->d, p->S, ST_RESID, p->coef, nullptr, x, b, r, nullptr, nullptr, nullptr, nullptr,
+                         (cudaStream_t)stream));
+  RK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  return RK_OK;
+}
+
+int rk_dots(rk_context* ctx, int64_t n, int32_t nq, const double* Q, int64_t ld, const double* w, double* out,
+            void* stream) {
+  if (!ctx || !w || !out || (nq > 0 && !Q) || nq < 0 || n <= 0 || ld < n)
+    return fail(RK_E_INVALID, "bad argument to rk_dots");
+  const size_t need = (size_t)red_blocks(n) * (size_t)(nq + 1);
+  if (need > ctx->part_n) {
+    dev_free(ctx, ctx->part);
+    ctx->part = (double*)dev_alloc(ctx, need * sizeof(double));
+    ctx->part_n = ctx->part ? need : 0;
+    if (!ctx->part) return fail(RK_E_OOM, "partials allocation failed");
+  }
+  DotsArgs a{};
+  a.n = n;
+  a.nq = nq;
+  a.Q = Q;
+  a.ld = ld;
+  a.w = w;
+  a.part = ctx->part;
+  a.counter = ctx->counter;
+  a.out = out;
+  RK_CUDA(launch_dots(a, (cudaStream_t)stream));
+  RK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  return RK_OK;
+}
+
+int rk_set_recycle(rk_problem* p, const double* U, const double* C, int32_t k, void* stream) {
+  if (!p) return fail(RK_E_INVALID, "NULL problem");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (k < 0) return fail(RK_E_INVALID, "k < 0");
+  if (k == 0) {
+    p->kdim = 0;
+    return RK_OK;
+  }
+  if (!U) return fail(RK_E_INVALID, "U is NULL");
+  RK_TRY(ensure_capacity(p, k, std::max(p->mcap, 1), st));
+  p->kdim = 0;  // replaced below; on any error the problem is left without a recycle space
+  double* Ud = p->Ublk(k);
+  double* Cd = p->Cblk(k);
+  RK_CUDA(cudaMemcpy2DAsync(Ud, sizeof(double) * p->ld, U, sizeof(double) * p->n, sizeof(double) * p->n, k,
+                            cudaMemcpyDeviceToDevice, st));
+  double* G = p->eta;                       // k x k
+  double* Rinv = p->eta + (size_t)k * k;    // k x k
+  double* Rw = p->sb.hrws;                  // k x k scratch
+  if (!C) {
+    // line 1a: C~ = A U; thin QR by CholQR2 (C~ = C R), U <- U R^{-1}
+    for (int c = 0; c < k; ++c)
+      RK_CUDA(launch_stencil(p->d, p->S, ST_PLAIN, p->coef, nullptr, Ud + (int64_t)c * p->ld, nullptr,
+                             Cd + (int64_t)c * p->ld, nullptr, nullptr, nullptr, nullptr, st));
+    for (int pass = 0; pass < 2; ++pass) {
+      GramArgs g{};
+      g.n = p->n;
+      g.na = k;
+      g.nb = 0;
+      g.nu = k;
+      g.A = Cd;
+      g.lda = p->ld;
+      g.Bm = nullptr;
+      g.ldb = p->ld;
+      g.d = nullptr;
+      g.U = Cd;
+      g.ldu = p->ld;
+      g.part = p->part;
+      g.counter = p->counter;
+      g.out = G;
+      RK_CUDA(launch_gram(g, st));
+      RK_CUDA(launch_chol_rinv(k, G, Rinv, Rw, p->istat, st));
+      int hs = 0;
+      RK_CUDA(cudaMemcpyAsync(&hs, p->istat, sizeof(int), cudaMemcpyDeviceToHost, st));
+      RK_CUDA(cudaStreamSynchronize(st));
+      if (hs != 0) return fail(RK_E_INVALID, "A U is rank deficient (Cholesky of C~^T C~ failed)");
+      RK_TRY(gemm_launch(p, Cd, k, nullptr, 0, nullptr, Rinv, k, Cd, 0, st));
+      RK_TRY(gemm_launch(p, Ud, k, nullptr, 0, nullptr, Rinv, k, Ud, 0, st));
+    }
+  } else {
+    RK_CUDA(cudaMemcpy2DAsync(Cd, sizeof(double) * p->ld, C, sizeof(double) * p->n, sizeof(double) * p->n, k,
+                              cudaMemcpyDeviceToDevice, st));
+    // invariants: ||C^T C - I||_F and ||A U - C||_F
+    GramArgs g{};
+    g.n = p->n;
+    g.na = k;
+    g.nb = 0;
+    g.nu = k;
+    g.A = Cd;
+    g.lda = p->ld;
+    g.ldb = p->ld;
+    g.d = nullptr;
+    g.U = Cd;
+    g.ldu = p->ld;
+    g.part = p->part;
+    g.counter = p->counter;
+    g.out = G;
+    RK_CUDA(launch_gram(g, st));
+    std::vector<double> hg((size_t)k * k);
+    RK_CUDA(cudaMemcpyAsync(hg.data(), G, sizeof(double) * k * k, cudaMemcpyDeviceToHost, st));
+    RK_CUDA(cudaStreamSynchronize(st));
+    double e = 0.0;
+    for (int a = 0; a < k; ++a)
+      for (int c = 0; c < k; ++c) {
+        const double t = hg[a + (size_t)c * k] - (a == c ? 1.0 : 0.0);
+        e += t * t;
+      }
+    if (std::sqrt(e) > 1e-10) return fail(RK_E_RECYCLE_INVARIANT, "||C^T C - I||_F = " + std::to_string(std::sqrt(e)));
+    double* tmp = p->Vcol(0);
+    double eau = 0.0, un = 0.0;
+    for (int c = 0; c < k; ++c) {
+      RK_CUDA(launch_stencil(p->d, p->S, ST_PLAIN, p->coef, nullptr, Ud + (int64_t)c * p->ld, nullptr, tmp, nullptr,
+                             nullptr, nullptr, nullptr, st));
+      // tmp <- tmp - C_c, ||tmp||^2
+      double* onev = p->eta + (size_t)2 * k * k;
+      const double one = 1.0;
+      RK_CUDA(cudaMemcpyAsync(onev, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+      RK_TRY(update_launch(p, Cd + (int64_t)c * p->ld, 1, onev, tmp, &p->st->nrm2[2], nullptr, st));
+      RK_TRY(norm2_into(p, Ud + (int64_t)c * p->ld, 3, st));
+      RK_TRY(sync_state(p, st));
+      eau += p->st_h->nrm2[2];
+      un += p->st_h->nrm2[3];
+    }
+    if (std::sqrt(eau) > 1e-10 * p->anorm_f * std::sqrt(un))
+      return fail(RK_E_RECYCLE_INVARIANT, "||A U - C||_F too large: " + std::to_string(std::sqrt(eau)));
+  }
+  RK_CUDA(cudaStreamSynchronize(st));
+  p->kdim = k;
+  return RK_OK;
+}
+
+int rk_get_recycle(const rk_problem* p, double* U, double* C, int32_t* k, void* stream) {
+  if (!p || !k) return fail(RK_E_INVALID, "NULL argument");
+  if (*k < p->kdim) {
+    *k = p->kdim;
+    return fail(RK_E_INVALID, "capacity smaller than the recycle dimension");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int kd = p->kdim;
+  if (kd > 0) {
+    if (U)
+      RK_CUDA(cudaMemcpy2DAsync(U, sizeof(double) * p->n, p->Ublk(kd), sizeof(double) * p->ld,
+                                sizeof(double) * p->n, kd, cudaMemcpyDeviceToDevice, st));
+    if (C)
+      RK_CUDA(cudaMemcpy2DAsync(C, sizeof(double) * p->n, p->Cblk(kd), sizeof(double) * p->ld,
+                                sizeof(double) * p->n, kd, cudaMemcpyDeviceToDevice, st));
+    RK_CUDA(cudaStreamSynchronize(st));
+  }
+  *k = kd;
+  return RK_OK;
+}
+
+int rk_solve(rk_problem* p, const double* b, double* x, const rk_solve_params* params, rk_solve_info* info,
+             void* stream) {
+  if (!p || !b || !x || !params) return fail(RK_E_INVALID, "NULL argument");
+  rk_solve_params prm = *params;
+  if (!(prm.tol > 0.0)) return fail(RK_E_INVALID, "tol must be positive");
+  if (prm.precision != RK_FP64) return fail(RK_E_INVALID, "only RK_FP64 is supported in this version");
+  if (prm.k < 0) return fail(RK_E_INVALID, "k < 0");
+  rk_solve_info loc{};
+  rk_solve_info& inf = info ? *info : loc;
+  std::memset(&inf, 0, sizeof(inf));
+  cudaStream_t st = (cudaStream_t)stream;
+  int mode = prm.mode;
+  if (mode == RK_HYBRID) mode = p->solves < prm.hybrid_switch ? RK_RGCROT : RK_RBICGSTAB;
+  inf.mode_used = mode;
+  int rc;
+  if (mode == RK_GMRES || mode == RK_RGCROT) {
+    if (prm.m <= 0) return fail(RK_E_INVALID, "m must be positive");
+    rc = solve_gcr(p, b, x, prm, inf, mode == RK_RGCROT, mode == RK_RGCROT && prm.update_recycle != 0, st);
+  } else if (mode == RK_RBICGSTAB) {
+    rc = solve_bicg(p, b, x, prm, inf, prm.k > 0, st);
+  } else {
+    return fail(RK_E_INVALID, "unknown mode");
+  }
+  if (rc == RK_OK || rc == RK_E_NOT_CONVERGED || rc == RK_E_BREAKDOWN) p->solves += 1;
+  return rc;
+}
+
+int rk_profile_enable(rk_problem* p, int32_t on) {
+  if (!p) return fail(RK_E_INVALID, "NULL problem");
+  p->prof.reset();
+  p->prof.on = on != 0;
+  return RK_OK;
+}
+
+int rk_profile_read(rk_problem* p, rk_prof_entry* out, int32_t cap, int32_t* count) {
+  if (!p || !count) return fail(RK_E_INVALID, "NULL argument");
+  p->prof.flush();
+  int nout = 0;
+  for (int c = 0; c < PC_COUNT; ++c) {
+    if (nout < cap && out) {
+      std::memset(&out[nout], 0, sizeof(rk_prof_entry));
+      std::strncpy(out[nout].name, kProfNames[c], sizeof(out[nout].name) - 1);
+      out[nout].launches = p->prof.launches[c];
+      out[nout].ms = p->prof.ms[c];
+      out[nout].bytes = p->prof.bytes[c];
+    }
+    ++nout;
+  }
+  *count = nout;
+  return RK_OK;
+}
+
+int rk_problem_stats(const rk_problem* p, int32_t* solves, int32_t* recycle_dim, int64_t* n) {
+  if (!p) return fail(RK_E_INVALID, "NULL problem");
+  if (solves) *solves = p->solves;
+  if (recycle_dim) *recycle_dim = p->kdim;
+  if (n) *n = p->n;
+  return RK_OK;
+}
+
+}  // extern "C"

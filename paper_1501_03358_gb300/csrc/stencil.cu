@@ -1,0 +1,155 @@
+// Structured-grid stencil products (7 or 19 bands) with the right point-Jacobi
+// preconditioner fused into the operand load.
+//
+// Operator: the banded "diagonal storage" matrix of Sec. 2.1 ("Data Layout");
+// preconditioner: point Jacobi M = diag(A) applied from the right (Sec. 2.1,
+// "Preconditioners"). Each CTA owns a 32 x 8 tile of (x, y) columns and
+// marches through a chunk of z planes, keeping three consecutive planes of
+// z = M^{-1} v (with a one-cell halo) in shared memory, so every operand is
+// fetched from HBM once per tile and scaled once. Per output cell the
+// arithmetic order is fixed:
+//   w = c_0 * z_P;  w = fma(c_s, z_{nb(s)}, w) for s = 1 .. S-1
+// (out-of-domain neighbours contribute fma(0, 0, w)).
+#include "rk_internal.h"
+#include "rk_device.cuh"
+
+namespace rk {
+
+namespace {
+
+// neighbour coordinate for a halo load: c in [-1, n]; -1 when the plane or
+// row lies outside a non-periodic axis (or is never used).
+__device__ __forceinline__ int halo_coord(int c, int n, int periodic) {
+  if (c >= 0 && c < n) return c;
+  if (c == -1) return periodic ? n - 1 : -1;
+  if (c == n) return periodic ? 0 : -1;
+  return -1;
+}
+
+template <int S, int MODE>
+__global__ void __launch_bounds__(kTX* kTY) k_stencil(Dims d, const double* __restrict__ coef,
+                                                      const double* __restrict__ dinv,
+                                                      const double* __restrict__ v,
+                                                      const double* __restrict__ b, double* __restrict__ y,
+                                                      double* part, unsigned* counter, double* nrm2,
+                                                      const int* skip, int zchunk) {
+  if (skip != nullptr && *skip != 0) return;
+  __shared__ double sz[3][kTY + 2][kTX + 2];
+  __shared__ double red[32];
+  __shared__ int lastflag;
+  const int tx = threadIdx.x & (kTX - 1), ty = threadIdx.x / kTX;
+  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+  const int k0 = blockIdx.z * zchunk;
+  const int k1 = min(k0 + zchunk, d.nz);
+  const int gi = x0 + tx, gj = y0 + ty;
+  const bool active = gi < d.nx && gj < d.ny;
+  const int64_t N = d.n;
+  const int64_t plane = (int64_t)d.nx * d.ny;
+
+  auto load_plane = [&](int kk, int slot) {
+    const int kw = halo_coord(kk, d.nz, d.pz);
+    for (int t = threadIdx.x; t < (kTY + 2) * (kTX + 2); t += kTX * kTY) {
+      const int ly = t / (kTX + 2), lx = t - ly * (kTX + 2);
+      const int xw = halo_coord(x0 + lx - 1, d.nx, d.px);
+      const int yw = halo_coord(y0 + ly - 1, d.ny, d.py);
+      double val = 0.0;
+      if (kw >= 0 && xw >= 0 && yw >= 0) {
+        const int64_t q = (int64_t)xw + (int64_t)d.nx * yw + plane * kw;
+        if (MODE == ST_PREC)
+          val = __dmul_rn(__ldg(&v[q]), __ldg(&dinv[q]));
+        else
+          val = __ldg(&v[q]);
+      }
+      sz[slot][ly][lx] = val;
+    }
+  };
+
+  double acc2 = 0.0;
+  if (k0 < k1) {
+    load_plane(k0 - 1, (k0 + 2) % 3);
+    load_plane(k0, k0 % 3);
+    for (int k = k0; k < k1; ++k) {
+      load_plane(k + 1, (k + 1) % 3);
+      __syncthreads();
+      if (active) {
+        const int sc = k % 3, sm = (k + 2) % 3, sp = (k + 1) % 3;
+        const int64_t p = (int64_t)gi + (int64_t)d.nx * gj + plane * k;
+        const int cx = tx + 1, cy = ty + 1;
+        double w = __dmul_rn(__ldg(&coef[p]), sz[sc][cy][cx]);
+        w = fma(__ldg(&coef[1 * N + p]), sz[sc][cy][cx - 1], w);
+        w = fma(__ldg(&coef[2 * N + p]), sz[sc][cy][cx + 1], w);
+        w = fma(__ldg(&coef[3 * N + p]), sz[sc][cy - 1][cx], w);
+        w = fma(__ldg(&coef[4 * N + p]), sz[sc][cy + 1][cx], w);
+        w = fma(__ldg(&coef[5 * N + p]), sz[sm][cy][cx], w);
+        w = fma(__ldg(&coef[6 * N + p]), sz[sp][cy][cx], w);
+        if (S == 19) {
+          w = fma(__ldg(&coef[7 * N + p]), sz[sc][cy - 1][cx - 1], w);
+          w = fma(__ldg(&coef[8 * N + p]), sz[sc][cy - 1][cx + 1], w);
+          w = fma(__ldg(&coef[9 * N + p]), sz[sc][cy + 1][cx - 1], w);
+          w = fma(__ldg(&coef[10 * N + p]), sz[sc][cy + 1][cx + 1], w);
+          w = fma(__ldg(&coef[11 * N + p]), sz[sm][cy][cx - 1], w);
+          w = fma(__ldg(&coef[12 * N + p]), sz[sm][cy][cx + 1], w);
+          w = fma(__ldg(&coef[13 * N + p]), sz[sp][cy][cx - 1], w);
+          w = fma(__ldg(&coef[14 * N + p]), sz[sp][cy][cx + 1], w);
+          w = fma(__ldg(&coef[15 * N + p]), sz[sm][cy - 1][cx], w);
+          w = fma(__ldg(&coef[16 * N + p]), sz[sm][cy + 1][cx], w);
+          w = fma(__ldg(&coef[17 * N + p]), sz[sp][cy - 1][cx], w);
+          w = fma(__ldg(&coef[18 * N + p]), sz[sp][cy + 1][cx], w);
+        }
+        if (MODE == ST_RESID) w = __ldg(&b[p]) - w;
+        y[p] = w;
+        acc2 = fma(w, w, acc2);
+      }
+      __syncthreads();
+    }
+  }
+  if (part == nullptr) return;
+  const double s = block_sum(acc2, red);
+  const int nb = gridDim.x * gridDim.y * gridDim.z;
+  const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  if (threadIdx.x == 0) part[bid] = s;
+  if (arrive_last(counter, &lastflag)) reduce_partials(part, nb, 1, nrm2);
+}
+
+void stencil_grid(const Dims& d, dim3& grid, int& zchunk) {
+  const int tx = (d.nx + kTX - 1) / kTX, ty = (d.ny + kTY - 1) / kTY;
+  const int tiles = tx * ty;
+  int nzc = (3 * kNumSM + tiles - 1) / tiles;
+  if (nzc > d.nz) nzc = d.nz;
+  if (nzc < 1) nzc = 1;
+  zchunk = (d.nz + nzc - 1) / nzc;
+  nzc = (d.nz + zchunk - 1) / zchunk;
+  grid = dim3(tx, ty, nzc);
+}
+
+}  // namespace
+
+int stencil_blocks(const Dims& d) {
+  dim3 g;
+  int zc;
+  stencil_grid(d, g, zc);
+  return (int)(g.x * g.y * g.z);
+}
+
+cudaError_t launch_stencil(const Dims& d, int S, int mode, const double* coef, const double* dinv,
+                           const double* v, const double* b, double* y, double* part, unsigned* counter,
+                           double* nrm2, const int* skip, cudaStream_t st) {
+  dim3 grid;
+  int zchunk;
+  stencil_grid(d, grid, zchunk);
+  const dim3 block(kTX * kTY);
+#define RK_ST(SS, MM) k_stencil<SS, MM><<<grid, block, 0, st>>>(d, coef, dinv, v, b, y, part, counter, nrm2, skip, zchunk)
+  if (S == 7) {
+    if (mode == ST_PREC) RK_ST(7, ST_PREC);
+    else if (mode == ST_PLAIN) RK_ST(7, ST_PLAIN);
+    else RK_ST(7, ST_RESID);
+  } else {
+    if (mode == ST_PREC) RK_ST(19, ST_PREC);
+    else if (mode == ST_PLAIN) RK_ST(19, ST_PLAIN);
+    else RK_ST(19, ST_RESID);
+  }
+#undef RK_ST
+  return cudaGetLastError();
+}
+
+}  // namespace rk

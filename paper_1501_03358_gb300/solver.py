@@ -1,0 +1,195 @@
+"""Python face of librk: problems, recycle spaces and solves on torch CUDA
+tensors. Argument marshalling only — every step runs in librk's kernels.
+
+Shapes: coefficients (S, N) float64; vectors (N,) float64; a recycle space
+is a (k, N) float64 tensor whose row c is column c of U (so it is the N x k
+column-major array the C ABI expects)."""
+import ctypes
+
+import torch
+
+from . import native as N
+
+_TORCH_ALLOC = None
+
+
+def _torch_allocator():
+    """ctypes callbacks that draw device memory from torch's caching allocator."""
+    global _TORCH_ALLOC
+    if _TORCH_ALLOC is None:
+        def _alloc(size, user):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(size))
+            except Exception:
+                return None
+
+        def _free(ptr, user):
+            try:
+                torch.cuda.caching_allocator_delete(int(ptr))
+            except Exception:
+                pass
+
+        _TORCH_ALLOC = (N.ALLOC_FN(_alloc), N.FREE_FN(_free))
+    return _TORCH_ALLOC
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dptr(t: torch.Tensor):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _f64_cuda(t, shape=None):
+    if not torch.is_tensor(t):
+        t = torch.as_tensor(t)
+    t = t.to(device="cuda", dtype=torch.float64).contiguous()
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t
+
+
+class Context:
+    """A librk context on the current CUDA device (memory from torch)."""
+
+    def __init__(self, use_torch_allocator: bool = True):
+        self.lib = N.load()
+        self._h = ctypes.c_void_p()
+        if use_torch_allocator:
+            a, f = _torch_allocator()
+        else:
+            a, f = N.ALLOC_FN(), N.FREE_FN()
+        self._cb = (a, f)
+        N.check(self.lib.rk_context_create(a, f, None, ctypes.byref(self._h)))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def dots(self, Q: torch.Tensor, w: torch.Tensor, stream=None) -> torch.Tensor:
+        """out[q] = Q[q] . w for the rows of Q ((nq, N), row-contiguous)."""
+        Q = _f64_cuda(Q)
+        w = _f64_cuda(w)
+        n = w.numel()
+        nq = Q.shape[0] if Q.dim() == 2 else 0
+        out = torch.empty(max(nq, 1), dtype=torch.float64, device="cuda")
+        ld = Q.stride(0) if nq else n
+        N.check(self.lib.rk_dots(self._h, n, nq, _dptr(Q), ld, _dptr(w), _dptr(out), _stream_ptr(stream)))
+        return out[:nq]
+
+    def close(self):
+        if self._h:
+            self.lib.rk_context_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Problem:
+    """A banded operator on a structured grid with its recycle space."""
+
+    def __init__(self, ctx: Context, grid, coef, stream=None):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        nx, ny, nz = grid.nx, grid.ny, grid.nz
+        per = grid.periodic
+        self.n = nx * ny * nz
+        self.grid = grid
+        coef = _f64_cuda(coef)
+        self.S = coef.shape[0]
+        if coef.shape != (self.S, self.n):
+            raise ValueError("coef must be (S, N)")
+        g = N.rk_grid(nx, ny, nz, (ctypes.c_uint8 * 3)(*[1 if p else 0 for p in per]), 0)
+        self._h = ctypes.c_void_p()
+        N.check(self.lib.rk_create_problem(ctx.handle, ctypes.byref(g), self.S, _dptr(coef), _stream_ptr(stream),
+                                           ctypes.byref(self._h)))
+
+    def apply(self, v, precond=True, stream=None):
+        v = _f64_cuda(v, (self.n,))
+        y = torch.empty_like(v)
+        N.check(self.lib.rk_apply(self._h, _dptr(v), _dptr(y), 1 if precond else 0, _stream_ptr(stream)))
+        return y
+
+    def residual(self, b, x, stream=None):
+        b = _f64_cuda(b, (self.n,))
+        x = _f64_cuda(x, (self.n,))
+        r = torch.empty_like(b)
+        N.check(self.lib.rk_residual(self._h, _dptr(b), _dptr(x), _dptr(r), _stream_ptr(stream)))
+        return r
+
+    def set_recycle(self, U, C=None, stream=None):
+        if U is None or (torch.is_tensor(U) and U.numel() == 0):
+            N.check(self.lib.rk_set_recycle(self._h, None, None, 0, _stream_ptr(stream)))
+            return
+        U = _f64_cuda(U)
+        k = U.shape[0]
+        if U.shape != (k, self.n):
+            raise ValueError("U must be (k, N)")
+        Cp = None
+        if C is not None:
+            C = _f64_cuda(C, (k, self.n))
+            Cp = _dptr(C)
+        N.check(self.lib.rk_set_recycle(self._h, _dptr(U), Cp, k, _stream_ptr(stream)))
+
+    def stats(self):
+        s, k, n = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        N.check(self.lib.rk_problem_stats(self._h, ctypes.byref(s), ctypes.byref(k), ctypes.byref(n)))
+        return dict(solves=s.value, recycle_dim=k.value, n=n.value)
+
+    def profile(self, on: bool = True):
+        """Enable (and reset) or disable per-kernel-class timing of solves."""
+        N.check(self.lib.rk_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self):
+        """{class: {"launches", "ms", "bytes"}} accumulated since profile(True)."""
+        arr = (N.rk_prof_entry * 16)()
+        cnt = ctypes.c_int32()
+        N.check(self.lib.rk_profile_read(self._h, arr, 16, ctypes.byref(cnt)))
+        return {arr[i].name.decode(): dict(launches=arr[i].launches, ms=arr[i].ms, bytes=arr[i].bytes)
+                for i in range(min(cnt.value, 16))}
+
+    def get_recycle(self, stream=None):
+        k = self.stats()["recycle_dim"]
+        U = torch.empty((max(k, 1), self.n), dtype=torch.float64, device="cuda")
+        C = torch.empty_like(U)
+        kk = ctypes.c_int32(max(k, 1))
+        N.check(self.lib.rk_get_recycle(self._h, _dptr(U), _dptr(C), ctypes.byref(kk), _stream_ptr(stream)))
+        return U[: kk.value], C[: kk.value]
+
+    def solve(self, b, x0=None, tol=1e-8, m=40, k=20, mode="rGCROT", max_matvec=2000, hybrid_switch=5,
+              update_recycle=True, out=None, stream=None, check_status=False):
+        """Solve A x = b; returns (x, info dict). x0 defaults to 0."""
+        b = _f64_cuda(b, (self.n,))
+        if out is None:
+            out = torch.zeros_like(b) if x0 is None else _f64_cuda(x0, (self.n,)).clone()
+        elif x0 is not None:
+            out.copy_(_f64_cuda(x0, (self.n,)))
+        prm = N.rk_solve_params(float(tol), int(m), int(k), int(max_matvec), int(hybrid_switch), N.MODES[mode],
+                                N.RK_FP64, 1 if update_recycle else 0, 0)
+        if mode == "BiCGStab":
+            prm.k = 0
+        info = N.rk_solve_info()
+        rc = self.lib.rk_solve(self._h, _dptr(b), _dptr(out), ctypes.byref(prm), ctypes.byref(info),
+                               _stream_ptr(stream))
+        if rc not in (N.RK_OK, N.RK_E_NOT_CONVERGED, N.RK_E_BREAKDOWN) or (check_status and rc != N.RK_OK):
+            N.check(rc)
+        d = info.as_dict()
+        d["status_name"] = N.STATUS_NAMES.get(rc, rc)
+        return out, d
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.rk_problem_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

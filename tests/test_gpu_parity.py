@@ -1,0 +1,330 @@
+"""GPU path (librk through its C ABI) against the CPU oracle.
+
+Bars (element by element on the same seeded inputs):
+* structured-grid products A M^{-1} v, A v, b - A x: bit-exact (same band
+  order of fused multiply-adds on both sides);
+* block inner products: |d - d_ref| <= 1e-13 ||Q_q|| ||w|| (normwise);
+* solves: ||b - A x|| / ||b|| <= tol; ||x - x_oracle|| <= max(1e-6, 2 kappa
+  tol) ||x_oracle|| (two solutions that both meet the tolerance can differ by
+  up to kappa(A) tol, so 1e-6 is only attainable when kappa tol is below it);
+  matrix-vector products within +-2 of the oracle's, widened to the oracle's
+  own spread when rounding-level (1e-14 relative) perturbations of b move the
+  oracle's count by more than that (restarted runs of many cycles are chaotic
+  under rounding; the GPU orthogonalises by classical Gram-Schmidt with
+  reorthogonalisation and the oracle by modified Gram-Schmidt, so iterates
+  agree to rounding, not bit for bit);
+* recycle spaces: compared as subspaces (||C C^T - C' C'^T||_2), never column
+  by column, plus A U = C and C^T C = I.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from problems import Grid, make_config, random_operator, porous_skew_19pt
+from problems.operators import sphere_pack
+from problems.fields import rng_for
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1501_03358_gb300 import Context
+    c = Context()
+    yield c
+    c.close()
+
+
+def gpu_problem(ctx, grid, coef):
+    from paper_1501_03358_gb300 import Problem
+    return Problem(ctx, grid, torch.from_numpy(np.ascontiguousarray(coef)))
+
+
+def t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+GRIDS = [
+    ((37, 11, 5), (False, False, False)),
+    ((32, 8, 9), (True, False, True)),
+    ((33, 9, 7), (True, True, True)),
+    ((1, 1, 1), (False, False, False)),
+    ((2, 3, 4), (True, True, False)),
+    ((64, 17, 3), (False, True, False)),
+]
+
+
+@pytest.mark.parametrize("S", [7, 19])
+@pytest.mark.parametrize("dims,per", GRIDS)
+def test_stencil_bit_exact(ctx, S, dims, per):
+    g = Grid(*dims, per)
+    coef = random_operator(g, S, np.random.default_rng(hash((S, dims)) % 2**32))
+    prob = gpu_problem(ctx, g, coef)
+    op = oracle.Stencil(g, coef)
+    rng = np.random.default_rng(3)
+    v = rng.standard_normal(g.n)
+    b = rng.standard_normal(g.n)
+    y1 = prob.apply(t(v), precond=True).cpu().numpy()
+    y2 = prob.apply(t(v), precond=False).cpu().numpy()
+    r = prob.residual(t(b), t(v)).cpu().numpy()
+    assert np.array_equal(y1, op.apply_prec(v))
+    assert np.array_equal(y2, op.apply(v))
+    assert np.array_equal(r, op.residual(b, v))
+
+
+@pytest.mark.parametrize("n,nq", [(1, 1), (1000, 3), (4099, 17), (100003, 40), (262144, 61)])
+def test_block_dots(ctx, n, nq):
+    rng = np.random.default_rng(n + nq)
+    Q = rng.standard_normal((nq, n))
+    Q[0] *= 1e-3
+    w = rng.standard_normal(n)
+    got = ctx.dots(t(Q), t(w)).cpu().numpy()
+    ref = np.array([math.fsum(Q[q] * w) for q in range(nq)])  # exactly rounded products' sum
+    bound = 1e-13 * np.linalg.norm(Q, axis=1) * np.linalg.norm(w)
+    assert np.all(np.abs(got - ref) <= bound)
+
+
+_KAPPA = {}
+
+
+def kappa(grid, coef):
+    key = (grid, coef.tobytes()[:4096], coef.shape)
+    if key not in _KAPPA:
+        _KAPPA[key] = float(np.linalg.cond(oracle.dense_matrix(grid, coef)))
+    return _KAPPA[key]
+
+
+def perturbed(b, seed):
+    return b * (1.0 + 1e-14 * np.random.default_rng(seed).standard_normal(b.size))
+
+
+def mv_slack(run, b, base):
+    """+-2, or twice the spread of the oracle's own counts over three
+    rounding-level perturbations of b when that is larger (three samples
+    underestimate the spread of a chaotic count)."""
+    counts = [base] + [run(perturbed(b, s))["matvecs"] for s in (1, 2, 3)]
+    return max(2, 2 * (max(counts) - min(counts))), counts
+
+
+def check_solve(op, b, xg, info, xo, io, tol, slack=2, kap=None):
+    rel = np.linalg.norm(op.residual(b, xg)) / np.linalg.norm(b)
+    assert rel <= tol * 1.0000001, (rel, info)
+    assert info["status"] == 0, info
+    xtol = 1e-6 if kap is None else max(1e-6, 2.0 * kap * tol)
+    assert np.linalg.norm(xg - xo) <= xtol * np.linalg.norm(xo), (np.linalg.norm(xg - xo) / np.linalg.norm(xo), xtol)
+    assert abs(info["matvecs"] - io["matvecs"]) <= slack, (info["matvecs"], io["matvecs"], slack)
+
+
+def subspace_gap(C1, C2):
+    """||C1 C1^T - C2 C2^T||_2 for orthonormal N x k bases (sine of the largest
+    principal angle)."""
+    s = np.linalg.svd(C1.T @ C2, compute_uv=False)
+    s = np.clip(s, 0.0, 1.0)
+    return float(np.sqrt(max(0.0, 1.0 - s.min() ** 2)))
+
+
+@pytest.mark.parametrize("cfg_id,size,m", [(1, 12, 30), (2, 12, 40), (1, 10, 7), (1, 8, 200)])
+def test_gmres_parity(ctx, cfg_id, size, m):
+    cfg = make_config(cfg_id, size=size)
+    prob = gpu_problem(ctx, cfg.grid, cfg.coef)
+    op = oracle.Stencil(cfg.grid, cfg.coef)
+    b = cfg.rhs(0)
+    x, info = prob.solve(t(b), tol=1e-8, m=m, k=0, mode="GMRES", max_matvec=8000)
+    run = lambda bb: oracle.gmres(op, bb, tol=1e-8, m=m, max_matvec=8000)[1]
+    xo, io = oracle.gmres(op, b, tol=1e-8, m=m, max_matvec=8000)
+    slack, counts = mv_slack(run, b, io["matvecs"]) if io["cycles"] > 3 else (2, None)
+    check_solve(op, b, x.cpu().numpy(), info, xo, io, 1e-8, slack, kappa(cfg.grid, cfg.coef))
+
+
+@pytest.mark.parametrize("cfg_id,size,m,k,steps", [(1, 12, 30, 10, 5), (2, 12, 40, 20, 4), (1, 9, 6, 4, 4)])
+def test_rgcrot_sequence_parity(ctx, cfg_id, size, m, k, steps):
+    """rGCROT(m,k) over a sequence of right-hand sides with the recycle space
+    carried across steps (Algorithm 3 with line 14a after every cycle)."""
+    cfg = make_config(cfg_id, size=size)
+    prob = gpu_problem(ctx, cfg.grid, cfg.coef)
+    op = oracle.Stencil(cfg.grid, cfg.coef)
+    kap = kappa(cfg.grid, cfg.coef)
+    seq = oracle.RecyclingSequence(op, mode="rGCROT", m=m, k=k, tol=1e-8, max_matvec=5000)
+    for s in range(steps):
+        b = cfg.rhs(s)
+        x, info = prob.solve(t(b), tol=1e-8, m=m, k=k, mode="rGCROT", max_matvec=5000)
+        U0, C0 = seq.U, seq.C
+        xo, io = seq.solve(b)
+        slack = 2
+        if io["cycles"] > 3:
+            run = lambda bb: oracle.rgcrot(op, bb, tol=1e-8, m=m, k=k, U=U0, C=C0, max_matvec=5000)[3]
+            slack, _ = mv_slack(run, b, io["matvecs"])
+        check_solve(op, b, x.cpu().numpy(), info, xo, io, 1e-8, slack, kap)
+        U, C = prob.get_recycle()
+        U, C = U.cpu().numpy().T, C.cpu().numpy().T
+        assert U.shape[1] == seq.U.shape[1] == info["recycle_dim"]
+        A_U = np.stack([op.apply(u) for u in U.T], axis=1)
+        assert np.linalg.norm(A_U - C) <= 1e-10 * np.linalg.norm(C) * max(1.0, np.abs(cfg.coef).max())
+        assert np.linalg.norm(C.T @ C - np.eye(C.shape[1])) <= 1e-11
+
+
+@pytest.mark.parametrize("cfg_id,size,m,k", [(1, 10, 12, 6), (2, 10, 20, 8), (1, 8, 30, 10)])
+def test_harmonic_ritz_cycles_match_oracle(ctx, cfg_id, size, m, k):
+    """Recycle space after one and after two cycles (line 14a by harmonic Ritz
+    vectors, computed on the device) spans the oracle's (SciPy eig of the
+    pencil) to within rounding-level principal angles."""
+    cfg = make_config(cfg_id, size=size)
+    prob = gpu_problem(ctx, cfg.grid, cfg.coef)
+    op = oracle.Stencil(cfg.grid, cfg.coef)
+    b = cfg.rhs(0)
+    U = C = None
+    for cyc in range(2):
+        prob.solve(t(b), tol=1e-14, m=m, k=k, mode="rGCROT", max_matvec=m)
+        _, U, C, _ = oracle.rgcrot(op, b, tol=1e-14, m=m, k=k, U=U, C=C, max_matvec=m)
+        Ug, Cg = prob.get_recycle()
+        Cg = Cg.cpu().numpy().T
+        assert Cg.shape == C.shape
+        assert subspace_gap(Cg, C) <= 1e-6, (cyc, subspace_gap(Cg, C))
+
+
+def test_recycle_set_get_roundtrip_and_line_1a(ctx):
+    cfg = make_config(1, size=10)
+    prob = gpu_problem(ctx, cfg.grid, cfg.coef)
+    op = oracle.Stencil(cfg.grid, cfg.coef)
+    _, U, C, _ = oracle.rgcrot(op, cfg.rhs(0), tol=1e-10, m=10, k=6)
+    kk = U.shape[1]  # 6, or 5 when the cut falls inside a conjugate pair
+    # C given: stored as is
+    prob.set_recycle(t(U.T), t(C.T))
+    U2, C2 = prob.get_recycle()
+    assert np.array_equal(U2.cpu().numpy(), U.T) and np.array_equal(C2.cpu().numpy(), C.T)
+    # C omitted: line 1a forms C = orth(A U) and rescales U so that A U = C
+    Uraw = U @ np.diag([1.0, 2.0, -3.0, 0.5, 4.0, 1.5][:kk])
+    prob.set_recycle(t(Uraw.T))
+    U3, C3 = prob.get_recycle()
+    U3, C3 = U3.cpu().numpy().T, C3.cpu().numpy().T
+    # range(A U) equals range(C) only as far as the oracle's own A U = C holds
+    A_Uo = np.stack([op.apply(u) for u in U.T], axis=1)
+    assert subspace_gap(C3, C) <= 2.0 * np.linalg.norm(A_Uo - C, 2) + 1e-12
+    A_U = np.stack([op.apply(u) for u in U3.T], axis=1)
+    assert np.linalg.norm(A_U - C3) <= 1e-11 * np.linalg.norm(C3) * np.abs(cfg.coef).max()
+    assert np.linalg.norm(C3.T @ C3 - np.eye(kk)) <= 1e-12
+    # an inconsistent pair is refused
+    from paper_1501_03358_gb300.native import RKError, RK_E_RECYCLE_INVARIANT
+    with pytest.raises(RKError) as e:
+        prob.set_recycle(t(U.T), t((C * 1.01).T))
+    assert e.value.code == RK_E_RECYCLE_INVARIANT
+
+
+@pytest.mark.parametrize("with_space", [False, True])
+def test_rbicgstab_parity(ctx, with_space):
+    cfg = make_config(1, size=14)
+    prob = gpu_problem(ctx, cfg.grid, cfg.coef)
+    op = oracle.Stencil(cfg.grid, cfg.coef)
+    U = C = None
+    if with_space:
+        _, U, C, _ = oracle.rgcrot(op, cfg.rhs(0), tol=1e-9, m=20, k=8)
+        prob.set_recycle(t(U.T), t(C.T))
+    b = cfg.rhs(2)
+    x, info = prob.solve(t(b), tol=1e-8, k=8 if with_space else 0, mode="rBiCGStab", max_matvec=3000)
+    xo, io = oracle.rbicgstab(op, b, tol=1e-8, U=U, C=C, max_matvec=3000)
+    run = lambda bb: oracle.rbicgstab(op, bb, tol=1e-8, U=U, C=C, max_matvec=3000)[1]
+    slack, _ = mv_slack(run, b, io["matvecs"])
+    check_solve(op, b, x.cpu().numpy(), info, xo, io, 1e-8, slack, kappa(cfg.grid, cfg.coef))
+
+
+def test_hybrid_sequence_porous(ctx):
+    """Hybrid (Sec. 2.4) on a small skewed porous problem (19 points): rGCROT
+    for the first steps, then rBiCGStab with the recycle space frozen."""
+    n = (14, 12, 10)
+    solid, _ = sphere_pack(n, 2.5, 0.3, rng_for(77, 3), max_attempts=20000)
+    grid, coef = porous_skew_19pt(n, np.where(solid, 1e-4, 1.0), 15.0)
+    prob = gpu_problem(ctx, grid, coef)
+    op = oracle.Stencil(grid, coef)
+    kap = kappa(grid, coef)
+    seq = oracle.RecyclingSequence(op, mode="hybrid", m=20, k=10, tol=1e-8, hybrid_switch=2, max_matvec=4000)
+    base = np.random.default_rng(5).standard_normal(grid.n)
+    for s in range(4):
+        b = base + 0.05 * s * np.random.default_rng(100 + s).standard_normal(grid.n)
+        x, info = prob.solve(t(b), tol=1e-8, m=20, k=10, mode="hybrid", hybrid_switch=2, max_matvec=4000)
+        xo, io = seq.solve(b)
+        assert info["mode_used"] == (1 if s < 2 else 2)
+        slack = 2
+        rel = np.linalg.norm(op.residual(b, x.cpu().numpy())) / np.linalg.norm(b)
+        assert rel <= 1e-8 and info["status"] == 0
+        xtol = max(1e-6, 2.0 * kap * 1e-8)
+        assert np.linalg.norm(x.cpu().numpy() - xo) <= xtol * np.linalg.norm(xo)
+        if io["matvecs"] > 2 * slack:
+            U0, C0 = (seq.U, seq.C)
+            run = (lambda bb: oracle.rbicgstab(op, bb, tol=1e-8, U=U0, C=C0, max_matvec=4000)[1]) if s >= 2 else None
+            if run is not None:
+                slack = max(slack, mv_slack(run, b, io["matvecs"])[0])
+        assert abs(info["matvecs"] - io["matvecs"]) <= slack, (s, info["matvecs"], io["matvecs"])
+
+
+def test_zero_rhs_and_exact_recycling(ctx):
+    cfg = make_config(1, size=8)
+    prob = gpu_problem(ctx, cfg.grid, cfg.coef)
+    op = oracle.Stencil(cfg.grid, cfg.coef)
+    x, info = prob.solve(t(np.zeros(cfg.n)), mode="rGCROT", m=10, k=4)
+    assert info["matvecs"] == 0 and info["status"] == 0 and float(x.abs().max()) == 0.0
+    _, U, C, _ = oracle.rgcrot(op, cfg.rhs(0), tol=1e-10, m=10, k=4)
+    prob.set_recycle(t(U.T), t(C.T))
+    bb = C @ np.array([1.0, -2.0, 0.5, 3.0])[: C.shape[1]]
+    for mode in ("rGCROT", "rBiCGStab"):
+        prob.set_recycle(t(U.T), t(C.T))
+        x, info = prob.solve(t(bb), tol=1e-8, m=10, k=4, mode=mode, update_recycle=False)
+        assert info["matvecs"] == 0, (mode, info)
+        assert np.linalg.norm(op.residual(bb, x.cpu().numpy())) <= 1e-8 * np.linalg.norm(bb)
+
+
+def test_invalid_operator_rejected(ctx):
+    from paper_1501_03358_gb300.native import RKError, RK_E_INVALID
+    g = Grid(4, 4, 4, (False, False, False))
+    coef = random_operator(g, 7, np.random.default_rng(0))
+    coef[1, 0] = 0.5  # band -x of cell (0,0,0) points out of the x=0 face
+    with pytest.raises(RKError) as e:
+        gpu_problem(ctx, g, coef)
+    assert e.value.code == RK_E_INVALID
+    coef = random_operator(g, 7, np.random.default_rng(0))
+    coef[0, 5] = 0.0
+    with pytest.raises(RKError):
+        gpu_problem(ctx, g, coef)
+
+
+def test_nan_rhs_rejected(ctx):
+    from paper_1501_03358_gb300.native import RKError, RK_E_INVALID
+    cfg = make_config(1, size=6)
+    prob = gpu_problem(ctx, cfg.grid, cfg.coef)
+    b = cfg.rhs(0)
+    b[3] = np.nan
+    with pytest.raises(RKError) as e:
+        prob.solve(t(b))
+    assert e.value.code == RK_E_INVALID
+
+
+def test_not_converged_returns_last_iterate(ctx):
+    cfg = make_config(1, size=12)
+    prob = gpu_problem(ctx, cfg.grid, cfg.coef)
+    op = oracle.Stencil(cfg.grid, cfg.coef)
+    b = cfg.rhs(0)
+    x, info = prob.solve(t(b), tol=1e-12, m=5, k=0, mode="GMRES", max_matvec=10)
+    assert info["status_name"] == "RK_E_NOT_CONVERGED" and info["matvecs"] == 10
+    xo, io = oracle.gmres(op, b, tol=1e-12, m=5, max_matvec=10)
+    assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-8 * np.linalg.norm(xo)
+
+
+def test_full_size_channel_operator_and_solve(ctx):
+    """At the 128^3 channel size: every SpMV output bit-exact against the
+    oracle, and one rGCROT(40,20) solve reaching the tolerance with its true
+    residual recomputed by the oracle."""
+    cfg = make_config(2)
+    prob = gpu_problem(ctx, cfg.grid, cfg.coef)
+    op = oracle.Stencil(cfg.grid, cfg.coef)
+    v = np.random.default_rng(1).standard_normal(cfg.n)
+    assert np.array_equal(prob.apply(t(v)).cpu().numpy(), op.apply_prec(v))
+    b = cfg.rhs(0)
+    x, info = prob.solve(t(b), tol=1e-8, m=40, k=20, mode="rGCROT", max_matvec=20000)
+    rel = np.linalg.norm(op.residual(b, x.cpu().numpy())) / np.linalg.norm(b)
+    assert info["status"] == 0 and rel <= 1e-8
+    assert abs(rel - info["relres_true"]) <= 1e-3 * rel
