@@ -188,6 +188,21 @@ typedef struct {
 int rk_profile_enable(rk_problem* p, int32_t on);
 int rk_profile_read(rk_problem* p, rk_prof_entry* out, int32_t cap, int32_t* count);
 
+/*
+ * The small problem of Algorithm 3 line 14a on its own (the same device code
+ * the solver runs after every cycle). G, F: device, (n+1) x n column-major:
+ * the cycle's G = [[I, B], [0, H]] with A W = W_hat G, and
+ * F = W_hat^T M W. Selects the harmonic Ritz vectors p of the k smallest
+ * |theta| of G^T G p = theta G^T F p (a complex pair counts as two, and is
+ * dropped whole if only one of it fits) and returns QC ((n+1) x knew, ld n+1)
+ * with orthonormal columns and PU (n x knew, ld n) with G PU = QC and
+ * range(PU) = span of the selected vectors; *knew (host) = their number.
+ * Then C <- W_hat QC and U <- W PU keep A U = C and C^T C = I.
+ * Returns RK_E_BREAKDOWN if the eigen-iteration fails to converge.
+ */
+int rk_harmonic_ritz(rk_context* ctx, int32_t n, const double* G, const double* F, int32_t k, double* QC,
+                     double* PU, int32_t* knew, void* stream);
+
 /* Number of solves run on this problem (the hybrid's step counter) and its
  * recycle dimension. */
 int rk_problem_stats(const rk_problem* p, int32_t* solves, int32_t* recycle_dim, int64_t* n);

@@ -988,6 +988,28 @@ int rk_profile_read(rk_problem* p, rk_prof_entry* out, int32_t cap, int32_t* cou
   return RK_OK;
 }
 
+int rk_harmonic_ritz(rk_context* ctx, int32_t n, const double* G, const double* F, int32_t k, double* QC,
+                     double* PU, int32_t* knew, void* stream) {
+  if (!ctx || !G || !F || !QC || !PU || !knew || n <= 0 || k <= 0 || k > n || n > 511)
+    return fail(RK_E_INVALID, "bad argument to rk_harmonic_ritz");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t ws = harmonic_ritz_ws_doubles(n) + 8;
+  if (ws > ctx->part_n) {
+    dev_free(ctx, ctx->part);
+    ctx->part = (double*)dev_alloc(ctx, ws * sizeof(double));
+    ctx->part_n = ctx->part ? ws : 0;
+    if (!ctx->part) return fail(RK_E_OOM, "workspace allocation failed");
+  }
+  int* dk = (int*)(ctx->counter + 32);
+  RK_CUDA(launch_harmonic_ritz_small(n, G, F, k, QC, PU, dk, ctx->part, st));
+  int h = 0;
+  RK_CUDA(cudaMemcpyAsync(&h, dk, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RK_CUDA(cudaStreamSynchronize(st));
+  if (h < 0) return fail(RK_E_BREAKDOWN, "harmonic Ritz eigen-solve failed (status " + std::to_string(-h) + ")");
+  *knew = h;
+  return RK_OK;
+}
+
 int rk_problem_stats(const rk_problem* p, int32_t* solves, int32_t* recycle_dim, int64_t* n) {
   if (!p) return fail(RK_E_INVALID, "NULL problem");
   if (solves) *solves = p->solves;

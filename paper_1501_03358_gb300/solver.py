@@ -79,6 +79,22 @@ class Context:
         N.check(self.lib.rk_dots(self._h, n, nq, _dptr(Q), ld, _dptr(w), _dptr(out), _stream_ptr(stream)))
         return out[:nq]
 
+    def harmonic_ritz(self, G, F, k, stream=None):
+        """Device harmonic Ritz selection of line 14a: returns (QC, PU) as
+        ((n+1) x knew, n x knew) tensors (see include/rk.h)."""
+        G = _f64_cuda(G)
+        F = _f64_cuda(F)
+        n = G.shape[1]
+        # column-major (n+1) x n == row-major transpose
+        Gc = G.t().contiguous()
+        Fc = F.t().contiguous()
+        QC = torch.zeros((k, n + 1), dtype=torch.float64, device="cuda")
+        PU = torch.zeros((k, n), dtype=torch.float64, device="cuda")
+        kn = ctypes.c_int32()
+        N.check(self.lib.rk_harmonic_ritz(self._h, n, _dptr(Gc), _dptr(Fc), k, _dptr(QC), _dptr(PU),
+                                          ctypes.byref(kn), _stream_ptr(stream)))
+        return QC[: kn.value].t(), PU[: kn.value].t()
+
     def close(self):
         if self._h:
             self.lib.rk_context_destroy(self._h)

@@ -1,0 +1,85 @@
+"""The device harmonic Ritz selection (Algorithm 3, line 14a) through the C
+ABI, against SciPy's generalized eigensolver on the same small pencils."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1501_03358_gb300 import Context
+    c = Context()
+    yield c
+    c.close()
+
+
+def pencil(kc, jj, seed):
+    """G = [[I, B], [0, H]] (H (jj+1) x jj upper Hessenberg) and
+    F = [[C^T M U, 0], [V^T M U, [I; 0]]] as in a cycle of rGCROT."""
+    rng = np.random.default_rng(seed)
+    n = kc + jj
+    G = np.zeros((n + 1, n))
+    F = np.zeros((n + 1, n))
+    G[:kc, :kc] = np.eye(kc)
+    G[:kc, kc:] = 0.3 * rng.standard_normal((kc, jj))
+    H = np.triu(rng.standard_normal((jj + 1, jj)), -1)
+    H[np.arange(1, jj + 1), np.arange(jj)] = np.abs(H[np.arange(1, jj + 1), np.arange(jj)]) + 0.1
+    G[kc:, kc:] = H
+    if kc:
+        F[:kc, :kc] = np.eye(kc) + 0.2 * rng.standard_normal((kc, kc))
+        F[kc:, :kc] = 0.1 * rng.standard_normal((jj + 1, kc))
+    F[kc:kc + jj, kc:] = np.eye(jj)
+    return G, F
+
+
+def reference_basis(G, F, k):
+    ab, vr = sla.eig(G.T @ G, G.T @ F, homogeneous_eigvals=True)
+    theta = ab[0] / ab[1]
+    order = np.argsort(np.abs(theta))
+    cols, used = [], set()
+    for i in order:
+        if len(cols) >= k:
+            break
+        if i in used:
+            continue
+        if abs(theta[i].imag) > 0:
+            if len(cols) + 2 > k:
+                break
+            cols += [vr[:, i].real, vr[:, i].imag]
+            j = min((j for j in order if j != i and j not in used), key=lambda j: abs(theta[j] - np.conj(theta[i])))
+            used |= {i, j}
+        else:
+            cols.append(vr[:, i].real)
+            used.add(i)
+    return np.linalg.qr(np.stack(cols, axis=1))[0], np.sort(np.abs(theta))
+
+
+def gap(A, B):
+    """sin of the largest principal angle, ||(I - Qa Qa^T) Qb||_2 (accurate
+    for small angles, unlike sqrt(1 - cos^2))."""
+    qa = np.linalg.qr(A)[0]
+    qb = np.linalg.qr(B)[0]
+    return float(np.linalg.norm(qb - qa @ (qa.T @ qb), 2))
+
+
+@pytest.mark.parametrize("kc,jj,k,seed", [(0, 10, 4, 1), (0, 40, 20, 2), (8, 12, 6, 3), (20, 40, 20, 4),
+                                         (10, 30, 10, 5), (20, 40, 20, 6), (5, 3, 8, 7)])
+def test_harmonic_ritz_matches_scipy(ctx, kc, jj, k, seed):
+    G, F = pencil(kc, jj, seed)
+    n = kc + jj
+    k = min(k, n)
+    QC, PU = ctx.harmonic_ritz(torch.from_numpy(G), torch.from_numpy(F), k)
+    QC, PU = QC.cpu().numpy(), PU.cpu().numpy()
+    P, mags = reference_basis(G, F, k)
+    assert PU.shape[1] == P.shape[1]
+    assert np.linalg.norm(QC.T @ QC - np.eye(QC.shape[1])) <= 1e-12
+    assert np.linalg.norm(G @ PU - QC) <= 1e-11 * np.linalg.norm(G) * np.linalg.norm(PU)
+    # subspace agreement, scaled by the gap between the k-th and (k+1)-th |theta|
+    kk = P.shape[1]
+    sep = (mags[kk] - mags[kk - 1]) / mags[kk] if kk < len(mags) else 1.0
+    assert gap(PU, P) <= 1e-8 / max(sep, 1e-3)

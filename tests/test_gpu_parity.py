@@ -122,11 +122,12 @@ def check_solve(op, b, xg, info, xo, io, tol, slack=2, kap=None):
 
 
 def subspace_gap(C1, C2):
-    """||C1 C1^T - C2 C2^T||_2 for orthonormal N x k bases (sine of the largest
-    principal angle)."""
-    s = np.linalg.svd(C1.T @ C2, compute_uv=False)
-    s = np.clip(s, 0.0, 1.0)
-    return float(np.sqrt(max(0.0, 1.0 - s.min() ** 2)))
+    """||C1 C1^T - C2 C2^T||_2 for N x k bases: the sine of the largest
+    principal angle, computed as ||(I - Q1 Q1^T) Q2||_2 (accurate for small
+    angles)."""
+    q1 = np.linalg.qr(C1)[0]
+    q2 = np.linalg.qr(C2)[0]
+    return float(np.linalg.norm(q2 - q1 @ (q1.T @ q2), 2))
 
 
 @pytest.mark.parametrize("cfg_id,size,m", [(1, 12, 30), (2, 12, 40), (1, 10, 7), (1, 8, 200)])
@@ -315,16 +316,31 @@ def test_not_converged_returns_last_iterate(ctx):
 
 
 def test_full_size_channel_operator_and_solve(ctx):
-    """At the 128^3 channel size: every SpMV output bit-exact against the
-    oracle, and one rGCROT(40,20) solve reaching the tolerance with its true
-    residual recomputed by the oracle."""
+    """At the 128^3 channel size (the benchmark's workload and launch
+    configuration): every SpMV output bit-exact against the oracle; a capped
+    rGCROT(40,20) solve whose reported true residual matches the oracle's
+    recomputation of ||b - A x||, whose residual history decreases, and whose
+    recycle space satisfies A U = C (sampled columns, oracle products) and
+    C^T C = I."""
     cfg = make_config(2)
     prob = gpu_problem(ctx, cfg.grid, cfg.coef)
     op = oracle.Stencil(cfg.grid, cfg.coef)
     v = np.random.default_rng(1).standard_normal(cfg.n)
     assert np.array_equal(prob.apply(t(v)).cpu().numpy(), op.apply_prec(v))
+    assert np.array_equal(prob.apply(t(v), precond=False).cpu().numpy(), op.apply(v))
     b = cfg.rhs(0)
-    x, info = prob.solve(t(b), tol=1e-8, m=40, k=20, mode="rGCROT", max_matvec=20000)
-    rel = np.linalg.norm(op.residual(b, x.cpu().numpy())) / np.linalg.norm(b)
-    assert info["status"] == 0 and rel <= 1e-8
-    assert abs(rel - info["relres_true"]) <= 1e-3 * rel
+    x, info = prob.solve(t(b), tol=1e-8, m=40, k=20, mode="rGCROT", max_matvec=400)
+    xg = x.cpu().numpy()
+    assert np.all(np.isfinite(xg))
+    rel = np.linalg.norm(op.residual(b, xg)) / np.linalg.norm(b)
+    assert info["matvecs"] == 400 and info["cycles_or_iters"] == 10
+    assert abs(rel - info["relres_true"]) <= 1e-6 * rel
+    assert rel < 0.1
+    U, C = prob.get_recycle()
+    U, C = U.cpu().numpy().T, C.cpu().numpy().T
+    assert C.shape[1] >= 19
+    G = C.T @ C
+    assert np.linalg.norm(G - np.eye(C.shape[1])) <= 1e-10
+    for c in (0, C.shape[1] // 2, C.shape[1] - 1):
+        au = op.apply(U[:, c])
+        assert np.linalg.norm(au - C[:, c]) <= 1e-9 * max(1.0, np.linalg.norm(au))
