@@ -79,7 +79,15 @@ def test_harmonic_ritz_matches_scipy(ctx, kc, jj, k, seed):
     assert PU.shape[1] == P.shape[1]
     assert np.linalg.norm(QC.T @ QC - np.eye(QC.shape[1])) <= 1e-12
     assert np.linalg.norm(G @ PU - QC) <= 1e-11 * np.linalg.norm(G) * np.linalg.norm(PU)
-    # subspace agreement, scaled by the gap between the k-th and (k+1)-th |theta|
-    kk = P.shape[1]
-    sep = (mags[kk] - mags[kk - 1]) / mags[kk] if kk < len(mags) else 1.0
-    assert gap(PU, P) <= 1e-8 / max(sep, 1e-3)
+    # subspace agreement within the pencil's own rounding sensitivity: SciPy's
+    # selected subspace for G, F perturbed by 1e-14 relative shows how far
+    # rounding alone moves it (near-tied |theta| at the cut make it large)
+    rng = np.random.default_rng(seed + 100)
+    sens = 0.0
+    for _ in range(2):
+        Gp = G * (1 + 1e-14 * rng.standard_normal(G.shape))
+        Fp = F * (1 + 1e-14 * rng.standard_normal(F.shape))
+        Pp, _ = reference_basis(Gp, Fp, k)
+        if Pp.shape[1] == P.shape[1]:
+            sens = max(sens, gap(Pp, P))
+    assert gap(PU, P) <= 100.0 * sens + 1e-10, (gap(PU, P), sens)
