@@ -203,6 +203,31 @@ int rk_profile_read(rk_problem* p, rk_prof_entry* out, int32_t cap, int32_t* cou
 int rk_harmonic_ritz(rk_context* ctx, int32_t n, const double* G, const double* F, int32_t k, double* QC,
                      double* PU, int32_t* knew, void* stream);
 
+/*
+ * rk_dots without any device allocation. The paper has no counterpart: this
+ * entry point exists for callers that must not allocate device memory once
+ * they are running — for instance a serving process that reserves its whole
+ * memory budget at start-up, or an application whose memory manager forbids
+ * cudaMalloc on its critical path (cudaMalloc can synchronise the device and
+ * fragment a pool). rk_dots itself draws its reduction scratch from the
+ * context's allocator; this variant uses a fixed scratch array compiled into
+ * the library instead (304 KiB of per-block partial sums plus a counter, in
+ * static device memory that every GPU loading the library holds until the
+ * process exits), and calls no cudaMalloc, cudaFree or allocating routine.
+ *
+ * Same arguments and results as rk_dots (out[q] = Q_q^T w, q < nq, in the
+ * same fixed reduction order, so the two agree bit for bit), without a
+ * context. Limit: nq <= 64 columns (larger nq returns RK_E_INVALID with a
+ * message); any n. The first call on a device looks up the scratch array's
+ * device address (cudaGetSymbolAddress) and clears its counter, which
+ * synchronises that device: make the first call on each device before any
+ * stream capture. All calls share the one scratch array, whose contents
+ * persist from call to call: calls whose kernels overlap on a GPU (other
+ * threads or streams) race on it and must be serialised by the caller.
+ */
+int rk_dots_noalloc(int64_t n, int32_t nq, const double* Q, int64_t ld, const double* w, double* out,
+                    void* stream);
+
 /* Number of solves run on this problem (the hybrid's step counter) and its
  * recycle dimension. */
 int rk_problem_stats(const rk_problem* p, int32_t* solves, int32_t* recycle_dim, int64_t* n);

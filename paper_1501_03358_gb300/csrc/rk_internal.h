@@ -115,6 +115,9 @@ int gram_blocks(int64_t n);
 cudaError_t launch_copy(int64_t n, const double* src, double* dst, cudaStream_t st);
 cudaError_t launch_fill(int64_t n, double val, double* dst, cudaStream_t st);
 
+// Thread-local message returned by rk_last_error (solver.cu).
+void set_last_error(const char* msg);
+
 // ---- smalldense.cu : single-block kernels on the small Hessenberg problems.
 struct ArnoldiState;  // defined in solver.cu / smalldense.cu shared header below
 

@@ -34,6 +34,11 @@ int fail(int code, const std::string& msg) {
   g_err = msg;
   return code;
 }
+}  // namespace
+
+void rk::set_last_error(const char* msg) { g_err = msg; }
+
+namespace {
 
 #define RK_CUDA(x)                                                                                \
   do {                                                                                            \

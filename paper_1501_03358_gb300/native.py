@@ -27,7 +27,8 @@ RK_FP64, RK_MIXED = 0, 1
 # Every exported symbol that include/rk.h declares.
 EXPORTS = ("rk_last_error", "rk_version", "rk_context_create", "rk_context_destroy", "rk_create_problem",
            "rk_problem_destroy", "rk_set_recycle", "rk_get_recycle", "rk_solve", "rk_apply", "rk_residual",
-           "rk_dots", "rk_problem_stats", "rk_profile_enable", "rk_profile_read", "rk_harmonic_ritz")
+           "rk_dots", "rk_problem_stats", "rk_profile_enable", "rk_profile_read", "rk_harmonic_ritz",
+           "rk_dots_noalloc")
 
 
 class rk_grid(ctypes.Structure):
@@ -94,6 +95,7 @@ def load(path: str = LIB_PATH):
     L.rk_problem_stats.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i64)]
     L.rk_profile_enable.argtypes = [vp, i32]
     L.rk_harmonic_ritz.argtypes = [vp, i32, vp, vp, i32, vp, vp, ctypes.POINTER(i32), vp]
+    L.rk_dots_noalloc.argtypes = [i64, i32, vp, i64, vp, vp, vp]
     L.rk_profile_read.argtypes = [vp, ctypes.POINTER(rk_prof_entry), i32, ctypes.POINTER(i32)]
     for name in EXPORTS:
         if name not in ("rk_context_destroy", "rk_problem_destroy", "rk_last_error", "rk_version"):
