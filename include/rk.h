@@ -28,7 +28,10 @@
  *    exactly 0 (checked by rk_create_problem).
  *  - The recycle space is stored in x-space: U, C are N x k column-major
  *    (column c at offset c*N) with A U = C and C^T C = I; the R of line 1a
- *    is folded into U.
+ *    is folded into U. Inside the library U, C and the Arnoldi basis are kept
+ *    as double-float pairs (hi + lo of two FP32 numbers, about 48 significant
+ *    bits) and all projection arithmetic is double-float: a recycle space set
+ *    and read back agrees with the original to about 2^-46 relative.
  *  - Every pointer argument named "device" is CUDA device memory owned by
  *    the caller and only read or written during the call. Host pointers are
  *    named so. All GPU work is ordered on the stream passed to the call; the

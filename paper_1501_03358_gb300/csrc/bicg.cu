@@ -8,6 +8,7 @@
 #include <cmath>
 #include "rk_bicg.h"
 #include "rk_device.cuh"
+#include "rk_df.cuh"
 
 namespace rk {
 
@@ -53,21 +54,33 @@ __global__ void k_bicg_alpha(BicgScalars* s, const double* dots, int kc) {
 // half step of lines 10-10a is recorded (xi += alpha eta1 here, x~ += alpha p
 // by k_bicg_half).
 __global__ void __launch_bounds__(kRedThreads) k_bicg_s(BicgVecs v, BicgScalars* s, int64_t n, int kc,
-                                                        const double* C, int64_t ld, const double* eta1,
+                                                        const float2* C, int64_t ld, const double* eta1,
                                                         double* xi, double* part, unsigned* counter) {
   if (stopped(s)) return;
   __shared__ double red[32];
   __shared__ int lastflag;
   __shared__ double se[256];
-  for (int q = threadIdx.x; q < kc; q += blockDim.x) se[q] = eta1[q];
+  __shared__ float2 sedf[256];
+  for (int q = threadIdx.x; q < kc; q += blockDim.x) {
+    se[q] = eta1[q];
+    const df e = df_from_double(eta1[q]);
+    sedf[q] = make_float2(e.hi, e.lo);
+  }
   __syncthreads();
   const double alpha = s->alpha;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     double vi = v.v[i];
-    for (int q = 0; q < kc; ++q) vi = fma(-__ldg(&C[(int64_t)q * ld + i]), se[q], vi);
-    if (kc) v.v[i] = vi;
+    if (kc) {
+      float sh = 0.f, sl = 0.f;  // C eta1 in double-float
+      for (int q = 0; q < kc; ++q) {
+        const float2 c = __ldg(&C[(int64_t)q * ld + i]);
+        df_mac(sh, sl, c.x, c.y, sedf[q].x, sedf[q].y);
+      }
+      vi = (vi - (double)sh) - (double)sl;
+      v.v[i] = vi;
+    }
     const double si = fma(-alpha, vi, v.r[i]);
     v.s[i] = si;
     acc = fma(si, si, acc);
@@ -104,20 +117,30 @@ __global__ void __launch_bounds__(kRedThreads) k_bicg_half(BicgVecs v, BicgScala
 
 // lines 12a-13: t <- t - C eta2; omega = t^T s / t^T t (last block).
 __global__ void __launch_bounds__(kRedThreads) k_bicg_t(BicgVecs v, BicgScalars* s, int64_t n, int kc,
-                                                        const double* C, int64_t ld, const double* eta2,
+                                                        const float2* C, int64_t ld, const double* eta2,
                                                         double* part, unsigned* counter) {
   if (stopped(s)) return;
   __shared__ double red[32];
   __shared__ int lastflag;
-  __shared__ double se[256];
-  for (int q = threadIdx.x; q < kc; q += blockDim.x) se[q] = eta2[q];
+  __shared__ float2 sedf[256];
+  for (int q = threadIdx.x; q < kc; q += blockDim.x) {
+    const df e = df_from_double(eta2[q]);
+    sedf[q] = make_float2(e.hi, e.lo);
+  }
   __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   double ts = 0.0, tt = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     double ti = v.t[i];
-    for (int q = 0; q < kc; ++q) ti = fma(-__ldg(&C[(int64_t)q * ld + i]), se[q], ti);
-    if (kc) v.t[i] = ti;
+    if (kc) {
+      float sh = 0.f, sl = 0.f;  // C eta2 in double-float
+      for (int q = 0; q < kc; ++q) {
+        const float2 c = __ldg(&C[(int64_t)q * ld + i]);
+        df_mac(sh, sl, c.x, c.y, sedf[q].x, sedf[q].y);
+      }
+      ti = (ti - (double)sh) - (double)sl;
+      v.t[i] = ti;
+    }
     ts = fma(ti, v.s[i], ts);
     tt = fma(ti, ti, tt);
   }
@@ -236,7 +259,7 @@ cudaError_t launch_bicg_alpha(BicgScalars* s, const double* dots, int kc, cudaSt
   k_bicg_alpha<<<1, 32, 0, st>>>(s, dots, kc);
   return cudaGetLastError();
 }
-cudaError_t launch_bicg_s(const BicgVecs& v, BicgScalars* s, int64_t n, int kc, const double* C, int64_t ld,
+cudaError_t launch_bicg_s(const BicgVecs& v, BicgScalars* s, int64_t n, int kc, const float2* C, int64_t ld,
                           const double* eta1, double* xi, double* part, unsigned* counter, cudaStream_t st) {
   k_bicg_s<<<red_blocks(n), kRedThreads, 0, st>>>(v, s, n, kc, C, ld, eta1, xi, part, counter);
   return cudaGetLastError();
@@ -245,7 +268,7 @@ cudaError_t launch_bicg_half(const BicgVecs& v, BicgScalars* s, int64_t n, cudaS
   k_bicg_half<<<red_blocks(n), kRedThreads, 0, st>>>(v, s, n);
   return cudaGetLastError();
 }
-cudaError_t launch_bicg_t(const BicgVecs& v, BicgScalars* s, int64_t n, int kc, const double* C, int64_t ld,
+cudaError_t launch_bicg_t(const BicgVecs& v, BicgScalars* s, int64_t n, int kc, const float2* C, int64_t ld,
                           const double* eta2, double* part, unsigned* counter, cudaStream_t st) {
   k_bicg_t<<<red_blocks(n), kRedThreads, 0, st>>>(v, s, n, kc, C, ld, eta2, part, counter);
   return cudaGetLastError();

@@ -1,0 +1,103 @@
+// Double-float ("DF") arithmetic for the projection and orthogonalisation
+// kernels: a value is an unevaluated sum hi + lo of two FP32 numbers with
+// |lo| <= ulp(hi)/2 (about 48 significant bits), and products and sums are
+// carried with error-free transformations on the FP32 pipe:
+//   TwoProduct(a, b): p = a*b, e = fma(a, b, -p)     (exact: a*b = p + e)
+//   TwoSum(a, b):     s = a+b, the rounding error of s recovered with 4 adds
+//   FastTwoSum(a, b): the same when |a| >= |b| (2 adds)
+// (Dekker 1971; Knuth TAOCP vol. 2; Hida, Li, Bailey 2001 "double-double").
+// GB300 runs FP32 FMAs ~58x faster than FP64 FMAs, so one DF multiply-add
+// (~15 FP32 operations) costs about a quarter of an FP64 one and the
+// streaming kernels become memory-bound instead of FP64-bound.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace rk {
+
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df df_from_double(double d) {
+  const float h = __double2float_rn(d);
+  const float l = __double2float_rn(d - (double)h);
+  return {h, l};
+}
+
+__device__ __forceinline__ double df_to_double(float2 v) { return (double)v.x + (double)v.y; }
+__device__ __forceinline__ double df_to_double(df v) { return (double)v.hi + (double)v.lo; }
+
+__device__ __forceinline__ float2 df_pack(df v) { return make_float2(v.hi, v.lo); }
+
+// Fast2Sum with |a| >= |b| assumed
+__device__ __forceinline__ df df_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float e = __fsub_rn(b, __fsub_rn(s, a));
+  return {s, e};
+}
+
+// Accumulator (sh, sl) += (p + e) where p + e is an (unnormalised) pair;
+// TwoSum on the leading parts, then renormalise.
+__device__ __forceinline__ void df_acc(float& sh, float& sl, float p, float e) {
+  const float s = __fadd_rn(sh, p);
+  const float bb = __fsub_rn(s, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  const float t = __fadd_rn(sl, __fadd_rn(err, e));
+  const float s2 = __fadd_rn(s, t);
+  sl = __fsub_rn(t, __fsub_rn(s2, s));
+  sh = s2;
+}
+
+// Product of two DF numbers as an unnormalised pair (p, e): the low x low
+// term (relative size 2^-48) is dropped.
+__device__ __forceinline__ void df_mul_pair(float ah, float al, float bh, float bl, float& p, float& e) {
+  p = __fmul_rn(ah, bh);
+  float t = __fmaf_rn(ah, bh, -p);
+  t = __fmaf_rn(ah, bl, t);
+  e = __fmaf_rn(al, bh, t);
+}
+
+// s += a * b for DF a, b
+__device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al, float bh, float bl) {
+  float p, e;
+  df_mul_pair(ah, al, bh, bl, p, e);
+  df_acc(sh, sl, p, e);
+}
+
+// On GB300 every FP64<->FP32 conversion issues at the FP64 rate (about 2 per
+// clock per SM, like a DFMA), so the kernels below convert O(1) times per
+// element at most and keep their inner loops in FP32 operations.
+
+// a + b for DF a, b, normalised
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float bb = __fsub_rn(s, a.x);
+  float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+  e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+  const float h = __fadd_rn(s, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+// a * b for DF a, b, normalised
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  float p, e;
+  df_mul_pair(a.x, a.y, b.x, b.y, p, e);
+  const float h = __fadd_rn(p, e);
+  return make_float2(h, __fsub_rn(e, __fsub_rn(h, p)));
+}
+
+// Warp sum of DF values (xor tree; every lane gets the result)
+__device__ __forceinline__ float2 df_warp_sum(float2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    float2 w;
+    w.x = __shfl_xor_sync(0xffffffffu, v.x, o);
+    w.y = __shfl_xor_sync(0xffffffffu, v.y, o);
+    v = df_add(v, w);
+  }
+  return v;
+}
+
+}  // namespace rk

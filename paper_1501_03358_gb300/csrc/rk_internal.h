@@ -36,6 +36,11 @@ enum StencilMode { ST_PREC = 0, ST_PLAIN = 1, ST_RESID = 2 };
 cudaError_t launch_stencil(const Dims& d, int S, int mode, const double* coef, const double* dinv,
                            const double* v, const double* b, double* y, double* part,
                            unsigned* counter, double* nrm2, const int* skip_flag, cudaStream_t st);
+// The same products with a double-float input and/or output vector (the
+// arithmetic stays FP64 in the same order; v = hi + lo on load, the result
+// split into hi + lo on store).
+cudaError_t launch_stencil_df(const Dims& d, int S, int mode, const double* coef, const double* dinv,
+                              const void* v, bool v_df, void* y, bool y_df, const int* skip_flag, cudaStream_t st);
 int stencil_blocks(const Dims& d);
 
 // ---- blas.cu
@@ -57,63 +62,76 @@ struct DotsArgs {
 };
 cudaError_t launch_dots(const DotsArgs& a, cudaStream_t st);
 
-// y[i] -= sum_q Q[q*ld + i] * c[q]; optional: y2 = second output (if non-null
-// y is read from yin and written to y); nrm2 = ||y||^2 (deterministic).
-struct UpdateArgs {
-  int64_t n;
-  int nq;
-  const double* Q;
-  int64_t ld;
-  const double* c;    // device, nq
-  const double* yin;  // nullable (then yin = y)
-  double* y;
-  double* part;
-  unsigned* counter;
-  double* nrm2;       // nullable
-  const int* skip_flag;
-};
-cudaError_t launch_update(const UpdateArgs& a, cudaStream_t st);
-
-// Row-tiled small GEMM, in place safe:
-// out[c*ldo + i] = (accum ? out[c*ldo+i] : 0) + sum_q X_q[i] * P[q + c*np]
-// where the input columns X are na columns of A (ld lda) followed by nb columns
-// of Bm (ld ldb), the latter multiplied elementwise by bscale (nullable).
-// nc output columns. P is device, np x nc column-major with np = na + nb.
-struct GemmRowsArgs {
-  int64_t n;
-  int na, nb, nc;
-  const double* A; int64_t lda;
-  const double* Bm; int64_t ldb;
-  const double* bscale;
-  const double* P;      // device
-  const int* dyn_nb;    // nullable: device int overriding nb (<= nb)
-  const int* dyn_nc;    // nullable: device int overriding nc (<= nc)
-  double* out; int64_t ldo;
-  int accum;
-  const int* skip_flag;
-};
-cudaError_t launch_gemm_rows(const GemmRowsArgs& a, cudaStream_t st);
-
-// Gram block: out[q + l*nq] = sum_i Q_q[i] * d[i] * U_l[i], q < nq (Q = na
-// columns of A then nb of Bm), l < nu. Deterministic.
-struct GramArgs {
-  int64_t n;
-  int na, nb, nu;
-  const double* A; int64_t lda;
-  const double* Bm; int64_t ldb;
-  const double* d;
-  const double* U; int64_t ldu;
-  double* part;
-  unsigned* counter;
-  double* out;
-  const int* dyn_nb;
-};
-cudaError_t launch_gram(const GramArgs& a, cudaStream_t st);
+// Blocks of the double-float Gram kernel for n rows (a function of n alone).
 int gram_blocks(int64_t n);
 
 // Elementwise helpers for the BiCGStab recurrences (see solver.cu).
 cudaError_t launch_copy(int64_t n, const double* src, double* dst, cudaStream_t st);
 cudaError_t launch_fill(int64_t n, double val, double* dst, cudaStream_t st);
+
+// ---- dfblas.cu: the same roles over double-float (float2) columns.
+struct DFDotsArgs {
+  int64_t n;
+  int nq;
+  const float2* Q;     // nq DF columns, leading dimension ld
+  int64_t ld;
+  const double* extra[3];  // FP64 vectors dotted with w in FP64
+  int ne;
+  int self;            // append w^T w (DF)
+  const void* w;       // double* or float2*
+  double* part;        // red_blocks(n) * (nq + self + ne)
+  unsigned* counter;
+  double* out;         // [Q^T w (nq), w^T w (self), e^T w (ne)]
+  const int* skip_flag;
+};
+cudaError_t launch_dfdots(const DFDotsArgs& a, bool w_is_df, cudaStream_t st);
+
+struct DFUpdateArgs {
+  int64_t n;
+  int nq;
+  const float2* Q;
+  int64_t ld;
+  const double* c;          // device, nq
+  const void* yin;          // double* or float2*
+  void* yout;               // double* or float2* (may alias yin)
+  const double* scale_ptr;  // nullable
+  int scale_rsqrt;          // scale = 1/sqrt(*scale_ptr)
+  double* part;
+  unsigned* counter;
+  double* nrm2;             // nullable: ||y_out||^2
+  const int* skip_flag;
+};
+cudaError_t launch_dfupdate(const DFUpdateArgs& a, bool in_df, bool out_df, cudaStream_t st);
+
+struct DFGemmArgs {
+  int64_t n;
+  int na, nb, nc;
+  const float2* A; int64_t lda;
+  const float2* Bm; int64_t ldb;
+  const double* bscale;  // nullable, multiplies the Bm columns
+  const double* P;       // device, np x nc
+  void* out; int64_t ldo;  // float2* (DF) or double*
+  int accum;             // FP64 output only
+};
+cudaError_t launch_dfgemm_rows(const DFGemmArgs& a, bool out_df, cudaStream_t st);
+
+struct DFGramArgs {
+  int64_t n;
+  int na, nb, nu;
+  const float2* A; int64_t lda;
+  const float2* Bm; int64_t ldb;
+  const double* d;       // nullable
+  const float2* U; int64_t ldu;
+  double* part;
+  unsigned* counter;
+  double* out;
+};
+cudaError_t launch_dfgram(const DFGramArgs& a, cudaStream_t st);
+cudaError_t launch_to_df(int64_t n, const double* src, float2* dst, const double* scale_ptr, int scale_rsqrt,
+                         int ncols, int64_t lds, int64_t ldd, cudaStream_t st);
+cudaError_t launch_from_df(int64_t n, const float2* src, double* dst, int ncols, int64_t lds, int64_t ldd,
+                           cudaStream_t st);
+cudaError_t launch_axpy_scaled(int64_t n, const double* s, const double* v, double* x, cudaStream_t st);
 
 // Thread-local message returned by rk_last_error (solver.cu).
 void set_last_error(const char* msg);

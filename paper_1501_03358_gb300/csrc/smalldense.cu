@@ -43,10 +43,14 @@ __global__ void k_arn_coef(SolveState* s, SmallBuffers b, int kc, int j, int pas
 __global__ void k_arn_finalize(SolveState* s, SmallBuffers b, int kc, int j) {
   if (s->done || threadIdx.x != 0) return;
   const int ldh = b.m + 1;
-  const double nrm2 = s->nrm2[1];
+  // the second pass stored q_{j+1} = y2 * s2 with s2 = 1/||y1|| (1 if y1 = 0);
+  // nrm2[1] = ||q_{j+1}||^2, nrm2[2] = ||y1||^2
+  const double n1 = s->nrm2[2];
+  const double s2 = n1 > 0.0 ? rsqrt(n1) : 1.0;
+  const double nq2 = s->nrm2[1];
+  const double qn = sqrt(nq2);
   const double svj = b.sv[j];
-  const double nrm = sqrt(nrm2);
-  const double hnext = svj * nrm;
+  const double hnext = svj * (qn / s2);
   for (int l = 0; l < kc; ++l) b.B[l + (int64_t)j * b.kmax] = svj * b.hacc[l];
   for (int l = 0; l <= j; ++l) b.H[l + j * ldh] = svj * b.hacc[kc + l] / b.sv[l];
   b.H[j + 1 + j * ldh] = hnext;
@@ -74,8 +78,8 @@ __global__ void k_arn_finalize(SolveState* s, SmallBuffers b, int kc, int j) {
   const double est = fabs(b.g[j + 1]);
   s->est = est;
   s->jj = j + 1;
-  const bool happy = !(nrm2 > 0.0);
-  b.sv[j + 1] = happy ? 0.0 : 1.0 / nrm;
+  const bool happy = !(nq2 > 0.0);
+  b.sv[j + 1] = happy ? 0.0 : 1.0 / qn;
   if (est <= s->tolabs || happy) s->done = 1;
 }
 
@@ -780,13 +784,13 @@ __global__ void k_chol_rinv(int k, const double* G, double* Rinv, double* Rw, in
   *status = 0;
 }
 
-// Start of an Arnoldi cycle: g = rho e_1, v_1 = r / rho (column 0 stores r,
-// so its scale is 1/rho), no steps taken.
+// Start of an Arnoldi cycle: g = rho e_1, v_1 = r / rho (stored normalised in
+// column 0), no steps taken.
 __global__ void k_cycle_init(SolveState* s, SmallBuffers b) {
   const double rho = sqrt(s->rho2);
   for (int i = threadIdx.x; i <= b.m; i += blockDim.x) b.g[i] = i == 0 ? rho : 0.0;
   if (threadIdx.x == 0) {
-    b.sv[0] = rho > 0.0 ? 1.0 / rho : 0.0;
+    b.sv[0] = 1.0;  // column 0 holds r / rho
     s->done = rho > 0.0 ? 0 : 1;
     s->jj = 0;
   }

@@ -177,8 +177,9 @@ struct rk_problem {
   double* dinv = nullptr;
   double anorm_f = 0.0;  // ||A||_F
   int kmax = 0, mcap = 0, kdim = 0;
-  double* QB = nullptr;
-  double* Ub = nullptr;
+  float2* QB = nullptr;           // double-float basis [C | V]
+  float2* Ub = nullptr;           // double-float U
+  double* rvec = nullptr;         // FP64 residual of the rGCROT cycle
   double* bicg = nullptr;
   // small
   double* small = nullptr;
@@ -187,16 +188,16 @@ struct rk_problem {
   SolveState* st_h = nullptr;     // pinned host mirror
   BicgScalars* bs = nullptr;      // device
   BicgScalars* bs_h = nullptr;    // pinned host mirror
-  double* eta = nullptr;          // 3 x (kmax + 4): eta1, eta2, xi
+  double* eta = nullptr;          // eta1, eta2, xi, fold coefficients, k x k scratch
   double* part = nullptr;
   size_t part_n = 0;
   unsigned* counter = nullptr;
   int* istat = nullptr;           // device ints for small kernels
   int solves = 0;
 
-  double* Vcol(int j) const { return QB + (int64_t)(kmax + j) * ld; }
-  double* Cblk(int kc) const { return QB + (int64_t)(kmax - kc) * ld; }
-  double* Ublk(int kc) const { return Ub + (int64_t)(kmax - kc) * ld; }
+  float2* Vcol(int j) const { return QB + (int64_t)(kmax + j) * ld; }
+  float2* Cblk(int kc) const { return QB + (int64_t)(kmax - kc) * ld; }
+  float2* Ublk(int kc) const { return Ub + (int64_t)(kmax - kc) * ld; }
 };
 
 namespace {
@@ -227,8 +228,8 @@ int ensure_capacity(rk_problem* p, int kneed, int mneed, cudaStream_t st) {
   const int mcap = std::max(mneed, p->mcap);
   if (kmax > 256) return fail(RK_E_INVALID, "recycle dimension above 256 is not supported");
   if (kmax + mcap + 1 > 512) return fail(RK_E_INVALID, "k + m above 511 is not supported");
-  double* QB = nullptr;
-  double* Ub = nullptr;
+  float2* QB = nullptr;
+  float2* Ub = nullptr;
   RK_TRY(alloc_into(p->ctx, &QB, (size_t)(kmax + mcap + 1) * p->ld));
   if (kmax > 0) {
     int r = alloc_into(p->ctx, &Ub, (size_t)kmax * p->ld);
@@ -239,9 +240,9 @@ int ensure_capacity(rk_problem* p, int kneed, int mneed, cudaStream_t st) {
   }
   if (p->kdim > 0) {
     RK_CUDA(cudaMemcpyAsync(QB + (int64_t)(kmax - p->kdim) * p->ld, p->Cblk(p->kdim),
-                            sizeof(double) * p->ld * p->kdim, cudaMemcpyDeviceToDevice, st));
+                            sizeof(float2) * p->ld * p->kdim, cudaMemcpyDeviceToDevice, st));
     RK_CUDA(cudaMemcpyAsync(Ub + (int64_t)(kmax - p->kdim) * p->ld, p->Ublk(p->kdim),
-                            sizeof(double) * p->ld * p->kdim, cudaMemcpyDeviceToDevice, st));
+                            sizeof(float2) * p->ld * p->kdim, cudaMemcpyDeviceToDevice, st));
     RK_CUDA(cudaStreamSynchronize(st));
   }
   dev_free(p->ctx, p->QB);
@@ -250,6 +251,7 @@ int ensure_capacity(rk_problem* p, int kneed, int mneed, cudaStream_t st) {
   p->Ub = Ub;
   p->kmax = kmax;
   p->mcap = mcap;
+  if (!p->rvec) RK_TRY(alloc_into(p->ctx, &p->rvec, (size_t)p->ld));
   // small buffers
   free_small(p);
   const int m = mcap, nq = kmax + mcap + 2;
@@ -288,7 +290,7 @@ int ensure_capacity(rk_problem* p, int kneed, int mneed, cudaStream_t st) {
   b.PU = p->small + oPU;
   b.hrws = p->small + ows;
   RK_CUDA(cudaMemsetAsync(p->small, 0, total * sizeof(double), st));
-  RK_TRY(alloc_into(p->ctx, &p->eta, (size_t)3 * (kmax + 4) + (size_t)kmax * kmax * 2 + 16));
+  RK_TRY(alloc_into(p->ctx, &p->eta, (size_t)4 * (kmax + 4) + (size_t)kmax * kmax * 2 + 16));
   p->part_n = partials_needed(p, kmax, mcap);
   RK_TRY(alloc_into(p->ctx, &p->part, p->part_n));
   return RK_OK;
@@ -301,7 +303,7 @@ int sync_state(rk_problem* p, cudaStream_t st) {
   return RK_OK;
 }
 
-// sum of squares of a device vector into st->nrm2[slot]
+// sum of squares of an FP64 device vector into st->nrm2[slot]
 int norm2_into(rk_problem* p, const double* v, int slot, cudaStream_t st) {
   DotsArgs a{};
   a.n = p->n;
@@ -319,9 +321,10 @@ int norm2_into(rk_problem* p, const double* v, int slot, cudaStream_t st) {
   return RK_OK;
 }
 
-int dots_launch(rk_problem* p, const double* Q, int nq, const double* w, double* out, const int* skip,
-                cudaStream_t st, const double* extra0 = nullptr, int self = 0) {
-  DotsArgs a{};
+// out = [Q^T w (nq DF columns), w^T w (self), e^T w (extra, FP64)]
+int dfdots_launch(rk_problem* p, const float2* Q, int nq, const void* w, bool w_df, double* out, const int* skip,
+                  cudaStream_t st, const double* extra0 = nullptr, int self = 0) {
+  DFDotsArgs a{};
   a.n = p->n;
   a.nq = nq;
   a.Q = Q;
@@ -334,33 +337,38 @@ int dots_launch(rk_problem* p, const double* Q, int nq, const double* w, double*
   a.counter = p->counter;
   a.out = out;
   a.skip_flag = skip;
-  ProfScope ps(&p->prof, PC_DOTS, 8.0 * (nq + (extra0 ? 1 : 0) + 1) * (double)p->n, st);
-  RK_CUDA(launch_dots(a, st));
+  ProfScope ps(&p->prof, PC_DOTS, 8.0 * (nq + (extra0 ? 2 : 0) + 1) * (double)p->n, st);
+  RK_CUDA(launch_dfdots(a, w_df, st));
   return RK_OK;
 }
 
-int update_launch(rk_problem* p, const double* Q, int nq, const double* c, double* y, double* nrm2, const int* skip,
-                  cudaStream_t st) {
-  UpdateArgs a{};
+// yout = (yin - Q c) * scale, ||yout||^2 -> nrm2
+int dfupdate_launch(rk_problem* p, const float2* Q, int nq, const double* c, const void* yin, bool in_df, void* yout,
+                    bool out_df, double* nrm2, const int* skip, cudaStream_t st, const double* scale_ptr = nullptr,
+                    int scale_rsqrt = 0) {
+  DFUpdateArgs a{};
   a.n = p->n;
   a.nq = nq;
   a.Q = Q;
   a.ld = p->ld;
   a.c = c;
-  a.y = y;
+  a.yin = yin;
+  a.yout = yout;
+  a.scale_ptr = scale_ptr;
+  a.scale_rsqrt = scale_rsqrt;
   a.part = p->part;
   a.counter = p->counter;
   a.nrm2 = nrm2;
   a.skip_flag = skip;
   ProfScope ps(&p->prof, PC_UPDATE, 8.0 * (nq + 2) * (double)p->n, st);
-  RK_CUDA(launch_update(a, st));
+  RK_CUDA(launch_dfupdate(a, in_df, out_df, st));
   return RK_OK;
 }
 
-// out (+)= [A cols | dinv .* B cols] P
-int gemm_launch(rk_problem* p, const double* A, int na, const double* Bm, int nb, const double* bscale,
-                const double* P, int nc, double* out, int accum, cudaStream_t st) {
-  GemmRowsArgs a{};
+// out (+)= [A cols | bscale .* B cols] P  (A, B double-float; out DF or FP64)
+int dfgemm_launch(rk_problem* p, const float2* A, int na, const float2* Bm, int nb, const double* bscale,
+                  const double* P, int nc, void* out, bool out_df, int accum, cudaStream_t st) {
+  DFGemmArgs a{};
   a.n = p->n;
   a.na = na;
   a.nb = nb;
@@ -375,7 +383,7 @@ int gemm_launch(rk_problem* p, const double* A, int na, const double* Bm, int nb
   a.ldo = p->ld;
   a.accum = accum;
   ProfScope ps(&p->prof, PC_GEMM, 8.0 * (na + nb + nc * (accum ? 2 : 1) + (bscale ? 1 : 0)) * (double)p->n, st);
-  RK_CUDA(launch_gemm_rows(a, st));
+  RK_CUDA(launch_dfgemm_rows(a, out_df, st));
   return RK_OK;
 }
 
@@ -389,14 +397,22 @@ int stencil_launch(rk_problem* p, int mode, const double* v, const double* b, do
   return RK_OK;
 }
 
+int stencil_df_launch(rk_problem* p, int mode, const void* v, bool v_df, void* y, bool y_df, const int* skip,
+                      cudaStream_t st) {
+  ProfScope ps(&p->prof, PC_SPMV, 8.0 * (p->S + 2) * (double)p->n, st);
+  RK_CUDA(launch_stencil_df(p->d, p->S, mode, p->coef, mode == ST_PREC ? p->dinv : nullptr, v, v_df, y, y_df, skip,
+                            st));
+  return RK_OK;
+}
+
 // Line 1b at the start of a cycle: xi = C^T r, r <- r - C xi, x <- x + U xi;
-// ||r||^2 -> st->rho2.
+// ||r||^2 -> st->rho2 (r and x FP64).
 int project_residual(rk_problem* p, int kc, double* r, double* x, cudaStream_t st) {
   if (kc == 0) return RK_OK;  // ||r||^2 already in st->rho2
-  double* xi = p->eta;  // kc
-  RK_TRY(dots_launch(p, p->Cblk(kc), kc, r, xi, nullptr, st));
-  RK_TRY(update_launch(p, p->Cblk(kc), kc, xi, r, &p->st->rho2, nullptr, st));
-  RK_TRY(gemm_launch(p, p->Ublk(kc), kc, nullptr, 0, nullptr, xi, 1, x, 1, st));
+  double* xi = p->eta;        // kc
+  RK_TRY(dfdots_launch(p, p->Cblk(kc), kc, r, false, xi, nullptr, st));
+  RK_TRY(dfupdate_launch(p, p->Cblk(kc), kc, xi, r, false, r, false, &p->st->rho2, nullptr, st));
+  RK_TRY(dfgemm_launch(p, p->Ublk(kc), kc, nullptr, 0, nullptr, xi, 1, x, false, 1, st));
   return RK_OK;
 }
 
@@ -432,10 +448,9 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
     return RK_OK;
   }
   const double tolabs = prm.tol * bnorm;
-  // line 1: r = b - A x into column 0 of V; line 1b
-  double* r = p->Vcol(0);
-  RK_TRY(stencil_launch(p, ST_RESID, x, b, r, p->part, p->counter,
-                         &p->st->rho2, nullptr, st));
+  // line 1: r = b - A x (FP64); line 1b
+  double* r = p->rvec;
+  RK_TRY(stencil_launch(p, ST_RESID, x, b, r, p->part, p->counter, &p->st->rho2, nullptr, st));
   RK_TRY(project_residual(p, kc, r, x, st));
   words += (S + 3) + (kc ? 2.0 * kc + 3 : 0) + 1;
   RK_TRY(sync_state(p, st));
@@ -445,16 +460,22 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
   const int* done = &p->st->done;
   while (rho > tolabs && matvecs < maxmv) {
     const int steps = std::min(m, maxmv - matvecs);
+    // v_1 = r / rho, stored double-float (line 4)
+    RK_CUDA(launch_to_df(p->n, r, p->Vcol(0), &p->st->rho2, 1, 1, p->ld, p->ld, st));
     { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_cycle_init(p->st, p->sb, st)); }
     for (int j = 0; j < steps; ++j) {
-      RK_TRY(stencil_launch(p, ST_PREC, p->Vcol(j), nullptr, p->Vcol(j + 1), nullptr,
-                             nullptr, nullptr, done, st));
+      // line 6: w = A M^{-1} v_j into the slot of v_{j+1}
+      RK_TRY(stencil_df_launch(p, ST_PREC, p->Vcol(j), true, p->Vcol(j + 1), true, done, st));
+      // lines 6a-10 as two block classical Gram-Schmidt passes over [C V_j]
       const int nq = kc + j + 1;
-      for (int pass = 0; pass < 2; ++pass) {
-        RK_TRY(dots_launch(p, p->Cblk(kc), nq, p->Vcol(j + 1), p->sb.dots, done, st));
-        { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_arn_coef(p->st, p->sb, kc, j, pass, st)); }
-        RK_TRY(update_launch(p, p->Cblk(kc), nq, p->sb.coef, p->Vcol(j + 1), &p->st->nrm2[1], done, st));
-      }
+      RK_TRY(dfdots_launch(p, p->Cblk(kc), nq, p->Vcol(j + 1), true, p->sb.dots, done, st));
+      { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_arn_coef(p->st, p->sb, kc, j, 0, st)); }
+      RK_TRY(dfupdate_launch(p, p->Cblk(kc), nq, p->sb.coef, p->Vcol(j + 1), true, p->Vcol(j + 1), true,
+                             &p->st->nrm2[2], done, st));
+      RK_TRY(dfdots_launch(p, p->Cblk(kc), nq, p->Vcol(j + 1), true, p->sb.dots, done, st));
+      { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_arn_coef(p->st, p->sb, kc, j, 1, st)); }
+      RK_TRY(dfupdate_launch(p, p->Cblk(kc), nq, p->sb.coef, p->Vcol(j + 1), true, p->Vcol(j + 1), true,
+                             &p->st->nrm2[1], done, st, &p->st->nrm2[2], 1));
       { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_arn_finalize(p->st, p->sb, kc, j, st)); }
     }
     RK_TRY(sync_state(p, st));
@@ -465,12 +486,12 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
     cycles += 1;
     // lines 12-13a: y, z = -B y, x <- x + M^{-1} V_j y + U z
     { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_cycle_solve(p->st, p->sb, kc, st)); }
-    RK_TRY(gemm_launch(p, p->Ublk(kc), kc, p->Vcol(0), jj, p->dinv, p->sb.xcoef, 1, x, 1, st));
+    RK_TRY(dfgemm_launch(p, p->Ublk(kc), kc, p->Vcol(0), jj, p->dinv, p->sb.xcoef, 1, x, false, 1, st));
     words += model_words_cycle(p->S, kc, jj, m);
-    // line 14a: recycle update (harmonic Ritz), before column 0 is reused
+    // line 14a: recycle update (harmonic Ritz)
     if (update && k > 0) {
       if (kc > 0) {
-        GramArgs g{};
+        DFGramArgs g{};
         g.n = p->n;
         g.na = kc;
         g.nb = jj + 1;
@@ -485,23 +506,23 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
         g.part = p->part;
         g.counter = p->counter;
         g.out = p->sb.gram;
-        { ProfScope ps_(&p->prof, PC_GRAM, 8.0 * (g.na + g.nb + g.nu + 1) * (double)p->n, st); RK_CUDA(launch_gram(g, st)); }
+        { ProfScope ps_(&p->prof, PC_GRAM, 8.0 * (g.na + g.nb + g.nu + 1) * (double)p->n, st); RK_CUDA(launch_dfgram(g, st)); }
       }
       { ProfScope ps_(&p->prof, PC_HRITZ, 0.0, st); RK_CUDA(launch_harmonic_ritz(p->st, p->sb, kc, jj, k, st)); }
       RK_TRY(sync_state(p, st));
       const int knew = p->st_h->knew;
       if (p->st_h->hr_status == 0 && knew > 0) {
         // C <- [C V_{j+1}] QC, U <- [U, M^{-1} V_j] PU, both in place (row tiles)
-        RK_TRY(gemm_launch(p, p->Cblk(kc), kc, p->Vcol(0), jj + 1, nullptr, p->sb.QC, knew, p->Cblk(knew), 0, st));
-        RK_TRY(gemm_launch(p, p->Ublk(kc), kc, p->Vcol(0), jj, p->dinv, p->sb.PU, knew, p->Ublk(knew), 0, st));
+        RK_TRY(dfgemm_launch(p, p->Cblk(kc), kc, p->Vcol(0), jj + 1, nullptr, p->sb.QC, knew, p->Cblk(knew), true, 0,
+                             st));
+        RK_TRY(dfgemm_launch(p, p->Ublk(kc), kc, p->Vcol(0), jj, p->dinv, p->sb.PU, knew, p->Ublk(knew), true, 0, st));
         kc = knew;
         p->kdim = knew;
         words += 6.0 * kc + 3.0 * jj + 4;
       }
     }
-    // line 14: r = b - A x (true residual) into column 0; next cycle's line 1b
-    RK_TRY(stencil_launch(p, ST_RESID, x, b, r, p->part, p->counter,
-                           &p->st->rho2, nullptr, st));
+    // line 14: r = b - A x (true residual); next cycle's line 1b
+    RK_TRY(stencil_launch(p, ST_RESID, x, b, r, p->part, p->counter, &p->st->rho2, nullptr, st));
     RK_TRY(project_residual(p, kc, r, x, st));
     RK_TRY(sync_state(p, st));
     rho = std::sqrt(p->st_h->rho2);
@@ -534,6 +555,7 @@ int solve_bicg(rk_problem* p, const double* b, double* x, const rk_solve_params&
   double* eta1 = p->eta;
   double* eta2 = p->eta + (p->kmax + 4);
   double* xi = p->eta + 2 * (p->kmax + 4);
+  double* coefv = p->eta + 3 * (p->kmax + 4);
   RK_TRY(norm2_into(p, b, 0, st));
   { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_set_tol(p->st, prm.tol, st)); }
   RK_TRY(sync_state(p, st));
@@ -555,13 +577,12 @@ int solve_bicg(rk_problem* p, const double* b, double* x, const rk_solve_params&
   const int NB = 8;
   while (true) {
     // line 1: r = b - A x; line 1c: eta1 = C^T r, r -= C eta1, xi = -eta1
-    RK_TRY(stencil_launch(p, ST_RESID, x, b, v.r, p->part, p->counter,
-                           &p->st->rho2, nullptr, st));
+    RK_TRY(stencil_launch(p, ST_RESID, x, b, v.r, p->part, p->counter, &p->st->rho2, nullptr, st));
     if (kc) {
-      RK_TRY(dots_launch(p, p->Cblk(kc), kc, v.r, xi, nullptr, st));
-      RK_TRY(update_launch(p, p->Cblk(kc), kc, xi, v.r, &p->st->rho2, nullptr, st));
-      // xi = -eta1 (applied as x <- x - U xi at the end)
-      RK_TRY(gemm_launch(p, p->Ublk(kc), kc, nullptr, 0, nullptr, xi, 1, x, 1, st));
+      RK_TRY(dfdots_launch(p, p->Cblk(kc), kc, v.r, false, xi, nullptr, st));
+      RK_TRY(dfupdate_launch(p, p->Cblk(kc), kc, xi, v.r, false, v.r, false, &p->st->rho2, nullptr, st));
+      // xi = -eta1 enters x at once (x <- x + U eta1); xi restarts from 0
+      RK_TRY(dfgemm_launch(p, p->Ublk(kc), kc, nullptr, 0, nullptr, xi, 1, x, false, 1, st));
       RK_CUDA(cudaMemsetAsync(xi, 0, sizeof(double) * kc, st));
     }
     { ProfScope ps_(&p->prof, PC_BICG, 24.0 * p->n, st); RK_CUDA(launch_copy(p->n, v.r, v.rt, st)); RK_CUDA(launch_fill(p->n, 0.0, v.xt, st)); }
@@ -571,14 +592,12 @@ int solve_bicg(rk_problem* p, const double* b, double* x, const rk_solve_params&
     while (running) {
       for (int it = 0; it < NB; ++it) {
         { ProfScope ps_(&p->prof, PC_BICG, 32.0 * p->n, st); RK_CUDA(launch_bicg_p(v, p->bs, p->n, st)); }
-        RK_TRY(stencil_launch(p, ST_PREC, v.p, nullptr, v.v, nullptr, nullptr, nullptr,
-                               &p->bs->stop, st));
-        RK_TRY(dots_launch(p, p->Cblk(kc), kc, v.v, eta1, &p->bs->stop, st, v.rt));
+        RK_TRY(stencil_launch(p, ST_PREC, v.p, nullptr, v.v, nullptr, nullptr, nullptr, &p->bs->stop, st));
+        RK_TRY(dfdots_launch(p, p->Cblk(kc), kc, v.v, false, eta1, &p->bs->stop, st, v.rt));
         { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_bicg_alpha(p->bs, eta1, kc, st)); }
         { ProfScope ps_(&p->prof, PC_BICG, 8.0 * (kc + (kc ? 5 : 3)) * (double)p->n, st); RK_CUDA(launch_bicg_s(v, p->bs, p->n, kc, p->Cblk(kc), p->ld, eta1, xi, p->part, p->counter, st)); }
-        RK_TRY(stencil_launch(p, ST_PREC, v.s, nullptr, v.t, nullptr, nullptr, nullptr,
-                               &p->bs->stop, st));
-        if (kc) RK_TRY(dots_launch(p, p->Cblk(kc), kc, v.t, eta2, &p->bs->stop, st));
+        RK_TRY(stencil_launch(p, ST_PREC, v.s, nullptr, v.t, nullptr, nullptr, nullptr, &p->bs->stop, st));
+        if (kc) RK_TRY(dfdots_launch(p, p->Cblk(kc), kc, v.t, false, eta2, &p->bs->stop, st));
         { ProfScope ps_(&p->prof, PC_BICG, 8.0 * (kc + (kc ? 3 : 2)) * (double)p->n, st); RK_CUDA(launch_bicg_t(v, p->bs, p->n, kc, p->Cblk(kc), p->ld, eta2, p->part, p->counter, st)); }
         { ProfScope ps_(&p->prof, PC_BICG, 56.0 * p->n, st); RK_CUDA(launch_bicg_r(v, p->bs, p->n, kc, eta1, eta2, xi, p->part, p->counter, st)); }
       }
@@ -593,16 +612,17 @@ int solve_bicg(rk_problem* p, const double* b, double* x, const rk_solve_params&
     upd = p->bs_h->upd;
     words += (double)p->bs_h->it * (2 * S + 4.0 * kc + 22);
     const int flag = p->bs_h->flag;
-    // line 17a: x <- x + M^{-1} x~ - U xi  (one row-tiled pass over U and x~)
+    // line 17a: x <- x + M^{-1} x~ - U xi
     {
-      double* coefv = p->eta + 3 * (p->kmax + 4);  // [-xi (kc); 1]
-      { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_bicg_foldcoef(xi, kc, coefv, st)); }
-      RK_TRY(gemm_launch(p, p->Ublk(kc), kc, v.xt, 1, p->dinv, coefv, 1, x, 1, st));
+      RK_CUDA(launch_axpy_scaled(p->n, p->dinv, v.xt, x, st));
+      if (kc) {
+        { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_bicg_foldcoef(xi, kc, coefv, st)); }
+        RK_TRY(dfgemm_launch(p, p->Ublk(kc), kc, nullptr, 0, nullptr, coefv, 1, x, false, 1, st));
+      }
       words += kc + 4;
     }
     // true residual (replacement, R12)
-    RK_TRY(stencil_launch(p, ST_RESID, x, b, v.r, p->part, p->counter,
-                           &p->st->rho2, nullptr, st));
+    RK_TRY(stencil_launch(p, ST_RESID, x, b, v.r, p->part, p->counter, &p->st->rho2, nullptr, st));
     RK_TRY(sync_state(p, st));
     rel = std::sqrt(p->st_h->rho2) / bnorm;
     if (rel <= prm.tol) {
@@ -831,62 +851,51 @@ int rk_set_recycle(rk_problem* p, const double* U, const double* C, int32_t k, v
   if (!U) return fail(RK_E_INVALID, "U is NULL");
   RK_TRY(ensure_capacity(p, k, std::max(p->mcap, 1), st));
   p->kdim = 0;  // replaced below; on any error the problem is left without a recycle space
-  double* Ud = p->Ublk(k);
-  double* Cd = p->Cblk(k);
-  RK_CUDA(cudaMemcpy2DAsync(Ud, sizeof(double) * p->ld, U, sizeof(double) * p->n, sizeof(double) * p->n, k,
-                            cudaMemcpyDeviceToDevice, st));
-  double* G = p->eta;                       // k x k
-  double* Rinv = p->eta + (size_t)k * k;    // k x k
-  double* Rw = p->sb.hrws;                  // k x k scratch
+  float2* Ud = p->Ublk(k);
+  float2* Cd = p->Cblk(k);
+  // the caller's FP64 N x k (leading dimension N) into the double-float store
+  RK_CUDA(launch_to_df(p->n, U, Ud, nullptr, 0, k, p->n, p->ld, st));
+  double* G = p->eta;                     // k x k
+  double* Rinv = p->eta + (size_t)k * k;  // k x k
+  double* Rw = p->sb.hrws;                // k x k scratch
+  auto gram_cc = [&](float2* X) -> int {
+    DFGramArgs g{};
+    g.n = p->n;
+    g.na = k;
+    g.nb = 0;
+    g.nu = k;
+    g.A = X;
+    g.lda = p->ld;
+    g.Bm = nullptr;
+    g.ldb = p->ld;
+    g.d = nullptr;
+    g.U = X;
+    g.ldu = p->ld;
+    g.part = p->part;
+    g.counter = p->counter;
+    g.out = G;
+    RK_CUDA(launch_dfgram(g, st));
+    return RK_OK;
+  };
   if (!C) {
     // line 1a: C~ = A U; thin QR by CholQR2 (C~ = C R), U <- U R^{-1}
     for (int c = 0; c < k; ++c)
-      RK_CUDA(launch_stencil(p->d, p->S, ST_PLAIN, p->coef, nullptr, Ud + (int64_t)c * p->ld, nullptr,
-                             Cd + (int64_t)c * p->ld, nullptr, nullptr, nullptr, nullptr, st));
+      RK_CUDA(launch_stencil_df(p->d, p->S, ST_PLAIN, p->coef, nullptr, Ud + (int64_t)c * p->ld, true,
+                                Cd + (int64_t)c * p->ld, true, nullptr, st));
     for (int pass = 0; pass < 2; ++pass) {
-      GramArgs g{};
-      g.n = p->n;
-      g.na = k;
-      g.nb = 0;
-      g.nu = k;
-      g.A = Cd;
-      g.lda = p->ld;
-      g.Bm = nullptr;
-      g.ldb = p->ld;
-      g.d = nullptr;
-      g.U = Cd;
-      g.ldu = p->ld;
-      g.part = p->part;
-      g.counter = p->counter;
-      g.out = G;
-      RK_CUDA(launch_gram(g, st));
+      RK_TRY(gram_cc(Cd));
       RK_CUDA(launch_chol_rinv(k, G, Rinv, Rw, p->istat, st));
       int hs = 0;
       RK_CUDA(cudaMemcpyAsync(&hs, p->istat, sizeof(int), cudaMemcpyDeviceToHost, st));
       RK_CUDA(cudaStreamSynchronize(st));
       if (hs != 0) return fail(RK_E_INVALID, "A U is rank deficient (Cholesky of C~^T C~ failed)");
-      RK_TRY(gemm_launch(p, Cd, k, nullptr, 0, nullptr, Rinv, k, Cd, 0, st));
-      RK_TRY(gemm_launch(p, Ud, k, nullptr, 0, nullptr, Rinv, k, Ud, 0, st));
+      RK_TRY(dfgemm_launch(p, Cd, k, nullptr, 0, nullptr, Rinv, k, Cd, true, 0, st));
+      RK_TRY(dfgemm_launch(p, Ud, k, nullptr, 0, nullptr, Rinv, k, Ud, true, 0, st));
     }
   } else {
-    RK_CUDA(cudaMemcpy2DAsync(Cd, sizeof(double) * p->ld, C, sizeof(double) * p->n, sizeof(double) * p->n, k,
-                              cudaMemcpyDeviceToDevice, st));
+    RK_CUDA(launch_to_df(p->n, C, Cd, nullptr, 0, k, p->n, p->ld, st));
     // invariants: ||C^T C - I||_F and ||A U - C||_F
-    GramArgs g{};
-    g.n = p->n;
-    g.na = k;
-    g.nb = 0;
-    g.nu = k;
-    g.A = Cd;
-    g.lda = p->ld;
-    g.ldb = p->ld;
-    g.d = nullptr;
-    g.U = Cd;
-    g.ldu = p->ld;
-    g.part = p->part;
-    g.counter = p->counter;
-    g.out = G;
-    RK_CUDA(launch_gram(g, st));
+    RK_TRY(gram_cc(Cd));
     std::vector<double> hg((size_t)k * k);
     RK_CUDA(cudaMemcpyAsync(hg.data(), G, sizeof(double) * k * k, cudaMemcpyDeviceToHost, st));
     RK_CUDA(cudaStreamSynchronize(st));
@@ -897,17 +906,18 @@ int rk_set_recycle(rk_problem* p, const double* U, const double* C, int32_t k, v
         e += t * t;
       }
     if (std::sqrt(e) > 1e-10) return fail(RK_E_RECYCLE_INVARIANT, "||C^T C - I||_F = " + std::to_string(std::sqrt(e)));
-    double* tmp = p->Vcol(0);
+    double* tmp = p->rvec;
+    double* onev = p->eta + (size_t)2 * k * k;
+    const double one = 1.0;
+    RK_CUDA(cudaMemcpyAsync(onev, &one, sizeof(double), cudaMemcpyHostToDevice, st));
     double eau = 0.0, un = 0.0;
     for (int c = 0; c < k; ++c) {
-      RK_CUDA(launch_stencil(p->d, p->S, ST_PLAIN, p->coef, nullptr, Ud + (int64_t)c * p->ld, nullptr, tmp, nullptr,
-                             nullptr, nullptr, nullptr, st));
-      // tmp <- tmp - C_c, ||tmp||^2
-      double* onev = p->eta + (size_t)2 * k * k;
-      const double one = 1.0;
-      RK_CUDA(cudaMemcpyAsync(onev, &one, sizeof(double), cudaMemcpyHostToDevice, st));
-      RK_TRY(update_launch(p, Cd + (int64_t)c * p->ld, 1, onev, tmp, &p->st->nrm2[2], nullptr, st));
-      RK_TRY(norm2_into(p, Ud + (int64_t)c * p->ld, 3, st));
+      RK_CUDA(launch_stencil_df(p->d, p->S, ST_PLAIN, p->coef, nullptr, Ud + (int64_t)c * p->ld, true, tmp, false,
+                                nullptr, st));
+      // tmp <- A u_c - c_c, ||tmp||^2 ; ||u_c||^2
+      RK_TRY(dfupdate_launch(p, Cd + (int64_t)c * p->ld, 1, onev, tmp, false, tmp, false, &p->st->nrm2[2], nullptr,
+                             st));
+      RK_TRY(dfdots_launch(p, nullptr, 0, Ud + (int64_t)c * p->ld, true, &p->st->nrm2[3], nullptr, st, nullptr, 1));
       RK_TRY(sync_state(p, st));
       eau += p->st_h->nrm2[2];
       un += p->st_h->nrm2[3];
@@ -929,12 +939,8 @@ int rk_get_recycle(const rk_problem* p, double* U, double* C, int32_t* k, void* 
   cudaStream_t st = (cudaStream_t)stream;
   const int kd = p->kdim;
   if (kd > 0) {
-    if (U)
-      RK_CUDA(cudaMemcpy2DAsync(U, sizeof(double) * p->n, p->Ublk(kd), sizeof(double) * p->ld,
-                                sizeof(double) * p->n, kd, cudaMemcpyDeviceToDevice, st));
-    if (C)
-      RK_CUDA(cudaMemcpy2DAsync(C, sizeof(double) * p->n, p->Cblk(kd), sizeof(double) * p->ld,
-                                sizeof(double) * p->n, kd, cudaMemcpyDeviceToDevice, st));
+    if (U) RK_CUDA(launch_from_df(p->n, p->Ublk(kd), U, kd, p->ld, p->n, st));
+    if (C) RK_CUDA(launch_from_df(p->n, p->Cblk(kd), C, kd, p->ld, p->n, st));
     RK_CUDA(cudaStreamSynchronize(st));
   }
   *k = kd;

@@ -12,6 +12,7 @@
 // (out-of-domain neighbours contribute fma(0, 0, w)).
 #include "rk_internal.h"
 #include "rk_device.cuh"
+#include "rk_df.cuh"
 
 namespace rk {
 
@@ -26,11 +27,28 @@ __device__ __forceinline__ int halo_coord(int c, int n, int periodic) {
   return -1;
 }
 
-template <int S, int MODE>
+template <typename VT>
+__device__ __forceinline__ double ld_val(const VT* p, int64_t q);
+template <>
+__device__ __forceinline__ double ld_val<double>(const double* p, int64_t q) { return __ldg(&p[q]); }
+template <>
+__device__ __forceinline__ double ld_val<float2>(const float2* p, int64_t q) { return df_to_double(__ldg(&p[q])); }
+
+template <typename YT>
+__device__ __forceinline__ void st_val(YT* p, int64_t q, double w);
+template <>
+__device__ __forceinline__ void st_val<double>(double* p, int64_t q, double w) { p[q] = w; }
+template <>
+__device__ __forceinline__ void st_val<float2>(float2* p, int64_t q, double w) {
+  const df v = df_from_double(w);
+  p[q] = make_float2(v.hi, v.lo);
+}
+
+template <int S, int MODE, typename VT = double, typename YT = double>
 __global__ void __launch_bounds__(kTX* kTY) k_stencil(Dims d, const double* __restrict__ coef,
                                                       const double* __restrict__ dinv,
-                                                      const double* __restrict__ v,
-                                                      const double* __restrict__ b, double* __restrict__ y,
+                                                      const VT* __restrict__ v,
+                                                      const double* __restrict__ b, YT* __restrict__ y,
                                                       double* part, unsigned* counter, double* nrm2,
                                                       const int* skip, int zchunk) {
   if (skip != nullptr && *skip != 0) return;
@@ -56,9 +74,9 @@ __global__ void __launch_bounds__(kTX* kTY) k_stencil(Dims d, const double* __re
       if (kw >= 0 && xw >= 0 && yw >= 0) {
         const int64_t q = (int64_t)xw + (int64_t)d.nx * yw + plane * kw;
         if (MODE == ST_PREC)
-          val = __dmul_rn(__ldg(&v[q]), __ldg(&dinv[q]));
+          val = __dmul_rn(ld_val<VT>(v, q), __ldg(&dinv[q]));
         else
-          val = __ldg(&v[q]);
+          val = ld_val<VT>(v, q);
       }
       sz[slot][ly][lx] = val;
     }
@@ -97,7 +115,7 @@ __global__ void __launch_bounds__(kTX* kTY) k_stencil(Dims d, const double* __re
           w = fma(__ldg(&coef[18 * N + p]), sz[sp][cy + 1][cx], w);
         }
         if (MODE == ST_RESID) w = __ldg(&b[p]) - w;
-        y[p] = w;
+        st_val<YT>(y, p, w);
         acc2 = fma(w, w, acc2);
       }
       __syncthreads();
@@ -149,6 +167,31 @@ cudaError_t launch_stencil(const Dims& d, int S, int mode, const double* coef, c
     else RK_ST(19, ST_RESID);
   }
 #undef RK_ST
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stencil_df(const Dims& d, int S, int mode, const double* coef, const double* dinv,
+                              const void* v, bool v_df, void* y, bool y_df, const int* skip, cudaStream_t st) {
+  dim3 grid;
+  int zchunk;
+  stencil_grid(d, grid, zchunk);
+  const dim3 block(kTX * kTY);
+  if (mode == ST_RESID) return cudaErrorInvalidValue;
+#define RK_STD(SS, MM, VT, YT)                                                                                  \
+  k_stencil<SS, MM, VT, YT><<<grid, block, 0, st>>>(d, coef, dinv, (const VT*)v, nullptr, (YT*)y, nullptr, nullptr, \
+                                                    nullptr, skip, zchunk)
+#define RK_STD_TYPES(SS, MM)                    \
+  if (v_df && y_df) RK_STD(SS, MM, float2, float2); \
+  else if (v_df) RK_STD(SS, MM, float2, double);    \
+  else if (y_df) RK_STD(SS, MM, double, float2);    \
+  else RK_STD(SS, MM, double, double);
+  if (S == 7) {
+    if (mode == ST_PREC) { RK_STD_TYPES(7, ST_PREC) } else { RK_STD_TYPES(7, ST_PLAIN) }
+  } else {
+    if (mode == ST_PREC) { RK_STD_TYPES(19, ST_PREC) } else { RK_STD_TYPES(19, ST_PLAIN) }
+  }
+#undef RK_STD_TYPES
+#undef RK_STD
   return cudaGetLastError();
 }
 
