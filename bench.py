@@ -209,7 +209,7 @@ def run_ours(args, ws, rank, local):
     ctx = Context()
     prob = Problem(ctx, cfg.grid, torch.from_numpy(cfg.coef))
     x = torch.zeros(cfg.n, dtype=torch.float64, device="cuda")
-    kw = dict(tol=1e-8, m=m, k=k, mode=mode, max_matvec=args.max_matvec, hybrid_switch=5)
+    kw = dict(tol=1e-8, m=m, k=k, mode=mode, max_matvec=args.max_matvec, hybrid_switch=5, precision=args.precision)
     infos = []
     for t in range(W):
         x.zero_()
@@ -276,8 +276,9 @@ def run_ours(args, ws, rank, local):
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": K, "warmup": W,
         "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
+        "dtype": "f64" if args.precision == "fp64" else "f64+f32-operator", "data": "synthetic",
         "config": {"workload": args.workload, "grid": [edge] * 3, "stencil": cfg.S, "solver": f"{mode}({m},{k})",
+                   "precision": args.precision,
                    "tol": 1e-8, "sequence_steps_timed": [W, W + K - 1], "l2": "inputs larger than L2",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "solver_hbm_gbs": solver_gbs, "solver_hbm_frac": solver_gbs / hbm_peak,
@@ -319,6 +320,8 @@ def main():
     ap.add_argument("--workload", default="channel128", choices=sorted(WORKLOADS))
     ap.add_argument("--max-matvec", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="fp64: FP64 operator, double-float projections; mixed: FP32 inner operator (A11)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -77,7 +77,10 @@ typedef struct {
   int32_t max_matvec;    /* cap on matrix-vector products in the recurrences (<= 0: 2000) */
   int32_t hybrid_switch; /* RK_HYBRID: solves of this problem run with rGCROT before the switch */
   int32_t mode;          /* rk_mode */
-  int32_t precision;     /* rk_precision (RK_FP64 only in this version) */
+  int32_t precision;     /* rk_precision: RK_FP64, or RK_MIXED = the A M^{-1} products of the
+                            recurrences with an FP32 copy of the operator (FP32 accumulation),
+                            everything else as in RK_FP64, b - A x recomputed in FP64 every
+                            cycle / on convergence (residual replacement) */
   int32_t update_recycle;/* rGCROT: 1 = update U, C after every cycle (line 14a), 0 = keep */
   int32_t reserved;
 } rk_solve_params;
@@ -159,8 +162,10 @@ int rk_solve(rk_problem* p, const double* b, double* x, const rk_solve_params* p
 
 /*
  * Operator application (single products, for tests and callers that compose):
- * y = A (M^{-1} v) if precond != 0, else y = A v; and r = b - A x.
- * All vectors device, N doubles.
+ * precond = 1: y = A (M^{-1} v); 0: y = A v; 2: the FP32 operator of
+ * RK_MIXED, y = A32 (M32^{-1} v) with A32, M32^{-1} the coefficients and
+ * 1/a_pp rounded to FP32, v rounded to FP32, FP32 accumulation in band order,
+ * the result widened to FP64. And r = b - A x. All vectors device, N doubles.
  */
 int rk_apply(const rk_problem* p, const double* v, double* y, int32_t precond, void* stream);
 int rk_residual(const rk_problem* p, const double* b, const double* x, double* r, void* stream);

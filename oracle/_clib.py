@@ -41,6 +41,8 @@ def lib():
                 fn = getattr(L, name)
                 fn.restype = None
                 fn.argtypes = [i64, i64, i64, p, ctypes.c_int, p] + [p] * (extra + 1)
+            L.oracle_apply_prec_f32.restype = None
+            L.oracle_apply_prec_f32.argtypes = [i64, i64, i64, p, ctypes.c_int, p, p, p, p]
             L.oracle_jacobi_inverse.restype = None
             L.oracle_jacobi_inverse.argtypes = [i64, p, p]
             _lib = L
@@ -77,6 +79,13 @@ class Stencil:
         v = _c64(v)
         w = np.empty(self.n)
         lib().oracle_apply_prec(*self._dims(), _ptr(self.dinv), _ptr(v), _ptr(w))
+        return w
+
+    def apply_prec_f32(self, v):
+        """The mixed-precision inner operator A32 M32^{-1} v (FP32 arithmetic)."""
+        v = _c64(v)
+        w = np.empty(self.n)
+        lib().oracle_apply_prec_f32(*self._dims(), _ptr(self.dinv), _ptr(v), _ptr(w))
         return w
 
     def apply(self, x):

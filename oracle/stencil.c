@@ -81,6 +81,34 @@ void oracle_apply(int64_t nx, int64_t ny, int64_t nz, const uint8_t* per, int S,
   apply_core(nx, ny, nz, per, S, coef, 0, v, w);
 }
 
+/* Mixed-precision inner operator (FP32): with c32 = RN32(coef), d32 =
+ * RN32(1/a_pp) and z_q = RN32(RN32(v_q) * d32_q), w_p = RN32(c32_0 z_p) then
+ * w_p = fmaf(c32_s, z_nb, w_p) in band order; the result widened to double. */
+void oracle_apply_prec_f32(int64_t nx, int64_t ny, int64_t nz, const uint8_t* per, int S,
+                           const double* coef, const double* dinv, const double* v, double* y) {
+  const int64_t N = nx * ny * nz;
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < nz; ++k) {
+    for (int64_t j = 0; j < ny; ++j) {
+      for (int64_t i = 0; i < nx; ++i) {
+        const int64_t p = i + nx * (j + ny * k);
+        float zp = (float)v[p] * (float)dinv[p];
+        float w = (float)coef[p] * zp;
+        for (int s = 1; s < S; ++s) {
+          int64_t ii = wrap(i + OFF[s][0], nx, per[0]);
+          int64_t jj = wrap(j + OFF[s][1], ny, per[1]);
+          int64_t kk = wrap(k + OFF[s][2], nz, per[2]);
+          if (ii < 0 || jj < 0 || kk < 0) continue;
+          const int64_t q = ii + nx * (jj + ny * kk);
+          float zq = (float)v[q] * (float)dinv[q];
+          w = fmaf((float)coef[(int64_t)s * N + p], zq, w);
+        }
+        y[p] = (double)w;
+      }
+    }
+  }
+}
+
 /* r = b - A x, element by element: r_p = b_p - (A x)_p */
 void oracle_residual(int64_t nx, int64_t ny, int64_t nz, const uint8_t* per, int S,
                      const double* coef, const double* b, const double* x, double* r) {

@@ -73,6 +73,12 @@ __device__ __forceinline__ void block_df_reduce_cols(float2* vals, int ncol, flo
 
 // out[q] = Q_q^T w (q < nq, DF columns), then (self) w^T w in DF, then w^T e_k
 // for the FP64 extras e_k (FP64 arithmetic, used by rBiCGStab's r~).
+// Grid: x = element chunks (red_blocks(n)), y = groups of kDotGroup columns
+// (the last y slice takes the FP64 extras); each thread carries kDotGroup
+// independent double-float chains, so registers stay low and occupancy high;
+// w is re-read per group (from L2).
+constexpr int kDotGroup = 4;
+
 template <typename WT>
 __global__ void __launch_bounds__(kRedThreads) k_dfdots(DFDotsArgs a) {
   if (a.skip_flag != nullptr && *a.skip_flag != 0) return;
@@ -82,34 +88,36 @@ __global__ void __launch_bounds__(kRedThreads) k_dfdots(DFDotsArgs a) {
   const WT* w = (const WT*)a.w;
   const int ndf = a.nq + a.self;  // DF columns; the self column is w itself
   const int ncols = ndf + a.ne;
+  const int ngroups = (ndf + kDotGroup - 1) / kDotGroup;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  for (int c0 = 0; c0 < ndf; c0 += kDFCols) {
-    const int nc = min(kDFCols, ndf - c0);
-    float sh[kDFCols], sl[kDFCols];
+  if ((int)blockIdx.y < ngroups) {
+    const int c0 = blockIdx.y * kDotGroup;
+    const int nc = min(kDotGroup, ndf - c0);
+    float sh[kDotGroup], sl[kDotGroup];
 #pragma unroll
-    for (int q = 0; q < kDFCols; ++q) sh[q] = sl[q] = 0.f;
+    for (int q = 0; q < kDotGroup; ++q) sh[q] = sl[q] = 0.f;
+    const float2* base[kDotGroup];
+#pragma unroll
+    for (int q = 0; q < kDotGroup; ++q) {
+      const int col = c0 + q;
+      base[q] = (q < nc && col < a.nq) ? a.Q + (int64_t)col * a.ld : nullptr;
+    }
     for (int64_t i = i0; i < a.n; i += stride) {
       const float2 wv = load_df<WT>(w, i);
-      // every load of the element issued before any arithmetic (the
-      // double-float chains would otherwise serialise them)
-      float2 v[kDFCols];
+      float2 v[kDotGroup];
 #pragma unroll
-      for (int q = 0; q < kDFCols; ++q) {
-        const int col = c0 + q;
-        v[q] = (q < nc && col < a.nq) ? __ldg(&a.Q[(int64_t)col * a.ld + i]) : wv;
-      }
+      for (int q = 0; q < kDotGroup; ++q) v[q] = base[q] ? __ldg(&base[q][i]) : wv;
 #pragma unroll
-      for (int q = 0; q < kDFCols; ++q)
+      for (int q = 0; q < kDotGroup; ++q)
         if (q < nc) df_mac(sh[q], sl[q], v[q].x, v[q].y, wv.x, wv.y);
     }
     float2 vals[kDFCols];
 #pragma unroll
-    for (int q = 0; q < kDFCols; ++q) vals[q] = make_float2(sh[q], sl[q]);
+    for (int q = 0; q < kDotGroup; ++q) vals[q] = make_float2(sh[q], sl[q]);
     block_df_reduce_cols(vals, nc, red, a.part + (int64_t)blockIdx.x * ncols + c0);
-  }
-  if (a.ne > 0) {
+  } else if (a.ne > 0) {
     double acc[3] = {0.0, 0.0, 0.0};
     for (int64_t i = i0; i < a.n; i += stride) {
       double wi;
@@ -393,10 +401,14 @@ int dfgemm_tile_rows(int np) { return np <= 96 ? 64 : 32; }
 }  // namespace
 
 cudaError_t launch_dfdots(const DFDotsArgs& a, bool w_is_df, cudaStream_t st) {
+  const int ndf = a.nq + a.self;
+  const int groups = (ndf + kDotGroup - 1) / kDotGroup + (a.ne > 0 ? 1 : 0);
+  if (groups == 0) return cudaSuccess;
+  const dim3 grid(red_blocks(a.n), groups);
   if (w_is_df)
-    k_dfdots<float2><<<red_blocks(a.n), kRedThreads, 0, st>>>(a);
+    k_dfdots<float2><<<grid, kRedThreads, 0, st>>>(a);
   else
-    k_dfdots<double><<<red_blocks(a.n), kRedThreads, 0, st>>>(a);
+    k_dfdots<double><<<grid, kRedThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 

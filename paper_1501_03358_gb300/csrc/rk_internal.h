@@ -39,6 +39,11 @@ cudaError_t launch_stencil(const Dims& d, int S, int mode, const double* coef, c
 // The same products with a double-float input and/or output vector (the
 // arithmetic stays FP64 in the same order; v = hi + lo on load, the result
 // split into hi + lo on store).
+// Mixed precision: A M^{-1} v with FP32 coefficients and 1/a_pp, FP32
+// accumulation, double-float or FP64 input/output.
+cudaError_t launch_stencil32(const Dims& d, int S, const float* coef32, const float* dinv32, const void* v,
+                             bool v_df, void* y, bool y_df, const int* skip, cudaStream_t st);
+cudaError_t launch_round_f32(int64_t n, const double* src, float* dst, cudaStream_t st);
 cudaError_t launch_stencil_df(const Dims& d, int S, int mode, const double* coef, const double* dinv,
                               const void* v, bool v_df, void* y, bool y_df, const int* skip_flag, cudaStream_t st);
 int stencil_blocks(const Dims& d);

@@ -180,6 +180,8 @@ struct rk_problem {
   float2* QB = nullptr;           // double-float basis [C | V]
   float2* Ub = nullptr;           // double-float U
   double* rvec = nullptr;         // FP64 residual of the rGCROT cycle
+  float* coef32 = nullptr;        // mixed precision: FP32 copy of the bands
+  float* dinv32 = nullptr;        // mixed precision: FP32 1/a_pp
   double* bicg = nullptr;
   // small
   double* small = nullptr;
@@ -405,6 +407,70 @@ int stencil_df_launch(rk_problem* p, int mode, const void* v, bool v_df, void* y
   return RK_OK;
 }
 
+// FP32 copy of the operator for the mixed-precision inner products (A11):
+// coefficients and 1/a_pp rounded to nearest once.
+int ensure_mixed(rk_problem* p, cudaStream_t st) {
+  if (p->coef32) return RK_OK;
+  RK_TRY(alloc_into(p->ctx, &p->coef32, (size_t)p->S * p->n));
+  RK_TRY(alloc_into(p->ctx, &p->dinv32, (size_t)p->ld));
+  RK_CUDA(launch_round_f32((int64_t)p->S * p->n, p->coef, p->coef32, st));
+  RK_CUDA(launch_round_f32(p->n, p->dinv, p->dinv32, st));
+  return RK_OK;
+}
+
+// A M^{-1} v of the recurrences: FP64 (bit-exact order) or, in mixed mode,
+// the FP32 operator
+int opapply_launch(rk_problem* p, bool mixed, const void* v, bool v_df, void* y, bool y_df, const int* skip,
+                   cudaStream_t st) {
+  if (!mixed) {
+    if (!v_df && !y_df)
+      return stencil_launch(p, ST_PREC, (const double*)v, nullptr, (double*)y, nullptr, nullptr, nullptr, skip, st);
+    return stencil_df_launch(p, ST_PREC, v, v_df, y, y_df, skip, st);
+  }
+  ProfScope ps(&p->prof, PC_SPMV, 8.0 * (0.5 * p->S + 2.5) * (double)p->n, st);
+  RK_CUDA(launch_stencil32(p->d, p->S, p->coef32, p->dinv32, v, v_df, y, y_df, skip, st));
+  return RK_OK;
+}
+
+// C = orth(A U) in FP64 with U rescaled so that A U = C (CholQR2 of line 1a)
+// for the k stored columns.
+int derive_c_from_u(rk_problem* p, int k, cudaStream_t st) {
+  float2* Ud = p->Ublk(k);
+  float2* Cd = p->Cblk(k);
+  double* G = p->eta;
+  double* Rinv = p->eta + (size_t)k * k;
+  double* Rw = p->sb.hrws;
+  for (int c = 0; c < k; ++c)
+    RK_CUDA(launch_stencil_df(p->d, p->S, ST_PLAIN, p->coef, nullptr, Ud + (int64_t)c * p->ld, true,
+                              Cd + (int64_t)c * p->ld, true, nullptr, st));
+  for (int pass = 0; pass < 2; ++pass) {
+    DFGramArgs g{};
+    g.n = p->n;
+    g.na = k;
+    g.nb = 0;
+    g.nu = k;
+    g.A = Cd;
+    g.lda = p->ld;
+    g.Bm = nullptr;
+    g.ldb = p->ld;
+    g.d = nullptr;
+    g.U = Cd;
+    g.ldu = p->ld;
+    g.part = p->part;
+    g.counter = p->counter;
+    g.out = G;
+    RK_CUDA(launch_dfgram(g, st));
+    RK_CUDA(launch_chol_rinv(k, G, Rinv, Rw, p->istat, st));
+    int hs = 0;
+    RK_CUDA(cudaMemcpyAsync(&hs, p->istat, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RK_CUDA(cudaStreamSynchronize(st));
+    if (hs != 0) return fail(RK_E_INVALID, "A U is rank deficient (Cholesky of C~^T C~ failed)");
+    RK_TRY(dfgemm_launch(p, Cd, k, nullptr, 0, nullptr, Rinv, k, Cd, true, 0, st));
+    RK_TRY(dfgemm_launch(p, Ud, k, nullptr, 0, nullptr, Rinv, k, Ud, true, 0, st));
+  }
+  return RK_OK;
+}
+
 // Line 1b at the start of a cycle: xi = C^T r, r <- r - C xi, x <- x + U xi;
 // ||r||^2 -> st->rho2 (r and x FP64).
 int project_residual(rk_problem* p, int kc, double* r, double* x, cudaStream_t st) {
@@ -430,7 +496,9 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
   const int m = prm.m;
   const int k = recycle ? prm.k : 0;
   const int maxmv = prm.max_matvec > 0 ? prm.max_matvec : 2000;
+  const bool mixed = prm.precision == RK_MIXED;
   RK_TRY(ensure_capacity(p, std::max(k, p->kdim), m, st));
+  if (mixed) RK_TRY(ensure_mixed(p, st));
   int kc = recycle ? p->kdim : 0;
   const double S = p->S;
   double words = 0.0;
@@ -465,7 +533,7 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
     { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_cycle_init(p->st, p->sb, st)); }
     for (int j = 0; j < steps; ++j) {
       // line 6: w = A M^{-1} v_j into the slot of v_{j+1}
-      RK_TRY(stencil_df_launch(p, ST_PREC, p->Vcol(j), true, p->Vcol(j + 1), true, done, st));
+      RK_TRY(opapply_launch(p, mixed, p->Vcol(j), true, p->Vcol(j + 1), true, done, st));
       // lines 6a-10 as two block classical Gram-Schmidt passes over [C V_j]
       const int nq = kc + j + 1;
       RK_TRY(dfdots_launch(p, p->Cblk(kc), nq, p->Vcol(j + 1), true, p->sb.dots, done, st));
@@ -527,6 +595,11 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
     RK_TRY(sync_state(p, st));
     rho = std::sqrt(p->st_h->rho2);
   }
+  if (mixed && update && p->kdim > 0) {
+    // the FP32 operator leaves A U = C only to FP32 accuracy: re-derive C from
+    // U in FP64 so the space carried to the next solve keeps A U = C exactly
+    RK_TRY(derive_c_from_u(p, p->kdim, st));
+  }
   info.matvecs = matvecs;
   info.cycles_or_iters = cycles;
   info.relres_true = rho / bnorm;
@@ -541,7 +614,9 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
 int solve_bicg(rk_problem* p, const double* b, double* x, const rk_solve_params& prm, rk_solve_info& info,
                bool recycle, cudaStream_t st) {
   const int maxmv = prm.max_matvec > 0 ? prm.max_matvec : 2000;
+  const bool mixed = prm.precision == RK_MIXED;
   RK_TRY(ensure_capacity(p, p->kdim, std::max(p->mcap, 1), st));
+  if (mixed) RK_TRY(ensure_mixed(p, st));
   if (!p->bicg) RK_TRY(alloc_into(p->ctx, &p->bicg, (size_t)7 * p->ld));
   const int kc = recycle ? p->kdim : 0;
   BicgVecs v{};
@@ -592,11 +667,11 @@ int solve_bicg(rk_problem* p, const double* b, double* x, const rk_solve_params&
     while (running) {
       for (int it = 0; it < NB; ++it) {
         { ProfScope ps_(&p->prof, PC_BICG, 32.0 * p->n, st); RK_CUDA(launch_bicg_p(v, p->bs, p->n, st)); }
-        RK_TRY(stencil_launch(p, ST_PREC, v.p, nullptr, v.v, nullptr, nullptr, nullptr, &p->bs->stop, st));
+        RK_TRY(opapply_launch(p, mixed, v.p, false, v.v, false, &p->bs->stop, st));
         RK_TRY(dfdots_launch(p, p->Cblk(kc), kc, v.v, false, eta1, &p->bs->stop, st, v.rt));
         { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_bicg_alpha(p->bs, eta1, kc, st)); }
         { ProfScope ps_(&p->prof, PC_BICG, 8.0 * (kc + (kc ? 5 : 3)) * (double)p->n, st); RK_CUDA(launch_bicg_s(v, p->bs, p->n, kc, p->Cblk(kc), p->ld, eta1, xi, p->part, p->counter, st)); }
-        RK_TRY(stencil_launch(p, ST_PREC, v.s, nullptr, v.t, nullptr, nullptr, nullptr, &p->bs->stop, st));
+        RK_TRY(opapply_launch(p, mixed, v.s, false, v.t, false, &p->bs->stop, st));
         if (kc) RK_TRY(dfdots_launch(p, p->Cblk(kc), kc, v.t, false, eta2, &p->bs->stop, st));
         { ProfScope ps_(&p->prof, PC_BICG, 8.0 * (kc + (kc ? 3 : 2)) * (double)p->n, st); RK_CUDA(launch_bicg_t(v, p->bs, p->n, kc, p->Cblk(kc), p->ld, eta2, p->part, p->counter, st)); }
         { ProfScope ps_(&p->prof, PC_BICG, 56.0 * p->n, st); RK_CUDA(launch_bicg_r(v, p->bs, p->n, kc, eta1, eta2, xi, p->part, p->counter, st)); }
@@ -784,6 +859,9 @@ void rk_problem_destroy(rk_problem* p) {
   dev_free(c, p->dinv);
   dev_free(c, p->QB);
   dev_free(c, p->Ub);
+  dev_free(c, p->rvec);
+  dev_free(c, p->coef32);
+  dev_free(c, p->dinv32);
   dev_free(c, p->bicg);
   dev_free(c, p->small);
   dev_free(c, p->eta);
@@ -801,6 +879,13 @@ void rk_problem_destroy(rk_problem* p) {
 
 int rk_apply(const rk_problem* p, const double* v, double* y, int32_t precond, void* stream) {
   if (!p || !v || !y) return fail(RK_E_INVALID, "NULL argument");
+  if (precond == 2) {
+    rk_problem* pm = const_cast<rk_problem*>(p);
+    RK_TRY(ensure_mixed(pm, (cudaStream_t)stream));
+    RK_CUDA(launch_stencil32(p->d, p->S, p->coef32, p->dinv32, v, false, y, false, nullptr, (cudaStream_t)stream));
+    RK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return RK_OK;
+  }
   RK_CUDA(launch_stencil(p->d, p->S, precond ? ST_PREC : ST_PLAIN, p->coef, p->dinv, v, nullptr, y, nullptr,
                          nullptr, nullptr, nullptr, (cudaStream_t)stream));
   RK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
@@ -879,19 +964,7 @@ int rk_set_recycle(rk_problem* p, const double* U, const double* C, int32_t k, v
   };
   if (!C) {
     // line 1a: C~ = A U; thin QR by CholQR2 (C~ = C R), U <- U R^{-1}
-    for (int c = 0; c < k; ++c)
-      RK_CUDA(launch_stencil_df(p->d, p->S, ST_PLAIN, p->coef, nullptr, Ud + (int64_t)c * p->ld, true,
-                                Cd + (int64_t)c * p->ld, true, nullptr, st));
-    for (int pass = 0; pass < 2; ++pass) {
-      RK_TRY(gram_cc(Cd));
-      RK_CUDA(launch_chol_rinv(k, G, Rinv, Rw, p->istat, st));
-      int hs = 0;
-      RK_CUDA(cudaMemcpyAsync(&hs, p->istat, sizeof(int), cudaMemcpyDeviceToHost, st));
-      RK_CUDA(cudaStreamSynchronize(st));
-      if (hs != 0) return fail(RK_E_INVALID, "A U is rank deficient (Cholesky of C~^T C~ failed)");
-      RK_TRY(dfgemm_launch(p, Cd, k, nullptr, 0, nullptr, Rinv, k, Cd, true, 0, st));
-      RK_TRY(dfgemm_launch(p, Ud, k, nullptr, 0, nullptr, Rinv, k, Ud, true, 0, st));
-    }
+    RK_TRY(derive_c_from_u(p, k, st));
   } else {
     RK_CUDA(launch_to_df(p->n, C, Cd, nullptr, 0, k, p->n, p->ld, st));
     // invariants: ||C^T C - I||_F and ||A U - C||_F
@@ -952,7 +1025,7 @@ int rk_solve(rk_problem* p, const double* b, double* x, const rk_solve_params* p
   if (!p || !b || !x || !params) return fail(RK_E_INVALID, "NULL argument");
   rk_solve_params prm = *params;
   if (!(prm.tol > 0.0)) return fail(RK_E_INVALID, "tol must be positive");
-  if (prm.precision != RK_FP64) return fail(RK_E_INVALID, "only RK_FP64 is supported in this version");
+  if (prm.precision != RK_FP64 && prm.precision != RK_MIXED) return fail(RK_E_INVALID, "unknown precision");
   if (prm.k < 0) return fail(RK_E_INVALID, "k < 0");
   rk_solve_info loc{};
   rk_solve_info& inf = info ? *info : loc;

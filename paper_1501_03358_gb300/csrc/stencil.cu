@@ -129,6 +129,94 @@ __global__ void __launch_bounds__(kTX* kTY) k_stencil(Dims d, const double* __re
   if (arrive_last(counter, &lastflag)) reduce_partials(part, nb, 1, nrm2);
 }
 
+// FP32 operator (the mixed-precision inner product A M^{-1} v): coefficients
+// and 1/a_pp rounded to FP32 once, z = (float)v * dinv32, FP32 accumulation in
+// the same band order, result widened on store. Input and output are
+// double-float (the basis) or FP64 (rBiCGStab's vectors).
+template <typename VT>
+__device__ __forceinline__ float ld_f32(const VT* p, int64_t q);
+template <>
+__device__ __forceinline__ float ld_f32<double>(const double* p, int64_t q) { return __double2float_rn(__ldg(&p[q])); }
+template <>
+__device__ __forceinline__ float ld_f32<float2>(const float2* p, int64_t q) { return __ldg(&p[q]).x; }
+
+template <typename YT>
+__device__ __forceinline__ void st_f32(YT* p, int64_t q, float w);
+template <>
+__device__ __forceinline__ void st_f32<double>(double* p, int64_t q, float w) { p[q] = (double)w; }
+template <>
+__device__ __forceinline__ void st_f32<float2>(float2* p, int64_t q, float w) { p[q] = make_float2(w, 0.f); }
+
+template <int S, typename VT, typename YT>
+__global__ void __launch_bounds__(kTX* kTY) k_stencil32(Dims d, const float* __restrict__ coef,
+                                                        const float* __restrict__ dinv, const VT* __restrict__ v,
+                                                        YT* __restrict__ y, const int* skip, int zchunk) {
+  if (skip != nullptr && *skip != 0) return;
+  __shared__ float sz[3][kTY + 2][kTX + 2];
+  const int tx = threadIdx.x & (kTX - 1), ty = threadIdx.x / kTX;
+  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+  const int k0 = blockIdx.z * zchunk;
+  const int k1 = min(k0 + zchunk, d.nz);
+  const int gi = x0 + tx, gj = y0 + ty;
+  const bool active = gi < d.nx && gj < d.ny;
+  const int64_t N = d.n;
+  const int64_t plane = (int64_t)d.nx * d.ny;
+  auto load_plane = [&](int kk, int slot) {
+    const int kw = halo_coord(kk, d.nz, d.pz);
+    for (int t = threadIdx.x; t < (kTY + 2) * (kTX + 2); t += kTX * kTY) {
+      const int ly = t / (kTX + 2), lx = t - ly * (kTX + 2);
+      const int xw = halo_coord(x0 + lx - 1, d.nx, d.px);
+      const int yw = halo_coord(y0 + ly - 1, d.ny, d.py);
+      float val = 0.f;
+      if (kw >= 0 && xw >= 0 && yw >= 0) {
+        const int64_t q = (int64_t)xw + (int64_t)d.nx * yw + plane * kw;
+        val = __fmul_rn(ld_f32<VT>(v, q), __ldg(&dinv[q]));
+      }
+      sz[slot][ly][lx] = val;
+    }
+  };
+  if (k0 >= k1) return;
+  load_plane(k0 - 1, (k0 + 2) % 3);
+  load_plane(k0, k0 % 3);
+  for (int k = k0; k < k1; ++k) {
+    load_plane(k + 1, (k + 1) % 3);
+    __syncthreads();
+    if (active) {
+      const int sc = k % 3, sm = (k + 2) % 3, sp = (k + 1) % 3;
+      const int64_t p = (int64_t)gi + (int64_t)d.nx * gj + plane * k;
+      const int cx = tx + 1, cy = ty + 1;
+      float w = __fmul_rn(__ldg(&coef[p]), sz[sc][cy][cx]);
+      w = fmaf(__ldg(&coef[1 * N + p]), sz[sc][cy][cx - 1], w);
+      w = fmaf(__ldg(&coef[2 * N + p]), sz[sc][cy][cx + 1], w);
+      w = fmaf(__ldg(&coef[3 * N + p]), sz[sc][cy - 1][cx], w);
+      w = fmaf(__ldg(&coef[4 * N + p]), sz[sc][cy + 1][cx], w);
+      w = fmaf(__ldg(&coef[5 * N + p]), sz[sm][cy][cx], w);
+      w = fmaf(__ldg(&coef[6 * N + p]), sz[sp][cy][cx], w);
+      if (S == 19) {
+        w = fmaf(__ldg(&coef[7 * N + p]), sz[sc][cy - 1][cx - 1], w);
+        w = fmaf(__ldg(&coef[8 * N + p]), sz[sc][cy - 1][cx + 1], w);
+        w = fmaf(__ldg(&coef[9 * N + p]), sz[sc][cy + 1][cx - 1], w);
+        w = fmaf(__ldg(&coef[10 * N + p]), sz[sc][cy + 1][cx + 1], w);
+        w = fmaf(__ldg(&coef[11 * N + p]), sz[sm][cy][cx - 1], w);
+        w = fmaf(__ldg(&coef[12 * N + p]), sz[sm][cy][cx + 1], w);
+        w = fmaf(__ldg(&coef[13 * N + p]), sz[sp][cy][cx - 1], w);
+        w = fmaf(__ldg(&coef[14 * N + p]), sz[sp][cy][cx + 1], w);
+        w = fmaf(__ldg(&coef[15 * N + p]), sz[sm][cy - 1][cx], w);
+        w = fmaf(__ldg(&coef[16 * N + p]), sz[sm][cy + 1][cx], w);
+        w = fmaf(__ldg(&coef[17 * N + p]), sz[sp][cy - 1][cx], w);
+        w = fmaf(__ldg(&coef[18 * N + p]), sz[sp][cy + 1][cx], w);
+      }
+      st_f32<YT>(y, p, w);
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_round_f32(int64_t n, const double* __restrict__ src, float* __restrict__ dst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = __double2float_rn(src[i]);
+}
+
 void stencil_grid(const Dims& d, dim3& grid, int& zchunk) {
   const int tx = (d.nx + kTX - 1) / kTX, ty = (d.ny + kTY - 1) / kTY;
   const int tiles = tx * ty;
@@ -167,6 +255,34 @@ cudaError_t launch_stencil(const Dims& d, int S, int mode, const double* coef, c
     else RK_ST(19, ST_RESID);
   }
 #undef RK_ST
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stencil32(const Dims& d, int S, const float* coef32, const float* dinv32, const void* v,
+                             bool v_df, void* y, bool y_df, const int* skip, cudaStream_t st) {
+  dim3 grid;
+  int zchunk;
+  stencil_grid(d, grid, zchunk);
+  const dim3 block(kTX * kTY);
+#define RK_S32(SS, VT, YT) \
+  k_stencil32<SS, VT, YT><<<grid, block, 0, st>>>(d, coef32, dinv32, (const VT*)v, (YT*)y, skip, zchunk)
+#define RK_S32_T(SS)                            \
+  if (v_df && y_df) RK_S32(SS, float2, float2); \
+  else if (v_df) RK_S32(SS, float2, double);    \
+  else if (y_df) RK_S32(SS, double, float2);    \
+  else RK_S32(SS, double, double);
+  if (S == 7) {
+    RK_S32_T(7)
+  } else {
+    RK_S32_T(19)
+  }
+#undef RK_S32_T
+#undef RK_S32
+  return cudaGetLastError();
+}
+
+cudaError_t launch_round_f32(int64_t n, const double* src, float* dst, cudaStream_t st) {
+  k_round_f32<<<red_blocks(n), kRedThreads, 0, st>>>(n, src, dst);
   return cudaGetLastError();
 }
 

@@ -126,10 +126,13 @@ class Problem:
         N.check(self.lib.rk_create_problem(ctx.handle, ctypes.byref(g), self.S, _dptr(coef), _stream_ptr(stream),
                                            ctypes.byref(self._h)))
 
-    def apply(self, v, precond=True, stream=None):
+    def apply(self, v, precond=True, stream=None, fp32=False):
+        """A M^{-1} v (precond), A v, or with fp32 the FP32 operator of the
+        mixed-precision mode."""
         v = _f64_cuda(v, (self.n,))
         y = torch.empty_like(v)
-        N.check(self.lib.rk_apply(self._h, _dptr(v), _dptr(y), 1 if precond else 0, _stream_ptr(stream)))
+        mode = 2 if fp32 else (1 if precond else 0)
+        N.check(self.lib.rk_apply(self._h, _dptr(v), _dptr(y), mode, _stream_ptr(stream)))
         return y
 
     def residual(self, b, x, stream=None):
@@ -179,15 +182,16 @@ class Problem:
         return U[: kk.value], C[: kk.value]
 
     def solve(self, b, x0=None, tol=1e-8, m=40, k=20, mode="rGCROT", max_matvec=2000, hybrid_switch=5,
-              update_recycle=True, out=None, stream=None, check_status=False):
+              update_recycle=True, out=None, stream=None, check_status=False, precision="fp64"):
         """Solve A x = b; returns (x, info dict). x0 defaults to 0."""
         b = _f64_cuda(b, (self.n,))
         if out is None:
             out = torch.zeros_like(b) if x0 is None else _f64_cuda(x0, (self.n,)).clone()
         elif x0 is not None:
             out.copy_(_f64_cuda(x0, (self.n,)))
+        prec = {"fp64": N.RK_FP64, "mixed": N.RK_MIXED}[precision]
         prm = N.rk_solve_params(float(tol), int(m), int(k), int(max_matvec), int(hybrid_switch), N.MODES[mode],
-                                N.RK_FP64, 1 if update_recycle else 0, 0)
+                                prec, 1 if update_recycle else 0, 0)
         if mode == "BiCGStab":
             prm.k = 0
         info = N.rk_solve_info()

@@ -82,6 +82,19 @@ def test_stencil_bit_exact(ctx, S, dims, per):
     assert np.array_equal(r, op.residual(b, v))
 
 
+@pytest.mark.parametrize("S", [7, 19])
+@pytest.mark.parametrize("dims,per", GRIDS[:4])
+def test_fp32_operator_bit_exact(ctx, S, dims, per):
+    """The mixed-precision inner operator (A11) matches the oracle's FP32
+    restatement bit for bit."""
+    g = Grid(*dims, per)
+    coef = random_operator(g, S, np.random.default_rng(hash((S, dims, 32)) % 2**32))
+    prob = gpu_problem(ctx, g, coef)
+    op = oracle.Stencil(g, coef)
+    v = np.random.default_rng(5).standard_normal(g.n)
+    assert np.array_equal(prob.apply(t(v), fp32=True).cpu().numpy(), op.apply_prec_f32(v))
+
+
 @pytest.mark.parametrize("n,nq", [(1, 1), (1000, 3), (4099, 17), (100003, 40), (262144, 61)])
 def test_block_dots(ctx, n, nq):
     rng = np.random.default_rng(n + nq)
@@ -274,6 +287,53 @@ def test_hybrid_sequence_porous(ctx):
             if run is not None:
                 slack = max(slack, mv_slack(run, b, io["matvecs"])[0])
         assert abs(info["matvecs"] - io["matvecs"]) <= slack, (s, info["matvecs"], io["matvecs"])
+
+
+def test_mixed_precision_sequence(ctx):
+    """Mixed precision (A11): FP32 inner operator inside the FP64/double-float
+    rGCROT recurrence with b - A x recomputed in FP64 every cycle. Every step
+    reaches ||b - A x|| / ||b|| <= 1e-8 (true residual, FP64), its solution
+    error against the FP64 oracle stays within the kappa bound, and the carried
+    recycle space keeps A U = C (re-derived in FP64 after each solve)."""
+    cfg = make_config(1, size=12)
+    prob = gpu_problem(ctx, cfg.grid, cfg.coef)
+    op = oracle.Stencil(cfg.grid, cfg.coef)
+    kap = kappa(cfg.grid, cfg.coef)
+    seq = oracle.RecyclingSequence(op, mode="rGCROT", m=30, k=10, tol=1e-8, max_matvec=5000)
+    for s in range(4):
+        b = cfg.rhs(s)
+        x, info = prob.solve(t(b), tol=1e-8, m=30, k=10, mode="rGCROT", precision="mixed", max_matvec=5000)
+        xo, io = seq.solve(b)
+        xg = x.cpu().numpy()
+        rel = np.linalg.norm(op.residual(b, xg)) / np.linalg.norm(b)
+        assert info["status"] == 0 and rel <= 1e-8
+        err = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
+        assert err <= max(1e-6, 2 * kap * 1e-8), err
+        assert info["matvecs"] <= 2 * io["matvecs"] + 60
+        U, C = prob.get_recycle()
+        U, C = U.cpu().numpy().T, C.cpu().numpy().T
+        A_U = np.stack([op.apply(u) for u in U.T], axis=1)
+        assert np.linalg.norm(A_U - C) <= 1e-10 * np.linalg.norm(C) * np.abs(cfg.coef).max()
+
+
+def test_mixed_precision_hybrid_porous(ctx):
+    n = (14, 12, 10)
+    solid, _ = sphere_pack(n, 2.5, 0.3, rng_for(77, 3), max_attempts=20000)
+    grid, coef = porous_skew_19pt(n, np.where(solid, 1e-4, 1.0), 15.0)
+    prob = gpu_problem(ctx, grid, coef)
+    op = oracle.Stencil(grid, coef)
+    kap = kappa(grid, coef)
+    seq = oracle.RecyclingSequence(op, mode="hybrid", m=20, k=10, tol=1e-8, hybrid_switch=2, max_matvec=4000)
+    base = np.random.default_rng(5).standard_normal(grid.n)
+    for s in range(4):
+        b = base + 0.05 * s * np.random.default_rng(100 + s).standard_normal(grid.n)
+        x, info = prob.solve(t(b), tol=1e-8, m=20, k=10, mode="hybrid", hybrid_switch=2, max_matvec=4000,
+                             precision="mixed")
+        xo, io = seq.solve(b)
+        xg = x.cpu().numpy()
+        rel = np.linalg.norm(op.residual(b, xg)) / np.linalg.norm(b)
+        assert info["status"] == 0 and rel <= 1e-8, (s, info)
+        assert np.linalg.norm(xg - xo) <= max(1e-6, 2 * kap * 1e-8) * np.linalg.norm(xo)
 
 
 def test_zero_rhs_and_exact_recycling(ctx):

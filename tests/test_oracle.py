@@ -234,3 +234,21 @@ def test_zero_rhs():
         assert info["matvecs"] == 0 and np.all(x == 0)
     x, U, C, info = rgcrot(op, z)
     assert info["matvecs"] == 0 and np.all(x == 0)
+
+
+@pytest.mark.parametrize("S", [7, 19])
+def test_fp32_operator_within_rounding_bound(S):
+    """The mixed-precision inner operator (coefficients, 1/a_pp and v rounded
+    to FP32, FP32 accumulation) stays within the FP32 rounding bound of the
+    FP64 operator: |w32 - w64| <= (S + 3) u32 sum_s |c_s| |z_s| elementwise."""
+    g = Grid(6, 5, 4, (True, False, True))
+    coef = random_operator(g, S, np.random.default_rng(S + 7))
+    op = Stencil(g, coef)
+    A = dense_matrix(g, coef)
+    v = np.random.default_rng(8).standard_normal(g.n)
+    w64 = op.apply_prec(v)
+    w32 = op.apply_prec_f32(v)
+    z = v / coef[0]
+    bound = (S + 3) * 2.0 ** -24 * (np.abs(A) @ np.abs(z))
+    assert np.all(np.abs(w32 - w64) <= bound)
+    assert np.any(w32 != w64)  # it is not the FP64 operator
