@@ -205,6 +205,128 @@ __global__ void __launch_bounds__(kRedThreads) k_dfupdate(DFUpdateArgs a) {
   if (arrive_last(a.counter, &lastflag)) reduce_partials(a.part, gridDim.x, 1, a.nrm2);
 }
 
+// Delayed-reorthogonalisation inner products: [Q^T p, Q^T w, p^T p, p^T w,
+// w^T w]. Grid: x = element chunks (red_blocks(n)), y = groups of kDotGroup
+// columns of Q plus one slice for the three scalars. Each thread carries
+// 2 x kDotGroup double-float chains that share every load of Q.
+__global__ void __launch_bounds__(kRedThreads) k_dfdots2(DFDots2Args a) {
+  if (a.skip_flag != nullptr && *a.skip_flag != 0) return;
+  __shared__ float2 red[kWarps][kDFCols];
+  __shared__ int lastflag;
+  const int ncols = 2 * a.nq + 3;
+  const int ngroups = (a.nq + kDotGroup - 1) / kDotGroup;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double* prow = a.part + (int64_t)blockIdx.x * ncols;
+  float2 vals[kDFCols];
+  if ((int)blockIdx.y < ngroups) {
+    const int c0 = blockIdx.y * kDotGroup;
+    const int nc = min(kDotGroup, a.nq - c0);
+    float ph[kDotGroup], pl[kDotGroup], wh[kDotGroup], wl[kDotGroup];
+#pragma unroll
+    for (int q = 0; q < kDotGroup; ++q) ph[q] = pl[q] = wh[q] = wl[q] = 0.f;
+    const float2* base[kDotGroup];
+#pragma unroll
+    for (int q = 0; q < kDotGroup; ++q) base[q] = a.Q + (int64_t)(q < nc ? c0 + q : c0) * a.ld;
+    for (int64_t i = i0; i < a.n; i += stride) {
+      const float2 pv = __ldg(&a.p[i]);
+      const float2 wv = __ldg(&a.w[i]);
+      float2 v[kDotGroup];
+#pragma unroll
+      for (int q = 0; q < kDotGroup; ++q) v[q] = __ldg(&base[q][i]);
+#pragma unroll
+      for (int q = 0; q < kDotGroup; ++q) {
+        if (q < nc) {
+          df_mac(ph[q], pl[q], v[q].x, v[q].y, pv.x, pv.y);
+          df_mac(wh[q], wl[q], v[q].x, v[q].y, wv.x, wv.y);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kDotGroup; ++q) vals[q] = make_float2(ph[q], pl[q]);
+    block_df_reduce_cols(vals, nc, red, prow + c0);
+#pragma unroll
+    for (int q = 0; q < kDotGroup; ++q) vals[q] = make_float2(wh[q], wl[q]);
+    block_df_reduce_cols(vals, nc, red, prow + a.nq + c0);
+  } else {
+    float s0h = 0.f, s0l = 0.f, s1h = 0.f, s1l = 0.f, s2h = 0.f, s2l = 0.f;
+    for (int64_t i = i0; i < a.n; i += stride) {
+      const float2 pv = __ldg(&a.p[i]);
+      const float2 wv = __ldg(&a.w[i]);
+      df_mac(s0h, s0l, pv.x, pv.y, pv.x, pv.y);
+      df_mac(s1h, s1l, pv.x, pv.y, wv.x, wv.y);
+      df_mac(s2h, s2l, wv.x, wv.y, wv.x, wv.y);
+    }
+    vals[0] = make_float2(s0h, s0l);
+    vals[1] = make_float2(s1h, s1l);
+    vals[2] = make_float2(s2h, s2l);
+    block_df_reduce_cols(vals, 3, red, prow + 2 * a.nq);
+  }
+  if (arrive_last(a.counter, &lastflag)) reduce_partials(a.part, gridDim.x, ncols, a.out);
+}
+
+// v = (p - Q a) s0 into p; p_next = (w - Q b) s1 - v s2 into w (mode 0), or
+// only v (mode 1). One read of Q feeds both double-float chains.
+__global__ void __launch_bounds__(kRedThreads) k_dfupdate2(DFUpdate2Args a) {
+  const int mode = *a.mode;
+  if (mode != 0 && mode != 1) return;
+  extern __shared__ float2 cab[];  // -a (nq) | -b (nq)
+  __shared__ float2 sc[3];
+  for (int q = threadIdx.x; q < a.nq; q += blockDim.x) {
+    cab[q] = split2(-a.a[q]);
+    cab[a.nq + q] = split2(-a.b[q]);
+  }
+  if (threadIdx.x < 3) sc[threadIdx.x] = split2(a.scal[threadIdx.x]);
+  __syncthreads();
+  const float2 s0 = sc[0], s1 = sc[1], s2 = sc[2];
+  const float2* ca = cab;
+  const float2* cb = cab + a.nq;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (mode == 1) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+      const float2 pv = a.p[i];
+      float ah = pv.x, al = pv.y;
+      const float2* col = a.Q + i;
+      for (int q = 0; q < a.nq; ++q) {
+        const float2 v = __ldg(col + (int64_t)q * a.ld);
+        df_mac(ah, al, v.x, v.y, ca[q].x, ca[q].y);
+      }
+      a.p[i] = df_mul(make_float2(ah, al), s0);
+    }
+    return;
+  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    const float2 pv = a.p[i];
+    const float2 wv = a.w[i];
+    float ah = pv.x, al = pv.y, bh = wv.x, bl = wv.y;
+    const float2* col = a.Q + i;
+    int q = 0;
+    for (; q + 4 <= a.nq; q += 4) {
+      const float2 v0 = __ldg(col + (int64_t)(q + 0) * a.ld);
+      const float2 v1 = __ldg(col + (int64_t)(q + 1) * a.ld);
+      const float2 v2 = __ldg(col + (int64_t)(q + 2) * a.ld);
+      const float2 v3 = __ldg(col + (int64_t)(q + 3) * a.ld);
+      df_mac(ah, al, v0.x, v0.y, ca[q + 0].x, ca[q + 0].y);
+      df_mac(bh, bl, v0.x, v0.y, cb[q + 0].x, cb[q + 0].y);
+      df_mac(ah, al, v1.x, v1.y, ca[q + 1].x, ca[q + 1].y);
+      df_mac(bh, bl, v1.x, v1.y, cb[q + 1].x, cb[q + 1].y);
+      df_mac(ah, al, v2.x, v2.y, ca[q + 2].x, ca[q + 2].y);
+      df_mac(bh, bl, v2.x, v2.y, cb[q + 2].x, cb[q + 2].y);
+      df_mac(ah, al, v3.x, v3.y, ca[q + 3].x, ca[q + 3].y);
+      df_mac(bh, bl, v3.x, v3.y, cb[q + 3].x, cb[q + 3].y);
+    }
+    for (; q < a.nq; ++q) {
+      const float2 v = __ldg(col + (int64_t)q * a.ld);
+      df_mac(ah, al, v.x, v.y, ca[q].x, ca[q].y);
+      df_mac(bh, bl, v.x, v.y, cb[q].x, cb[q].y);
+    }
+    const float2 vf = df_mul(make_float2(ah, al), s0);
+    const float2 pn = df_add(df_mul(make_float2(bh, bl), s1), df_neg(df_mul(vf, s2)));
+    a.p[i] = vf;
+    a.w[i] = pn;
+  }
+}
+
 // Row-tiled X P with X = [A (na DF cols), Bm (nb DF cols) .* bscale]; out is
 // DF (in place safe per tile) or FP64 (optionally accumulated).
 template <typename OT>
@@ -423,6 +545,18 @@ cudaError_t launch_dfupdate(const DFUpdateArgs& a, bool in_df, bool out_df, cuda
     k_dfupdate<double, float2><<<g, kRedThreads, smem, st>>>(a);
   else
     k_dfupdate<double, double><<<g, kRedThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dfdots2(const DFDots2Args& a, cudaStream_t st) {
+  const dim3 grid(red_blocks(a.n), (a.nq + kDotGroup - 1) / kDotGroup + 1);
+  k_dfdots2<<<grid, kRedThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dfupdate2(const DFUpdate2Args& a, cudaStream_t st) {
+  const size_t smem = (size_t)(a.nq > 0 ? 2 * a.nq : 1) * sizeof(float2);
+  k_dfupdate2<<<red_blocks(a.n), kRedThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -108,6 +108,41 @@ struct DFUpdateArgs {
 };
 cudaError_t launch_dfupdate(const DFUpdateArgs& a, bool in_df, bool out_df, cudaStream_t st);
 
+// Fused inner products of one delayed-reorthogonalisation Arnoldi step:
+// out = [Q^T p (nq), Q^T w (nq), p^T p, p^T w, w^T w] for the pending basis
+// vector p and its product w = A M^{-1} p (both double-float columns).
+struct DFDots2Args {
+  int64_t n;
+  int nq;
+  const float2* Q;
+  int64_t ld;
+  const float2* p;
+  const float2* w;
+  double* part;       // red_blocks(n) * (2 nq + 3)
+  unsigned* counter;
+  double* out;        // 2 nq + 3
+  const int* skip_flag;
+};
+cudaError_t launch_dfdots2(const DFDots2Args& a, cudaStream_t st);
+
+// The update of the same step, one pass over Q:
+//   v      = (p - Q a) * scal[0]                      (final basis vector, into p)
+//   p_next = (w - Q b) * scal[1] - v * scal[2]        (next pending vector, into w)
+// *mode: 0 both, 1 v only, anything else: nothing.
+struct DFUpdate2Args {
+  int64_t n;
+  int nq;
+  const float2* Q;
+  int64_t ld;
+  const double* a;     // device, nq
+  const double* b;     // device, nq
+  const double* scal;  // device, 3
+  float2* p;
+  float2* w;
+  const int* mode;
+};
+cudaError_t launch_dfupdate2(const DFUpdate2Args& a, cudaStream_t st);
+
 struct DFGemmArgs {
   int64_t n;
   int na, nb, nc;

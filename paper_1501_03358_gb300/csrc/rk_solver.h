@@ -14,13 +14,15 @@ struct SolveState {
   double rho2;       // ||r||^2 from the last residual / projection
   double nrm2[4];    // norms from fused reductions
   double bic[16];    // rBiCGStab scalars (see solver.cu)
+  double scal[4];    // Arnoldi step: 1/alpha, 1/(alpha beta), h_jj/beta, beta
   int done;          // the current cycle stops (estimate met, happy breakdown)
   int jj;            // Arnoldi steps completed in the cycle
   int knew;          // recycle dimension after the last update
   int hr_status;     // 0 ok, else the harmonic Ritz solve failed (space kept)
   int bic_flag;      // rBiCGStab: 1 converged (||s|| or ||r||), 2 breakdown
   int bic_stop;      // rBiCGStab: skip further kernels this batch
-  int pad[2];
+  int upd_mode;      // Arnoldi update pass: 0 v_j and p_{j+1}, 1 v_j only, 2 none
+  int nspmv;         // products A M^{-1} p taken in the current cycle
 };
 
 struct SmallBuffers {
@@ -31,9 +33,9 @@ struct SmallBuffers {
   double* g;      // m+1
   double* cs;     // m
   double* sn;     // m
-  double* sv;     // m+2: column scales, v_l = sv[l] * q_l (stored q_l)
-  double* hacc;   // nqmax: accumulated projection coefficients (stored units)
-  double* dots;   // nqmax + 4: reduced inner products
+  double* sv;     // m+2: column scales, v_l = sv[l] * q_l (stored q_l; 0 after a breakdown)
+  double* hacc;   // nqmax: first-pass coefficients of the newest Hessenberg column
+  double* dots;   // 2 nqmax + 8: reduced inner products
   double* coef;   // nqmax: coefficients handed to the update kernel
   double* y;      // m
   double* xcoef;  // nqmax: coefficients of the solution update
@@ -44,8 +46,7 @@ struct SmallBuffers {
   size_t hrws_doubles;
 };
 
-cudaError_t launch_arn_coef(SolveState* s, SmallBuffers b, int kc, int j, int pass, cudaStream_t st);
-cudaError_t launch_arn_finalize(SolveState* s, SmallBuffers b, int kc, int j, cudaStream_t st);
+cudaError_t launch_dcgs_coef(SolveState* s, SmallBuffers b, int kc, int j, int final_pass, cudaStream_t st);
 cudaError_t launch_cycle_solve(SolveState* s, SmallBuffers b, int kc, cudaStream_t st);
 cudaError_t launch_harmonic_ritz(SolveState* s, SmallBuffers b, int kc, int jj, int k, cudaStream_t st);
 cudaError_t launch_set_scalar(SolveState* s, int which, cudaStream_t st);

@@ -23,64 +23,141 @@ namespace {
 constexpr int kHRThreads = 128;
 
 // ---------------------------------------------------------------- Arnoldi
-__global__ void k_arn_coef(SolveState* s, SmallBuffers b, int kc, int j, int pass) {
-  if (s->done) return;
-  const int nq = kc + j + 1;
+// One step of the Arnoldi process (Algorithm 1 lines 4-11; Algorithm 3 lines
+// 6-11 with Q = [C, V]) by classical Gram-Schmidt with delayed
+// reorthogonalisation: the stored column j holds p_j, orthogonalised once
+// and scaled by an estimate of its norm, and column j+1 holds w = A M^{-1} p_j.
+// With Q = [C, v_0 .. v_{j-1}] and dots = [a = Q^T p_j, b = Q^T w, p^T p,
+// p^T w, w^T w] from one fused pass:
+//   v_j = (p_j - Q a) / alpha,   alpha^2 = p^T p - ||a||^2   (second pass of p_j),
+// which completes Hessenberg column j-1 (it gains beta_{j-1} a and
+// h_{j,j-1} = beta_{j-1} alpha) and its Givens rotation and residual estimate.
+// Then, since A M^{-1} v_j = (w - A M^{-1} Q a) / alpha and ||a|| is at the
+// rounding level, w / alpha stands for A M^{-1} v_j: its first-pass
+// coefficients are b / alpha against Q and h_jj = (p^T w - a^T b) / alpha^2
+// against v_j, and the next pending vector is p_{j+1} = u / beta_j,
+// u = w/alpha - Q b/alpha - v_j h_jj, with the Pythagorean estimate
+// beta_j^2 = (w^T w - ||b||^2) / alpha^2 - h_jj^2 (any error in beta_j is
+// removed at step j+1, which measures p_{j+1}^T p_{j+1}).
+// final_pass (cycle end, dots = [a, p^T p]): completes column j-1 and the
+// scale of v_j only.
+// Sets upd_mode for the update pass: 0 (v_j and p_{j+1}), 1 (v_j only: the
+// cycle stops here), 2 (nothing).
+__global__ void k_dcgs_coef(SolveState* s, SmallBuffers b, int kc, int j, int final_pass) {
+  __shared__ double red[32];
+  __shared__ int sh_skip, sh_stop;
+  __shared__ double sh_alpha, sh_ia, sh_bprev;
+  if (threadIdx.x == 0) {
+    sh_skip = s->done;
+    if (!sh_skip && !final_pass) s->nspmv += 1;
+  }
+  __syncthreads();
+  if (sh_skip) {
+    if (threadIdx.x == 0) s->upd_mode = 2;
+    return;
+  }
+  const int nq = kc + j;
+  const double* A = b.dots;
+  const double* Bv = b.dots + nq;
+  double aa = 0.0, ab = 0.0, bb = 0.0;
   for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-    const double d = b.dots[q];
-    double c;
-    if (q < kc) {
-      c = d;
-    } else {
-      const double sl = b.sv[q - kc];
-      c = sl * sl * d;
+    const double x = A[q];
+    aa = fma(x, x, aa);
+    if (!final_pass) {
+      const double y = Bv[q];
+      ab = fma(x, y, ab);
+      bb = fma(y, y, bb);
     }
-    b.coef[q] = c;
-    b.hacc[q] = pass == 0 ? c : b.hacc[q] + c;
   }
-}
-
-__global__ void k_arn_finalize(SolveState* s, SmallBuffers b, int kc, int j) {
-  if (s->done || threadIdx.x != 0) return;
+  aa = block_sum(aa, red);
+  if (!final_pass) {
+    ab = block_sum(ab, red);
+    bb = block_sum(bb, red);
+  }
   const int ldh = b.m + 1;
-  // the second pass stored q_{j+1} = y2 * s2 with s2 = 1/||y1|| (1 if y1 = 0);
-  // nrm2[1] = ||q_{j+1}||^2, nrm2[2] = ||y1||^2
-  const double n1 = s->nrm2[2];
-  const double s2 = n1 > 0.0 ? rsqrt(n1) : 1.0;
-  const double nq2 = s->nrm2[1];
-  const double qn = sqrt(nq2);
-  const double svj = b.sv[j];
-  const double hnext = svj * (qn / s2);
-  for (int l = 0; l < kc; ++l) b.B[l + (int64_t)j * b.kmax] = svj * b.hacc[l];
-  for (int l = 0; l <= j; ++l) b.H[l + j * ldh] = svj * b.hacc[kc + l] / b.sv[l];
-  b.H[j + 1 + j * ldh] = hnext;
-  for (int l = j + 2; l <= b.m; ++l) b.H[l + j * ldh] = 0.0;
-  // progressive Givens QR of the Hessenberg column j
-  double* R = b.R + j * ldh;
-  for (int l = 0; l <= j + 1; ++l) R[l] = b.H[l + j * ldh];
-  for (int i = 0; i < j; ++i) {
-    const double t = b.cs[i] * R[i] + b.sn[i] * R[i + 1];
-    R[i + 1] = -b.sn[i] * R[i] + b.cs[i] * R[i + 1];
-    R[i] = t;
+  if (threadIdx.x == 0) {
+    const double pp = A[final_pass ? nq : 2 * nq];
+    const double al2 = pp - aa;
+    const double alpha = (pp > 0.0 && al2 > 1e-28 * pp) ? sqrt(al2) : 0.0;
+    sh_alpha = alpha;
+    sh_ia = alpha > 0.0 ? 1.0 / alpha : 0.0;
+    sh_bprev = s->scal[3];
+    b.sv[j] = alpha > 0.0 ? 1.0 : 0.0;
+    if (j == 0) b.g[0] *= alpha;  // r = rho p_0 = rho alpha v_0 + rho C a
+    sh_stop = 0;
   }
-  double c = 1.0, sg = 0.0, r = R[j];
-  if (R[j + 1] != 0.0) {
-    r = hypot(R[j], R[j + 1]);
-    c = R[j] / r;
-    sg = R[j + 1] / r;
+  __syncthreads();
+  const double alpha = sh_alpha, ia = sh_ia, bprev = sh_bprev;
+  if (j >= 1) {
+    const int c = j - 1;
+    for (int l = threadIdx.x; l < nq; l += blockDim.x) {
+      const double h = fma(bprev, A[l], b.hacc[l]);
+      if (l < kc)
+        b.B[l + (int64_t)c * b.kmax] = h;
+      else
+        b.H[(l - kc) + c * ldh] = h;
+    }
+    for (int l = j + threadIdx.x; l <= b.m; l += blockDim.x) b.H[l + c * ldh] = l == j ? bprev * alpha : 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      // progressive Givens QR of column c; |g_{c+1}| is the residual estimate
+      double* R = b.R + c * ldh;
+      for (int l = 0; l <= c + 1; ++l) R[l] = b.H[l + c * ldh];
+      for (int i = 0; i < c; ++i) {
+        const double t = b.cs[i] * R[i] + b.sn[i] * R[i + 1];
+        R[i + 1] = -b.sn[i] * R[i] + b.cs[i] * R[i + 1];
+        R[i] = t;
+      }
+      double cg = 1.0, sg = 0.0, rr = R[c];
+      if (R[c + 1] != 0.0) {
+        rr = hypot(R[c], R[c + 1]);
+        cg = R[c] / rr;
+        sg = R[c + 1] / rr;
+      }
+      b.cs[c] = cg;
+      b.sn[c] = sg;
+      R[c] = rr;
+      R[c + 1] = 0.0;
+      b.g[c + 1] = -sg * b.g[c];
+      b.g[c] = cg * b.g[c];
+      const double est = fabs(b.g[c + 1]);
+      s->est = est;
+      s->jj = j;
+      if (est <= s->tolabs || alpha == 0.0) {
+        s->done = 1;
+        sh_stop = 1;
+      }
+    }
+    __syncthreads();
+  } else if (threadIdx.x == 0 && alpha == 0.0) {
+    s->done = 1;
+    s->jj = 0;
+    sh_stop = 1;
   }
-  b.cs[j] = c;
-  b.sn[j] = sg;
-  R[j] = r;
-  R[j + 1] = 0.0;
-  b.g[j + 1] = -sg * b.g[j];
-  b.g[j] = c * b.g[j];
-  const double est = fabs(b.g[j + 1]);
-  s->est = est;
-  s->jj = j + 1;
-  const bool happy = !(nq2 > 0.0);
-  b.sv[j + 1] = happy ? 0.0 : 1.0 / qn;
-  if (est <= s->tolabs || happy) s->done = 1;
+  __syncthreads();
+  if (final_pass || sh_stop) {
+    if (threadIdx.x == 0) {
+      s->scal[0] = ia;
+      s->upd_mode = alpha > 0.0 ? 1 : 2;
+    }
+    return;
+  }
+  // first pass of column j
+  for (int l = threadIdx.x; l < nq; l += blockDim.x) b.hacc[l] = Bv[l] * ia;
+  if (threadIdx.x == 0) {
+    const double pw = A[2 * nq + 1], ww = A[2 * nq + 2];
+    const double ia2 = ia * ia;
+    const double hj = (pw - ab) * ia2;
+    const double ref = ww * ia2;
+    const double u2 = (ww - bb) * ia2 - hj * hj;
+    const double beta = u2 > 1e-20 * ref ? sqrt(u2) : (ref > 0.0 ? sqrt(ref) : 1.0);
+    b.hacc[nq] = hj;
+    s->scal[0] = ia;
+    s->scal[1] = ia / beta;
+    s->scal[2] = hj / beta;
+    s->scal[3] = beta;
+    s->upd_mode = 0;
+  }
 }
 
 __global__ void k_cycle_solve(SolveState* s, SmallBuffers b, int kc) {
@@ -790,9 +867,12 @@ __global__ void k_cycle_init(SolveState* s, SmallBuffers b) {
   const double rho = sqrt(s->rho2);
   for (int i = threadIdx.x; i <= b.m; i += blockDim.x) b.g[i] = i == 0 ? rho : 0.0;
   if (threadIdx.x == 0) {
-    b.sv[0] = 1.0;  // column 0 holds r / rho
+    b.sv[0] = 1.0;  // column 0 holds p_0 = r / rho
     s->done = rho > 0.0 ? 0 : 1;
     s->jj = 0;
+    s->nspmv = 0;
+    s->upd_mode = 2;
+    s->scal[3] = 1.0;
   }
 }
 
@@ -814,13 +894,8 @@ size_t hr_doubles_host(int n) { return (size_t)2 * (n + 1) * n + (size_t)3 * n *
 
 size_t harmonic_ritz_ws_doubles(int n) { return hr_doubles_host(n); }
 
-cudaError_t launch_arn_coef(SolveState* s, SmallBuffers b, int kc, int j, int pass, cudaStream_t st) {
-  k_arn_coef<<<1, 128, 0, st>>>(s, b, kc, j, pass);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_arn_finalize(SolveState* s, SmallBuffers b, int kc, int j, cudaStream_t st) {
-  k_arn_finalize<<<1, 32, 0, st>>>(s, b, kc, j);
+cudaError_t launch_dcgs_coef(SolveState* s, SmallBuffers b, int kc, int j, int final_pass, cudaStream_t st) {
+  k_dcgs_coef<<<1, 128, 0, st>>>(s, b, kc, j, final_pass);
   return cudaGetLastError();
 }
 

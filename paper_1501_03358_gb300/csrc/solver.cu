@@ -205,7 +205,7 @@ struct rk_problem {
 namespace {
 
 size_t partials_needed(const rk_problem* p, int kmax, int mcap) {
-  const int nq = kmax + mcap + 6;
+  const int nq = 2 * (kmax + mcap + 1) + 6;
   size_t a = (size_t)red_blocks(p->n) * nq;
   size_t b = (size_t)gram_blocks(p->n) * (size_t)(kmax + mcap + 1) * (size_t)std::max(kmax, 1);
   size_t c = (size_t)stencil_blocks(p->d) + 4;
@@ -271,7 +271,7 @@ int ensure_capacity(rk_problem* p, int kneed, int mneed, cudaStream_t st) {
   };
   const size_t oH = take((size_t)(m + 1) * m), oR = take((size_t)(m + 1) * m), oB = take((size_t)b.kmax * m),
                og = take(m + 1), ocs = take(m), osn = take(m), osv = take(m + 2), ohacc = take(nq),
-               odots = take(nq + 4), ocoef = take(nq), oy = take(m), ox = take(nq),
+               odots = take(2 * (size_t)nq + 8), ocoef = take(nq), oy = take(m), ox = take(nq),
                ogram = take((size_t)(kmax + m + 1) * b.kmax), oQC = take((size_t)(kmax + m + 1) * b.kmax),
                oPU = take((size_t)(kmax + m) * b.kmax), ows = take(b.hrws_doubles);
   RK_TRY(alloc_into(p->ctx, &p->small, total));
@@ -364,6 +364,44 @@ int dfupdate_launch(rk_problem* p, const float2* Q, int nq, const double* c, con
   a.skip_flag = skip;
   ProfScope ps(&p->prof, PC_UPDATE, 8.0 * (nq + 2) * (double)p->n, st);
   RK_CUDA(launch_dfupdate(a, in_df, out_df, st));
+  return RK_OK;
+}
+
+// dots = [Q^T p, Q^T w, p^T p, p^T w, w^T w] of one Arnoldi step
+int dfdots2_launch(rk_problem* p, const float2* Q, int nq, const float2* pv, const float2* w, double* out,
+                   const int* skip, cudaStream_t st) {
+  DFDots2Args a{};
+  a.n = p->n;
+  a.nq = nq;
+  a.Q = Q;
+  a.ld = p->ld;
+  a.p = pv;
+  a.w = w;
+  a.part = p->part;
+  a.counter = p->counter;
+  a.out = out;
+  a.skip_flag = skip;
+  ProfScope ps(&p->prof, PC_DOTS, 8.0 * (nq + 2) * (double)p->n, st);
+  RK_CUDA(launch_dfdots2(a, st));
+  return RK_OK;
+}
+
+// v = (p - Q a) s0 (in place), p_next = (w - Q b) s1 - v s2 (in place of w)
+int dfupdate2_launch(rk_problem* p, const float2* Q, int nq, const double* ca, const double* cb, const double* scal,
+                     float2* pv, float2* w, const int* mode, bool both, cudaStream_t st) {
+  DFUpdate2Args a{};
+  a.n = p->n;
+  a.nq = nq;
+  a.Q = Q;
+  a.ld = p->ld;
+  a.a = ca;
+  a.b = cb;
+  a.scal = scal;
+  a.p = pv;
+  a.w = w;
+  a.mode = mode;
+  ProfScope ps(&p->prof, PC_UPDATE, 8.0 * (nq + (both ? 4 : 2)) * (double)p->n, st);
+  RK_CUDA(launch_dfupdate2(a, st));
   return RK_OK;
 }
 
@@ -531,26 +569,32 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
     // v_1 = r / rho, stored double-float (line 4)
     RK_CUDA(launch_to_df(p->n, r, p->Vcol(0), &p->st->rho2, 1, 1, p->ld, p->ld, st));
     { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_cycle_init(p->st, p->sb, st)); }
+    // lines 6-11: one product, one fused inner-product pass and one update
+    // pass per step (Gram-Schmidt against [C V_j] with the second pass of
+    // each vector delayed to the next step)
     for (int j = 0; j < steps; ++j) {
-      // line 6: w = A M^{-1} v_j into the slot of v_{j+1}
       RK_TRY(opapply_launch(p, mixed, p->Vcol(j), true, p->Vcol(j + 1), true, done, st));
-      // lines 6a-10 as two block classical Gram-Schmidt passes over [C V_j]
-      const int nq = kc + j + 1;
-      RK_TRY(dfdots_launch(p, p->Cblk(kc), nq, p->Vcol(j + 1), true, p->sb.dots, done, st));
-      { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_arn_coef(p->st, p->sb, kc, j, 0, st)); }
-      RK_TRY(dfupdate_launch(p, p->Cblk(kc), nq, p->sb.coef, p->Vcol(j + 1), true, p->Vcol(j + 1), true,
-                             &p->st->nrm2[2], done, st));
-      RK_TRY(dfdots_launch(p, p->Cblk(kc), nq, p->Vcol(j + 1), true, p->sb.dots, done, st));
-      { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_arn_coef(p->st, p->sb, kc, j, 1, st)); }
-      RK_TRY(dfupdate_launch(p, p->Cblk(kc), nq, p->sb.coef, p->Vcol(j + 1), true, p->Vcol(j + 1), true,
-                             &p->st->nrm2[1], done, st, &p->st->nrm2[2], 1));
-      { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_arn_finalize(p->st, p->sb, kc, j, st)); }
+      const int nq = kc + j;
+      RK_TRY(dfdots2_launch(p, p->Cblk(kc), nq, p->Vcol(j), p->Vcol(j + 1), p->sb.dots, done, st));
+      { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_dcgs_coef(p->st, p->sb, kc, j, 0, st)); }
+      RK_TRY(dfupdate2_launch(p, p->Cblk(kc), nq, p->sb.dots, p->sb.dots + nq, p->st->scal, p->Vcol(j),
+                              p->Vcol(j + 1), &p->st->upd_mode, true, st));
+    }
+    // cycle end without convergence: second pass of the last vector
+    // (completes column steps-1; v_steps is kept for the recycle update)
+    {
+      const int nq = kc + steps;
+      RK_TRY(dfdots_launch(p, p->Cblk(kc), nq, p->Vcol(steps), true, p->sb.dots, done, st, nullptr, 1));
+      { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_dcgs_coef(p->st, p->sb, kc, steps, 1, st)); }
+      if (update && k > 0)
+        RK_TRY(dfupdate2_launch(p, p->Cblk(kc), nq, p->sb.dots, p->sb.dots, p->st->scal, p->Vcol(steps),
+                                p->Vcol(steps), &p->st->upd_mode, false, st));
     }
     RK_TRY(sync_state(p, st));
     const int jj = p->st_h->jj;
     if (jj == 0) break;
     est = p->st_h->est / bnorm;
-    matvecs += jj;
+    matvecs += p->st_h->nspmv;
     cycles += 1;
     // lines 12-13a: y, z = -B y, x <- x + M^{-1} V_j y + U z
     { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_cycle_solve(p->st, p->sb, kc, st)); }
