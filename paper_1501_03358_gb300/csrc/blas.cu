@@ -70,9 +70,9 @@ __global__ void k_fill(int64_t n, double val, double* __restrict__ dst) {
 }  // namespace
 
 int gram_blocks(int64_t n) {
-  int64_t b = (n + 4095) / 4096;
+  int64_t b = (n + 1023) / 1024;
   if (b < 1) b = 1;
-  if (b > 2 * kNumSM) b = 2 * kNumSM;
+  if (b > 4 * kNumSM) b = 4 * kNumSM;
   return (int)b;
 }
 

@@ -13,13 +13,13 @@
 #include "rk_internal.h"
 #include "rk_device.cuh"
 #include "rk_df.cuh"
+#include "rk_async.cuh"
 
 namespace rk {
 
 namespace {
 
 constexpr int kDFCols = 16;
-constexpr int kOutPT = 4;  // output columns per thread in k_dfgemm_rows
 constexpr int kWarps = kRedThreads / 32;
 
 template <typename T>
@@ -206,63 +206,163 @@ __global__ void __launch_bounds__(kRedThreads) k_dfupdate(DFUpdateArgs a) {
 }
 
 // Delayed-reorthogonalisation inner products: [Q^T p, Q^T w, p^T p, p^T w,
-// w^T w]. Grid: x = element chunks (red_blocks(n)), y = groups of kDotGroup
-// columns of Q plus one slice for the three scalars. Each thread carries
-// 2 x kDotGroup double-float chains that share every load of Q.
-__global__ void __launch_bounds__(kRedThreads) k_dfdots2(DFDots2Args a) {
+// w^T w]. Grid: x = contiguous row ranges of rpb rows (dots2_blocks(n)),
+// y = groups of kDotGroup columns of Q plus one slice for the three
+// scalars. A block streams its vectors (p, w and its kDotGroup columns)
+// through a kD2Stages-deep ring of shared-memory stages of kD2Rows rows,
+// filled by bulk asynchronous copies (one thread issues them, an mbarrier
+// per stage completes them), so the loads in flight do not depend on
+// registers. Each thread carries 2 x kDotGroup double-float chains that share
+// every value of Q. Each column group has its own completion counter: the
+// last row block of a group sums that group's partials (fixed order).
+__device__ __forceinline__ bool arrive_last_x(unsigned* counter, int* flag_smem) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned t = atomicAdd(counter, 1u);
+    *flag_smem = (t == gridDim.x - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  const bool last = *flag_smem != 0;
+  if (last) {
+    __threadfence();
+    if (threadIdx.x == 0) *counter = 0u;
+  }
+  return last;
+}
+
+constexpr int kD2Rows = 512;   // rows per stage (2 per thread)
+constexpr int kD2Stages = 3;
+constexpr int kD2Vecs = 2 + kDotGroup;
+constexpr size_t kD2Smem = (size_t)kD2Stages * kD2Vecs * kD2Rows * sizeof(float2);
+
+__global__ void __launch_bounds__(kRedThreads) k_dfdots2(DFDots2Args a, int64_t rpb) {
   if (a.skip_flag != nullptr && *a.skip_flag != 0) return;
+  extern __shared__ __align__(128) float2 d2buf[];  // [stage][vector][row]
+  __shared__ __align__(8) uint64_t full[kD2Stages];
   __shared__ float2 red[kWarps][kDFCols];
-  __shared__ int lastflag;
+  __shared__ int lastflag, abort_flag;
   const int ncols = 2 * a.nq + 3;
   const int ngroups = (a.nq + kDotGroup - 1) / kDotGroup;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double* prow = a.part + (int64_t)blockIdx.x * ncols;
-  float2 vals[kDFCols];
-  if ((int)blockIdx.y < ngroups) {
-    const int c0 = blockIdx.y * kDotGroup;
-    const int nc = min(kDotGroup, a.nq - c0);
-    float ph[kDotGroup], pl[kDotGroup], wh[kDotGroup], wl[kDotGroup];
+  const bool scal = (int)blockIdx.y >= ngroups;
+  const int c0 = blockIdx.y * kDotGroup;
+  const int nc = scal ? 0 : min(kDotGroup, a.nq - c0);
+  const int nvec = 2 + nc;  // only this group's columns are copied
+  const int64_t begin = (int64_t)blockIdx.x * rpb;
+  const int64_t end = min(a.n, begin + rpb);
+  const int nst = end > begin ? (int)((end - begin + kD2Rows - 1) / kD2Rows) : 0;
+  const float2* src[kD2Vecs];
+  src[0] = a.p;
+  src[1] = a.w;
 #pragma unroll
-    for (int q = 0; q < kDotGroup; ++q) ph[q] = pl[q] = wh[q] = wl[q] = 0.f;
-    const float2* base[kDotGroup];
+  for (int q = 0; q < kDotGroup; ++q) src[2 + q] = a.Q + (int64_t)(q < nc ? c0 + q : 0) * a.ld;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kD2Stages; ++s) mbar_init(&full[s], 1);
+    mbar_init_fence();
+    abort_flag = 0;
+  }
+  __syncthreads();
+  // stage s: rows [begin + s*kD2Rows, +rr); an odd last row is read directly
+  auto issue = [&](int s) {
+    const int slot = s % kD2Stages;
+    const int64_t r0 = begin + (int64_t)s * kD2Rows;
+    const int64_t rr = min((int64_t)kD2Rows, end - r0);
+    const unsigned bytes = (unsigned)((rr & ~(int64_t)1) * sizeof(float2));
+    mbar_arrive_expect_tx(&full[slot], bytes * nvec);
+    if (bytes)
+      for (int v = 0; v < nvec; ++v)
+        bulk_g2s(d2buf + ((int64_t)slot * kD2Vecs + v) * kD2Rows, src[v] + r0, bytes, &full[slot]);
+  };
+  if (threadIdx.x == 0)
+    for (int s = 0; s < kD2Stages && s < nst; ++s) issue(s);
+  float ph[kDotGroup], pl[kDotGroup], wh[kDotGroup], wl[kDotGroup];
 #pragma unroll
-    for (int q = 0; q < kDotGroup; ++q) base[q] = a.Q + (int64_t)(q < nc ? c0 + q : c0) * a.ld;
-    for (int64_t i = i0; i < a.n; i += stride) {
-      const float2 pv = __ldg(&a.p[i]);
-      const float2 wv = __ldg(&a.w[i]);
-      float2 v[kDotGroup];
+  for (int q = 0; q < kDotGroup; ++q) ph[q] = pl[q] = wh[q] = wl[q] = 0.f;
+  float s0h = 0.f, s0l = 0.f, s1h = 0.f, s1l = 0.f, s2h = 0.f, s2l = 0.f;
+  for (int s = 0; s < nst; ++s) {
+    const int slot = s % kD2Stages;
+    if (!mbar_wait_bounded(&full[slot], (unsigned)((s / kD2Stages) & 1))) {
+      abort_flag = 1;
+      if (a.err) atomicExch(a.err, 1);
+    }
+    __syncthreads();
+    if (abort_flag) break;
+    const int64_t r0 = begin + (int64_t)s * kD2Rows;
+    const int rr = (int)min((int64_t)kD2Rows, end - r0);
+    const float2* sb = d2buf + (int64_t)slot * kD2Vecs * kD2Rows;
+    if (rr == kD2Rows) {
+      // full stage: two rows per thread, no conditions
 #pragma unroll
-      for (int q = 0; q < kDotGroup; ++q) v[q] = __ldg(&base[q][i]);
+      for (int h = 0; h < kD2Rows / kRedThreads; ++h) {
+        const int r = threadIdx.x + h * kRedThreads;
+        const float2 pv = sb[r], wv = sb[kD2Rows + r];
+        if (scal) {
+          df_mac(s0h, s0l, pv.x, pv.y, pv.x, pv.y);
+          df_mac(s1h, s1l, pv.x, pv.y, wv.x, wv.y);
+          df_mac(s2h, s2l, wv.x, wv.y, wv.x, wv.y);
+        } else {
 #pragma unroll
-      for (int q = 0; q < kDotGroup; ++q) {
-        if (q < nc) {
-          df_mac(ph[q], pl[q], v[q].x, v[q].y, pv.x, pv.y);
-          df_mac(wh[q], wl[q], v[q].x, v[q].y, wv.x, wv.y);
+          for (int q = 0; q < kDotGroup; ++q) {
+            const float2 v = sb[(2 + q) * kD2Rows + r];
+            df_mac(ph[q], pl[q], v.x, v.y, pv.x, pv.y);
+            df_mac(wh[q], wl[q], v.x, v.y, wv.x, wv.y);
+          }
+        }
+      }
+    } else {
+      for (int r = threadIdx.x; r < rr; r += kRedThreads) {
+        const bool direct = (r == rr - 1) && (rr & 1);
+        const float2 pv = direct ? a.p[r0 + r] : sb[r];
+        const float2 wv = direct ? a.w[r0 + r] : sb[kD2Rows + r];
+        if (scal) {
+          df_mac(s0h, s0l, pv.x, pv.y, pv.x, pv.y);
+          df_mac(s1h, s1l, pv.x, pv.y, wv.x, wv.y);
+          df_mac(s2h, s2l, wv.x, wv.y, wv.x, wv.y);
+        } else {
+#pragma unroll
+          for (int q = 0; q < kDotGroup; ++q) {
+            const float2 v = direct ? src[2 + q][r0 + r] : sb[(2 + q) * kD2Rows + r];
+            df_mac(ph[q], pl[q], v.x, v.y, pv.x, pv.y);
+            df_mac(wh[q], wl[q], v.x, v.y, wv.x, wv.y);
+          }
         }
       }
     }
+    __syncthreads();  // the stage has been read: refill it
+    if (threadIdx.x == 0 && s + kD2Stages < nst) issue(s + kD2Stages);
+  }
+  double* prow = a.part + (int64_t)blockIdx.x * ncols;
+  float2 vals[kDFCols];
+  int cA, nA, cB = 0, nB = 0;  // this group's partial columns
+  if (!scal) {
 #pragma unroll
     for (int q = 0; q < kDotGroup; ++q) vals[q] = make_float2(ph[q], pl[q]);
     block_df_reduce_cols(vals, nc, red, prow + c0);
 #pragma unroll
     for (int q = 0; q < kDotGroup; ++q) vals[q] = make_float2(wh[q], wl[q]);
     block_df_reduce_cols(vals, nc, red, prow + a.nq + c0);
+    cA = c0;
+    nA = nc;
+    cB = a.nq + c0;
+    nB = nc;
   } else {
-    float s0h = 0.f, s0l = 0.f, s1h = 0.f, s1l = 0.f, s2h = 0.f, s2l = 0.f;
-    for (int64_t i = i0; i < a.n; i += stride) {
-      const float2 pv = __ldg(&a.p[i]);
-      const float2 wv = __ldg(&a.w[i]);
-      df_mac(s0h, s0l, pv.x, pv.y, pv.x, pv.y);
-      df_mac(s1h, s1l, pv.x, pv.y, wv.x, wv.y);
-      df_mac(s2h, s2l, wv.x, wv.y, wv.x, wv.y);
-    }
     vals[0] = make_float2(s0h, s0l);
     vals[1] = make_float2(s1h, s1l);
     vals[2] = make_float2(s2h, s2l);
     block_df_reduce_cols(vals, 3, red, prow + 2 * a.nq);
+    cA = 2 * a.nq;
+    nA = 3;
   }
-  if (arrive_last(a.counter, &lastflag)) reduce_partials(a.part, gridDim.x, ncols, a.out);
+  if (arrive_last_x(a.counter + blockIdx.y, &lastflag)) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int t = wid; t < nA + nB; t += kWarps) {
+      const int c = t < nA ? cA + t : cB + (t - nA);
+      double sum = 0.0;
+      for (int bx = lane; bx < (int)gridDim.x; bx += 32) sum += __ldcg(&a.part[(int64_t)bx * ncols + c]);
+      sum = warp_sum(sum);
+      if (lane == 0) a.out[c] = sum;
+    }
+  }
 }
 
 // v = (p - Q a) s0 into p; p_next = (w - Q b) s1 - v s2 into w (mode 0), or
@@ -270,17 +370,18 @@ __global__ void __launch_bounds__(kRedThreads) k_dfdots2(DFDots2Args a) {
 __global__ void __launch_bounds__(kRedThreads) k_dfupdate2(DFUpdate2Args a) {
   const int mode = *a.mode;
   if (mode != 0 && mode != 1) return;
-  extern __shared__ float2 cab[];  // -a (nq) | -b (nq)
+  extern __shared__ float2 cab[];  // -a | -b, each padded to nq8 = round_up(nq, 8) with zeros
   __shared__ float2 sc[3];
-  for (int q = threadIdx.x; q < a.nq; q += blockDim.x) {
-    cab[q] = split2(-a.a[q]);
-    cab[a.nq + q] = split2(-a.b[q]);
+  const int nq8 = (a.nq + 7) & ~7;
+  for (int q = threadIdx.x; q < nq8; q += blockDim.x) {
+    cab[q] = q < a.nq ? split2(-a.a[q]) : make_float2(0.f, 0.f);
+    cab[nq8 + q] = (q < a.nq && mode == 0) ? split2(-a.b[q]) : make_float2(0.f, 0.f);
   }
   if (threadIdx.x < 3) sc[threadIdx.x] = split2(a.scal[threadIdx.x]);
   __syncthreads();
   const float2 s0 = sc[0], s1 = sc[1], s2 = sc[2];
   const float2* ca = cab;
-  const float2* cb = cab + a.nq;
+  const float2* cb = cab + nq8;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   if (mode == 1) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
@@ -300,25 +401,18 @@ __global__ void __launch_bounds__(kRedThreads) k_dfupdate2(DFUpdate2Args a) {
     const float2 wv = a.w[i];
     float ah = pv.x, al = pv.y, bh = wv.x, bl = wv.y;
     const float2* col = a.Q + i;
-    int q = 0;
-    for (; q + 4 <= a.nq; q += 4) {
-      const float2 v0 = __ldg(col + (int64_t)(q + 0) * a.ld);
-      const float2 v1 = __ldg(col + (int64_t)(q + 1) * a.ld);
-      const float2 v2 = __ldg(col + (int64_t)(q + 2) * a.ld);
-      const float2 v3 = __ldg(col + (int64_t)(q + 3) * a.ld);
-      df_mac(ah, al, v0.x, v0.y, ca[q + 0].x, ca[q + 0].y);
-      df_mac(bh, bl, v0.x, v0.y, cb[q + 0].x, cb[q + 0].y);
-      df_mac(ah, al, v1.x, v1.y, ca[q + 1].x, ca[q + 1].y);
-      df_mac(bh, bl, v1.x, v1.y, cb[q + 1].x, cb[q + 1].y);
-      df_mac(ah, al, v2.x, v2.y, ca[q + 2].x, ca[q + 2].y);
-      df_mac(bh, bl, v2.x, v2.y, cb[q + 2].x, cb[q + 2].y);
-      df_mac(ah, al, v3.x, v3.y, ca[q + 3].x, ca[q + 3].y);
-      df_mac(bh, bl, v3.x, v3.y, cb[q + 3].x, cb[q + 3].y);
-    }
-    for (; q < a.nq; ++q) {
-      const float2 v = __ldg(col + (int64_t)q * a.ld);
-      df_mac(ah, al, v.x, v.y, ca[q].x, ca[q].y);
-      df_mac(bh, bl, v.x, v.y, cb[q].x, cb[q].y);
+    // chunks of 8 columns, the last one predicated (no scalar tail: every
+    // load of a row is issued before its multiply-adds)
+    for (int q = 0; q < a.nq; q += 8) {
+      float2 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        v[u] = q + u < a.nq ? __ldg(col + (int64_t)(q + u) * a.ld) : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        df_mac(ah, al, v[u].x, v[u].y, ca[q + u].x, ca[q + u].y);
+        df_mac(bh, bl, v[u].x, v[u].y, cb[q + u].x, cb[q + u].y);
+      }
     }
     const float2 vf = df_mul(make_float2(ah, al), s0);
     const float2 pn = df_add(df_mul(make_float2(bh, bl), s1), df_neg(df_mul(vf, s2)));
@@ -327,68 +421,83 @@ __global__ void __launch_bounds__(kRedThreads) k_dfupdate2(DFUpdate2Args a) {
   }
 }
 
-// Row-tiled X P with X = [A (na DF cols), Bm (nb DF cols) .* bscale]; out is
-// DF (in place safe per tile) or FP64 (optionally accumulated).
-template <typename OT>
-__global__ void __launch_bounds__(256) k_dfgemm_rows(DFGemmArgs a, int tr) {
-  extern __shared__ float2 xs[];  // X: np * tr | P: np * nc | scale: tr
+// Row-tiled X P (the solution and recycle updates, lines 13-13a and 14a)
+// with X = [A (na DF cols), diag(bscale) Bm (nb DF cols)] and P (np x nc,
+// FP64, column-major). P is held in shared memory as DF, transposed and
+// zero-padded to ncg * CB columns. A block of ncg * tr threads takes a tile
+// of tr rows; thread (g, r) computes row r for the CB output columns
+// g*CB .. g*CB+CB-1, so one shared-memory load of X feeds CB independent
+// double-float chains and the inner loop has no conditions. The row scale
+// is applied once per output: acc = bscale_i * sum_{B} X P, then the A
+// columns are added. out is DF (in place safe: a tile is read completely
+// before it is written) or FP64 (optionally accumulated).
+template <typename OT, int CB>
+__global__ void __launch_bounds__(256) k_dfgemm2(DFGemmArgs a, int tr, int ncp) {
+  extern __shared__ float2 xs[];  // X: np * tr | PT: np * ncp | SC: tr
   const int np = a.na + a.nb;
   float2* X = xs;
-  float2* P = xs + (int64_t)np * tr;
-  float2* SC = P + (int64_t)np * a.nc;
-  for (int t = threadIdx.x; t < np * a.nc; t += blockDim.x) P[t] = split2(a.P[t]);
+  float2* PT = xs + (int64_t)np * tr;
+  float2* SC = PT + (int64_t)np * ncp;
+  const int nthr = blockDim.x;
+  for (int t = threadIdx.x; t < np * ncp; t += nthr) {
+    const int q = t / ncp, c = t - q * ncp;
+    PT[t] = c < a.nc ? split2(a.P[(int64_t)c * np + q]) : make_float2(0.f, 0.f);
+  }
+  const int g = threadIdx.x / tr, r = threadIdx.x - g * tr;
+  const int c0 = g * CB;
   const int64_t ntiles = (a.n + tr - 1) / tr;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t r0 = tile * tr;
-    __syncthreads();
-    if (a.bscale) {
-      for (int r = threadIdx.x; r < tr; r += blockDim.x) {
-        const int64_t i = r0 + r;
-        SC[r] = i < a.n ? split2(__ldg(&a.bscale[i])) : make_float2(0.f, 0.f);
-      }
-      __syncthreads();
-    }
-    for (int t = threadIdx.x; t < np * tr; t += blockDim.x) {
-      const int q = t / tr, r = t - q * tr;
-      const int64_t i = r0 + r;
-      if (i < a.n) {
-        const float2* src = q < a.na ? &a.A[(int64_t)q * a.lda + i] : &a.Bm[(int64_t)(q - a.na) * a.ldb + i];
-        cp_async8(&X[t], src);
-      } else {
+    __syncthreads();  // previous tile fully consumed (and written, for in-place DF)
+    for (int t = threadIdx.x; t < np * tr; t += nthr) {
+      const int q = t / tr, rr = t - q * tr;
+      const int64_t i = r0 + rr;
+      const float2* src = q < a.na ? a.A + (int64_t)q * a.lda : a.Bm + (int64_t)(q - a.na) * a.ldb;
+      if (i < a.n)
+        cp_async8(&X[t], src + i);
+      else
         X[t] = make_float2(0.f, 0.f);
+    }
+    if (a.bscale) {
+      for (int rr = threadIdx.x; rr < tr; rr += nthr) {
+        const int64_t i = r0 + rr;
+        SC[rr] = i < a.n ? split2(__ldg(&a.bscale[i])) : make_float2(0.f, 0.f);
       }
     }
     cp_async_wait_all();
-    if (a.bscale && a.nb > 0) {
-      __syncthreads();
-      for (int t = a.na * tr + threadIdx.x; t < np * tr; t += blockDim.x) X[t] = df_mul(X[t], SC[t % tr]);
-    }
     __syncthreads();
-    // each thread: one row, kOutPT output columns (independent chains that
-    // share every X load)
-    const int ncg = (a.nc + kOutPT - 1) / kOutPT;
-    for (int t = threadIdx.x; t < ncg * tr; t += blockDim.x) {
-      const int cg = t / tr, r = t - cg * tr;
-      const int64_t i = r0 + r;
-      if (i >= a.n) continue;
-      const int c0 = cg * kOutPT;
-      float sh[kOutPT], sl[kOutPT];
+    float sh[CB], sl[CB];
 #pragma unroll
-      for (int u = 0; u < kOutPT; ++u) sh[u] = sl[u] = 0.f;
-      for (int q = 0; q < np; ++q) {
-        const float2 xv = X[q * tr + r];
+    for (int u = 0; u < CB; ++u) sh[u] = sl[u] = 0.f;
+    const float2* pt = PT + c0;
+    // B columns first (they carry the row scale), then the scale, then A
+    for (int q = a.na; q < np; ++q) {
+      const float2 xv = X[q * tr + r];
+      const float2* pq = pt + (int64_t)q * ncp;
 #pragma unroll
-        for (int u = 0; u < kOutPT; ++u) {
-          if (c0 + u < a.nc) {
-            const float2 pv = P[(int64_t)(c0 + u) * np + q];
-            df_mac(sh[u], sl[u], xv.x, xv.y, pv.x, pv.y);
-          }
-        }
+      for (int u = 0; u < CB; ++u) df_mac(sh[u], sl[u], xv.x, xv.y, pq[u].x, pq[u].y);
+    }
+    if (a.bscale && a.nb > 0) {
+      const float2 sc = SC[r];
+#pragma unroll
+      for (int u = 0; u < CB; ++u) {
+        const float2 v = df_mul(make_float2(sh[u], sl[u]), sc);
+        sh[u] = v.x;
+        sl[u] = v.y;
       }
+    }
+    for (int q = 0; q < a.na; ++q) {
+      const float2 xv = X[q * tr + r];
+      const float2* pq = pt + (int64_t)q * ncp;
 #pragma unroll
-      for (int u = 0; u < kOutPT; ++u) {
+      for (int u = 0; u < CB; ++u) df_mac(sh[u], sl[u], xv.x, xv.y, pq[u].x, pq[u].y);
+    }
+    const int64_t i = r0 + r;
+    if (i < a.n) {
+#pragma unroll
+      for (int u = 0; u < CB; ++u) {
         const int c = c0 + u;
-        if (c >= a.nc) continue;
+        if (c >= a.nc) break;
         if constexpr (std::is_same<OT, float2>::value) {
           ((float2*)a.out)[(int64_t)c * a.ldo + i] = make_float2(sh[u], sl[u]);
         } else {
@@ -401,95 +510,168 @@ __global__ void __launch_bounds__(256) k_dfgemm_rows(DFGemmArgs a, int tr) {
   }
 }
 
-constexpr int kDFGramPPT = 8;
-
-// out[q + l*np] = sum_i X_q[i] * (d[i] * U_l[i]), X = [A, Bm] DF, U DF.
-__global__ void __launch_bounds__(256) k_dfgram(DFGramArgs a, int pair0, int npairs_pass, int tr) {
-  extern __shared__ float2 gs[];
-  __shared__ int lastflag;
+// One output column (x updates): out_i (+)= sum_{q<na} A_q[i] p_q
+// + bscale_i sum_{q>=na} B_q[i] p_q, streamed straight from global memory
+// (each value is used once), coefficients in shared memory as DF.
+template <typename OT>
+__global__ void __launch_bounds__(kRedThreads) k_dfgemv(DFGemmArgs a) {
+  extern __shared__ float2 pv[];
   const int np = a.na + a.nb;
-  float2* X = gs;                       // np * tr
-  float2* Y = gs + (int64_t)np * tr;    // nu * tr
-  float2* D = Y + (int64_t)a.nu * tr;   // tr
-  float sh[kDFGramPPT], sl[kDFGramPPT];
-  int qq[kDFGramPPT], ll[kDFGramPPT];
-#pragma unroll
-  for (int t = 0; t < kDFGramPPT; ++t) {
-    sh[t] = sl[t] = 0.f;
-    const int pr = pair0 + threadIdx.x + t * blockDim.x;
-    qq[t] = pr % np;
-    ll[t] = pr / np;
-  }
-  const int pend = pair0 + npairs_pass;
-  const int64_t ntiles = (a.n + tr - 1) / tr;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t r0 = tile * tr;
-    __syncthreads();
-    if (a.d != nullptr) {
-      for (int r = threadIdx.x; r < tr; r += blockDim.x) {
-        const int64_t i = r0 + r;
-        D[r] = i < a.n ? split2(__ldg(&a.d[i])) : make_float2(0.f, 0.f);
-      }
-      __syncthreads();
+  for (int q = threadIdx.x; q < np; q += blockDim.x) pv[q] = split2(a.P[q]);
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    float bh = 0.f, bl = 0.f, ah = 0.f, al = 0.f;
+    int q = 0;
+    for (; q + 4 <= a.nb; q += 4) {
+      const float2 v0 = __ldg(a.Bm + (int64_t)(q + 0) * a.ldb + i);
+      const float2 v1 = __ldg(a.Bm + (int64_t)(q + 1) * a.ldb + i);
+      const float2 v2 = __ldg(a.Bm + (int64_t)(q + 2) * a.ldb + i);
+      const float2 v3 = __ldg(a.Bm + (int64_t)(q + 3) * a.ldb + i);
+      df_mac(bh, bl, v0.x, v0.y, pv[a.na + q + 0].x, pv[a.na + q + 0].y);
+      df_mac(bh, bl, v1.x, v1.y, pv[a.na + q + 1].x, pv[a.na + q + 1].y);
+      df_mac(bh, bl, v2.x, v2.y, pv[a.na + q + 2].x, pv[a.na + q + 2].y);
+      df_mac(bh, bl, v3.x, v3.y, pv[a.na + q + 3].x, pv[a.na + q + 3].y);
     }
-    // tiles stored row-major (X[r][q], Y[r][l]): in the product loop the
-    // lanes of a warp read consecutive q (and mostly one l), so shared-memory
-    // accesses are conflict-free; global reads stay coalesced along r
-    for (int t = threadIdx.x; t < np * tr; t += blockDim.x) {
-      const int q = t / tr, r = t - q * tr;
-      const int64_t i = r0 + r;
-      float2* dst = &X[r * np + q];
-      if (i < a.n)
-        cp_async8(dst, q < a.na ? &a.A[(int64_t)q * a.lda + i] : &a.Bm[(int64_t)(q - a.na) * a.ldb + i]);
-      else
-        *dst = make_float2(0.f, 0.f);
+    for (; q < a.nb; ++q) {
+      const float2 v = __ldg(a.Bm + (int64_t)q * a.ldb + i);
+      df_mac(bh, bl, v.x, v.y, pv[a.na + q].x, pv[a.na + q].y);
     }
-    for (int t = threadIdx.x; t < a.nu * tr; t += blockDim.x) {
-      const int l = t / tr, r = t - l * tr;
-      const int64_t i = r0 + r;
-      float2* dst = &Y[r * a.nu + l];
-      if (i < a.n)
-        cp_async8(dst, &a.U[(int64_t)l * a.ldu + i]);
-      else
-        *dst = make_float2(0.f, 0.f);
+    q = 0;
+    for (; q + 4 <= a.na; q += 4) {
+      const float2 v0 = __ldg(a.A + (int64_t)(q + 0) * a.lda + i);
+      const float2 v1 = __ldg(a.A + (int64_t)(q + 1) * a.lda + i);
+      const float2 v2 = __ldg(a.A + (int64_t)(q + 2) * a.lda + i);
+      const float2 v3 = __ldg(a.A + (int64_t)(q + 3) * a.lda + i);
+      df_mac(ah, al, v0.x, v0.y, pv[q + 0].x, pv[q + 0].y);
+      df_mac(ah, al, v1.x, v1.y, pv[q + 1].x, pv[q + 1].y);
+      df_mac(ah, al, v2.x, v2.y, pv[q + 2].x, pv[q + 2].y);
+      df_mac(ah, al, v3.x, v3.y, pv[q + 3].x, pv[q + 3].y);
     }
-    cp_async_wait_all();
-    if (a.d != nullptr) {
-      __syncthreads();
-      for (int t = threadIdx.x; t < a.nu * tr; t += blockDim.x) Y[t] = df_mul(Y[t], D[t / a.nu]);
+    for (; q < a.na; ++q) {
+      const float2 v = __ldg(a.A + (int64_t)q * a.lda + i);
+      df_mac(ah, al, v.x, v.y, pv[q].x, pv[q].y);
     }
-    __syncthreads();
-    // the thread's pairs advance together, row by row: kDFGramPPT
-    // independent double-float chains per thread
-    for (int r = 0; r < tr; ++r) {
-#pragma unroll
-      for (int t = 0; t < kDFGramPPT; ++t) {
-        const int pr = pair0 + threadIdx.x + t * blockDim.x;
-        if (pr < pend) {
-          const float2 xv = X[r * np + qq[t]], yv = Y[r * a.nu + ll[t]];
-          df_mac(sh[t], sl[t], xv.x, xv.y, yv.x, yv.y);
-        }
-      }
-    }
-  }
-  const int total = np * a.nu;
-#pragma unroll
-  for (int t = 0; t < kDFGramPPT; ++t) {
-    const int pr = pair0 + threadIdx.x + t * blockDim.x;
-    if (pr < pend) a.part[(int64_t)blockIdx.x * total + pr] = (double)sh[t] + (double)sl[t];
-  }
-  if (arrive_last(a.counter, &lastflag)) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int c = pair0 + wid; c < pend; c += nw) {
-      double s = 0.0;
-      for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(&a.part[(int64_t)b * total + c]);
-      s = warp_sum(s);
-      if (lane == 0) a.out[c] = s;
+    float2 bsum = make_float2(bh, bl);
+    if (a.bscale && a.nb > 0) bsum = df_mul(bsum, split2(__ldg(&a.bscale[i])));
+    const float2 r = df_add(make_float2(ah, al), bsum);
+    if constexpr (std::is_same<OT, float2>::value) {
+      ((float2*)a.out)[i] = r;
+    } else {
+      double* o = (double*)a.out + i;
+      const double sv = df_to_double(r);
+      *o = a.accum ? *o + sv : sv;
     }
   }
 }
 
-// dst (DF) = src (FP64) * scale; scale = 1, *scale_ptr, or 1/sqrt(*scale_ptr)
+// Gram blocks out[q + l*np] = sum_i X_q[i] d[i] U_l[i] (the inner products
+// of the harmonic Ritz problem, line 14a). Each thread owns a 4 x 4 set of
+// (q, l) pairs (strided by the number of sets) and a slice of the tile's rows (rows r = slice, slice + ns,
+// ...); per row it reads 4 X and 4 Y values for 16 double-float
+// multiply-adds. Tiles are row-major with odd strides (8-byte elements, so
+// the row-by-row tile stores of a warp fall in distinct banks). The
+// slices are summed in shared memory and each block writes its partials;
+// a separate kernel reduces them over blocks in a fixed order.
+constexpr int kGramTR = 64;
+__global__ void __launch_bounds__(256) k_dfgram2(DFGramArgs a, int ob0, int nob, int ns, int sx, int sy) {
+  extern __shared__ float2 gs2[];
+  const int np = a.na + a.nb;
+  const int nbq = (np + 3) / 4;
+  float2* X = gs2;                          // kGramTR * sx
+  float2* Y = X + (int64_t)kGramTR * sx;    // kGramTR * sy
+  float2* D = Y + (int64_t)kGramTR * sy;    // kGramTR
+  const int slice = threadIdx.x / nob, ob = threadIdx.x - slice * nob;
+  const bool active = slice < ns;
+  const int obg = ob0 + ob;
+  const int nbl = (a.nu + 3) / 4;
+  // the thread's pairs: q = qi + nbq*u, l = li + nbl*v (u, v < 4); adjacent
+  // threads take adjacent q, so a warp's X reads are conflict-free
+  const int qi = obg % nbq, li = obg / nbq;
+  float sh[16], sl[16];
+#pragma unroll
+  for (int t = 0; t < 16; ++t) sh[t] = sl[t] = 0.f;
+  const int64_t ntiles = (a.n + kGramTR - 1) / kGramTR;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t r0 = tile * kGramTR;
+    __syncthreads();
+    for (int t = threadIdx.x; t < np * kGramTR; t += blockDim.x) {
+      const int q = t / kGramTR, r = t % kGramTR;
+      const float2* src = q < a.na ? a.A + (int64_t)q * a.lda : a.Bm + (int64_t)(q - a.na) * a.ldb;
+      const int64_t i = r0 + r;
+      if (i < a.n)
+        cp_async8(&X[r * sx + q], src + i);
+      else
+        X[r * sx + q] = make_float2(0.f, 0.f);
+    }
+    for (int t = threadIdx.x; t < a.nu * kGramTR; t += blockDim.x) {
+      const int l = t / kGramTR, r = t % kGramTR;
+      const int64_t i = r0 + r;
+      if (i < a.n)
+        cp_async8(&Y[r * sy + l], a.U + (int64_t)l * a.ldu + i);
+      else
+        Y[r * sy + l] = make_float2(0.f, 0.f);
+    }
+    for (int r = threadIdx.x; r < kGramTR; r += blockDim.x) {
+      const int64_t i = r0 + r;
+      D[r] = (a.d != nullptr && i < a.n) ? split2(__ldg(&a.d[i])) : make_float2(1.f, 0.f);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (a.d != nullptr) {
+      for (int t = threadIdx.x; t < kGramTR * a.nu; t += blockDim.x) {
+        const int r = t / a.nu, l = t - r * a.nu;
+        Y[r * sy + l] = df_mul(Y[r * sy + l], D[r]);
+      }
+      __syncthreads();
+    }
+    if (active) {
+      for (int r = slice; r < kGramTR; r += ns) {
+        float2 xv[4], yv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          xv[u] = X[r * sx + qi + nbq * u];
+          yv[u] = Y[r * sy + li + nbl * u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) df_mac(sh[u * 4 + v], sl[u * 4 + v], xv[u].x, xv[u].y, yv[v].x, yv[v].y);
+      }
+    }
+  }
+  // sum the slices: reuse the tile storage as [ns][nob][16] DF values
+  __syncthreads();
+  float2* red = gs2;
+  if (active) {
+#pragma unroll
+    for (int t = 0; t < 16; ++t) red[((int64_t)slice * nob + ob) * 16 + t] = make_float2(sh[t], sl[t]);
+  }
+  __syncthreads();
+  const int total = np * a.nu;
+  for (int t = threadIdx.x; t < nob * 16; t += blockDim.x) {
+    const int o = t / 16, e = t - o * 16;
+    const int og = ob0 + o;
+    const int q = og % nbq + nbq * (e / 4), l = og / nbq + ((a.nu + 3) / 4) * (e % 4);
+    if (q >= np || l >= a.nu) continue;
+    float2 s = red[(int64_t)o * 16 + e];
+    for (int sl2 = 1; sl2 < ns; ++sl2) s = df_add(s, red[((int64_t)sl2 * nob + o) * 16 + e]);
+    a.part[(int64_t)blockIdx.x * total + q + (int64_t)l * np] = df_to_double(s);
+  }
+}
+
+// out[c] = sum_b part[b * ncols + c], one warp per column, fixed order.
+__global__ void __launch_bounds__(256) k_reduce_cols(const double* __restrict__ part, int nblocks, int ncols,
+                                                     double* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (c >= ncols) return;
+  double s = 0.0;
+  for (int b = lane; b < nblocks; b += 32) s += part[(int64_t)b * ncols + c];
+  s = warp_sum(s);
+  if (lane == 0) out[c] = s;
+}
+
 __global__ void __launch_bounds__(kRedThreads) k_to_df(int64_t n, const double* __restrict__ src,
                                                        float2* __restrict__ dst, const double* scale_ptr,
                                                        int scale_rsqrt, int ncols, int64_t lds, int64_t ldd) {
@@ -518,7 +700,6 @@ __global__ void __launch_bounds__(kRedThreads) k_axpy_scaled(int64_t n, const do
     x[i] = fma(__ldg(&s[i]), __ldg(&v[i]), x[i]);
 }
 
-int dfgemm_tile_rows(int np) { return np <= 96 ? 64 : 32; }
 
 }  // namespace
 
@@ -548,60 +729,123 @@ cudaError_t launch_dfupdate(const DFUpdateArgs& a, bool in_df, bool out_df, cuda
   return cudaGetLastError();
 }
 
+int dots2_blocks(int64_t n) {
+  int64_t b = (n + 16 * kD2Rows - 1) / (16 * kD2Rows);
+  if (b < 1) b = 1;
+  if (b > kNumSM) b = kNumSM;
+  return (int)b;
+}
+
 cudaError_t launch_dfdots2(const DFDots2Args& a, cudaStream_t st) {
-  const dim3 grid(red_blocks(a.n), (a.nq + kDotGroup - 1) / kDotGroup + 1);
-  k_dfdots2<<<grid, kRedThreads, 0, st>>>(a);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_dfdots2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kD2Smem);
+    attr = true;
+  }
+  const int xb = dots2_blocks(a.n);
+  const int64_t per = (a.n + xb - 1) / xb;
+  const int64_t rpb = (per + kD2Rows - 1) / kD2Rows * kD2Rows;  // even: 16-byte aligned stages
+  const dim3 grid(xb, (a.nq + kDotGroup - 1) / kDotGroup + 1);
+  k_dfdots2<<<grid, kRedThreads, kD2Smem, st>>>(a, rpb);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dfupdate2(const DFUpdate2Args& a, cudaStream_t st) {
-  const size_t smem = (size_t)(a.nq > 0 ? 2 * a.nq : 1) * sizeof(float2);
+  const size_t smem = (size_t)(a.nq > 0 ? 2 * ((a.nq + 7) & ~7) : 1) * sizeof(float2);
   k_dfupdate2<<<red_blocks(a.n), kRedThreads, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+template <typename OT, int CB>
+static cudaError_t gemm2_go(const DFGemmArgs& a, int tr, int ncp, int threads, size_t smem, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_dfgemm2<OT, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    attr = true;
+  }
+  const int64_t ntiles = (a.n + tr - 1) / tr;
+  const int64_t cap = (int64_t)kNumSM * 4;
+  const int blocks = (int)(ntiles < cap ? ntiles : cap);
+  k_dfgemm2<OT, CB><<<blocks, threads, smem, st>>>(a, tr, ncp);
+  return cudaGetLastError();
+}
+
+// widths of the column groups that are compiled
+constexpr int kGemmCB[] = {2, 4, 6, 8, 10, 12, 16};
+
+template <typename OT>
+static cudaError_t gemm2_pick(const DFGemmArgs& a, int cb, int tr, int ncp, int threads, size_t smem,
+                              cudaStream_t st) {
+  switch (cb) {
+    case 2: return gemm2_go<OT, 2>(a, tr, ncp, threads, smem, st);
+    case 4: return gemm2_go<OT, 4>(a, tr, ncp, threads, smem, st);
+    case 6: return gemm2_go<OT, 6>(a, tr, ncp, threads, smem, st);
+    case 8: return gemm2_go<OT, 8>(a, tr, ncp, threads, smem, st);
+    case 10: return gemm2_go<OT, 10>(a, tr, ncp, threads, smem, st);
+    case 12: return gemm2_go<OT, 12>(a, tr, ncp, threads, smem, st);
+    default: return gemm2_go<OT, 16>(a, tr, ncp, threads, smem, st);
+  }
 }
 
 cudaError_t launch_dfgemm_rows(const DFGemmArgs& a, bool out_df, cudaStream_t st) {
   const int np = a.na + a.nb;
   if (np == 0 || a.nc == 0) return cudaSuccess;
-  const int tr = dfgemm_tile_rows(np);
-  const size_t smem = ((size_t)np * tr + (size_t)np * a.nc + tr) * sizeof(float2);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_dfgemm_rows<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    cudaFuncSetAttribute(k_dfgemm_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    attr = true;
+  if (a.nc == 1) {
+    const size_t smem = (size_t)np * sizeof(float2);
+    if (out_df)
+      k_dfgemv<float2><<<red_blocks(a.n), kRedThreads, smem, st>>>(a);
+    else
+      k_dfgemv<double><<<red_blocks(a.n), kRedThreads, smem, st>>>(a);
+    return cudaGetLastError();
   }
-  if (smem > 220 * 1024) return cudaErrorInvalidValue;
-  const int64_t ntiles = (a.n + tr - 1) / tr;
-  const int blocks = (int)(ntiles < 4 * kNumSM ? ntiles : 4 * kNumSM);
-  if (out_df)
-    k_dfgemm_rows<float2><<<blocks, 256, smem, st>>>(a, tr);
-  else
-    k_dfgemm_rows<double><<<blocks, 256, smem, st>>>(a, tr);
-  return cudaGetLastError();
+  // column groups: a power of two with at most 16 columns per group; the
+  // group width rounded up to a compiled one (P padded with zero columns)
+  int ncg = 1;
+  while (ncg * 16 < a.nc) ncg *= 2;
+  int cb = (a.nc + ncg - 1) / ncg;
+  for (int w : kGemmCB)
+    if (w >= cb) {
+      cb = w;
+      break;
+    }
+  const int ncp = ncg * cb;
+  int tr = 256 / ncg;
+  if (tr > 128) tr = 128;
+  while (tr > 8 && ((size_t)np * tr + (size_t)np * ncp + tr) * sizeof(float2) > 200 * 1024) tr /= 2;
+  const size_t smem = ((size_t)np * tr + (size_t)np * ncp + tr) * sizeof(float2);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  const int threads = ncg * tr;
+  return out_df ? gemm2_pick<float2>(a, cb, tr, ncp, threads, smem, st)
+                : gemm2_pick<double>(a, cb, tr, ncp, threads, smem, st);
 }
 
 cudaError_t launch_dfgram(const DFGramArgs& a, cudaStream_t st) {
   const int np = a.na + a.nb;
   const int total = np * a.nu;
   if (total == 0) return cudaSuccess;
-  const int tr = 32;
-  const size_t smem = ((size_t)np * tr + (size_t)a.nu * tr + tr) * sizeof(float2);
+  const int nbq = (np + 3) / 4, nbl = (a.nu + 3) / 4;
+  const int nblk = nbq * nbl;
+  const int sx = ((np + 3) / 4) * 4 + 1, sy = ((a.nu + 3) / 4) * 4 + 1;
+  const size_t tiles = ((size_t)kGramTR * (sx + sy) + kGramTR) * sizeof(float2);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_dfgram, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(k_dfgram2, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     attr = true;
   }
-  if (smem > 220 * 1024) return cudaErrorInvalidValue;
-  const int per_pass = 256 * kDFGramPPT;
   const int blocks = gram_blocks(a.n);
-  for (int p0 = 0; p0 < total; p0 += per_pass) {
-    const int npp = total - p0 < per_pass ? total - p0 : per_pass;
-    k_dfgram<<<blocks, 256, smem, st>>>(a, p0, npp, tr);
+  for (int ob0 = 0; ob0 < nblk; ob0 += 256) {
+    const int nob = nblk - ob0 < 256 ? nblk - ob0 : 256;
+    int ns = 256 / nob;
+    if (ns > 8) ns = 8;
+    const size_t red = (size_t)ns * nob * 16 * sizeof(float2);
+    const size_t smem = tiles > red ? tiles : red;
+    if (smem > 220 * 1024) return cudaErrorInvalidValue;
+    k_dfgram2<<<blocks, 256, smem, st>>>(a, ob0, nob, ns, sx, sy);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  return cudaSuccess;
+  k_reduce_cols<<<(total + 7) / 8, 256, 0, st>>>(a.part, blocks, total, a.out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_to_df(int64_t n, const double* src, float2* dst, const double* scale_ptr, int scale_rsqrt,

@@ -9,6 +9,11 @@ namespace rk {
 constexpr int kNumSM = 152;          // GB300
 constexpr int kRedThreads = 256;     // block size of the streaming reductions
 constexpr int kMaxRedBlocks = 4 * kNumSM;
+// Completion counters of a problem: [0, kGroupCounters) for single-counter
+// reductions, [kGroupCounters, kCounters) one per column group of the
+// fused Arnoldi inner products.
+constexpr int kGroupCounters = 64;
+constexpr int kCounters = 1024;
 
 // Stencil tile: one thread per (x, y) column of a 32 x 8 tile, marching in z.
 constexpr int kTX = 32;
@@ -118,12 +123,15 @@ struct DFDots2Args {
   int64_t ld;
   const float2* p;
   const float2* w;
-  double* part;       // red_blocks(n) * (2 nq + 3)
-  unsigned* counter;
+  double* part;       // dots2_blocks(n) * (2 nq + 3)
+  unsigned* counter;  // one per column group (ceil(nq / 4) + 1 of them)
   double* out;        // 2 nq + 3
   const int* skip_flag;
+  int* err;           // set nonzero if a bounded wait gives up
 };
 cudaError_t launch_dfdots2(const DFDots2Args& a, cudaStream_t st);
+// x-extent of its grid (a function of n alone)
+int dots2_blocks(int64_t n);
 
 // The update of the same step, one pass over Q:
 //   v      = (p - Q a) * scal[0]                      (final basis vector, into p)

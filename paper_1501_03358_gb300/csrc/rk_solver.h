@@ -23,6 +23,8 @@ struct SolveState {
   int bic_stop;      // rBiCGStab: skip further kernels this batch
   int upd_mode;      // Arnoldi update pass: 0 v_j and p_{j+1}, 1 v_j only, 2 none
   int nspmv;         // products A M^{-1} p taken in the current cycle
+  int dev_err;       // nonzero: a bounded device wait gave up (kernel id)
+  int pad_;
 };
 
 struct SmallBuffers {

@@ -188,7 +188,7 @@ struct HRWork {
   double* v;   // n + 1
   double* wr;  // n
   double* wi;  // n
-  int* sel;    // n  (selected start index; -1 end)
+  int* sel;    // n + 1 (selected start index; -1 end), then n flags
 };
 
 __device__ HRWork hr_carve(double* base, int n) {
@@ -554,35 +554,41 @@ __device__ void hr_core(HRWork w, int n, int k, double* QC, int ldqc, double* PU
     return;
   }
   // ---- 5. selection: eigenvalues mu of largest modulus (theta = 1/mu smallest).
+  //         |mu|^2 and Re theta = Re mu / |mu|^2 once per eigenvalue (in
+  //         parallel, into X as scratch), then a serial pick of the best
+  //         remaining entity by comparisons only; a complex pair is one entity
+  //         (its first member, wi > 0) and is taken only if both fit.
+  double* mag2 = w.X;
+  double* reth = w.X + n;
+  int* used = w.sel + n + 1;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double m2 = w.wr[i] * w.wr[i] + w.wi[i] * w.wi[i];
+    mag2[i] = m2;
+    reth[i] = m2 > 0.0 ? w.wr[i] / m2 : 0.0;
+    used[i] = (w.wi[i] < 0.0 || !(m2 > 0.0)) ? 1 : 0;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     int taken = 0, ns = 0;
-    // mark: use wi to find blocks; sel holds the start index of each chosen entity
-    for (int pass = 0; pass < n; ++pass) {
+    const double tie_hi = 1.0 + 2e-12, tie_lo = 1.0 - 2e-12;
+    while (taken < k) {
       int best = -1;
-      double bmag = -1.0, bre = 0.0;
+      double bm = -1.0, br = 0.0;
       for (int i = 0; i < n; ++i) {
-        if (w.wi[i] < 0.0) continue;  // second member of a pair is represented by the first
-        bool used = false;
-        for (int t = 0; t < ns; ++t)
-          if (w.sel[t] == i) used = true;
-        if (used) continue;
-        const double mag = hypot(w.wr[i], w.wi[i]);
-        if (!(mag > 0.0)) continue;
-        const double ret = w.wr[i] / (mag * mag);  // Re theta
-        const bool better = mag > bmag * (1.0 + 1e-12) ||
-                            (mag >= bmag * (1.0 - 1e-12) && ret < bre);
-        if (best < 0 || better) {
+        if (used[i]) continue;
+        const double m2 = mag2[i], rt = reth[i];
+        if (best < 0 || m2 > bm * tie_hi || (m2 >= bm * tie_lo && rt < br)) {
           best = i;
-          bmag = mag;
-          bre = ret;
+          bm = m2;
+          br = rt;
         }
       }
       if (best < 0) break;
       const int need = w.wi[best] > 0.0 ? 2 : 1;
       if (taken + need > k) break;
+      used[best] = 1;
       w.sel[ns++] = best;
       taken += need;
-      if (taken == k) break;
     }
     w.sel[ns] = -1;
     sh_knew = taken;
@@ -888,7 +894,7 @@ __global__ void k_set_scalar(SolveState* s, int which) {
   if (which == 0) s->done = 0;
 }
 
-size_t hr_doubles_host(int n) { return (size_t)2 * (n + 1) * n + (size_t)3 * n * n + 5 * (size_t)n + 8; }
+size_t hr_doubles_host(int n) { return (size_t)2 * (n + 1) * n + (size_t)3 * n * n + 6 * (size_t)n + 8; }
 
 }  // namespace
 

@@ -302,6 +302,11 @@ int sync_state(rk_problem* p, cudaStream_t st) {
   RK_CUDA(cudaMemcpyAsync(p->st_h, p->st, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
   RK_CUDA(cudaStreamSynchronize(st));
   p->prof.flush();
+  if (p->st_h->dev_err != 0) {
+    const int e = p->st_h->dev_err;
+    RK_CUDA(cudaMemsetAsync(&p->st->dev_err, 0, sizeof(int), st));
+    return fail(RK_E_DEVICE_TIMEOUT, "a bounded device wait gave up (code " + std::to_string(e) + ")");
+  }
   return RK_OK;
 }
 
@@ -378,9 +383,10 @@ int dfdots2_launch(rk_problem* p, const float2* Q, int nq, const float2* pv, con
   a.p = pv;
   a.w = w;
   a.part = p->part;
-  a.counter = p->counter;
+  a.counter = p->counter + kGroupCounters;
   a.out = out;
   a.skip_flag = skip;
+  a.err = &p->st->dev_err;
   ProfScope ps(&p->prof, PC_DOTS, 8.0 * (nq + 2) * (double)p->n, st);
   RK_CUDA(launch_dfdots2(a, st));
   return RK_OK;
@@ -839,7 +845,7 @@ int rk_create_problem(rk_context* ctx, const rk_grid* grid, int32_t S, const dou
   int r;
   if ((r = alloc_into(ctx, &p->coef, (size_t)S * p->n)) != RK_OK) return cleanup(r);
   if ((r = alloc_into(ctx, &p->dinv, (size_t)p->ld)) != RK_OK) return cleanup(r);
-  if ((r = alloc_into(ctx, &p->counter, 64)) != RK_OK) return cleanup(r);
+  if ((r = alloc_into(ctx, &p->counter, kCounters)) != RK_OK) return cleanup(r);
   if ((r = alloc_into(ctx, &p->st, 1)) != RK_OK) return cleanup(r);
   if ((r = alloc_into(ctx, &p->bs, 1)) != RK_OK) return cleanup(r);
   if ((r = alloc_into(ctx, &p->istat, 16)) != RK_OK) return cleanup(r);
@@ -849,7 +855,7 @@ int rk_create_problem(rk_context* ctx, const rk_grid* grid, int32_t S, const dou
     return cleanup(fail(RK_E_OOM, "pinned host allocation failed"));
   }
   if (cudaMemcpyAsync(p->coef, coef, sizeof(double) * S * p->n, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
-      cudaMemsetAsync(p->counter, 0, 64 * sizeof(unsigned), st) != cudaSuccess ||
+      cudaMemsetAsync(p->counter, 0, kCounters * sizeof(unsigned), st) != cudaSuccess ||
       cudaMemsetAsync(p->st, 0, sizeof(SolveState), st) != cudaSuccess ||
       cudaMemsetAsync(p->bs, 0, sizeof(BicgScalars), st) != cudaSuccess)
     return cleanup(fail(RK_E_CUDA, "copying the coefficients failed"));
