@@ -100,4 +100,44 @@ __device__ __forceinline__ float2 df_warp_sum(float2 v) {
   return v;
 }
 
+// ---- scalar double-float helpers for the small dense eigenproblem ----
+
+__device__ __forceinline__ float2 df_make(double d) {
+  const df v = df_from_double(d);
+  return make_float2(v.hi, v.lo);
+}
+
+__device__ __forceinline__ float2 df_sub(float2 a, float2 b) { return df_add(a, df_neg(b)); }
+
+// c + a * b, normalised
+__device__ __forceinline__ float2 df_fma(float2 a, float2 b, float2 c) {
+  float sh = c.x, sl = c.y;
+  df_mac(sh, sl, a.x, a.y, b.x, b.y);
+  return make_float2(sh, sl);
+}
+
+// a / b (three-term long division: q1 + q2 + q3, each from the FP32
+// quotient of the current remainder)
+__device__ __forceinline__ float2 df_div(float2 a, float2 b) {
+  const float q1 = __fdiv_rn(a.x, b.x);
+  float2 r = df_fma(make_float2(-q1, 0.f), b, a);
+  const float q2 = __fdiv_rn(r.x, b.x);
+  r = df_fma(make_float2(-q2, 0.f), b, r);
+  const float q3 = __fdiv_rn(r.x, b.x);
+  const df s = df_fast_two_sum(q1, q2);
+  return df_add(make_float2(s.hi, s.lo), make_float2(q3, 0.f));
+}
+
+// sqrt(a) for a >= 0: FP32 root, then one Newton correction in DF
+__device__ __forceinline__ float2 df_sqrt(float2 a) {
+  if (!(a.x > 0.f)) return make_float2(0.f, 0.f);
+  const float s = __fsqrt_rn(a.x);
+  const float2 e = df_fma(make_float2(-s, 0.f), make_float2(s, 0.f), a);  // a - s^2
+  const float t = __fdiv_rn(e.x, 2.f * s);
+  const df r = df_fast_two_sum(s, t);
+  return make_float2(r.hi, r.lo);
+}
+
+__device__ __forceinline__ float2 df_absv(float2 a) { return a.x < 0.f ? df_neg(a) : a; }
+
 }  // namespace rk

@@ -15,6 +15,7 @@
 #include <cmath>
 #include "rk_solver.h"
 #include "rk_device.cuh"
+#include "rk_df.cuh"
 
 namespace rk {
 
@@ -257,22 +258,6 @@ __device__ void apply_right(double* A, int ld, int r0, int r1, int c0, int len, 
   }
 }
 
-// 3- or 2-vector Householder computed by one thread (no block sync).
-__device__ void house_small(double x, double y, double z, int len, double* v, double* tau) {
-  const double nrm = len == 3 ? sqrt(x * x + y * y + z * z) : sqrt(x * x + y * y);
-  if (nrm == 0.0 || (y == 0.0 && (len == 2 || z == 0.0))) {
-    v[0] = 1.0; v[1] = 0.0; v[2] = 0.0;
-    *tau = 0.0;
-    return;
-  }
-  const double beta = x <= 0.0 ? nrm : -nrm;
-  const double v0 = x - beta;
-  v[0] = 1.0;
-  v[1] = y / v0;
-  v[2] = len == 3 ? z / v0 : 0.0;
-  *tau = (beta - x) / beta;
-}
-
 // Complex helpers
 struct cplx { double re, im; };
 __device__ __forceinline__ cplx cmul(cplx a, cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
@@ -283,6 +268,260 @@ __device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
   return {(a.re * br + a.im * bi) / (d * s), (a.im * br - a.re * bi) / (d * s)};
 }
 
+// 3- or 2-vector Householder reflector in double-float (one thread):
+// (I - tau v v^T) [x y z]^T = [beta 0 0]^T with v = [1, v1, v2].
+// The vector is first scaled by a power of two (exact) so that its largest
+// component is in [0.5, 1): the bulge entries become tiny as the iteration
+// converges, and their squares would leave the FP32 exponent range.
+__device__ void house_small_df(float2 x, float2 y, float2 z, int len, float2* v, float2* tau) {
+  const bool tail_zero = y.x == 0.f && (len == 2 || z.x == 0.f);
+  const float mx = fmaxf(fabsf(x.x), fmaxf(fabsf(y.x), len == 3 ? fabsf(z.x) : 0.f));
+  v[0] = make_float2(1.f, 0.f);
+  if (!(mx > 0.f) || tail_zero) {
+    v[1] = v[2] = make_float2(0.f, 0.f);
+    *tau = make_float2(0.f, 0.f);
+    return;
+  }
+  int ex;
+  frexpf(mx, &ex);
+  const float sc = ldexpf(1.f, -ex);
+  x = make_float2(x.x * sc, x.y * sc);
+  y = make_float2(y.x * sc, y.y * sc);
+  z = make_float2(z.x * sc, z.y * sc);
+  float2 ss = df_mul(x, x);
+  ss = df_fma(y, y, ss);
+  if (len == 3) ss = df_fma(z, z, ss);
+  const float2 nrm = df_sqrt(ss);
+  const float2 beta = x.x <= 0.f ? nrm : df_neg(nrm);
+  const float2 v0 = df_sub(x, beta);
+  const float2 rv0 = df_div(make_float2(1.f, 0.f), v0);
+  v[1] = df_mul(y, rv0);
+  v[2] = len == 3 ? df_mul(z, rv0) : make_float2(0.f, 0.f);
+  *tau = df_div(df_sub(beta, x), beta);
+}
+
+// h <- (I - tau v v^T) h for a 3-vector (v0 = 1) or a 2-vector (v2 = 0)
+__device__ __forceinline__ void refl3_df(float2& h0, float2& h1, float2& h2, float2 v1, float2 v2, float2 tau) {
+  float2 t = df_fma(v1, h1, h0);
+  t = df_fma(v2, h2, t);
+  const float2 ww = df_mul(tau, t);
+  h0 = df_sub(h0, ww);
+  h1 = df_fma(df_neg(ww), v1, h1);
+  h2 = df_fma(df_neg(ww), v2, h2);
+}
+__device__ __forceinline__ void refl2_df(float2& h0, float2& h1, float2 v1, float2 tau) {
+  const float2 ww = df_mul(tau, df_fma(v1, h1, h0));
+  h0 = df_sub(h0, ww);
+  h1 = df_fma(df_neg(ww), v1, h1);
+}
+
+// Francis double-shift QR (implicit, bulge chasing with 3x3 reflectors;
+// exceptional shifts at iterations 10 and 20 of one eigenvalue; deflation
+// when |h_{l,l-1}| <= 2^-47 (|h_{l-1,l-1}| + |h_ll|); 2x2 blocks with real
+// eigenvalues split by a rotation) on Hd (n x n Hessenberg, DF), with the
+// transformations accumulated into Zd. Block-wide; eigenvalues to wr, wi
+// (FP64). On more than 40 n iterations *sfail is set.
+__device__ void francis_df(float2* Hd, float2* Zd, int n, double* wr, double* wi, float hn, int* su, int* sl,
+                           int* siter, int* stotal, int* sfail) {
+  __shared__ float2 v3[3], tau3, rot[2];
+  __shared__ int c_real;
+  const float eps = 7.105427357601002e-15f;  // 2^-47
+  const int tid = threadIdx.x;
+#define HD(i, j) Hd[(i) + (int64_t)(j) * n]
+#define ZD(i, j) Zd[(i) + (int64_t)(j) * n]
+  while (true) {
+    __syncthreads();
+    const int u = *su;
+    if (u < 0 || *sfail) break;
+    if (tid == 0) {
+      int l = u;
+      while (l > 0) {
+        float sc = fabsf(HD(l - 1, l - 1).x) + fabsf(HD(l, l).x);
+        if (sc == 0.f) sc = hn;
+        if (fabsf(HD(l, l - 1).x) <= eps * sc) break;
+        --l;
+      }
+      if (l > 0) HD(l, l - 1) = make_float2(0.f, 0.f);
+      *sl = l;
+    }
+    __syncthreads();
+    const int l = *sl;
+    if (l == u) {  // 1 x 1 block
+      if (tid == 0) {
+        wr[u] = df_to_double(HD(u, u));
+        wi[u] = 0.0;
+        *su = u - 1;
+        *siter = 0;
+      }
+      continue;
+    }
+    if (l == u - 1) {  // 2 x 2 block: split if real (FP64 rotation), record the pair if complex
+      if (tid == 0) {
+        const double a = df_to_double(HD(u - 1, u - 1)), bb = df_to_double(HD(u - 1, u));
+        const double c = df_to_double(HD(u, u - 1)), d = df_to_double(HD(u, u));
+        const double p = 0.5 * (a - d);
+        const double disc = p * p + bb * c;
+        if (disc >= 0.0) {
+          const double sq = sqrt(disc);
+          const double zz = p + (p >= 0.0 ? sq : -sq);
+          double cs = 1.0, sn = 0.0;
+          if (zz != 0.0 || c != 0.0) {
+            const double r = hypot(zz, c);
+            cs = zz / r;
+            sn = c / r;
+          }
+          rot[0] = df_make(cs);
+          rot[1] = df_make(sn);
+          c_real = 1;
+        } else {
+          c_real = 0;
+          wr[u - 1] = 0.5 * (a + d);
+          wr[u] = 0.5 * (a + d);
+          wi[u - 1] = sqrt(-disc);
+          wi[u] = -sqrt(-disc);
+        }
+      }
+      __syncthreads();
+      if (c_real) {
+        const float2 cs = rot[0], sn = rot[1];
+        for (int j = u - 1 + tid; j < n; j += blockDim.x) {
+          const float2 h1 = HD(u - 1, j), h2 = HD(u, j);
+          HD(u - 1, j) = df_fma(sn, h2, df_mul(cs, h1));
+          HD(u, j) = df_fma(cs, h2, df_neg(df_mul(sn, h1)));
+        }
+        __syncthreads();
+        for (int i = tid; i <= u; i += blockDim.x) {
+          const float2 h1 = HD(i, u - 1), h2 = HD(i, u);
+          HD(i, u - 1) = df_fma(sn, h2, df_mul(cs, h1));
+          HD(i, u) = df_fma(cs, h2, df_neg(df_mul(sn, h1)));
+        }
+        for (int i = tid; i < n; i += blockDim.x) {
+          const float2 z1 = ZD(i, u - 1), z2 = ZD(i, u);
+          ZD(i, u - 1) = df_fma(sn, z2, df_mul(cs, z1));
+          ZD(i, u) = df_fma(cs, z2, df_neg(df_mul(sn, z1)));
+        }
+        __syncthreads();
+        if (tid == 0) {
+          HD(u, u - 1) = make_float2(0.f, 0.f);
+          wr[u - 1] = df_to_double(HD(u - 1, u - 1));
+          wr[u] = df_to_double(HD(u, u));
+          wi[u - 1] = 0.0;
+          wi[u] = 0.0;
+        }
+      }
+      if (tid == 0) {
+        *su = u - 2;
+        *siter = 0;
+      }
+      continue;
+    }
+    // Francis double-shift step on the active window [l, u]
+    if (tid == 0) {
+      *siter += 1;
+      *stotal += 1;
+      if (*stotal > 40 * n) *sfail = 1;
+      float2 sh, th;
+      if (*siter == 10 || *siter == 20) {
+        const float2 ww = df_add(df_absv(HD(u, u - 1)), u >= 2 ? df_absv(HD(u - 1, u - 2)) : make_float2(0.f, 0.f));
+        sh = df_mul(make_float2(1.5f, 0.f), ww);
+        th = df_mul(ww, ww);
+      } else {
+        sh = df_add(HD(u - 1, u - 1), HD(u, u));
+        th = df_sub(df_mul(HD(u - 1, u - 1), HD(u, u)), df_mul(HD(u - 1, u), HD(u, u - 1)));
+      }
+      const float2 hll = HD(l, l), h1l = HD(l + 1, l);
+      float2 fx = df_fma(hll, hll, df_mul(HD(l, l + 1), h1l));
+      fx = df_add(df_fma(df_neg(sh), hll, fx), th);
+      const float2 fy = df_mul(h1l, df_sub(df_add(hll, HD(l + 1, l + 1)), sh));
+      const float2 fz = (l + 2 <= u) ? df_mul(h1l, HD(l + 2, l + 1)) : make_float2(0.f, 0.f);
+      house_small_df(fx, fy, fz, 3, v3, &tau3);
+    }
+    __syncthreads();
+    if (*sfail) break;
+    for (int kk = l; kk <= u - 2; ++kk) {
+      const float2 tau = tau3, v1 = v3[1], v2 = v3[2];
+      if (tau.x != 0.f) {
+        const int q = kk > l ? kk - 1 : l;
+        for (int j = q + tid; j < n; j += blockDim.x) {
+          float2 h0 = HD(kk, j), h1 = HD(kk + 1, j), h2 = HD(kk + 2, j);
+          refl3_df(h0, h1, h2, v1, v2, tau);
+          HD(kk, j) = h0;
+          HD(kk + 1, j) = h1;
+          HD(kk + 2, j) = h2;
+        }
+        __syncthreads();
+        const int rmaxi = kk + 3 < u ? kk + 3 : u;
+        if (tid < 64) {
+          for (int i = tid; i <= rmaxi; i += 64) {
+            float2 h0 = HD(i, kk), h1 = HD(i, kk + 1), h2 = HD(i, kk + 2);
+            refl3_df(h0, h1, h2, v1, v2, tau);
+            HD(i, kk) = h0;
+            HD(i, kk + 1) = h1;
+            HD(i, kk + 2) = h2;
+          }
+        } else {
+          for (int i = tid - 64; i < n; i += (int)blockDim.x - 64) {
+            float2 z0 = ZD(i, kk), z1 = ZD(i, kk + 1), z2 = ZD(i, kk + 2);
+            refl3_df(z0, z1, z2, v1, v2, tau);
+            ZD(i, kk) = z0;
+            ZD(i, kk + 1) = z1;
+            ZD(i, kk + 2) = z2;
+          }
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        const float2 fx = HD(kk + 1, kk), fy = HD(kk + 2, kk);
+        if (kk < u - 2) {
+          house_small_df(fx, fy, HD(kk + 3, kk), 3, v3, &tau3);
+        } else {
+          house_small_df(fx, fy, make_float2(0.f, 0.f), 2, v3, &tau3);
+        }
+      }
+      __syncthreads();
+    }
+    // final 2-vector reflector on rows / columns u-1, u (computed above)
+    {
+      const float2 tau = tau3, v1 = v3[1];
+      if (tau.x != 0.f) {
+        const int q = u - 2 >= l ? u - 2 : l;
+        for (int j = q + tid; j < n; j += blockDim.x) {
+          float2 h0 = HD(u - 1, j), h1 = HD(u, j);
+          refl2_df(h0, h1, v1, tau);
+          HD(u - 1, j) = h0;
+          HD(u, j) = h1;
+        }
+        __syncthreads();
+        if (tid < 64) {
+          for (int i = tid; i <= u; i += 64) {
+            float2 h0 = HD(i, u - 1), h1 = HD(i, u);
+            refl2_df(h0, h1, v1, tau);
+            HD(i, u - 1) = h0;
+            HD(i, u) = h1;
+          }
+        } else {
+          for (int i = tid - 64; i < n; i += (int)blockDim.x - 64) {
+            float2 z0 = ZD(i, u - 1), z1 = ZD(i, u);
+            refl2_df(z0, z1, v1, tau);
+            ZD(i, u - 1) = z0;
+            ZD(i, u) = z1;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // entries below the subdiagonal are zero by construction
+    if (tid == 0) {
+      for (int i = l + 2; i <= u; ++i) {
+        HD(i, i - 2) = make_float2(0.f, 0.f);
+        if (i >= l + 3) HD(i, i - 3) = make_float2(0.f, 0.f);
+      }
+    }
+  }
+#undef HD
+#undef ZD
+}
+
 // Core: G, F already in w.G, w.F (ld n+1). Outputs QC (ld ldqc, n+1 rows),
 // PU (ld ldpu, n rows), *knew_out, *status_out (0 ok).
 __device__ void hr_core(HRWork w, int n, int k, double* QC, int ldqc, double* PU, int ldpu, int* knew_out,
@@ -290,8 +529,6 @@ __device__ void hr_core(HRWork w, int n, int k, double* QC, int ldqc, double* PU
   __shared__ double red[32];
   __shared__ double sh_beta, sh_tau;
   __shared__ int sh_u, sh_l, sh_iter, sh_total, sh_fail, sh_knew;
-  __shared__ double sh_v3[3];
-  __shared__ double sh_tau3;
   const int ldg = n + 1;
   const double eps = 2.220446049250313e-16;
 
@@ -342,14 +579,34 @@ __device__ void hr_core(HRWork w, int n, int k, double* QC, int ldqc, double* PU
     for (int i = threadIdx.x; i < len; i += blockDim.x) x[i] = i == 0 ? sh_beta : 0.0;
     __syncthreads();
   }
-  // ---- 4. Francis double-shift QR to real Schur form (T in M, vectors in Z).
+  // ---- 4. Real Schur form (T in M, Schur vectors in Z) by Francis
+  //         double-shift QR. The iteration is a long chain of small
+  //         dependent steps, and on this GPU an FP64 instruction costs a warp
+  //         ~64 cycles even with one lane active, so the sweep runs in
+  //         double-float arithmetic on the FP32 pipe (about 48 significant
+  //         bits): H and Z are converted once into the F and M workspaces,
+  //         the Schur vectors are updated by threads 64.. (other warps) in
+  //         the same phase as the column updates of H, and T and Z are
+  //         converted back to FP64 at the end.
   double hnorm = 0.0;
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) hnorm = fmax(hnorm, fabs(w.M[t]));
-  {
-    // block max via sum of squares of maxima is not needed; use sum of |.| bound
-    double s = block_sum(hnorm, red);
-    hnorm = s;
+  hnorm = block_sum(hnorm, red);  // a bound on max |h_ij|, used only for zero tests
+  // H is scaled by a power of two (exact) so that its entries stay well inside
+  // the FP32 exponent range of double-float numbers; T and the eigenvalues
+  // are scaled back afterwards.
+  __shared__ double sh_scale;
+  if (threadIdx.x == 0) {
+    int ex = 0;
+    if (hnorm > 0.0 && isfinite(hnorm)) frexp(hnorm, &ex);
+    sh_scale = ldexp(1.0, -ex);
   }
+  __syncthreads();
+  const double hscale = sh_scale;
+  float2* Hd = reinterpret_cast<float2*>(w.F);
+  float2* Zd = reinterpret_cast<float2*>(w.M);
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) Hd[t] = df_make(w.M[t] * hscale);
+  __syncthreads();
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) Zd[t] = df_make(w.Z[t]);
   if (threadIdx.x == 0) {
     sh_u = n - 1;
     sh_iter = 0;
@@ -357,197 +614,17 @@ __device__ void hr_core(HRWork w, int n, int k, double* QC, int ldqc, double* PU
     sh_fail = 0;
   }
   __syncthreads();
+  francis_df(Hd, Zd, n, w.wr, w.wi, (float)(hnorm * hscale), &sh_u, &sh_l, &sh_iter, &sh_total, &sh_fail);
+  __syncthreads();
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) w.Z[t] = df_to_double(Zd[t]);
+  __syncthreads();
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) w.M[t] = df_to_double(Hd[t]) / hscale;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    w.wr[t] /= hscale;
+    w.wi[t] /= hscale;
+  }
   double* H = w.M;
 #define HH(i, j) H[(i) + (int64_t)(j) * n]
-  while (true) {
-    __syncthreads();
-    const int u = sh_u;
-    if (u < 0 || sh_fail) break;
-    if (threadIdx.x == 0) {
-      int l = u;
-      while (l > 0) {
-        double s = fabs(HH(l - 1, l - 1)) + fabs(HH(l, l));
-        if (s == 0.0) s = hnorm;
-        if (fabs(HH(l, l - 1)) <= eps * s) break;
-        --l;
-      }
-      if (l > 0) HH(l, l - 1) = 0.0;
-      sh_l = l;
-    }
-    __syncthreads();
-    const int l = sh_l;
-    if (l == u) {  // 1 x 1 block
-      if (threadIdx.x == 0) {
-        w.wr[u] = HH(u, u);
-        w.wi[u] = 0.0;
-        sh_u = u - 1;
-        sh_iter = 0;
-      }
-      continue;
-    }
-    if (l == u - 1) {  // 2 x 2 block: split if real, record the pair if complex
-      __shared__ double c_cs, c_sn;
-      __shared__ int c_real;
-      if (threadIdx.x == 0) {
-        const double a = HH(u - 1, u - 1), bb = HH(u - 1, u), c = HH(u, u - 1), d = HH(u, u);
-        const double p = 0.5 * (a - d);
-        const double disc = p * p + bb * c;
-        if (disc >= 0.0) {
-          const double sq = sqrt(disc);
-          const double zz = p + (p >= 0.0 ? sq : -sq);
-          double cs = 1.0, sn = 0.0;
-          if (zz != 0.0 || c != 0.0) {
-            const double r = hypot(zz, c);
-            cs = zz / r;
-            sn = c / r;
-          }
-          c_cs = cs;
-          c_sn = sn;
-          c_real = 1;
-        } else {
-          c_real = 0;
-          w.wr[u - 1] = 0.5 * (a + d);
-          w.wr[u] = 0.5 * (a + d);
-          w.wi[u - 1] = sqrt(-disc);
-          w.wi[u] = -sqrt(-disc);
-        }
-      }
-      __syncthreads();
-      if (c_real) {
-        const double cs = c_cs, sn = c_sn;
-        for (int j = u - 1 + threadIdx.x; j < n; j += blockDim.x) {
-          const double h1 = HH(u - 1, j), h2 = HH(u, j);
-          HH(u - 1, j) = cs * h1 + sn * h2;
-          HH(u, j) = -sn * h1 + cs * h2;
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i <= u; i += blockDim.x) {
-          const double h1 = HH(i, u - 1), h2 = HH(i, u);
-          HH(i, u - 1) = cs * h1 + sn * h2;
-          HH(i, u) = -sn * h1 + cs * h2;
-        }
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-          const double z1 = w.Z[i + (int64_t)(u - 1) * n], z2 = w.Z[i + (int64_t)u * n];
-          w.Z[i + (int64_t)(u - 1) * n] = cs * z1 + sn * z2;
-          w.Z[i + (int64_t)u * n] = -sn * z1 + cs * z2;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          HH(u, u - 1) = 0.0;
-          w.wr[u - 1] = HH(u - 1, u - 1);
-          w.wr[u] = HH(u, u);
-          w.wi[u - 1] = 0.0;
-          w.wi[u] = 0.0;
-        }
-      }
-      if (threadIdx.x == 0) {
-        sh_u = u - 2;
-        sh_iter = 0;
-      }
-      continue;
-    }
-    // Francis double-shift step on the active window [l, u]
-    __shared__ double fx, fy, fz;
-    if (threadIdx.x == 0) {
-      sh_iter += 1;
-      sh_total += 1;
-      if (sh_total > 40 * n) sh_fail = 1;
-      double s, t;
-      if (sh_iter == 10 || sh_iter == 20) {
-        const double ww = fabs(HH(u, u - 1)) + (u >= 2 ? fabs(HH(u - 1, u - 2)) : 0.0);
-        s = 1.5 * ww;
-        t = ww * ww;
-      } else {
-        s = HH(u - 1, u - 1) + HH(u, u);
-        t = HH(u - 1, u - 1) * HH(u, u) - HH(u - 1, u) * HH(u, u - 1);
-      }
-      fx = HH(l, l) * HH(l, l) + HH(l, l + 1) * HH(l + 1, l) - s * HH(l, l) + t;
-      fy = HH(l + 1, l) * (HH(l, l) + HH(l + 1, l + 1) - s);
-      fz = (l + 2 <= u) ? HH(l + 1, l) * HH(l + 2, l + 1) : 0.0;
-    }
-    __syncthreads();
-    if (sh_fail) break;
-    for (int kk = l; kk <= u - 2; ++kk) {
-      if (threadIdx.x == 0) house_small(fx, fy, fz, 3, sh_v3, &sh_tau3);
-      __syncthreads();
-      const double tau = sh_tau3;
-      const double v1 = sh_v3[1], v2 = sh_v3[2];
-      if (tau != 0.0) {
-        const int q = kk > l ? kk - 1 : l;
-        for (int j = q + threadIdx.x; j < n; j += blockDim.x) {
-          const double h0 = HH(kk, j), h1 = HH(kk + 1, j), h2 = HH(kk + 2, j);
-          const double ww = tau * (h0 + v1 * h1 + v2 * h2);
-          HH(kk, j) = h0 - ww;
-          HH(kk + 1, j) = h1 - ww * v1;
-          HH(kk + 2, j) = h2 - ww * v2;
-        }
-        __syncthreads();
-        const int rmaxi = kk + 3 < u ? kk + 3 : u;
-        for (int i = threadIdx.x; i <= rmaxi; i += blockDim.x) {
-          const double h0 = HH(i, kk), h1 = HH(i, kk + 1), h2 = HH(i, kk + 2);
-          const double ww = tau * (h0 + v1 * h1 + v2 * h2);
-          HH(i, kk) = h0 - ww;
-          HH(i, kk + 1) = h1 - ww * v1;
-          HH(i, kk + 2) = h2 - ww * v2;
-        }
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-          double* z0 = w.Z + i + (int64_t)kk * n;
-          const double h0 = z0[0], h1 = z0[n], h2 = z0[2 * (int64_t)n];
-          const double ww = tau * (h0 + v1 * h1 + v2 * h2);
-          z0[0] = h0 - ww;
-          z0[n] = h1 - ww * v1;
-          z0[2 * (int64_t)n] = h2 - ww * v2;
-        }
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        fx = HH(kk + 1, kk);
-        fy = HH(kk + 2, kk);
-        fz = kk < u - 2 ? HH(kk + 3, kk) : 0.0;
-        if (kk > l) {
-          // entries below the bulge are zero by construction
-        }
-      }
-      __syncthreads();
-    }
-    // final 2-vector reflector on rows u-1, u
-    if (threadIdx.x == 0) house_small(fx, fy, 0.0, 2, sh_v3, &sh_tau3);
-    __syncthreads();
-    {
-      const double tau = sh_tau3;
-      const double v1 = sh_v3[1];
-      if (tau != 0.0) {
-        const int q = u - 2 >= l ? u - 2 : l;
-        for (int j = q + threadIdx.x; j < n; j += blockDim.x) {
-          const double h0 = HH(u - 1, j), h1 = HH(u, j);
-          const double ww = tau * (h0 + v1 * h1);
-          HH(u - 1, j) = h0 - ww;
-          HH(u, j) = h1 - ww * v1;
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i <= u; i += blockDim.x) {
-          const double h0 = HH(i, u - 1), h1 = HH(i, u);
-          const double ww = tau * (h0 + v1 * h1);
-          HH(i, u - 1) = h0 - ww;
-          HH(i, u) = h1 - ww * v1;
-        }
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-          const double h0 = w.Z[i + (int64_t)(u - 1) * n], h1 = w.Z[i + (int64_t)u * n];
-          const double ww = tau * (h0 + v1 * h1);
-          w.Z[i + (int64_t)(u - 1) * n] = h0 - ww;
-          w.Z[i + (int64_t)u * n] = h1 - ww * v1;
-        }
-      }
-    }
-    __syncthreads();
-    // clean the entries below the subdiagonal created by rounding
-    if (threadIdx.x == 0) {
-      for (int i = l + 2; i <= u; ++i) {
-        HH(i, i - 2) = 0.0;
-        if (i >= l + 3) HH(i, i - 3) = 0.0;
-      }
-    }
-  }
   __syncthreads();
   if (sh_fail) {
     if (threadIdx.x == 0) { *status_out = 2; *knew_out = 0; }
