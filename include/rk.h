@@ -180,6 +180,57 @@ int rk_dots(rk_context* ctx, int64_t n, int32_t nq, const double* Q, int64_t ld,
             double* out, void* stream);
 
 /*
+ * Solve n independent problems, one right-hand side each (one time step of
+ * n sequences; the batched and serving workloads of the recycling solver).
+ * Equivalent to calling rk_solve(problems[i], b[i], x[i], &params[i],
+ * &infos[i]) for every i, except that the solves run concurrently: a pool of
+ * nthreads host threads (<= 0: min(n, 16)), each driving its own CUDA
+ * stream, takes problems from a shared queue. problems, b, x, params, infos:
+ * host arrays of n entries (b[i], x[i] device pointers as in rk_solve). The
+ * batch starts after the work already queued on `stream`, and work queued on
+ * `stream` afterwards runs after the whole batch; the call returns when every
+ * solve has finished (infos valid). A problem may appear only once per batch
+ * (RK_E_INVALID otherwise); distinct problems share nothing on the device,
+ * so each solve gives exactly the result it gives alone. Returns RK_OK if
+ * every solve returned RK_OK, else the status of the first failing one (in
+ * batch order); every infos[i].status holds its own status. The paper
+ * solves one system at a time; this entry point has no counterpart there.
+ */
+int rk_solve_batch(rk_problem* const* problems, const double* const* b, double* const* x, int32_t n,
+                   const rk_solve_params* params, rk_solve_info* infos, int32_t nthreads, void* stream);
+
+/*
+ * Device bytes currently held by a problem (operator copies, basis and
+ * recycle storage, workspace), for memory budgets. No counterpart in the
+ * paper.
+ */
+int rk_problem_memory(const rk_problem* p, int64_t* device_bytes);
+
+/*
+ * Free a problem's basis, recycle and solver workspace, keeping the operator
+ * (memory pressure: a serving process evicting an idle problem). The recycle
+ * space is dropped: save it first with rk_get_recycle and restore it with
+ * rk_set_recycle. The next solve reallocates what it needs. Synchronises
+ * `stream` first. No counterpart in the paper.
+ */
+int rk_problem_release(rk_problem* p, void* stream);
+
+/*
+ * Exact spill and restore of the recycle space (U and C as stored, in
+ * double-float): an opaque blob of rk_recycle_bytes(p) bytes in device
+ * memory (a 32-byte header, then the columns). rk_export_recycle writes it
+ * into buf (cap bytes, RK_E_INVALID if smaller); rk_import_recycle makes it
+ * the problem's recycle space (the problem must have the same N; RK_E_INVALID
+ * otherwise). Unlike rk_get_recycle / rk_set_recycle, whose FP64 copy rounds
+ * a double-float pair, the round trip is bit-exact, so a problem spilled
+ * from device memory and restored continues with identical iterates.
+ * Both synchronise `stream`. No counterpart in the paper.
+ */
+int rk_recycle_bytes(const rk_problem* p, int64_t* bytes);
+int rk_export_recycle(const rk_problem* p, void* buf, int64_t cap, void* stream);
+int rk_import_recycle(rk_problem* p, const void* buf, int64_t bytes, void* stream);
+
+/*
  * Opt-in kernel timing of the solves of a problem: CUDA events on the solve's
  * stream around every launch, summed per kernel class ("spmv", "residual",
  * "dots", "update", "gemm_rows", "gram", "small", "bicg", "harmonic_ritz") with the class's

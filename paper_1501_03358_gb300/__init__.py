@@ -6,7 +6,7 @@ rGCROT -> rBiCGStab hybrid of arXiv 1501.03358, as a C-ABI CUDA library
 Importing the package is cheap; ``Context``/``Problem`` load librk.so on
 first use and raise if it has not been built (there is no CPU fallback)."""
 
-__all__ = ["Context", "Problem", "build"]
+__all__ = ["Context", "Problem", "solve_batch", "build"]
 
 
 def build(force: bool = False) -> str:
@@ -15,7 +15,7 @@ def build(force: bool = False) -> str:
 
 
 def __getattr__(name):
-    if name in ("Context", "Problem"):
+    if name in ("Context", "Problem", "solve_batch"):
         from . import solver
         return getattr(solver, name)
     raise AttributeError(name)

@@ -737,11 +737,12 @@ int dots2_blocks(int64_t n) {
 }
 
 cudaError_t launch_dfdots2(const DFDots2Args& a, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
+  // one-time attribute setup (thread-safe static initialisation)
+  static const bool attr = [] {
     cudaFuncSetAttribute(k_dfdots2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kD2Smem);
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   const int xb = dots2_blocks(a.n);
   const int64_t per = (a.n + xb - 1) / xb;
   const int64_t rpb = (per + kD2Rows - 1) / kD2Rows * kD2Rows;  // even: 16-byte aligned stages
@@ -758,11 +759,12 @@ cudaError_t launch_dfupdate2(const DFUpdate2Args& a, cudaStream_t st) {
 
 template <typename OT, int CB>
 static cudaError_t gemm2_go(const DFGemmArgs& a, int tr, int ncp, int threads, size_t smem, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
+  // one-time attribute setup (thread-safe static initialisation)
+  static const bool attr = [] {
     cudaFuncSetAttribute(k_dfgemm2<OT, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   const int64_t ntiles = (a.n + tr - 1) / tr;
   const int64_t cap = (int64_t)kNumSM * 4;
   const int blocks = (int)(ntiles < cap ? ntiles : cap);
@@ -827,11 +829,12 @@ cudaError_t launch_dfgram(const DFGramArgs& a, cudaStream_t st) {
   const int nblk = nbq * nbl;
   const int sx = ((np + 3) / 4) * 4 + 1, sy = ((a.nu + 3) / 4) * 4 + 1;
   const size_t tiles = ((size_t)kGramTR * (sx + sy) + kGramTR) * sizeof(float2);
-  static bool attr = false;
-  if (!attr) {
+  // one-time attribute setup (thread-safe static initialisation)
+  static const bool attr = [] {
     cudaFuncSetAttribute(k_dfgram2, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   const int blocks = gram_blocks(a.n);
   for (int ob0 = 0; ob0 < nblk; ob0 += 256) {
     const int nob = nblk - ob0 < 256 ? nblk - ob0 : 256;

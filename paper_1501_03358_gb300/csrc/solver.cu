@@ -19,6 +19,8 @@
 #include <string>
 #include <vector>
 #include <algorithm>
+#include <atomic>
+#include <thread>
 
 #include "rk.h"
 #include "rk_internal.h"
@@ -193,6 +195,7 @@ struct rk_problem {
   double* eta = nullptr;          // eta1, eta2, xi, fold coefficients, k x k scratch
   double* part = nullptr;
   size_t part_n = 0;
+  size_t small_n = 0, eta_n = 0;  // doubles held by small / eta
   unsigned* counter = nullptr;
   int* istat = nullptr;           // device ints for small kernels
   int solves = 0;
@@ -216,6 +219,8 @@ size_t partials_needed(const rk_problem* p, int kmax, int mcap) {
 void free_small(rk_problem* p) {
   dev_free(p->ctx, p->small);
   p->small = nullptr;
+  p->small_n = 0;
+  p->eta_n = 0;
   dev_free(p->ctx, p->eta);
   p->eta = nullptr;
   dev_free(p->ctx, p->part);
@@ -275,6 +280,7 @@ int ensure_capacity(rk_problem* p, int kneed, int mneed, cudaStream_t st) {
                ogram = take((size_t)(kmax + m + 1) * b.kmax), oQC = take((size_t)(kmax + m + 1) * b.kmax),
                oPU = take((size_t)(kmax + m) * b.kmax), ows = take(b.hrws_doubles);
   RK_TRY(alloc_into(p->ctx, &p->small, total));
+  p->small_n = total;
   b.H = p->small + oH;
   b.R = p->small + oR;
   b.B = p->small + oB;
@@ -292,7 +298,8 @@ int ensure_capacity(rk_problem* p, int kneed, int mneed, cudaStream_t st) {
   b.PU = p->small + oPU;
   b.hrws = p->small + ows;
   RK_CUDA(cudaMemsetAsync(p->small, 0, total * sizeof(double), st));
-  RK_TRY(alloc_into(p->ctx, &p->eta, (size_t)4 * (kmax + 4) + (size_t)kmax * kmax * 2 + 16));
+  p->eta_n = (size_t)4 * (kmax + 4) + (size_t)kmax * kmax * 2 + 16;
+  RK_TRY(alloc_into(p->ctx, &p->eta, p->eta_n));
   p->part_n = partials_needed(p, kmax, mcap);
   RK_TRY(alloc_into(p->ctx, &p->part, p->part_n));
   return RK_OK;
@@ -1149,6 +1156,163 @@ int rk_problem_stats(const rk_problem* p, int32_t* solves, int32_t* recycle_dim,
   if (solves) *solves = p->solves;
   if (recycle_dim) *recycle_dim = p->kdim;
   if (n) *n = p->n;
+  return RK_OK;
+}
+
+
+int rk_problem_memory(const rk_problem* p, int64_t* device_bytes) {
+  if (!p || !device_bytes) return fail(RK_E_INVALID, "NULL argument");
+  const size_t ld = (size_t)p->ld, n = (size_t)p->n, S = (size_t)p->S;
+  size_t b = 8 * S * n + 8 * ld + sizeof(unsigned) * kCounters + sizeof(SolveState) + sizeof(BicgScalars) +
+             16 * sizeof(int);
+  if (p->QB) b += 8 * (size_t)(p->kmax + p->mcap + 1) * ld;
+  if (p->Ub) b += 8 * (size_t)p->kmax * ld;
+  if (p->rvec) b += 8 * ld;
+  if (p->coef32) b += 4 * S * n;
+  if (p->dinv32) b += 4 * ld;
+  if (p->bicg) b += 8 * 7 * ld;
+  b += 8 * (p->small_n + p->eta_n + (p->part ? p->part_n : 0));
+  *device_bytes = (int64_t)b;
+  return RK_OK;
+}
+
+int rk_problem_release(rk_problem* p, void* stream) {
+  if (!p) return fail(RK_E_INVALID, "NULL problem");
+  RK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  rk_context* c = p->ctx;
+  dev_free(c, p->QB);
+  dev_free(c, p->Ub);
+  dev_free(c, p->rvec);
+  dev_free(c, p->bicg);
+  p->QB = nullptr;
+  p->Ub = nullptr;
+  p->rvec = nullptr;
+  p->bicg = nullptr;
+  free_small(p);
+  p->part_n = 0;
+  p->kmax = 0;
+  p->mcap = 0;
+  p->kdim = 0;
+  return RK_OK;
+}
+
+int rk_solve_batch(rk_problem* const* problems, const double* const* b, double* const* x, int32_t n,
+                   const rk_solve_params* params, rk_solve_info* infos, int32_t nthreads, void* stream) {
+  if (n < 0) return fail(RK_E_INVALID, "n < 0");
+  if (n == 0) return RK_OK;
+  if (!problems || !b || !x || !params || !infos) return fail(RK_E_INVALID, "NULL argument");
+  {
+    std::vector<const rk_problem*> v(problems, problems + n);
+    std::sort(v.begin(), v.end());
+    for (int i = 0; i < n; ++i) {
+      if (!v[i]) return fail(RK_E_INVALID, "NULL problem in the batch");
+      if (i > 0 && v[i] == v[i - 1]) return fail(RK_E_INVALID, "a problem appears twice in the batch");
+    }
+  }
+  const int T = std::max(1, std::min<int>(n, nthreads > 0 ? nthreads : 16));
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0;
+  RK_CUDA(cudaGetDevice(&dev));
+  // the batch starts after the work already queued on `stream`
+  cudaEvent_t start;
+  RK_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+  RK_CUDA(cudaEventRecord(start, st));
+  std::vector<cudaStream_t> ws(T, nullptr);
+  int rc_setup = RK_OK;
+  for (int t = 0; t < T && rc_setup == RK_OK; ++t) {
+    if (cudaStreamCreateWithFlags(&ws[t], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamWaitEvent(ws[t], start, 0) != cudaSuccess)
+      rc_setup = RK_E_CUDA;
+  }
+  std::vector<int> rc(n, RK_OK);
+  std::vector<std::string> msg(n);
+  if (rc_setup == RK_OK) {
+    std::atomic<int> next{0};
+    auto worker = [&](int t) {
+      cudaSetDevice(dev);
+      for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1)) {
+        rc[i] = rk_solve(problems[i], b[i], x[i], &params[i], &infos[i], ws[t]);
+        if (rc[i] != RK_OK) msg[i] = rk_last_error();
+        infos[i].status = rc[i];
+      }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < T; ++t) pool.emplace_back(worker, t);
+    worker(0);
+    for (auto& th : pool) th.join();
+  }
+  // work queued on `stream` afterwards runs after the whole batch
+  for (int t = 0; t < T; ++t) {
+    if (!ws[t]) continue;
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) {
+      cudaEventRecord(e, ws[t]);
+      cudaStreamWaitEvent(st, e, 0);
+      cudaEventDestroy(e);
+    }
+    cudaStreamDestroy(ws[t]);
+  }
+  cudaEventDestroy(start);
+  if (rc_setup != RK_OK) return fail(rc_setup, "creating the batch streams failed");
+  for (int i = 0; i < n; ++i)
+    if (rc[i] != RK_OK) return fail(rc[i], "problem " + std::to_string(i) + ": " + msg[i]);
+  return RK_OK;
+}
+
+
+// Opaque recycle-space blob: 4 int64 (magic, n, k, reserved), then U and C as
+// stored (k double-float columns of n each).
+static const int64_t kRecycleMagic = 0x524b524543594331LL;  // "RKRECYC1"
+
+int rk_recycle_bytes(const rk_problem* p, int64_t* bytes) {
+  if (!p || !bytes) return fail(RK_E_INVALID, "NULL argument");
+  *bytes = 32 + 2 * (int64_t)p->kdim * p->n * (int64_t)sizeof(float2);
+  return RK_OK;
+}
+
+int rk_export_recycle(const rk_problem* p, void* buf, int64_t cap, void* stream) {
+  if (!p || !buf) return fail(RK_E_INVALID, "NULL argument");
+  int64_t need = 0;
+  RK_TRY(rk_recycle_bytes(p, &need));
+  if (cap < need) return fail(RK_E_INVALID, "export buffer too small");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t hdr[4] = {kRecycleMagic, p->n, p->kdim, 0};
+  char* b = (char*)buf;
+  RK_CUDA(cudaMemcpyAsync(b, hdr, sizeof(hdr), cudaMemcpyHostToDevice, st));
+  const int k = p->kdim;
+  if (k > 0) {
+    const size_t col = sizeof(float2) * (size_t)p->n;
+    RK_CUDA(cudaMemcpy2DAsync(b + 32, col, p->Ublk(k), sizeof(float2) * p->ld, col, k, cudaMemcpyDeviceToDevice, st));
+    RK_CUDA(cudaMemcpy2DAsync(b + 32 + col * k, col, p->Cblk(k), sizeof(float2) * p->ld, col, k,
+                              cudaMemcpyDeviceToDevice, st));
+  }
+  RK_CUDA(cudaStreamSynchronize(st));
+  return RK_OK;
+}
+
+int rk_import_recycle(rk_problem* p, const void* buf, int64_t bytes, void* stream) {
+  if (!p || !buf) return fail(RK_E_INVALID, "NULL argument");
+  if (bytes < 32) return fail(RK_E_INVALID, "recycle blob too short");
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t hdr[4];
+  RK_CUDA(cudaMemcpyAsync(hdr, buf, sizeof(hdr), cudaMemcpyDeviceToHost, st));
+  RK_CUDA(cudaStreamSynchronize(st));
+  if (hdr[0] != kRecycleMagic) return fail(RK_E_INVALID, "not a recycle blob");
+  if (hdr[1] != p->n) return fail(RK_E_INVALID, "recycle blob is for another problem size");
+  const int64_t k = hdr[2];
+  if (k < 0 || k > 256) return fail(RK_E_INVALID, "bad recycle dimension in blob");
+  const size_t col = sizeof(float2) * (size_t)p->n;
+  if (bytes < 32 + 2 * (int64_t)col * k) return fail(RK_E_INVALID, "recycle blob too short");
+  p->kdim = 0;
+  if (k == 0) return RK_OK;
+  RK_TRY(ensure_capacity(p, (int)k, std::max(p->mcap, 1), st));
+  const char* b = (const char*)buf;
+  RK_CUDA(cudaMemcpy2DAsync(p->Ublk((int)k), sizeof(float2) * p->ld, b + 32, col, col, k, cudaMemcpyDeviceToDevice,
+                            st));
+  RK_CUDA(cudaMemcpy2DAsync(p->Cblk((int)k), sizeof(float2) * p->ld, b + 32 + col * k, col, col, k,
+                            cudaMemcpyDeviceToDevice, st));
+  RK_CUDA(cudaStreamSynchronize(st));
+  p->kdim = (int)k;
   return RK_OK;
 }
 

@@ -28,7 +28,8 @@ RK_FP64, RK_MIXED = 0, 1
 EXPORTS = ("rk_last_error", "rk_version", "rk_context_create", "rk_context_destroy", "rk_create_problem",
            "rk_problem_destroy", "rk_set_recycle", "rk_get_recycle", "rk_solve", "rk_apply", "rk_residual",
            "rk_dots", "rk_problem_stats", "rk_profile_enable", "rk_profile_read", "rk_harmonic_ritz",
-           "rk_dots_noalloc")
+           "rk_dots_noalloc", "rk_solve_batch", "rk_problem_memory", "rk_problem_release",
+           "rk_recycle_bytes", "rk_export_recycle", "rk_import_recycle")
 
 
 class rk_grid(ctypes.Structure):

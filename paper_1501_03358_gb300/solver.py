@@ -184,16 +184,8 @@ class Problem:
     def solve(self, b, x0=None, tol=1e-8, m=40, k=20, mode="rGCROT", max_matvec=2000, hybrid_switch=5,
               update_recycle=True, out=None, stream=None, check_status=False, precision="fp64"):
         """Solve A x = b; returns (x, info dict). x0 defaults to 0."""
-        b = _f64_cuda(b, (self.n,))
-        if out is None:
-            out = torch.zeros_like(b) if x0 is None else _f64_cuda(x0, (self.n,)).clone()
-        elif x0 is not None:
-            out.copy_(_f64_cuda(x0, (self.n,)))
-        prec = {"fp64": N.RK_FP64, "mixed": N.RK_MIXED}[precision]
-        prm = N.rk_solve_params(float(tol), int(m), int(k), int(max_matvec), int(hybrid_switch), N.MODES[mode],
-                                prec, 1 if update_recycle else 0, 0)
-        if mode == "BiCGStab":
-            prm.k = 0
+        b, out = self._bx(b, x0, out)
+        prm = _params(tol, m, k, mode, max_matvec, hybrid_switch, update_recycle, precision)
         info = N.rk_solve_info()
         rc = self.lib.rk_solve(self._h, _dptr(b), _dptr(out), ctypes.byref(prm), ctypes.byref(info),
                                _stream_ptr(stream))
@@ -202,6 +194,38 @@ class Problem:
         d = info.as_dict()
         d["status_name"] = N.STATUS_NAMES.get(rc, rc)
         return out, d
+
+    def _bx(self, b, x0, out):
+        b = _f64_cuda(b, (self.n,))
+        if out is None:
+            out = torch.zeros_like(b) if x0 is None else _f64_cuda(x0, (self.n,)).clone()
+        elif x0 is not None:
+            out.copy_(_f64_cuda(x0, (self.n,)))
+        return b, out
+
+    def memory(self) -> int:
+        """Device bytes held by this problem."""
+        v = ctypes.c_int64()
+        N.check(self.lib.rk_problem_memory(self._h, ctypes.byref(v)))
+        return int(v.value)
+
+    def export_recycle(self, stream=None) -> torch.Tensor:
+        """The stored recycle space as an opaque uint8 device tensor (exact)."""
+        nb = ctypes.c_int64()
+        N.check(self.lib.rk_recycle_bytes(self._h, ctypes.byref(nb)))
+        buf = torch.empty(int(nb.value), dtype=torch.uint8, device="cuda")
+        N.check(self.lib.rk_export_recycle(self._h, _dptr(buf), ctypes.c_int64(buf.numel()), _stream_ptr(stream)))
+        return buf
+
+    def import_recycle(self, blob: torch.Tensor, stream=None):
+        """Restore a space saved by export_recycle (bit-exact)."""
+        blob = blob.to(device="cuda", dtype=torch.uint8).contiguous()
+        N.check(self.lib.rk_import_recycle(self._h, _dptr(blob), ctypes.c_int64(blob.numel()), _stream_ptr(stream)))
+
+    def release(self, stream=None):
+        """Free the basis / recycle / workspace memory (the recycle space is
+        dropped; save it with get_recycle first to restore it later)."""
+        N.check(self.lib.rk_problem_release(self._h, _stream_ptr(stream)))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -213,3 +237,53 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+
+def _params(tol, m, k, mode, max_matvec, hybrid_switch, update_recycle, precision):
+    prec = {"fp64": N.RK_FP64, "mixed": N.RK_MIXED}[precision]
+    prm = N.rk_solve_params(float(tol), int(m), int(k), int(max_matvec), int(hybrid_switch), N.MODES[mode],
+                            prec, 1 if update_recycle else 0, 0)
+    if mode == "BiCGStab":
+        prm.k = 0
+    return prm
+
+
+def solve_batch(problems, bs, outs=None, params=None, nthreads=0, stream=None, check_status=False, **kw):
+    """Solve one right-hand side on each of several distinct problems
+    concurrently (rk_solve_batch). ``params``: one dict of solve() keyword
+    arguments per problem, or None to use ``kw`` for all. Returns (outs,
+    infos); outs[i] holds x0 on entry if given (zeros otherwise). A failing
+    solve is reported in its info ("status", "status_name") and does not
+    raise unless ``check_status``; invalid batch arguments raise."""
+    n = len(problems)
+    if len(bs) != n:
+        raise ValueError("one right-hand side per problem")
+    outs = [None] * n if outs is None else list(outs)
+    bl, xl = [], []
+    for i, p in enumerate(problems):
+        b, x = p._bx(bs[i], None, outs[i])
+        bl.append(b)
+        xl.append(x)
+    plist = params if params is not None else [kw] * n
+    defaults = dict(tol=1e-8, m=40, k=20, mode="rGCROT", max_matvec=2000, hybrid_switch=5, update_recycle=True,
+                    precision="fp64")
+    prm = (N.rk_solve_params * n)()
+    for i in range(n):
+        d = dict(defaults, **plist[i])
+        prm[i] = _params(d["tol"], d["m"], d["k"], d["mode"], d["max_matvec"], d["hybrid_switch"],
+                         d["update_recycle"], d["precision"])
+    infos = (N.rk_solve_info * n)()
+    H = (ctypes.c_void_p * n)(*[p._h.value for p in problems])
+    B = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bl])
+    X = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xl])
+    lib = problems[0].lib if n else N.load()
+    rc = lib.rk_solve_batch(H, B, X, ctypes.c_int32(n), prm, infos, ctypes.c_int32(nthreads), _stream_ptr(stream))
+    per_problem = rc != N.RK_OK and any(infos[i].status == rc for i in range(n))
+    if (rc != N.RK_OK and not per_problem) or (check_status and rc != N.RK_OK):
+        N.check(rc)  # a batch-level error (bad arguments), or any failure when asked
+    out_infos = []
+    for i in range(n):
+        d = infos[i].as_dict()
+        d["status_name"] = N.STATUS_NAMES.get(infos[i].status, infos[i].status)
+        out_infos.append(d)
+    return xl, out_infos

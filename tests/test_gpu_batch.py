@@ -1,0 +1,134 @@
+"""Batched solves (rk_solve_batch) and problem memory management: a batch of
+independent problems gives exactly what each problem gives alone, failures
+stay with their problem, and a released problem whose recycle space is
+restored continues bit-identically (checkpoint / resume of the sequence)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from problems.configs import config4_problem  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1501_03358_gb300 import Context
+    c = Context()
+    yield c
+    c.close()
+
+
+def small_set(n, max_edge=40):
+    return [config4_problem(p, max_edge=max_edge, min_edge=12) for p in range(n)]
+
+
+KW = dict(tol=1e-8, m=30, k=8, mode="hybrid", hybrid_switch=2, max_matvec=3000)
+
+
+def test_batch_equals_alone(ctx):
+    from paper_1501_03358_gb300 import Problem, solve_batch
+    cfgs = small_set(6)
+    alone = [Problem(ctx, c.grid, torch.from_numpy(c.coef)) for c in cfgs]
+    batch = [Problem(ctx, c.grid, torch.from_numpy(c.coef)) for c in cfgs]
+    for t in range(4):  # steps 0-1 rGCROT, 2-3 rBiCGStab with the frozen space
+        bs = [torch.from_numpy(c.rhs(t)).cuda() for c in cfgs]
+        precision = "mixed" if t % 2 else "fp64"
+        xs, infos = solve_batch(batch, bs, nthreads=3, precision=precision, **KW)
+        for i, p in enumerate(alone):
+            xa, ia = p.solve(bs[i], precision=precision, **KW)
+            assert infos[i]["status"] == ia["status"] == 0, (t, i, infos[i], ia)
+            assert infos[i]["matvecs"] == ia["matvecs"]
+            assert infos[i]["mode_used"] == ia["mode_used"]
+            assert torch.equal(xs[i], xa), (t, i)
+            assert infos[i]["recycle_dim"] == ia["recycle_dim"]
+    for p in alone + batch:
+        p.close()
+
+
+def test_batch_failure_stays_with_its_problem(ctx):
+    from paper_1501_03358_gb300 import Problem, solve_batch
+    from paper_1501_03358_gb300.native import RKError, RK_E_INVALID
+    cfgs = small_set(3)
+    probs = [Problem(ctx, c.grid, torch.from_numpy(c.coef)) for c in cfgs]
+    bs = [torch.from_numpy(c.rhs(0)).cuda() for c in cfgs]
+    bs[1][5] = float("nan")
+    xs, infos = solve_batch(probs, bs, **KW)
+    assert infos[1]["status"] == RK_E_INVALID
+    assert infos[0]["status"] == 0 and infos[2]["status"] == 0
+    with pytest.raises(RKError):
+        solve_batch(probs, bs, check_status=True, **KW)
+    with pytest.raises(RKError):  # the same problem twice in one batch
+        solve_batch([probs[0], probs[0]], [bs[0], bs[0]], **KW)
+    for p in probs:
+        p.close()
+
+
+def test_release_and_restore_is_exact(ctx):
+    from paper_1501_03358_gb300 import Problem
+    c = small_set(1, max_edge=32)[0]
+    kw = dict(KW, mode="rGCROT")
+    a = Problem(ctx, c.grid, torch.from_numpy(c.coef))
+    b = Problem(ctx, c.grid, torch.from_numpy(c.coef))
+    rhs = [torch.from_numpy(c.rhs(t)).cuda() for t in range(3)]
+    for t in range(2):
+        a.solve(rhs[t], **kw)
+        b.solve(rhs[t], **kw)
+    full = b.memory()
+    blob = b.export_recycle().cpu()
+    U, C = b.get_recycle()
+    b.release()
+    assert b.memory() < full
+    assert b.stats()["recycle_dim"] == 0
+    # the FP64 copy restores the space to double rounding; the blob exactly
+    c2 = Problem(ctx, c.grid, torch.from_numpy(c.coef))
+    c2.set_recycle(U, C)
+    U2, C2 = c2.get_recycle()
+    assert torch.allclose(U2, U, rtol=2.0 ** -52, atol=0) and torch.allclose(C2, C, rtol=2.0 ** -52, atol=0)
+    c2.close()
+    b.import_recycle(blob)
+    xa, ia = a.solve(rhs[2], **kw)
+    xb, ib = b.solve(rhs[2], **kw)
+    assert ia["matvecs"] == ib["matvecs"]
+    assert torch.equal(xa, xb)
+    a.close()
+    b.close()
+
+
+def test_serving_with_eviction_matches_direct_sequences(ctx):
+    """Requests for several problems under a budget that holds only part of
+    their workspaces: every request is solved, problems are evicted and
+    restored, and each problem's results equal its sequence solved directly."""
+    from paper_1501_03358_gb300 import Problem
+    from paper_1501_03358_gb300.serving import Server
+    cfgs = small_set(4, max_edge=36)
+    kw = dict(KW, mode="rGCROT")
+    direct = {}
+    for i, c in enumerate(cfgs):
+        p = Problem(ctx, c.grid, torch.from_numpy(c.coef))
+        direct[i] = [p.solve(torch.from_numpy(c.rhs(t)).cuda(), **kw) for t in range(3)]
+        full = p.memory()
+        p.close()
+    # operators plus about two problems' workspace
+    op_bytes = sum(8 * (c.S + 2) * c.n for c in cfgs)
+    budget = op_bytes + 2 * max(8 * (kw["k"] * 2 + kw["m"] + 12) * c.n for c in cfgs)
+    srv = Server(ctx, budget, kw, max_batch=2)
+    for i, c in enumerate(cfgs):
+        srv.add(i, c.grid, torch.from_numpy(c.coef))
+    for t in range(3):
+        for i, c in enumerate(cfgs):
+            srv.submit(i, torch.from_numpy(c.rhs(t)).cuda())
+    srv.drain()
+    assert len(srv.done) == 12
+    assert srv.evictions > 0 and srv.restores > 0
+    seen = {i: 0 for i in range(4)}
+    for r in sorted(srv.done, key=lambda r: r.rid):
+        t = seen[r.name]
+        seen[r.name] += 1
+        xd, idd = direct[r.name][t]
+        assert r.info["status"] == 0
+        assert r.info["matvecs"] == idd["matvecs"], (r.name, t)
+        assert torch.equal(r.x, xd), (r.name, t)
+    srv.close()
