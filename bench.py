@@ -24,6 +24,8 @@ import statistics
 import subprocess
 import sys
 import threading
+
+import numpy as np
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -35,6 +37,10 @@ WORKLOADS = {
     "channel128": (2, 128, "rGCROT", 40, 20),
     "porous192": (3, 192, "hybrid", 40, 20),
     "convdiff32": (1, 32, "rGCROT", 30, 10),
+    # batched uneven set: 64 porous problems, edges log-uniform in [24, 96]
+    "batch64": (4, 0, "hybrid", 40, 10),
+    # serving: resident problems, Poisson requests, memory budget with eviction
+    "serve": (5, 0, "hybrid", 40, 20),
 }
 # Matrix-vector products per solve of the channel128 sequence in steady state
 # (steps 3-12 of the sequence), measured on the GB300 arm; used only to turn
@@ -323,6 +329,227 @@ def run_ours(args, ws, rank, local):
     ctx.close()
 
 
+def _percentiles(v):
+    return {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99))}
+
+
+def run_batch(args, ws, rank, local):
+    """Config 4: 64 independent porous problems (edges log-uniform in
+    [24, 96] per axis, solid fraction U[0.1, 0.4], skew U[0, 15] deg), one
+    right-hand side each per time step, hybrid rGCROT(40,10) -> rBiCGStab
+    (switch after 5 steps), solved together by rk_solve_batch. One bench step
+    is one time step of all 64 sequences; value = solves/s."""
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__ as g
+    g.build()
+    from problems.configs import config4_problem, CONFIG_SEED_BASE
+    from paper_1501_03358_gb300 import Context, Problem, solve_batch
+    _, _, mode, m, k = WORKLOADS["batch64"]
+    seed = None if rank == 0 else CONFIG_SEED_BASE + 4 + 1000 * rank
+    cfgs = [config4_problem(p, seed=seed) for p in range(args.nprob)]
+    W, K = args.warmup, args.steps
+    prec = args.precision or "mixed"
+    ctx = Context()
+    probs = [Problem(ctx, c.grid, torch.from_numpy(c.coef)) for c in cfgs]
+    kw = dict(tol=1e-8, m=m, k=k, mode=mode, hybrid_switch=5, max_matvec=args.max_matvec, precision=prec)
+    rhs_host = [[torch.from_numpy(c.rhs(t)).pin_memory() for c in cfgs] for t in range(W + 2 * K)]
+    rhs_dev = [[h.to("cuda", non_blocking=True) for h in row] for row in rhs_host[:W + K]]
+    xs = [torch.zeros(c.n, dtype=torch.float64, device="cuda") for c in cfgs]
+    for t in range(W):
+        for x in xs:
+            x.zero_()
+        solve_batch(probs, rhs_dev[t], outs=xs, nthreads=args.threads, **kw)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier(ws)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    lat, infos = [], []
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for t in range(W, W + K):
+        ts = torch.cuda.Event(enable_timing=True)
+        te = torch.cuda.Event(enable_timing=True)
+        ts.record(stream)
+        for x in xs:
+            x.zero_()
+        _, inf = solve_batch(probs, rhs_dev[t], outs=xs, nthreads=args.threads, **kw)
+        te.record(stream)
+        lat.append((ts, te))
+        infos.extend(inf)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = sampler.stop()
+    ms = max_over_ranks(ws, e0.elapsed_time(e1))
+    lat_ms = [a.elapsed_time(b) for a, b in lat]
+    # e2e: host right-hand sides in, host solutions out, every step
+    xh = [torch.empty(c.n, dtype=torch.float64).pin_memory() for c in cfgs]
+    bdev = [torch.empty(c.n, dtype=torch.float64, device="cuda") for c in cfgs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for t in range(W + K, W + 2 * K):
+        for i in range(len(cfgs)):
+            bdev[i].copy_(rhs_host[t][i], non_blocking=True)
+            xs[i].zero_()
+        solve_batch(probs, bdev, outs=xs, nthreads=args.threads, **kw)
+        for i in range(len(cfgs)):
+            xh[i].copy_(xs[i], non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = max_over_ranks(ws, time.perf_counter() - t0)
+    ntot = sum(c.n for c in cfgs)
+    model = sum(i["model_bytes"] for i in infos)
+    peaks, peak_src = load_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = model / (ms * 1e-3) / 1e9
+    nsol = len(cfgs) * K
+    line = {
+        "metric": METRIC, "value": ws * nsol / (ms * 1e-3), "unit": "solves/s", "n_gpus": ws, "steps": K,
+        "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == "fp64" else "f64+f32-operator", "data": "synthetic",
+        "config": {"workload": "batch64", "problems": len(cfgs), "cells_total": ntot,
+                   "edges": "log-uniform [24, 96] per axis", "stencil": 19, "solver": f"{mode}({m},{k})",
+                   "hybrid_switch": 5, "precision": prec, "tol": 1e-8, "threads": args.threads or min(len(cfgs), 16),
+                   "sequence_steps_timed": [W, W + K - 1], "l2": "inputs larger than L2",
+                   "parallelism": "replicas" if ws > 1 else "single",
+                   "executor": "rk_solve_batch: host worker threads, one CUDA stream each"},
+        "solver_hbm_gbs": achieved, "solver_hbm_frac": achieved / hbm_peak,
+        "latency_ms": dict(_percentiles(lat_ms), unit="one time step of all problems"),
+        "matvecs_per_solve": statistics.mean(i["matvecs"] for i in infos),
+        "relres_max": max(i["relres_true"] for i in infos),
+        "all_converged": all(i["status"] == 0 for i in infos),
+        "roofline": {"bound": "hbm", "kernel": "whole solver (modelled bytes, concurrent streams)",
+                     "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                     "traffic": None, "peak_source": peak_src},
+        "gpu_launches": None,
+        "e2e": {"value": ws * nsol / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * ntot,
+                "d2h_bytes_per_step": 8 * ntot},
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        c0 = cfgs[0]
+        op = oracle.Stencil(c0.grid, c0.coef)
+        tt = time.perf_counter()
+        _, _, _, inf = oracle.rgcrot(op, c0.rhs(0), tol=1e-14, m=m, k=k, max_matvec=2 * m)
+        per_cell_mv = (time.perf_counter() - tt) / max(inf["matvecs"], 1) / c0.n
+        step_mv_cells = sum(i["matvecs"] * cfgs[j % len(cfgs)].n for j, i in enumerate(infos)) / K
+        threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        line["cpu_baseline"] = {"value": len(cfgs) / (per_cell_mv * step_mv_cells), "unit": "solves/s",
+                                "cores": threads, "kind": "oracle",
+                                "sample": f"two rGCROT({m},{k}) cycles of problem 0 ({c0.n} cells): "
+                                          f"{per_cell_mv * 1e9:.1f} ns per matvec per cell; solves/s = problems / "
+                                          f"(that x sum over problems of cells x matvecs per step measured above)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for p in probs:
+        p.close()
+    ctx.close()
+
+
+def run_serve(args, ws, rank, local):
+    """Serving loop (reduced config 5): resident problems of mixed sizes
+    (channel and porous generators alternating), requests = the next
+    right-hand side of one problem, arriving as a Poisson process at
+    ``--rate-frac`` of the measured burst capacity; admission by a device
+    memory budget with LRU eviction of recycle spaces (exact spill to pinned
+    host memory). Reports solves/s and p50/p99 latency (completion - arrival),
+    and the same arrivals served by plain FP64 GMRES(40) without recycling."""
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__ as g
+    g.build()
+    from problems import make_config
+    from problems.configs import porous_problem, ConfigProblem
+    from paper_1501_03358_gb300 import Context
+    from paper_1501_03358_gb300.serving import Server
+    edges = [int(e) for e in args.serve_edges.split(",")]
+    cfgs = []
+    for i in range(args.nprob):
+        e = edges[i % len(edges)]
+        if i % 2 == 0:
+            cfgs.append(make_config(2, size=e, seed=20150113 + 5 + 1000 * rank + i))
+        else:
+            gr, coef, got = porous_problem((e, e, e), 0.25, 10.0, 20150113 + 5 + 1000 * rank + i,
+                                           max_attempts=200_000)
+            ones = np.ones(e)
+            cfgs.append(ConfigProblem(f"serve{i}", gr, 19, coef, {}, 20, 20150113 + 5 + i, "div",
+                                      dict(sigma=4.0, hx=ones, hy=ones, hz=ones, walls=(False, True, True))))
+    nreq = args.requests
+    rng = np.random.default_rng(20150113 + 55 + rank)
+    order = [int(i) for i in rng.integers(0, len(cfgs), nreq)]
+    seen = [0] * len(cfgs)
+    reqs = []
+    for i in order:
+        reqs.append((i, torch.from_numpy(cfgs[i].rhs(seen[i] + 1)).cuda()))
+        seen[i] += 1
+    ctx = Context()
+    footprint = sum(8 * (c.S + 2) * c.n + 8 * (2 * 20 + 40 + 12) * c.n for c in cfgs)
+    budget = int(args.budget_frac * footprint)
+
+    def serve(kw, rate):
+        srv = Server(ctx, budget, kw, max_batch=args.max_batch, nthreads=args.threads)
+        for i, c in enumerate(cfgs):
+            srv.add(i, c.grid, torch.from_numpy(c.coef))
+        # warm-up: one request per problem (builds recycle spaces), untimed
+        for i, c in enumerate(cfgs):
+            srv.submit(i, torch.from_numpy(c.rhs(0)).cuda())
+        srv.drain()
+        srv.done.clear()
+        arr = np.cumsum(rng.exponential(1.0 / rate, nreq)) if rate else np.zeros(nreq)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nxt = 0
+        while nxt < nreq or srv.queue:
+            now = time.perf_counter() - t0
+            while nxt < nreq and arr[nxt] <= now:
+                srv.submit(reqs[nxt][0], reqs[nxt][1], arrival=t0 + arr[nxt])
+                nxt += 1
+            if srv.queue:
+                srv.step()
+            elif nxt < nreq:
+                time.sleep(max(0.0, min(arr[nxt] - now, 0.01)))
+        wall = time.perf_counter() - t0
+        lat = [1e3 * (r.finish - r.arrival) for r in srv.done]
+        res = {"solves_per_s": len(srv.done) / wall, "latency_ms": _percentiles(lat),
+               "converged": sum(1 for r in srv.done if r.info["status"] == 0), "requests": len(srv.done),
+               "evictions": srv.evictions, "restores": srv.restores,
+               "matvecs_per_solve": statistics.mean(r.info["matvecs"] for r in srv.done)}
+        srv.close()
+        return res
+
+    cap_mv = min(args.max_matvec, 4000)
+    rkw = dict(tol=1e-8, m=40, k=20, mode="hybrid", hybrid_switch=5, max_matvec=cap_mv,
+               precision=args.precision or "mixed")
+    gkw = dict(tol=1e-8, m=40, k=0, mode="GMRES", max_matvec=cap_mv, precision="fp64")
+    cap = serve(rkw, None)                      # burst: all requests at t = 0
+    rate = args.rate_frac * cap["solves_per_s"]
+    live = serve(rkw, rate)
+    gm = serve(gkw, rate)
+    peaks, peak_src = load_peaks()
+    line = {
+        "metric": METRIC, "value": live["solves_per_s"], "unit": "solves/s", "n_gpus": ws, "steps": nreq,
+        "warmup": len(cfgs), "ms_per_step": 1e3 / max(live["solves_per_s"], 1e-9), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32-operator", "data": "synthetic",
+        "config": {"workload": "serve", "problems": len(cfgs), "edges": edges, "requests": nreq,
+                   "budget_bytes": budget, "budget_frac_of_footprint": args.budget_frac,
+                   "rate_per_s": rate, "rate_frac_of_capacity": args.rate_frac, "max_batch": args.max_batch,
+                   "solver": "hybrid rGCROT(40,20)->rBiCGStab, mixed", "tol": 1e-8, "max_matvec": cap_mv,
+                   "reduced": "edges and problem count reduced from the 32 x {64..256}^3 / 120 GB serving set"},
+        "latency_ms": live["latency_ms"], "serving": live, "burst_capacity": cap,
+        "gmres40_no_recycling_same_arrivals": gm,
+        "roofline": None, "gpu_launches": None,
+        "e2e": {"value": live["solves_per_s"], "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,15 +562,36 @@ def main():
     ap.add_argument("--preroll", type=int, default=12,
                     help="untimed sequence steps before warm-up (stops at the first converged one)")
     ap.add_argument("--preroll-matvec", type=int, default=4000, help="matvec cap of each pre-roll solve")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
-                    help="fp64: FP64 operator, double-float projections; mixed: FP32 inner operator (A11)")
+    ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
+                    help="fp64: FP64 operator, double-float projections; mixed: FP32 inner operator (A11). "
+                         "Default fp64 for the single-sequence workloads, mixed for batch64 and serve")
+    ap.add_argument("--nprob", type=int, default=None, help="problems (batch64: 64; serve: 12)")
+    ap.add_argument("--threads", type=int, default=0, help="rk_solve_batch worker threads (0: min(n, 16))")
+    ap.add_argument("--requests", type=int, default=60, help="serve: number of timed requests")
+    ap.add_argument("--serve-edges", default="32,48,64,96", help="serve: grid edges, cycled over problems")
+    ap.add_argument("--budget-frac", type=float, default=0.6, help="serve: memory budget / full footprint")
+    ap.add_argument("--rate-frac", type=float, default=0.7, help="serve: arrival rate / burst capacity")
+    ap.add_argument("--max-batch", type=int, default=8, help="serve: requests per batch")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     ws, rank, local = dist_init()
+    if args.nprob is None:
+        args.nprob = 64 if args.workload == "batch64" else 12
     if args.impl == "reference":
-        run_reference(args, ws, rank)
+        if args.workload in ("batch64", "serve"):
+            if rank == 0:
+                print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times single sequences; "
+                                  "batch64 reports its oracle baseline in cpu_baseline"}), flush=True)
+        else:
+            run_reference(args, ws, rank)
+    elif args.workload == "batch64":
+        run_batch(args, ws, rank, local)
+    elif args.workload == "serve":
+        run_serve(args, ws, rank, local)
     else:
+        if args.precision is None:
+            args.precision = "fp64"
         run_ours(args, ws, rank, local)
     if ws > 1:
         import torch.distributed as dist
