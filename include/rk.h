@@ -185,7 +185,7 @@ int rk_dots(rk_context* ctx, int64_t n, int32_t nq, const double* Q, int64_t ld,
  * Equivalent to calling rk_solve(problems[i], b[i], x[i], &params[i],
  * &infos[i]) for every i, except that the solves run concurrently: a pool of
  * nthreads host threads (<= 0: min(n, 16)), each driving its own CUDA
- * stream, takes problems from a shared queue. problems, b, x, params, infos:
+ * stream, takes problems from a shared queue, largest N first. problems, b, x, params, infos:
  * host arrays of n entries (b[i], x[i] device pointers as in rk_solve). The
  * batch starts after the work already queued on `stream`, and work queued on
  * `stream` afterwards runs after the whole batch; the call returns when every

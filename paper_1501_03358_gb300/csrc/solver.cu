@@ -1226,11 +1226,17 @@ int rk_solve_batch(rk_problem* const* problems, const double* const* b, double* 
   }
   std::vector<int> rc(n, RK_OK);
   std::vector<std::string> msg(n);
+  // largest problems first (longest-processing-time order), so that the
+  // batch does not end with one large solve running alone
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b2) { return problems[a]->n > problems[b2]->n; });
   if (rc_setup == RK_OK) {
     std::atomic<int> next{0};
     auto worker = [&](int t) {
       cudaSetDevice(dev);
-      for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1)) {
+      for (int q = next.fetch_add(1); q < n; q = next.fetch_add(1)) {
+        const int i = order[q];
         rc[i] = rk_solve(problems[i], b[i], x[i], &params[i], &infos[i], ws[t]);
         if (rc[i] != RK_OK) msg[i] = rk_last_error();
         infos[i].status = rc[i];
