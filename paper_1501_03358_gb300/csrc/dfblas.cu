@@ -736,13 +736,18 @@ int dots2_blocks(int64_t n) {
   return (int)b;
 }
 
-cudaError_t launch_dfdots2(const DFDots2Args& a, cudaStream_t st) {
-  // one-time attribute setup (thread-safe static initialisation)
+// one-time attribute setup (thread-safe static initialisation); also run
+// when a problem is created, so that it never happens inside a graph capture
+void dfblas_prepare() {
   static const bool attr = [] {
     cudaFuncSetAttribute(k_dfdots2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kD2Smem);
     return true;
   }();
   (void)attr;
+}
+
+cudaError_t launch_dfdots2(const DFDots2Args& a, cudaStream_t st) {
+  dfblas_prepare();
   const int xb = dots2_blocks(a.n);
   const int64_t per = (a.n + xb - 1) / xb;
   const int64_t rpb = (per + kD2Rows - 1) / kD2Rows * kD2Rows;  // even: 16-byte aligned stages

@@ -130,6 +130,8 @@ struct DFDots2Args {
   int* err;           // set nonzero if a bounded wait gives up
 };
 cudaError_t launch_dfdots2(const DFDots2Args& a, cudaStream_t st);
+// one-time kernel attribute setup of the streaming kernels (idempotent)
+void dfblas_prepare();
 // x-extent of its grid (a function of n alone)
 int dots2_blocks(int64_t n);
 

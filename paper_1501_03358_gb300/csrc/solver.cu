@@ -18,6 +18,7 @@
 #include <cstring>
 #include <string>
 #include <vector>
+#include <map>
 #include <algorithm>
 #include <atomic>
 #include <thread>
@@ -172,6 +173,14 @@ struct ProfScope {
 struct rk_problem {
   rk_context* ctx = nullptr;
   Profiler prof;
+  // Captured Arnoldi cycles keyed by (recycle dim, steps, mixed, keep v_steps);
+  // valid while the buffers they reference are (cleared on reallocation).
+  std::map<uint64_t, cudaGraphExec_t> graphs;
+  cudaStream_t capture_stream = nullptr;  // capture only (graphs launch on the caller's stream)
+  void drop_graphs() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    graphs.clear();
+  }
   Dims d{};
   int S = 7;
   int64_t n = 0, ld = 0;
@@ -231,6 +240,7 @@ void free_small(rk_problem* p) {
 // the stored recycle space.
 int ensure_capacity(rk_problem* p, int kneed, int mneed, cudaStream_t st) {
   if (kneed <= p->kmax && mneed <= p->mcap && p->QB) return RK_OK;
+  p->drop_graphs();
   const int kmax = std::max(kneed, p->kmax);
   const int mcap = std::max(mneed, p->mcap);
   if (kmax > 256) return fail(RK_E_INVALID, "recycle dimension above 256 is not supported");
@@ -462,6 +472,7 @@ int stencil_df_launch(rk_problem* p, int mode, const void* v, bool v_df, void* y
 // coefficients and 1/a_pp rounded to nearest once.
 int ensure_mixed(rk_problem* p, cudaStream_t st) {
   if (p->coef32) return RK_OK;
+  p->drop_graphs();
   RK_TRY(alloc_into(p->ctx, &p->coef32, (size_t)p->S * p->n));
   RK_TRY(alloc_into(p->ctx, &p->dinv32, (size_t)p->ld));
   RK_CUDA(launch_round_f32((int64_t)p->S * p->n, p->coef, p->coef32, st));
@@ -579,29 +590,59 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
   const int* done = &p->st->done;
   while (rho > tolabs && matvecs < maxmv) {
     const int steps = std::min(m, maxmv - matvecs);
-    // v_1 = r / rho, stored double-float (line 4)
-    RK_CUDA(launch_to_df(p->n, r, p->Vcol(0), &p->st->rho2, 1, 1, p->ld, p->ld, st));
-    { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_cycle_init(p->st, p->sb, st)); }
-    // lines 6-11: one product, one fused inner-product pass and one update
-    // pass per step (Gram-Schmidt against [C V_j] with the second pass of
-    // each vector delayed to the next step)
-    for (int j = 0; j < steps; ++j) {
-      RK_TRY(opapply_launch(p, mixed, p->Vcol(j), true, p->Vcol(j + 1), true, done, st));
-      const int nq = kc + j;
-      RK_TRY(dfdots2_launch(p, p->Cblk(kc), nq, p->Vcol(j), p->Vcol(j + 1), p->sb.dots, done, st));
-      { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_dcgs_coef(p->st, p->sb, kc, j, 0, st)); }
-      RK_TRY(dfupdate2_launch(p, p->Cblk(kc), nq, p->sb.dots, p->sb.dots + nq, p->st->scal, p->Vcol(j),
-                              p->Vcol(j + 1), &p->st->upd_mode, true, st));
-    }
-    // cycle end without convergence: second pass of the last vector
-    // (completes column steps-1; v_steps is kept for the recycle update)
-    {
+    // one Arnoldi cycle (lines 4-11 and the second pass of the last vector):
+    // a fixed launch sequence whose kernels skip themselves once the device
+    // flags say the cycle has stopped, so it is captured once per shape into
+    // a CUDA graph and replayed (not while the per-kernel profiler runs)
+    const bool keep_last = update && k > 0;
+    auto cycle = [&](cudaStream_t st) -> int {
+      // v_1 = r / rho, stored double-float (line 4)
+      RK_CUDA(launch_to_df(p->n, r, p->Vcol(0), &p->st->rho2, 1, 1, p->ld, p->ld, st));
+      { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_cycle_init(p->st, p->sb, st)); }
+      // lines 6-11: one product, one fused inner-product pass and one update
+      // pass per step (Gram-Schmidt against [C V_j] with the second pass of
+      // each vector delayed to the next step)
+      for (int j = 0; j < steps; ++j) {
+        RK_TRY(opapply_launch(p, mixed, p->Vcol(j), true, p->Vcol(j + 1), true, done, st));
+        const int nq = kc + j;
+        RK_TRY(dfdots2_launch(p, p->Cblk(kc), nq, p->Vcol(j), p->Vcol(j + 1), p->sb.dots, done, st));
+        { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_dcgs_coef(p->st, p->sb, kc, j, 0, st)); }
+        RK_TRY(dfupdate2_launch(p, p->Cblk(kc), nq, p->sb.dots, p->sb.dots + nq, p->st->scal, p->Vcol(j),
+                                p->Vcol(j + 1), &p->st->upd_mode, true, st));
+      }
+      // cycle end without convergence: second pass of the last vector
+      // (completes column steps-1; v_steps is kept for the recycle update)
       const int nq = kc + steps;
       RK_TRY(dfdots_launch(p, p->Cblk(kc), nq, p->Vcol(steps), true, p->sb.dots, done, st, nullptr, 1));
       { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_dcgs_coef(p->st, p->sb, kc, steps, 1, st)); }
-      if (update && k > 0)
+      if (keep_last)
         RK_TRY(dfupdate2_launch(p, p->Cblk(kc), nq, p->sb.dots, p->sb.dots, p->st->scal, p->Vcol(steps),
                                 p->Vcol(steps), &p->st->upd_mode, false, st));
+      return RK_OK;
+    };
+    if (p->prof.on) {
+      RK_TRY(cycle(st));
+    } else {
+      const uint64_t key = ((uint64_t)kc << 32) | ((uint64_t)steps << 2) | (mixed ? 2u : 0u) | (keep_last ? 1u : 0u);
+      auto it = p->graphs.find(key);
+      if (it == p->graphs.end()) {
+        cudaGraph_t g = nullptr;
+        if (!p->capture_stream) RK_CUDA(cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking));
+        RK_CUDA(cudaStreamBeginCapture(p->capture_stream, cudaStreamCaptureModeThreadLocal));
+        const int rc = cycle(p->capture_stream);
+        const cudaError_t ce = cudaStreamEndCapture(p->capture_stream, &g);
+        if (rc != RK_OK) {
+          if (g) cudaGraphDestroy(g);
+          return rc;
+        }
+        if (ce != cudaSuccess) return fail(RK_E_CUDA, std::string("graph capture failed: ") + cudaGetErrorString(ce));
+        cudaGraphExec_t ge = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) return fail(RK_E_CUDA, std::string("graph instantiation failed: ") + cudaGetErrorString(ie));
+        it = p->graphs.emplace(key, ge).first;
+      }
+      RK_CUDA(cudaGraphLaunch(it->second, st));
     }
     RK_TRY(sync_state(p, st));
     const int jj = p->st_h->jj;
@@ -850,6 +891,7 @@ int rk_create_problem(rk_context* ctx, const rk_grid* grid, int32_t S, const dou
     return code;
   };
   int r;
+  dfblas_prepare();
   if ((r = alloc_into(ctx, &p->coef, (size_t)S * p->n)) != RK_OK) return cleanup(r);
   if ((r = alloc_into(ctx, &p->dinv, (size_t)p->ld)) != RK_OK) return cleanup(r);
   if ((r = alloc_into(ctx, &p->counter, kCounters)) != RK_OK) return cleanup(r);
@@ -911,6 +953,8 @@ int rk_create_problem(rk_context* ctx, const rk_grid* grid, int32_t S, const dou
 
 void rk_problem_destroy(rk_problem* p) {
   if (!p) return;
+  p->drop_graphs();
+  if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
   rk_context* c = p->ctx;
   dev_free(c, p->coef);
   dev_free(c, p->dinv);
@@ -1179,6 +1223,7 @@ int rk_problem_memory(const rk_problem* p, int64_t* device_bytes) {
 int rk_problem_release(rk_problem* p, void* stream) {
   if (!p) return fail(RK_E_INVALID, "NULL problem");
   RK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  p->drop_graphs();
   rk_context* c = p->ctx;
   dev_free(c, p->QB);
   dev_free(c, p->Ub);
