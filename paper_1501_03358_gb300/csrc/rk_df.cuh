@@ -140,4 +140,31 @@ __device__ __forceinline__ float2 df_sqrt(float2 a) {
 
 __device__ __forceinline__ float2 df_absv(float2 a) { return a.x < 0.f ? df_neg(a) : a; }
 
+// Faster variants for scalar chains whose operands are scaled near 1 (the
+// small eigenproblem): the FP32 seeds come from the approximate reciprocal
+// and square root (a few ulp); the double-float remainder steps that follow
+// correct any seed error of that size, so the results keep ~2^-46 accuracy.
+__device__ __forceinline__ float2 df_div_fast(float2 a, float2 b) {
+  const float r = __fdividef(1.f, b.x);
+  const float q1 = a.x * r;
+  float2 rem = df_fma(make_float2(-q1, 0.f), b, a);
+  const float q2 = rem.x * r;
+  rem = df_fma(make_float2(-q2, 0.f), b, rem);
+  const float q3 = rem.x * r;
+  const df s = df_fast_two_sum(q1, q2);
+  return df_add(make_float2(s.hi, s.lo), make_float2(q3, 0.f));
+}
+
+__device__ __forceinline__ float2 df_sqrt_fast(float2 a) {
+  if (!(a.x > 0.f)) return make_float2(0.f, 0.f);
+  const float s = a.x * rsqrtf(a.x);
+  float2 e = df_fma(make_float2(-s, 0.f), make_float2(s, 0.f), a);  // a - s^2
+  const float t = e.x * __fdividef(0.5f, s);
+  const df r = df_fast_two_sum(s, t);
+  // one more correction: the seed is only a few ulp accurate
+  const float2 r2 = make_float2(r.hi, r.lo);
+  e = df_sub(a, df_mul(r2, r2));
+  return df_add(r2, make_float2(e.x * __fdividef(0.5f, r.hi), 0.f));
+}
+
 }  // namespace rk

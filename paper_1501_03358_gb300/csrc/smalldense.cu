@@ -247,17 +247,6 @@ __device__ void apply_left(double* A, int ld, int r0, int len, int c0, int c1, c
   }
 }
 
-// A(r, c0 + i) -= tau * (A(r, c0:c0+len) v) v_i for rows r in [r0, r1).
-__device__ void apply_right(double* A, int ld, int r0, int r1, int c0, int len, const double* v, double tau) {
-  if (tau == 0.0) return;
-  for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-    double w = 0.0;
-    for (int i = 0; i < len; ++i) w = fma(A[r + (int64_t)(c0 + i) * ld], v[i], w);
-    w *= tau;
-    for (int i = 0; i < len; ++i) A[r + (int64_t)(c0 + i) * ld] = fma(-w, v[i], A[r + (int64_t)(c0 + i) * ld]);
-  }
-}
-
 // Complex helpers
 struct cplx { double re, im; };
 __device__ __forceinline__ cplx cmul(cplx a, cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
@@ -291,13 +280,14 @@ __device__ void house_small_df(float2 x, float2 y, float2 z, int len, float2* v,
   float2 ss = df_mul(x, x);
   ss = df_fma(y, y, ss);
   if (len == 3) ss = df_fma(z, z, ss);
-  const float2 nrm = df_sqrt(ss);
+  const float2 nrm = df_sqrt_fast(ss);
   const float2 beta = x.x <= 0.f ? nrm : df_neg(nrm);
   const float2 v0 = df_sub(x, beta);
-  const float2 rv0 = df_div(make_float2(1.f, 0.f), v0);
+  // the two quotients are independent (their chains overlap)
+  const float2 rv0 = df_div_fast(make_float2(1.f, 0.f), v0);
+  *tau = df_div_fast(df_sub(beta, x), beta);
   v[1] = df_mul(y, rv0);
   v[2] = len == 3 ? df_mul(z, rv0) : make_float2(0.f, 0.f);
-  *tau = df_div(df_sub(beta, x), beta);
 }
 
 // h <- (I - tau v v^T) h for a 3-vector (v0 = 1) or a 2-vector (v2 = 0)
@@ -315,19 +305,105 @@ __device__ __forceinline__ void refl2_df(float2& h0, float2& h1, float2 v1, floa
   h1 = df_fma(df_neg(ww), v1, h1);
 }
 
+// Block sum of per-thread double-float values; every thread gets the result.
+__device__ float2 block_df_sum(float2 v, float2* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = df_warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  float2 t = red[0];
+  for (int q = 1; q < nw; ++q) t = df_add(t, red[q]);
+  return t;
+}
+
+// Householder reduction to upper Hessenberg form H = Z^T M Z in double-float
+// (the reflectors of column c act on rows/columns c+1..n-1; Z accumulates
+// them). H has leading dimension ldh, Z leading dimension n; v is a scratch
+// vector of n double-float values. Block-wide; the Z updates run on threads
+// 64.. while threads 0..63 update the rows of H.
+__device__ void hessenberg_df(float2* H, int ldh, float2* Z, int n, float2* v) {
+  __shared__ float2 red2[32];
+  __shared__ float2 hb[2];  // beta, tau
+  const int tid = threadIdx.x, bd = blockDim.x;
+  for (int c = 0; c + 2 < n; ++c) {
+    const int len = n - c - 1;
+    float2* x = H + (int64_t)c * ldh + c + 1;
+    float sh = 0.f, sl = 0.f;
+    for (int i = tid + 1; i < len; i += bd) df_mac(sh, sl, x[i].x, x[i].y, x[i].x, x[i].y);
+    const float2 sig = block_df_sum(make_float2(sh, sl), red2);
+    const float2 alpha = x[0];
+    if (!(sig.x > 0.f)) {
+      for (int i = tid; i < len; i += bd) v[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
+      if (tid == 0) {
+        hb[0] = alpha;
+        hb[1] = make_float2(0.f, 0.f);
+      }
+    } else {
+      const float2 nrm = df_sqrt_fast(df_fma(alpha, alpha, sig));
+      const float2 beta = alpha.x <= 0.f ? nrm : df_neg(nrm);
+      const float2 rv0 = df_div_fast(make_float2(1.f, 0.f), df_sub(alpha, beta));
+      for (int i = tid; i < len; i += bd) v[i] = i == 0 ? make_float2(1.f, 0.f) : df_mul(x[i], rv0);
+      if (tid == 0) {
+        hb[0] = beta;
+        hb[1] = df_div_fast(df_sub(beta, alpha), beta);
+      }
+    }
+    __syncthreads();
+    const float2 tau = hb[1];
+    if (tau.x != 0.f) {
+      // from the left: columns c..n-1, rows c+1..n-1
+      for (int j = c + tid; j < n; j += bd) {
+        float2* col = H + (int64_t)j * ldh + c + 1;
+        float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f;
+        int i = 0;
+        for (; i + 1 < len; i += 2) {
+          df_mac(ah, al, v[i].x, v[i].y, col[i].x, col[i].y);
+          df_mac(bh, bl, v[i + 1].x, v[i + 1].y, col[i + 1].x, col[i + 1].y);
+        }
+        if (i < len) df_mac(ah, al, v[i].x, v[i].y, col[i].x, col[i].y);
+        const float2 ww = df_neg(df_mul(tau, df_add(make_float2(ah, al), make_float2(bh, bl))));
+        for (int i2 = 0; i2 < len; ++i2) col[i2] = df_fma(ww, v[i2], col[i2]);
+      }
+      __syncthreads();
+      // from the right: rows 0..n-1 of H (threads 0..63) and of Z (threads 64..)
+      const bool zpart = tid >= 64;
+      float2* A = zpart ? Z : H;
+      const int lda = zpart ? n : ldh;
+      const int t0 = zpart ? tid - 64 : tid, ts = zpart ? bd - 64 : 64;
+      for (int r = t0; r < n; r += ts) {
+        float2* row = A + r + (int64_t)(c + 1) * lda;
+        float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f;
+        int i = 0;
+        for (; i + 1 < len; i += 2) {
+          df_mac(ah, al, row[(int64_t)i * lda].x, row[(int64_t)i * lda].y, v[i].x, v[i].y);
+          df_mac(bh, bl, row[(int64_t)(i + 1) * lda].x, row[(int64_t)(i + 1) * lda].y, v[i + 1].x, v[i + 1].y);
+        }
+        if (i < len) df_mac(ah, al, row[(int64_t)i * lda].x, row[(int64_t)i * lda].y, v[i].x, v[i].y);
+        const float2 ww = df_neg(df_mul(tau, df_add(make_float2(ah, al), make_float2(bh, bl))));
+        for (int i2 = 0; i2 < len; ++i2) row[(int64_t)i2 * lda] = df_fma(ww, v[i2], row[(int64_t)i2 * lda]);
+      }
+      __syncthreads();
+    }
+    for (int i = tid; i < len; i += bd) x[i] = i == 0 ? hb[0] : make_float2(0.f, 0.f);
+    __syncthreads();
+  }
+}
+
 // Francis double-shift QR (implicit, bulge chasing with 3x3 reflectors;
 // exceptional shifts at iterations 10 and 20 of one eigenvalue; deflation
 // when |h_{l,l-1}| <= 2^-47 (|h_{l-1,l-1}| + |h_ll|); 2x2 blocks with real
 // eigenvalues split by a rotation) on Hd (n x n Hessenberg, DF), with the
-// transformations accumulated into Zd. Block-wide; eigenvalues to wr, wi
-// (FP64). On more than 40 n iterations *sfail is set.
-__device__ void francis_df(float2* Hd, float2* Zd, int n, double* wr, double* wi, float hn, int* su, int* sl,
-                           int* siter, int* stotal, int* sfail) {
+// transformations accumulated into Zd. hn: max |h_ij|. Block-wide;
+// eigenvalues to wr, wi (FP64). On more than 40 n iterations *sfail is set.
+__device__ void francis_df(float2* Hd, int ldh, float2* Zd, int n, double* wr, double* wi, float hn, int* su,
+                           int* sl, int* siter, int* stotal, int* sfail) {
   __shared__ float2 v3[3], tau3, rot[2];
   __shared__ int c_real;
-  const float eps = 7.105427357601002e-15f;  // 2^-47
+  const float eps = 7.105427357601002e-15f;    // 2^-47
+  const float floor_abs = 1.4210854715202004e-14f * hn;  // 2^-46 max |h_ij|
   const int tid = threadIdx.x;
-#define HD(i, j) Hd[(i) + (int64_t)(j) * n]
+#define HD(i, j) Hd[(i) + (int64_t)(j) * ldh]
 #define ZD(i, j) Zd[(i) + (int64_t)(j) * n]
   while (true) {
     __syncthreads();
@@ -336,9 +412,12 @@ __device__ void francis_df(float2* Hd, float2* Zd, int n, double* wr, double* wi
     if (tid == 0) {
       int l = u;
       while (l > 0) {
-        float sc = fabsf(HD(l - 1, l - 1).x) + fabsf(HD(l, l).x);
-        if (sc == 0.f) sc = hn;
-        if (fabsf(HD(l, l - 1).x) <= eps * sc) break;
+        // relative to the neighbouring diagonal, with an absolute floor at the
+        // double-float rounding level of the whole matrix (a subdiagonal next
+        // to eigenvalues near zero cannot drop below that noise)
+        const float h = fabsf(HD(l, l - 1).x);
+        const float sc = fabsf(HD(l - 1, l - 1).x) + fabsf(HD(l, l).x);
+        if (h <= eps * sc || h <= floor_abs) break;
         --l;
       }
       if (l > 0) HD(l, l - 1) = make_float2(0.f, 0.f);
@@ -563,37 +642,20 @@ __device__ void hr_core(HRWork w, int n, int k, double* QC, int ldqc, double* PU
       w.M[i + (int64_t)c * n] = t / w.G[c + (int64_t)c * ldg];
     }
   }
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) w.Z[t] = (t % (n + 1)) == 0 ? 1.0 : 0.0;
   __syncthreads();
-  // ---- 3. Hessenberg reduction M = Z H Z^T.
-  for (int c = 0; c + 2 < n; ++c) {
-    const int len = n - c - 1;
-    double* x = w.M + (int64_t)c * n + c + 1;
-    house(x, len, w.v, &sh_beta, &sh_tau, red);
-    const double tau = sh_tau;
-    apply_left(w.M, n, c + 1, len, c, n, w.v, tau);
-    __syncthreads();
-    apply_right(w.M, n, 0, n, c + 1, len, w.v, tau);
-    apply_right(w.Z, n, 0, n, c + 1, len, w.v, tau);
-    __syncthreads();
-    for (int i = threadIdx.x; i < len; i += blockDim.x) x[i] = i == 0 ? sh_beta : 0.0;
-    __syncthreads();
-  }
-  // ---- 4. Real Schur form (T in M, Schur vectors in Z) by Francis
-  //         double-shift QR. The iteration is a long chain of small
-  //         dependent steps, and on this GPU an FP64 instruction costs a warp
-  //         ~64 cycles even with one lane active, so the sweep runs in
-  //         double-float arithmetic on the FP32 pipe (about 48 significant
-  //         bits): H and Z are converted once into the F and M workspaces,
-  //         the Schur vectors are updated by threads 64.. (other warps) in
-  //         the same phase as the column updates of H, and T and Z are
-  //         converted back to FP64 at the end.
+  // ---- 3./4. Hessenberg form and real Schur form (T in M, Schur vectors
+  //         in Z). Both are long chains of small dependent steps, and on this
+  //         GPU an FP64 instruction costs a warp ~64 cycles even with one
+  //         lane active, so they run in double-float arithmetic on the FP32
+  //         pipe (about 48 significant bits): M, scaled by a power of two
+  //         (exact) so that its entries stay well inside the FP32 exponent
+  //         range, is converted once into the F workspace (leading dimension
+  //         n+1, conflict-free column sweeps), Z into the M workspace; the
+  //         Schur-vector updates run on other warps than the row updates of
+  //         H; T (scaled back), Z and the eigenvalues return to FP64.
   double hnorm = 0.0;
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) hnorm = fmax(hnorm, fabs(w.M[t]));
-  hnorm = block_sum(hnorm, red);  // a bound on max |h_ij|, used only for zero tests
-  // H is scaled by a power of two (exact) so that its entries stay well inside
-  // the FP32 exponent range of double-float numbers; T and the eigenvalues
-  // are scaled back afterwards.
+  hnorm = block_sum(hnorm, red);  // a bound on max |m_ij|, used for the scale and zero tests
   __shared__ double sh_scale;
   if (threadIdx.x == 0) {
     int ex = 0;
@@ -602,11 +664,27 @@ __device__ void hr_core(HRWork w, int n, int k, double* QC, int ldqc, double* PU
   }
   __syncthreads();
   const double hscale = sh_scale;
+  const int ldh = n + 1;
   float2* Hd = reinterpret_cast<float2*>(w.F);
   float2* Zd = reinterpret_cast<float2*>(w.M);
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) Hd[t] = df_make(w.M[t] * hscale);
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int r = t % n, c = t / n;
+    Hd[r + (int64_t)c * ldh] = df_make(w.M[t] * hscale);
+  }
   __syncthreads();
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) Zd[t] = df_make(w.Z[t]);
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x)
+    Zd[t] = make_float2((t % (n + 1)) == 0 ? 1.f : 0.f, 0.f);
+  __syncthreads();
+  hessenberg_df(Hd, ldh, Zd, n, reinterpret_cast<float2*>(w.v));
+  __shared__ float sh_hmax;
+  {
+    float hm = 0.f;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) hm = fmaxf(hm, fabsf(Hd[t % n + (int64_t)(t / n) * ldh].x));
+    for (int o = 16; o > 0; o >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
+    if (threadIdx.x == 0) sh_hmax = 0.f;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(&sh_hmax), __float_as_int(hm));
+  }
   if (threadIdx.x == 0) {
     sh_u = n - 1;
     sh_iter = 0;
@@ -614,11 +692,14 @@ __device__ void hr_core(HRWork w, int n, int k, double* QC, int ldqc, double* PU
     sh_fail = 0;
   }
   __syncthreads();
-  francis_df(Hd, Zd, n, w.wr, w.wi, (float)(hnorm * hscale), &sh_u, &sh_l, &sh_iter, &sh_total, &sh_fail);
+  francis_df(Hd, ldh, Zd, n, w.wr, w.wi, sh_hmax, &sh_u, &sh_l, &sh_iter, &sh_total, &sh_fail);
   __syncthreads();
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) w.Z[t] = df_to_double(Zd[t]);
   __syncthreads();
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) w.M[t] = df_to_double(Hd[t]) / hscale;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int r = t % n, c = t / n;
+    w.M[t] = df_to_double(Hd[r + (int64_t)c * ldh]) / hscale;
+  }
   for (int t = threadIdx.x; t < n; t += blockDim.x) {
     w.wr[t] /= hscale;
     w.wi[t] /= hscale;

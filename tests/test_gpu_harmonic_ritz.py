@@ -91,3 +91,50 @@ def test_harmonic_ritz_matches_scipy(ctx, kc, jj, k, seed):
         if Pp.shape[1] == P.shape[1]:
             sens = max(sens, gap(Pp, P))
     assert gap(PU, P) <= 100.0 * sens + 1e-10, (gap(PU, P), sens)
+
+
+def test_pencil_with_near_zero_eigenvalues(ctx):
+    """The second-cycle pencil of rGCROT(20,10) on a small skewed porous
+    problem: M'' has eigenvalues near zero, whose neighbouring diagonal
+    entries are tiny, so a purely relative deflation test never fires at the
+    double-float noise level of the subdiagonal. The Schur iteration must
+    still converge (status ok) and select the oracle's subspace."""
+    import oracle
+    import oracle.krylov as K
+    from problems.operators import sphere_pack, porous_skew_19pt
+    from problems.fields import rng_for
+    n = (14, 12, 10)
+    solid, _ = sphere_pack(n, 2.5, 0.3, rng_for(77, 3), max_attempts=20000)
+    grid, coef = porous_skew_19pt(n, np.where(solid, 1e-4, 1.0), 15.0)
+    op = oracle.Stencil(grid, coef)
+    b = np.random.default_rng(5).standard_normal(grid.n)
+    pens = []
+    orig = K.harmonic_ritz_update
+
+    def hook(op_, U, C, V, B, H, jj, k, return_theta=False):
+        kc = 0 if U is None else U.shape[1]
+        nn = kc + jj
+        G = np.zeros((nn + 1, nn))
+        F = np.zeros((nn + 1, nn))
+        if kc:
+            G[:kc, :kc] = np.eye(kc)
+            G[:kc, kc:] = B[:kc, :jj]
+            MU = U * op_.coef[0][:, None]
+            F[:kc, :kc] = C.T @ MU
+            F[kc:, :kc] = V[: jj + 1] @ MU
+        G[kc:, kc:] = H[: jj + 1, :jj]
+        F[kc:kc + jj, kc:] = np.eye(jj)
+        pens.append((G, F))
+        return orig(op_, U, C, V, B, H, jj, k, return_theta)
+
+    K.harmonic_ritz_update = hook
+    try:
+        oracle.rgcrot(op, b, tol=1e-8, m=20, k=10, max_matvec=40)
+    finally:
+        K.harmonic_ritz_update = orig
+    G, F = pens[1]
+    QC, PU = ctx.harmonic_ritz(torch.from_numpy(G), torch.from_numpy(F), 10)
+    PU = PU.cpu().numpy()
+    P, _ = reference_basis(G, F, 10)
+    assert PU.shape[1] == P.shape[1] == 9  # the third complex pair is split by the cut and dropped
+    assert gap(PU, P) <= 1e-8
