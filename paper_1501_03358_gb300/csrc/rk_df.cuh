@@ -167,4 +167,52 @@ __device__ __forceinline__ float2 df_sqrt_fast(float2 a) {
   return df_add(r2, make_float2(e.x * __fdividef(0.5f, r.hi), 0.f));
 }
 
+// Exact FP32 <-> FP64 conversions by IEEE-754 bit manipulation on the integer
+// pipe. On GB300 the hardware conversions issue at the FP64 rate (as slowly as
+// a DFMA), which makes them a large share of an FP64 kernel that reads and
+// writes double-float vectors. Normal numbers take the integer path; zeros,
+// subnormals, infinities and NaNs fall back to the hardware conversion.
+__device__ __forceinline__ double f32_to_f64_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e - 1u < 254u) {  // normal: widen the exponent bias, shift the mantissa
+    const unsigned long long bits = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                    ((unsigned long long)(e + 896u) << 52) |
+                                    ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)bits);
+  }
+  return (double)f;
+}
+
+// Round to nearest, ties to even (the FP32 value nearest to d).
+__device__ __forceinline__ float f64_to_f32_rn(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7ff) - 896;  // FP32 biased exponent
+  if (e >= 1 && e <= 254) {
+    const unsigned long long m = b & 0xfffffffffffffull;
+    unsigned mant = (unsigned)(m >> 29);
+    const unsigned rem = (unsigned)(m & 0x1fffffffu);
+    const unsigned half = 0x10000000u;
+    mant += (rem > half || (rem == half && (mant & 1u))) ? 1u : 0u;
+    unsigned ex = (unsigned)e;
+    if (mant == 0x800000u) {  // the rounding carried into the exponent
+      mant = 0;
+      ex += 1;
+    }
+    if (ex <= 254u) return __uint_as_float((unsigned)((b >> 32) & 0x80000000u) | (ex << 23) | mant);
+  }
+  return __double2float_rn(d);
+}
+
+// double-float <-> FP64 with the exact conversions above (the same values as
+// df_to_double / df_from_double)
+__device__ __forceinline__ double df_to_double_i(float2 v) {
+  return f32_to_f64_exact(v.x) + f32_to_f64_exact(v.y);
+}
+__device__ __forceinline__ float2 df_from_double_i(double d) {
+  const float h = f64_to_f32_rn(d);
+  const float l = f64_to_f32_rn(d - f32_to_f64_exact(h));
+  return make_float2(h, l);
+}
+
 }  // namespace rk

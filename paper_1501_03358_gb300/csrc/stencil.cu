@@ -32,17 +32,14 @@ __device__ __forceinline__ double ld_val(const VT* p, int64_t q);
 template <>
 __device__ __forceinline__ double ld_val<double>(const double* p, int64_t q) { return __ldg(&p[q]); }
 template <>
-__device__ __forceinline__ double ld_val<float2>(const float2* p, int64_t q) { return df_to_double(__ldg(&p[q])); }
+__device__ __forceinline__ double ld_val<float2>(const float2* p, int64_t q) { return df_to_double_i(__ldg(&p[q])); }
 
 template <typename YT>
 __device__ __forceinline__ void st_val(YT* p, int64_t q, double w);
 template <>
 __device__ __forceinline__ void st_val<double>(double* p, int64_t q, double w) { p[q] = w; }
 template <>
-__device__ __forceinline__ void st_val<float2>(float2* p, int64_t q, double w) {
-  const df v = df_from_double(w);
-  p[q] = make_float2(v.hi, v.lo);
-}
+__device__ __forceinline__ void st_val<float2>(float2* p, int64_t q, double w) { p[q] = df_from_double_i(w); }
 
 template <int S, int MODE, typename VT = double, typename YT = double>
 __global__ void __launch_bounds__(kTX* kTY) k_stencil(Dims d, const double* __restrict__ coef,
@@ -116,7 +113,7 @@ __global__ void __launch_bounds__(kTX* kTY) k_stencil(Dims d, const double* __re
         }
         if (MODE == ST_RESID) w = __ldg(&b[p]) - w;
         st_val<YT>(y, p, w);
-        acc2 = fma(w, w, acc2);
+        if (part != nullptr) acc2 = fma(w, w, acc2);
       }
       __syncthreads();
     }
