@@ -291,22 +291,34 @@ __global__ void __launch_bounds__(kRedThreads) k_dfdots2(DFDots2Args a, int64_t 
     const int rr = (int)min((int64_t)kD2Rows, end - r0);
     const float2* sb = d2buf + (int64_t)slot * kD2Vecs * kD2Rows;
     if (rr == kD2Rows) {
-      // full stage: two rows per thread, no conditions
+      // full stage: two rows per thread, no conditions; lazy double-float
+      // accumulation, renormalised once per stage
 #pragma unroll
       for (int h = 0; h < kD2Rows / kRedThreads; ++h) {
         const int r = threadIdx.x + h * kRedThreads;
         const float2 pv = sb[r], wv = sb[kD2Rows + r];
         if (scal) {
-          df_mac(s0h, s0l, pv.x, pv.y, pv.x, pv.y);
-          df_mac(s1h, s1l, pv.x, pv.y, wv.x, wv.y);
-          df_mac(s2h, s2l, wv.x, wv.y, wv.x, wv.y);
+          df_mac_lazy(s0h, s0l, pv.x, pv.y, pv.x, pv.y);
+          df_mac_lazy(s1h, s1l, pv.x, pv.y, wv.x, wv.y);
+          df_mac_lazy(s2h, s2l, wv.x, wv.y, wv.x, wv.y);
         } else {
 #pragma unroll
           for (int q = 0; q < kDotGroup; ++q) {
             const float2 v = sb[(2 + q) * kD2Rows + r];
-            df_mac(ph[q], pl[q], v.x, v.y, pv.x, pv.y);
-            df_mac(wh[q], wl[q], v.x, v.y, wv.x, wv.y);
+            df_mac_lazy(ph[q], pl[q], v.x, v.y, pv.x, pv.y);
+            df_mac_lazy(wh[q], wl[q], v.x, v.y, wv.x, wv.y);
           }
+        }
+      }
+      if (scal) {
+        df_renorm(s0h, s0l);
+        df_renorm(s1h, s1l);
+        df_renorm(s2h, s2l);
+      } else {
+#pragma unroll
+        for (int q = 0; q < kDotGroup; ++q) {
+          df_renorm(ph[q], pl[q]);
+          df_renorm(wh[q], wl[q]);
         }
       }
     } else {
@@ -410,9 +422,11 @@ __global__ void __launch_bounds__(kRedThreads) k_dfupdate2(DFUpdate2Args a) {
         v[u] = q + u < a.nq ? __ldg(col + (int64_t)(q + u) * a.ld) : make_float2(0.f, 0.f);
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        df_mac(ah, al, v[u].x, v[u].y, ca[q + u].x, ca[q + u].y);
-        df_mac(bh, bl, v[u].x, v[u].y, cb[q + u].x, cb[q + u].y);
+        df_mac_lazy(ah, al, v[u].x, v[u].y, ca[q + u].x, ca[q + u].y);
+        df_mac_lazy(bh, bl, v[u].x, v[u].y, cb[q + u].x, cb[q + u].y);
       }
+      df_renorm(ah, al);
+      df_renorm(bh, bl);
     }
     const float2 vf = df_mul(make_float2(ah, al), s0);
     const float2 pn = df_add(df_mul(make_float2(bh, bl), s1), df_neg(df_mul(vf, s2)));
@@ -470,13 +484,22 @@ __global__ void __launch_bounds__(256) k_dfgemm2(DFGemmArgs a, int tr, int ncp) 
 #pragma unroll
     for (int u = 0; u < CB; ++u) sh[u] = sl[u] = 0.f;
     const float2* pt = PT + c0;
-    // B columns first (they carry the row scale), then the scale, then A
-    for (int q = a.na; q < np; ++q) {
-      const float2 xv = X[q * tr + r];
-      const float2* pq = pt + (int64_t)q * ncp;
+    // B columns first (they carry the row scale), then the scale, then A;
+    // lazy double-float accumulation, renormalised every 8 terms
+    auto run = [&](int q0, int q1) {
+      for (int qb = q0; qb < q1; qb += 8) {
+        const int qe = min(qb + 8, q1);
+        for (int q = qb; q < qe; ++q) {
+          const float2 xv = X[q * tr + r];
+          const float2* pq = pt + (int64_t)q * ncp;
 #pragma unroll
-      for (int u = 0; u < CB; ++u) df_mac(sh[u], sl[u], xv.x, xv.y, pq[u].x, pq[u].y);
-    }
+          for (int u = 0; u < CB; ++u) df_mac_lazy(sh[u], sl[u], xv.x, xv.y, pq[u].x, pq[u].y);
+        }
+#pragma unroll
+        for (int u = 0; u < CB; ++u) df_renorm(sh[u], sl[u]);
+      }
+    };
+    run(a.na, np);
     if (a.bscale && a.nb > 0) {
       const float2 sc = SC[r];
 #pragma unroll
@@ -486,12 +509,7 @@ __global__ void __launch_bounds__(256) k_dfgemm2(DFGemmArgs a, int tr, int ncp) 
         sl[u] = v.y;
       }
     }
-    for (int q = 0; q < a.na; ++q) {
-      const float2 xv = X[q * tr + r];
-      const float2* pq = pt + (int64_t)q * ncp;
-#pragma unroll
-      for (int u = 0; u < CB; ++u) df_mac(sh[u], sl[u], xv.x, xv.y, pq[u].x, pq[u].y);
-    }
+    run(0, a.na);
     const int64_t i = r0 + r;
     if (i < a.n) {
 #pragma unroll
@@ -626,6 +644,7 @@ __global__ void __launch_bounds__(256) k_dfgram2(DFGramArgs a, int ob0, int nob,
       __syncthreads();
     }
     if (active) {
+      int cnt = 0;
       for (int r = slice; r < kGramTR; r += ns) {
         float2 xv[4], yv[4];
 #pragma unroll
@@ -636,8 +655,16 @@ __global__ void __launch_bounds__(256) k_dfgram2(DFGramArgs a, int ob0, int nob,
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
-          for (int v = 0; v < 4; ++v) df_mac(sh[u * 4 + v], sl[u * 4 + v], xv[u].x, xv[u].y, yv[v].x, yv[v].y);
+          for (int v = 0; v < 4; ++v)
+            df_mac_lazy(sh[u * 4 + v], sl[u * 4 + v], xv[u].x, xv[u].y, yv[v].x, yv[v].y);
+        if (++cnt == 8) {  // lazy accumulation, renormalised every 8 rows
+          cnt = 0;
+#pragma unroll
+          for (int t = 0; t < 16; ++t) df_renorm(sh[t], sl[t]);
+        }
       }
+#pragma unroll
+      for (int t = 0; t < 16; ++t) df_renorm(sh[t], sl[t]);
     }
   }
   // sum the slices: reuse the tile storage as [ns][nob][16] DF values

@@ -215,4 +215,28 @@ __device__ __forceinline__ float2 df_from_double_i(double d) {
   return make_float2(h, l);
 }
 
+// Lazy accumulation for short dense blocks (the recycle GEMM and Gram): the
+// products' leading parts are added to s exactly (TwoSum) and every
+// lower-order piece (TwoSum error, product error, cross terms) goes into the
+// FP32 companion c; df_renorm folds c back into (s, c) as a normalised pair.
+// Renormalising every 8 terms keeps |c| within a few ulp of s, so the error
+// stays within a small constant of the renormalising df_mac (11 instead of
+// 15 FP32 instructions per multiply-add).
+__device__ __forceinline__ void df_mac_lazy(float& s, float& c, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  const float t = __fadd_rn(s, p);
+  const float bb = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, e));
+}
+__device__ __forceinline__ void df_renorm(float& s, float& c) {
+  const float t = __fadd_rn(s, c);
+  c = __fsub_rn(c, __fsub_rn(t, s));
+  s = t;
+}
+
 }  // namespace rk

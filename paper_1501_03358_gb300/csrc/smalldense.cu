@@ -100,13 +100,22 @@ __global__ void k_dcgs_coef(SolveState* s, SmallBuffers b, int kc, int j, int fi
     }
     for (int l = j + threadIdx.x; l <= b.m; l += blockDim.x) b.H[l + c * ldh] = l == j ? bprev * alpha : 0.0;
     __syncthreads();
+    // the rotation chain below is serial: stage its operands in shared memory
+    extern __shared__ double gv[];  // column (m + 2) | cs (m) | sn (m)
+    double* R = gv;
+    double* scs = gv + b.m + 2;
+    double* ssn = scs + b.m;
+    for (int l = threadIdx.x; l <= c + 1; l += blockDim.x) R[l] = b.H[l + c * ldh];
+    for (int i = threadIdx.x; i < c; i += blockDim.x) {
+      scs[i] = b.cs[i];
+      ssn[i] = b.sn[i];
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
       // progressive Givens QR of column c; |g_{c+1}| is the residual estimate
-      double* R = b.R + c * ldh;
-      for (int l = 0; l <= c + 1; ++l) R[l] = b.H[l + c * ldh];
       for (int i = 0; i < c; ++i) {
-        const double t = b.cs[i] * R[i] + b.sn[i] * R[i + 1];
-        R[i + 1] = -b.sn[i] * R[i] + b.cs[i] * R[i + 1];
+        const double t = scs[i] * R[i] + ssn[i] * R[i + 1];
+        R[i + 1] = -ssn[i] * R[i] + scs[i] * R[i + 1];
         R[i] = t;
       }
       double cg = 1.0, sg = 0.0, rr = R[c];
@@ -119,6 +128,7 @@ __global__ void k_dcgs_coef(SolveState* s, SmallBuffers b, int kc, int j, int fi
       b.sn[c] = sg;
       R[c] = rr;
       R[c + 1] = 0.0;
+      for (int l = 0; l <= c + 1; ++l) b.R[l + c * ldh] = R[l];
       b.g[c + 1] = -sg * b.g[c];
       b.g[c] = cg * b.g[c];
       const double est = fabs(b.g[c + 1]);
@@ -161,21 +171,48 @@ __global__ void k_dcgs_coef(SolveState* s, SmallBuffers b, int kc, int j, int fi
   }
 }
 
-__global__ void k_cycle_solve(SolveState* s, SmallBuffers b, int kc) {
-  if (threadIdx.x != 0) return;
+// Lines 12-12a: y = R^{-1} g (the Givens-rotated least squares), z = -B y,
+// and the coefficients of the solution update. Column-oriented back
+// substitution: the reciprocals of the diagonal are formed in parallel,
+// then per column one scalar and a parallel update of the right-hand side
+// (R and g staged in shared memory); z one thread per row of B.
+constexpr int kSolveThreads = 128;
+constexpr int kSolveStageMax = 72;  // R staged in shared memory up to m = 72
+template <bool STAGED>
+__global__ void __launch_bounds__(kSolveThreads) k_cycle_solve(SolveState* s, SmallBuffers b, int kc) {
+  extern __shared__ double cs_sm[];  // [R (jj x jj, ld jj)] | g' (jj) | 1/r_ll (jj) | y (jj)
   const int jj = s->jj;
   const int ldh = b.m + 1;
-  for (int i = jj - 1; i >= 0; --i) {
-    double t = b.g[i];
-    for (int l = i + 1; l < jj; ++l) t -= b.R[i + l * ldh] * b.y[l];
-    b.y[i] = t / b.R[i + i * ldh];
+  const double* R = STAGED ? cs_sm : b.R;
+  const int ldr = STAGED ? jj : ldh;
+  double* gp = cs_sm + (STAGED ? (size_t)jj * jj : 0);
+  double* rinv = gp + jj;
+  double* y = rinv + jj;
+  if (STAGED)
+    for (int t = threadIdx.x; t < jj * jj; t += blockDim.x) {
+      const int r = t % jj, c = t / jj;
+      cs_sm[t] = r <= c ? b.R[r + c * ldh] : 0.0;
+    }
+  for (int t = threadIdx.x; t < jj; t += blockDim.x) {
+    gp[t] = b.g[t];
+    rinv[t] = 1.0 / b.R[t + t * ldh];
   }
-  for (int q = 0; q < kc; ++q) {
+  __syncthreads();
+  for (int l = jj - 1; l >= 0; --l) {
+    const double yl = gp[l] * rinv[l];
+    for (int i = threadIdx.x; i < l; i += blockDim.x) gp[i] = fma(-R[i + (int64_t)l * ldr], yl, gp[i]);
+    if (threadIdx.x == 0) y[l] = yl;
+    __syncthreads();
+  }
+  for (int q = threadIdx.x; q < kc; q += blockDim.x) {
     double z = 0.0;
-    for (int l = 0; l < jj; ++l) z = fma(b.B[q + (int64_t)l * b.kmax], b.y[l], z);
+    for (int l = 0; l < jj; ++l) z = fma(b.B[q + (int64_t)l * b.kmax], y[l], z);
     b.xcoef[q] = -z;  // z = -B y (line 12a)
   }
-  for (int l = 0; l < jj; ++l) b.xcoef[kc + l] = b.sv[l] * b.y[l];
+  for (int l = threadIdx.x; l < jj; l += blockDim.x) {
+    b.y[l] = y[l];
+    b.xcoef[kc + l] = b.sv[l] * y[l];
+  }
 }
 
 // ------------------------------------------------------------ harmonic Ritz
@@ -398,7 +435,7 @@ __device__ void hessenberg_df(float2* H, int ldh, float2* Z, int n, float2* v) {
 // eigenvalues to wr, wi (FP64). On more than 40 n iterations *sfail is set.
 __device__ void francis_df(float2* Hd, int ldh, float2* Zd, int n, double* wr, double* wi, float hn, int* su,
                            int* sl, int* siter, int* stotal, int* sfail) {
-  __shared__ float2 v3[3], tau3, rot[2];
+  __shared__ float2 v3[3], tau3, rot[2], fxyz[3];
   __shared__ int c_real;
   const float eps = 7.105427357601002e-15f;    // 2^-47
   const float floor_abs = 1.4210854715202004e-14f * hn;  // 2^-46 max |h_ij|
@@ -517,8 +554,13 @@ __device__ void francis_df(float2* Hd, int ldh, float2* Zd, int n, double* wr, d
     }
     __syncthreads();
     if (*sfail) break;
+    // the bulge chase: each step applies its reflector from the left (rows
+    // kk..kk+2) and from the right (columns kk..kk+2, Schur vectors on other
+    // warps); the threads that update rows kk+1..kk+3 of column kk publish
+    // the new bulge entries in fxyz, and every thread then forms the next
+    // reflector itself (same inputs, same result), one barrier per step less
+    float2 tau = tau3, v1 = v3[1], v2 = v3[2];
     for (int kk = l; kk <= u - 2; ++kk) {
-      const float2 tau = tau3, v1 = v3[1], v2 = v3[2];
       if (tau.x != 0.f) {
         const int q = kk > l ? kk - 1 : l;
         for (int j = q + tid; j < n; j += blockDim.x) {
@@ -537,6 +579,7 @@ __device__ void francis_df(float2* Hd, int ldh, float2* Zd, int n, double* wr, d
             HD(i, kk) = h0;
             HD(i, kk + 1) = h1;
             HD(i, kk + 2) = h2;
+            if (i > kk) fxyz[i - kk - 1] = h0;
           }
         } else {
           for (int i = tid - 64; i < n; i += (int)blockDim.x - 64) {
@@ -547,21 +590,22 @@ __device__ void francis_df(float2* Hd, int ldh, float2* Zd, int n, double* wr, d
             ZD(i, kk + 2) = z2;
           }
         }
+      } else {
+        __syncthreads();  // every thread has formed its reflector from fxyz
+        if (tid == 0)
+          for (int i = 0; i < 3 && kk + 1 + i <= u; ++i) fxyz[i] = HD(kk + 1 + i, kk);
       }
       __syncthreads();
-      if (tid == 0) {
-        const float2 fx = HD(kk + 1, kk), fy = HD(kk + 2, kk);
-        if (kk < u - 2) {
-          house_small_df(fx, fy, HD(kk + 3, kk), 3, v3, &tau3);
-        } else {
-          house_small_df(fx, fy, make_float2(0.f, 0.f), 2, v3, &tau3);
-        }
-      }
-      __syncthreads();
+      float2 vv[3];
+      if (kk < u - 2)
+        house_small_df(fxyz[0], fxyz[1], fxyz[2], 3, vv, &tau);
+      else
+        house_small_df(fxyz[0], fxyz[1], make_float2(0.f, 0.f), 2, vv, &tau);
+      v1 = vv[1];
+      v2 = vv[2];
     }
-    // final 2-vector reflector on rows / columns u-1, u (computed above)
+    // final 2-vector reflector on rows / columns u-1, u (formed above)
     {
-      const float2 tau = tau3, v1 = v3[1];
       if (tau.x != 0.f) {
         const int q = u - 2 >= l ? u - 2 : l;
         for (int j = q + tid; j < n; j += blockDim.x) {
@@ -588,7 +632,6 @@ __device__ void francis_df(float2* Hd, int ldh, float2* Zd, int n, double* wr, d
         }
       }
     }
-    __syncthreads();
     // entries below the subdiagonal are zero by construction
     if (tid == 0) {
       for (int i = l + 2; i <= u; ++i) {
@@ -1059,12 +1102,17 @@ size_t hr_doubles_host(int n) { return (size_t)2 * (n + 1) * n + (size_t)3 * n *
 size_t harmonic_ritz_ws_doubles(int n) { return hr_doubles_host(n); }
 
 cudaError_t launch_dcgs_coef(SolveState* s, SmallBuffers b, int kc, int j, int final_pass, cudaStream_t st) {
-  k_dcgs_coef<<<1, 128, 0, st>>>(s, b, kc, j, final_pass);
+  k_dcgs_coef<<<1, 128, (3 * (size_t)b.m + 2) * sizeof(double), st>>>(s, b, kc, j, final_pass);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cycle_solve(SolveState* s, SmallBuffers b, int kc, cudaStream_t st) {
-  k_cycle_solve<<<1, 32, 0, st>>>(s, b, kc);
+  if (b.m <= kSolveStageMax) {
+    const size_t smem = ((size_t)b.m * b.m + 3 * (size_t)b.m) * sizeof(double);
+    k_cycle_solve<true><<<1, kSolveThreads, smem, st>>>(s, b, kc);
+  } else {
+    k_cycle_solve<false><<<1, kSolveThreads, 3 * (size_t)b.m * sizeof(double), st>>>(s, b, kc);
+  }
   return cudaGetLastError();
 }
 
