@@ -210,38 +210,47 @@ __global__ void __launch_bounds__(kRedThreads) k_dfupdate(DFUpdateArgs a) {
 // y = groups of kDotGroup columns of Q plus one slice for the three
 // scalars. A block streams its vectors (p, w and its kDotGroup columns)
 // through a kD2Stages-deep ring of shared-memory stages of kD2Rows rows,
-// filled by bulk asynchronous copies (one thread issues them, an mbarrier
-// per stage completes them), so the loads in flight do not depend on
-// registers. Each thread carries 2 x kDotGroup double-float chains that share
+// filled by bulk asynchronous copies: a producer warp refills a stage as soon
+// as every consumer warp has released it ("empty" mbarrier) and the copies
+// complete on the stage's "full" mbarrier, so the consumers never wait on a
+// block-wide barrier and the loads in flight do not depend on registers. Each thread carries 2 x kDotGroup double-float chains that share
 // every value of Q. Each column group has its own completion counter: the
 // last row block of a group sums that group's partials (fixed order).
-__device__ __forceinline__ bool arrive_last_x(unsigned* counter, int* flag_smem) {
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned t = atomicAdd(counter, 1u);
-    *flag_smem = (t == gridDim.x - 1) ? 1 : 0;
-  }
-  __syncthreads();
-  const bool last = *flag_smem != 0;
-  if (last) {
-    __threadfence();
-    if (threadIdx.x == 0) *counter = 0u;
-  }
-  return last;
-}
-
 constexpr int kD2Rows = 512;   // rows per stage (2 per thread)
 constexpr int kD2Stages = 3;
 constexpr int kD2Vecs = 2 + kDotGroup;
 constexpr size_t kD2Smem = (size_t)kD2Stages * kD2Vecs * kD2Rows * sizeof(float2);
 
-__global__ void __launch_bounds__(kRedThreads) k_dfdots2(DFDots2Args a, int64_t rpb) {
+// Block reduction of per-thread DF values for ncol columns among the first
+// kRedThreads threads only (named barrier; the producer warp is absent).
+__device__ __forceinline__ void consumer_df_reduce_cols(float2* vals, int ncol, float2 (*red)[kDFCols],
+                                                        double* dst) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < kDFCols; ++q) {
+    if (q < ncol) {
+      const float2 s = df_warp_sum(vals[q]);
+      if (lane == 0) red[wid][q] = s;
+    }
+  }
+  named_sync(kRedThreads);
+  if (threadIdx.x < ncol) {
+    float2 s = red[0][threadIdx.x];
+    for (int w = 1; w < kWarps; ++w) s = df_add(s, red[w][threadIdx.x]);
+    dst[threadIdx.x] = df_to_double(s);
+  }
+  named_sync(kRedThreads);
+}
+
+constexpr int kD2Threads = kRedThreads + 32;  // 8 consumer warps + 1 producer warp
+
+__global__ void __launch_bounds__(kD2Threads) k_dfdots2(DFDots2Args a, int64_t rpb) {
   if (a.skip_flag != nullptr && *a.skip_flag != 0) return;
   extern __shared__ __align__(128) float2 d2buf[];  // [stage][vector][row]
   __shared__ __align__(8) uint64_t full[kD2Stages];
+  __shared__ __align__(8) uint64_t empty[kD2Stages];
   __shared__ float2 red[kWarps][kDFCols];
-  __shared__ int lastflag, abort_flag;
+  __shared__ int lastflag;
   const int ncols = 2 * a.nq + 3;
   const int ngroups = (a.nq + kDotGroup - 1) / kDotGroup;
   const bool scal = (int)blockIdx.y >= ngroups;
@@ -257,24 +266,34 @@ __global__ void __launch_bounds__(kRedThreads) k_dfdots2(DFDots2Args a, int64_t 
 #pragma unroll
   for (int q = 0; q < kDotGroup; ++q) src[2 + q] = a.Q + (int64_t)(q < nc ? c0 + q : 0) * a.ld;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kD2Stages; ++s) mbar_init(&full[s], 1);
+    for (int s = 0; s < kD2Stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kWarps);
+    }
     mbar_init_fence();
-    abort_flag = 0;
   }
   __syncthreads();
-  // stage s: rows [begin + s*kD2Rows, +rr); an odd last row is read directly
-  auto issue = [&](int s) {
-    const int slot = s % kD2Stages;
-    const int64_t r0 = begin + (int64_t)s * kD2Rows;
-    const int64_t rr = min((int64_t)kD2Rows, end - r0);
-    const unsigned bytes = (unsigned)((rr & ~(int64_t)1) * sizeof(float2));
-    mbar_arrive_expect_tx(&full[slot], bytes * nvec);
-    if (bytes)
-      for (int v = 0; v < nvec; ++v)
-        bulk_g2s(d2buf + ((int64_t)slot * kD2Vecs + v) * kD2Rows, src[v] + r0, bytes, &full[slot]);
-  };
-  if (threadIdx.x == 0)
-    for (int s = 0; s < kD2Stages && s < nst; ++s) issue(s);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (wid == kWarps) {
+    // producer: refill a stage once every consumer warp has released it
+    if (lane == 0) {
+      for (int s = 0; s < nst; ++s) {
+        const int slot = s % kD2Stages;
+        if (s >= kD2Stages && !mbar_wait_bounded(&empty[slot], (unsigned)((s / kD2Stages - 1) & 1))) {
+          if (a.err) atomicExch(a.err, 2);
+          break;
+        }
+        const int64_t r0 = begin + (int64_t)s * kD2Rows;
+        const int64_t rr = min((int64_t)kD2Rows, end - r0);
+        const unsigned bytes = (unsigned)((rr & ~(int64_t)1) * sizeof(float2));
+        mbar_arrive_expect_tx(&full[slot], bytes * nvec);
+        if (bytes)
+          for (int v = 0; v < nvec; ++v)
+            bulk_g2s(d2buf + ((int64_t)slot * kD2Vecs + v) * kD2Rows, src[v] + r0, bytes, &full[slot]);
+      }
+    }
+    return;
+  }
   float ph[kDotGroup], pl[kDotGroup], wh[kDotGroup], wl[kDotGroup];
 #pragma unroll
   for (int q = 0; q < kDotGroup; ++q) ph[q] = pl[q] = wh[q] = wl[q] = 0.f;
@@ -282,11 +301,9 @@ __global__ void __launch_bounds__(kRedThreads) k_dfdots2(DFDots2Args a, int64_t 
   for (int s = 0; s < nst; ++s) {
     const int slot = s % kD2Stages;
     if (!mbar_wait_bounded(&full[slot], (unsigned)((s / kD2Stages) & 1))) {
-      abort_flag = 1;
       if (a.err) atomicExch(a.err, 1);
+      break;
     }
-    __syncthreads();
-    if (abort_flag) break;
     const int64_t r0 = begin + (int64_t)s * kD2Rows;
     const int rr = (int)min((int64_t)kD2Rows, end - r0);
     const float2* sb = d2buf + (int64_t)slot * kD2Vecs * kD2Rows;
@@ -340,8 +357,8 @@ __global__ void __launch_bounds__(kRedThreads) k_dfdots2(DFDots2Args a, int64_t 
         }
       }
     }
-    __syncthreads();  // the stage has been read: refill it
-    if (threadIdx.x == 0 && s + kD2Stages < nst) issue(s + kD2Stages);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[slot]);  // this warp has read the stage
   }
   double* prow = a.part + (int64_t)blockIdx.x * ncols;
   float2 vals[kDFCols];
@@ -349,10 +366,10 @@ __global__ void __launch_bounds__(kRedThreads) k_dfdots2(DFDots2Args a, int64_t 
   if (!scal) {
 #pragma unroll
     for (int q = 0; q < kDotGroup; ++q) vals[q] = make_float2(ph[q], pl[q]);
-    block_df_reduce_cols(vals, nc, red, prow + c0);
+    consumer_df_reduce_cols(vals, nc, red, prow + c0);
 #pragma unroll
     for (int q = 0; q < kDotGroup; ++q) vals[q] = make_float2(wh[q], wl[q]);
-    block_df_reduce_cols(vals, nc, red, prow + a.nq + c0);
+    consumer_df_reduce_cols(vals, nc, red, prow + a.nq + c0);
     cA = c0;
     nA = nc;
     cB = a.nq + c0;
@@ -361,12 +378,21 @@ __global__ void __launch_bounds__(kRedThreads) k_dfdots2(DFDots2Args a, int64_t 
     vals[0] = make_float2(s0h, s0l);
     vals[1] = make_float2(s1h, s1l);
     vals[2] = make_float2(s2h, s2l);
-    block_df_reduce_cols(vals, 3, red, prow + 2 * a.nq);
+    consumer_df_reduce_cols(vals, 3, red, prow + 2 * a.nq);
     cA = 2 * a.nq;
     nA = 3;
   }
-  if (arrive_last_x(a.counter + blockIdx.y, &lastflag)) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // the last row block of this group sums the group's partials
+  __threadfence();
+  named_sync(kRedThreads);
+  if (threadIdx.x == 0) {
+    const unsigned t = atomicAdd(a.counter + blockIdx.y, 1u);
+    lastflag = (t == gridDim.x - 1) ? 1 : 0;
+  }
+  named_sync(kRedThreads);
+  if (lastflag) {
+    __threadfence();
+    if (threadIdx.x == 0) a.counter[blockIdx.y] = 0u;
     for (int t = wid; t < nA + nB; t += kWarps) {
       const int c = t < nA ? cA + t : cB + (t - nA);
       double sum = 0.0;
@@ -779,7 +805,7 @@ cudaError_t launch_dfdots2(const DFDots2Args& a, cudaStream_t st) {
   const int64_t per = (a.n + xb - 1) / xb;
   const int64_t rpb = (per + kD2Rows - 1) / kD2Rows * kD2Rows;  // even: 16-byte aligned stages
   const dim3 grid(xb, (a.nq + kDotGroup - 1) / kDotGroup + 1);
-  k_dfdots2<<<grid, kRedThreads, kD2Smem, st>>>(a, rpb);
+  k_dfdots2<<<grid, kD2Threads, kD2Smem, st>>>(a, rpb);
   return cudaGetLastError();
 }
 
