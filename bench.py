@@ -37,6 +37,8 @@ WORKLOADS = {
     "channel128": (2, 128, "rGCROT", 40, 20),
     "porous192": (3, 192, "hybrid", 40, 20),
     "convdiff32": (1, 32, "rGCROT", 30, 10),
+    # the channel at 96^3: a smaller case of the same kernels (profiling)
+    "channel96": (2, 96, "rGCROT", 40, 20),
     # batched uneven set: 64 porous problems, edges log-uniform in [24, 96]
     "batch64": (4, 0, "hybrid", 40, 10),
     # serving: resident problems, Poisson requests, memory budget with eviction
@@ -45,7 +47,7 @@ WORKLOADS = {
 # Matrix-vector products per solve of the channel128 sequence in steady state
 # (steps 3-12 of the sequence), measured on the GB300 arm; used only to turn
 # the reference arm's per-cycle time into solves/s.
-MV_PER_SOLVE = {"channel128": 1400.0, "convdiff32": 60.0, "porous192": 400.0}
+MV_PER_SOLVE = {"channel128": 1500.0, "channel96": 1100.0, "convdiff32": 60.0, "porous192": 400.0}
 
 
 def load_peaks():
@@ -281,6 +283,12 @@ def run_ours(args, ws, rank, local):
 
     peaks, peak_src = load_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    # DRAM traffic of one launch over its algorithmic bytes, from one ncu
+    # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the same
+    # kernels on the 96^3 channel: dots at nq = 40 (335.2 MB for 297.3 MB),
+    # update at nq = 58 (437.9 MB for 438.8 MB). Every operand is far larger
+    # than L2 at both sizes, so the ratio carries over to 128^3.
+    traffic_ratio = {"dots": 335.2 / 297.3, "update": 437.9 / 438.8}
     # dominant kernel class by time
     dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
     dname, d = dom
@@ -304,7 +312,12 @@ def run_ours(args, ws, rank, local):
         "matvecs_per_solve": statistics.mean(mv), "relres_max": max(i["relres_true"] for i in tinfo),
         "all_converged": all(i["status"] == 0 for i in tinfo),
         "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
+                     "frac": achieved / hbm_peak,
+                     "traffic": (traffic_ratio[dname] * d["bytes"] / max(d["launches"], 1)
+                                 if dname in traffic_ratio else None),
+                     "traffic_source": "ncu DRAM bytes / algorithmic bytes on the 96^3 channel x this run's "
+                                       "algorithmic bytes per launch" if dname in traffic_ratio else None,
+                     "peak_source": peak_src,
                      "launches": d["launches"], "avg_launch_us": 1000.0 * d["ms"] / max(d["launches"], 1),
                      "bytes_per_launch": d["bytes"] / max(d["launches"], 1)},
         "kernel_classes": {kname: {"ms": round(v["ms"], 3), "launches": v["launches"],
