@@ -47,6 +47,10 @@ WORKLOADS = {
 # Matrix-vector products per solve of the channel128 sequence in steady state
 # (steps 3-12 of the sequence), measured on the GB300 arm; used only to turn
 # the reference arm's per-cycle time into solves/s.
+# arithmetic of the path per precision: FP64 operator and true residual with
+# double-float basis and projections; the same with the recurrences' products
+# in double-float; or with those products in FP32
+DTYPES = {"fp64": "f64", "df": "f64+df64-operator", "mixed": "f64+f32-operator"}
 MV_PER_SOLVE = {"channel128": 1500.0, "channel96": 1100.0, "convdiff32": 60.0, "porous192": 400.0}
 
 
@@ -301,7 +305,7 @@ def run_ours(args, ws, rank, local):
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": K, "warmup": W,
         "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f64+f32-operator", "data": "synthetic",
+        "dtype": DTYPES[args.precision], "data": "synthetic",
         "config": {"workload": args.workload, "grid": [edge] * 3, "stencil": cfg.S, "solver": f"{mode}({m},{k})",
                    "precision": args.precision,
                    "tol": 1e-8, "preroll_steps": P, "preroll_matvec_cap": args.preroll_matvec,
@@ -422,7 +426,7 @@ def run_batch(args, ws, rank, local):
     line = {
         "metric": METRIC, "value": ws * nsol / (ms * 1e-3), "unit": "solves/s", "n_gpus": ws, "steps": K,
         "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if prec == "fp64" else "f64+f32-operator", "data": "synthetic",
+        "dtype": DTYPES[prec], "data": "synthetic",
         "config": {"workload": "batch64", "problems": len(cfgs), "cells_total": ntot,
                    "edges": "log-uniform [24, 96] per axis", "stencil": 19, "solver": f"{mode}({m},{k})",
                    "hybrid_switch": 5, "precision": prec, "tol": 1e-8, "threads": args.threads or min(len(cfgs), 16),
@@ -575,8 +579,9 @@ def main():
     ap.add_argument("--preroll", type=int, default=12,
                     help="untimed sequence steps before warm-up (stops at the first converged one)")
     ap.add_argument("--preroll-matvec", type=int, default=4000, help="matvec cap of each pre-roll solve")
-    ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
-                    help="fp64: FP64 operator, double-float projections; mixed: FP32 inner operator (A11). "
+    ap.add_argument("--precision", default=None, choices=["fp64", "df", "mixed"],
+                    help="fp64: FP64 operator, double-float projections; df: double-float operator in the "
+                         "recurrences; mixed: FP32 inner operator (A11). "
                          "Default fp64 for the single-sequence workloads, mixed for batch64 and serve")
     ap.add_argument("--nprob", type=int, default=None, help="problems (batch64: 64; serve: 12)")
     ap.add_argument("--threads", type=int, default=0, help="rk_solve_batch worker threads (0: min(n, 16))")

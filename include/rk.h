@@ -62,7 +62,7 @@ typedef enum {
 } rk_status;
 
 typedef enum { RK_GMRES = 0, RK_RGCROT = 1, RK_RBICGSTAB = 2, RK_HYBRID = 3 } rk_mode;
-typedef enum { RK_FP64 = 0, RK_MIXED = 1 } rk_precision;
+typedef enum { RK_FP64 = 0, RK_MIXED = 1, RK_DF = 2 } rk_precision;
 
 typedef struct {
   int32_t nx, ny, nz;
@@ -80,7 +80,10 @@ typedef struct {
   int32_t precision;     /* rk_precision: RK_FP64, or RK_MIXED = the A M^{-1} products of the
                             recurrences with an FP32 copy of the operator (FP32 accumulation),
                             everything else as in RK_FP64, b - A x recomputed in FP64 every
-                            cycle / on convergence (residual replacement) */
+                            cycle / on convergence (residual replacement); or RK_DF = those
+                            products with a double-float copy of the operator (bands and
+                            1/a_pp rounded to ~48 bits once, double-float accumulation in band
+                            order), everything else as in RK_FP64 */
   int32_t update_recycle;/* rGCROT: 1 = update U, C after every cycle (line 14a), 0 = keep */
   int32_t reserved;
 } rk_solve_params;
@@ -165,7 +168,11 @@ int rk_solve(rk_problem* p, const double* b, double* x, const rk_solve_params* p
  * precond = 1: y = A (M^{-1} v); 0: y = A v; 2: the FP32 operator of
  * RK_MIXED, y = A32 (M32^{-1} v) with A32, M32^{-1} the coefficients and
  * 1/a_pp rounded to FP32, v rounded to FP32, FP32 accumulation in band order,
- * the result widened to FP64. And r = b - A x. All vectors device, N doubles.
+ * the result widened to FP64; 3: the double-float operator of RK_DF,
+ * y = A_df (M_df^{-1} v) with v rounded to double-float and the result
+ * widened to FP64 (exact). Other values: RK_E_INVALID. The operator copies
+ * of modes 2 and 3 are made on first use (and freed by rk_problem_release).
+ * And r = b - A x. All vectors device, N doubles.
  */
 int rk_apply(const rk_problem* p, const double* v, double* y, int32_t precond, void* stream);
 int rk_residual(const rk_problem* p, const double* b, const double* x, double* r, void* stream);

@@ -48,6 +48,11 @@ cudaError_t launch_stencil(const Dims& d, int S, int mode, const double* coef, c
 // accumulation, double-float or FP64 input/output.
 cudaError_t launch_stencil32(const Dims& d, int S, const float* coef32, const float* dinv32, const void* v,
                              bool v_df, void* y, bool y_df, const int* skip, cudaStream_t st);
+// Double-float operator (RK_DF): bands and 1/a_pp as double-float copies
+// (launch_round_df), v and y double-float (v_df / y_df) or FP64.
+cudaError_t launch_round_df(int64_t n, const double* src, float2* dst, cudaStream_t st);
+cudaError_t launch_stencil_dd(const Dims& d, int S, bool precond, const float2* coefd, const float2* dinvd,
+                              const void* v, bool v_df, void* y, bool y_df, const int* skip, cudaStream_t st);
 cudaError_t launch_round_f32(int64_t n, const double* src, float* dst, cudaStream_t st);
 cudaError_t launch_stencil_df(const Dims& d, int S, int mode, const double* coef, const double* dinv,
                               const void* v, bool v_df, void* y, bool y_df, const int* skip_flag, cudaStream_t st);

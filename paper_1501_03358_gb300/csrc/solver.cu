@@ -173,7 +173,7 @@ struct ProfScope {
 struct rk_problem {
   rk_context* ctx = nullptr;
   Profiler prof;
-  // Captured Arnoldi cycles keyed by (recycle dim, steps, mixed, keep v_steps);
+  // Captured Arnoldi cycles keyed by (recycle dim, steps, operator precision, keep v_steps);
   // valid while the buffers they reference are (cleared on reallocation).
   std::map<uint64_t, cudaGraphExec_t> graphs;
   cudaStream_t capture_stream = nullptr;  // capture only (graphs launch on the caller's stream)
@@ -193,6 +193,8 @@ struct rk_problem {
   double* rvec = nullptr;         // FP64 residual of the rGCROT cycle
   float* coef32 = nullptr;        // mixed precision: FP32 copy of the bands
   float* dinv32 = nullptr;        // mixed precision: FP32 1/a_pp
+  float2* coefdf = nullptr;       // RK_DF: double-float copy of the bands
+  float2* dinvdf = nullptr;       // RK_DF: double-float 1/a_pp
   double* bicg = nullptr;
   // small
   double* small = nullptr;
@@ -480,11 +482,34 @@ int ensure_mixed(rk_problem* p, cudaStream_t st) {
   return RK_OK;
 }
 
-// A M^{-1} v of the recurrences: FP64 (bit-exact order) or, in mixed mode,
-// the FP32 operator
-int opapply_launch(rk_problem* p, bool mixed, const void* v, bool v_df, void* y, bool y_df, const int* skip,
+// Double-float copy of the operator for RK_DF: bands and 1/a_pp rounded to
+// double-float once.
+int ensure_dfop(rk_problem* p, cudaStream_t st) {
+  if (p->coefdf) return RK_OK;
+  p->drop_graphs();
+  RK_TRY(alloc_into(p->ctx, &p->coefdf, (size_t)p->S * p->n));
+  RK_TRY(alloc_into(p->ctx, &p->dinvdf, (size_t)p->ld));
+  RK_CUDA(launch_round_df((int64_t)p->S * p->n, p->coef, p->coefdf, st));
+  RK_CUDA(launch_round_df(p->n, p->dinv, p->dinvdf, st));
+  return RK_OK;
+}
+
+int ensure_operator(rk_problem* p, int precision, cudaStream_t st) {
+  if (precision == RK_MIXED) return ensure_mixed(p, st);
+  if (precision == RK_DF) return ensure_dfop(p, st);
+  return RK_OK;
+}
+
+// A M^{-1} v of the recurrences: FP64 (bit-exact order), the FP32 operator
+// (RK_MIXED) or the double-float operator (RK_DF)
+int opapply_launch(rk_problem* p, int precision, const void* v, bool v_df, void* y, bool y_df, const int* skip,
                    cudaStream_t st) {
-  if (!mixed) {
+  if (precision == RK_DF) {
+    ProfScope ps(&p->prof, PC_SPMV, 8.0 * (p->S + 2) * (double)p->n, st);
+    RK_CUDA(launch_stencil_dd(p->d, p->S, true, p->coefdf, p->dinvdf, v, v_df, y, y_df, skip, st));
+    return RK_OK;
+  }
+  if (precision != RK_MIXED) {
     if (!v_df && !y_df)
       return stencil_launch(p, ST_PREC, (const double*)v, nullptr, (double*)y, nullptr, nullptr, nullptr, skip, st);
     return stencil_df_launch(p, ST_PREC, v, v_df, y, y_df, skip, st);
@@ -559,8 +584,9 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
   const int k = recycle ? prm.k : 0;
   const int maxmv = prm.max_matvec > 0 ? prm.max_matvec : 2000;
   const bool mixed = prm.precision == RK_MIXED;
+  const int opk = prm.precision;
   RK_TRY(ensure_capacity(p, std::max(k, p->kdim), m, st));
-  if (mixed) RK_TRY(ensure_mixed(p, st));
+  RK_TRY(ensure_operator(p, opk, st));
   int kc = recycle ? p->kdim : 0;
   const double S = p->S;
   double words = 0.0;
@@ -603,7 +629,7 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
       // pass per step (Gram-Schmidt against [C V_j] with the second pass of
       // each vector delayed to the next step)
       for (int j = 0; j < steps; ++j) {
-        RK_TRY(opapply_launch(p, mixed, p->Vcol(j), true, p->Vcol(j + 1), true, done, st));
+        RK_TRY(opapply_launch(p, opk, p->Vcol(j), true, p->Vcol(j + 1), true, done, st));
         const int nq = kc + j;
         RK_TRY(dfdots2_launch(p, p->Cblk(kc), nq, p->Vcol(j), p->Vcol(j + 1), p->sb.dots, done, st));
         { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_dcgs_coef(p->st, p->sb, kc, j, 0, st)); }
@@ -623,7 +649,7 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
     if (p->prof.on) {
       RK_TRY(cycle(st));
     } else {
-      const uint64_t key = ((uint64_t)kc << 32) | ((uint64_t)steps << 2) | (mixed ? 2u : 0u) | (keep_last ? 1u : 0u);
+      const uint64_t key = ((uint64_t)kc << 32) | ((uint64_t)steps << 3) | ((uint64_t)opk << 1) | (keep_last ? 1u : 0u);
       auto it = p->graphs.find(key);
       if (it == p->graphs.end()) {
         cudaGraph_t g = nullptr;
@@ -712,9 +738,9 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
 int solve_bicg(rk_problem* p, const double* b, double* x, const rk_solve_params& prm, rk_solve_info& info,
                bool recycle, cudaStream_t st) {
   const int maxmv = prm.max_matvec > 0 ? prm.max_matvec : 2000;
-  const bool mixed = prm.precision == RK_MIXED;
+  const int opk = prm.precision;
   RK_TRY(ensure_capacity(p, p->kdim, std::max(p->mcap, 1), st));
-  if (mixed) RK_TRY(ensure_mixed(p, st));
+  RK_TRY(ensure_operator(p, opk, st));
   if (!p->bicg) RK_TRY(alloc_into(p->ctx, &p->bicg, (size_t)7 * p->ld));
   const int kc = recycle ? p->kdim : 0;
   BicgVecs v{};
@@ -765,11 +791,11 @@ int solve_bicg(rk_problem* p, const double* b, double* x, const rk_solve_params&
     while (running) {
       for (int it = 0; it < NB; ++it) {
         { ProfScope ps_(&p->prof, PC_BICG, 32.0 * p->n, st); RK_CUDA(launch_bicg_p(v, p->bs, p->n, st)); }
-        RK_TRY(opapply_launch(p, mixed, v.p, false, v.v, false, &p->bs->stop, st));
+        RK_TRY(opapply_launch(p, opk, v.p, false, v.v, false, &p->bs->stop, st));
         RK_TRY(dfdots_launch(p, p->Cblk(kc), kc, v.v, false, eta1, &p->bs->stop, st, v.rt));
         { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_bicg_alpha(p->bs, eta1, kc, st)); }
         { ProfScope ps_(&p->prof, PC_BICG, 8.0 * (kc + (kc ? 5 : 3)) * (double)p->n, st); RK_CUDA(launch_bicg_s(v, p->bs, p->n, kc, p->Cblk(kc), p->ld, eta1, xi, p->part, p->counter, st)); }
-        RK_TRY(opapply_launch(p, mixed, v.s, false, v.t, false, &p->bs->stop, st));
+        RK_TRY(opapply_launch(p, opk, v.s, false, v.t, false, &p->bs->stop, st));
         if (kc) RK_TRY(dfdots_launch(p, p->Cblk(kc), kc, v.t, false, eta2, &p->bs->stop, st));
         { ProfScope ps_(&p->prof, PC_BICG, 8.0 * (kc + (kc ? 3 : 2)) * (double)p->n, st); RK_CUDA(launch_bicg_t(v, p->bs, p->n, kc, p->Cblk(kc), p->ld, eta2, p->part, p->counter, st)); }
         { ProfScope ps_(&p->prof, PC_BICG, 56.0 * p->n, st); RK_CUDA(launch_bicg_r(v, p->bs, p->n, kc, eta1, eta2, xi, p->part, p->counter, st)); }
@@ -963,6 +989,8 @@ void rk_problem_destroy(rk_problem* p) {
   dev_free(c, p->rvec);
   dev_free(c, p->coef32);
   dev_free(c, p->dinv32);
+  dev_free(c, p->coefdf);
+  dev_free(c, p->dinvdf);
   dev_free(c, p->bicg);
   dev_free(c, p->small);
   dev_free(c, p->eta);
@@ -987,6 +1015,15 @@ int rk_apply(const rk_problem* p, const double* v, double* y, int32_t precond, v
     RK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     return RK_OK;
   }
+  if (precond == 3) {
+    rk_problem* pm = const_cast<rk_problem*>(p);
+    RK_TRY(ensure_dfop(pm, (cudaStream_t)stream));
+    RK_CUDA(launch_stencil_dd(p->d, p->S, true, p->coefdf, p->dinvdf, v, false, y, false, nullptr,
+                              (cudaStream_t)stream));
+    RK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return RK_OK;
+  }
+  if (precond < 0 || precond > 3) return fail(RK_E_INVALID, "precond must be 0..3");
   RK_CUDA(launch_stencil(p->d, p->S, precond ? ST_PREC : ST_PLAIN, p->coef, p->dinv, v, nullptr, y, nullptr,
                          nullptr, nullptr, nullptr, (cudaStream_t)stream));
   RK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
@@ -1126,7 +1163,8 @@ int rk_solve(rk_problem* p, const double* b, double* x, const rk_solve_params* p
   if (!p || !b || !x || !params) return fail(RK_E_INVALID, "NULL argument");
   rk_solve_params prm = *params;
   if (!(prm.tol > 0.0)) return fail(RK_E_INVALID, "tol must be positive");
-  if (prm.precision != RK_FP64 && prm.precision != RK_MIXED) return fail(RK_E_INVALID, "unknown precision");
+  if (prm.precision != RK_FP64 && prm.precision != RK_MIXED && prm.precision != RK_DF)
+    return fail(RK_E_INVALID, "unknown precision");
   if (prm.k < 0) return fail(RK_E_INVALID, "k < 0");
   rk_solve_info loc{};
   rk_solve_info& inf = info ? *info : loc;
@@ -1214,6 +1252,8 @@ int rk_problem_memory(const rk_problem* p, int64_t* device_bytes) {
   if (p->rvec) b += 8 * ld;
   if (p->coef32) b += 4 * S * n;
   if (p->dinv32) b += 4 * ld;
+  if (p->coefdf) b += 8 * S * n;
+  if (p->dinvdf) b += 8 * ld;
   if (p->bicg) b += 8 * 7 * ld;
   b += 8 * (p->small_n + p->eta_n + (p->part ? p->part_n : 0));
   *device_bytes = (int64_t)b;
@@ -1229,10 +1269,18 @@ int rk_problem_release(rk_problem* p, void* stream) {
   dev_free(c, p->Ub);
   dev_free(c, p->rvec);
   dev_free(c, p->bicg);
+  dev_free(c, p->coef32);
+  dev_free(c, p->dinv32);
+  dev_free(c, p->coefdf);
+  dev_free(c, p->dinvdf);
   p->QB = nullptr;
   p->Ub = nullptr;
   p->rvec = nullptr;
   p->bicg = nullptr;
+  p->coef32 = nullptr;
+  p->dinv32 = nullptr;
+  p->coefdf = nullptr;
+  p->dinvdf = nullptr;
   free_small(p);
   p->part_n = 0;
   p->kmax = 0;

@@ -209,15 +209,159 @@ __global__ void __launch_bounds__(kTX* kTY) k_stencil32(Dims d, const float* __r
   }
 }
 
+// Double-float operator (the recurrences' products in RK_DF): the bands and
+// 1/a_pp rounded once to double-float (about 48 bits), z = v * (1/a_pp) as a
+// normalised double-float product, and per output cell the S band products
+// summed in the fixed band order with TwoProduct and lazy double-float
+// accumulation (renormalised after every 8 bands and at the end). Everything
+// runs on the FP32 pipe; the FP64 stencil above is bound by the FP64 issue
+// rate of this GPU (about one DFMA per 64 cycles per sub-partition warp), this
+// one by HBM.
+template <typename VT>
+__device__ __forceinline__ float2 ld_df(const VT* p, int64_t q);
+template <>
+__device__ __forceinline__ float2 ld_df<float2>(const float2* p, int64_t q) { return __ldg(&p[q]); }
+template <>
+__device__ __forceinline__ float2 ld_df<double>(const double* p, int64_t q) { return df_from_double_i(__ldg(&p[q])); }
+
+template <typename YT>
+__device__ __forceinline__ void st_df(YT* p, int64_t q, float2 w);
+template <>
+__device__ __forceinline__ void st_df<float2>(float2* p, int64_t q, float2 w) { p[q] = w; }
+template <>
+__device__ __forceinline__ void st_df<double>(double* p, int64_t q, float2 w) { p[q] = df_to_double_i(w); }
+
+template <int S, int MODE, typename VT, typename YT>
+__global__ void __launch_bounds__(kTX* kTY) k_stencil_dd(Dims d, const float2* __restrict__ coef,
+                                                         const float2* __restrict__ dinv,
+                                                         const VT* __restrict__ v, YT* __restrict__ y,
+                                                         const int* skip, int zchunk) {
+  if (skip != nullptr && *skip != 0) return;
+  __shared__ float2 sz[3][kTY + 2][kTX + 2];
+  const int tx = threadIdx.x & (kTX - 1), ty = threadIdx.x / kTX;
+  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+  const int k0 = blockIdx.z * zchunk;
+  const int k1 = min(k0 + zchunk, d.nz);
+  const int gi = x0 + tx, gj = y0 + ty;
+  const bool active = gi < d.nx && gj < d.ny;
+  const int64_t N = d.n;
+  const int64_t plane = (int64_t)d.nx * d.ny;
+  // The haloed tile has (kTY + 2)(kTX + 2) <= 2 kTX kTY cells: each thread
+  // owns at most two, whose in-plane offsets (-1 outside a wall) are fixed.
+  static_assert((kTY + 2) * (kTX + 2) <= 2 * kTX * kTY, "two halo cells per thread");
+  constexpr int kCells = (kTY + 2) * (kTX + 2);
+  int64_t hoff[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int t = threadIdx.x + r * kTX * kTY;
+    hoff[r] = -1;
+    if (t < kCells) {
+      const int ly = t / (kTX + 2), lx = t - ly * (kTX + 2);
+      const int xw = halo_coord(x0 + lx - 1, d.nx, d.px);
+      const int yw = halo_coord(y0 + ly - 1, d.ny, d.py);
+      if (xw >= 0 && yw >= 0) hoff[r] = (int64_t)xw + (int64_t)d.nx * yw;
+    }
+  }
+  // operands of one plane: fetched into registers one plane ahead, so their
+  // latency overlaps a whole plane of arithmetic; scaled and stored later
+  float2 rv[2], rd[2];
+  auto fetch = [&](int kk) {
+    const int kw = halo_coord(kk, d.nz, d.pz);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      rv[r] = rd[r] = make_float2(0.f, 0.f);
+      if (kw >= 0 && hoff[r] >= 0) {
+        const int64_t q = hoff[r] + plane * kw;
+        rv[r] = ld_df<VT>(v, q);
+        if (MODE == ST_PREC) rd[r] = __ldg(&dinv[q]);
+      }
+    }
+  };
+  auto store = [&](int slot) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int t = threadIdx.x + r * kTX * kTY;
+      if (t < kCells) (&sz[slot][0][0])[t] = MODE == ST_PREC ? df_mul(rv[r], rd[r]) : rv[r];
+    }
+  };
+  if (k0 >= k1) return;
+  fetch(k0 - 1);
+  store((k0 + 2) % 3);
+  fetch(k0);
+  store(k0 % 3);
+  fetch(k0 + 1);
+  for (int k = k0; k < k1; ++k) {
+    // slot (k + 1) % 3 held plane k - 2, last read before the previous barrier
+    store((k + 1) % 3);
+    if (k + 1 < k1) fetch(k + 2);
+    // the first seven bands of this plane are requested before the barrier
+    const int64_t p = (int64_t)gi + (int64_t)d.nx * gj + plane * k;
+    float2 cf[7];
+#pragma unroll
+    for (int s = 0; s < 7; ++s) cf[s] = active ? __ldg(&coef[s * N + p]) : make_float2(0.f, 0.f);
+    __syncthreads();
+    if (active) {
+      const int sc = k % 3, sm = (k + 2) % 3, sp = (k + 1) % 3;
+      const int cx = tx + 1, cy = ty + 1;
+      float s, c;
+      {
+        const float2 z = sz[sc][cy][cx];
+        df_mul_pair(cf[0].x, cf[0].y, z.x, z.y, s, c);
+      }
+      auto mac = [&](int band, float2 z) {
+        const float2 a = band < 7 ? cf[band < 7 ? band : 0] : __ldg(&coef[band * N + p]);
+        df_mac_lazy(s, c, a.x, a.y, z.x, z.y);
+      };
+      mac(1, sz[sc][cy][cx - 1]);
+      mac(2, sz[sc][cy][cx + 1]);
+      mac(3, sz[sc][cy - 1][cx]);
+      mac(4, sz[sc][cy + 1][cx]);
+      mac(5, sz[sm][cy][cx]);
+      mac(6, sz[sp][cy][cx]);
+      if (S == 19) {
+        mac(7, sz[sc][cy - 1][cx - 1]);
+        df_renorm(s, c);
+        mac(8, sz[sc][cy - 1][cx + 1]);
+        mac(9, sz[sc][cy + 1][cx - 1]);
+        mac(10, sz[sc][cy + 1][cx + 1]);
+        mac(11, sz[sm][cy][cx - 1]);
+        mac(12, sz[sm][cy][cx + 1]);
+        mac(13, sz[sp][cy][cx - 1]);
+        mac(14, sz[sp][cy][cx + 1]);
+        mac(15, sz[sm][cy - 1][cx]);
+        df_renorm(s, c);
+        mac(16, sz[sm][cy + 1][cx]);
+        mac(17, sz[sp][cy - 1][cx]);
+        mac(18, sz[sp][cy + 1][cx]);
+      }
+      df_renorm(s, c);
+      st_df<YT>(y, p, make_float2(s, c));
+    }
+    __syncthreads();
+  }
+}
+
+// FP64 -> double-float rounding of the operator (RK_DF): hi = RN(x),
+// lo = RN(x - hi).
+__global__ void k_round_df(int64_t n, const double* __restrict__ src, float2* __restrict__ dst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = df_from_double_i(src[i]);
+}
+
 __global__ void k_round_f32(int64_t n, const double* __restrict__ src, float* __restrict__ dst) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     dst[i] = __double2float_rn(src[i]);
 }
 
-void stencil_grid(const Dims& d, dim3& grid, int& zchunk) {
+// Grid of (x, y) tiles x z chunks with about per_sm blocks per SM: 3 for the
+// FP64 kernel (FP64-issue bound), 4 for the double-float one, which is bound
+// by memory latency and bandwidth and needs many blocks' loads in flight
+// (5 fit per SM at 48 registers; 4 leaves room for the rounding of the chunk
+// count, so the grid still runs as one wave).
+void stencil_grid(const Dims& d, dim3& grid, int& zchunk, int per_sm = 3) {
   const int tx = (d.nx + kTX - 1) / kTX, ty = (d.ny + kTY - 1) / kTY;
   const int tiles = tx * ty;
-  int nzc = (3 * kNumSM + tiles - 1) / tiles;
+  int nzc = (per_sm * kNumSM + tiles - 1) / tiles;
   if (nzc > d.nz) nzc = d.nz;
   if (nzc < 1) nzc = 1;
   zchunk = (d.nz + nzc - 1) / nzc;
@@ -305,6 +449,34 @@ cudaError_t launch_stencil_df(const Dims& d, int S, int mode, const double* coef
   }
 #undef RK_STD_TYPES
 #undef RK_STD
+  return cudaGetLastError();
+}
+
+cudaError_t launch_round_df(int64_t n, const double* src, float2* dst, cudaStream_t st) {
+  k_round_df<<<red_blocks(n), kRedThreads, 0, st>>>(n, src, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stencil_dd(const Dims& d, int S, bool precond, const float2* coefd, const float2* dinvd,
+                              const void* v, bool v_df, void* y, bool y_df, const int* skip, cudaStream_t st) {
+  dim3 grid;
+  int zchunk;
+  stencil_grid(d, grid, zchunk, 4);
+  const dim3 block(kTX * kTY);
+#define RK_SDD(SS, MM, VT, YT) \
+  k_stencil_dd<SS, MM, VT, YT><<<grid, block, 0, st>>>(d, coefd, dinvd, (const VT*)v, (YT*)y, skip, zchunk)
+#define RK_SDD_TYPES(SS, MM)                         \
+  if (v_df && y_df) RK_SDD(SS, MM, float2, float2); \
+  else if (v_df) RK_SDD(SS, MM, float2, double);    \
+  else if (y_df) RK_SDD(SS, MM, double, float2);    \
+  else RK_SDD(SS, MM, double, double);
+  if (S == 7) {
+    if (precond) { RK_SDD_TYPES(7, ST_PREC) } else { RK_SDD_TYPES(7, ST_PLAIN) }
+  } else {
+    if (precond) { RK_SDD_TYPES(19, ST_PREC) } else { RK_SDD_TYPES(19, ST_PLAIN) }
+  }
+#undef RK_SDD_TYPES
+#undef RK_SDD
   return cudaGetLastError();
 }
 

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "RK_OK", 1: "RK_E_INVALID", 2: "RK_E_OOM", 3: "RK_E_NOT_CONVE
 RK_GMRES, RK_RGCROT, RK_RBICGSTAB, RK_HYBRID = 0, 1, 2, 3
 MODES = {"GMRES": RK_GMRES, "rGCROT": RK_RGCROT, "rBiCGStab": RK_RBICGSTAB, "BiCGStab": RK_RBICGSTAB,
          "hybrid": RK_HYBRID}
-RK_FP64, RK_MIXED = 0, 1
+RK_FP64, RK_MIXED, RK_DF = 0, 1, 2
 
 # Every exported symbol that include/rk.h declares.
 EXPORTS = ("rk_last_error", "rk_version", "rk_context_create", "rk_context_destroy", "rk_create_problem",

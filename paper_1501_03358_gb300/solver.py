@@ -126,12 +126,12 @@ class Problem:
         N.check(self.lib.rk_create_problem(ctx.handle, ctypes.byref(g), self.S, _dptr(coef), _stream_ptr(stream),
                                            ctypes.byref(self._h)))
 
-    def apply(self, v, precond=True, stream=None, fp32=False):
-        """A M^{-1} v (precond), A v, or with fp32 the FP32 operator of the
-        mixed-precision mode."""
+    def apply(self, v, precond=True, stream=None, fp32=False, df=False):
+        """A M^{-1} v (precond), A v, or with fp32 / df the FP32 / double-float
+        operator (with the preconditioner) of the "mixed" / "df" precisions."""
         v = _f64_cuda(v, (self.n,))
         y = torch.empty_like(v)
-        mode = 2 if fp32 else (1 if precond else 0)
+        mode = 2 if fp32 else (3 if df else (1 if precond else 0))
         N.check(self.lib.rk_apply(self._h, _dptr(v), _dptr(y), mode, _stream_ptr(stream)))
         return y
 
@@ -240,7 +240,7 @@ class Problem:
 
 
 def _params(tol, m, k, mode, max_matvec, hybrid_switch, update_recycle, precision):
-    prec = {"fp64": N.RK_FP64, "mixed": N.RK_MIXED}[precision]
+    prec = {"fp64": N.RK_FP64, "mixed": N.RK_MIXED, "df": N.RK_DF}[precision]
     prm = N.rk_solve_params(float(tol), int(m), int(k), int(max_matvec), int(hybrid_switch), N.MODES[mode],
                             prec, 1 if update_recycle else 0, 0)
     if mode == "BiCGStab":

@@ -95,6 +95,35 @@ def test_fp32_operator_bit_exact(ctx, S, dims, per):
     assert np.array_equal(prob.apply(t(v), fp32=True).cpu().numpy(), op.apply_prec_f32(v))
 
 
+def df_operator_bound(g, coef, v):
+    """Elementwise bound for the double-float operator: every input (bands,
+    1/a_pp, v) is rounded to double-float (relative 2^-48), z = v / a_pp and
+    each band product lose at most a few units of 2^-48, and the lazy
+    accumulation (renormalised every 8 bands) adds at most S + 1 more; the FP64
+    oracle's own error is S 2^-53. (S + 8) 2^-46 sum_s |c_s| |z_s| covers all
+    of these with room to spare."""
+    S = coef.shape[0]
+    z = np.abs(v / coef[0])
+    return (S + 8) * 2.0 ** -46 * oracle.Stencil(g, np.abs(coef)).apply(z)
+
+
+@pytest.mark.parametrize("S", [7, 19])
+@pytest.mark.parametrize("dims,per", GRIDS[:4])
+def test_df_operator_within_rounding_bound(ctx, S, dims, per):
+    """The double-float operator of the "df" precision (bands and 1/a_pp
+    rounded to double-float once, double-float products and accumulation in
+    band order) against the FP64 oracle, element by element."""
+    g = Grid(*dims, per)
+    coef = random_operator(g, S, np.random.default_rng(hash((S, dims, 48)) % 2**32))
+    prob = gpu_problem(ctx, g, coef)
+    op = oracle.Stencil(g, coef)
+    v = np.random.default_rng(6).standard_normal(g.n)
+    got = prob.apply(t(v), df=True).cpu().numpy()
+    ref = op.apply_prec(v)
+    assert np.all(np.abs(got - ref) <= df_operator_bound(g, coef, v))
+    assert np.any(got != ref)  # it is not the FP64 operator
+
+
 @pytest.mark.parametrize("n,nq", [(1, 1), (1000, 3), (4099, 17), (100003, 40), (262144, 61)])
 def test_block_dots(ctx, n, nq):
     rng = np.random.default_rng(n + nq)
@@ -316,6 +345,57 @@ def test_mixed_precision_sequence(ctx):
         assert np.linalg.norm(A_U - C) <= 1e-10 * np.linalg.norm(C) * np.abs(cfg.coef).max()
 
 
+@pytest.mark.parametrize("cfg_id,size,m,k,steps", [(1, 12, 30, 10, 4), (2, 12, 40, 20, 3)])
+def test_df_precision_sequence_parity(ctx, cfg_id, size, m, k, steps):
+    """rGCROT(m,k) sequence with the double-float operator in the Arnoldi
+    products: the same bars as the FP64 sequence (tolerance met on the FP64
+    true residual, x within the kappa bound of the oracle's, matvecs within
+    the oracle's own rounding-level spread) and A U = C, C^T C = I for the
+    carried space."""
+    cfg = make_config(cfg_id, size=size)
+    prob = gpu_problem(ctx, cfg.grid, cfg.coef)
+    op = oracle.Stencil(cfg.grid, cfg.coef)
+    kap = kappa(cfg.grid, cfg.coef)
+    seq = oracle.RecyclingSequence(op, mode="rGCROT", m=m, k=k, tol=1e-8, max_matvec=5000)
+    for s in range(steps):
+        b = cfg.rhs(s)
+        x, info = prob.solve(t(b), tol=1e-8, m=m, k=k, mode="rGCROT", max_matvec=5000, precision="df")
+        U0, C0 = seq.U, seq.C
+        xo, io = seq.solve(b)
+        slack = 2
+        if io["cycles"] > 3:
+            run = lambda bb: oracle.rgcrot(op, bb, tol=1e-8, m=m, k=k, U=U0, C=C0, max_matvec=5000)[3]
+            slack, _ = mv_slack(run, b, io["matvecs"])
+        check_solve(op, b, x.cpu().numpy(), info, xo, io, 1e-8, slack, kap)
+        U, C = prob.get_recycle()
+        U, C = U.cpu().numpy().T, C.cpu().numpy().T
+        A_U = np.stack([op.apply(u) for u in U.T], axis=1)
+        assert np.linalg.norm(A_U - C) <= 1e-10 * np.linalg.norm(C) * max(1.0, np.abs(cfg.coef).max())
+        assert np.linalg.norm(C.T @ C - np.eye(C.shape[1])) <= 1e-11
+
+
+def test_df_precision_hybrid_porous(ctx):
+    """The hybrid rGCROT -> rBiCGStab sequence on the porous 19-point problem
+    with the double-float operator (FP64 vectors in the rBiCGStab phase)."""
+    n = (14, 12, 10)
+    solid, _ = sphere_pack(n, 2.5, 0.3, rng_for(77, 3), max_attempts=20000)
+    grid, coef = porous_skew_19pt(n, np.where(solid, 1e-4, 1.0), 15.0)
+    prob = gpu_problem(ctx, grid, coef)
+    op = oracle.Stencil(grid, coef)
+    kap = kappa(grid, coef)
+    seq = oracle.RecyclingSequence(op, mode="hybrid", m=20, k=10, tol=1e-8, hybrid_switch=2, max_matvec=4000)
+    base = np.random.default_rng(5).standard_normal(grid.n)
+    for s in range(4):
+        b = base + 0.05 * s * np.random.default_rng(100 + s).standard_normal(grid.n)
+        x, info = prob.solve(t(b), tol=1e-8, m=20, k=10, mode="hybrid", hybrid_switch=2, max_matvec=4000,
+                             precision="df")
+        xo, io = seq.solve(b)
+        xg = x.cpu().numpy()
+        rel = np.linalg.norm(op.residual(b, xg)) / np.linalg.norm(b)
+        assert info["status"] == 0 and rel <= 1e-8, (s, info)
+        assert np.linalg.norm(xg - xo) <= max(1e-6, 2 * kap * 1e-8) * np.linalg.norm(xo)
+
+
 def test_mixed_precision_hybrid_porous(ctx):
     n = (14, 12, 10)
     solid, _ = sphere_pack(n, 2.5, 0.3, rng_for(77, 3), max_attempts=20000)
@@ -388,21 +468,26 @@ def test_not_converged_returns_last_iterate(ctx):
     assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-8 * np.linalg.norm(xo)
 
 
-def test_full_size_channel_operator_and_solve(ctx):
+@pytest.mark.parametrize("precision", ["fp64", "df"])
+def test_full_size_channel_operator_and_solve(ctx, precision):
     """At the 128^3 channel size (the benchmark's workload and launch
-    configuration): every SpMV output bit-exact against the oracle; a capped
-    rGCROT(40,20) solve whose reported true residual matches the oracle's
-    recomputation of ||b - A x||, whose residual history decreases, and whose
-    recycle space satisfies A U = C (sampled columns, oracle products) and
-    C^T C = I."""
+    configuration): every SpMV output bit-exact against the oracle (the
+    double-float operator within its rounding bound); a capped rGCROT(40,20)
+    solve whose reported true residual matches the oracle's recomputation of
+    ||b - A x||, whose residual history decreases, and whose recycle space
+    satisfies A U = C (sampled columns, oracle products) and C^T C = I."""
     cfg = make_config(2)
     prob = gpu_problem(ctx, cfg.grid, cfg.coef)
     op = oracle.Stencil(cfg.grid, cfg.coef)
     v = np.random.default_rng(1).standard_normal(cfg.n)
-    assert np.array_equal(prob.apply(t(v)).cpu().numpy(), op.apply_prec(v))
-    assert np.array_equal(prob.apply(t(v), precond=False).cpu().numpy(), op.apply(v))
+    if precision == "fp64":
+        assert np.array_equal(prob.apply(t(v)).cpu().numpy(), op.apply_prec(v))
+        assert np.array_equal(prob.apply(t(v), precond=False).cpu().numpy(), op.apply(v))
+    else:
+        got = prob.apply(t(v), df=True).cpu().numpy()
+        assert np.all(np.abs(got - op.apply_prec(v)) <= df_operator_bound(cfg.grid, cfg.coef, v))
     b = cfg.rhs(0)
-    x, info = prob.solve(t(b), tol=1e-8, m=40, k=20, mode="rGCROT", max_matvec=400)
+    x, info = prob.solve(t(b), tol=1e-8, m=40, k=20, mode="rGCROT", max_matvec=400, precision=precision)
     xg = x.cpu().numpy()
     assert np.all(np.isfinite(xg))
     rel = np.linalg.norm(op.residual(b, xg)) / np.linalg.norm(b)
