@@ -7,7 +7,7 @@
  * the Krylov methods of Sec. 2.2-2.4:
  *   RK_GMRES      GMRES(m), Algorithm 1;
  *   RK_RGCROT     rGCROT(m,k) with a recycle space carried across solves,
- *                 Algorithm 3 (recycle update of line 14a by harmonic Ritz
+ *                 Algorithm 3 (recycle update after each cycle by harmonic Ritz
  *                 vectors);
  *   RK_RBICGSTAB  rBiCGStab with one recycle space, Algorithm 4 (k = 0 or no
  *                 recycle space: plain BiCGStab, Algorithm 2);
@@ -27,7 +27,7 @@
  *    Periodic axes wrap; a band pointing out of a non-periodic face must be
  *    exactly 0 (checked by rk_create_problem).
  *  - The recycle space is stored in x-space: U, C are N x k column-major
- *    (column c at offset c*N) with A U = C and C^T C = I; the R of line 1a
+ *    (column c at offset c*N) with A U = C and C^T C = I; the R of the QR that forms C
  *    is folded into U. Inside the library U, C and the Arnoldi basis are kept
  *    as double-float pairs (hi + lo of two FP32 numbers, about 48 significant
  *    bits) and all projection arithmetic is double-float: a recycle space set
@@ -84,7 +84,7 @@ typedef struct {
                             products with a double-float copy of the operator (bands and
                             1/a_pp rounded to ~48 bits once, double-float accumulation in band
                             order), everything else as in RK_FP64 */
-  int32_t update_recycle;/* rGCROT: 1 = update U, C after every cycle (line 14a), 0 = keep */
+  int32_t update_recycle;/* rGCROT: 1 = update U, C after every cycle (Algorithm 3), 0 = keep */
   int32_t reserved;
 } rk_solve_params;
 
@@ -133,9 +133,9 @@ int rk_create_problem(rk_context* ctx, const rk_grid* grid, int32_t S, const dou
 void rk_problem_destroy(rk_problem* p);
 
 /*
- * Set the recycle space (Algorithm 3 line 1a / Algorithm 4 lines 1a-1b).
+ * Set the recycle space (the forming of C from U in Algorithms 3 and 4).
  * U: device, N x k column-major. C: device N x k or NULL. With C == NULL the
- * library forms C~ = A U and its thin QR C~ = C R (line 1a) and stores
+ * library forms C~ = A U and its thin QR C~ = C R and stores
  * U R^{-1}, so that A U = C, C^T C = I. With C given it checks
  * ||A U - C||_F <= 1e-10 ||A||_F ||U||_F and ||C^T C - I||_F <= 1e-10 and
  * returns RK_E_RECYCLE_INVARIANT otherwise. k = 0 clears the space. On any
@@ -178,8 +178,8 @@ int rk_apply(const rk_problem* p, const double* v, double* y, int32_t precond, v
 int rk_residual(const rk_problem* p, const double* b, const double* x, double* r, void* stream);
 
 /*
- * Block inner products used by the projections (Algorithm 3 lines 6a-9,
- * Algorithm 4 lines 1c, 7a, 12a): out[q] = Q_q^T w for the nq columns of Q
+ * Block inner products used by the projections (the C and V projections of
+ * Algorithm 3, the C projections of Algorithm 4): out[q] = Q_q^T w for the nq columns of Q
  * (device, column-major, leading dimension ld >= N), w device, out device
  * (nq doubles). The reduction order is fixed by N alone (deterministic).
  */
@@ -255,7 +255,7 @@ int rk_profile_enable(rk_problem* p, int32_t on);
 int rk_profile_read(rk_problem* p, rk_prof_entry* out, int32_t cap, int32_t* count);
 
 /*
- * The small problem of Algorithm 3 line 14a on its own (the same device code
+ * The small problem of Algorithm 3's recycle update on its own (the same device code
  * the solver runs after every cycle). G, F: device, (n+1) x n column-major:
  * the cycle's G = [[I, B], [0, H]] with A W = W_hat G, and
  * F = W_hat^T M W. Selects the harmonic Ritz vectors p of the k smallest

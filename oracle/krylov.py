@@ -10,25 +10,25 @@ NumPy/SciPy LAPACK. Readings of the paper that this module takes:
 * Convergence is tested relative to ||b||; GMRES(m) and rGCROT stop a cycle
   at the first step whose least-squares residual estimate |g_{j+1}| meets the
   tolerance (the in-cycle estimate of the note under Algorithm 1) and then
-  recompute b - A x (line 14); another cycle runs if that is still above.
-* Matrix-vector products are counted in the recurrences only (lines 6 and
-  the BiCGStab lines 7 and 12); b - A x and the A U of line 1a are not.
-* Algorithm 3, line 13a: the solution takes x <- x + U z with z = -B y, the
-  sign that the derivation of eq. (xm_UV_rm) gives (x_m = x_0 + V_m y + U z);
+  recompute the true residual b - A x; another cycle runs if that is still above.
+* Matrix-vector products are counted in the recurrences only (the Arnoldi
+  product, and BiCGStab's two products); b - A x and the A U that forms C are not.
+* Algorithm 3, the U-part of the solution update: x <- x + U z with z = -B y,
+  the sign that the derivation of eq. (xm_UV_rm) gives (x_m = x_0 + V_m y + U z);
   the listing's 'x - U(R^{-1} z)' contradicts it, and with U stored as U R^{-1}
   (so that A U = C) no R appears.
-* Line 14a (recycle-space update) uses harmonic Ritz vectors (the GCRO-DR
+* The recycle-space update uses harmonic Ritz vectors (the GCRO-DR
   selection named in the title of Algorithm 3), after every cycle; see
   ``harmonic_ritz_update``.
-* The projection of line 1b (xi = C^T r, r <- r - C xi, x <- x + U xi) is
+* The projection of the initial residual onto C (xi = C^T r, r <- r - C xi, x <- x + U xi) is
   applied at the top of every cycle, not only the first. In exact arithmetic
-  the residual of line 14 is already orthogonal to the updated C (it is
+  the true residual at the end of a cycle is already orthogonal to the updated C (it is
   W_hat times a vector orthogonal to range(G)), so the iterates are
   unchanged; in floating point its C-component is amplified by every update
   (by about 30x per cycle on the 5^3 convection-diffusion problem), which
   breaks v_1 ⟂ C (eq. V_perp_C) within a few cycles.
 * BiCGStab's shadow residual is r~ = r_0 (the note under Algorithm 2), taken
-  after the projection of line 1c in Algorithm 4.
+  after the projection of the initial residual in Algorithm 4.
 """
 import numpy as np
 import scipy.linalg as sla
@@ -54,7 +54,7 @@ def _givens(a, b):
 
 class _LS:
     """Progressive Givens QR of the (j+1) x j Hessenberg matrix and rotated rhs
-    (Algorithm 1/3, line 12: y = argmin || e_1 rho - H y ||)."""
+    (Algorithms 1 and 3: y = argmin || e_1 rho - H y ||)."""
 
     def __init__(self, m, rho):
         self.R = np.zeros((m + 1, m))
@@ -92,8 +92,8 @@ def _op(grid_or_op, coef=None):
 def gmres(op, b, x0=None, tol=1e-8, m=30, max_matvec=2000, keep_cycle=False):
     """GMRES(m), Algorithm 1, right-preconditioned by M = diag(A).
 
-    Arnoldi with modified Gram-Schmidt (lines 7-9) on A M^{-1}; solution
-    update x <- x + M^{-1} V_j y (line 13); true residual (line 14)."""
+    Arnoldi with modified Gram-Schmidt on A M^{-1}; solution
+    update x <- x + M^{-1} V_j y; true residual b - A x after every cycle."""
     n = op.n
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=float)
     bnorm = float(np.linalg.norm(b))
@@ -143,7 +143,7 @@ def gmres(op, b, x0=None, tol=1e-8, m=30, max_matvec=2000, keep_cycle=False):
 
 # --------------------------------------------------------------------------- recycle space helpers
 def recycle_from_u(op, U):
-    """Line 1a: C~ = A U, thin QR C~ = C R; return (U R^{-1}, C) so A U = C."""
+    """Forming C from U (Algorithms 3 and 4): C~ = A U, thin QR C~ = C R; return (U R^{-1}, C) so A U = C."""
     Ct = np.stack([op.apply(u) for u in U.T], axis=1)
     Q, R = np.linalg.qr(Ct)
     Unew = sla.solve_triangular(R, U.T, trans="T", lower=False).T  # U R^{-1}
@@ -151,7 +151,7 @@ def recycle_from_u(op, U):
 
 
 def harmonic_ritz_update(op, U, C, V, B, H, jj, k, return_theta=False):
-    """Line 14a: new recycle space from harmonic Ritz vectors.
+    """Recycle-space update of Algorithm 3: new recycle space from harmonic Ritz vectors.
 
     W = [U, M^{-1} V_j] (x-space) and W_hat = [C, V_{j+1}] satisfy
     A W = W_hat G with G = [[I, B], [0, H_j]] (the augmented Arnoldi relation,
@@ -224,7 +224,7 @@ def rgcrot(op, b, x0=None, tol=1e-8, m=30, k=10, U=None, C=None, update=True, ma
     """rGCROT(m,k), Algorithm 3, right-preconditioned by M = diag(A).
 
     U, C are N x k_cur arrays (or None) with A U = C, C^T C = I; if only U is
-    given, line 1a makes C. Returns (x, U, C, info)."""
+    given, C is formed from it (recycle_from_u). Returns (x, U, C, info)."""
     n = op.n
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=float)
     bnorm = float(np.linalg.norm(b))
@@ -235,9 +235,9 @@ def rgcrot(op, b, x0=None, tol=1e-8, m=30, k=10, U=None, C=None, update=True, ma
     kc = 0 if U is None else U.shape[1]
     if bnorm == 0.0:
         return np.zeros(n), U, C, _info(OK, 0, 0, 0, 0.0, 0.0, [], kc)
-    rhat = op.residual(b, x)                      # line 1
+    rhat = op.residual(b, x)                      # initial residual
     if kc:
-        xi = C.T @ rhat                           # line 1b
+        xi = C.T @ rhat                           # projection onto C
         r = rhat - C @ xi
         x = x + U @ xi
     else:
@@ -248,11 +248,11 @@ def rgcrot(op, b, x0=None, tol=1e-8, m=30, k=10, U=None, C=None, update=True, ma
     est = rho / bnorm
     last = None
     first = True
-    while rho > tol * bnorm and matvecs < max_matvec:   # line 3
+    while rho > tol * bnorm and matvecs < max_matvec:   # outer loop
         if kc and not first:
-            # line 1b again: v_1 must be orthogonal to the (updated) C for
-            # eq. V_perp_C; the residual of line 14 is only orthogonal to it
-            # up to rounding, and each update of line 14a amplifies the drift.
+            # the projection onto C again: v_1 must be orthogonal to the (updated) C for
+            # eq. V_perp_C; the true residual is only orthogonal to it
+            # up to rounding, and each recycle update amplifies the drift.
             xi = C.T @ r
             r = r - C @ xi
             x = x + U @ xi
@@ -261,19 +261,19 @@ def rgcrot(op, b, x0=None, tol=1e-8, m=30, k=10, U=None, C=None, update=True, ma
         V = np.zeros((m + 1, n))
         H = np.zeros((m + 1, m))
         Bm = np.zeros((max(kc, 1), m))
-        V[0] = r / rho                                  # line 4
+        V[0] = r / rho                                  # v_1 = r / ||r||
         ls = _LS(m, rho)
         jj = 0
-        for j in range(m):                              # line 5
-            w = op.apply_prec(V[j])                     # line 6
+        for j in range(m):                              # Arnoldi steps
+            w = op.apply_prec(V[j])                     # w = A M^{-1} v_j
             matvecs += 1
-            for l in range(kc):                         # lines 6a-6c
+            for l in range(kc):                         # B column: w <- w - C C^T w
                 Bm[l, j] = C[:, l] @ w
                 w = w - C[:, l] * Bm[l, j]
-            for l in range(j + 1):                      # lines 7-9
+            for l in range(j + 1):                      # modified Gram-Schmidt against V_j
                 H[l, j] = V[l] @ w
                 w = w - V[l] * H[l, j]
-            H[j + 1, j] = np.linalg.norm(w)             # line 10
+            H[j + 1, j] = np.linalg.norm(w)             # h_{j+1,j} = ||w||
             happy = H[j + 1, j] == 0.0
             if not happy:
                 V[j + 1] = w / H[j + 1, j]
@@ -282,19 +282,19 @@ def rgcrot(op, b, x0=None, tol=1e-8, m=30, k=10, U=None, C=None, update=True, ma
             jj = j + 1
             if e <= tol * bnorm or happy or matvecs >= max_matvec:
                 break
-        y = ls.solve(jj)                                # line 12
-        x = x + op.minv(V[:jj].T @ y)                   # line 13
+        y = ls.solve(jj)                                # least squares for y
+        x = x + op.minv(V[:jj].T @ y)                   # x <- x + M^{-1} V_j y
         if kc:
-            z = -Bm[:kc, :jj] @ y                       # line 12a
-            x = x + U @ z                               # line 13a
-        r = op.residual(b, x)                           # line 14
+            z = -Bm[:kc, :jj] @ y                       # z = -B y
+            x = x + U @ z                               # x <- x + U z
+        r = op.residual(b, x)                           # true residual
         rho = float(np.linalg.norm(r))
         cycles += 1
         hist.append(rho / bnorm)
         if keep_cycle:
             last = dict(V=V[: jj + 1].copy(), H=H[: jj + 1, :jj].copy(), B=Bm[:kc, :jj].copy(),
                         C=None if C is None else C.copy(), U=None if U is None else U.copy(), y=y, jj=jj)
-        if update and k > 0:                            # line 14a
+        if update and k > 0:                            # recycle-space update
             U, C = harmonic_ritz_update(op, U, C, V, Bm, H, jj, k)
             kc = 0 if U is None else U.shape[1]
     st = OK if rho <= tol * bnorm else NOT_CONVERGED
@@ -313,7 +313,7 @@ def bicgstab(op, b, x0=None, tol=1e-8, max_matvec=2000):
     bnorm = float(np.linalg.norm(b))
     if bnorm == 0.0:
         return np.zeros(n), _info(OK, 0, 0, 0, 0.0, 0.0, [])
-    r = op.residual(b, x)                               # line 1
+    r = op.residual(b, x)                               # initial residual
     rt = r.copy()                                       # r~ = r_0
     xt = np.zeros(n)
     matvecs = it = 0
@@ -321,36 +321,36 @@ def bicgstab(op, b, x0=None, tol=1e-8, max_matvec=2000):
     status = NOT_CONVERGED
     p = v = None
     alpha = omega = rho_old = 0.0
-    while np.linalg.norm(r) > tol * bnorm and matvecs < max_matvec:  # line 3
-        rho = rt @ r                                    # line 4
-        if rho == 0.0:                                  # line 5
+    while np.linalg.norm(r) > tol * bnorm and matvecs < max_matvec:  # iteration
+        rho = rt @ r                                    # rho = (r~, r)
+        if rho == 0.0:                                  # breakdown test
             status = BREAKDOWN
             break
-        if it == 0:                                     # line 6
+        if it == 0:                                     # first search direction
             p = r.copy()
         else:
             beta = (rho / rho_old) * (alpha / omega)
             p = r + beta * (p - omega * v)
-        v = op.apply_prec(p)                            # line 7
+        v = op.apply_prec(p)                            # v = A M^{-1} p
         matvecs += 1
-        alpha = rho / (rt @ v)                          # line 8
+        alpha = rho / (rt @ v)                          # alpha
         s = r - alpha * v
-        if np.linalg.norm(s) <= tol * bnorm:            # lines 9-10
+        if np.linalg.norm(s) <= tol * bnorm:            # early exit on ||s||
             xt = xt + alpha * p
             r = s
             it += 1
             hist.append(np.linalg.norm(r) / bnorm)
             break
-        t = op.apply_prec(s)                            # line 12
+        t = op.apply_prec(s)                            # t = A M^{-1} s
         matvecs += 1
         tt = t @ t
         if tt == 0.0:
             status = BREAKDOWN
             break
-        omega = (t @ s) / tt                            # line 13
-        xt = xt + alpha * p + omega * s                 # line 14
-        r = s - omega * t                               # line 15
-        rho_old = rho                                   # line 16
+        omega = (t @ s) / tt                            # omega
+        xt = xt + alpha * p + omega * s                 # x~ update
+        r = s - omega * t                               # r update
+        rho_old = rho                                   # keep rho
         it += 1
         hist.append(np.linalg.norm(r) / bnorm)
         if omega == 0.0:
@@ -370,65 +370,65 @@ def _rbicgstab_pass(op, b, x, tol, U, C, max_matvec, bnorm, callback=None):
     breakdown, updated-residual norm, history)."""
     n = op.n
     kc = 0 if C is None else C.shape[1]
-    rhat = op.residual(b, x)                            # line 1
+    rhat = op.residual(b, x)                            # initial residual
     if kc:
-        eta1 = C.T @ rhat                               # line 1c
+        eta1 = C.T @ rhat                               # projection onto C
         r = rhat - C @ eta1
         xi = -eta1
     else:
         r = rhat
         xi = np.zeros(0)
-    rt = r.copy()                                       # line 2: r~ = r_0
+    rt = r.copy()                                       # shadow residual r~ = r_0
     xt = np.zeros(n)
     matvecs = it = 0
     hist = []
     brk = False
     p = v = None
     alpha = omega = rho_old = 0.0
-    while np.linalg.norm(r) > tol * bnorm and matvecs < max_matvec:   # line 3
-        rho = rt @ r                                    # line 4
-        if abs(rho) <= 1e-14 * np.linalg.norm(rt) * np.linalg.norm(r):   # line 5
+    while np.linalg.norm(r) > tol * bnorm and matvecs < max_matvec:   # iteration
+        rho = rt @ r                                    # rho = (r~, r)
+        if abs(rho) <= 1e-14 * np.linalg.norm(rt) * np.linalg.norm(r):   # breakdown test
             brk = True
             break
-        if it == 0:                                     # line 6
+        if it == 0:                                     # first search direction
             p = r.copy()
         else:
             beta = (rho / rho_old) * (alpha / omega)
             p = r + beta * (p - omega * v)
-        v = op.apply_prec(p)                            # line 7
+        v = op.apply_prec(p)                            # v = A M^{-1} p
         matvecs += 1
         if kc:
-            eta1 = C.T @ v                              # line 7a
+            eta1 = C.T @ v                              # eta1 = C^T v
             v = v - C @ eta1
         rtv = rt @ v
         if rtv == 0.0:
             brk = True
             break
-        alpha = rho / rtv                               # line 8
+        alpha = rho / rtv                               # alpha
         s = r - alpha * v
-        if np.linalg.norm(s) <= tol * bnorm:            # line 9
-            xt = xt + alpha * p                         # line 10
+        if np.linalg.norm(s) <= tol * bnorm:            # early exit on ||s||
+            xt = xt + alpha * p                         # x~ update
             r = s
             if kc:
-                xi = xi + alpha * eta1                  # line 10a
+                xi = xi + alpha * eta1                  # postponed U coefficient
             it += 1
             hist.append(np.linalg.norm(r) / bnorm)
             break
-        t = op.apply_prec(s)                            # line 12
+        t = op.apply_prec(s)                            # t = A M^{-1} s
         matvecs += 1
         if kc:
-            eta2 = C.T @ t                              # line 12a
+            eta2 = C.T @ t                              # eta2 = C^T t
             t = t - C @ eta2
         tt = t @ t
         if tt == 0.0:
             brk = True
             break
-        omega = (t @ s) / tt                            # line 13
+        omega = (t @ s) / tt                            # omega
         if kc:
-            xi = xi + alpha * eta1 + omega * eta2       # line 13a
-        xt = xt + alpha * p + omega * s                 # line 14
-        r = s - omega * t                               # line 15
-        rho_old = rho                                   # line 16
+            xi = xi + alpha * eta1 + omega * eta2       # postponed U coefficient
+        xt = xt + alpha * p + omega * s                 # x~ update
+        r = s - omega * t                               # r update
+        rho_old = rho                                   # keep rho
         it += 1
         hist.append(np.linalg.norm(r) / bnorm)
         if callback is not None:
@@ -438,7 +438,7 @@ def _rbicgstab_pass(op, b, x, tol, U, C, max_matvec, bnorm, callback=None):
             break
     if callback is not None:
         callback(r)
-    x = x + op.minv(xt)                                 # line 17a (and x = x_hat + M^{-1} x~)
+    x = x + op.minv(xt)                                 # x = x_hat + M^{-1} x~, then the postponed U part
     if kc:
         x = x - U @ xi
     return x, matvecs, it, brk, float(np.linalg.norm(r)), hist
@@ -448,7 +448,7 @@ def rbicgstab(op, b, x0=None, tol=1e-8, U=None, C=None, max_matvec=2000, max_res
     """rBiCGStab with one recycle space, Algorithm 4, right-preconditioned.
 
     When the updated residual meets the tolerance the postponed U update is
-    folded in (line 17a) and the true residual b - A x is checked; if it is
+    folded in and the true residual b - A x is checked; if it is
     above the tolerance, or on breakdown, Algorithm 4 restarts from the
     current x (at most ``max_restarts`` times)."""
     n = op.n
@@ -457,7 +457,7 @@ def rbicgstab(op, b, x0=None, tol=1e-8, U=None, C=None, max_matvec=2000, max_res
     if U is not None and U.shape[1] == 0:
         U = C = None
     if U is not None and C is None:
-        U, C = recycle_from_u(op, U)                    # line 1b
+        U, C = recycle_from_u(op, U)                    # forming C from U
     kc = 0 if U is None else U.shape[1]
     if bnorm == 0.0:
         return np.zeros(n), _info(OK, 0, 0, 0, 0.0, 0.0, [], kc)

@@ -1,7 +1,7 @@
 // Fused vector kernels of rBiCGStab with one recycle space (Algorithm 4;
 // Algorithm 2 when the recycle space is empty), right-preconditioned. The
 // scalar recurrences (alpha, omega, beta, rho, the postponed U coefficients
-// xi of lines 10a/13a) are advanced on the device by the last block of each
+// xi) are advanced on the device by the last block of each
 // reduction, so a batch of iterations runs without host synchronisation; a
 // device flag stops the remaining kernels of a batch on convergence or
 // breakdown.
@@ -16,10 +16,10 @@ namespace {
 
 __device__ __forceinline__ bool stopped(const BicgScalars* s) { return s->stop != 0; }
 
-// line 6: p = r (first iteration) or p = r + beta (p - omega v)
+// p = r (first iteration) or p = r + beta (p - omega v)
 __global__ void __launch_bounds__(kRedThreads) k_bicg_p(BicgVecs v, BicgScalars* s, int64_t n) {
   if (stopped(s)) return;
-  if (s->matvecs >= s->maxmv) {  // the cap of line 3 (i <= max_itn)
+  if (s->matvecs >= s->maxmv) {  // the iteration cap (i <= max_itn)
     __syncthreads();
     if (threadIdx.x == 0) {
       s->flag = 3;
@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(kRedThreads) k_bicg_p(BicgVecs v, BicgScalars*
   }
 }
 
-// line 8 (after 7a): alpha = rho / (r~^T v); r~ is orthogonal to C, so r~^T v
+// alpha = rho / (r~^T v) after the C projection of v; r~ is orthogonal to C, so r~^T v
 // equals r~^T (v - C eta1).
 __global__ void k_bicg_alpha(BicgScalars* s, const double* dots, int kc) {
   if (threadIdx.x != 0 || stopped(s)) return;
@@ -50,8 +50,8 @@ __global__ void k_bicg_alpha(BicgScalars* s, const double* dots, int kc) {
   s->alpha = s->rho / rtv;
 }
 
-// lines 7a-9: v <- v - C eta1; s = r - alpha v; ||s||; on convergence the
-// half step of lines 10-10a is recorded (xi += alpha eta1 here, x~ += alpha p
+// v <- v - C eta1; s = r - alpha v; ||s||; on convergence the
+// half step is recorded (xi += alpha eta1 here, x~ += alpha p
 // by k_bicg_half).
 __global__ void __launch_bounds__(kRedThreads) k_bicg_s(BicgVecs v, BicgScalars* s, int64_t n, int kc,
                                                         const float2* C, int64_t ld, const double* eta1,
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kRedThreads) k_bicg_s(BicgVecs v, BicgScalars*
   }
 }
 
-// line 10 on convergence at the half step: x~ += alpha p
+// on convergence at the half step: x~ += alpha p
 __global__ void __launch_bounds__(kRedThreads) k_bicg_half(BicgVecs v, BicgScalars* s, int64_t n) {
   if (s->half != 1) return;
   const double alpha = s->alpha;
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kRedThreads) k_bicg_half(BicgVecs v, BicgScala
   }
 }
 
-// lines 12a-13: t <- t - C eta2; omega = t^T s / t^T t (last block).
+// t <- t - C eta2; omega = t^T s / t^T t (last block).
 __global__ void __launch_bounds__(kRedThreads) k_bicg_t(BicgVecs v, BicgScalars* s, int64_t n, int kc,
                                                         const float2* C, int64_t ld, const double* eta2,
                                                         double* part, unsigned* counter) {
@@ -167,9 +167,9 @@ __global__ void __launch_bounds__(kRedThreads) k_bicg_t(BicgVecs v, BicgScalars*
   }
 }
 
-// lines 13a-16: xi += alpha eta1 + omega eta2; x~ += alpha p + omega s;
+// xi += alpha eta1 + omega eta2; x~ += alpha p + omega s;
 // r = s - omega t; rho = r~^T r, beta = (rho/rho_old)(alpha/omega); the
-// convergence (line 3) and breakdown (line 5) tests of the next iteration.
+// convergence and breakdown tests of the next iteration.
 __global__ void __launch_bounds__(kRedThreads) k_bicg_r(BicgVecs v, BicgScalars* s, int64_t n, int kc,
                                                         const double* eta1, const double* eta2, double* xi,
                                                         double* part, unsigned* counter) {
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kRedThreads) k_bicg_r(BicgVecs v, BicgScalars*
   }
 }
 
-// Start of a pass of Algorithm 4 (after line 1c): r~ = r_0, rho = r~^T r_0.
+// Start of a pass of Algorithm 4 (after the initial C projection): r~ = r_0, rho = r~^T r_0.
 __global__ void k_bicg_init(BicgScalars* s, const double* rho2, double tolabs, int maxmv) {
   if (threadIdx.x != 0) return;
   s->rho = *rho2;
@@ -234,7 +234,7 @@ __global__ void k_bicg_init(BicgScalars* s, const double* rho2, double tolabs, i
   s->stop = s->flag != 0 ? 1 : 0;
 }
 
-// coefficients of the fold of line 17a: [-xi; 1]
+// coefficients of the final fold x <- x + M^{-1} x~ - U xi: [-xi; 1]
 __global__ void k_bicg_foldcoef(const double* xi, int kc, double* coefv) {
   for (int q = threadIdx.x; q <= kc; q += blockDim.x) coefv[q] = q < kc ? -xi[q] : 1.0;
 }

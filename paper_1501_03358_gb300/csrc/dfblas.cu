@@ -1,8 +1,8 @@
 // Streaming kernels over the double-float basis [C V] and U (float2 per
 // element: hi, lo). Same roles as their FP64 counterparts — block inner
-// products for the projections (Algorithm 3 lines 6a-9; Algorithm 4 lines
-// 1c, 7a, 12a), the orthogonalisation update with its fused norm, the
-// row-tiled solution and recycle updates (lines 13-13a, 14a) and the harmonic
+// products for the projections (Algorithms 3 and 4), the orthogonalisation
+// update with its fused norm, the row-tiled solution and recycle updates
+// (Algorithm 3) and the harmonic
 // Ritz inner products — with every multiply-add in double-float arithmetic
 // on the FP32 pipe (rk_df.cuh). Inner loops contain no FP64 instruction and
 // no FP64<->FP32 conversion (both issue at the FP64 rate on GB300); per-thread
@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(kRedThreads) k_dfupdate2(DFUpdate2Args a) {
   }
 }
 
-// Row-tiled X P (the solution and recycle updates, lines 13-13a and 14a)
+// Row-tiled X P (the solution and recycle updates of Algorithm 3)
 // with X = [A (na DF cols), diag(bscale) Bm (nb DF cols)] and P (np x nc,
 // FP64, column-major). P is held in shared memory as DF, transposed and
 // zero-padded to ncg * CB columns. A block of ncg * tr threads takes a tile
@@ -610,7 +610,7 @@ __global__ void __launch_bounds__(kRedThreads) k_dfgemv(DFGemmArgs a) {
 }
 
 // Gram blocks out[q + l*np] = sum_i X_q[i] d[i] U_l[i] (the inner products
-// of the harmonic Ritz problem, line 14a). Each thread owns a 4 x 4 set of
+// of the harmonic Ritz problem of the recycle update). Each thread owns a 4 x 4 set of
 // (q, l) pairs (strided by the number of sets) and a slice of the tile's rows (rows r = slice, slice + ns,
 // ...); per row it reads 4 X and 4 Y values for 16 double-float
 // multiply-adds. Tiles are row-major with odd strides (8-byte elements, so
@@ -746,7 +746,7 @@ __global__ void __launch_bounds__(kRedThreads) k_from_df(int64_t n, const float2
       dst[c * ldd + i] = df_to_double(__ldg(&src[c * lds + i]));
 }
 
-// x += dinv .* xt (FP64), the M^{-1} x~ of Algorithm 4 line 17a
+// x += dinv .* xt (FP64), the final M^{-1} x~ of Algorithm 4
 __global__ void __launch_bounds__(kRedThreads) k_axpy_scaled(int64_t n, const double* __restrict__ s,
                                                              const double* __restrict__ v, double* __restrict__ x) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)

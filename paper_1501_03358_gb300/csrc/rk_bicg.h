@@ -8,9 +8,9 @@ struct BicgVecs {
   double* r;   // residual r_i (orthogonal to C)
   double* rt;  // shadow residual r~ = r_0
   double* p;   // search direction (preconditioned space)
-  double* v;   // A M^{-1} p, projected (line 7a)
+  double* v;   // A M^{-1} p, projected onto C's complement
   double* s;   // s = r - alpha v
-  double* t;   // A M^{-1} s, projected (line 12a)
+  double* t;   // A M^{-1} s, projected onto C's complement
   double* xt;  // x~: sum of alpha p + omega s (preconditioned space)
 };
 
@@ -25,7 +25,7 @@ struct BicgScalars {
   int matvecs;     // matrix-vector products of this pass
   int flag;        // 0 running, 1 converged (updated residual), 2 breakdown
   int stop;        // nonzero: the remaining kernels of the batch return
-  int half;        // 1: converged at line 9 (x~ += alpha p pending)
+  int half;        // 1: converged at the half step (x~ += alpha p pending)
   int maxmv;       // cap on matrix-vector products of this pass (flag 3 when reached)
   int pad[2];
 };

@@ -1,9 +1,9 @@
 // Single-block kernels on the small problems of the Krylov cycle:
-//  - the Givens least-squares update of each Arnoldi step (Algorithm 1/3,
-//    line 12, with the in-cycle residual estimate of the note under
-//    Algorithm 1) and the cycle's solve (lines 12-12a);
-//  - the harmonic Ritz selection of the recycle space (Algorithm 3, line
-//    14a), done entirely on the device:
+//  - the Givens least-squares update of each Arnoldi step (Algorithms 1
+//    and 3, with the in-cycle residual estimate of the note under
+//    Algorithm 1) and the cycle's solve for y and z = -B y;
+//  - the harmonic Ritz selection of the recycle space (Algorithm 3's
+//    recycle update), done entirely on the device:
 //      G = Q_G R_G (Householder),  M'' = (Q_G^T F) R_G^{-1},
 //      real Schur form of M'' (Hessenberg + Francis double-shift QR),
 //      eigenvectors of the k eigenvalues mu = 1/theta of largest modulus,
@@ -24,8 +24,8 @@ namespace {
 constexpr int kHRThreads = 128;
 
 // ---------------------------------------------------------------- Arnoldi
-// One step of the Arnoldi process (Algorithm 1 lines 4-11; Algorithm 3 lines
-// 6-11 with Q = [C, V]) by classical Gram-Schmidt with delayed
+// One step of the Arnoldi process (Algorithm 1; Algorithm 3 with
+// Q = [C, V]) by classical Gram-Schmidt with delayed
 // reorthogonalisation: the stored column j holds p_j, orthogonalised once
 // and scaled by an estimate of its norm, and column j+1 holds w = A M^{-1} p_j.
 // With Q = [C, v_0 .. v_{j-1}] and dots = [a = Q^T p_j, b = Q^T w, p^T p,
@@ -171,7 +171,7 @@ __global__ void k_dcgs_coef(SolveState* s, SmallBuffers b, int kc, int j, int fi
   }
 }
 
-// Lines 12-12a: y = R^{-1} g (the Givens-rotated least squares), z = -B y,
+// The cycle's solve: y = R^{-1} g (the Givens-rotated least squares), z = -B y,
 // and the coefficients of the solution update. Column-oriented back
 // substitution: the reciprocals of the diagonal are formed in parallel,
 // then per column one scalar and a parallel update of the right-hand side
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_cycle_solve(SolveState* s, Sm
   for (int q = threadIdx.x; q < kc; q += blockDim.x) {
     double z = 0.0;
     for (int l = 0; l < jj; ++l) z = fma(b.B[q + (int64_t)l * b.kmax], y[l], z);
-    b.xcoef[q] = -z;  // z = -B y (line 12a)
+    b.xcoef[q] = -z;  // z = -B y
   }
   for (int l = threadIdx.x; l < jj; l += blockDim.x) {
     b.y[l] = y[l];
@@ -1038,7 +1038,7 @@ __global__ void __launch_bounds__(kHRThreads) k_harmonic_ritz_small(int n, const
 }
 
 // Cholesky G = R^T R of a k x k Gram matrix and R^{-1} (upper), one thread;
-// used by the CholQR of line 1a (C~ = A U = C R). status: 0 ok, 1 not SPD.
+// used by the CholQR that forms C from U (C~ = A U = C R). status: 0 ok, 1 not SPD.
 __global__ void k_chol_rinv(int k, const double* G, double* Rinv, double* Rw, int* status) {
   if (threadIdx.x != 0) return;
   for (int t = 0; t < k * k; ++t) Rw[t] = 0.0;

@@ -519,7 +519,7 @@ int opapply_launch(rk_problem* p, int precision, const void* v, bool v_df, void*
   return RK_OK;
 }
 
-// C = orth(A U) in FP64 with U rescaled so that A U = C (CholQR2 of line 1a)
+// C = orth(A U) in FP64 with U rescaled so that A U = C (CholQR2, as when C is formed from U)
 // for the k stored columns.
 int derive_c_from_u(rk_problem* p, int k, cudaStream_t st) {
   float2* Ud = p->Ublk(k);
@@ -558,7 +558,7 @@ int derive_c_from_u(rk_problem* p, int k, cudaStream_t st) {
   return RK_OK;
 }
 
-// Line 1b at the start of a cycle: xi = C^T r, r <- r - C xi, x <- x + U xi;
+// Projection onto C at the start of a cycle: xi = C^T r, r <- r - C xi, x <- x + U xi;
 // ||r||^2 -> st->rho2 (r and x FP64).
 int project_residual(rk_problem* p, int kc, double* r, double* x, cudaStream_t st) {
   if (kc == 0) return RK_OK;  // ||r||^2 already in st->rho2
@@ -604,7 +604,7 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
     return RK_OK;
   }
   const double tolabs = prm.tol * bnorm;
-  // line 1: r = b - A x (FP64); line 1b
+  // initial residual r = b - A x (FP64); its projection onto C
   double* r = p->rvec;
   RK_TRY(stencil_launch(p, ST_RESID, x, b, r, p->part, p->counter, &p->st->rho2, nullptr, st));
   RK_TRY(project_residual(p, kc, r, x, st));
@@ -616,16 +616,16 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
   const int* done = &p->st->done;
   while (rho > tolabs && matvecs < maxmv) {
     const int steps = std::min(m, maxmv - matvecs);
-    // one Arnoldi cycle (lines 4-11 and the second pass of the last vector):
+    // one Arnoldi cycle (and the second pass of the last vector):
     // a fixed launch sequence whose kernels skip themselves once the device
     // flags say the cycle has stopped, so it is captured once per shape into
     // a CUDA graph and replayed (not while the per-kernel profiler runs)
     const bool keep_last = update && k > 0;
     auto cycle = [&](cudaStream_t st) -> int {
-      // v_1 = r / rho, stored double-float (line 4)
+      // v_1 = r / rho, stored double-float
       RK_CUDA(launch_to_df(p->n, r, p->Vcol(0), &p->st->rho2, 1, 1, p->ld, p->ld, st));
       { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_cycle_init(p->st, p->sb, st)); }
-      // lines 6-11: one product, one fused inner-product pass and one update
+      // per step: one product, one fused inner-product pass and one update
       // pass per step (Gram-Schmidt against [C V_j] with the second pass of
       // each vector delayed to the next step)
       for (int j = 0; j < steps; ++j) {
@@ -676,11 +676,11 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
     est = p->st_h->est / bnorm;
     matvecs += p->st_h->nspmv;
     cycles += 1;
-    // lines 12-13a: y, z = -B y, x <- x + M^{-1} V_j y + U z
+    // y, z = -B y, x <- x + M^{-1} V_j y + U z
     { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_cycle_solve(p->st, p->sb, kc, st)); }
     RK_TRY(dfgemm_launch(p, p->Ublk(kc), kc, p->Vcol(0), jj, p->dinv, p->sb.xcoef, 1, x, false, 1, st));
     words += model_words_cycle(p->S, kc, jj, m);
-    // line 14a: recycle update (harmonic Ritz)
+    // recycle update (harmonic Ritz)
     if (update && k > 0) {
       if (kc > 0) {
         DFGramArgs g{};
@@ -713,7 +713,7 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
         words += 6.0 * kc + 3.0 * jj + 4;
       }
     }
-    // line 14: r = b - A x (true residual); next cycle's line 1b
+    // true residual r = b - A x; the next cycle projects it onto C
     RK_TRY(stencil_launch(p, ST_RESID, x, b, r, p->part, p->counter, &p->st->rho2, nullptr, st));
     RK_TRY(project_residual(p, kc, r, x, st));
     RK_TRY(sync_state(p, st));
@@ -775,7 +775,7 @@ int solve_bicg(rk_problem* p, const double* b, double* x, const rk_solve_params&
   int status = RK_E_NOT_CONVERGED;
   const int NB = 8;
   while (true) {
-    // line 1: r = b - A x; line 1c: eta1 = C^T r, r -= C eta1, xi = -eta1
+    // r = b - A x; its projection: eta1 = C^T r, r -= C eta1, xi = -eta1
     RK_TRY(stencil_launch(p, ST_RESID, x, b, v.r, p->part, p->counter, &p->st->rho2, nullptr, st));
     if (kc) {
       RK_TRY(dfdots_launch(p, p->Cblk(kc), kc, v.r, false, xi, nullptr, st));
@@ -811,7 +811,7 @@ int solve_bicg(rk_problem* p, const double* b, double* x, const rk_solve_params&
     upd = p->bs_h->upd;
     words += (double)p->bs_h->it * (2 * S + 4.0 * kc + 22);
     const int flag = p->bs_h->flag;
-    // line 17a: x <- x + M^{-1} x~ - U xi
+    // final fold: x <- x + M^{-1} x~ - U xi
     {
       RK_CUDA(launch_axpy_scaled(p->n, p->dinv, v.xt, x, st));
       if (kc) {
@@ -1101,7 +1101,7 @@ int rk_set_recycle(rk_problem* p, const double* U, const double* C, int32_t k, v
     return RK_OK;
   };
   if (!C) {
-    // line 1a: C~ = A U; thin QR by CholQR2 (C~ = C R), U <- U R^{-1}
+    // forming C from U: C~ = A U; thin QR by CholQR2 (C~ = C R), U <- U R^{-1}
     RK_TRY(derive_c_from_u(p, k, st));
   } else {
     RK_CUDA(launch_to_df(p->n, C, Cd, nullptr, 0, k, p->n, p->ld, st));

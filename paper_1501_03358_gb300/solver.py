@@ -80,7 +80,7 @@ class Context:
         return out[:nq]
 
     def harmonic_ritz(self, G, F, k, stream=None):
-        """Device harmonic Ritz selection of line 14a: returns (QC, PU) as
+        """Device harmonic Ritz selection of the recycle update (Algorithm 3): returns (QC, PU) as
         ((n+1) x knew, n x knew) tensors (see include/rk.h)."""
         G = _f64_cuda(G)
         F = _f64_cuda(F)

@@ -1,4 +1,4 @@
-"""The device harmonic Ritz selection (Algorithm 3, line 14a) through the C
+"""The device harmonic Ritz selection (Algorithm 3's recycle update) through the C
 ABI, against SciPy's generalized eigensolver on the same small pencils."""
 import numpy as np
 import pytest

@@ -200,7 +200,7 @@ def test_gmres_parity(ctx, cfg_id, size, m):
 @pytest.mark.parametrize("cfg_id,size,m,k,steps", [(1, 12, 30, 10, 5), (2, 12, 40, 20, 4), (1, 9, 6, 4, 4)])
 def test_rgcrot_sequence_parity(ctx, cfg_id, size, m, k, steps):
     """rGCROT(m,k) over a sequence of right-hand sides with the recycle space
-    carried across steps (Algorithm 3 with line 14a after every cycle)."""
+    carried across steps (Algorithm 3, recycle update after every cycle)."""
     cfg = make_config(cfg_id, size=size)
     prob = gpu_problem(ctx, cfg.grid, cfg.coef)
     op = oracle.Stencil(cfg.grid, cfg.coef)
@@ -226,7 +226,7 @@ def test_rgcrot_sequence_parity(ctx, cfg_id, size, m, k, steps):
 
 @pytest.mark.parametrize("cfg_id,size,m,k", [(1, 10, 12, 6), (2, 10, 20, 8), (1, 8, 30, 10)])
 def test_harmonic_ritz_cycles_match_oracle(ctx, cfg_id, size, m, k):
-    """Recycle space after one and after two cycles (line 14a by harmonic Ritz
+    """Recycle space after one and after two cycles (updated by harmonic Ritz
     vectors, computed on the device) spans the oracle's (SciPy eig of the
     pencil) to within rounding-level principal angles."""
     cfg = make_config(cfg_id, size=size)
@@ -243,7 +243,7 @@ def test_harmonic_ritz_cycles_match_oracle(ctx, cfg_id, size, m, k):
         assert subspace_gap(Cg, C) <= 1e-6, (cyc, subspace_gap(Cg, C))
 
 
-def test_recycle_set_get_roundtrip_and_line_1a(ctx):
+def test_recycle_set_get_roundtrip_and_forming_c(ctx):
     cfg = make_config(1, size=10)
     prob = gpu_problem(ctx, cfg.grid, cfg.coef)
     op = oracle.Stencil(cfg.grid, cfg.coef)
@@ -254,7 +254,7 @@ def test_recycle_set_get_roundtrip_and_line_1a(ctx):
     U2, C2 = prob.get_recycle()
     assert np.all(np.abs(U2.cpu().numpy() - U.T) <= 2.0 ** -46 * np.abs(U.T))
     assert np.all(np.abs(C2.cpu().numpy() - C.T) <= 2.0 ** -46 * np.abs(C.T))
-    # C omitted: line 1a forms C = orth(A U) and rescales U so that A U = C
+    # C omitted: the library forms C = orth(A U) and rescales U so that A U = C
     Uraw = U @ np.diag([1.0, 2.0, -3.0, 0.5, 4.0, 1.5][:kk])
     prob.set_recycle(t(Uraw.T))
     U3, C3 = prob.get_recycle()

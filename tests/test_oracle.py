@@ -176,7 +176,7 @@ def test_harmonic_ritz_values_dense():
 
 
 def test_exact_recycling():
-    """If b lies in range(C) the initial projection (line 1b / 1c) solves the
+    """If b lies in range(C) the initial projection onto C solves the
     system: no matrix-vector products and x = U C^T b."""
     name, grid, coef, b = PROBS[0]
     op = Stencil(grid, coef)
