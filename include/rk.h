@@ -187,6 +187,26 @@ int rk_dots(rk_context* ctx, int64_t n, int32_t nq, const double* Q, int64_t ld,
             double* out, void* stream);
 
 /*
+ * The row-tiled product of the recycle updates of Algorithm 3 (C <- W_hat QC,
+ * U <- W PU) on its own: out = [A, diag(s) B] P with A (N x na) and B
+ * (N x nb) device FP64 column-major (leading dimensions lda, ldb >= N; either
+ * part may be empty), s device N doubles or NULL (identity), P device FP64
+ * (na + nb) x nc column-major with leading dimension na + nb, out device
+ * N x nc FP64 (leading dimension ldo >= N). A and B are first rounded to
+ * double-float, as the solver stores its basis. engine = 1 runs the
+ * tensor-core kernel the solver uses for 2 <= nc <= 32 and na + nb <= 64
+ * (7 BF16 digits per operand, exact FP32 accumulation per digit level on the
+ * fifth-generation tensor cores); engine = 0 the double-float kernel on the
+ * FP32 pipe. RK_E_INVALID for bad arguments or a shape the tensor-core
+ * engine does not take; RK_E_DEVICE_TIMEOUT if a bounded device wait gave
+ * up. Allocates temporary device memory through the context's allocator;
+ * synchronises `stream`. No counterpart in the paper (a test entry point).
+ */
+int rk_row_gemm(rk_context* ctx, int64_t n, int32_t na, const double* A, int64_t lda, int32_t nb,
+                const double* B, int64_t ldb, const double* s, const double* P, int32_t nc, double* out,
+                int64_t ldo, int32_t engine, void* stream);
+
+/*
  * Solve n independent problems, one right-hand side each (one time step of
  * n sequences; the batched and serving workloads of the recycling solver).
  * Equivalent to calling rk_solve(problems[i], b[i], x[i], &params[i],

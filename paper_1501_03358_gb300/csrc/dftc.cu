@@ -1,0 +1,375 @@
+// Row-tiled double-float X P on the tensor cores (the in-place recycle
+// updates C <- W_hat QC and U <- W PU of Algorithm 3).
+//
+// A double-float product cannot run on BF16 tensor cores directly, but an
+// integer one can, exactly: each row r of X = [A, diag(bscale) Bm] is scaled
+// by a power of two 2^-E_r (|x| < 2^E_r over the row) and written as seven
+// signed 8-bit digits, x = 2^E_r sum_i s_i 256^-i (s_1 in [-256, 256], the
+// others in [-128, 128]); each column c of P likewise with 2^F_c and digits
+// t_j. BF16 holds such integers exactly, a digit product is an integer of at
+// most 2^16, and FP32 accumulation is exact while a sum stays below 2^24.
+// The products are grouped by level L = i + j:
+//   X P = 2^(E_r + F_c) sum_L 256^-L (sum_{i+j=L} s_i t_j),
+// each level accumulated exactly in its own 32 TMEM columns (K <= 64 keeps
+// every level sum below 2^23.2). Levels 2..8 are kept (28 digit pairs); what
+// is dropped lies below 2^-50 of |X||P|, and seven digits hold all 48 bits
+// of a double-float value within 2^8 of its row's largest. For digit row i,
+// one MMA with B = [t_1 | ... | t_(8-i)] (N = 32 (8 - i)) accumulates every
+// level i + j at once into TMEM columns 32 (i - 1) .. 223, so a 16-wide K
+// step is 7 MMAs. The epilogue reads the 7 level sums, combines them in
+// double-float (every term exact) and applies 2^(E_r + F_c).
+//
+// One block per SM, a persistent loop over tiles of 128 rows (one TMEM lane
+// per row). Eight producer warps: warp w owns rows 32 (w % 4) .. +31 (its
+// TMEM lanes) and half w / 4 of K. One issuer warp: it brings each tile of X
+// (and the row scales) into shared memory by bulk asynchronous copies one
+// tile ahead, and issues the MMAs. Per tile a producer finds its half-row
+// maximum, trades it with the warp owning the other half (a 64-thread named
+// barrier), writes per 16 columns of K its 8 x 7 digits into one of two
+// digit buffers (canonical K-major layout) and arrives on the buffer's
+// "full" barrier; the issuer waits for all eight warps, issues the 7 MMAs
+// and commits them to the buffer's "free" barrier. After the tile's last
+// MMAs a commit on "tmem full" releases the epilogue, in which each producer
+// reads its lanes' level sums for its 16 output columns; "tmem free" lets
+// the issuer start the next tile. No block-wide barrier inside the loop. The
+// digits of P are made once per launch by k_tc_digits_p.
+#include <cuda_bf16.h>
+
+#include "rk_internal.h"
+#include "rk_df.cuh"
+#include "rk_tcgen05.cuh"
+
+namespace rk {
+
+namespace {
+
+constexpr int kTcRows = 128;                    // rows per tile = MMA M = TMEM lanes
+constexpr int kTcProducers = 8;                 // producer warps (two per row: K halves)
+constexpr int kTcThreads = 32 * (kTcProducers + 1);  // + the issuer warp
+constexpr int kTcDigits = 7;                    // digits per operand
+constexpr float kTcBase = 256.f;                // digit base
+constexpr int kTcCols = 32;                     // output columns per level (MMA N per digit of P)
+constexpr int kTcTmem = 256;                    // 7 levels x 32 columns, rounded to a power of two
+constexpr int kTcKMax = 64;                     // K <= 64 keeps every level sum exact
+constexpr int kTcPlane = kTcRows * 16 * 2;      // one digit plane of a 16-wide K step (bytes)
+constexpr int kTcABuf = kTcDigits * kTcPlane;   // 28 KB per digit buffer
+constexpr int kTcBRows = kTcDigits * kTcCols;   // 224 rows of B: (digit j, column c)
+constexpr int kTcBBytes = kTcBRows * kTcKMax * 2;             // 28 KB
+constexpr int kTcXBuf = kTcRows * kTcKMax * (int)sizeof(float2);  // 64 KB per X tile
+constexpr size_t kTcSmem = 2 * (size_t)kTcXBuf + 2 * (size_t)kTcABuf + kTcBBytes + 2 * kTcRows * sizeof(double);
+
+// element offset of (row, k) in a K-major canonical operand with kg 8-wide
+// core-matrix columns along K
+__host__ __device__ __forceinline__ int tc_off(int row, int k, int kg) {
+  return (((row >> 3) * kg + (k >> 3)) << 6) + ((row & 7) << 3) + (k & 7);
+}
+
+// Digits of P (np x nc, FP64, column-major, leading dimension np): B rows
+// n = 32 j + c hold digit j+1 of column c over k = 0..kp-1 (zero outside
+// np x nc); fexp[c] = F_c. Seven base-256 digits hold all 53 bits.
+__global__ void k_tc_digits_p(int np, int nc, int kp, const double* __restrict__ P, __nv_bfloat16* __restrict__ B,
+                              int* __restrict__ fexp) {
+  __shared__ int fs[kTcCols];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int c = warp; c < kTcCols; c += nwarp) {
+    double m = 0.0;
+    if (c < nc)
+      for (int q = lane; q < np; q += 32) m = fmax(m, fabs(P[(int64_t)c * np + q]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) fs[c] = m > 0.0 ? ilogb(m) + 1 : 0;  // |P_qc| < 2^F_c
+  }
+  __syncthreads();
+  const int kg = kp >> 3;
+  for (int t = threadIdx.x; t < kTcCols * kp; t += blockDim.x) {
+    const int c = t / kp, q = t - c * kp;
+    double y = (c < nc && q < np) ? ldexp(P[(int64_t)c * np + q], -fs[c]) : 0.0;
+    for (int j = 0; j < kTcDigits; ++j) {
+      y *= 256.0;
+      const double d = rint(y);
+      y -= d;
+      B[tc_off(j * kTcCols + c, q, kg)] = __double2bfloat16(d);
+    }
+  }
+  if (threadIdx.x < kTcCols) fexp[threadIdx.x] = fs[threadIdx.x];
+}
+
+// Two digits (integers of at most 9 significant bits, so the low 16 bits of
+// their FP32 encodings are zero) as a BF16 pair: the high halves, lo first.
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
+}
+
+// Round to the nearest integer, ties to even, for |y| < 2^22: adding and
+// subtracting 1.5 * 2^23 leaves no fraction bits (two FP32 adds).
+__device__ __forceinline__ float round_small(float y) {
+  const float m = 12582912.f;
+  return __fsub_rn(__fadd_rn(y, m), m);
+}
+
+// x * 2^ex for the epilogue: exponent arithmetic when x and the result are
+// normal numbers, ldexpf otherwise
+__device__ __forceinline__ float scale_pow2(float x, int ex) {
+  const unsigned u = __float_as_uint(x);
+  const int e = (int)((u >> 23) & 0xffu);
+  if (e >= 1 && e <= 254 && e + ex >= 1 && e + ex <= 254) return __uint_as_float(u + ((unsigned)ex << 23));
+  return ldexpf(x, ex);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_dfgemm_tc(DFGemmArgs a, const __nv_bfloat16* __restrict__ bdig,
+                                                                const int* __restrict__ fexp, int kp, int bulk_ok,
+                                                                int* err) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  float2* xs = reinterpret_cast<float2*>(tsm);               // [2][kTcKMax][kTcRows] X tiles
+  unsigned char* dg = tsm + 2 * kTcXBuf;                      // [2] digit buffers
+  unsigned char* sB = dg + 2 * kTcABuf;                       // digits of P
+  double* bsv = reinterpret_cast<double*>(sB + kTcBBytes);    // [2][kTcRows] row scales
+  __shared__ __align__(8) uint64_t xfull[2], xfree[2], dfull[2], dfree[2], tfull, tfree;
+  __shared__ uint32_t tslot;
+  __shared__ int fs[kTcCols];
+  __shared__ float rmax[2][2][kTcRows];  // [tile parity][K half][row]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int np = a.na + a.nb;
+  const int kg = kp >> 3, nks = kp >> 4;
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(bdig);
+    uint4* dst = reinterpret_cast<uint4*>(sB);
+    const int n16 = kTcBRows * kp * 2 / 16;
+    for (int i = tid; i < n16; i += kTcThreads) dst[i] = __ldg(&src[i]);
+  }
+  if (tid < kTcCols) fs[tid] = fexp[tid];
+  if (warp == 0) tc_alloc(&tslot, kTcTmem);
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&xfull[b], 1);
+      mbar_init(&xfree[b], kTcProducers);
+      mbar_init(&dfull[b], kTcProducers);
+      mbar_init(&dfree[b], 1);
+    }
+    mbar_init(&tfull, 1);
+    mbar_init(&tfree, kTcProducers);
+    mbar_init_fence();
+  }
+  fence_async_shared();
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
+  const uint32_t taddr = tslot;
+  const int64_t ntiles = (a.n + kTcRows - 1) / kTcRows;
+  // a tile comes by bulk copies when it is full and the operands are aligned
+  // (only the ragged last tile, or every tile of unaligned operands, does not)
+  auto is_bulk = [&](int64_t t) { return bulk_ok != 0 && (t + 1) * kTcRows <= a.n; };
+  bool ok = true;
+  auto wait = [&](uint64_t* bar, unsigned parity) { ok = mbar_wait_bounded(bar, parity) && ok; };
+  if (warp == kTcProducers) {
+    // ---------------------------------------------------------------- issuer
+    if (lane == 0) {
+      auto issue = [&](int64_t t, int b) {
+        const int64_t r0 = t * kTcRows;
+        const unsigned bytes = kTcRows * (unsigned)sizeof(float2);
+        fence_async_shared();
+        mbar_arrive_expect_tx(&xfull[b], bytes * np + (a.bscale ? kTcRows * (unsigned)sizeof(double) : 0u));
+        for (int q = 0; q < np; ++q) {
+          const float2* src = q < a.na ? a.A + (int64_t)q * a.lda + r0 : a.Bm + (int64_t)(q - a.na) * a.ldb + r0;
+          bulk_g2s(xs + ((int64_t)b * kTcKMax + q) * kTcRows, src, bytes, &xfull[b]);
+        }
+        if (a.bscale) bulk_g2s(bsv + b * kTcRows, a.bscale + r0, kTcRows * (unsigned)sizeof(double), &xfull[b]);
+      };
+      const uint32_t bdesc0 = smem_u32(sB), dg_u = smem_u32(dg);
+      int cc = 0, it = 0;
+      for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int xb = it & 1;
+        if (it == 0 && is_bulk(tile)) issue(tile, 0);
+        const int64_t nx = tile + gridDim.x;
+        if (nx < ntiles && is_bulk(nx)) {
+          if (it >= 1) wait(&xfree[xb ^ 1], (unsigned)(((it - 1) >> 1) & 1));  // tile it-1 read that buffer
+          issue(nx, xb ^ 1);
+        }
+        if (it >= 1) wait(&tfree, (unsigned)((it - 1) & 1));  // the previous epilogue has read TMEM
+        for (int ks = 0; ks < nks; ++ks, ++cc) {
+          const int b = cc & 1;
+          wait(&dfull[b], (unsigned)((cc >> 1) & 1));
+          tc_fence_after_sync();
+#pragma unroll
+          for (int i = 0; i < kTcDigits; ++i) {
+            const uint64_t ad = tc_smem_desc(dg_u + b * kTcABuf + i * kTcPlane, 128, 256);
+            const uint64_t bd = tc_smem_desc(bdesc0 + ks * 256, 128, kg * 128);
+            tc_mma_bf16(taddr + kTcCols * i, ad, bd, tc_idesc_bf16(kTcRows, kTcCols * (kTcDigits - i)),
+                        (ks > 0 || i > 0) ? 1u : 0u);
+          }
+          tc_commit(&dfree[b]);
+        }
+        tc_commit(&tfull);
+      }
+    }
+  } else {
+    // ---------------------------------------------------------------- producers
+    const int rl = 32 * (warp & 3) + lane;  // row in the tile = TMEM lane
+    const int half = warp >> 2;             // K half for digits, column half in the epilogue
+    const int pairbar = 1 + (warp & 3);     // named barrier of warps w and w + 4
+    int cc = 0, it = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+      const int xb = it & 1;
+      const int64_t r0 = tile * kTcRows;
+      const int64_t row = r0 + rl;
+      const bool valid = row < a.n;
+      float2* X = xs + (int64_t)xb * kTcKMax * kTcRows;
+      double* bs = bsv + xb * kTcRows;
+      if (is_bulk(tile)) {
+        wait(&xfull[xb], (unsigned)((it >> 1) & 1));
+      } else {
+        // this thread's own elements (its row, its K half) and row scale
+        for (int ks = 0; ks < nks; ++ks)
+          for (int e = 0; e < 8; ++e) {
+            const int q = ks * 16 + half * 8 + e;
+            if (q >= np) break;
+            float2 v = make_float2(0.f, 0.f);
+            if (valid)
+              v = q < a.na ? __ldg(&a.A[(int64_t)q * a.lda + row]) : __ldg(&a.Bm[(int64_t)(q - a.na) * a.ldb + row]);
+            X[q * kTcRows + rl] = v;
+          }
+        if (a.bscale) bs[rl] = valid ? __ldg(&a.bscale[row]) : 0.0;
+      }
+      const float2 sc = a.bscale ? df_from_double_i(bs[rl]) : make_float2(1.f, 0.f);
+      // the B part scaled by the row scale once, in place; half-row maximum
+      float mx = 0.f;
+      for (int ks = 0; ks < nks; ++ks)
+        for (int e = 0; e < 8; ++e) {
+          const int q = ks * 16 + half * 8 + e;
+          if (q >= np) break;
+          float2 x = X[q * kTcRows + rl];
+          if (q >= a.na) {
+            x = df_mul(x, sc);
+            X[q * kTcRows + rl] = x;
+          }
+          mx = fmaxf(mx, fabsf(x.x));
+        }
+      rmax[xb][half][rl] = mx;
+      named_barrier_sync(pairbar, 64);
+      mx = fmaxf(rmax[xb][0][rl], rmax[xb][1][rl]);
+      int E = mx > 0.f ? ilogbf(mx) + 1 : 0;
+      E = E < -125 ? -125 : (E > 126 ? 126 : E);  // keep 2^-E a normal FP32 number
+      const float scale = __int_as_float((127 - E) << 23);
+      for (int ks = 0; ks < nks; ++ks, ++cc) {
+        const int b = cc & 1;
+        if (cc >= 2) wait(&dfree[b], (unsigned)(((cc >> 1) - 1) & 1));  // the MMAs that read it last
+        unsigned char* buf = dg + b * kTcABuf;
+        uint32_t pk[kTcDigits][4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+          float d0[kTcDigits], d1[kTcDigits];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int q = ks * 16 + half * 8 + e + u;
+            const float2 x = q < np ? X[q * kTcRows + rl] : make_float2(0.f, 0.f);
+            float yh = x.x * scale, yl = x.y * scale;  // exact (power of two)
+#pragma unroll
+            for (int i = 0; i < kTcDigits; ++i) {
+              yh *= kTcBase;
+              yl *= kTcBase;
+              const float sd = round_small(yh);
+              const float rh = yh - sd;  // exact: the fraction of yh
+              const float t = rh + yl;   // Fast2Sum: rh == 0 or |rh| >= 2 |yl|
+              yl = yl - (t - rh);
+              yh = t;
+              (u ? d1 : d0)[i] = sd;
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < kTcDigits; ++i) pk[i][e >> 1] = pack_bf16(d0[i], d1[i]);
+        }
+        const int off = (((rl >> 3) * 2 + half) << 7) + ((rl & 7) << 4);
+#pragma unroll
+        for (int i = 0; i < kTcDigits; ++i)
+          *reinterpret_cast<uint4*>(buf + i * kTcPlane + off) = make_uint4(pk[i][0], pk[i][1], pk[i][2], pk[i][3]);
+        fence_async_shared();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&dfull[b]);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&xfree[xb]);  // done with this X tile
+      // epilogue: this warp's 32 lanes, output columns 16 half .. +15
+      wait(&tfull, (unsigned)(it & 1));
+      tc_fence_after_sync();
+      if (half * 16 < a.nc) {
+        const uint32_t tl = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + 16 * half;
+        float sh[16], sl[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) sh[u] = sl[u] = 0.f;
+#pragma unroll
+        for (int L = kTcDigits + 1; L >= 2; --L) {
+          float v[16];
+          tc_load16(tl + kTcCols * (L - 2), v);
+          const float w = __int_as_float((127 - 8 * L) << 23);  // 256^-L
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const float p = v[u] * w;  // exact
+            const float s2 = sh[u] + p;
+            const float bb = s2 - sh[u];
+            sl[u] += (sh[u] - (s2 - bb)) + (p - bb);
+            sh[u] = s2;
+          }
+        }
+        if (valid) {
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const int c = 16 * half + u;
+            if (c < a.nc) {
+              const float hi = sh[u] + sl[u];
+              const float lo = sl[u] - (hi - sh[u]);
+              const int ex = E + fs[c];
+              reinterpret_cast<float2*>(a.out)[(int64_t)c * a.ldo + row] =
+                  make_float2(scale_pow2(hi, ex), scale_pow2(lo, ex));
+            }
+          }
+        }
+      }
+      tc_fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tfree);
+    }
+  }
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
+  if (warp == 0) tc_dealloc(taddr, kTcTmem);
+  if (!ok && err != nullptr) atomicExch(err, 3);
+}
+
+}  // namespace
+
+size_t dfgemm_tc_ws_bytes() { return (size_t)kTcBBytes + kTcCols * sizeof(int); }
+
+bool dfgemm_tc_supported(const DFGemmArgs& a, bool out_df) {
+  const int np = a.na + a.nb;
+  return out_df && a.accum == 0 && a.nc >= 2 && a.nc <= kTcCols && np >= 1 && np <= kTcKMax;
+}
+
+void dfgemm_tc_prepare() {
+  static const bool attr = [] {
+    cudaFuncSetAttribute(k_dfgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    return true;
+  }();
+  (void)attr;
+}
+
+cudaError_t launch_dfgemm_tc(const DFGemmArgs& a, void* ws, int* err, cudaStream_t st) {
+  const int np = a.na + a.nb;
+  const int kp = (np + 15) & ~15;
+  __nv_bfloat16* bdig = reinterpret_cast<__nv_bfloat16*>(ws);
+  int* fexp = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(ws) + kTcBBytes);
+  k_tc_digits_p<<<1, 256, 0, st>>>(np, a.nc, kp, a.P, bdig, fexp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  dfgemm_tc_prepare();
+  const int64_t ntiles = (a.n + kTcRows - 1) / kTcRows;
+  const int blocks = (int)(ntiles < kNumSM ? ntiles : kNumSM);
+  if (blocks == 0) return cudaSuccess;
+  // bulk copies need 16-byte aligned column segments
+  auto al16 = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
+  const int bulk_ok = (a.na == 0 || (al16(a.A) && (a.lda & 1) == 0)) && (a.nb == 0 || (al16(a.Bm) && (a.ldb & 1) == 0)) &&
+                      (a.bscale == nullptr || al16(a.bscale));
+  k_dfgemm_tc<<<blocks, kTcThreads, kTcSmem, st>>>(a, bdig, fexp, kp, bulk_ok, err);
+  return cudaGetLastError();
+}
+
+}  // namespace rk

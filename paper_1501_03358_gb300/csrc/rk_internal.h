@@ -169,6 +169,14 @@ struct DFGemmArgs {
   int accum;             // FP64 output only
 };
 cudaError_t launch_dfgemm_rows(const DFGemmArgs& a, bool out_df, cudaStream_t st);
+// The same product on the tensor cores (digit-sliced, exact FP32
+// accumulation; dftc.cu): DF output, 2 <= nc <= 32, na + nb <= 64. ws holds
+// dfgemm_tc_ws_bytes() (16-byte aligned); err receives 3 if a bounded wait
+// gave up.
+size_t dfgemm_tc_ws_bytes();
+bool dfgemm_tc_supported(const DFGemmArgs& a, bool out_df);
+cudaError_t launch_dfgemm_tc(const DFGemmArgs& a, void* ws, int* err, cudaStream_t st);
+void dfgemm_tc_prepare();
 
 struct DFGramArgs {
   int64_t n;

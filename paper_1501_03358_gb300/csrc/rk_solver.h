@@ -45,6 +45,7 @@ struct SmallBuffers {
   double* QC;     // (kmax + m + 1) x kmax: C <- W_hat QC
   double* PU;     // (kmax + m) x kmax:     U <- W PU
   double* hrws;   // workspace of the harmonic Ritz solve (global fallback)
+  double* tcws;   // digits of P for the tensor-core recycle update (dfgemm_tc_ws_bytes())
   size_t hrws_doubles;
 };
 

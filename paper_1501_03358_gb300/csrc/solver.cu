@@ -290,7 +290,8 @@ int ensure_capacity(rk_problem* p, int kneed, int mneed, cudaStream_t st) {
                og = take(m + 1), ocs = take(m), osn = take(m), osv = take(m + 2), ohacc = take(nq),
                odots = take(2 * (size_t)nq + 8), ocoef = take(nq), oy = take(m), ox = take(nq),
                ogram = take((size_t)(kmax + m + 1) * b.kmax), oQC = take((size_t)(kmax + m + 1) * b.kmax),
-               oPU = take((size_t)(kmax + m) * b.kmax), ows = take(b.hrws_doubles);
+               oPU = take((size_t)(kmax + m) * b.kmax), ows = take(b.hrws_doubles),
+               otc = take((dfgemm_tc_ws_bytes() + 7) / 8);
   RK_TRY(alloc_into(p->ctx, &p->small, total));
   p->small_n = total;
   b.H = p->small + oH;
@@ -309,6 +310,7 @@ int ensure_capacity(rk_problem* p, int kneed, int mneed, cudaStream_t st) {
   b.QC = p->small + oQC;
   b.PU = p->small + oPU;
   b.hrws = p->small + ows;
+  b.tcws = p->small + otc;
   RK_CUDA(cudaMemsetAsync(p->small, 0, total * sizeof(double), st));
   p->eta_n = (size_t)4 * (kmax + 4) + (size_t)kmax * kmax * 2 + 16;
   RK_TRY(alloc_into(p->ctx, &p->eta, p->eta_n));
@@ -448,7 +450,10 @@ int dfgemm_launch(rk_problem* p, const float2* A, int na, const float2* Bm, int 
   a.ldo = p->ld;
   a.accum = accum;
   ProfScope ps(&p->prof, PC_GEMM, 8.0 * (na + nb + nc * (accum ? 2 : 1) + (bscale ? 1 : 0)) * (double)p->n, st);
-  RK_CUDA(launch_dfgemm_rows(a, out_df, st));
+  if (p->sb.tcws != nullptr && dfgemm_tc_supported(a, out_df))
+    RK_CUDA(launch_dfgemm_tc(a, p->sb.tcws, &p->st->dev_err, st));
+  else
+    RK_CUDA(launch_dfgemm_rows(a, out_df, st));
   return RK_OK;
 }
 
@@ -918,6 +923,7 @@ int rk_create_problem(rk_context* ctx, const rk_grid* grid, int32_t S, const dou
   };
   int r;
   dfblas_prepare();
+  dfgemm_tc_prepare();
   if ((r = alloc_into(ctx, &p->coef, (size_t)S * p->n)) != RK_OK) return cleanup(r);
   if ((r = alloc_into(ctx, &p->dinv, (size_t)p->ld)) != RK_OK) return cleanup(r);
   if ((r = alloc_into(ctx, &p->counter, kCounters)) != RK_OK) return cleanup(r);
@@ -1061,6 +1067,61 @@ int rk_dots(rk_context* ctx, int64_t n, int32_t nq, const double* Q, int64_t ld,
   RK_CUDA(launch_dots(a, (cudaStream_t)stream));
   RK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
   return RK_OK;
+}
+
+int rk_row_gemm(rk_context* ctx, int64_t n, int32_t na, const double* A, int64_t lda, int32_t nb, const double* B,
+                int64_t ldb, const double* s, const double* P, int32_t nc, double* out, int64_t ldo, int32_t engine,
+                void* stream) {
+  if (!ctx || n <= 0 || na < 0 || nb < 0 || na + nb < 1 || nc < 1 || !P || !out || ldo < n ||
+      (na > 0 && (!A || lda < n)) || (nb > 0 && (!B || ldb < n)) || (engine != 0 && engine != 1))
+    return fail(RK_E_INVALID, "bad argument to rk_row_gemm");
+  cudaStream_t st = (cudaStream_t)stream;
+  DFGemmArgs a{};
+  a.n = n;
+  a.na = na;
+  a.nb = nb;
+  a.nc = nc;
+  a.bscale = s;
+  a.P = P;
+  a.ldo = n;
+  a.lda = n;
+  a.ldb = n;
+  a.accum = 0;
+  if (engine == 1 && !dfgemm_tc_supported(a, true))
+    return fail(RK_E_INVALID, "rk_row_gemm: the tensor-core engine needs 2 <= nc <= 32 and na + nb <= 64");
+  // double-float copies of the operands, as the solver stores them
+  const size_t cols = (size_t)na + nb + nc;
+  float2* buf = (float2*)dev_alloc(ctx, cols * (size_t)n * sizeof(float2));
+  void* ws = engine == 1 ? dev_alloc(ctx, dfgemm_tc_ws_bytes()) : nullptr;
+  int* err = (int*)dev_alloc(ctx, sizeof(int));
+  int rc = RK_OK;
+  if (!buf || !err || (engine == 1 && !ws)) {
+    rc = fail(RK_E_OOM, "rk_row_gemm: workspace allocation failed");
+  } else {
+    float2* Ad = buf;
+    float2* Bd = buf + (size_t)na * n;
+    float2* Od = Bd + (size_t)nb * n;
+    a.A = Ad;
+    a.Bm = Bd;
+    a.out = Od;
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e == cudaSuccess && na > 0) e = launch_to_df(n, A, Ad, nullptr, 0, na, lda, n, st);
+    if (e == cudaSuccess && nb > 0) e = launch_to_df(n, B, Bd, nullptr, 0, nb, ldb, n, st);
+    if (e == cudaSuccess) e = engine == 1 ? launch_dfgemm_tc(a, ws, err, st) : launch_dfgemm_rows(a, true, st);
+    if (e == cudaSuccess) e = launch_from_df(n, Od, out, nc, n, ldo, st);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess)
+      rc = fail(RK_E_CUDA, std::string("rk_row_gemm: ") + cudaGetErrorString(e));
+    else if (herr != 0)
+      rc = fail(RK_E_DEVICE_TIMEOUT, "rk_row_gemm: a bounded device wait gave up");
+  }
+  cudaStreamSynchronize(st);
+  dev_free(ctx, buf);
+  dev_free(ctx, ws);
+  dev_free(ctx, err);
+  return rc;
 }
 
 int rk_set_recycle(rk_problem* p, const double* U, const double* C, int32_t k, void* stream) {

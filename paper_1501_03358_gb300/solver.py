@@ -79,6 +79,26 @@ class Context:
         N.check(self.lib.rk_dots(self._h, n, nq, _dptr(Q), ld, _dptr(w), _dptr(out), _stream_ptr(stream)))
         return out[:nq]
 
+    def row_gemm(self, A, B, s, P, engine=1, stream=None):
+        """[A, diag(s) B] P for A (na, N), B (nb, N) row-contiguous (either may
+        be None), s (N,) or None, P (na + nb, nc): the recycle-update product
+        through rk_row_gemm (engine 1: tensor cores, 0: FP32 pipe). Returns
+        (nc, N)."""
+        n = (A if A is not None else B).shape[1]
+        A = _f64_cuda(A) if A is not None else None
+        B = _f64_cuda(B) if B is not None else None
+        s = _f64_cuda(s, (n,)) if s is not None else None
+        na = A.shape[0] if A is not None else 0
+        nb = B.shape[0] if B is not None else 0
+        P = _f64_cuda(P)
+        nc = P.shape[1]
+        Pc = P.t().contiguous()  # column-major (na + nb) x nc
+        out = torch.empty((nc, n), dtype=torch.float64, device="cuda")
+        N.check(self.lib.rk_row_gemm(self._h, n, na, _dptr(A) if A is not None else None, n, nb,
+                                     _dptr(B) if B is not None else None, n, _dptr(s) if s is not None else None,
+                                     _dptr(Pc), nc, _dptr(out), n, engine, _stream_ptr(stream)))
+        return out
+
     def harmonic_ritz(self, G, F, k, stream=None):
         """Device harmonic Ritz selection of the recycle update (Algorithm 3): returns (QC, PU) as
         ((n+1) x knew, n x knew) tensors (see include/rk.h)."""

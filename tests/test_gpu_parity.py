@@ -136,6 +136,57 @@ def test_block_dots(ctx, n, nq):
     assert np.all(np.abs(got - ref) <= bound)
 
 
+@pytest.mark.parametrize("engine", [1, 0])
+@pytest.mark.parametrize("n,na,nb,nc,scaled", [
+    (1, 3, 2, 2, False), (127, 20, 41, 20, True), (129, 61, 0, 20, False), (1000, 20, 40, 20, True),
+    (5003, 0, 64, 32, True), (4099, 32, 32, 7, False), (300, 1, 0, 2, False), (70000, 20, 41, 20, True),
+    (70001, 20, 41, 20, True)])
+def test_row_gemm_recycle_update(ctx, engine, n, na, nb, nc, scaled):
+    """[A, diag(s) B] P (the recycle-update product) against an exact
+    reference, element by element. FP32-pipe engine (double-float products,
+    lazy accumulation over up to 128 terms): |out - X P| <= 2^-44 (|X| |P|).
+    Tensor-core engine: the inputs rounded to double-float (2^-48 |X|), a
+    double-float epilogue, and the fixed-point digits, which truncate each
+    element below 2^-56 of its row's (X) or column's (P) largest:
+    |out - X P| <= 2^-45 (|X| |P|) + 2^-52 K max_row|X| max_col|P|.
+    Scales within a row and within a column of P span 2^8. 70000 rows
+    span hundreds of tiles per block (bulk-copied tiles prefetched one
+    ahead, then a ragged last tile); 70001 rows give operands the bulk copy
+    cannot take (odd leading dimension: every tile loaded by the threads)."""
+    rng = np.random.default_rng(n * 131 + na * 7 + nb + nc)
+    A = rng.standard_normal((na, n)) * np.exp2(rng.integers(-4, 5, size=(na, 1))) if na else None
+    B = rng.standard_normal((nb, n)) if nb else None
+    sv = np.exp(rng.standard_normal(n)) if scaled else None
+    P = rng.standard_normal((na + nb, nc)) * np.exp2(rng.integers(-4, 5, size=(na + nb, nc)))
+    X = np.concatenate([m for m in (A, None if B is None else (B * sv if scaled else B)) if m is not None], axis=0)
+    if scaled:
+        # the B part of the reference with the row scale applied exactly
+        Xl = np.concatenate([m.astype(np.longdouble) for m in (A,) if m is not None] +
+                            [B.astype(np.longdouble) * sv.astype(np.longdouble)], axis=0)
+    else:
+        Xl = X.astype(np.longdouble)
+    ref = (Xl.T @ P.astype(np.longdouble)).T
+    got = ctx.row_gemm(None if A is None else t(A), None if B is None else t(B), None if sv is None else t(sv),
+                       t(P), engine=engine).cpu().numpy()
+    comp = (np.abs(X).T @ np.abs(P)).T
+    if engine == 1:
+        K = na + nb
+        bound = 2.0 ** -45 * comp + 2.0 ** -52 * K * np.abs(P).max(axis=0)[:, None] * np.abs(X).max(axis=0)[None, :]
+    else:
+        bound = 2.0 ** -44 * comp
+    err = np.abs((got.astype(np.longdouble) - ref).astype(np.float64))
+    assert np.all(err <= bound), float(np.max(err / np.maximum(bound, 1e-300)))
+
+
+def test_row_gemm_tensor_engine_limits(ctx):
+    from paper_1501_03358_gb300.native import RKError
+    A = t(np.ones((65, 64)))
+    with pytest.raises(RKError):
+        ctx.row_gemm(A, None, None, t(np.ones((65, 4))), engine=1)
+    with pytest.raises(RKError):
+        ctx.row_gemm(t(np.ones((4, 64))), None, None, t(np.ones((4, 33))), engine=1)
+
+
 _KAPPA = {}
 
 
