@@ -4,14 +4,15 @@
 // A double-float product cannot run on BF16 tensor cores directly, but an
 // integer one can, exactly: each row r of X = [A, diag(bscale) Bm] is scaled
 // by a power of two 2^-E_r (|x| < 2^E_r over the row) and written as seven
-// signed 8-bit digits, x = 2^E_r sum_i s_i 256^-i (s_1 in [-256, 256], the
-// others in [-128, 128]); each column c of P likewise with 2^F_c and digits
-// t_j. BF16 holds such integers exactly, a digit product is an integer of at
-// most 2^16, and FP32 accumulation is exact while a sum stays below 2^24.
-// The products are grouped by level L = i + j:
+// signed digits, x = 2^E_r sum_i s_i 256^-i + (below 2^(E_r - 57)), with
+// |s_1|, |s_7| <= 256, |s_4| <= 192 and the others <= 128; each column c of
+// P likewise with 2^F_c and digits t_j (|t_1| <= 256, the others <= 128).
+// BF16 holds such integers exactly (at most 8 significant bits), a digit
+// product is an integer of at most 2^16, and FP32 accumulation is exact
+// while a sum stays below 2^24. The products are grouped by level L = i + j:
 //   X P = 2^(E_r + F_c) sum_L 256^-L (sum_{i+j=L} s_i t_j),
-// each level accumulated exactly in its own 32 TMEM columns (K <= 64 keeps
-// every level sum below 2^23.2). Levels 2..8 are kept (28 digit pairs); what
+// each level accumulated exactly in its own 32 TMEM columns (with K <= 64
+// every level sum stays below 2^23.6). Levels 2..8 are kept (28 digit pairs); what
 // is dropped lies below 2^-50 of |X||P|, and seven digits hold all 48 bits
 // of a double-float value within 2^8 of its row's largest. For digit row i,
 // one MMA with B = [t_1 | ... | t_(8-i)] (N = 32 (8 - i)) accumulates every
@@ -47,7 +48,6 @@ constexpr int kTcRows = 128;                    // rows per tile = MMA M = TMEM 
 constexpr int kTcProducers = 8;                 // producer warps (two per row: K halves)
 constexpr int kTcThreads = 32 * (kTcProducers + 1);  // + the issuer warp
 constexpr int kTcDigits = 7;                    // digits per operand
-constexpr float kTcBase = 256.f;                // digit base
 constexpr int kTcCols = 32;                     // output columns per level (MMA N per digit of P)
 constexpr int kTcTmem = 256;                    // 7 levels x 32 columns, rounded to a power of two
 constexpr int kTcKMax = 64;                     // K <= 64 keeps every level sum exact
@@ -97,13 +97,6 @@ __global__ void k_tc_digits_p(int np, int nc, int kp, const double* __restrict__
 // their FP32 encodings are zero) as a BF16 pair: the high halves, lo first.
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
-}
-
-// Round to the nearest integer, ties to even, for |y| < 2^22: adding and
-// subtracting 1.5 * 2^23 leaves no fraction bits (two FP32 adds).
-__device__ __forceinline__ float round_small(float y) {
-  const float m = 12582912.f;
-  return __fsub_rn(__fadd_rn(y, m), m);
 }
 
 // x * 2^ex for the epilogue: exponent arithmetic when x and the result are
@@ -253,34 +246,49 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dfgemm_tc(DFGemmArgs a, const
         const int b = cc & 1;
         if (cc >= 2) wait(&dfree[b], (unsigned)(((cc >> 1) - 1) & 1));  // the MMAs that read it last
         unsigned char* buf = dg + b * kTcABuf;
-        uint32_t pk[kTcDigits][4];
-#pragma unroll
-        for (int e = 0; e < 8; e += 2) {
-          float d0[kTcDigits], d1[kTcDigits];
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const int q = ks * 16 + half * 8 + e + u;
-            const float2 x = q < np ? X[q * kTcRows + rl] : make_float2(0.f, 0.f);
-            float yh = x.x * scale, yl = x.y * scale;  // exact (power of two)
-#pragma unroll
-            for (int i = 0; i < kTcDigits; ++i) {
-              yh *= kTcBase;
-              yl *= kTcBase;
-              const float sd = round_small(yh);
-              const float rh = yh - sd;  // exact: the fraction of yh
-              const float t = rh + yl;   // Fast2Sum: rh == 0 or |rh| >= 2 |yl|
-              yl = yl - (t - rh);
-              yh = t;
-              (u ? d1 : d0)[i] = sd;
-            }
-          }
-#pragma unroll
-          for (int i = 0; i < kTcDigits; ++i) pk[i][e >> 1] = pack_bf16(d0[i], d1[i]);
-        }
+        // The 8 elements of this thread's row and K half, digit by digit
+        // (ILP 8). Digit i is yh rounded to a multiple of 256^-i, taken as
+        // (yh + 1.5 2^(23-8i)) - 1.5 2^(23-8i) (the sum's ulp is 256^-i),
+        // subtracted exactly and scaled by 256^i. The low word joins the
+        // remainder after digit 3 (Fast2Sum: the remainder is a multiple of
+        // ulp(yh) >= 2 |yl| or zero) and its rounding error before digit 7.
         const int off = (((rl >> 3) * 2 + half) << 7) + ((rl & 7) << 4);
+        float yh[8], yl[8];
 #pragma unroll
-        for (int i = 0; i < kTcDigits; ++i)
-          *reinterpret_cast<uint4*>(buf + i * kTcPlane + off) = make_uint4(pk[i][0], pk[i][1], pk[i][2], pk[i][3]);
+        for (int e = 0; e < 8; ++e) {
+          const int q = ks * 16 + half * 8 + e;
+          const float2 x = q < np ? X[q * kTcRows + rl] : make_float2(0.f, 0.f);
+          yh[e] = __fmul_rn(x.x, scale);  // exact (power of two)
+          yl[e] = __fmul_rn(x.y, scale);
+        }
+        auto digit = [&](int i, bool keep_rest) {
+          const float sig = __int_as_float((127 + 23 - 8 * (i + 1)) << 23) * 1.5f;
+          const float up = __int_as_float((127 + 8 * (i + 1)) << 23);
+          float d[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const float sv = __fsub_rn(__fadd_rn(yh[e], sig), sig);
+            if (keep_rest) yh[e] = __fsub_rn(yh[e], sv);
+            d[e] = __fmul_rn(sv, up);
+          }
+          *reinterpret_cast<uint4*>(buf + i * kTcPlane + off) =
+              make_uint4(pack_bf16(d[0], d[1]), pack_bf16(d[2], d[3]), pack_bf16(d[4], d[5]), pack_bf16(d[6], d[7]));
+        };
+        digit(0, true);
+        digit(1, true);
+        digit(2, true);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const float t = __fadd_rn(yh[e], yl[e]);
+          yl[e] = __fsub_rn(yl[e], __fsub_rn(t, yh[e]));
+          yh[e] = t;
+        }
+        digit(3, true);
+        digit(4, true);
+        digit(5, true);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) yh[e] = __fadd_rn(yh[e], yl[e]);
+        digit(6, false);
         fence_async_shared();
         __syncwarp();
         if (lane == 0) mbar_arrive(&dfull[b]);
@@ -290,18 +298,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dfgemm_tc(DFGemmArgs a, const
       // epilogue: this warp's 32 lanes, output columns 16 half .. +15
       wait(&tfull, (unsigned)(it & 1));
       tc_fence_after_sync();
-      if (half * 16 < a.nc) {
-        const uint32_t tl = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + 16 * half;
-        float sh[16], sl[16];
+      // groups of 8 of this warp's 16 output columns that exist
+      for (int g = 0; g < 2 && 16 * half + 8 * g < a.nc; ++g) {
+        const int c0 = 16 * half + 8 * g;
+        const uint32_t tl = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + c0;
+        float sh[8], sl[8];
 #pragma unroll
-        for (int u = 0; u < 16; ++u) sh[u] = sl[u] = 0.f;
+        for (int u = 0; u < 8; ++u) sh[u] = sl[u] = 0.f;
 #pragma unroll
         for (int L = kTcDigits + 1; L >= 2; --L) {
-          float v[16];
-          tc_load16(tl + kTcCols * (L - 2), v);
+          float v[8];
+          tc_load8(tl + kTcCols * (L - 2), v);
           const float w = __int_as_float((127 - 8 * L) << 23);  // 256^-L
 #pragma unroll
-          for (int u = 0; u < 16; ++u) {
+          for (int u = 0; u < 8; ++u) {
             const float p = v[u] * w;  // exact
             const float s2 = sh[u] + p;
             const float bb = s2 - sh[u];
@@ -311,8 +321,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dfgemm_tc(DFGemmArgs a, const
         }
         if (valid) {
 #pragma unroll
-          for (int u = 0; u < 16; ++u) {
-            const int c = 16 * half + u;
+          for (int u = 0; u < 8; ++u) {
+            const int c = c0 + u;
             if (c < a.nc) {
               const float hi = sh[u] + sl[u];
               const float lo = sl[u] - (hi - sh[u]);

@@ -757,37 +757,61 @@ __device__ void hr_core(HRWork w, int n, int k, double* QC, int ldqc, double* PU
   // ---- 5. selection: eigenvalues mu of largest modulus (theta = 1/mu smallest).
   //         |mu|^2 and Re theta = Re mu / |mu|^2 once per eigenvalue (in
   //         parallel, into X as scratch), then a serial pick of the best
-  //         remaining entity by comparisons only; a complex pair is one entity
-  //         (its first member, wi > 0) and is taken only if both fit.
+  //         remaining entity; a complex pair is one entity (its first member,
+  //         wi > 0) and is taken only if both fit. The scan compares integer
+  //         images of the FP64 keys (a non-negative double orders like its
+  //         bit pattern; a signed one like the pattern with the magnitude bits
+  //         flipped when negative), which decide exactly as the FP64
+  //         comparisons do but run on the integer pipe; the tie bounds
+  //         |mu_best|^2 (1 +- 2e-12) are formed in FP64 when the best changes.
   double* mag2 = w.X;
-  double* reth = w.X + n;
+  long long* rkey = reinterpret_cast<long long*>(w.X + n);
   int* used = w.sel + n + 1;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double m2 = w.wr[i] * w.wr[i] + w.wi[i] * w.wi[i];
     mag2[i] = m2;
-    reth[i] = m2 > 0.0 ? w.wr[i] / m2 : 0.0;
+    const double rt = m2 > 0.0 ? w.wr[i] / m2 : 0.0;
+    const long long bits = __double_as_longlong(rt == 0.0 ? 0.0 : rt);
+    rkey[i] = bits < 0 ? (bits ^ 0x7fffffffffffffffLL) : bits;
     used[i] = (w.wi[i] < 0.0 || !(m2 > 0.0)) ? 1 : 0;
   }
+  // the scan's operands in shared memory (n <= kSelMax; else from X)
+  constexpr int kSelMax = 256;
+  __shared__ long long sel_m[kSelMax], sel_r[kSelMax];
+  __shared__ int sel_u[kSelMax];
+  const bool sel_sm = n <= kSelMax;
+  __syncthreads();
+  if (sel_sm)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      sel_m[i] = __double_as_longlong(mag2[i]);
+      sel_r[i] = rkey[i];
+      sel_u[i] = used[i];
+    }
   __syncthreads();
   if (threadIdx.x == 0) {
     int taken = 0, ns = 0;
     const double tie_hi = 1.0 + 2e-12, tie_lo = 1.0 - 2e-12;
+    long long* km = sel_sm ? sel_m : nullptr;
+    long long* kr = sel_sm ? sel_r : rkey;
+    int* ku = sel_sm ? sel_u : used;
     while (taken < k) {
       int best = -1;
-      double bm = -1.0, br = 0.0;
+      long long bhi = 0, blo = 0, brk = 0;
       for (int i = 0; i < n; ++i) {
-        if (used[i]) continue;
-        const double m2 = mag2[i], rt = reth[i];
-        if (best < 0 || m2 > bm * tie_hi || (m2 >= bm * tie_lo && rt < br)) {
+        if (ku[i]) continue;
+        const long long m = km ? km[i] : __double_as_longlong(mag2[i]);  // mag2 > 0 here
+        const long long rk = kr[i];
+        if (best < 0 || m > bhi || (m >= blo && rk < brk)) {
           best = i;
-          bm = m2;
-          br = rt;
+          bhi = __double_as_longlong(mag2[i] * tie_hi);
+          blo = __double_as_longlong(mag2[i] * tie_lo);
+          brk = rk;
         }
       }
       if (best < 0) break;
       const int need = w.wi[best] > 0.0 ? 2 : 1;
       if (taken + need > k) break;
-      used[best] = 1;
+      ku[best] = 1;
       w.sel[ns++] = best;
       taken += need;
     }
@@ -909,22 +933,31 @@ __device__ void hr_core(HRWork w, int n, int k, double* QC, int ldqc, double* PU
     Y[t] = s;
   }
   __syncthreads();
+  // classical Gram-Schmidt, two passes: per pass all inner products with
+  // the kept columns at once (a warp per inner product), then one update
+  double* sh_d = w.v;  // the inner products (kept <= n of them; v is free here)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   int kept = 0;
   for (int c = 0; c < knew; ++c) {
     double* yc = Y + (int64_t)c * n;
     double s0 = 0.0;
     for (int r = threadIdx.x; r < n; r += blockDim.x) s0 = fma(yc[r], yc[r], s0);
     const double n0 = sqrt(block_sum(s0, red));
-    for (int pass = 0; pass < 2; ++pass) {
-      for (int c2 = 0; c2 < kept; ++c2) {
+    for (int pass = 0; pass < 2 && kept > 0; ++pass) {
+      for (int c2 = warp; c2 < kept; c2 += nwarp) {
         const double* qc = w.X + (int64_t)c2 * n;
         double d = 0.0;
-        for (int r = threadIdx.x; r < n; r += blockDim.x) d = fma(qc[r], yc[r], d);
-        d = block_sum(d, red);
-        __syncthreads();
-        for (int r = threadIdx.x; r < n; r += blockDim.x) yc[r] = fma(-d, qc[r], yc[r]);
-        __syncthreads();
+        for (int r = lane; r < n; r += 32) d = fma(qc[r], yc[r], d);
+        d = warp_sum(d);
+        if (lane == 0) sh_d[c2] = d;
       }
+      __syncthreads();
+      for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        double t = yc[r];
+        for (int c2 = 0; c2 < kept; ++c2) t = fma(-sh_d[c2], w.X[r + (int64_t)c2 * n], t);
+        yc[r] = t;
+      }
+      __syncthreads();
     }
     double s1 = 0.0;
     for (int r = threadIdx.x; r < n; r += blockDim.x) s1 = fma(yc[r], yc[r], s1);
@@ -943,27 +976,48 @@ __device__ void hr_core(HRWork w, int n, int k, double* QC, int ldqc, double* PU
     QC[r + (int64_t)c * ldqc] = r < n ? w.X[r + (int64_t)c * n] : 0.0;
   }
   __syncthreads();
-  for (int c = n - 1; c >= 0; --c) {
-    const int len = n + 1 - c;
-    const double tau = w.tau[c];
-    for (int j = threadIdx.x; j < kept; j += blockDim.x) {
-      double* col = QC + (int64_t)j * ldqc + c;
+  // Q_G applied to each column by a warp (lanes over rows): the columns are
+  // independent, so no block barrier between reflectors
+  // (two columns per warp at a time, so the two dependent chains overlap)
+  for (int j0 = 2 * warp; j0 < kept; j0 += 2 * nwarp) {
+    const bool two = j0 + 1 < kept;
+    double* colA = QC + (int64_t)j0 * ldqc;
+    double* colB = QC + (int64_t)(two ? j0 + 1 : j0) * ldqc;
+    for (int c = n - 1; c >= 0; --c) {
+      const int len = n + 1 - c;
       const double* vv = w.G + (int64_t)c * ldg + c;  // vv[0] holds R_G(c,c); the reflector has v[0] = 1
-      double s = col[0];
-      for (int i = 1; i < len; ++i) s = fma(vv[i], col[i], s);
-      s *= tau;
-      col[0] -= s;
-      for (int i = 1; i < len; ++i) col[i] = fma(-s, vv[i], col[i]);
+      double sa = 0.0, sb = 0.0;
+      for (int i = lane; i < len; i += 32) {
+        const double vi = i == 0 ? 1.0 : vv[i];
+        sa = fma(vi, colA[c + i], sa);
+        sb = fma(vi, colB[c + i], sb);
+      }
+      const double tc = w.tau[c];
+      sa = warp_sum(sa) * tc;
+      sb = warp_sum(sb) * tc;
+      for (int i = lane; i < len; i += 32) {
+        const double vi = i == 0 ? 1.0 : vv[i];
+        colA[c + i] = fma(-sa, vi, colA[c + i]);
+        if (two) colB[c + i] = fma(-sb, vi, colB[c + i]);
+      }
+      __syncwarp();
     }
-    __syncthreads();
   }
-  for (int j = threadIdx.x; j < kept; j += blockDim.x) {
-    const double* q2 = w.X + (int64_t)j * n;
+  // PU = R_G^{-1} Q2 by column-oriented back substitution, a warp per
+  // column: pu_r = t_r / R_rr, then t_i -= R_ir pu_r for i < r (lanes)
+  double* rdiag = w.v;  // 1 / R_G(r, r)
+  for (int r = threadIdx.x; r < n; r += blockDim.x) rdiag[r] = 1.0 / w.G[r + (int64_t)r * ldg];
+  __syncthreads();
+  for (int j = warp; j < kept; j += nwarp) {
     double* pu = PU + (int64_t)j * ldpu;
+    for (int r = lane; r < n; r += 32) pu[r] = w.X[r + (int64_t)j * n];
+    __syncwarp();
     for (int r = n - 1; r >= 0; --r) {
-      double t = q2[r];
-      for (int c = r + 1; c < n; ++c) t = fma(-w.G[r + (int64_t)c * ldg], pu[c], t);
-      pu[r] = t / w.G[r + (int64_t)r * ldg];
+      const double pr = pu[r] * rdiag[r];
+      __syncwarp();
+      if (lane == 0) pu[r] = pr;
+      for (int i = lane; i < r; i += 32) pu[i] = fma(-w.G[i + (int64_t)r * ldg], pr, pu[i]);
+      __syncwarp();
     }
   }
   __syncthreads();
