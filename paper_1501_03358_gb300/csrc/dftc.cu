@@ -21,19 +21,20 @@
 // double-float (every term exact) and applies 2^(E_r + F_c).
 //
 // One block per SM, a persistent loop over tiles of 128 rows (one TMEM lane
-// per row). Eight producer warps: warp w owns rows 32 (w % 4) .. +31 (its
-// TMEM lanes) and half w / 4 of K. One issuer warp: it brings each tile of X
-// (and the row scales) into shared memory by bulk asynchronous copies one
-// tile ahead, and issues the MMAs. Per tile a producer finds its half-row
+// per row). A loader warp brings each tile of X (and the row scales) into
+// shared memory by bulk asynchronous copies, two tiles ahead (three tile
+// buffers). Eight producer warps: warp w owns rows 32 (w % 4) .. +31 (its
+// TMEM lanes) and half w / 4 of K. Per tile a producer finds its half-row
 // maximum, trades it with the warp owning the other half (a 64-thread named
 // barrier), writes per 16 columns of K its 8 x 7 digits into one of two
-// digit buffers (canonical K-major layout) and arrives on the buffer's
-// "full" barrier; the issuer waits for all eight warps, issues the 7 MMAs
-// and commits them to the buffer's "free" barrier. After the tile's last
-// MMAs a commit on "tmem full" releases the epilogue, in which each producer
-// reads its lanes' level sums for its 16 output columns; "tmem free" lets
-// the issuer start the next tile. No block-wide barrier inside the loop. The
-// digits of P are made once per launch by k_tc_digits_p.
+// digit buffers in TMEM (the MMAs' A operand) and arrives on the buffer's
+// "full" barrier; the MMA issuer warp waits for all eight, issues the 7 MMAs
+// (B, the digits of P, in shared memory) and commits them to the buffer's
+// "free" barrier. After the tile's last MMAs a commit on "tmem full"
+// releases the epilogue, in which each producer reads its lanes' level sums
+// for its output columns; "tmem free" lets the issuer start the next tile.
+// No block-wide barrier inside the loop. The digits of P are made once per
+// launch by k_tc_digits_p.
 #include <cuda_bf16.h>
 
 #include "rk_internal.h"
@@ -46,17 +47,18 @@ namespace {
 
 constexpr int kTcRows = 128;                    // rows per tile = MMA M = TMEM lanes
 constexpr int kTcProducers = 8;                 // producer warps (two per row: K halves)
-constexpr int kTcThreads = 32 * (kTcProducers + 1);  // + the issuer warp
+constexpr int kTcThreads = 32 * (kTcProducers + 2);  // + the MMA issuer and the loader warps
 constexpr int kTcDigits = 7;                    // digits per operand
 constexpr int kTcCols = 32;                     // output columns per level (MMA N per digit of P)
-constexpr int kTcTmem = 256;                    // 7 levels x 32 columns, rounded to a power of two
+constexpr int kTcTmem = 512;                    // 7 levels x 32 accumulator columns, then the A digits
+constexpr int kTcADig = 256;                    // TMEM column of the first A digit buffer
 constexpr int kTcKMax = 64;                     // K <= 64 keeps every level sum exact
-constexpr int kTcPlane = kTcRows * 16 * 2;      // one digit plane of a 16-wide K step (bytes)
-constexpr int kTcABuf = kTcDigits * kTcPlane;   // 28 KB per digit buffer
+constexpr int kTcADigCols = 64;                 // TMEM columns per A digit buffer (7 planes x 8 used)
+constexpr int kTcXStages = 3;                   // X tiles in shared memory (two prefetched ahead)
 constexpr int kTcBRows = kTcDigits * kTcCols;   // 224 rows of B: (digit j, column c)
 constexpr int kTcBBytes = kTcBRows * kTcKMax * 2;             // 28 KB
 constexpr int kTcXBuf = kTcRows * kTcKMax * (int)sizeof(float2);  // 64 KB per X tile
-constexpr size_t kTcSmem = 2 * (size_t)kTcXBuf + 2 * (size_t)kTcABuf + kTcBBytes + 2 * kTcRows * sizeof(double);
+constexpr size_t kTcSmem = kTcXStages * (size_t)kTcXBuf + kTcBBytes + kTcXStages * kTcRows * sizeof(double);
 
 // element offset of (row, k) in a K-major canonical operand with kg 8-wide
 // core-matrix columns along K
@@ -112,11 +114,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dfgemm_tc(DFGemmArgs a, const
                                                                 const int* __restrict__ fexp, int kp, int bulk_ok,
                                                                 int* err) {
   extern __shared__ __align__(1024) unsigned char tsm[];
-  float2* xs = reinterpret_cast<float2*>(tsm);               // [2][kTcKMax][kTcRows] X tiles
-  unsigned char* dg = tsm + 2 * kTcXBuf;                      // [2] digit buffers
-  unsigned char* sB = dg + 2 * kTcABuf;                       // digits of P
-  double* bsv = reinterpret_cast<double*>(sB + kTcBBytes);    // [2][kTcRows] row scales
-  __shared__ __align__(8) uint64_t xfull[2], xfree[2], dfull[2], dfree[2], tfull, tfree;
+  float2* xs = reinterpret_cast<float2*>(tsm);                     // [kTcXStages][kTcKMax][kTcRows] X tiles
+  unsigned char* sB = tsm + kTcXStages * kTcXBuf;                   // digits of P
+  double* bsv = reinterpret_cast<double*>(sB + kTcBBytes);          // [kTcXStages][kTcRows] row scales
+  __shared__ __align__(8) uint64_t xfull[kTcXStages], xfree[kTcXStages], dfull[2], dfree[2], tfull, tfree;
   __shared__ uint32_t tslot;
   __shared__ int fs[kTcCols];
   __shared__ float rmax[2][2][kTcRows];  // [tile parity][K half][row]
@@ -132,9 +133,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dfgemm_tc(DFGemmArgs a, const
   if (tid < kTcCols) fs[tid] = fexp[tid];
   if (warp == 0) tc_alloc(&tslot, kTcTmem);
   if (tid == 0) {
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kTcXStages; ++b) {
       mbar_init(&xfull[b], 1);
       mbar_init(&xfree[b], kTcProducers);
+    }
+    for (int b = 0; b < 2; ++b) {
       mbar_init(&dfull[b], kTcProducers);
       mbar_init(&dfree[b], 1);
     }
@@ -153,8 +156,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dfgemm_tc(DFGemmArgs a, const
   auto is_bulk = [&](int64_t t) { return bulk_ok != 0 && (t + 1) * kTcRows <= a.n; };
   bool ok = true;
   auto wait = [&](uint64_t* bar, unsigned parity) { ok = mbar_wait_bounded(bar, parity) && ok; };
-  if (warp == kTcProducers) {
-    // ---------------------------------------------------------------- issuer
+  if (warp == kTcProducers + 1) {
+    // ---------------------------------------------------------------- loader
     if (lane == 0) {
       auto issue = [&](int64_t t, int b) {
         const int64_t r0 = t * kTcRows;
@@ -167,16 +170,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dfgemm_tc(DFGemmArgs a, const
         }
         if (a.bscale) bulk_g2s(bsv + b * kTcRows, a.bscale + r0, kTcRows * (unsigned)sizeof(double), &xfull[b]);
       };
-      const uint32_t bdesc0 = smem_u32(sB), dg_u = smem_u32(dg);
+      // the first two tiles, then one tile per producer tile finished: tile
+      // it + 2 goes into the buffer tile it - 1 has released
+      for (int p = 0; p < 2; ++p) {
+        const int64_t t = blockIdx.x + (int64_t)p * gridDim.x;
+        if (t < ntiles && is_bulk(t)) issue(t, p);
+      }
+      int it = 0;
+      for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int64_t nx = tile + 2 * (int64_t)gridDim.x;
+        if (nx < ntiles && is_bulk(nx)) {
+          const int nb = (it + 2) % kTcXStages;
+          if (it >= 1) wait(&xfree[nb], (unsigned)(((it - 1) / kTcXStages) & 1));
+          issue(nx, nb);
+        }
+      }
+    }
+  } else if (warp == kTcProducers) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t bdesc0 = smem_u32(sB);
       int cc = 0, it = 0;
       for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-        const int xb = it & 1;
-        if (it == 0 && is_bulk(tile)) issue(tile, 0);
-        const int64_t nx = tile + gridDim.x;
-        if (nx < ntiles && is_bulk(nx)) {
-          if (it >= 1) wait(&xfree[xb ^ 1], (unsigned)(((it - 1) >> 1) & 1));  // tile it-1 read that buffer
-          issue(nx, xb ^ 1);
-        }
         if (it >= 1) wait(&tfree, (unsigned)((it - 1) & 1));  // the previous epilogue has read TMEM
         for (int ks = 0; ks < nks; ++ks, ++cc) {
           const int b = cc & 1;
@@ -184,10 +199,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dfgemm_tc(DFGemmArgs a, const
           tc_fence_after_sync();
 #pragma unroll
           for (int i = 0; i < kTcDigits; ++i) {
-            const uint64_t ad = tc_smem_desc(dg_u + b * kTcABuf + i * kTcPlane, 128, 256);
             const uint64_t bd = tc_smem_desc(bdesc0 + ks * 256, 128, kg * 128);
-            tc_mma_bf16(taddr + kTcCols * i, ad, bd, tc_idesc_bf16(kTcRows, kTcCols * (kTcDigits - i)),
-                        (ks > 0 || i > 0) ? 1u : 0u);
+            tc_mma_bf16_ta(taddr + kTcCols * i, taddr + kTcADig + b * kTcADigCols + 8 * i, bd,
+                           tc_idesc_bf16(kTcRows, kTcCols * (kTcDigits - i)), (ks > 0 || i > 0) ? 1u : 0u);
           }
           tc_commit(&dfree[b]);
         }
@@ -201,14 +215,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dfgemm_tc(DFGemmArgs a, const
     const int pairbar = 1 + (warp & 3);     // named barrier of warps w and w + 4
     int cc = 0, it = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-      const int xb = it & 1;
+      const int xb = it % kTcXStages;
       const int64_t r0 = tile * kTcRows;
       const int64_t row = r0 + rl;
       const bool valid = row < a.n;
       float2* X = xs + (int64_t)xb * kTcKMax * kTcRows;
       double* bs = bsv + xb * kTcRows;
       if (is_bulk(tile)) {
-        wait(&xfull[xb], (unsigned)((it >> 1) & 1));
+        wait(&xfull[xb], (unsigned)((it / kTcXStages) & 1));
       } else {
         // this thread's own elements (its row, its K half) and row scale
         for (int ks = 0; ks < nks; ++ks)
@@ -223,41 +237,44 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dfgemm_tc(DFGemmArgs a, const
         if (a.bscale) bs[rl] = valid ? __ldg(&a.bscale[row]) : 0.0;
       }
       const float2 sc = a.bscale ? df_from_double_i(bs[rl]) : make_float2(1.f, 0.f);
-      // the B part scaled by the row scale once, in place; half-row maximum
-      float mx = 0.f;
+      // half-row maximum of the high words; for the B part max |b| |s| with
+      // 2^-20 of headroom, which bounds the double-float products taken
+      // with the digits (their high words differ from b_hi s_hi by < 2^-22)
+      float mxa = 0.f, mxb = 0.f;
       for (int ks = 0; ks < nks; ++ks)
         for (int e = 0; e < 8; ++e) {
           const int q = ks * 16 + half * 8 + e;
           if (q >= np) break;
-          float2 x = X[q * kTcRows + rl];
-          if (q >= a.na) {
-            x = df_mul(x, sc);
-            X[q * kTcRows + rl] = x;
-          }
-          mx = fmaxf(mx, fabsf(x.x));
+          const float xh = fabsf(X[q * kTcRows + rl].x);
+          if (q < a.na)
+            mxa = fmaxf(mxa, xh);
+          else
+            mxb = fmaxf(mxb, xh);
         }
-      rmax[xb][half][rl] = mx;
+      float mx = fmaxf(mxa, mxb * fabsf(sc.x) * 1.00000095367431640625f);
+      rmax[it & 1][half][rl] = mx;
       named_barrier_sync(pairbar, 64);
-      mx = fmaxf(rmax[xb][0][rl], rmax[xb][1][rl]);
+      mx = fmaxf(rmax[it & 1][0][rl], rmax[it & 1][1][rl]);
       int E = mx > 0.f ? ilogbf(mx) + 1 : 0;
       E = E < -125 ? -125 : (E > 126 ? 126 : E);  // keep 2^-E a normal FP32 number
       const float scale = __int_as_float((127 - E) << 23);
       for (int ks = 0; ks < nks; ++ks, ++cc) {
         const int b = cc & 1;
         if (cc >= 2) wait(&dfree[b], (unsigned)(((cc >> 1) - 1) & 1));  // the MMAs that read it last
-        unsigned char* buf = dg + b * kTcABuf;
+        // this warp's lanes, this K half's 4 columns of each digit plane
+        const uint32_t ta = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + kTcADig + b * kTcADigCols + 4 * half;
         // The 8 elements of this thread's row and K half, digit by digit
         // (ILP 8). Digit i is yh rounded to a multiple of 256^-i, taken as
         // (yh + 1.5 2^(23-8i)) - 1.5 2^(23-8i) (the sum's ulp is 256^-i),
         // subtracted exactly and scaled by 256^i. The low word joins the
         // remainder after digit 3 (Fast2Sum: the remainder is a multiple of
         // ulp(yh) >= 2 |yl| or zero) and its rounding error before digit 7.
-        const int off = (((rl >> 3) * 2 + half) << 7) + ((rl & 7) << 4);
         float yh[8], yl[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
           const int q = ks * 16 + half * 8 + e;
-          const float2 x = q < np ? X[q * kTcRows + rl] : make_float2(0.f, 0.f);
+          float2 x = q < np ? X[q * kTcRows + rl] : make_float2(0.f, 0.f);
+          if (q >= a.na && q < np) x = df_mul(x, sc);
           yh[e] = __fmul_rn(x.x, scale);  // exact (power of two)
           yl[e] = __fmul_rn(x.y, scale);
         }
@@ -271,8 +288,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dfgemm_tc(DFGemmArgs a, const
             if (keep_rest) yh[e] = __fsub_rn(yh[e], sv);
             d[e] = __fmul_rn(sv, up);
           }
-          *reinterpret_cast<uint4*>(buf + i * kTcPlane + off) =
-              make_uint4(pack_bf16(d[0], d[1]), pack_bf16(d[2], d[3]), pack_bf16(d[4], d[5]), pack_bf16(d[6], d[7]));
+          tc_store4(ta + 8 * i, pack_bf16(d[0], d[1]), pack_bf16(d[2], d[3]), pack_bf16(d[4], d[5]),
+                    pack_bf16(d[6], d[7]));
         };
         digit(0, true);
         digit(1, true);
@@ -289,7 +306,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dfgemm_tc(DFGemmArgs a, const
 #pragma unroll
         for (int e = 0; e < 8; ++e) yh[e] = __fadd_rn(yh[e], yl[e]);
         digit(6, false);
-        fence_async_shared();
+        tc_wait_store();
+        tc_fence_before_sync();
         __syncwarp();
         if (lane == 0) mbar_arrive(&dfull[b]);
       }
@@ -305,14 +323,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dfgemm_tc(DFGemmArgs a, const
         float sh[8], sl[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) sh[u] = sl[u] = 0.f;
+        uint32_t lv[kTcDigits][8];
+#pragma unroll
+        for (int L = 2; L <= kTcDigits + 1; ++L) tc_load8_async(tl + kTcCols * (L - 2), lv[L - 2]);
+        tc_wait_load();
 #pragma unroll
         for (int L = kTcDigits + 1; L >= 2; --L) {
-          float v[8];
-          tc_load8(tl + kTcCols * (L - 2), v);
           const float w = __int_as_float((127 - 8 * L) << 23);  // 256^-L
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
-            const float p = v[u] * w;  // exact
+            const float p = __uint_as_float(lv[L - 2][u]) * w;  // exact
             const float s2 = sh[u] + p;
             const float bb = s2 - sh[u];
             sl[u] += (sh[u] - (s2 - bb)) + (p - bb);
