@@ -85,7 +85,15 @@ typedef struct {
                             1/a_pp rounded to ~48 bits once, double-float accumulation in band
                             order), everything else as in RK_FP64 */
   int32_t update_recycle;/* rGCROT: 1 = update U, C after every cycle (Algorithm 3), 0 = keep */
-  int32_t reserved;
+  int32_t hybrid_refresh;  /* RK_HYBRID, Sec. 2.4 "intermittent solves with rGCROT": after the
+                              switch, every hybrid_refresh-th solve runs rGCROT (updating U, C);
+                              0 = never */
+  int32_t hybrid_fallback; /* RK_HYBRID, Sec. 2.4 "switch back to rGCROT": an rBiCGStab solve that
+                              breaks down or has used hybrid_fallback matrix-vector products
+                              without converging is finished by rGCROT from its current iterate
+                              (within max_matvec in total), and the hybrid starts a new rGCROT
+                              phase: that solve and the next hybrid_switch - 1 use rGCROT;
+                              0 = off */
 } rk_solve_params;
 
 typedef struct {

@@ -489,18 +489,47 @@ class RecyclingSequence:
     """Solves a sequence A x_t = b_t carrying the recycle space (U, C) across
     steps (Sec. 1, Sec. 2.3). mode: 'GMRES', 'rGCROT', 'BiCGStab',
     'rBiCGStab' or 'hybrid' (rGCROT with recycle update for the first
-    ``hybrid_switch`` steps, then rBiCGStab with U, C frozen; Sec. 2.4)."""
+    ``hybrid_switch`` steps, then rBiCGStab with U, C frozen; Sec. 2.4).
 
-    def __init__(self, op, mode="rGCROT", m=30, k=10, tol=1e-8, hybrid_switch=5, max_matvec=2000):
+    The two variants Sec. 2.4 mentions, in this reading: ``refresh`` = R > 0
+    runs every R-th solve after the switch with rGCROT ("intermittent solves
+    with rGCROT to update the recycle space"); ``fallback`` = F > 0 stops an
+    rBiCGStab solve that breaks down or has used F matrix-vector products
+    without converging, finishes it with rGCROT from its current iterate
+    (within ``max_matvec`` in total) and starts a new rGCROT phase with that
+    solve ("if convergence is poor ... switch back to rGCROT")."""
+
+    def __init__(self, op, mode="rGCROT", m=30, k=10, tol=1e-8, hybrid_switch=5, max_matvec=2000, refresh=0,
+                 fallback=0):
         self.op, self.mode, self.m, self.k, self.tol = op, mode, m, k, tol
         self.hybrid_switch, self.max_matvec = hybrid_switch, max_matvec
+        self.refresh, self.fallback = refresh, fallback
         self.U = self.C = None
         self.t = 0
+        self.base = 0  # first solve of the current rGCROT phase (hybrid)
 
     def solve(self, b, x0=None):
         mode = self.mode
         if mode == "hybrid":
-            mode = "rGCROT" if self.t < self.hybrid_switch else "rBiCGStab"
+            t = self.t - self.base
+            refresh = self.refresh > 0 and t >= self.hybrid_switch and \
+                (t - self.hybrid_switch + 1) % self.refresh == 0
+            mode = "rGCROT" if (t < self.hybrid_switch or refresh) else "rBiCGStab"
+            if mode == "rBiCGStab" and self.fallback > 0:
+                cap = min(self.fallback, self.max_matvec)
+                x, info = rbicgstab(self.op, b, x0, self.tol, self.U, self.C, cap)
+                if info["status"] != OK and info["matvecs"] < self.max_matvec:
+                    used = info["matvecs"]
+                    x, self.U, self.C, ig = rgcrot(self.op, b, x, self.tol, self.m, self.k, self.U, self.C,
+                                                   update=True, max_matvec=self.max_matvec - used)
+                    ig["matvecs"] += used
+                    ig["restarts"] += info["restarts"]
+                    info = ig
+                    mode = "rGCROT"
+                    self.base = self.t
+                info["mode"] = mode
+                self.t += 1
+                return x, info
         if mode == "GMRES":
             x, info = gmres(self.op, b, x0, self.tol, self.m, self.max_matvec)
         elif mode == "rGCROT":

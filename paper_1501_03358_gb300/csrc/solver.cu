@@ -210,6 +210,7 @@ struct rk_problem {
   unsigned* counter = nullptr;
   int* istat = nullptr;           // device ints for small kernels
   int solves = 0;
+  int hyb_base = 0;  // first solve of the current rGCROT phase of RK_HYBRID
 
   float2* Vcol(int j) const { return QB + (int64_t)(kmax + j) * ld; }
   float2* Cblk(int kc) const { return QB + (int64_t)(kmax - kc) * ld; }
@@ -1231,15 +1232,45 @@ int rk_solve(rk_problem* p, const double* b, double* x, const rk_solve_params* p
   rk_solve_info& inf = info ? *info : loc;
   std::memset(&inf, 0, sizeof(inf));
   cudaStream_t st = (cudaStream_t)stream;
+  if (prm.hybrid_refresh < 0 || prm.hybrid_fallback < 0) return fail(RK_E_INVALID, "negative hybrid parameter");
   int mode = prm.mode;
-  if (mode == RK_HYBRID) mode = p->solves < prm.hybrid_switch ? RK_RGCROT : RK_RBICGSTAB;
+  const bool hybrid = mode == RK_HYBRID;
+  if (hybrid) {
+    // Sec. 2.4: rGCROT for the first hybrid_switch solves of a phase, then
+    // rBiCGStab with U, C frozen; every hybrid_refresh-th solve after the
+    // switch runs rGCROT to update the space
+    const int t = p->solves - p->hyb_base;
+    const bool refresh = prm.hybrid_refresh > 0 && t >= prm.hybrid_switch &&
+                         (t - prm.hybrid_switch + 1) % prm.hybrid_refresh == 0;
+    mode = (t < prm.hybrid_switch || refresh) ? RK_RGCROT : RK_RBICGSTAB;
+  }
   inf.mode_used = mode;
   int rc;
   if (mode == RK_GMRES || mode == RK_RGCROT) {
     if (prm.m <= 0) return fail(RK_E_INVALID, "m must be positive");
     rc = solve_gcr(p, b, x, prm, inf, mode == RK_RGCROT, mode == RK_RGCROT && prm.update_recycle != 0, st);
   } else if (mode == RK_RBICGSTAB) {
-    rc = solve_bicg(p, b, x, prm, inf, prm.k > 0, st);
+    const int maxmv = prm.max_matvec > 0 ? prm.max_matvec : 2000;
+    const bool fallback = hybrid && prm.hybrid_fallback > 0;
+    rk_solve_params pb = prm;
+    if (fallback && prm.hybrid_fallback < maxmv) pb.max_matvec = prm.hybrid_fallback;
+    rc = solve_bicg(p, b, x, pb, inf, prm.k > 0, st);
+    if (fallback && (rc == RK_E_NOT_CONVERGED || rc == RK_E_BREAKDOWN) && inf.matvecs < maxmv) {
+      // Sec. 2.4 "switch back to rGCROT": finish from the current iterate
+      // and start a new rGCROT phase with this solve
+      if (prm.m <= 0) return fail(RK_E_INVALID, "m must be positive");
+      rk_solve_info ig{};
+      rk_solve_params pg = prm;
+      pg.max_matvec = maxmv - inf.matvecs;
+      const int rg = solve_gcr(p, b, x, pg, ig, true, prm.update_recycle != 0, st);
+      ig.matvecs += inf.matvecs;
+      ig.restarts += inf.restarts;
+      ig.model_bytes += inf.model_bytes;
+      ig.mode_used = RK_RGCROT;
+      inf = ig;
+      rc = rg;
+      p->hyb_base = p->solves;
+    }
   } else {
     return fail(RK_E_INVALID, "unknown mode");
   }

@@ -202,10 +202,12 @@ class Problem:
         return U[: kk.value], C[: kk.value]
 
     def solve(self, b, x0=None, tol=1e-8, m=40, k=20, mode="rGCROT", max_matvec=2000, hybrid_switch=5,
-              update_recycle=True, out=None, stream=None, check_status=False, precision="fp64"):
+              update_recycle=True, out=None, stream=None, check_status=False, precision="fp64", hybrid_refresh=0,
+              hybrid_fallback=0):
         """Solve A x = b; returns (x, info dict). x0 defaults to 0."""
         b, out = self._bx(b, x0, out)
-        prm = _params(tol, m, k, mode, max_matvec, hybrid_switch, update_recycle, precision)
+        prm = _params(tol, m, k, mode, max_matvec, hybrid_switch, update_recycle, precision, hybrid_refresh,
+                      hybrid_fallback)
         info = N.rk_solve_info()
         rc = self.lib.rk_solve(self._h, _dptr(b), _dptr(out), ctypes.byref(prm), ctypes.byref(info),
                                _stream_ptr(stream))
@@ -259,10 +261,11 @@ class Problem:
             pass
 
 
-def _params(tol, m, k, mode, max_matvec, hybrid_switch, update_recycle, precision):
+def _params(tol, m, k, mode, max_matvec, hybrid_switch, update_recycle, precision, hybrid_refresh=0,
+            hybrid_fallback=0):
     prec = {"fp64": N.RK_FP64, "mixed": N.RK_MIXED, "df": N.RK_DF}[precision]
     prm = N.rk_solve_params(float(tol), int(m), int(k), int(max_matvec), int(hybrid_switch), N.MODES[mode],
-                            prec, 1 if update_recycle else 0, 0)
+                            prec, 1 if update_recycle else 0, int(hybrid_refresh), int(hybrid_fallback))
     if mode == "BiCGStab":
         prm.k = 0
     return prm
@@ -286,12 +289,12 @@ def solve_batch(problems, bs, outs=None, params=None, nthreads=0, stream=None, c
         xl.append(x)
     plist = params if params is not None else [kw] * n
     defaults = dict(tol=1e-8, m=40, k=20, mode="rGCROT", max_matvec=2000, hybrid_switch=5, update_recycle=True,
-                    precision="fp64")
+                    precision="fp64", hybrid_refresh=0, hybrid_fallback=0)
     prm = (N.rk_solve_params * n)()
     for i in range(n):
         d = dict(defaults, **plist[i])
         prm[i] = _params(d["tol"], d["m"], d["k"], d["mode"], d["max_matvec"], d["hybrid_switch"],
-                         d["update_recycle"], d["precision"])
+                         d["update_recycle"], d["precision"], d["hybrid_refresh"], d["hybrid_fallback"])
     infos = (N.rk_solve_info * n)()
     H = (ctypes.c_void_p * n)(*[p._h.value for p in problems])
     B = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bl])

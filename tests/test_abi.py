@@ -43,8 +43,33 @@ def test_version_and_error_without_gpu(lib):
     assert isinstance(lib.rk_last_error(), bytes)
 
 
-def test_struct_layouts_match_header():
+def test_struct_layouts_match_header(tmp_path):
+    """The binding's structures have the size and field offsets that a C
+    compiler gives the header's (gcc on the host, which uses the same
+    layout rules as the device compiler's host side)."""
+    import shutil
+    import subprocess
     from paper_1501_03358_gb300 import native
-    assert ctypes.sizeof(native.rk_grid) == 16
-    assert ctypes.sizeof(native.rk_solve_params) == 8 + 8 * 4
-    assert ctypes.sizeof(native.rk_solve_info) == 6 * 4 + 3 * 8
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"rk_grid": native.rk_grid, "rk_solve_params": native.rk_solve_params,
+               "rk_solve_info": native.rk_solve_info}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "rk.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        name, field, val = line.split()
+        got[(name, field)] = int(val)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)

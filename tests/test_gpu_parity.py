@@ -369,6 +369,43 @@ def test_hybrid_sequence_porous(ctx):
         assert abs(info["matvecs"] - io["matvecs"]) <= slack, (s, info["matvecs"], io["matvecs"])
 
 
+@pytest.mark.parametrize("refresh,fallback", [(2, 0), (0, 6), (3, 6)])
+def test_hybrid_variants_match_oracle(ctx, refresh, fallback):
+    """The hybrid variants of Sec. 2.4 on the small porous problem: rGCROT
+    refresh solves every `refresh` solves after the switch, and the switch
+    back to rGCROT when rBiCGStab has not converged after `fallback`
+    products. Per solve: the same mode as the oracle's schedule (a fallback
+    solve reports rGCROT), convergence on the true residual, x within the
+    kappa bound of the oracle's, products within 25% (a fallback solve's
+    rGCROT part starts from an rBiCGStab iterate, which moves the count)."""
+    n = (14, 12, 10)
+    solid, _ = sphere_pack(n, 2.5, 0.3, rng_for(77, 3), max_attempts=20000)
+    grid, coef = porous_skew_19pt(n, np.where(solid, 1e-4, 1.0), 15.0)
+    prob = gpu_problem(ctx, grid, coef)
+    op = oracle.Stencil(grid, coef)
+    kap = kappa(grid, coef)
+    seq = oracle.RecyclingSequence(op, mode="hybrid", m=20, k=10, tol=1e-8, hybrid_switch=2, max_matvec=4000,
+                                   refresh=refresh, fallback=fallback)
+    base = np.random.default_rng(5).standard_normal(grid.n)
+    code = {"rGCROT": 1, "rBiCGStab": 2}
+    fell_back = 0
+    for s in range(6):
+        b = base + 0.05 * s * np.random.default_rng(100 + s).standard_normal(grid.n)
+        x, info = prob.solve(t(b), tol=1e-8, m=20, k=10, mode="hybrid", hybrid_switch=2, max_matvec=4000,
+                             hybrid_refresh=refresh, hybrid_fallback=fallback)
+        base_before = seq.base
+        xo, io = seq.solve(b)
+        fell_back += int(seq.base != base_before)
+        assert info["mode_used"] == code[io["mode"]], (s, info["mode_used"], io["mode"])
+        xg = x.cpu().numpy()
+        rel = np.linalg.norm(op.residual(b, xg)) / np.linalg.norm(b)
+        assert rel <= 1e-8 and info["status"] == 0, (s, info)
+        assert np.linalg.norm(xg - xo) <= max(1e-6, 2.0 * kap * 1e-8) * np.linalg.norm(xo)
+        assert abs(info["matvecs"] - io["matvecs"]) <= max(4, int(0.25 * io["matvecs"])), (s, info, io)
+    if fallback:
+        assert fell_back >= 1
+
+
 def test_mixed_precision_sequence(ctx):
     """Mixed precision (A11): FP32 inner operator inside the FP64/double-float
     rGCROT recurrence with b - A x recomputed in FP64 every cycle. Every step

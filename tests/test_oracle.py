@@ -252,3 +252,61 @@ def test_fp32_operator_within_rounding_bound(S):
     bound = (S + 3) * 2.0 ** -24 * (np.abs(A) @ np.abs(z))
     assert np.all(np.abs(w32 - w64) <= bound)
     assert np.any(w32 != w64)  # it is not the FP64 operator
+
+
+def _porous_small():
+    n = (8, 7, 6)
+    solid, _ = sphere_pack(n, 1.5, 0.25, rng_for(41, 3), max_attempts=5000)
+    grid, coef = porous_skew_19pt(n, np.where(solid, 1e-3, 1.0), 15.0)
+    return grid, coef, Stencil(grid, coef)
+
+
+def test_hybrid_refresh_schedule():
+    """Hybrid with intermittent rGCROT solves (Sec. 2.4): with a switch after
+    2 solves and a refresh period of 2, the modes run rGCROT, rGCROT,
+    rBiCGStab, rGCROT, rBiCGStab, rGCROT; the recycle space changes exactly
+    on the rGCROT solves and every solve converges."""
+    grid, coef, op = _porous_small()
+    seq = oracle.RecyclingSequence(op, mode="hybrid", m=10, k=6, tol=1e-9, hybrid_switch=2, refresh=2,
+                                   max_matvec=3000)
+    base = np.random.default_rng(9).standard_normal(grid.n)
+    modes = []
+    for s in range(6):
+        b = base + 0.1 * s * np.random.default_rng(50 + s).standard_normal(grid.n)
+        C0 = None if seq.C is None else seq.C.copy()
+        x, info = seq.solve(b)
+        modes.append(info["mode"])
+        assert info["status"] == oracle.krylov.OK
+        assert np.linalg.norm(op.residual(b, x)) <= 1e-9 * np.linalg.norm(b) * 1.0000001
+        changed = C0 is None or C0.shape != seq.C.shape or not np.array_equal(C0, seq.C)
+        assert changed == (info["mode"] == "rGCROT"), (s, info["mode"])
+    assert modes == ["rGCROT", "rGCROT", "rBiCGStab", "rGCROT", "rBiCGStab", "rGCROT"]
+
+
+def test_hybrid_fallback_switches_back():
+    """Hybrid with the switch back to rGCROT (Sec. 2.4): an rBiCGStab solve
+    that has not converged after F products is finished by rGCROT from its
+    iterate (converging within the total budget, the products of both parts
+    counted), and the next solve runs rGCROT again (a new phase of
+    hybrid_switch solves starts with the fallback solve)."""
+    grid, coef, op = _porous_small()
+    F = 4
+    seq = oracle.RecyclingSequence(op, mode="hybrid", m=10, k=6, tol=1e-9, hybrid_switch=2, fallback=F,
+                                   max_matvec=3000)
+    plain = oracle.RecyclingSequence(op, mode="hybrid", m=10, k=6, tol=1e-9, hybrid_switch=2, max_matvec=3000)
+    base = np.random.default_rng(11).standard_normal(grid.n)
+    modes = []
+    for s in range(5):
+        b = base + 0.1 * s * np.random.default_rng(70 + s).standard_normal(grid.n)
+        x, info = seq.solve(b)
+        _, ip = plain.solve(b)
+        modes.append(info["mode"])
+        assert info["status"] == oracle.krylov.OK
+        assert np.linalg.norm(op.residual(b, x)) <= 1e-9 * np.linalg.norm(b) * 1.0000001
+        if s == 2:
+            # the plain hybrid needs more than F products here, so this solve fell back
+            assert ip["mode"] == "rBiCGStab" and ip["matvecs"] > F
+            assert info["mode"] == "rGCROT" and info["matvecs"] > F
+    # fallback at solve 2 starts a phase: solve 3 is rGCROT, solve 4 rBiCGStab (falling back again)
+    assert modes[:4] == ["rGCROT", "rGCROT", "rGCROT", "rGCROT"]
+    assert seq.base in (2, 4)
