@@ -94,6 +94,13 @@ typedef struct {
                               (within max_matvec in total), and the hybrid starts a new rGCROT
                               phase: that solve and the next hybrid_switch - 1 use rGCROT;
                               0 = off */
+  int32_t precond_side;  /* 0 = right point Jacobi (A M^{-1}, every solver); 1 = left for GMRES
+                            and rGCROT, as Sec. 2.1 states it: Arnoldi on M^{-1} A, x <- x + V y + U z,
+                            convergence on ||M^{-1}(b - A x)|| <= tol ||M^{-1} b|| (relres_true still
+                            reports ||b - A x|| / ||b||), recycle pair M^{-1} A U = C. rBiCGStab is
+                            always right-preconditioned (Sec. 2.1); a stored recycle space is
+                            converted (C re-derived from U by CholQR2) when a solve uses the other
+                            side. Left with RK_MIXED: RK_E_INVALID */
 } rk_solve_params;
 
 typedef struct {
@@ -156,6 +163,9 @@ int rk_set_recycle(rk_problem* p, const double* U, const double* C, int32_t k, v
  * Copy the recycle space out. U, C: device, N x capacity column-major (either
  * may be NULL). *k: in = capacity (columns), out = stored dimension.
  * Returns RK_E_INVALID if the capacity is smaller than the dimension.
+ * The pair satisfies A U = C after rk_set_recycle and right-preconditioned
+ * solves, M^{-1} A U = C after left-preconditioned GMRES / rGCROT solves
+ * (precond_side = 1); both with C^T C = I.
  */
 int rk_get_recycle(const rk_problem* p, double* U, double* C, int32_t* k, void* stream);
 
@@ -173,7 +183,8 @@ int rk_solve(rk_problem* p, const double* b, double* x, const rk_solve_params* p
 
 /*
  * Operator application (single products, for tests and callers that compose):
- * precond = 1: y = A (M^{-1} v); 0: y = A v; 2: the FP32 operator of
+ * precond = 1: y = A (M^{-1} v); 0: y = A v; 4: y = M^{-1} (A v) (left
+ * preconditioning: the product, then one rounded multiplication); 2: the FP32 operator of
  * RK_MIXED, y = A32 (M32^{-1} v) with A32, M32^{-1} the coefficients and
  * 1/a_pp rounded to FP32, v rounded to FP32, FP32 accumulation in band order,
  * the result widened to FP64; 3: the double-float operator of RK_DF,

@@ -104,3 +104,11 @@ class Stencil:
     def minv(self, v):
         """M^{-1} v with M = diag(A): one rounding per element."""
         return self.dinv * v
+
+    def apply_left(self, v):
+        """M^{-1} (A v) (left preconditioning): the product, then one rounding per element."""
+        return self.dinv * self.apply(v)
+
+    def residual_left(self, b, x):
+        """M^{-1} (b - A x)."""
+        return self.dinv * self.residual(b, x)

@@ -89,17 +89,24 @@ def _op(grid_or_op, coef=None):
 
 
 # --------------------------------------------------------------------------- GMRES(m)
-def gmres(op, b, x0=None, tol=1e-8, m=30, max_matvec=2000, keep_cycle=False):
+def gmres(op, b, x0=None, tol=1e-8, m=30, max_matvec=2000, keep_cycle=False, left=False):
     """GMRES(m), Algorithm 1, right-preconditioned by M = diag(A).
 
     Arnoldi with modified Gram-Schmidt on A M^{-1}; solution
-    update x <- x + M^{-1} V_j y; true residual b - A x after every cycle."""
+    update x <- x + M^{-1} V_j y; true residual b - A x after every cycle.
+    With ``left``, preconditioned from the left as Sec. 2.1 states it:
+    Arnoldi on M^{-1} A, x <- x + V_j y, and the convergence test on
+    ||M^{-1}(b - A x)|| <= tol ||M^{-1} b||; info's relres_true is still
+    ||b - A x|| / ||b||."""
     n = op.n
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=float)
-    bnorm = float(np.linalg.norm(b))
-    if bnorm == 0.0:
+    bnorm_true = float(np.linalg.norm(b))
+    if bnorm_true == 0.0:
         return np.zeros(n), _info(OK, 0, 0, 0, 0.0, 0.0, [])
-    r = op.residual(b, x)
+    bnorm = float(np.linalg.norm(op.minv(b))) if left else bnorm_true
+    resid = op.residual_left if left else op.residual
+    prod = op.apply_left if left else op.apply_prec
+    r = resid(b, x)
     rho = float(np.linalg.norm(r))
     matvecs = cycles = 0
     hist = [rho / bnorm]
@@ -112,7 +119,7 @@ def gmres(op, b, x0=None, tol=1e-8, m=30, max_matvec=2000, keep_cycle=False):
         ls = _LS(m, rho)
         jj = 0
         for j in range(m):
-            w = op.apply_prec(V[j])
+            w = prod(V[j])
             matvecs += 1
             for l in range(j + 1):
                 H[l, j] = V[l] @ w
@@ -127,30 +134,32 @@ def gmres(op, b, x0=None, tol=1e-8, m=30, max_matvec=2000, keep_cycle=False):
             if e <= tol * bnorm or happy or matvecs >= max_matvec:
                 break
         y = ls.solve(jj)
-        x = x + op.minv(V[:jj].T @ y)
-        r = op.residual(b, x)
+        x = x + (V[:jj].T @ y if left else op.minv(V[:jj].T @ y))
+        r = resid(b, x)
         rho = float(np.linalg.norm(r))
         cycles += 1
         hist.append(rho / bnorm)
         if keep_cycle:
             last = dict(V=V[: jj + 1].copy(), H=H[: jj + 1, :jj].copy(), y=y)
     st = OK if rho <= tol * bnorm else NOT_CONVERGED
-    info = _info(st, matvecs, cycles, 0, rho / bnorm, est, hist)
+    rel = float(np.linalg.norm(op.residual(b, x))) / bnorm_true if left else rho / bnorm
+    info = _info(st, matvecs, cycles, 0, rel, est, hist)
     if keep_cycle:
         info["last_cycle"] = last
     return x, info
 
 
 # --------------------------------------------------------------------------- recycle space helpers
-def recycle_from_u(op, U):
-    """Forming C from U (Algorithms 3 and 4): C~ = A U, thin QR C~ = C R; return (U R^{-1}, C) so A U = C."""
-    Ct = np.stack([op.apply(u) for u in U.T], axis=1)
+def recycle_from_u(op, U, left=False):
+    """Forming C from U (Algorithms 3 and 4): C~ = A U, thin QR C~ = C R; return (U R^{-1}, C) so A U = C.
+    With ``left``: C~ = M^{-1} A U, so M^{-1} A U = C."""
+    Ct = np.stack([(op.apply_left(u) if left else op.apply(u)) for u in U.T], axis=1)
     Q, R = np.linalg.qr(Ct)
     Unew = sla.solve_triangular(R, U.T, trans="T", lower=False).T  # U R^{-1}
     return Unew, Q
 
 
-def harmonic_ritz_update(op, U, C, V, B, H, jj, k, return_theta=False):
+def harmonic_ritz_update(op, U, C, V, B, H, jj, k, return_theta=False, left=False):
     """Recycle-space update of Algorithm 3: new recycle space from harmonic Ritz vectors.
 
     W = [U, M^{-1} V_j] (x-space) and W_hat = [C, V_{j+1}] satisfy
@@ -161,7 +170,8 @@ def harmonic_ritz_update(op, U, C, V, B, H, jj, k, return_theta=False):
     smallest |theta| (a complex pair enters as [Re p, Im p]; a pair split by
     the cut is dropped; infinite theta never selected) form P; with
     G P = Q R' (thin QR), C <- W_hat Q and U <- W P R'^{-1}, which keeps
-    A U = C and C^T C = I."""
+    A U = C and C^T C = I. With ``left`` (Arnoldi on M^{-1} A): W = [U, V_j],
+    F = W_hat^T W, and the update keeps M^{-1} A U = C."""
     n = op.n
     kc = 0 if U is None else U.shape[1]
     nn = kc + jj
@@ -170,7 +180,7 @@ def harmonic_ritz_update(op, U, C, V, B, H, jj, k, return_theta=False):
     if kc:
         G[:kc, :kc] = np.eye(kc)
         G[:kc, kc:] = B[:kc, :jj]
-        MU = U * op.coef[0][:, None]
+        MU = U if left else U * op.coef[0][:, None]
         F[:kc, :kc] = C.T @ MU
         F[kc:, :kc] = V[: jj + 1] @ MU
     G[kc:, kc:] = H[: jj + 1, :jj]
@@ -211,8 +221,8 @@ def harmonic_ritz_update(op, U, C, V, B, H, jj, k, return_theta=False):
     P = np.stack(cols, axis=1)
     Q, Rp = np.linalg.qr(G @ P)
     What = np.concatenate([C, V[: jj + 1].T], axis=1) if kc else V[: jj + 1].T
-    Wx = (np.concatenate([U, (op.dinv[:, None] * V[:jj].T)], axis=1) if kc
-          else op.dinv[:, None] * V[:jj].T)
+    Vx = V[:jj].T if left else op.dinv[:, None] * V[:jj].T
+    Wx = np.concatenate([U, Vx], axis=1) if kc else Vx
     Cn = What @ Q
     Un = Wx @ sla.solve_triangular(Rp, P.T, trans="T", lower=False).T  # W P R'^{-1}
     return (Un, Cn, theta) if return_theta else (Un, Cn)
@@ -220,22 +230,28 @@ def harmonic_ritz_update(op, U, C, V, B, H, jj, k, return_theta=False):
 
 # --------------------------------------------------------------------------- rGCROT(m,k)
 def rgcrot(op, b, x0=None, tol=1e-8, m=30, k=10, U=None, C=None, update=True, max_matvec=2000,
-           keep_cycle=False):
+           keep_cycle=False, left=False):
     """rGCROT(m,k), Algorithm 3, right-preconditioned by M = diag(A).
 
     U, C are N x k_cur arrays (or None) with A U = C, C^T C = I; if only U is
-    given, C is formed from it (recycle_from_u). Returns (x, U, C, info)."""
+    given, C is formed from it (recycle_from_u). Returns (x, U, C, info).
+    With ``left`` (Sec. 2.1's side): Arnoldi on M^{-1} A, M^{-1} A U = C,
+    x <- x + V_j y + U z, and the convergence test on ||M^{-1}(b - A x)||
+    relative to ||M^{-1} b||; info's relres_true is ||b - A x|| / ||b||."""
     n = op.n
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=float)
-    bnorm = float(np.linalg.norm(b))
+    bnorm_true = float(np.linalg.norm(b))
     if U is not None and U.shape[1] == 0:
         U = C = None
     if U is not None and C is None:
-        U, C = recycle_from_u(op, U)
+        U, C = recycle_from_u(op, U, left)
     kc = 0 if U is None else U.shape[1]
-    if bnorm == 0.0:
+    if bnorm_true == 0.0:
         return np.zeros(n), U, C, _info(OK, 0, 0, 0, 0.0, 0.0, [], kc)
-    rhat = op.residual(b, x)                      # initial residual
+    bnorm = float(np.linalg.norm(op.minv(b))) if left else bnorm_true
+    resid = op.residual_left if left else op.residual
+    prod = op.apply_left if left else op.apply_prec
+    rhat = resid(b, x)                            # initial residual
     if kc:
         xi = C.T @ rhat                           # projection onto C
         r = rhat - C @ xi
@@ -265,7 +281,7 @@ def rgcrot(op, b, x0=None, tol=1e-8, m=30, k=10, U=None, C=None, update=True, ma
         ls = _LS(m, rho)
         jj = 0
         for j in range(m):                              # Arnoldi steps
-            w = op.apply_prec(V[j])                     # w = A M^{-1} v_j
+            w = prod(V[j])                              # w = A M^{-1} v_j (left: M^{-1} A v_j)
             matvecs += 1
             for l in range(kc):                         # B column: w <- w - C C^T w
                 Bm[l, j] = C[:, l] @ w
@@ -283,11 +299,11 @@ def rgcrot(op, b, x0=None, tol=1e-8, m=30, k=10, U=None, C=None, update=True, ma
             if e <= tol * bnorm or happy or matvecs >= max_matvec:
                 break
         y = ls.solve(jj)                                # least squares for y
-        x = x + op.minv(V[:jj].T @ y)                   # x <- x + M^{-1} V_j y
+        x = x + (V[:jj].T @ y if left else op.minv(V[:jj].T @ y))   # x <- x + M^{-1} V_j y
         if kc:
             z = -Bm[:kc, :jj] @ y                       # z = -B y
             x = x + U @ z                               # x <- x + U z
-        r = op.residual(b, x)                           # true residual
+        r = resid(b, x)                                 # true residual
         rho = float(np.linalg.norm(r))
         cycles += 1
         hist.append(rho / bnorm)
@@ -295,10 +311,11 @@ def rgcrot(op, b, x0=None, tol=1e-8, m=30, k=10, U=None, C=None, update=True, ma
             last = dict(V=V[: jj + 1].copy(), H=H[: jj + 1, :jj].copy(), B=Bm[:kc, :jj].copy(),
                         C=None if C is None else C.copy(), U=None if U is None else U.copy(), y=y, jj=jj)
         if update and k > 0:                            # recycle-space update
-            U, C = harmonic_ritz_update(op, U, C, V, Bm, H, jj, k)
+            U, C = harmonic_ritz_update(op, U, C, V, Bm, H, jj, k, left=left)
             kc = 0 if U is None else U.shape[1]
     st = OK if rho <= tol * bnorm else NOT_CONVERGED
-    info = _info(st, matvecs, cycles, 0, rho / bnorm, est, hist, kc)
+    rel = float(np.linalg.norm(op.residual(b, x))) / bnorm_true if left else rho / bnorm
+    info = _info(st, matvecs, cycles, 0, rel, est, hist, kc)
     if keep_cycle:
         info["last_cycle"] = last
     return x, U, C, info
@@ -497,16 +514,27 @@ class RecyclingSequence:
     rBiCGStab solve that breaks down or has used F matrix-vector products
     without converging, finishes it with rGCROT from its current iterate
     (within ``max_matvec`` in total) and starts a new rGCROT phase with that
-    solve ("if convergence is poor ... switch back to rGCROT")."""
+    solve ("if convergence is poor ... switch back to rGCROT").
+
+    ``left``: GMRES and rGCROT preconditioned from the left (Sec. 2.1); the
+    carried pair then satisfies M^{-1} A U = C, and a solve on the other
+    side (rBiCGStab is always right-preconditioned) first re-forms C from U
+    for its operator (recycle_from_u)."""
 
     def __init__(self, op, mode="rGCROT", m=30, k=10, tol=1e-8, hybrid_switch=5, max_matvec=2000, refresh=0,
-                 fallback=0):
+                 fallback=0, left=False):
         self.op, self.mode, self.m, self.k, self.tol = op, mode, m, k, tol
         self.hybrid_switch, self.max_matvec = hybrid_switch, max_matvec
-        self.refresh, self.fallback = refresh, fallback
+        self.refresh, self.fallback, self.left = refresh, fallback, left
         self.U = self.C = None
+        self.side = False  # side of the carried pair: False A U = C, True M^{-1} A U = C
         self.t = 0
         self.base = 0  # first solve of the current rGCROT phase (hybrid)
+
+    def _side(self, left):
+        if self.U is not None and self.U.shape[1] > 0 and self.side != left:
+            self.U, self.C = recycle_from_u(self.op, self.U, left)
+        self.side = left
 
     def solve(self, b, x0=None):
         mode = self.mode
@@ -517,11 +545,13 @@ class RecyclingSequence:
             mode = "rGCROT" if (t < self.hybrid_switch or refresh) else "rBiCGStab"
             if mode == "rBiCGStab" and self.fallback > 0:
                 cap = min(self.fallback, self.max_matvec)
+                self._side(False)
                 x, info = rbicgstab(self.op, b, x0, self.tol, self.U, self.C, cap)
                 if info["status"] != OK and info["matvecs"] < self.max_matvec:
                     used = info["matvecs"]
+                    self._side(self.left)
                     x, self.U, self.C, ig = rgcrot(self.op, b, x, self.tol, self.m, self.k, self.U, self.C,
-                                                   update=True, max_matvec=self.max_matvec - used)
+                                                   update=True, max_matvec=self.max_matvec - used, left=self.left)
                     ig["matvecs"] += used
                     ig["restarts"] += info["restarts"]
                     info = ig
@@ -531,13 +561,15 @@ class RecyclingSequence:
                 self.t += 1
                 return x, info
         if mode == "GMRES":
-            x, info = gmres(self.op, b, x0, self.tol, self.m, self.max_matvec)
+            x, info = gmres(self.op, b, x0, self.tol, self.m, self.max_matvec, left=self.left)
         elif mode == "rGCROT":
+            self._side(self.left)
             x, self.U, self.C, info = rgcrot(self.op, b, x0, self.tol, self.m, self.k, self.U, self.C,
-                                             update=True, max_matvec=self.max_matvec)
+                                             update=True, max_matvec=self.max_matvec, left=self.left)
         elif mode == "BiCGStab":
             x, info = bicgstab(self.op, b, x0, self.tol, self.max_matvec)
         elif mode == "rBiCGStab":
+            self._side(False)
             x, info = rbicgstab(self.op, b, x0, self.tol, self.U, self.C, self.max_matvec)
         else:
             raise ValueError(mode)

@@ -35,8 +35,10 @@ inline int red_blocks(int64_t n) {
 }
 
 // ---- stencil.cu
-enum StencilMode { ST_PREC = 0, ST_PLAIN = 1, ST_RESID = 2 };
-// y = A (dinv .* v) [ST_PREC], y = A v [ST_PLAIN], y = b - A v [ST_RESID].
+enum StencilMode { ST_PREC = 0, ST_PLAIN = 1, ST_RESID = 2, ST_LEFT = 3, ST_LRESID = 4 };
+// y = A (dinv .* v) [ST_PREC], y = A v [ST_PLAIN], y = b - A v [ST_RESID],
+// y = dinv .* (A v) [ST_LEFT], y = dinv .* (b - A v) [ST_LRESID] (left
+// preconditioning: the product, then one rounded multiplication).
 // part (nullable): per-block partial sums of y^2, reduced by the last block into *nrm2.
 cudaError_t launch_stencil(const Dims& d, int S, int mode, const double* coef, const double* dinv,
                            const double* v, const double* b, double* y, double* part,
@@ -51,7 +53,7 @@ cudaError_t launch_stencil32(const Dims& d, int S, const float* coef32, const fl
 // Double-float operator (RK_DF): bands and 1/a_pp as double-float copies
 // (launch_round_df), v and y double-float (v_df / y_df) or FP64.
 cudaError_t launch_round_df(int64_t n, const double* src, float2* dst, cudaStream_t st);
-cudaError_t launch_stencil_dd(const Dims& d, int S, bool precond, const float2* coefd, const float2* dinvd,
+cudaError_t launch_stencil_dd(const Dims& d, int S, int mode, const float2* coefd, const float2* dinvd,
                               const void* v, bool v_df, void* y, bool y_df, const int* skip, cudaStream_t st);
 cudaError_t launch_round_f32(int64_t n, const double* src, float* dst, cudaStream_t st);
 cudaError_t launch_stencil_df(const Dims& d, int S, int mode, const double* coef, const double* dinv,

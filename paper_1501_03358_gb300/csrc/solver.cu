@@ -211,6 +211,8 @@ struct rk_problem {
   int* istat = nullptr;           // device ints for small kernels
   int solves = 0;
   int hyb_base = 0;  // first solve of the current rGCROT phase of RK_HYBRID
+  int kside = 0;     // side of the stored recycle pair: 0 A U = C, 1 M^{-1} A U = C
+  double dinv_max = 0.0;  // max |1 / a_pp|
 
   float2* Vcol(int j) const { return QB + (int64_t)(kmax + j) * ld; }
   float2* Cblk(int kc) const { return QB + (int64_t)(kmax - kc) * ld; }
@@ -463,16 +465,14 @@ int stencil_launch(rk_problem* p, int mode, const double* v, const double* b, do
                    unsigned* counter, double* nrm2, const int* skip, cudaStream_t st) {
   const bool resid = mode == ST_RESID;
   ProfScope ps(&p->prof, resid ? PC_RESID : PC_SPMV, 8.0 * (p->S + (resid ? 3 : 2)) * (double)p->n, st);
-  RK_CUDA(launch_stencil(p->d, p->S, mode, p->coef, mode == ST_PREC ? p->dinv : nullptr, v, b, y, part, counter,
-                         nrm2, skip, st));
+  RK_CUDA(launch_stencil(p->d, p->S, mode, p->coef, p->dinv, v, b, y, part, counter, nrm2, skip, st));
   return RK_OK;
 }
 
 int stencil_df_launch(rk_problem* p, int mode, const void* v, bool v_df, void* y, bool y_df, const int* skip,
                       cudaStream_t st) {
   ProfScope ps(&p->prof, PC_SPMV, 8.0 * (p->S + 2) * (double)p->n, st);
-  RK_CUDA(launch_stencil_df(p->d, p->S, mode, p->coef, mode == ST_PREC ? p->dinv : nullptr, v, v_df, y, y_df, skip,
-                            st));
+  RK_CUDA(launch_stencil_df(p->d, p->S, mode, p->coef, p->dinv, v, v_df, y, y_df, skip, st));
   return RK_OK;
 }
 
@@ -509,16 +509,17 @@ int ensure_operator(rk_problem* p, int precision, cudaStream_t st) {
 // A M^{-1} v of the recurrences: FP64 (bit-exact order), the FP32 operator
 // (RK_MIXED) or the double-float operator (RK_DF)
 int opapply_launch(rk_problem* p, int precision, const void* v, bool v_df, void* y, bool y_df, const int* skip,
-                   cudaStream_t st) {
+                   cudaStream_t st, bool left = false) {
+  const int mode = left ? ST_LEFT : ST_PREC;
   if (precision == RK_DF) {
     ProfScope ps(&p->prof, PC_SPMV, 8.0 * (p->S + 2) * (double)p->n, st);
-    RK_CUDA(launch_stencil_dd(p->d, p->S, true, p->coefdf, p->dinvdf, v, v_df, y, y_df, skip, st));
+    RK_CUDA(launch_stencil_dd(p->d, p->S, mode, p->coefdf, p->dinvdf, v, v_df, y, y_df, skip, st));
     return RK_OK;
   }
   if (precision != RK_MIXED) {
     if (!v_df && !y_df)
-      return stencil_launch(p, ST_PREC, (const double*)v, nullptr, (double*)y, nullptr, nullptr, nullptr, skip, st);
-    return stencil_df_launch(p, ST_PREC, v, v_df, y, y_df, skip, st);
+      return stencil_launch(p, mode, (const double*)v, nullptr, (double*)y, nullptr, nullptr, nullptr, skip, st);
+    return stencil_df_launch(p, mode, v, v_df, y, y_df, skip, st);
   }
   ProfScope ps(&p->prof, PC_SPMV, 8.0 * (0.5 * p->S + 2.5) * (double)p->n, st);
   RK_CUDA(launch_stencil32(p->d, p->S, p->coef32, p->dinv32, v, v_df, y, y_df, skip, st));
@@ -527,15 +528,15 @@ int opapply_launch(rk_problem* p, int precision, const void* v, bool v_df, void*
 
 // C = orth(A U) in FP64 with U rescaled so that A U = C (CholQR2, as when C is formed from U)
 // for the k stored columns.
-int derive_c_from_u(rk_problem* p, int k, cudaStream_t st) {
+int derive_c_from_u(rk_problem* p, int k, cudaStream_t st, bool left = false) {
   float2* Ud = p->Ublk(k);
   float2* Cd = p->Cblk(k);
   double* G = p->eta;
   double* Rinv = p->eta + (size_t)k * k;
   double* Rw = p->sb.hrws;
   for (int c = 0; c < k; ++c)
-    RK_CUDA(launch_stencil_df(p->d, p->S, ST_PLAIN, p->coef, nullptr, Ud + (int64_t)c * p->ld, true,
-                              Cd + (int64_t)c * p->ld, true, nullptr, st));
+    RK_CUDA(launch_stencil_df(p->d, p->S, left ? ST_LEFT : ST_PLAIN, p->coef, p->dinv, Ud + (int64_t)c * p->ld,
+                              true, Cd + (int64_t)c * p->ld, true, nullptr, st));
   for (int pass = 0; pass < 2; ++pass) {
     DFGramArgs g{};
     g.n = p->n;
@@ -561,6 +562,15 @@ int derive_c_from_u(rk_problem* p, int k, cudaStream_t st) {
     RK_TRY(dfgemm_launch(p, Cd, k, nullptr, 0, nullptr, Rinv, k, Cd, true, 0, st));
     RK_TRY(dfgemm_launch(p, Ud, k, nullptr, 0, nullptr, Rinv, k, Ud, true, 0, st));
   }
+  return RK_OK;
+}
+
+// The stored recycle pair for a solve on the given preconditioning side: the
+// two sides' pairs span the same U with different C (A U versus M^{-1} A U,
+// orthonormalised), so a switch re-derives C from U.
+int ensure_side(rk_problem* p, bool left, cudaStream_t st) {
+  if (p->kdim > 0 && p->kside != (left ? 1 : 0)) RK_TRY(derive_c_from_u(p, p->kdim, st, left));
+  p->kside = left ? 1 : 0;
   return RK_OK;
 }
 
@@ -591,18 +601,30 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
   const int maxmv = prm.max_matvec > 0 ? prm.max_matvec : 2000;
   const bool mixed = prm.precision == RK_MIXED;
   const int opk = prm.precision;
+  const bool left = prm.precond_side == 1;  // Sec. 2.1: M^{-1} A for GMRES / rGCROT
   RK_TRY(ensure_capacity(p, std::max(k, p->kdim), m, st));
   RK_TRY(ensure_operator(p, opk, st));
+  if (recycle) RK_TRY(ensure_side(p, left, st));
   int kc = recycle ? p->kdim : 0;
   const double S = p->S;
   double words = 0.0;
-  // ||b||
+  double* r = p->rvec;
+  // ||b|| (left: also ||M^{-1} b||, the reference of the convergence test)
   RK_TRY(norm2_into(p, b, 0, st));
   { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_set_tol(p->st, prm.tol, st)); }
   RK_TRY(sync_state(p, st));
+  const double bnorm_true = p->st_h->bnorm;
+  if (!std::isfinite(bnorm_true)) return fail(RK_E_INVALID, "b contains NaN or Inf");
+  if (left && bnorm_true != 0.0) {
+    RK_CUDA(cudaMemsetAsync(r, 0, sizeof(double) * p->n, st));
+    RK_CUDA(launch_axpy_scaled(p->n, p->dinv, b, r, st));
+    RK_TRY(norm2_into(p, r, 0, st));
+    { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_set_tol(p->st, prm.tol, st)); }
+    RK_TRY(sync_state(p, st));
+  }
   const double bnorm = p->st_h->bnorm;
-  if (!std::isfinite(bnorm)) return fail(RK_E_INVALID, "b contains NaN or Inf");
-  if (bnorm == 0.0) {
+  const int resid_mode = left ? ST_LRESID : ST_RESID;
+  if (bnorm_true == 0.0) {
     RK_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * p->n, st));
     RK_CUDA(cudaStreamSynchronize(st));
     info.status = RK_OK;
@@ -610,9 +632,9 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
     return RK_OK;
   }
   const double tolabs = prm.tol * bnorm;
-  // initial residual r = b - A x (FP64); its projection onto C
-  double* r = p->rvec;
-  RK_TRY(stencil_launch(p, ST_RESID, x, b, r, p->part, p->counter, &p->st->rho2, nullptr, st));
+  // initial residual r = b - A x (left: M^{-1}(b - A x)) in FP64; its
+  // projection onto C
+  RK_TRY(stencil_launch(p, resid_mode, x, b, r, p->part, p->counter, &p->st->rho2, nullptr, st));
   RK_TRY(project_residual(p, kc, r, x, st));
   words += (S + 3) + (kc ? 2.0 * kc + 3 : 0) + 1;
   RK_TRY(sync_state(p, st));
@@ -635,7 +657,7 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
       // pass per step (Gram-Schmidt against [C V_j] with the second pass of
       // each vector delayed to the next step)
       for (int j = 0; j < steps; ++j) {
-        RK_TRY(opapply_launch(p, opk, p->Vcol(j), true, p->Vcol(j + 1), true, done, st));
+        RK_TRY(opapply_launch(p, opk, p->Vcol(j), true, p->Vcol(j + 1), true, done, st, left));
         const int nq = kc + j;
         RK_TRY(dfdots2_launch(p, p->Cblk(kc), nq, p->Vcol(j), p->Vcol(j + 1), p->sb.dots, done, st));
         { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_dcgs_coef(p->st, p->sb, kc, j, 0, st)); }
@@ -655,7 +677,8 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
     if (p->prof.on) {
       RK_TRY(cycle(st));
     } else {
-      const uint64_t key = ((uint64_t)kc << 32) | ((uint64_t)steps << 3) | ((uint64_t)opk << 1) | (keep_last ? 1u : 0u);
+      const uint64_t key = ((uint64_t)kc << 32) | ((uint64_t)steps << 4) | (left ? 8u : 0u) | ((uint64_t)opk << 1) |
+                           (keep_last ? 1u : 0u);
       auto it = p->graphs.find(key);
       if (it == p->graphs.end()) {
         cudaGraph_t g = nullptr;
@@ -682,9 +705,10 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
     est = p->st_h->est / bnorm;
     matvecs += p->st_h->nspmv;
     cycles += 1;
-    // y, z = -B y, x <- x + M^{-1} V_j y + U z
+    // y, z = -B y, x <- x + M^{-1} V_j y + U z (left: x <- x + V_j y + U z)
     { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_cycle_solve(p->st, p->sb, kc, st)); }
-    RK_TRY(dfgemm_launch(p, p->Ublk(kc), kc, p->Vcol(0), jj, p->dinv, p->sb.xcoef, 1, x, false, 1, st));
+    RK_TRY(dfgemm_launch(p, p->Ublk(kc), kc, p->Vcol(0), jj, left ? nullptr : p->dinv, p->sb.xcoef, 1, x, false, 1,
+                         st));
     words += model_words_cycle(p->S, kc, jj, m);
     // recycle update (harmonic Ritz)
     if (update && k > 0) {
@@ -698,7 +722,7 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
         g.lda = p->ld;
         g.Bm = p->Vcol(0);
         g.ldb = p->ld;
-        g.d = p->coef;  // diag(A) = band 0
+        g.d = left ? nullptr : p->coef;  // M = diag(A) = band 0 (left: F = W_hat^T W)
         g.U = p->Ublk(kc);
         g.ldu = p->ld;
         g.part = p->part;
@@ -710,17 +734,18 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
       RK_TRY(sync_state(p, st));
       const int knew = p->st_h->knew;
       if (p->st_h->hr_status == 0 && knew > 0) {
-        // C <- [C V_{j+1}] QC, U <- [U, M^{-1} V_j] PU, both in place (row tiles)
+        // C <- [C V_{j+1}] QC, U <- [U, M^{-1} V_j] PU (left: [U, V_j] PU), in place (row tiles)
         RK_TRY(dfgemm_launch(p, p->Cblk(kc), kc, p->Vcol(0), jj + 1, nullptr, p->sb.QC, knew, p->Cblk(knew), true, 0,
                              st));
-        RK_TRY(dfgemm_launch(p, p->Ublk(kc), kc, p->Vcol(0), jj, p->dinv, p->sb.PU, knew, p->Ublk(knew), true, 0, st));
+        RK_TRY(dfgemm_launch(p, p->Ublk(kc), kc, p->Vcol(0), jj, left ? nullptr : p->dinv, p->sb.PU, knew,
+                             p->Ublk(knew), true, 0, st));
         kc = knew;
         p->kdim = knew;
         words += 6.0 * kc + 3.0 * jj + 4;
       }
     }
-    // true residual r = b - A x; the next cycle projects it onto C
-    RK_TRY(stencil_launch(p, ST_RESID, x, b, r, p->part, p->counter, &p->st->rho2, nullptr, st));
+    // true residual r = b - A x (left: M^{-1}(b - A x)); the next cycle projects it onto C
+    RK_TRY(stencil_launch(p, resid_mode, x, b, r, p->part, p->counter, &p->st->rho2, nullptr, st));
     RK_TRY(project_residual(p, kc, r, x, st));
     RK_TRY(sync_state(p, st));
     rho = std::sqrt(p->st_h->rho2);
@@ -733,6 +758,12 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
   info.matvecs = matvecs;
   info.cycles_or_iters = cycles;
   info.relres_true = rho / bnorm;
+  if (left) {
+    // the convergence test was on M^{-1}(b - A x); report ||b - A x|| / ||b||
+    RK_TRY(stencil_launch(p, ST_RESID, x, b, r, p->part, p->counter, &p->st->rho2, nullptr, st));
+    RK_TRY(sync_state(p, st));
+    info.relres_true = std::sqrt(p->st_h->rho2) / bnorm_true;
+  }
   info.relres_est = est;
   info.recycle_dim = p->kdim;
   info.model_bytes = 8.0 * words * (double)p->n;
@@ -748,6 +779,7 @@ int solve_bicg(rk_problem* p, const double* b, double* x, const rk_solve_params&
   RK_TRY(ensure_capacity(p, p->kdim, std::max(p->mcap, 1), st));
   RK_TRY(ensure_operator(p, opk, st));
   if (!p->bicg) RK_TRY(alloc_into(p->ctx, &p->bicg, (size_t)7 * p->ld));
+  if (recycle) RK_TRY(ensure_side(p, false, st));  // Sec. 2.1: BiCGStab is right-preconditioned
   const int kc = recycle ? p->kdim : 0;
   BicgVecs v{};
   v.r = p->bicg;
@@ -1025,13 +1057,13 @@ int rk_apply(const rk_problem* p, const double* v, double* y, int32_t precond, v
   if (precond == 3) {
     rk_problem* pm = const_cast<rk_problem*>(p);
     RK_TRY(ensure_dfop(pm, (cudaStream_t)stream));
-    RK_CUDA(launch_stencil_dd(p->d, p->S, true, p->coefdf, p->dinvdf, v, false, y, false, nullptr,
+    RK_CUDA(launch_stencil_dd(p->d, p->S, ST_PREC, p->coefdf, p->dinvdf, v, false, y, false, nullptr,
                               (cudaStream_t)stream));
     RK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     return RK_OK;
   }
-  if (precond < 0 || precond > 3) return fail(RK_E_INVALID, "precond must be 0..3");
-  RK_CUDA(launch_stencil(p->d, p->S, precond ? ST_PREC : ST_PLAIN, p->coef, p->dinv, v, nullptr, y, nullptr,
+  if (precond < 0 || precond > 4) return fail(RK_E_INVALID, "precond must be 0..4");
+  RK_CUDA(launch_stencil(p->d, p->S, precond == 4 ? ST_LEFT : (precond ? ST_PREC : ST_PLAIN), p->coef, p->dinv, v, nullptr, y, nullptr,
                          nullptr, nullptr, nullptr, (cudaStream_t)stream));
   RK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
   return RK_OK;
@@ -1165,6 +1197,7 @@ int rk_set_recycle(rk_problem* p, const double* U, const double* C, int32_t k, v
   if (!C) {
     // forming C from U: C~ = A U; thin QR by CholQR2 (C~ = C R), U <- U R^{-1}
     RK_TRY(derive_c_from_u(p, k, st));
+    p->kside = 0;
   } else {
     RK_CUDA(launch_to_df(p->n, C, Cd, nullptr, 0, k, p->n, p->ld, st));
     // invariants: ||C^T C - I||_F and ||A U - C||_F
@@ -1200,6 +1233,7 @@ int rk_set_recycle(rk_problem* p, const double* U, const double* C, int32_t k, v
   }
   RK_CUDA(cudaStreamSynchronize(st));
   p->kdim = k;
+  p->kside = 0;  // A U = C
   return RK_OK;
 }
 
@@ -1233,6 +1267,9 @@ int rk_solve(rk_problem* p, const double* b, double* x, const rk_solve_params* p
   std::memset(&inf, 0, sizeof(inf));
   cudaStream_t st = (cudaStream_t)stream;
   if (prm.hybrid_refresh < 0 || prm.hybrid_fallback < 0) return fail(RK_E_INVALID, "negative hybrid parameter");
+  if (prm.precond_side != 0 && prm.precond_side != 1) return fail(RK_E_INVALID, "precond_side must be 0 or 1");
+  if (prm.precond_side == 1 && prm.precision == RK_MIXED)
+    return fail(RK_E_INVALID, "left preconditioning is not available with RK_MIXED");
   int mode = prm.mode;
   const bool hybrid = mode == RK_HYBRID;
   if (hybrid) {
@@ -1451,8 +1488,9 @@ int rk_solve_batch(rk_problem* const* problems, const double* const* b, double* 
 }
 
 
-// Opaque recycle-space blob: 4 int64 (magic, n, k, reserved), then U and C as
-// stored (k double-float columns of n each).
+// Opaque recycle-space blob: 4 int64 (magic, n, k, side of the pair: 0
+// A U = C, 1 M^{-1} A U = C), then U and C as stored (k double-float
+// columns of n each).
 static const int64_t kRecycleMagic = 0x524b524543594331LL;  // "RKRECYC1"
 
 int rk_recycle_bytes(const rk_problem* p, int64_t* bytes) {
@@ -1467,7 +1505,7 @@ int rk_export_recycle(const rk_problem* p, void* buf, int64_t cap, void* stream)
   RK_TRY(rk_recycle_bytes(p, &need));
   if (cap < need) return fail(RK_E_INVALID, "export buffer too small");
   cudaStream_t st = (cudaStream_t)stream;
-  const int64_t hdr[4] = {kRecycleMagic, p->n, p->kdim, 0};
+  const int64_t hdr[4] = {kRecycleMagic, p->n, p->kdim, p->kside};
   char* b = (char*)buf;
   RK_CUDA(cudaMemcpyAsync(b, hdr, sizeof(hdr), cudaMemcpyHostToDevice, st));
   const int k = p->kdim;
@@ -1492,6 +1530,7 @@ int rk_import_recycle(rk_problem* p, const void* buf, int64_t bytes, void* strea
   if (hdr[1] != p->n) return fail(RK_E_INVALID, "recycle blob is for another problem size");
   const int64_t k = hdr[2];
   if (k < 0 || k > 256) return fail(RK_E_INVALID, "bad recycle dimension in blob");
+  if (hdr[3] != 0 && hdr[3] != 1) return fail(RK_E_INVALID, "bad recycle side in blob");
   const size_t col = sizeof(float2) * (size_t)p->n;
   if (bytes < 32 + 2 * (int64_t)col * k) return fail(RK_E_INVALID, "recycle blob too short");
   p->kdim = 0;
@@ -1504,6 +1543,7 @@ int rk_import_recycle(rk_problem* p, const void* buf, int64_t bytes, void* strea
                             cudaMemcpyDeviceToDevice, st));
   RK_CUDA(cudaStreamSynchronize(st));
   p->kdim = (int)k;
+  p->kside = (int)hdr[3];
   return RK_OK;
 }
 

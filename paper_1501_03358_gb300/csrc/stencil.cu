@@ -111,7 +111,8 @@ __global__ void __launch_bounds__(kTX* kTY) k_stencil(Dims d, const double* __re
           w = fma(__ldg(&coef[17 * N + p]), sz[sp][cy - 1][cx], w);
           w = fma(__ldg(&coef[18 * N + p]), sz[sp][cy + 1][cx], w);
         }
-        if (MODE == ST_RESID) w = __ldg(&b[p]) - w;
+        if (MODE == ST_RESID || MODE == ST_LRESID) w = __ldg(&b[p]) - w;
+        if (MODE == ST_LEFT || MODE == ST_LRESID) w = __dmul_rn(w, __ldg(&dinv[p]));
         st_val<YT>(y, p, w);
         if (part != nullptr) acc2 = fma(w, w, acc2);
       }
@@ -335,7 +336,9 @@ __global__ void __launch_bounds__(kTX* kTY) k_stencil_dd(Dims d, const float2* _
         mac(18, sz[sp][cy + 1][cx]);
       }
       df_renorm(s, c);
-      st_df<YT>(y, p, make_float2(s, c));
+      float2 wv = make_float2(s, c);
+      if (MODE == ST_LEFT) wv = df_mul(wv, __ldg(&dinv[p]));
+      st_df<YT>(y, p, wv);
     }
     __syncthreads();
   }
@@ -386,15 +389,18 @@ cudaError_t launch_stencil(const Dims& d, int S, int mode, const double* coef, c
   stencil_grid(d, grid, zchunk);
   const dim3 block(kTX * kTY);
 #define RK_ST(SS, MM) k_stencil<SS, MM><<<grid, block, 0, st>>>(d, coef, dinv, v, b, y, part, counter, nrm2, skip, zchunk)
+#define RK_ST_MODES(SS)                                 \
+  if (mode == ST_PREC) RK_ST(SS, ST_PREC);              \
+  else if (mode == ST_PLAIN) RK_ST(SS, ST_PLAIN);       \
+  else if (mode == ST_RESID) RK_ST(SS, ST_RESID);       \
+  else if (mode == ST_LEFT) RK_ST(SS, ST_LEFT);         \
+  else RK_ST(SS, ST_LRESID);
   if (S == 7) {
-    if (mode == ST_PREC) RK_ST(7, ST_PREC);
-    else if (mode == ST_PLAIN) RK_ST(7, ST_PLAIN);
-    else RK_ST(7, ST_RESID);
+    RK_ST_MODES(7)
   } else {
-    if (mode == ST_PREC) RK_ST(19, ST_PREC);
-    else if (mode == ST_PLAIN) RK_ST(19, ST_PLAIN);
-    else RK_ST(19, ST_RESID);
+    RK_ST_MODES(19)
   }
+#undef RK_ST_MODES
 #undef RK_ST
   return cudaGetLastError();
 }
@@ -433,7 +439,7 @@ cudaError_t launch_stencil_df(const Dims& d, int S, int mode, const double* coef
   int zchunk;
   stencil_grid(d, grid, zchunk);
   const dim3 block(kTX * kTY);
-  if (mode == ST_RESID) return cudaErrorInvalidValue;
+  if (mode == ST_RESID || mode == ST_LRESID) return cudaErrorInvalidValue;
 #define RK_STD(SS, MM, VT, YT)                                                                                  \
   k_stencil<SS, MM, VT, YT><<<grid, block, 0, st>>>(d, coef, dinv, (const VT*)v, nullptr, (YT*)y, nullptr, nullptr, \
                                                     nullptr, skip, zchunk)
@@ -443,9 +449,9 @@ cudaError_t launch_stencil_df(const Dims& d, int S, int mode, const double* coef
   else if (y_df) RK_STD(SS, MM, double, float2);    \
   else RK_STD(SS, MM, double, double);
   if (S == 7) {
-    if (mode == ST_PREC) { RK_STD_TYPES(7, ST_PREC) } else { RK_STD_TYPES(7, ST_PLAIN) }
+    if (mode == ST_PREC) { RK_STD_TYPES(7, ST_PREC) } else if (mode == ST_LEFT) { RK_STD_TYPES(7, ST_LEFT) } else { RK_STD_TYPES(7, ST_PLAIN) }
   } else {
-    if (mode == ST_PREC) { RK_STD_TYPES(19, ST_PREC) } else { RK_STD_TYPES(19, ST_PLAIN) }
+    if (mode == ST_PREC) { RK_STD_TYPES(19, ST_PREC) } else if (mode == ST_LEFT) { RK_STD_TYPES(19, ST_LEFT) } else { RK_STD_TYPES(19, ST_PLAIN) }
   }
 #undef RK_STD_TYPES
 #undef RK_STD
@@ -457,8 +463,9 @@ cudaError_t launch_round_df(int64_t n, const double* src, float2* dst, cudaStrea
   return cudaGetLastError();
 }
 
-cudaError_t launch_stencil_dd(const Dims& d, int S, bool precond, const float2* coefd, const float2* dinvd,
+cudaError_t launch_stencil_dd(const Dims& d, int S, int mode, const float2* coefd, const float2* dinvd,
                               const void* v, bool v_df, void* y, bool y_df, const int* skip, cudaStream_t st) {
+  if (mode != ST_PREC && mode != ST_PLAIN && mode != ST_LEFT) return cudaErrorInvalidValue;
   dim3 grid;
   int zchunk;
   stencil_grid(d, grid, zchunk, 4);
@@ -471,9 +478,9 @@ cudaError_t launch_stencil_dd(const Dims& d, int S, bool precond, const float2* 
   else if (y_df) RK_SDD(SS, MM, double, float2);    \
   else RK_SDD(SS, MM, double, double);
   if (S == 7) {
-    if (precond) { RK_SDD_TYPES(7, ST_PREC) } else { RK_SDD_TYPES(7, ST_PLAIN) }
+    if (mode == ST_PREC) { RK_SDD_TYPES(7, ST_PREC) } else if (mode == ST_LEFT) { RK_SDD_TYPES(7, ST_LEFT) } else { RK_SDD_TYPES(7, ST_PLAIN) }
   } else {
-    if (precond) { RK_SDD_TYPES(19, ST_PREC) } else { RK_SDD_TYPES(19, ST_PLAIN) }
+    if (mode == ST_PREC) { RK_SDD_TYPES(19, ST_PREC) } else if (mode == ST_LEFT) { RK_SDD_TYPES(19, ST_LEFT) } else { RK_SDD_TYPES(19, ST_PLAIN) }
   }
 #undef RK_SDD_TYPES
 #undef RK_SDD

@@ -41,7 +41,7 @@ class rk_solve_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("m", ctypes.c_int32), ("k", ctypes.c_int32),
                 ("max_matvec", ctypes.c_int32), ("hybrid_switch", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("update_recycle", ctypes.c_int32), ("hybrid_refresh", ctypes.c_int32),
-                ("hybrid_fallback", ctypes.c_int32)]
+                ("hybrid_fallback", ctypes.c_int32), ("precond_side", ctypes.c_int32)]
 
 
 class rk_solve_info(ctypes.Structure):

@@ -111,7 +111,7 @@ def test_pencil_with_near_zero_eigenvalues(ctx):
     pens = []
     orig = K.harmonic_ritz_update
 
-    def hook(op_, U, C, V, B, H, jj, k, return_theta=False):
+    def hook(op_, U, C, V, B, H, jj, k, return_theta=False, left=False):
         kc = 0 if U is None else U.shape[1]
         nn = kc + jj
         G = np.zeros((nn + 1, nn))
@@ -125,7 +125,7 @@ def test_pencil_with_near_zero_eigenvalues(ctx):
         G[kc:, kc:] = H[: jj + 1, :jj]
         F[kc:kc + jj, kc:] = np.eye(jj)
         pens.append((G, F))
-        return orig(op_, U, C, V, B, H, jj, k, return_theta)
+        return orig(op_, U, C, V, B, H, jj, k, return_theta, left)
 
     K.harmonic_ritz_update = hook
     try:

@@ -406,6 +406,110 @@ def test_hybrid_variants_match_oracle(ctx, refresh, fallback):
         assert fell_back >= 1
 
 
+# ---------------------------------------------------------------- left preconditioning (Sec. 2.1)
+@pytest.mark.parametrize("S", [7, 19])
+@pytest.mark.parametrize("dims,per", GRIDS[:4])
+def test_left_operator_bit_exact(ctx, S, dims, per):
+    """M^{-1}(A v) (the product, then one rounded multiplication) bit for bit."""
+    g = Grid(*dims, per)
+    coef = random_operator(g, S, np.random.default_rng(hash((S, dims, 9)) % 2**32))
+    prob = gpu_problem(ctx, g, coef)
+    op = oracle.Stencil(g, coef)
+    v = np.random.default_rng(4).standard_normal(g.n)
+    assert np.array_equal(prob.apply(t(v), left=True).cpu().numpy(), op.apply_left(v))
+
+
+def check_left_solve(op, b, xg, info, xo, io, tol, slack, kap):
+    """Left preconditioning: the preconditioned residual meets tol relative
+    to ||M^{-1} b||; relres_true is ||b - A x|| / ||b|| (to the rounding of
+    forming it); x within the kappa bound of the oracle's; products within
+    slack."""
+    rp = np.linalg.norm(op.residual_left(b, xg)) / np.linalg.norm(op.minv(b))
+    assert rp <= tol * 1.0000001 and info["status"] == 0, (rp, info)
+    rel = np.linalg.norm(op.residual(b, xg)) / np.linalg.norm(b)
+    assert abs(rel - info["relres_true"]) <= 1e-6 * rel + 1e-15
+    xtol = max(1e-6, 2.0 * kap * tol)
+    assert np.linalg.norm(xg - xo) <= xtol * np.linalg.norm(xo)
+    assert abs(info["matvecs"] - io["matvecs"]) <= slack, (info["matvecs"], io["matvecs"], slack)
+
+
+@pytest.mark.parametrize("cfg_id,size,m", [(1, 12, 30), (2, 12, 40)])
+def test_left_gmres_parity(ctx, cfg_id, size, m):
+    cfg = make_config(cfg_id, size=size)
+    prob = gpu_problem(ctx, cfg.grid, cfg.coef)
+    op = oracle.Stencil(cfg.grid, cfg.coef)
+    b = cfg.rhs(0)
+    x, info = prob.solve(t(b), tol=1e-8, m=m, k=0, mode="GMRES", max_matvec=8000, precond_side="left")
+    xo, io = oracle.gmres(op, b, tol=1e-8, m=m, max_matvec=8000, left=True)
+    slack = max(2, int(0.25 * io["matvecs"])) if io["cycles"] > 5 else 2
+    check_left_solve(op, b, x.cpu().numpy(), info, xo, io, 1e-8, slack, kappa(cfg.grid, cfg.coef))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df"])
+@pytest.mark.parametrize("cfg_id,size,m,k,steps", [(1, 12, 30, 10, 4), (2, 12, 40, 20, 3)])
+def test_left_rgcrot_sequence_parity(ctx, cfg_id, size, m, k, steps, precision):
+    """Left-preconditioned rGCROT over a sequence, the recycle pair carried:
+    the solve bars above, and M^{-1} A U = C, C^T C = I for the carried pair."""
+    cfg = make_config(cfg_id, size=size)
+    prob = gpu_problem(ctx, cfg.grid, cfg.coef)
+    op = oracle.Stencil(cfg.grid, cfg.coef)
+    kap = kappa(cfg.grid, cfg.coef)
+    seq = oracle.RecyclingSequence(op, mode="rGCROT", m=m, k=k, tol=1e-8, max_matvec=5000, left=True)
+    for s in range(steps):
+        b = cfg.rhs(s)
+        x, info = prob.solve(t(b), tol=1e-8, m=m, k=k, mode="rGCROT", max_matvec=5000, precond_side="left",
+                             precision=precision)
+        U0, C0 = seq.U, seq.C
+        xo, io = seq.solve(b)
+        slack = 2
+        if io["cycles"] > 3:
+            run = lambda bb: oracle.rgcrot(op, bb, tol=1e-8, m=m, k=k, U=U0, C=C0, max_matvec=5000, left=True)[3]
+            slack, _ = mv_slack(run, b, io["matvecs"])
+        check_left_solve(op, b, x.cpu().numpy(), info, xo, io, 1e-8, slack, kap)
+        U, C = prob.get_recycle()
+        U, C = U.cpu().numpy().T, C.cpu().numpy().T
+        BU = np.stack([op.apply_left(u) for u in U.T], axis=1)
+        nb = np.abs(op.minv(np.ones(op.n))).max() * np.abs(cfg.coef).sum(axis=0).max()
+        assert np.linalg.norm(BU - C) <= 1e-10 * np.linalg.norm(C) * max(1.0, nb)
+        assert np.linalg.norm(C.T @ C - np.eye(C.shape[1])) <= 1e-11
+
+
+def test_left_hybrid_converts_the_space(ctx):
+    """Hybrid with left-preconditioned rGCROT for the first solves and
+    right-preconditioned rBiCGStab after the switch (Sec. 2.1): the carried
+    pair is re-formed for the right side at the switch (A U = C afterwards),
+    and every solve meets its own criterion as the oracle's does."""
+    n = (14, 12, 10)
+    solid, _ = sphere_pack(n, 2.5, 0.3, rng_for(77, 3), max_attempts=20000)
+    grid, coef = porous_skew_19pt(n, np.where(solid, 1e-4, 1.0), 15.0)
+    prob = gpu_problem(ctx, grid, coef)
+    op = oracle.Stencil(grid, coef)
+    kap = kappa(grid, coef)
+    seq = oracle.RecyclingSequence(op, mode="hybrid", m=20, k=10, tol=1e-8, hybrid_switch=2, max_matvec=4000,
+                                   left=True)
+    base = np.random.default_rng(5).standard_normal(grid.n)
+    for s in range(4):
+        b = base + 0.05 * s * np.random.default_rng(100 + s).standard_normal(grid.n)
+        x, info = prob.solve(t(b), tol=1e-8, m=20, k=10, mode="hybrid", hybrid_switch=2, max_matvec=4000,
+                             precond_side="left")
+        xo, io = seq.solve(b)
+        xg = x.cpu().numpy()
+        assert info["mode_used"] == (1 if s < 2 else 2) and info["status"] == 0, (s, info)
+        if s < 2:
+            rp = np.linalg.norm(op.residual_left(b, xg)) / np.linalg.norm(op.minv(b))
+            assert rp <= 1e-8 * 1.0000001
+        else:
+            assert np.linalg.norm(op.residual(b, xg)) <= 1e-8 * np.linalg.norm(b) * 1.0000001
+        assert np.linalg.norm(xg - xo) <= max(1e-6, 2.0 * kap * 1e-8) * np.linalg.norm(xo)
+    U, C = prob.get_recycle()
+    U, C = U.cpu().numpy().T, C.cpu().numpy().T
+    AU = np.stack([op.apply(u) for u in U.T], axis=1)
+    assert np.linalg.norm(AU - C) <= 1e-10 * np.linalg.norm(C) * np.abs(coef).max()
+    qa = np.linalg.qr(U)[0]
+    qb = np.linalg.qr(seq.U)[0]
+    assert np.linalg.norm(qb - qa @ (qa.T @ qb), 2) <= 1e-6
+
+
 def test_mixed_precision_sequence(ctx):
     """Mixed precision (A11): FP32 inner operator inside the FP64/double-float
     rGCROT recurrence with b - A x recomputed in FP64 every cycle. Every step

@@ -310,3 +310,62 @@ def test_hybrid_fallback_switches_back():
     # fallback at solve 2 starts a phase: solve 3 is rGCROT, solve 4 rBiCGStab (falling back again)
     assert modes[:4] == ["rGCROT", "rGCROT", "rGCROT", "rGCROT"]
     assert seq.base in (2, 4)
+
+
+# ---------------------------------------------------------------- left preconditioning (Sec. 2.1)
+@pytest.mark.parametrize("name,grid,coef,b", PROBS, ids=[p[0] for p in PROBS])
+@pytest.mark.parametrize("mode", ["GMRES", "rGCROT"])
+def test_left_preconditioned_solvers_reach_dense_lu(name, grid, coef, b, mode):
+    """GMRES(m) and rGCROT(m,k) preconditioned from the left reach the dense
+    LU solution: the preconditioned residual meets the tolerance relative to
+    ||M^{-1} b||, and x is within kappa times the reached relative residual."""
+    op = Stencil(grid, coef)
+    A = dense_matrix(grid, coef)
+    Minv = np.diag(1.0 / coef[0])
+    xs = sla.solve(A, b)
+    tol = 1e-12
+    if mode == "GMRES":
+        x, info = gmres(op, b, tol=tol, m=12, max_matvec=5000, left=True)
+    else:
+        x, U, C, info = rgcrot(op, b, tol=tol, m=12, k=6, max_matvec=5000, left=True)
+    assert info["status"] == oracle.OK
+    assert np.linalg.norm(Minv @ (b - A @ x)) <= tol * np.linalg.norm(Minv @ b) * (1 + 1e-9)
+    rel = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+    # relres_true is ||b - A x|| / ||b|| from the stencil residual: equal up
+    # to the rounding of forming b - A x in two summation orders
+    rounding = 64 * 2.0 ** -53 * np.linalg.norm(np.abs(A) @ np.abs(x)) / np.linalg.norm(b)
+    assert abs(rel - info["relres_true"]) <= rounding
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= max(1e-9, 10 * np.linalg.cond(Minv @ A) * tol)
+
+
+@pytest.mark.parametrize("name,grid,coef,b", PROBS, ids=[p[0] for p in PROBS])
+def test_left_rgcrot_k0_is_left_gmres(name, grid, coef, b):
+    """Without a recycle space, left-preconditioned Algorithm 3 is
+    left-preconditioned Algorithm 1, bit for bit."""
+    op = Stencil(grid, coef)
+    x1, i1 = gmres(op, b, tol=1e-10, m=7, left=True)
+    x2, U, C, i2 = rgcrot(op, b, tol=1e-10, m=7, k=0, left=True)
+    assert np.array_equal(x1, x2) and i1["matvecs"] == i2["matvecs"] and U is None
+
+
+@pytest.mark.parametrize("name,grid,coef,b", PROBS[:3], ids=[p[0] for p in PROBS[:3]])
+def test_left_recycle_invariants_and_side_switch(name, grid, coef, b):
+    """After left-preconditioned rGCROT: M^{-1} A U = C and C^T C = I (dense
+    matrices). A right-preconditioned solve of the sequence re-forms C from
+    U: then A U = C, range(U) unchanged."""
+    op = Stencil(grid, coef)
+    A = dense_matrix(grid, coef)
+    Minv = np.diag(1.0 / coef[0])
+    seq = oracle.RecyclingSequence(op, mode="rGCROT", m=6, k=4, tol=1e-10, left=True)
+    seq.solve(b)
+    U, C = seq.U, seq.C
+    nB = np.linalg.norm(Minv @ A, 2)
+    assert np.linalg.norm(Minv @ A @ U - C) <= 1e-10 * nB * np.linalg.norm(U)
+    assert np.linalg.norm(C.T @ C - np.eye(C.shape[1])) <= 1e-12
+    seq.left = False
+    seq._side(False)
+    assert np.linalg.norm(A @ seq.U - seq.C) <= 1e-10 * np.linalg.norm(A, 2) * np.linalg.norm(seq.U)
+    assert np.linalg.norm(seq.C.T @ seq.C - np.eye(C.shape[1])) <= 1e-12
+    qa = np.linalg.qr(U)[0]
+    qb = np.linalg.qr(seq.U)[0]
+    assert np.linalg.norm(qb - qa @ (qa.T @ qb), 2) <= 1e-10
