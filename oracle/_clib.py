@@ -45,6 +45,9 @@ def lib():
             L.oracle_apply_prec_f32.argtypes = [i64, i64, i64, p, ctypes.c_int, p, p, p, p]
             L.oracle_jacobi_inverse.restype = None
             L.oracle_jacobi_inverse.argtypes = [i64, p, p]
+            L.oracle_schwarz_jacobi.restype = None
+            L.oracle_schwarz_jacobi.argtypes = [i64, i64, i64, p, ctypes.c_int, p, p, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, p, p]
             _lib = L
     return _lib
 
@@ -104,6 +107,24 @@ class Stencil:
     def minv(self, v):
         """M^{-1} v with M = diag(A): one rounding per element."""
         return self.dinv * v
+
+    # the "Jacobi preconditioner" of Sec. 2.1 (see oracle_schwarz_jacobi)
+    SCHWARZ_BOX = (16, 8, 8)
+    SCHWARZ_OVERLAP = 1
+    SCHWARZ_SWEEPS = 5
+    SCHWARZ_OMEGA = 2.0 / 3.0
+
+    def schwarz(self, r, box=None, overlap=None, sweeps=None, omega=None):
+        """z = M^{-1} r for the sub-domain damped-Jacobi preconditioner
+        (parameters default to the class constants)."""
+        r = _c64(r)
+        z = np.empty(self.n)
+        bx, by, bz = self.SCHWARZ_BOX if box is None else box
+        lib().oracle_schwarz_jacobi(*self._dims(), _ptr(self.dinv), bx, by, bz,
+                                    self.SCHWARZ_OVERLAP if overlap is None else overlap,
+                                    self.SCHWARZ_SWEEPS if sweeps is None else sweeps,
+                                    self.SCHWARZ_OMEGA if omega is None else omega, _ptr(r), _ptr(z))
+        return z
 
     def apply_left(self, v):
         """M^{-1} (A v) (left preconditioning): the product, then one rounding per element."""

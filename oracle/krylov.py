@@ -52,6 +52,30 @@ def _givens(a, b):
     return a / r, b / r, r
 
 
+class _Prec:
+    """The preconditioner M of a solve: "jacobi" = diag(A) (point Jacobi,
+    Sec. 2.1 reading R5) or "schwarz" = the sub-domain damped-Jacobi
+    preconditioner of Sec. 2.1 (Stencil.schwarz). left(v) = M^{-1} A v,
+    right(v) = A M^{-1} v."""
+
+    def __init__(self, op, kind="jacobi"):
+        if kind not in ("jacobi", "schwarz"):
+            raise ValueError(kind)
+        self.op, self.kind = op, kind
+
+    def minv(self, v):
+        return self.op.minv(v) if self.kind == "jacobi" else self.op.schwarz(v)
+
+    def left(self, v):
+        return self.op.apply_left(v) if self.kind == "jacobi" else self.op.schwarz(self.op.apply(v))
+
+    def right(self, v):
+        return self.op.apply_prec(v) if self.kind == "jacobi" else self.op.apply(self.op.schwarz(v))
+
+    def resid_left(self, b, x):
+        return self.op.residual_left(b, x) if self.kind == "jacobi" else self.op.schwarz(self.op.residual(b, x))
+
+
 class _LS:
     """Progressive Givens QR of the (j+1) x j Hessenberg matrix and rotated rhs
     (Algorithms 1 and 3: y = argmin || e_1 rho - H y ||)."""
@@ -89,7 +113,7 @@ def _op(grid_or_op, coef=None):
 
 
 # --------------------------------------------------------------------------- GMRES(m)
-def gmres(op, b, x0=None, tol=1e-8, m=30, max_matvec=2000, keep_cycle=False, left=False):
+def gmres(op, b, x0=None, tol=1e-8, m=30, max_matvec=2000, keep_cycle=False, left=False, prec="jacobi"):
     """GMRES(m), Algorithm 1, right-preconditioned by M = diag(A).
 
     Arnoldi with modified Gram-Schmidt on A M^{-1}; solution
@@ -97,15 +121,19 @@ def gmres(op, b, x0=None, tol=1e-8, m=30, max_matvec=2000, keep_cycle=False, lef
     With ``left``, preconditioned from the left as Sec. 2.1 states it:
     Arnoldi on M^{-1} A, x <- x + V_j y, and the convergence test on
     ||M^{-1}(b - A x)|| <= tol ||M^{-1} b||; info's relres_true is still
-    ||b - A x|| / ||b||."""
+    ||b - A x|| / ||b||. ``prec``: "jacobi" (point Jacobi) or "schwarz" (the
+    sub-domain preconditioner of Sec. 2.1, left side only)."""
+    P = _Prec(op, prec)
+    if prec != "jacobi" and not left:
+        raise ValueError("the sub-domain preconditioner is applied from the left for GMRES")
     n = op.n
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=float)
     bnorm_true = float(np.linalg.norm(b))
     if bnorm_true == 0.0:
         return np.zeros(n), _info(OK, 0, 0, 0, 0.0, 0.0, [])
-    bnorm = float(np.linalg.norm(op.minv(b))) if left else bnorm_true
-    resid = op.residual_left if left else op.residual
-    prod = op.apply_left if left else op.apply_prec
+    bnorm = float(np.linalg.norm(P.minv(b))) if left else bnorm_true
+    resid = P.resid_left if left else op.residual
+    prod = P.left if left else op.apply_prec
     r = resid(b, x)
     rho = float(np.linalg.norm(r))
     matvecs = cycles = 0
@@ -150,10 +178,11 @@ def gmres(op, b, x0=None, tol=1e-8, m=30, max_matvec=2000, keep_cycle=False, lef
 
 
 # --------------------------------------------------------------------------- recycle space helpers
-def recycle_from_u(op, U, left=False):
+def recycle_from_u(op, U, left=False, prec="jacobi"):
     """Forming C from U (Algorithms 3 and 4): C~ = A U, thin QR C~ = C R; return (U R^{-1}, C) so A U = C.
     With ``left``: C~ = M^{-1} A U, so M^{-1} A U = C."""
-    Ct = np.stack([(op.apply_left(u) if left else op.apply(u)) for u in U.T], axis=1)
+    P = _Prec(op, prec)
+    Ct = np.stack([(P.left(u) if left else op.apply(u)) for u in U.T], axis=1)
     Q, R = np.linalg.qr(Ct)
     Unew = sla.solve_triangular(R, U.T, trans="T", lower=False).T  # U R^{-1}
     return Unew, Q
@@ -230,27 +259,31 @@ def harmonic_ritz_update(op, U, C, V, B, H, jj, k, return_theta=False, left=Fals
 
 # --------------------------------------------------------------------------- rGCROT(m,k)
 def rgcrot(op, b, x0=None, tol=1e-8, m=30, k=10, U=None, C=None, update=True, max_matvec=2000,
-           keep_cycle=False, left=False):
+           keep_cycle=False, left=False, prec="jacobi"):
     """rGCROT(m,k), Algorithm 3, right-preconditioned by M = diag(A).
 
     U, C are N x k_cur arrays (or None) with A U = C, C^T C = I; if only U is
     given, C is formed from it (recycle_from_u). Returns (x, U, C, info).
     With ``left`` (Sec. 2.1's side): Arnoldi on M^{-1} A, M^{-1} A U = C,
     x <- x + V_j y + U z, and the convergence test on ||M^{-1}(b - A x)||
-    relative to ||M^{-1} b||; info's relres_true is ||b - A x|| / ||b||."""
+    relative to ||M^{-1} b||; info's relres_true is ||b - A x|| / ||b||.
+    ``prec``: "jacobi" or "schwarz" (the latter from the left only)."""
+    P = _Prec(op, prec)
+    if prec != "jacobi" and not left:
+        raise ValueError("the sub-domain preconditioner is applied from the left for rGCROT")
     n = op.n
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=float)
     bnorm_true = float(np.linalg.norm(b))
     if U is not None and U.shape[1] == 0:
         U = C = None
     if U is not None and C is None:
-        U, C = recycle_from_u(op, U, left)
+        U, C = recycle_from_u(op, U, left, prec)
     kc = 0 if U is None else U.shape[1]
     if bnorm_true == 0.0:
         return np.zeros(n), U, C, _info(OK, 0, 0, 0, 0.0, 0.0, [], kc)
-    bnorm = float(np.linalg.norm(op.minv(b))) if left else bnorm_true
-    resid = op.residual_left if left else op.residual
-    prod = op.apply_left if left else op.apply_prec
+    bnorm = float(np.linalg.norm(P.minv(b))) if left else bnorm_true
+    resid = P.resid_left if left else op.residual
+    prod = P.left if left else op.apply_prec
     rhat = resid(b, x)                            # initial residual
     if kc:
         xi = C.T @ rhat                           # projection onto C
@@ -322,9 +355,11 @@ def rgcrot(op, b, x0=None, tol=1e-8, m=30, k=10, U=None, C=None, update=True, ma
 
 
 # --------------------------------------------------------------------------- BiCGStab
-def bicgstab(op, b, x0=None, tol=1e-8, max_matvec=2000):
+def bicgstab(op, b, x0=None, tol=1e-8, max_matvec=2000, prec="jacobi"):
     """BiCGStab, Algorithm 2, right-preconditioned: the iterates p, s live in
-    the preconditioned space and x = x_0 + M^{-1} (sum of alpha p + omega s)."""
+    the preconditioned space and x = x_0 + M^{-1} (sum of alpha p + omega s).
+    ``prec``: "jacobi" or "schwarz" (Sec. 2.1's sub-domain preconditioner)."""
+    P = _Prec(op, prec)
     n = op.n
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=float)
     bnorm = float(np.linalg.norm(b))
@@ -348,7 +383,7 @@ def bicgstab(op, b, x0=None, tol=1e-8, max_matvec=2000):
         else:
             beta = (rho / rho_old) * (alpha / omega)
             p = r + beta * (p - omega * v)
-        v = op.apply_prec(p)                            # v = A M^{-1} p
+        v = P.right(p)                                  # v = A M^{-1} p
         matvecs += 1
         alpha = rho / (rt @ v)                          # alpha
         s = r - alpha * v
@@ -358,7 +393,7 @@ def bicgstab(op, b, x0=None, tol=1e-8, max_matvec=2000):
             it += 1
             hist.append(np.linalg.norm(r) / bnorm)
             break
-        t = op.apply_prec(s)                            # t = A M^{-1} s
+        t = P.right(s)                                  # t = A M^{-1} s
         matvecs += 1
         tt = t @ t
         if tt == 0.0:
@@ -373,7 +408,7 @@ def bicgstab(op, b, x0=None, tol=1e-8, max_matvec=2000):
         if omega == 0.0:
             status = BREAKDOWN
             break
-    x = x + op.minv(xt)
+    x = x + P.minv(xt)
     rtrue = op.residual(b, x)
     rel = float(np.linalg.norm(rtrue)) / bnorm
     if status != BREAKDOWN:
@@ -382,9 +417,10 @@ def bicgstab(op, b, x0=None, tol=1e-8, max_matvec=2000):
 
 
 # --------------------------------------------------------------------------- rBiCGStab
-def _rbicgstab_pass(op, b, x, tol, U, C, max_matvec, bnorm, callback=None):
+def _rbicgstab_pass(op, b, x, tol, U, C, max_matvec, bnorm, callback=None, prec="jacobi"):
     """One run of Algorithm 4 from x_hat = x; returns (x, matvecs, its,
     breakdown, updated-residual norm, history)."""
+    P = _Prec(op, prec)
     n = op.n
     kc = 0 if C is None else C.shape[1]
     rhat = op.residual(b, x)                            # initial residual
@@ -412,7 +448,7 @@ def _rbicgstab_pass(op, b, x, tol, U, C, max_matvec, bnorm, callback=None):
         else:
             beta = (rho / rho_old) * (alpha / omega)
             p = r + beta * (p - omega * v)
-        v = op.apply_prec(p)                            # v = A M^{-1} p
+        v = P.right(p)                                  # v = A M^{-1} p
         matvecs += 1
         if kc:
             eta1 = C.T @ v                              # eta1 = C^T v
@@ -431,7 +467,7 @@ def _rbicgstab_pass(op, b, x, tol, U, C, max_matvec, bnorm, callback=None):
             it += 1
             hist.append(np.linalg.norm(r) / bnorm)
             break
-        t = op.apply_prec(s)                            # t = A M^{-1} s
+        t = P.right(s)                                  # t = A M^{-1} s
         matvecs += 1
         if kc:
             eta2 = C.T @ t                              # eta2 = C^T t
@@ -455,13 +491,14 @@ def _rbicgstab_pass(op, b, x, tol, U, C, max_matvec, bnorm, callback=None):
             break
     if callback is not None:
         callback(r)
-    x = x + op.minv(xt)                                 # x = x_hat + M^{-1} x~, then the postponed U part
+    x = x + P.minv(xt)                                  # x = x_hat + M^{-1} x~, then the postponed U part
     if kc:
         x = x - U @ xi
     return x, matvecs, it, brk, float(np.linalg.norm(r)), hist
 
 
-def rbicgstab(op, b, x0=None, tol=1e-8, U=None, C=None, max_matvec=2000, max_restarts=3, callback=None):
+def rbicgstab(op, b, x0=None, tol=1e-8, U=None, C=None, max_matvec=2000, max_restarts=3, callback=None,
+              prec="jacobi"):
     """rBiCGStab with one recycle space, Algorithm 4, right-preconditioned.
 
     When the updated residual meets the tolerance the postponed U update is
@@ -483,7 +520,7 @@ def rbicgstab(op, b, x0=None, tol=1e-8, U=None, C=None, max_matvec=2000, max_res
     status = NOT_CONVERGED
     upd = np.inf
     while True:
-        x, mv, it, brk, upd, h = _rbicgstab_pass(op, b, x, tol, U, C, max_matvec - matvecs, bnorm, callback)
+        x, mv, it, brk, upd, h = _rbicgstab_pass(op, b, x, tol, U, C, max_matvec - matvecs, bnorm, callback, prec)
         matvecs += mv
         its += it
         hist += h
@@ -522,8 +559,9 @@ class RecyclingSequence:
     for its operator (recycle_from_u)."""
 
     def __init__(self, op, mode="rGCROT", m=30, k=10, tol=1e-8, hybrid_switch=5, max_matvec=2000, refresh=0,
-                 fallback=0, left=False):
+                 fallback=0, left=False, prec="jacobi"):
         self.op, self.mode, self.m, self.k, self.tol = op, mode, m, k, tol
+        self.prec = prec
         self.hybrid_switch, self.max_matvec = hybrid_switch, max_matvec
         self.refresh, self.fallback, self.left = refresh, fallback, left
         self.U = self.C = None
@@ -533,7 +571,7 @@ class RecyclingSequence:
 
     def _side(self, left):
         if self.U is not None and self.U.shape[1] > 0 and self.side != left:
-            self.U, self.C = recycle_from_u(self.op, self.U, left)
+            self.U, self.C = recycle_from_u(self.op, self.U, left, self.prec)
         self.side = left
 
     def solve(self, b, x0=None):
@@ -546,12 +584,13 @@ class RecyclingSequence:
             if mode == "rBiCGStab" and self.fallback > 0:
                 cap = min(self.fallback, self.max_matvec)
                 self._side(False)
-                x, info = rbicgstab(self.op, b, x0, self.tol, self.U, self.C, cap)
+                x, info = rbicgstab(self.op, b, x0, self.tol, self.U, self.C, cap, prec=self.prec)
                 if info["status"] != OK and info["matvecs"] < self.max_matvec:
                     used = info["matvecs"]
                     self._side(self.left)
                     x, self.U, self.C, ig = rgcrot(self.op, b, x, self.tol, self.m, self.k, self.U, self.C,
-                                                   update=True, max_matvec=self.max_matvec - used, left=self.left)
+                                                   update=True, max_matvec=self.max_matvec - used, left=self.left,
+                                                   prec=self.prec)
                     ig["matvecs"] += used
                     ig["restarts"] += info["restarts"]
                     info = ig
@@ -561,16 +600,16 @@ class RecyclingSequence:
                 self.t += 1
                 return x, info
         if mode == "GMRES":
-            x, info = gmres(self.op, b, x0, self.tol, self.m, self.max_matvec, left=self.left)
+            x, info = gmres(self.op, b, x0, self.tol, self.m, self.max_matvec, left=self.left, prec=self.prec)
         elif mode == "rGCROT":
             self._side(self.left)
             x, self.U, self.C, info = rgcrot(self.op, b, x0, self.tol, self.m, self.k, self.U, self.C,
-                                             update=True, max_matvec=self.max_matvec, left=self.left)
+                                             update=True, max_matvec=self.max_matvec, left=self.left, prec=self.prec)
         elif mode == "BiCGStab":
-            x, info = bicgstab(self.op, b, x0, self.tol, self.max_matvec)
+            x, info = bicgstab(self.op, b, x0, self.tol, self.max_matvec, prec=self.prec)
         elif mode == "rBiCGStab":
             self._side(False)
-            x, info = rbicgstab(self.op, b, x0, self.tol, self.U, self.C, self.max_matvec)
+            x, info = rbicgstab(self.op, b, x0, self.tol, self.U, self.C, self.max_matvec, prec=self.prec)
         else:
             raise ValueError(mode)
         info["mode"] = mode

@@ -22,6 +22,7 @@
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 static const int OFF[19][3] = {
     {0, 0, 0},
@@ -116,4 +117,85 @@ void oracle_residual(int64_t nx, int64_t ny, int64_t nz, const uint8_t* per, int
   apply_core(nx, ny, nz, per, S, coef, 0, x, r);
 #pragma omp parallel for schedule(static)
   for (int64_t p = 0; p < N; ++p) r[p] = b[p] - r[p];
+}
+
+/*
+ * The "Jacobi preconditioner" of Sec. 2.1 (reading of this implementation):
+ * overlapping sub-domains solved inexactly by damped Jacobi, then one damped
+ * point-Jacobi sweep on the global problem. z = M^{-1} r:
+ *   - the grid is cut into boxes of bx x by x bz owned cells (the last box
+ *     along an axis may be smaller); each box is extended by `ov` cells on
+ *     every side (wrapping on periodic axes; cells beyond a non-periodic face
+ *     are absent). The extended cells are the local unknowns (a cell reached
+ *     twice by wrapping is two unknowns);
+ *   - local problem: A restricted to the extended cells (couplings to cells
+ *     outside the extended box dropped); `sweeps` damped Jacobi sweeps from
+ *     zero, each  s = c_0 z_e, s = fma(c_s, z_nb, s) in band order over the
+ *     present neighbours, t = r_e - s, u = dinv_e * t, z_e <- fma(omega, u, z_e);
+ *   - restriction: every cell takes the value of its own box's local solve;
+ *   - one global sweep of the same form with the full operator:
+ *     z_p <- fma(omega, dinv_p * (r_p - (A z)_p), z_p).
+ */
+void oracle_schwarz_jacobi(int64_t nx, int64_t ny, int64_t nz, const uint8_t* per, int S,
+                           const double* coef, const double* dinv, int bx, int by, int bz, int ov,
+                           int sweeps, double omega, const double* r, double* z) {
+  const int64_t N = nx * ny * nz;
+  const int64_t nbx = (nx + bx - 1) / bx, nby = (ny + by - 1) / by, nbz = (nz + bz - 1) / bz;
+#pragma omp parallel for schedule(dynamic)
+  for (int64_t box = 0; box < nbx * nby * nbz; ++box) {
+    const int64_t ib = box % nbx, jb = (box / nbx) % nby, kb = box / (nbx * nby);
+    const int64_t x0 = ib * bx, y0 = jb * by, z0 = kb * bz;
+    const int64_t x1 = x0 + bx < nx ? x0 + bx : nx, y1 = y0 + by < ny ? y0 + by : ny, z1 = z0 + bz < nz ? z0 + bz : nz;
+    const int64_t ex = (x1 - x0) + 2 * ov, ey = (y1 - y0) + 2 * ov, ez = (z1 - z0) + 2 * ov;
+    const int64_t ne = ex * ey * ez;
+    int64_t* gidx = (int64_t*)malloc(sizeof(int64_t) * ne);
+    double* za = (double*)calloc(ne, sizeof(double));
+    double* zb = (double*)calloc(ne, sizeof(double));
+    for (int64_t c = 0; c < ez; ++c)
+      for (int64_t b = 0; b < ey; ++b)
+        for (int64_t a = 0; a < ex; ++a) {
+          const int64_t gi = wrap(x0 - ov + a, nx, per[0]), gj = wrap(y0 - ov + b, ny, per[1]),
+                        gk = wrap(z0 - ov + c, nz, per[2]);
+          gidx[a + ex * (b + ey * c)] = (gi < 0 || gj < 0 || gk < 0) ? -1 : gi + nx * (gj + ny * gk);
+        }
+    for (int sw = 0; sw < sweeps; ++sw) {
+      for (int64_t c = 0; c < ez; ++c)
+        for (int64_t b = 0; b < ey; ++b)
+          for (int64_t a = 0; a < ex; ++a) {
+            const int64_t e = a + ex * (b + ey * c);
+            const int64_t p = gidx[e];
+            if (p < 0) continue;
+            double s = coef[p] * za[e];
+            for (int t = 1; t < S; ++t) {
+              const int64_t aa = a + OFF[t][0], bb = b + OFF[t][1], cc = c + OFF[t][2];
+              if (aa < 0 || aa >= ex || bb < 0 || bb >= ey || cc < 0 || cc >= ez) continue;
+              const int64_t q = aa + ex * (bb + ey * cc);
+              if (gidx[q] < 0) continue;
+              s = fma(coef[(int64_t)t * N + p], za[q], s);
+            }
+            const double u = dinv[p] * (r[p] - s);
+            zb[e] = fma(omega, u, za[e]);
+          }
+      double* tmp = za;
+      za = zb;
+      zb = tmp;
+    }
+    for (int64_t k = z0; k < z1; ++k)
+      for (int64_t j = y0; j < y1; ++j)
+        for (int64_t i = x0; i < x1; ++i)
+          z[i + nx * (j + ny * k)] = za[(i - x0 + ov) + ex * ((j - y0 + ov) + ey * (k - z0 + ov))];
+    free(gidx);
+    free(za);
+    free(zb);
+  }
+  /* the global point-Jacobi sweep */
+  double* az = (double*)malloc(sizeof(double) * N);
+  apply_core(nx, ny, nz, per, S, coef, 0, z, az);
+#pragma omp parallel for schedule(static)
+  for (int64_t p = 0; p < N; ++p) {
+    const double u = dinv[p] * (r[p] - az[p]);
+    az[p] = fma(omega, u, z[p]);
+  }
+  for (int64_t p = 0; p < N; ++p) z[p] = az[p];
+  free(az);
 }

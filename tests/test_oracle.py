@@ -369,3 +369,105 @@ def test_left_recycle_invariants_and_side_switch(name, grid, coef, b):
     qa = np.linalg.qr(U)[0]
     qb = np.linalg.qr(seq.U)[0]
     assert np.linalg.norm(qb - qa @ (qa.T @ qb), 2) <= 1e-10
+
+
+# ---------------------------------------------------------------- the sub-domain Jacobi preconditioner (Sec. 2.1)
+def _schwarz_dense(grid, coef, box, ov, sweeps, omega):
+    """The preconditioner as an explicit matrix, from its definition with
+    dense algebra: per box, the extended index set, A restricted to it, the
+    damped Jacobi polynomial sum_{t<sweeps} (I - w D^-1 A_b)^t w D^-1; owned
+    rows kept (restriction); then the global sweep
+    M^-1 = Z + w D^-1 (I - A Z)."""
+    A = dense_matrix(grid, coef)
+    n = grid.n
+    d = np.diag(A).copy()
+    nx, ny, nz = grid.nx, grid.ny, grid.nz
+    per = grid.periodic
+    def wrapc(c, m, p):
+        if 0 <= c < m:
+            return c
+        return (c % m) if p else -1
+    Z = np.zeros((n, n))
+    bx, by, bz = box
+    for kb in range(0, nz, bz):
+        for jb in range(0, ny, by):
+            for ib in range(0, nx, bx):
+                x1, y1, z1 = min(ib + bx, nx), min(jb + by, ny), min(kb + bz, nz)
+                ext = []
+                for c in range(kb - ov, z1 + ov):
+                    for b_ in range(jb - ov, y1 + ov):
+                        for a in range(ib - ov, x1 + ov):
+                            g = (wrapc(a, nx, per[0]), wrapc(b_, ny, per[1]), wrapc(c, nz, per[2]))
+                            ext.append(None if min(g) < 0 else g[0] + nx * (g[1] + ny * g[2]))
+                ex, ey = (x1 - ib) + 2 * ov, (y1 - jb) + 2 * ov
+                loc = [(e, gidx) for e, gidx in enumerate(ext) if gidx is not None]
+                m_ = len(loc)
+                Ab = np.zeros((m_, m_))
+                pos = {e: t for t, (e, _) in enumerate(loc)}
+                for t, (e, gp) in enumerate(loc):
+                    a, rem = e % ex, e // ex
+                    b_, c = rem % ey, rem // ey
+                    for t2, (e2, gq) in enumerate(loc):
+                        a2, rem2 = e2 % ex, e2 // ex
+                        b2, c2 = rem2 % ey, rem2 // ey
+                        da, db, dc = a2 - a, b2 - b_, c2 - c
+                        if max(abs(da), abs(db), abs(dc)) > 1:
+                            continue
+                        # the band coupling cell gp to its (da, db, dc) neighbour
+                        for s_, off in enumerate(OFFSETS[:coef.shape[0]]):
+                            if off == (da, db, dc):
+                                Ab[t, t2] = coef[s_][gp]
+                dinv_b = np.array([1.0 / d[gp] for _, gp in loc])
+                J = np.eye(m_) - omega * dinv_b[:, None] * Ab
+                Pb = np.zeros((m_, m_))
+                T = np.eye(m_)
+                for _ in range(sweeps):
+                    Pb += T
+                    T = J @ T
+                Pb = Pb * (omega * dinv_b)[None, :]
+                # owned rows, columns scattered to their global cells
+                for t, (e, gp) in enumerate(loc):
+                    a, rem = e % ex, e // ex
+                    b_, c = rem % ey, rem // ey
+                    if ov <= a < ex - ov and ov <= b_ < ey - ov and ov <= c < (z1 - kb) + ov:
+                        for t2, (_, gq) in enumerate(loc):
+                            Z[gp, gq] += Pb[t, t2]
+    return Z + omega * (1.0 / d)[:, None] * (np.eye(n) - A @ Z)
+
+
+OFFSETS = [(0, 0, 0), (-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1),
+           (-1, -1, 0), (1, -1, 0), (-1, 1, 0), (1, 1, 0), (-1, 0, -1), (1, 0, -1), (-1, 0, 1), (1, 0, 1),
+           (0, -1, -1), (0, 1, -1), (0, -1, 1), (0, 1, 1)]
+
+
+@pytest.mark.parametrize("S", [7, 19])
+@pytest.mark.parametrize("per", [(False, False, False), (True, False, True)])
+def test_schwarz_preconditioner_matches_its_dense_definition(S, per):
+    """The C loops of the sub-domain preconditioner equal the matrix built
+    from its definition (dense restriction, damped-Jacobi polynomial,
+    restriction to owned cells, global sweep), column by column."""
+    g = Grid(7, 6, 5, per)
+    coef = random_operator(g, S, np.random.default_rng(S + 31), dominance=0.5)
+    op = Stencil(g, coef)
+    box, ov, sweeps, omega = (3, 4, 2), 1, 5, 2.0 / 3.0
+    Md = _schwarz_dense(g, coef, box, ov, sweeps, omega)
+    r = np.random.default_rng(3).standard_normal(g.n)
+    z = op.schwarz(r, box=box, overlap=ov, sweeps=sweeps, omega=omega)
+    assert np.allclose(z, Md @ r, rtol=1e-12, atol=1e-12 * np.abs(Md @ r).max())
+
+
+def test_schwarz_preconditioner_is_linear_and_converges_to_the_inverse():
+    """A fixed linear operator (so GMRES needs no flexible storage), and with
+    one box covering the grid and many sweeps it tends to A^{-1}."""
+    c = make_config(1, size=5)  # convection-diffusion M-matrix: damped Jacobi converges
+    g, coef = c.grid, c.coef
+    op = Stencil(g, coef)
+    rng = np.random.default_rng(6)
+    r1, r2 = rng.standard_normal(g.n), rng.standard_normal(g.n)
+    z = op.schwarz(2.0 * r1 - 3.0 * r2)
+    zl = 2.0 * op.schwarz(r1) - 3.0 * op.schwarz(r2)
+    assert np.linalg.norm(z - zl) <= 1e-13 * np.linalg.norm(z)
+    A = dense_matrix(g, coef)
+    # damped Jacobi on the whole (unsplit) problem: spectral radius 0.992 here
+    zi = op.schwarz(r1, box=(g.nx, g.ny, g.nz), overlap=1, sweeps=4000, omega=2.0 / 3.0)
+    assert np.linalg.norm(A @ zi - r1) <= 1e-12 * np.linalg.norm(r1)
