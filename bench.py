@@ -52,6 +52,9 @@ WORKLOADS = {
 # in double-float; or with those products in FP32
 DTYPES = {"fp64": "f64", "df": "f64+df64-operator", "mixed": "f64+f32-operator"}
 MV_PER_SOLVE = {"channel128": 1500.0, "channel96": 1100.0, "convdiff32": 60.0, "porous192": 400.0}
+# the same with the sub-domain preconditioner (left rGCROT)
+MV_PER_SOLVE_SD = {"channel128": 150.0, "channel96": 110.0, "convdiff32": 10.0, "porous192": 60.0}
+FP64_TFLOPS = 1.25
 
 
 def load_peaks():
@@ -147,7 +150,36 @@ def max_over_ranks(ws, v):
     return float(t.item())
 
 
-def oracle_cycle_sample(cfg, mode, m, k, cycles=2):
+def _oracle_prec(precond):
+    """The oracle's solver arguments for a --precond choice: the sub-domain
+    preconditioner is applied from the left in rGCROT (Sec. 2.1)."""
+    return dict(left=True, prec="schwarz") if precond == "subdomain" else {}
+
+
+def subdomain_flops(grid, S):
+    """FP64 flops of one launch of the sub-domain local-sweep kernel (an FMA
+    counts 2, a multiply or add 1): per grown-box cell inside the grid, the
+    first sweep from zero is omega (dinv r) (2 flops) and each later sweep
+    s = a_0 z + sum fma(a_t, z_t), u = dinv (r - s), z += omega u (2S + 3);
+    the last sweep runs on owned cells only. Grown-box cells inside the grid
+    factor per axis, so the sums over boxes are products of per-axis sums."""
+    box, ov, sweeps = (16, 8, 8), 1, 5
+    dims = (grid.nx, grid.ny, grid.nz)
+    g = []
+    for n, bsz, per in zip(dims, box, grid.periodic):
+        tot = 0
+        for c0 in range(0, n, bsz):
+            w = min(bsz, n - c0)
+            lo = ov if (per or c0 > 0) else 0
+            hi = ov if (per or c0 + w < n) else 0
+            tot += w + lo + hi
+        g.append(tot)
+    grown = g[0] * g[1] * g[2]
+    per_cell = 2 * S + 3
+    return 2.0 * grown + (sweeps - 2) * per_cell * grown + per_cell * grid.n
+
+
+def oracle_cycle_sample(cfg, mode, m, k, cycles=2, precond="jacobi"):
     """Time the CPU oracle on `cycles` rGCROT cycles of step 0 of the workload
     (the first builds the recycle space; the last is timed). Returns
     (seconds per matvec of a cycle at recycle dimension k, threads)."""
@@ -159,7 +191,8 @@ def oracle_cycle_sample(cfg, mode, m, k, cycles=2):
     per_mv = None
     for c in range(cycles):
         t0 = time.perf_counter()
-        _, U, C, info = oracle.rgcrot(op, b, tol=1e-14, m=m, k=k, U=U, C=C, max_matvec=m)
+        _, U, C, info = oracle.rgcrot(op, b, tol=1e-14, m=m, k=k, U=U, C=C, max_matvec=m,
+                                      **_oracle_prec(precond))
         dt = time.perf_counter() - t0
         per_mv = dt / max(info["matvecs"], 1)
     threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
@@ -176,18 +209,19 @@ def run_reference(args, ws, rank):
     import oracle
     op = oracle.Stencil(cfg.grid, cfg.coef)
     b = cfg.rhs(0)
-    _, U, C, _ = oracle.rgcrot(op, b, tol=1e-14, m=m, k=k, max_matvec=m)
+    pk = _oracle_prec(args.precond)
+    _, U, C, _ = oracle.rgcrot(op, b, tol=1e-14, m=m, k=k, max_matvec=m, **pk)
     for _ in range(max(args.warmup - 1, 0)):
-        _, U, C, _ = oracle.rgcrot(op, b, tol=1e-14, m=m, k=k, U=U, C=C, max_matvec=m)
+        _, U, C, _ = oracle.rgcrot(op, b, tol=1e-14, m=m, k=k, U=U, C=C, max_matvec=m, **pk)
     times = []
     t_all = time.perf_counter()
     for s in range(args.steps):
         t0 = time.perf_counter()
-        _, U, C, info = oracle.rgcrot(op, b, tol=1e-14, m=m, k=k, U=U, C=C, max_matvec=m)
+        _, U, C, info = oracle.rgcrot(op, b, tol=1e-14, m=m, k=k, U=U, C=C, max_matvec=m, **pk)
         times.append((time.perf_counter() - t0) / max(info["matvecs"], 1))
     total = time.perf_counter() - t_all
     per_mv = statistics.mean(times)
-    mv = MV_PER_SOLVE[args.workload]
+    mv = (MV_PER_SOLVE_SD if args.precond == "subdomain" else MV_PER_SOLVE)[args.workload]
     value = 1.0 / (per_mv * mv)
     threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     sample = (f"each step: one rGCROT({m},{k}) cycle ({m} matvecs, recycle dim {k}) of step 0 of {args.workload}; "
@@ -196,7 +230,7 @@ def run_reference(args, ws, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "grid": [edge] * 3, "solver": f"{mode}({m},{k})", "tol": 1e-8,
-                       "l2": "inputs larger than L2"},
+                       "precond": args.precond, "l2": "inputs larger than L2"},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -219,7 +253,8 @@ def run_ours(args, ws, rank, local):
     ctx = Context()
     prob = Problem(ctx, cfg.grid, torch.from_numpy(cfg.coef))
     x = torch.zeros(cfg.n, dtype=torch.float64, device="cuda")
-    kw = dict(tol=1e-8, m=m, k=k, mode=mode, max_matvec=args.max_matvec, hybrid_switch=5, precision=args.precision)
+    kw = dict(tol=1e-8, m=m, k=k, mode=mode, max_matvec=args.max_matvec, hybrid_switch=5, precision=args.precision,
+              precond=args.precond, precond_side="left" if args.precond == "subdomain" else "right")
     # sequence pre-roll (untimed, before warm-up): the first solves of a
     # sequence build the recycle space and may stall until it holds the
     # slowest modes; run them with a matvec cap, stopping at the first one
@@ -297,6 +332,23 @@ def run_ours(args, ws, rank, local):
     dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
     dname, d = dom
     achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
+    roof = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak,
+            "traffic": (traffic_ratio[dname] * d["bytes"] / max(d["launches"], 1)
+                        if dname in traffic_ratio else None),
+            "traffic_source": "ncu DRAM bytes / algorithmic bytes on the 96^3 channel x this run's "
+                              "algorithmic bytes per launch" if dname in traffic_ratio else None,
+            "peak_source": peak_src,
+            "launches": d["launches"], "avg_launch_us": 1000.0 * d["ms"] / max(d["launches"], 1),
+            "bytes_per_launch": d["bytes"] / max(d["launches"], 1)}
+    if dname == "subdomain_local":
+        # bound by the FP64 pipe: FP64 flops per launch over the nominal FP64
+        # rate (1.25 TFLOP/s at the 2070 MHz maximum SM clock)
+        fl = subdomain_flops(cfg.grid, cfg.S)
+        tf = fl * d["launches"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
+        roof.update({"bound": "alu", "achieved": tf, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
+                     "frac": tf / FP64_TFLOPS, "traffic": None, "traffic_source": None,
+                     "peak_source": "nominal FP64 rate", "flops_per_launch": fl})
     total_model = sum(i["model_bytes"] for i in tinfo)
     solver_gbs = total_model / (ms * 1e-3) / 1e9
     launches = int(sum(v["launches"] for v in prof.values()))
@@ -307,7 +359,7 @@ def run_ours(args, ws, rank, local):
         "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": DTYPES[args.precision], "data": "synthetic",
         "config": {"workload": args.workload, "grid": [edge] * 3, "stencil": cfg.S, "solver": f"{mode}({m},{k})",
-                   "precision": args.precision,
+                   "precision": args.precision, "precond": args.precond,
                    "tol": 1e-8, "preroll_steps": P, "preroll_matvec_cap": args.preroll_matvec,
                    "sequence_steps_timed": [t0s + W, t0s + W + K - 1], "l2": "inputs larger than L2",
                    "parallelism": "replicas" if ws > 1 else "single"},
@@ -315,15 +367,7 @@ def run_ours(args, ws, rank, local):
         "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99))},
         "matvecs_per_solve": statistics.mean(mv), "relres_max": max(i["relres_true"] for i in tinfo),
         "all_converged": all(i["status"] == 0 for i in tinfo),
-        "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak,
-                     "traffic": (traffic_ratio[dname] * d["bytes"] / max(d["launches"], 1)
-                                 if dname in traffic_ratio else None),
-                     "traffic_source": "ncu DRAM bytes / algorithmic bytes on the 96^3 channel x this run's "
-                                       "algorithmic bytes per launch" if dname in traffic_ratio else None,
-                     "peak_source": peak_src,
-                     "launches": d["launches"], "avg_launch_us": 1000.0 * d["ms"] / max(d["launches"], 1),
-                     "bytes_per_launch": d["bytes"] / max(d["launches"], 1)},
+        "roofline": roof,
         "kernel_classes": {kname: {"ms": round(v["ms"], 3), "launches": v["launches"],
                                    "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
                            for kname, v in prof.items() if v["launches"]},
@@ -333,7 +377,7 @@ def run_ours(args, ws, rank, local):
         "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        per_mv, threads = oracle_cycle_sample(cfg, mode, m, k, cycles=2)
+        per_mv, threads = oracle_cycle_sample(cfg, mode, m, k, cycles=2, precond=args.precond)
         mvs = statistics.mean(mv)
         line["cpu_baseline"] = {"value": 1.0 / (per_mv * mvs), "unit": "solves/s", "cores": threads,
                                 "kind": "oracle",
@@ -583,6 +627,9 @@ def main():
                     help="fp64: FP64 operator, double-float projections; df: double-float operator in the "
                          "recurrences; mixed: FP32 inner operator (A11). "
                          "Default fp64 for the single-sequence workloads, mixed for batch64 and serve")
+    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "subdomain"],
+                    help="jacobi: right point Jacobi; subdomain: Sec. 2.1's sub-domain Jacobi preconditioner "
+                         "(5 damped local sweeps on overlapping 16x8x8 boxes, one global sweep), left in rGCROT")
     ap.add_argument("--nprob", type=int, default=None, help="problems (batch64: 64; serve: 12)")
     ap.add_argument("--threads", type=int, default=0, help="rk_solve_batch worker threads (0: min(n, 16))")
     ap.add_argument("--requests", type=int, default=60, help="serve: number of timed requests")

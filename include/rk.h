@@ -64,6 +64,23 @@ typedef enum {
 typedef enum { RK_GMRES = 0, RK_RGCROT = 1, RK_RBICGSTAB = 2, RK_HYBRID = 3 } rk_mode;
 typedef enum { RK_FP64 = 0, RK_MIXED = 1, RK_DF = 2 } rk_precision;
 
+/*
+ * The preconditioner M (Sec. 2.1, "Preconditioners").
+ * RK_PC_JACOBI: point Jacobi, M = diag(A).
+ * RK_PC_SUBDOMAIN: the paper's sub-domain Jacobi preconditioner. The grid is
+ * cut into boxes of 16 x 8 x 8 owned cells (the last box along an axis takes
+ * the remainder); each box grown by one cell per side (wrapping on periodic
+ * axes, cut at non-periodic faces) carries the local problem "A restricted to
+ * the grown box" (couplings leaving it dropped), solved inexactly by 5 damped
+ * Jacobi sweeps z <- z + omega D^{-1} (r - A_loc z) from z = 0 with
+ * omega = 2/3; each box keeps its own cells' values (restricted additive
+ * Schwarz), and one damped point-Jacobi sweep z <- z + omega D^{-1} (r - A z)
+ * on the whole grid follows. A fixed linear operator, evaluated in FP64 in a
+ * fixed order (bands in storage order, one fma each):
+ *   s = a_0 z_p; s = fma(a_t, z_nb, s); u = dinv_p (r_p - s); z_p <- fma(omega, u, z_p).
+ */
+typedef enum { RK_PC_JACOBI = 0, RK_PC_SUBDOMAIN = 1 } rk_preconditioner;
+
 typedef struct {
   int32_t nx, ny, nz;
   uint8_t periodic[3]; /* nonzero: that axis wraps */
@@ -94,13 +111,20 @@ typedef struct {
                               (within max_matvec in total), and the hybrid starts a new rGCROT
                               phase: that solve and the next hybrid_switch - 1 use rGCROT;
                               0 = off */
-  int32_t precond_side;  /* 0 = right point Jacobi (A M^{-1}, every solver); 1 = left for GMRES
+  int32_t precond_side;  /* 0 = right preconditioning (A M^{-1}, every solver); 1 = left for GMRES
                             and rGCROT, as Sec. 2.1 states it: Arnoldi on M^{-1} A, x <- x + V y + U z,
-                            convergence on ||M^{-1}(b - A x)|| <= tol ||M^{-1} b|| (relres_true still
-                            reports ||b - A x|| / ||b||), recycle pair M^{-1} A U = C. rBiCGStab is
+                            recycle pair M^{-1} A U = C; the cycles stop early on their own residual
+                            M^{-1}(b - A x) against a target that starts at tol ||M^{-1} b||, and the
+                            solve stops on ||b - A x|| <= tol ||b|| (checked after every cycle; when
+                            the target is met but the true residual is not, the target is scaled by
+                            tol ||b|| / ||b - A x||). rBiCGStab is
                             always right-preconditioned (Sec. 2.1); a stored recycle space is
                             converted (C re-derived from U by CholQR2) when a solve uses the other
                             side. Left with RK_MIXED: RK_E_INVALID */
+  int32_t precond;       /* rk_preconditioner. RK_PC_SUBDOMAIN: precision RK_FP64 only; GMRES,
+                            rGCROT and the hybrid's rGCROT phase left-preconditioned only
+                            (precond_side = 1), rBiCGStab right-preconditioned (x <- x + M^{-1} x~);
+                            otherwise RK_E_INVALID */
 } rk_solve_params;
 
 typedef struct {
@@ -189,8 +213,11 @@ int rk_solve(rk_problem* p, const double* b, double* x, const rk_solve_params* p
  * 1/a_pp rounded to FP32, v rounded to FP32, FP32 accumulation in band order,
  * the result widened to FP64; 3: the double-float operator of RK_DF,
  * y = A_df (M_df^{-1} v) with v rounded to double-float and the result
- * widened to FP64 (exact). Other values: RK_E_INVALID. The operator copies
- * of modes 2 and 3 are made on first use (and freed by rk_problem_release).
+ * widened to FP64 (exact); 5: y = M^{-1} v and 6: y = M^{-1} (A v) with the
+ * sub-domain preconditioner (RK_PC_SUBDOMAIN), y must not alias v. Other
+ * values: RK_E_INVALID. The operator copies of modes 2 and 3 and the
+ * workspace of modes 5 and 6 are made on first use (and freed by
+ * rk_problem_release).
  * And r = b - A x. All vectors device, N doubles.
  */
 int rk_apply(const rk_problem* p, const double* v, double* y, int32_t precond, void* stream);
@@ -279,7 +306,7 @@ int rk_import_recycle(rk_problem* p, const void* buf, int64_t bytes, void* strea
 /*
  * Opt-in kernel timing of the solves of a problem: CUDA events on the solve's
  * stream around every launch, summed per kernel class ("spmv", "residual",
- * "dots", "update", "gemm_rows", "gram", "small", "bicg", "harmonic_ritz") with the class's
+ * "dots", "update", "gemm_rows", "gram", "small", "bicg", "harmonic_ritz", "subdomain_local") with the class's
  * algorithmic HBM bytes (the library's byte model of each launch).
  * rk_profile_enable resets the counters; rk_profile_read copies up to cap
  * entries to out (host) and sets *count to the number of classes.

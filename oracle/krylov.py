@@ -76,6 +76,24 @@ class _Prec:
         return self.op.residual_left(b, x) if self.kind == "jacobi" else self.op.schwarz(self.op.residual(b, x))
 
 
+def _stop_test(left, op, b, x, rho, tolp, toltrue):
+    """The stop test of GMRES and rGCROT (Sec. 4: the L2 norm of the
+    residual, ||b - A x|| <= tol ||b||). Right preconditioning: the cycle's
+    residual is the true one. Left (reading N12): the cycles work on
+    M^{-1}(b - A x) with the target tolp; the true residual decides, and when
+    the preconditioned target is met but the true residual is not, the target
+    is scaled down by the observed shortfall. Returns (converged, tolp,
+    ||b - A x|| or None)."""
+    if not left:
+        return rho <= tolp, tolp, None
+    rt = float(np.linalg.norm(op.residual(b, x)))
+    if rt <= toltrue:
+        return True, tolp, rt
+    if rho <= tolp:
+        tolp = rho * (toltrue / rt)
+    return False, tolp, rt
+
+
 class _LS:
     """Progressive Givens QR of the (j+1) x j Hessenberg matrix and rotated rhs
     (Algorithms 1 and 3: y = argmin || e_1 rho - H y ||)."""
@@ -119,9 +137,9 @@ def gmres(op, b, x0=None, tol=1e-8, m=30, max_matvec=2000, keep_cycle=False, lef
     Arnoldi with modified Gram-Schmidt on A M^{-1}; solution
     update x <- x + M^{-1} V_j y; true residual b - A x after every cycle.
     With ``left``, preconditioned from the left as Sec. 2.1 states it:
-    Arnoldi on M^{-1} A, x <- x + V_j y, and the convergence test on
-    ||M^{-1}(b - A x)|| <= tol ||M^{-1} b||; info's relres_true is still
-    ||b - A x|| / ||b||. ``prec``: "jacobi" (point Jacobi) or "schwarz" (the
+    Arnoldi on M^{-1} A, x <- x + V_j y, the cycles' target on
+    ||M^{-1}(b - A x)|| starting at tol ||M^{-1} b||, and the stop test on
+    ||b - A x|| <= tol ||b|| (_stop_test). ``prec``: "jacobi" (point Jacobi) or "schwarz" (the
     sub-domain preconditioner of Sec. 2.1, left side only)."""
     P = _Prec(op, prec)
     if prec != "jacobi" and not left:
@@ -140,7 +158,9 @@ def gmres(op, b, x0=None, tol=1e-8, m=30, max_matvec=2000, keep_cycle=False, lef
     hist = [rho / bnorm]
     est = rho / bnorm
     last = None
-    while rho > tol * bnorm and matvecs < max_matvec:
+    tolp, toltrue = tol * bnorm, tol * bnorm_true
+    conv, tolp, rt = _stop_test(left, op, b, x, rho, tolp, toltrue)
+    while not conv and matvecs < max_matvec:
         V = np.zeros((m + 1, n))
         H = np.zeros((m + 1, m))
         V[0] = r / rho
@@ -159,7 +179,7 @@ def gmres(op, b, x0=None, tol=1e-8, m=30, max_matvec=2000, keep_cycle=False, lef
             e = ls.add_column(j, H[: j + 2, j])
             est = e / bnorm
             jj = j + 1
-            if e <= tol * bnorm or happy or matvecs >= max_matvec:
+            if e <= tolp or happy or matvecs >= max_matvec:
                 break
         y = ls.solve(jj)
         x = x + (V[:jj].T @ y if left else op.minv(V[:jj].T @ y))
@@ -169,8 +189,9 @@ def gmres(op, b, x0=None, tol=1e-8, m=30, max_matvec=2000, keep_cycle=False, lef
         hist.append(rho / bnorm)
         if keep_cycle:
             last = dict(V=V[: jj + 1].copy(), H=H[: jj + 1, :jj].copy(), y=y)
-    st = OK if rho <= tol * bnorm else NOT_CONVERGED
-    rel = float(np.linalg.norm(op.residual(b, x))) / bnorm_true if left else rho / bnorm
+        conv, tolp, rt = _stop_test(left, op, b, x, rho, tolp, toltrue)
+    st = OK if conv else NOT_CONVERGED
+    rel = rt / bnorm_true if left else rho / bnorm
     info = _info(st, matvecs, cycles, 0, rel, est, hist)
     if keep_cycle:
         info["last_cycle"] = last
@@ -265,8 +286,9 @@ def rgcrot(op, b, x0=None, tol=1e-8, m=30, k=10, U=None, C=None, update=True, ma
     U, C are N x k_cur arrays (or None) with A U = C, C^T C = I; if only U is
     given, C is formed from it (recycle_from_u). Returns (x, U, C, info).
     With ``left`` (Sec. 2.1's side): Arnoldi on M^{-1} A, M^{-1} A U = C,
-    x <- x + V_j y + U z, and the convergence test on ||M^{-1}(b - A x)||
-    relative to ||M^{-1} b||; info's relres_true is ||b - A x|| / ||b||.
+    x <- x + V_j y + U z, the cycles' target on ||M^{-1}(b - A x)|| starting
+    at tol ||M^{-1} b||, and the stop test on ||b - A x|| <= tol ||b||
+    (_stop_test).
     ``prec``: "jacobi" or "schwarz" (the latter from the left only)."""
     P = _Prec(op, prec)
     if prec != "jacobi" and not left:
@@ -297,7 +319,9 @@ def rgcrot(op, b, x0=None, tol=1e-8, m=30, k=10, U=None, C=None, update=True, ma
     est = rho / bnorm
     last = None
     first = True
-    while rho > tol * bnorm and matvecs < max_matvec:   # outer loop
+    tolp, toltrue = tol * bnorm, tol * bnorm_true
+    conv, tolp, rt = _stop_test(left, op, b, x, rho, tolp, toltrue)
+    while not conv and matvecs < max_matvec:            # outer loop
         if kc and not first:
             # the projection onto C again: v_1 must be orthogonal to the (updated) C for
             # eq. V_perp_C; the true residual is only orthogonal to it
@@ -329,7 +353,7 @@ def rgcrot(op, b, x0=None, tol=1e-8, m=30, k=10, U=None, C=None, update=True, ma
             e = ls.add_column(j, H[: j + 2, j])
             est = e / bnorm
             jj = j + 1
-            if e <= tol * bnorm or happy or matvecs >= max_matvec:
+            if e <= tolp or happy or matvecs >= max_matvec:
                 break
         y = ls.solve(jj)                                # least squares for y
         x = x + (V[:jj].T @ y if left else op.minv(V[:jj].T @ y))   # x <- x + M^{-1} V_j y
@@ -346,8 +370,9 @@ def rgcrot(op, b, x0=None, tol=1e-8, m=30, k=10, U=None, C=None, update=True, ma
         if update and k > 0:                            # recycle-space update
             U, C = harmonic_ritz_update(op, U, C, V, Bm, H, jj, k, left=left)
             kc = 0 if U is None else U.shape[1]
-    st = OK if rho <= tol * bnorm else NOT_CONVERGED
-    rel = float(np.linalg.norm(op.residual(b, x))) / bnorm_true if left else rho / bnorm
+        conv, tolp, rt = _stop_test(left, op, b, x, rho, tolp, toltrue)
+    st = OK if conv else NOT_CONVERGED
+    rel = rt / bnorm_true if left else rho / bnorm
     info = _info(st, matvecs, cycles, 0, rel, est, hist, kc)
     if keep_cycle:
         info["last_cycle"] = last

@@ -35,10 +35,12 @@ inline int red_blocks(int64_t n) {
 }
 
 // ---- stencil.cu
-enum StencilMode { ST_PREC = 0, ST_PLAIN = 1, ST_RESID = 2, ST_LEFT = 3, ST_LRESID = 4 };
+enum StencilMode { ST_PREC = 0, ST_PLAIN = 1, ST_RESID = 2, ST_LEFT = 3, ST_LRESID = 4, ST_JSWEEP = 5 };
 // y = A (dinv .* v) [ST_PREC], y = A v [ST_PLAIN], y = b - A v [ST_RESID],
 // y = dinv .* (A v) [ST_LEFT], y = dinv .* (b - A v) [ST_LRESID] (left
-// preconditioning: the product, then one rounded multiplication).
+// preconditioning: the product, then one rounded multiplication),
+// y = fma(kSdOmega, dinv .* (b - A v), v) [ST_JSWEEP: one damped point-Jacobi
+// sweep from v for A y = b, the global sweep of the sub-domain preconditioner].
 // part (nullable): per-block partial sums of y^2, reduced by the last block into *nrm2.
 cudaError_t launch_stencil(const Dims& d, int S, int mode, const double* coef, const double* dinv,
                            const double* v, const double* b, double* y, double* part,
@@ -59,6 +61,25 @@ cudaError_t launch_round_f32(int64_t n, const double* src, float* dst, cudaStrea
 cudaError_t launch_stencil_df(const Dims& d, int S, int mode, const double* coef, const double* dinv,
                               const void* v, bool v_df, void* y, bool y_df, const int* skip_flag, cudaStream_t st);
 int stencil_blocks(const Dims& d);
+// The global damped sweep y = fma(kSdOmega, dinv .* (r - A z), z), y FP64 or
+// double-float; part (nullable) as for launch_stencil.
+cudaError_t launch_jsweep(const Dims& d, int S, const double* coef, const double* dinv, const double* z,
+                          const double* r, void* y, bool y_df, double* part, unsigned* counter, double* nrm2,
+                          const int* skip, cudaStream_t st);
+
+// ---- subdomain.cu: the sub-domain Jacobi preconditioner of Sec. 2.1 (box of
+// owned cells, overlap, local damped Jacobi sweeps from zero, relaxation)
+constexpr int kSdBX = 16, kSdBY = 8, kSdBZ = 8;
+constexpr int kSdOverlap = 1;
+constexpr int kSdSweeps = 5;
+constexpr double kSdOmega = 2.0 / 3.0;
+int64_t subdomain_boxes(const Dims& d);
+// z = the restricted local solutions for right-hand side r (every cell of z
+// written); the global sweep is launch_jsweep(z, r).
+cudaError_t launch_subdomain_local(const Dims& d, int S, const double* coef, const double* dinv, const double* r,
+                                   double* z, const int* skip, cudaStream_t st);
+// x += v
+cudaError_t launch_add(int64_t n, const double* v, double* x, cudaStream_t st);
 
 // ---- blas.cu
 // out[q] = sum_i Q[q*ld + i] * w[i] (q < nq), then extra vectors e[0..ne) (w

@@ -55,6 +55,8 @@ cudaError_t launch_harmonic_ritz(SolveState* s, SmallBuffers b, int kc, int jj, 
 cudaError_t launch_set_scalar(SolveState* s, int which, cudaStream_t st);
 cudaError_t launch_cycle_init(SolveState* s, SmallBuffers b, cudaStream_t st);
 cudaError_t launch_set_tol(SolveState* s, double tol, cudaStream_t st);
+// tolabs of the in-cycle stop test, set directly
+cudaError_t launch_set_tolabs(SolveState* s, double tolabs, cudaStream_t st);
 size_t harmonic_ritz_ws_doubles(int n);
 cudaError_t launch_chol_rinv(int k, const double* G, double* Rinv, double* Rw, int* status, cudaStream_t st);
 

@@ -1144,6 +1144,10 @@ __global__ void k_set_tol(SolveState* s, double tol) {
   s->tolabs = tol * s->bnorm;
 }
 
+__global__ void k_set_tolabs(SolveState* s, double tolabs) {
+  if (threadIdx.x == 0) s->tolabs = tolabs;
+}
+
 __global__ void k_set_scalar(SolveState* s, int which) {
   if (threadIdx.x != 0) return;
   if (which == 0) s->done = 0;
@@ -1212,6 +1216,11 @@ cudaError_t launch_cycle_init(SolveState* s, SmallBuffers b, cudaStream_t st) {
 
 cudaError_t launch_set_tol(SolveState* s, double tol, cudaStream_t st) {
   k_set_tol<<<1, 32, 0, st>>>(s, tol);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_tolabs(SolveState* s, double tolabs, cudaStream_t st) {
+  k_set_tolabs<<<1, 32, 0, st>>>(s, tolabs);
   return cudaGetLastError();
 }
 

@@ -105,8 +105,8 @@ int alloc_into(rk_context* c, T** out, size_t count) {
 
 // Opt-in per-kernel-class timing: CUDA events recorded on the solve's stream
 // around every launch, reduced at the solve's synchronisation points.
-enum ProfClass { PC_SPMV = 0, PC_RESID, PC_DOTS, PC_UPDATE, PC_GEMM, PC_GRAM, PC_SMALL, PC_BICG, PC_HRITZ, PC_COUNT };
-static const char* kProfNames[PC_COUNT] = {"spmv", "residual", "dots", "update", "gemm_rows", "gram", "small", "bicg", "harmonic_ritz"};
+enum ProfClass { PC_SPMV = 0, PC_RESID, PC_DOTS, PC_UPDATE, PC_GEMM, PC_GRAM, PC_SMALL, PC_BICG, PC_HRITZ, PC_SUBDOMAIN, PC_COUNT };
+static const char* kProfNames[PC_COUNT] = {"spmv", "residual", "dots", "update", "gemm_rows", "gram", "small", "bicg", "harmonic_ritz", "subdomain_local"};
 
 struct Profiler {
   bool on = false;
@@ -195,6 +195,7 @@ struct rk_problem {
   float* dinv32 = nullptr;        // mixed precision: FP32 1/a_pp
   float2* coefdf = nullptr;       // RK_DF: double-float copy of the bands
   float2* dinvdf = nullptr;       // RK_DF: double-float 1/a_pp
+  double* sdw = nullptr;          // sub-domain preconditioner: 2 FP64 vectors (local result, operand)
   double* bicg = nullptr;
   // small
   double* small = nullptr;
@@ -211,7 +212,8 @@ struct rk_problem {
   int* istat = nullptr;           // device ints for small kernels
   int solves = 0;
   int hyb_base = 0;  // first solve of the current rGCROT phase of RK_HYBRID
-  int kside = 0;     // side of the stored recycle pair: 0 A U = C, 1 M^{-1} A U = C
+  int kside = 0;     // the stored recycle pair: 0 A U = C; 1 M^{-1} A U = C with point Jacobi;
+                     // 2 M^{-1} A U = C with the sub-domain preconditioner
   double dinv_max = 0.0;  // max |1 / a_pp|
 
   float2* Vcol(int j) const { return QB + (int64_t)(kmax + j) * ld; }
@@ -500,6 +502,28 @@ int ensure_dfop(rk_problem* p, cudaStream_t st) {
   return RK_OK;
 }
 
+// Workspace of the sub-domain preconditioner (Sec. 2.1): two FP64 vectors.
+int ensure_subdomain(rk_problem* p) {
+  if (p->sdw) return RK_OK;
+  p->drop_graphs();
+  return alloc_into(p->ctx, &p->sdw, (size_t)2 * p->ld);
+}
+
+// y = M^{-1} r with the sub-domain preconditioner (Sec. 2.1): the local
+// sweeps of every box into sdw, then the global damped sweep into y (FP64 or
+// double-float); with nrm2 set, ||y||^2 -> *nrm2. r must not alias sdw[0, ld).
+int subdomain_launch(rk_problem* p, const double* r, void* y, bool y_df, double* nrm2, const int* skip,
+                     cudaStream_t st) {
+  {
+    ProfScope ps(&p->prof, PC_SUBDOMAIN, 8.0 * (p->S + 3) * (double)p->n, st);
+    RK_CUDA(launch_subdomain_local(p->d, p->S, p->coef, p->dinv, r, p->sdw, skip, st));
+  }
+  ProfScope ps(&p->prof, PC_SPMV, 8.0 * (p->S + 4) * (double)p->n, st);
+  RK_CUDA(launch_jsweep(p->d, p->S, p->coef, p->dinv, p->sdw, r, y, y_df, nrm2 ? p->part : nullptr,
+                        nrm2 ? p->counter : nullptr, nrm2, skip, st));
+  return RK_OK;
+}
+
 int ensure_operator(rk_problem* p, int precision, cudaStream_t st) {
   if (precision == RK_MIXED) return ensure_mixed(p, st);
   if (precision == RK_DF) return ensure_dfop(p, st);
@@ -509,7 +533,21 @@ int ensure_operator(rk_problem* p, int precision, cudaStream_t st) {
 // A M^{-1} v of the recurrences: FP64 (bit-exact order), the FP32 operator
 // (RK_MIXED) or the double-float operator (RK_DF)
 int opapply_launch(rk_problem* p, int precision, const void* v, bool v_df, void* y, bool y_df, const int* skip,
-                   cudaStream_t st, bool left = false) {
+                   cudaStream_t st, bool left = false, int pc = RK_PC_JACOBI) {
+  if (pc == RK_PC_SUBDOMAIN) {
+    // M^{-1} (A v) or A (M^{-1} v) with the sub-domain preconditioner (FP64)
+    double* t = p->sdw + p->ld;
+    if (left) {
+      if (v_df)
+        RK_TRY(stencil_df_launch(p, ST_PLAIN, v, true, t, false, skip, st));
+      else
+        RK_TRY(stencil_launch(p, ST_PLAIN, (const double*)v, nullptr, t, nullptr, nullptr, nullptr, skip, st));
+      return subdomain_launch(p, t, y, y_df, nullptr, skip, st);
+    }
+    if (v_df || y_df) return fail(RK_E_INVALID, "right sub-domain product takes FP64 vectors");
+    RK_TRY(subdomain_launch(p, (const double*)v, t, false, nullptr, skip, st));
+    return stencil_launch(p, ST_PLAIN, t, nullptr, (double*)y, nullptr, nullptr, nullptr, skip, st);
+  }
   const int mode = left ? ST_LEFT : ST_PREC;
   if (precision == RK_DF) {
     ProfScope ps(&p->prof, PC_SPMV, 8.0 * (p->S + 2) * (double)p->n, st);
@@ -528,15 +566,22 @@ int opapply_launch(rk_problem* p, int precision, const void* v, bool v_df, void*
 
 // C = orth(A U) in FP64 with U rescaled so that A U = C (CholQR2, as when C is formed from U)
 // for the k stored columns.
-int derive_c_from_u(rk_problem* p, int k, cudaStream_t st, bool left = false) {
+int derive_c_from_u(rk_problem* p, int k, cudaStream_t st, bool left = false, int pc = RK_PC_JACOBI) {
   float2* Ud = p->Ublk(k);
   float2* Cd = p->Cblk(k);
   double* G = p->eta;
   double* Rinv = p->eta + (size_t)k * k;
   double* Rw = p->sb.hrws;
-  for (int c = 0; c < k; ++c)
-    RK_CUDA(launch_stencil_df(p->d, p->S, left ? ST_LEFT : ST_PLAIN, p->coef, p->dinv, Ud + (int64_t)c * p->ld,
-                              true, Cd + (int64_t)c * p->ld, true, nullptr, st));
+  if (left && pc == RK_PC_SUBDOMAIN) {
+    RK_TRY(ensure_subdomain(p));
+    for (int c = 0; c < k; ++c)
+      RK_TRY(opapply_launch(p, RK_FP64, Ud + (int64_t)c * p->ld, true, Cd + (int64_t)c * p->ld, true, nullptr, st,
+                            true, pc));
+  } else {
+    for (int c = 0; c < k; ++c)
+      RK_CUDA(launch_stencil_df(p->d, p->S, left ? ST_LEFT : ST_PLAIN, p->coef, p->dinv, Ud + (int64_t)c * p->ld,
+                                true, Cd + (int64_t)c * p->ld, true, nullptr, st));
+  }
   for (int pass = 0; pass < 2; ++pass) {
     DFGramArgs g{};
     g.n = p->n;
@@ -568,9 +613,10 @@ int derive_c_from_u(rk_problem* p, int k, cudaStream_t st, bool left = false) {
 // The stored recycle pair for a solve on the given preconditioning side: the
 // two sides' pairs span the same U with different C (A U versus M^{-1} A U,
 // orthonormalised), so a switch re-derives C from U.
-int ensure_side(rk_problem* p, bool left, cudaStream_t st) {
-  if (p->kdim > 0 && p->kside != (left ? 1 : 0)) RK_TRY(derive_c_from_u(p, p->kdim, st, left));
-  p->kside = left ? 1 : 0;
+int ensure_side(rk_problem* p, bool left, int pc, cudaStream_t st) {
+  const int want = left ? 1 + pc : 0;
+  if (p->kdim > 0 && p->kside != want) RK_TRY(derive_c_from_u(p, p->kdim, st, left, pc));
+  p->kside = want;
   return RK_OK;
 }
 
@@ -602,9 +648,12 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
   const bool mixed = prm.precision == RK_MIXED;
   const int opk = prm.precision;
   const bool left = prm.precond_side == 1;  // Sec. 2.1: M^{-1} A for GMRES / rGCROT
+  const int pc = prm.precond;
+  const bool sd = pc == RK_PC_SUBDOMAIN;   // left only (checked by rk_solve)
   RK_TRY(ensure_capacity(p, std::max(k, p->kdim), m, st));
   RK_TRY(ensure_operator(p, opk, st));
-  if (recycle) RK_TRY(ensure_side(p, left, st));
+  if (left) RK_TRY(ensure_subdomain(p));  // scratch for b - A x
+  if (recycle) RK_TRY(ensure_side(p, left, pc, st));
   int kc = recycle ? p->kdim : 0;
   const double S = p->S;
   double words = 0.0;
@@ -616,8 +665,12 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
   const double bnorm_true = p->st_h->bnorm;
   if (!std::isfinite(bnorm_true)) return fail(RK_E_INVALID, "b contains NaN or Inf");
   if (left && bnorm_true != 0.0) {
-    RK_CUDA(cudaMemsetAsync(r, 0, sizeof(double) * p->n, st));
-    RK_CUDA(launch_axpy_scaled(p->n, p->dinv, b, r, st));
+    if (sd) {
+      RK_TRY(subdomain_launch(p, b, r, false, nullptr, nullptr, st));
+    } else {
+      RK_CUDA(cudaMemsetAsync(r, 0, sizeof(double) * p->n, st));
+      RK_CUDA(launch_axpy_scaled(p->n, p->dinv, b, r, st));
+    }
     RK_TRY(norm2_into(p, r, 0, st));
     { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_set_tol(p->st, prm.tol, st)); }
     RK_TRY(sync_state(p, st));
@@ -631,18 +684,46 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
     info.recycle_dim = p->kdim;
     return RK_OK;
   }
-  const double tolabs = prm.tol * bnorm;
-  // initial residual r = b - A x (left: M^{-1}(b - A x)) in FP64; its
-  // projection onto C
-  RK_TRY(stencil_launch(p, resid_mode, x, b, r, p->part, p->counter, &p->st->rho2, nullptr, st));
+  // stop test (Sec. 4: the L2 norm of the residual): ||b - A x|| <= tol ||b||.
+  // The cycles work on their own residual (left: M^{-1}(b - A x)) with the
+  // target tolp; with left preconditioning the true residual is checked
+  // after every cycle and, when the preconditioned target is met but the
+  // true residual is not, the target is scaled down by the observed shortfall.
+  double tolp = prm.tol * bnorm;
+  const double toltrue = prm.tol * bnorm_true;
+  // r = b - A x (left: M^{-1}(b - A x)) in FP64 with ||r||^2 -> st->rho2
+  auto residual = [&]() -> int {
+    if (!sd) return stencil_launch(p, resid_mode, x, b, r, p->part, p->counter, &p->st->rho2, nullptr, st);
+    double* t = p->sdw + p->ld;
+    RK_TRY(stencil_launch(p, ST_RESID, x, b, t, nullptr, nullptr, nullptr, nullptr, st));
+    return subdomain_launch(p, t, r, false, &p->st->rho2, nullptr, st);
+  };
+  // left: ||b - A x||^2 of the current x -> st->nrm2[1]
+  auto true_norm = [&]() -> int {
+    if (!left) return RK_OK;
+    return stencil_launch(p, ST_RESID, x, b, p->sdw + p->ld, p->part, p->counter, &p->st->nrm2[1], nullptr, st);
+  };
+  double rho = 0.0, rt = 0.0;
+  auto converged = [&]() -> bool {
+    if (!left) return rho <= tolp;
+    rt = std::sqrt(p->st_h->nrm2[1]);
+    if (rt <= toltrue) return true;
+    if (rho <= tolp) tolp = rho * (toltrue / rt);
+    return false;
+  };
+  // initial residual; its projection onto C
+  RK_TRY(residual());
   RK_TRY(project_residual(p, kc, r, x, st));
-  words += (S + 3) + (kc ? 2.0 * kc + 3 : 0) + 1;
+  RK_TRY(true_norm());
+  words += (S + 3) + (kc ? 2.0 * kc + 3 : 0) + 1 + (left ? S + 3 : 0);
   RK_TRY(sync_state(p, st));
-  double rho = std::sqrt(p->st_h->rho2);
+  rho = std::sqrt(p->st_h->rho2);
   int matvecs = 0, cycles = 0;
   double est = rho / bnorm;
   const int* done = &p->st->done;
-  while (rho > tolabs && matvecs < maxmv) {
+  bool conv = converged();
+  while (!conv && matvecs < maxmv) {
+    if (left) { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_set_tolabs(p->st, tolp, st)); }
     const int steps = std::min(m, maxmv - matvecs);
     // one Arnoldi cycle (and the second pass of the last vector):
     // a fixed launch sequence whose kernels skip themselves once the device
@@ -657,7 +738,7 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
       // pass per step (Gram-Schmidt against [C V_j] with the second pass of
       // each vector delayed to the next step)
       for (int j = 0; j < steps; ++j) {
-        RK_TRY(opapply_launch(p, opk, p->Vcol(j), true, p->Vcol(j + 1), true, done, st, left));
+        RK_TRY(opapply_launch(p, opk, p->Vcol(j), true, p->Vcol(j + 1), true, done, st, left, pc));
         const int nq = kc + j;
         RK_TRY(dfdots2_launch(p, p->Cblk(kc), nq, p->Vcol(j), p->Vcol(j + 1), p->sb.dots, done, st));
         { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_dcgs_coef(p->st, p->sb, kc, j, 0, st)); }
@@ -677,8 +758,8 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
     if (p->prof.on) {
       RK_TRY(cycle(st));
     } else {
-      const uint64_t key = ((uint64_t)kc << 32) | ((uint64_t)steps << 4) | (left ? 8u : 0u) | ((uint64_t)opk << 1) |
-                           (keep_last ? 1u : 0u);
+      const uint64_t key = ((uint64_t)kc << 32) | ((uint64_t)pc << 28) | ((uint64_t)steps << 4) | (left ? 8u : 0u) |
+                           ((uint64_t)opk << 1) | (keep_last ? 1u : 0u);
       auto it = p->graphs.find(key);
       if (it == p->graphs.end()) {
         cudaGraph_t g = nullptr;
@@ -745,10 +826,13 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
       }
     }
     // true residual r = b - A x (left: M^{-1}(b - A x)); the next cycle projects it onto C
-    RK_TRY(stencil_launch(p, resid_mode, x, b, r, p->part, p->counter, &p->st->rho2, nullptr, st));
+    RK_TRY(residual());
     RK_TRY(project_residual(p, kc, r, x, st));
+    RK_TRY(true_norm());
+    words += left ? S + 3 : 0;
     RK_TRY(sync_state(p, st));
     rho = std::sqrt(p->st_h->rho2);
+    conv = converged();
   }
   if (mixed && update && p->kdim > 0) {
     // the FP32 operator leaves A U = C only to FP32 accuracy: re-derive C from
@@ -757,17 +841,12 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
   }
   info.matvecs = matvecs;
   info.cycles_or_iters = cycles;
-  info.relres_true = rho / bnorm;
-  if (left) {
-    // the convergence test was on M^{-1}(b - A x); report ||b - A x|| / ||b||
-    RK_TRY(stencil_launch(p, ST_RESID, x, b, r, p->part, p->counter, &p->st->rho2, nullptr, st));
-    RK_TRY(sync_state(p, st));
-    info.relres_true = std::sqrt(p->st_h->rho2) / bnorm_true;
-  }
+  // left: ||b - A x|| of the returned x (the last check ran on it)
+  info.relres_true = left ? rt / bnorm_true : rho / bnorm;
   info.relres_est = est;
   info.recycle_dim = p->kdim;
   info.model_bytes = 8.0 * words * (double)p->n;
-  info.status = rho <= tolabs ? RK_OK : RK_E_NOT_CONVERGED;
+  info.status = conv ? RK_OK : RK_E_NOT_CONVERGED;
   return info.status;
 }
 
@@ -779,7 +858,8 @@ int solve_bicg(rk_problem* p, const double* b, double* x, const rk_solve_params&
   RK_TRY(ensure_capacity(p, p->kdim, std::max(p->mcap, 1), st));
   RK_TRY(ensure_operator(p, opk, st));
   if (!p->bicg) RK_TRY(alloc_into(p->ctx, &p->bicg, (size_t)7 * p->ld));
-  if (recycle) RK_TRY(ensure_side(p, false, st));  // Sec. 2.1: BiCGStab is right-preconditioned
+  if (recycle) RK_TRY(ensure_side(p, false, prm.precond, st));  // Sec. 2.1: BiCGStab is right-preconditioned
+  const int pc = prm.precond;
   const int kc = recycle ? p->kdim : 0;
   BicgVecs v{};
   v.r = p->bicg;
@@ -829,11 +909,11 @@ int solve_bicg(rk_problem* p, const double* b, double* x, const rk_solve_params&
     while (running) {
       for (int it = 0; it < NB; ++it) {
         { ProfScope ps_(&p->prof, PC_BICG, 32.0 * p->n, st); RK_CUDA(launch_bicg_p(v, p->bs, p->n, st)); }
-        RK_TRY(opapply_launch(p, opk, v.p, false, v.v, false, &p->bs->stop, st));
+        RK_TRY(opapply_launch(p, opk, v.p, false, v.v, false, &p->bs->stop, st, false, pc));
         RK_TRY(dfdots_launch(p, p->Cblk(kc), kc, v.v, false, eta1, &p->bs->stop, st, v.rt));
         { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_bicg_alpha(p->bs, eta1, kc, st)); }
         { ProfScope ps_(&p->prof, PC_BICG, 8.0 * (kc + (kc ? 5 : 3)) * (double)p->n, st); RK_CUDA(launch_bicg_s(v, p->bs, p->n, kc, p->Cblk(kc), p->ld, eta1, xi, p->part, p->counter, st)); }
-        RK_TRY(opapply_launch(p, opk, v.s, false, v.t, false, &p->bs->stop, st));
+        RK_TRY(opapply_launch(p, opk, v.s, false, v.t, false, &p->bs->stop, st, false, pc));
         if (kc) RK_TRY(dfdots_launch(p, p->Cblk(kc), kc, v.t, false, eta2, &p->bs->stop, st));
         { ProfScope ps_(&p->prof, PC_BICG, 8.0 * (kc + (kc ? 3 : 2)) * (double)p->n, st); RK_CUDA(launch_bicg_t(v, p->bs, p->n, kc, p->Cblk(kc), p->ld, eta2, p->part, p->counter, st)); }
         { ProfScope ps_(&p->prof, PC_BICG, 56.0 * p->n, st); RK_CUDA(launch_bicg_r(v, p->bs, p->n, kc, eta1, eta2, xi, p->part, p->counter, st)); }
@@ -851,7 +931,12 @@ int solve_bicg(rk_problem* p, const double* b, double* x, const rk_solve_params&
     const int flag = p->bs_h->flag;
     // final fold: x <- x + M^{-1} x~ - U xi
     {
-      RK_CUDA(launch_axpy_scaled(p->n, p->dinv, v.xt, x, st));
+      if (pc == RK_PC_SUBDOMAIN) {
+        RK_TRY(subdomain_launch(p, v.xt, p->sdw + p->ld, false, nullptr, nullptr, st));
+        RK_CUDA(launch_add(p->n, p->sdw + p->ld, x, st));
+      } else {
+        RK_CUDA(launch_axpy_scaled(p->n, p->dinv, v.xt, x, st));
+      }
       if (kc) {
         { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_bicg_foldcoef(xi, kc, coefv, st)); }
         RK_TRY(dfgemm_launch(p, p->Ublk(kc), kc, nullptr, 0, nullptr, coefv, 1, x, false, 1, st));
@@ -1030,6 +1115,7 @@ void rk_problem_destroy(rk_problem* p) {
   dev_free(c, p->dinv32);
   dev_free(c, p->coefdf);
   dev_free(c, p->dinvdf);
+  dev_free(c, p->sdw);
   dev_free(c, p->bicg);
   dev_free(c, p->small);
   dev_free(c, p->eta);
@@ -1062,7 +1148,18 @@ int rk_apply(const rk_problem* p, const double* v, double* y, int32_t precond, v
     RK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     return RK_OK;
   }
-  if (precond < 0 || precond > 4) return fail(RK_E_INVALID, "precond must be 0..4");
+  if (precond == 5 || precond == 6) {
+    if (v == y) return fail(RK_E_INVALID, "y must not alias v");
+    rk_problem* pm = const_cast<rk_problem*>(p);
+    RK_TRY(ensure_subdomain(pm));
+    if (precond == 5)
+      RK_TRY(subdomain_launch(pm, v, y, false, nullptr, nullptr, (cudaStream_t)stream));
+    else
+      RK_TRY(opapply_launch(pm, RK_FP64, v, false, y, false, nullptr, (cudaStream_t)stream, true, RK_PC_SUBDOMAIN));
+    RK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return RK_OK;
+  }
+  if (precond < 0 || precond > 6) return fail(RK_E_INVALID, "precond must be 0..6");
   RK_CUDA(launch_stencil(p->d, p->S, precond == 4 ? ST_LEFT : (precond ? ST_PREC : ST_PLAIN), p->coef, p->dinv, v, nullptr, y, nullptr,
                          nullptr, nullptr, nullptr, (cudaStream_t)stream));
   RK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
@@ -1270,6 +1367,13 @@ int rk_solve(rk_problem* p, const double* b, double* x, const rk_solve_params* p
   if (prm.precond_side != 0 && prm.precond_side != 1) return fail(RK_E_INVALID, "precond_side must be 0 or 1");
   if (prm.precond_side == 1 && prm.precision == RK_MIXED)
     return fail(RK_E_INVALID, "left preconditioning is not available with RK_MIXED");
+  if (prm.precond != RK_PC_JACOBI && prm.precond != RK_PC_SUBDOMAIN) return fail(RK_E_INVALID, "unknown precond");
+  if (prm.precond == RK_PC_SUBDOMAIN) {
+    if (prm.precision != RK_FP64) return fail(RK_E_INVALID, "the sub-domain preconditioner runs in RK_FP64 only");
+    if (prm.mode != RK_RBICGSTAB && prm.precond_side != 1)
+      return fail(RK_E_INVALID, "the sub-domain preconditioner is applied from the left in GMRES and rGCROT");
+    RK_TRY(ensure_subdomain(p));
+  }
   int mode = prm.mode;
   const bool hybrid = mode == RK_HYBRID;
   if (hybrid) {
@@ -1383,6 +1487,7 @@ int rk_problem_memory(const rk_problem* p, int64_t* device_bytes) {
   if (p->dinv32) b += 4 * ld;
   if (p->coefdf) b += 8 * S * n;
   if (p->dinvdf) b += 8 * ld;
+  if (p->sdw) b += 8 * 2 * ld;
   if (p->bicg) b += 8 * 7 * ld;
   b += 8 * (p->small_n + p->eta_n + (p->part ? p->part_n : 0));
   *device_bytes = (int64_t)b;
@@ -1402,6 +1507,8 @@ int rk_problem_release(rk_problem* p, void* stream) {
   dev_free(c, p->dinv32);
   dev_free(c, p->coefdf);
   dev_free(c, p->dinvdf);
+  dev_free(c, p->sdw);
+  p->sdw = nullptr;
   p->QB = nullptr;
   p->Ub = nullptr;
   p->rvec = nullptr;
@@ -1530,7 +1637,7 @@ int rk_import_recycle(rk_problem* p, const void* buf, int64_t bytes, void* strea
   if (hdr[1] != p->n) return fail(RK_E_INVALID, "recycle blob is for another problem size");
   const int64_t k = hdr[2];
   if (k < 0 || k > 256) return fail(RK_E_INVALID, "bad recycle dimension in blob");
-  if (hdr[3] != 0 && hdr[3] != 1) return fail(RK_E_INVALID, "bad recycle side in blob");
+  if (hdr[3] < 0 || hdr[3] > 2) return fail(RK_E_INVALID, "bad recycle side in blob");
   const size_t col = sizeof(float2) * (size_t)p->n;
   if (bytes < 32 + 2 * (int64_t)col * k) return fail(RK_E_INVALID, "recycle blob too short");
   p->kdim = 0;

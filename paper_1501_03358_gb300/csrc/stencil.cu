@@ -111,8 +111,9 @@ __global__ void __launch_bounds__(kTX* kTY) k_stencil(Dims d, const double* __re
           w = fma(__ldg(&coef[17 * N + p]), sz[sp][cy - 1][cx], w);
           w = fma(__ldg(&coef[18 * N + p]), sz[sp][cy + 1][cx], w);
         }
-        if (MODE == ST_RESID || MODE == ST_LRESID) w = __ldg(&b[p]) - w;
-        if (MODE == ST_LEFT || MODE == ST_LRESID) w = __dmul_rn(w, __ldg(&dinv[p]));
+        if (MODE == ST_RESID || MODE == ST_LRESID || MODE == ST_JSWEEP) w = __ldg(&b[p]) - w;
+        if (MODE == ST_LEFT || MODE == ST_LRESID || MODE == ST_JSWEEP) w = __dmul_rn(w, __ldg(&dinv[p]));
+        if (MODE == ST_JSWEEP) w = fma(kSdOmega, w, sz[sc][cy][cx]);
         st_val<YT>(y, p, w);
         if (part != nullptr) acc2 = fma(w, w, acc2);
       }
@@ -402,6 +403,25 @@ cudaError_t launch_stencil(const Dims& d, int S, int mode, const double* coef, c
   }
 #undef RK_ST_MODES
 #undef RK_ST
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jsweep(const Dims& d, int S, const double* coef, const double* dinv, const double* z,
+                          const double* r, void* y, bool y_df, double* part, unsigned* counter, double* nrm2,
+                          const int* skip, cudaStream_t st) {
+  dim3 grid;
+  int zchunk;
+  stencil_grid(d, grid, zchunk);
+  const dim3 block(kTX * kTY);
+#define RK_SJ(SS, YT)                                                                                          \
+  k_stencil<SS, ST_JSWEEP, double, YT><<<grid, block, 0, st>>>(d, coef, dinv, z, r, (YT*)y, part, counter, nrm2, \
+                                                               skip, zchunk)
+  if (S == 7) {
+    if (y_df) RK_SJ(7, float2); else RK_SJ(7, double);
+  } else {
+    if (y_df) RK_SJ(19, float2); else RK_SJ(19, double);
+  }
+#undef RK_SJ
   return cudaGetLastError();
 }
 

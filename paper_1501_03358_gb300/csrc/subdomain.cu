@@ -1,0 +1,178 @@
+// The sub-domain Jacobi preconditioner of Sec. 2.1 ("Preconditioners"): the
+// grid is cut into boxes of kSdBX x kSdBY x kSdBZ owned cells; each box,
+// grown by kSdOverlap cells on every side (wrapping on periodic axes, cut at
+// non-periodic faces), carries the local problem A_ii z_i = r_i (A restricted
+// to the grown box: couplings to cells outside it are dropped), solved
+// inexactly by kSdSweeps damped Jacobi sweeps from z_i = 0. Each box keeps the
+// values of its own cells (restricted additive Schwarz); one damped
+// point-Jacobi sweep on the whole grid (the ST_JSWEEP stencil mode) follows.
+//
+// Every update of a grown-box cell e (global cell p) is evaluated as
+//   s = a_0(p) z_e;  s = fma(a_t(p), z_nb(e,t), s)  for t = 1 .. S-1;
+//   u = dinv_p (r_p - s);  z_e <- fma(omega, u, z_e)
+// with neighbours outside the grown box or the grid read as zero (a finite
+// band times zero adds nothing). The first sweep starts from zero, where this
+// reduces to z_e = omega (dinv_p r_p).
+//
+// One CTA per box; both sweep buffers of the grown box live in shared memory
+// with a ring of zeros around them, so neighbour reads need no bounds tests.
+// The bands, r and 1/a_pp are read from global memory (they stay in L1/L2
+// across the sweeps); the kernel is bound by the FP64 pipe, not by HBM.
+#include "rk_internal.h"
+#include "rk_device.cuh"
+
+namespace rk {
+
+namespace {
+
+constexpr int kEX = kSdBX + 2 * kSdOverlap;  // largest grown box
+constexpr int kEY = kSdBY + 2 * kSdOverlap;
+constexpr int kEZ = kSdBZ + 2 * kSdOverlap;
+constexpr int kPX = kEX + 2;  // with the ring of zeros
+constexpr int kPY = kEY + 2;
+constexpr int kPZ = kEZ + 2;
+constexpr int kPXY = kPX * kPY;
+constexpr int kPad = kPXY * kPZ;
+constexpr int kSdThreads = 256;
+constexpr int kCellsPer = (kEX * kEY * kEZ + kSdThreads - 1) / kSdThreads;
+static_assert(kSdSweeps >= 2, "the first and the last sweep are peeled");
+
+// coordinate of a grown-box cell along one axis; -1 beyond a non-periodic face
+__device__ __forceinline__ int sd_wrap(int c, int n, int periodic) {
+  if (c >= 0 && c < n) return c;
+  if (!periodic) return -1;
+  return c < 0 ? c + n : c - n;
+}
+
+// s = A_ii z at the grown-box cell with padded shared index q (global cell p),
+// bands in storage order
+template <int S>
+__device__ __forceinline__ double sd_row(const double* __restrict__ coef, int64_t N, int64_t p,
+                                         const double* z, int q) {
+  double s = __dmul_rn(__ldg(&coef[p]), z[q]);
+  s = fma(__ldg(&coef[1 * N + p]), z[q - 1], s);
+  s = fma(__ldg(&coef[2 * N + p]), z[q + 1], s);
+  s = fma(__ldg(&coef[3 * N + p]), z[q - kPX], s);
+  s = fma(__ldg(&coef[4 * N + p]), z[q + kPX], s);
+  s = fma(__ldg(&coef[5 * N + p]), z[q - kPXY], s);
+  s = fma(__ldg(&coef[6 * N + p]), z[q + kPXY], s);
+  if (S == 19) {
+    s = fma(__ldg(&coef[7 * N + p]), z[q - 1 - kPX], s);
+    s = fma(__ldg(&coef[8 * N + p]), z[q + 1 - kPX], s);
+    s = fma(__ldg(&coef[9 * N + p]), z[q - 1 + kPX], s);
+    s = fma(__ldg(&coef[10 * N + p]), z[q + 1 + kPX], s);
+    s = fma(__ldg(&coef[11 * N + p]), z[q - 1 - kPXY], s);
+    s = fma(__ldg(&coef[12 * N + p]), z[q + 1 - kPXY], s);
+    s = fma(__ldg(&coef[13 * N + p]), z[q - 1 + kPXY], s);
+    s = fma(__ldg(&coef[14 * N + p]), z[q + 1 + kPXY], s);
+    s = fma(__ldg(&coef[15 * N + p]), z[q - kPX - kPXY], s);
+    s = fma(__ldg(&coef[16 * N + p]), z[q + kPX - kPXY], s);
+    s = fma(__ldg(&coef[17 * N + p]), z[q - kPX + kPXY], s);
+    s = fma(__ldg(&coef[18 * N + p]), z[q + kPX + kPXY], s);
+  }
+  return s;
+}
+
+template <int S>
+__global__ void __launch_bounds__(kSdThreads, 2)
+    k_subdomain_local(Dims d, const double* __restrict__ coef, const double* __restrict__ dinv,
+                      const double* __restrict__ r, double* __restrict__ z, const int* skip, int nbx, int nby) {
+  if (skip != nullptr && *skip != 0) return;
+  __shared__ double buf[2][kPad];
+  const int box = blockIdx.x;
+  const int x0 = (box % nbx) * kSdBX, y0 = ((box / nbx) % nby) * kSdBY, z0 = (box / (nbx * nby)) * kSdBZ;
+  const int wx = min(kSdBX, d.nx - x0), wy = min(kSdBY, d.ny - y0), wz = min(kSdBZ, d.nz - z0);
+  const int ex = wx + 2 * kSdOverlap, ey = wy + 2 * kSdOverlap, ez = wz + 2 * kSdOverlap;
+  const int ne = ex * ey * ez;
+  const int64_t N = d.n;
+  const int64_t plane = (int64_t)d.nx * d.ny;
+  for (int t = threadIdx.x; t < 2 * kPad; t += kSdThreads) (&buf[0][0])[t] = 0.0;
+
+  // this thread's grown-box cells: global index (-1 outside the grid), padded
+  // shared index, r and 1/a_pp
+  int64_t gp[kCellsPer];
+  int pe[kCellsPer];
+  double rv[kCellsPer], dv[kCellsPer];
+#pragma unroll
+  for (int i = 0; i < kCellsPer; ++i) {
+    const int e = threadIdx.x + i * kSdThreads;
+    gp[i] = -1;
+    pe[i] = 0;
+    rv[i] = 0.0;
+    dv[i] = 0.0;
+    if (e < ne) {
+      const int a = e % ex, b = (e / ex) % ey, c = e / (ex * ey);
+      pe[i] = (a + 1) + kPX * ((b + 1) + kPY * (c + 1));
+      const int gi = sd_wrap(x0 - kSdOverlap + a, d.nx, d.px);
+      const int gj = sd_wrap(y0 - kSdOverlap + b, d.ny, d.py);
+      const int gk = sd_wrap(z0 - kSdOverlap + c, d.nz, d.pz);
+      if (gi >= 0 && gj >= 0 && gk >= 0) {
+        gp[i] = (int64_t)gi + (int64_t)d.nx * gj + plane * gk;
+        rv[i] = __ldg(&r[gp[i]]);
+        dv[i] = __ldg(&dinv[gp[i]]);
+      }
+    }
+  }
+  __syncthreads();
+  // sweep 1 from z = 0
+#pragma unroll
+  for (int i = 0; i < kCellsPer; ++i)
+    if (gp[i] >= 0) buf[0][pe[i]] = __dmul_rn(kSdOmega, __dmul_rn(dv[i], rv[i]));
+  __syncthreads();
+  // sweeps 2 .. kSdSweeps-1 over the whole grown box
+  int cur = 0;
+  for (int sw = 1; sw < kSdSweeps - 1; ++sw) {
+    const double* za = buf[cur];
+    double* zb = buf[cur ^ 1];
+#pragma unroll
+    for (int i = 0; i < kCellsPer; ++i) {
+      if (gp[i] < 0) continue;
+      const double s = sd_row<S>(coef, N, gp[i], za, pe[i]);
+      const double u = __dmul_rn(dv[i], rv[i] - s);
+      zb[pe[i]] = fma(kSdOmega, u, za[pe[i]]);
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  // the last sweep on the box's own cells only, written to z
+  const double* za = buf[cur];
+  const int nown = wx * wy * wz;
+  for (int e = threadIdx.x; e < nown; e += kSdThreads) {
+    const int a = e % wx, b = (e / wx) % wy, c = e / (wx * wy);
+    const int64_t p = (int64_t)(x0 + a) + (int64_t)d.nx * (y0 + b) + plane * (z0 + c);
+    const int q = (a + 1 + kSdOverlap) + kPX * ((b + 1 + kSdOverlap) + kPY * (c + 1 + kSdOverlap));
+    const double s = sd_row<S>(coef, N, p, za, q);
+    const double u = __dmul_rn(__ldg(&dinv[p]), __ldg(&r[p]) - s);
+    z[p] = fma(kSdOmega, u, za[q]);
+  }
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_add(int64_t n, const double* __restrict__ v, double* __restrict__ x) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = x[i] + __ldg(&v[i]);
+}
+
+}  // namespace
+
+int64_t subdomain_boxes(const Dims& d) {
+  return (int64_t)((d.nx + kSdBX - 1) / kSdBX) * ((d.ny + kSdBY - 1) / kSdBY) * ((d.nz + kSdBZ - 1) / kSdBZ);
+}
+
+cudaError_t launch_subdomain_local(const Dims& d, int S, const double* coef, const double* dinv, const double* r,
+                                   double* z, const int* skip, cudaStream_t st) {
+  const int nbx = (d.nx + kSdBX - 1) / kSdBX, nby = (d.ny + kSdBY - 1) / kSdBY;
+  const int64_t nb = subdomain_boxes(d);
+  if (nb <= 0 || nb > 0x7fffffff) return cudaErrorInvalidValue;
+  if (S == 7)
+    k_subdomain_local<7><<<(unsigned)nb, kSdThreads, 0, st>>>(d, coef, dinv, r, z, skip, nbx, nby);
+  else
+    k_subdomain_local<19><<<(unsigned)nb, kSdThreads, 0, st>>>(d, coef, dinv, r, z, skip, nbx, nby);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add(int64_t n, const double* v, double* x, cudaStream_t st) {
+  k_add<<<red_blocks(n), kRedThreads, 0, st>>>(n, v, x);
+  return cudaGetLastError();
+}
+
+}  // namespace rk

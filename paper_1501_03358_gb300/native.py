@@ -23,6 +23,7 @@ RK_GMRES, RK_RGCROT, RK_RBICGSTAB, RK_HYBRID = 0, 1, 2, 3
 MODES = {"GMRES": RK_GMRES, "rGCROT": RK_RGCROT, "rBiCGStab": RK_RBICGSTAB, "BiCGStab": RK_RBICGSTAB,
          "hybrid": RK_HYBRID}
 RK_FP64, RK_MIXED, RK_DF = 0, 1, 2
+RK_PC_JACOBI, RK_PC_SUBDOMAIN = 0, 1
 
 # Every exported symbol that include/rk.h declares.
 EXPORTS = ("rk_last_error", "rk_version", "rk_context_create", "rk_context_destroy", "rk_create_problem",
@@ -41,7 +42,8 @@ class rk_solve_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("m", ctypes.c_int32), ("k", ctypes.c_int32),
                 ("max_matvec", ctypes.c_int32), ("hybrid_switch", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("update_recycle", ctypes.c_int32), ("hybrid_refresh", ctypes.c_int32),
-                ("hybrid_fallback", ctypes.c_int32), ("precond_side", ctypes.c_int32)]
+                ("hybrid_fallback", ctypes.c_int32), ("precond_side", ctypes.c_int32),
+                ("precond", ctypes.c_int32)]
 
 
 class rk_solve_info(ctypes.Structure):

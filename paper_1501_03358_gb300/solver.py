@@ -146,13 +146,17 @@ class Problem:
         N.check(self.lib.rk_create_problem(ctx.handle, ctypes.byref(g), self.S, _dptr(coef), _stream_ptr(stream),
                                            ctypes.byref(self._h)))
 
-    def apply(self, v, precond=True, stream=None, fp32=False, df=False, left=False):
+    def apply(self, v, precond=True, stream=None, fp32=False, df=False, left=False, subdomain=None):
         """A M^{-1} v (precond), A v, M^{-1} A v (left), or with fp32 / df the
         FP32 / double-float operator (with the preconditioner) of the "mixed"
-        / "df" precisions."""
+        / "df" precisions. subdomain="minv": M^{-1} v, "left": M^{-1} A v with
+        the sub-domain preconditioner."""
         v = _f64_cuda(v, (self.n,))
         y = torch.empty_like(v)
-        mode = 2 if fp32 else (3 if df else (4 if left else (1 if precond else 0)))
+        if subdomain is not None:
+            mode = {"minv": 5, "left": 6}[subdomain]
+        else:
+            mode = 2 if fp32 else (3 if df else (4 if left else (1 if precond else 0)))
         N.check(self.lib.rk_apply(self._h, _dptr(v), _dptr(y), mode, _stream_ptr(stream)))
         return y
 
@@ -204,11 +208,11 @@ class Problem:
 
     def solve(self, b, x0=None, tol=1e-8, m=40, k=20, mode="rGCROT", max_matvec=2000, hybrid_switch=5,
               update_recycle=True, out=None, stream=None, check_status=False, precision="fp64", hybrid_refresh=0,
-              hybrid_fallback=0, precond_side="right"):
+              hybrid_fallback=0, precond_side="right", precond="jacobi"):
         """Solve A x = b; returns (x, info dict). x0 defaults to 0."""
         b, out = self._bx(b, x0, out)
         prm = _params(tol, m, k, mode, max_matvec, hybrid_switch, update_recycle, precision, hybrid_refresh,
-                      hybrid_fallback, precond_side)
+                      hybrid_fallback, precond_side, precond)
         info = N.rk_solve_info()
         rc = self.lib.rk_solve(self._h, _dptr(b), _dptr(out), ctypes.byref(prm), ctypes.byref(info),
                                _stream_ptr(stream))
@@ -263,11 +267,12 @@ class Problem:
 
 
 def _params(tol, m, k, mode, max_matvec, hybrid_switch, update_recycle, precision, hybrid_refresh=0,
-            hybrid_fallback=0, precond_side="right"):
+            hybrid_fallback=0, precond_side="right", precond="jacobi"):
     prec = {"fp64": N.RK_FP64, "mixed": N.RK_MIXED, "df": N.RK_DF}[precision]
     side = {"right": 0, "left": 1}[precond_side]
+    pc = {"jacobi": N.RK_PC_JACOBI, "subdomain": N.RK_PC_SUBDOMAIN}[precond]
     prm = N.rk_solve_params(float(tol), int(m), int(k), int(max_matvec), int(hybrid_switch), N.MODES[mode],
-                            prec, 1 if update_recycle else 0, int(hybrid_refresh), int(hybrid_fallback), side)
+                            prec, 1 if update_recycle else 0, int(hybrid_refresh), int(hybrid_fallback), side, pc)
     if mode == "BiCGStab":
         prm.k = 0
     return prm
@@ -291,13 +296,13 @@ def solve_batch(problems, bs, outs=None, params=None, nthreads=0, stream=None, c
         xl.append(x)
     plist = params if params is not None else [kw] * n
     defaults = dict(tol=1e-8, m=40, k=20, mode="rGCROT", max_matvec=2000, hybrid_switch=5, update_recycle=True,
-                    precision="fp64", hybrid_refresh=0, hybrid_fallback=0, precond_side="right")
+                    precision="fp64", hybrid_refresh=0, hybrid_fallback=0, precond_side="right", precond="jacobi")
     prm = (N.rk_solve_params * n)()
     for i in range(n):
         d = dict(defaults, **plist[i])
         prm[i] = _params(d["tol"], d["m"], d["k"], d["mode"], d["max_matvec"], d["hybrid_switch"],
                          d["update_recycle"], d["precision"], d["hybrid_refresh"], d["hybrid_fallback"],
-                         d["precond_side"])
+                         d["precond_side"], d["precond"])
     infos = (N.rk_solve_info * n)()
     H = (ctypes.c_void_p * n)(*[p._h.value for p in problems])
     B = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bl])

@@ -1,0 +1,164 @@
+"""The sub-domain Jacobi preconditioner of Sec. 2.1 on the GPU against the
+oracle (Stencil.schwarz and the solvers with prec="schwarz").
+
+Bars: M^{-1} v and M^{-1} A v bit for bit (the same FP64 operations in the
+same order on both sides, over grids whose boxes have ragged tails, wrap onto
+themselves on periodic axes, or are smaller than one box); solves as in
+test_gpu_parity (tolerance met, x within the kappa bound of the oracle's,
+matrix-vector products within the oracle's own spread under rounding-level
+perturbations of b).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from problems import Grid, make_config, random_operator, porous_skew_19pt
+from problems.operators import sphere_pack
+from problems.fields import rng_for
+import oracle
+from test_gpu_parity import ctx, gpu_problem, t, kappa, mv_slack, check_solve  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+SD_GRIDS = [
+    ((37, 19, 11), (False, False, False)),  # ragged boxes on every axis
+    ((40, 16, 17), (True, False, True)),
+    ((33, 9, 7), (True, True, True)),
+    ((16, 8, 8), (True, True, True)),       # one box whose grown box wraps onto itself
+    ((2, 3, 4), (True, True, False)),       # smaller than one box
+    ((1, 1, 1), (False, False, False)),
+    ((70, 9, 20), (False, True, False)),
+]
+
+
+@pytest.mark.parametrize("S", [7, 19])
+@pytest.mark.parametrize("dims,per", SD_GRIDS)
+def test_subdomain_apply_bit_exact(ctx, S, dims, per):
+    g = Grid(*dims, per)
+    coef = random_operator(g, S, np.random.default_rng(hash((S, dims, 11)) % 2**32))
+    prob = gpu_problem(ctx, g, coef)
+    op = oracle.Stencil(g, coef)
+    v = np.random.default_rng(6).standard_normal(g.n)
+    assert np.array_equal(prob.apply(t(v), subdomain="minv").cpu().numpy(), op.schwarz(v))
+    assert np.array_equal(prob.apply(t(v), subdomain="left").cpu().numpy(), op.schwarz(op.apply(v)))
+
+
+def test_subdomain_apply_full_size(ctx):
+    """The 128^3 channel operator (2048 boxes): M^{-1} v and M^{-1} A v bit
+    for bit over the whole field (the oracle's C loops finish in seconds)."""
+    cfg = make_config(2, size=128)
+    prob = gpu_problem(ctx, cfg.grid, cfg.coef)
+    op = oracle.Stencil(cfg.grid, cfg.coef)
+    v = cfg.rhs(0)
+    assert np.array_equal(prob.apply(t(v), subdomain="minv").cpu().numpy(), op.schwarz(v))
+    assert np.array_equal(prob.apply(t(v), subdomain="left").cpu().numpy(), op.schwarz(op.apply(v)))
+
+
+def check_sd_left(op, b, xg, info, xo, io, tol, slack, kap):
+    rel = np.linalg.norm(op.residual(b, xg)) / np.linalg.norm(b)
+    assert rel <= tol * 1.0000001 and info["status"] == 0, (rel, info)
+    assert abs(rel - info["relres_true"]) <= 1e-6 * rel + 1e-15
+    assert np.linalg.norm(xg - xo) <= max(1e-6, 2.0 * kap * tol) * np.linalg.norm(xo)
+    assert abs(info["matvecs"] - io["matvecs"]) <= slack, (info["matvecs"], io["matvecs"], slack)
+
+
+@pytest.mark.parametrize("cfg_id,size,m", [(1, 12, 30), (2, 12, 40)])
+def test_subdomain_left_gmres_parity(ctx, cfg_id, size, m):
+    cfg = make_config(cfg_id, size=size)
+    prob = gpu_problem(ctx, cfg.grid, cfg.coef)
+    op = oracle.Stencil(cfg.grid, cfg.coef)
+    b = cfg.rhs(0)
+    x, info = prob.solve(t(b), tol=1e-8, m=m, k=0, mode="GMRES", max_matvec=4000, precond_side="left",
+                         precond="subdomain")
+    xo, io = oracle.gmres(op, b, tol=1e-8, m=m, max_matvec=4000, left=True, prec="schwarz")
+    run = lambda bb: oracle.gmres(op, bb, tol=1e-8, m=m, max_matvec=4000, left=True, prec="schwarz")[1]
+    slack, _ = mv_slack(run, b, io["matvecs"])
+    check_sd_left(op, b, x.cpu().numpy(), info, xo, io, 1e-8, slack, kappa(cfg.grid, cfg.coef))
+
+
+@pytest.mark.parametrize("cfg_id,size,m,k,steps", [(1, 12, 30, 10, 3), (2, 14, 30, 10, 3)])
+def test_subdomain_left_rgcrot_sequence_parity(ctx, cfg_id, size, m, k, steps):
+    """Left rGCROT with the sub-domain preconditioner over a sequence: the
+    solve bars, and M^{-1} A U = C, C^T C = I for the carried pair."""
+    cfg = make_config(cfg_id, size=size)
+    prob = gpu_problem(ctx, cfg.grid, cfg.coef)
+    op = oracle.Stencil(cfg.grid, cfg.coef)
+    kap = kappa(cfg.grid, cfg.coef)
+    seq = oracle.RecyclingSequence(op, mode="rGCROT", m=m, k=k, tol=1e-8, max_matvec=3000, left=True,
+                                   prec="schwarz")
+    for s in range(steps):
+        b = cfg.rhs(s)
+        x, info = prob.solve(t(b), tol=1e-8, m=m, k=k, mode="rGCROT", max_matvec=3000, precond_side="left",
+                             precond="subdomain")
+        U0, C0 = seq.U, seq.C
+        xo, io = seq.solve(b)
+        run = lambda bb: oracle.rgcrot(op, bb, tol=1e-8, m=m, k=k, U=U0, C=C0, max_matvec=3000, left=True,
+                                       prec="schwarz")[3]
+        slack, _ = mv_slack(run, b, io["matvecs"])
+        check_sd_left(op, b, x.cpu().numpy(), info, xo, io, 1e-8, slack, kap)
+        U, C = prob.get_recycle()
+        U, C = U.cpu().numpy().T, C.cpu().numpy().T
+        BU = np.stack([op.schwarz(op.apply(u)) for u in U.T], axis=1)
+        assert np.linalg.norm(BU - C) <= 1e-10 * np.linalg.norm(C) * max(1.0, np.abs(cfg.coef).max())
+        assert np.linalg.norm(C.T @ C - np.eye(C.shape[1])) <= 1e-11
+
+
+@pytest.mark.parametrize("with_space", [False, True])
+def test_subdomain_rbicgstab_parity(ctx, with_space):
+    """rBiCGStab right-preconditioned with the sub-domain preconditioner:
+    v = A M^{-1} p, x <- x + M^{-1} x~ (Algorithm 4)."""
+    cfg = make_config(1, size=14)
+    prob = gpu_problem(ctx, cfg.grid, cfg.coef)
+    op = oracle.Stencil(cfg.grid, cfg.coef)
+    U = C = None
+    if with_space:
+        _, U, C, _ = oracle.rgcrot(op, cfg.rhs(0), tol=1e-9, m=20, k=8)
+        prob.set_recycle(t(U.T), t(C.T))
+    b = cfg.rhs(2)
+    x, info = prob.solve(t(b), tol=1e-8, k=8 if with_space else 0, mode="rBiCGStab", max_matvec=3000,
+                         precond="subdomain")
+    xo, io = oracle.rbicgstab(op, b, tol=1e-8, U=U, C=C, max_matvec=3000, prec="schwarz")
+    run = lambda bb: oracle.rbicgstab(op, bb, tol=1e-8, U=U, C=C, max_matvec=3000, prec="schwarz")[1]
+    slack, _ = mv_slack(run, b, io["matvecs"])
+    check_solve(op, b, x.cpu().numpy(), info, xo, io, 1e-8, slack, kappa(cfg.grid, cfg.coef))
+
+
+def test_subdomain_hybrid_sequence(ctx):
+    """Hybrid with the sub-domain preconditioner (Sec. 2.4 with Sec. 2.1's
+    Jacobi preconditioner): left rGCROT for the first solves, then
+    right-preconditioned rBiCGStab with the pair re-formed as A U = C."""
+    n = (20, 12, 10)
+    solid, _ = sphere_pack(n, 2.5, 0.3, rng_for(78, 3), max_attempts=20000)
+    grid, coef = porous_skew_19pt(n, np.where(solid, 1e-4, 1.0), 15.0)
+    prob = gpu_problem(ctx, grid, coef)
+    op = oracle.Stencil(grid, coef)
+    kap = kappa(grid, coef)
+    seq = oracle.RecyclingSequence(op, mode="hybrid", m=20, k=10, tol=1e-8, hybrid_switch=2, max_matvec=3000,
+                                   left=True, prec="schwarz")
+    base = np.random.default_rng(5).standard_normal(grid.n)
+    for s in range(4):
+        b = base + 0.05 * s * np.random.default_rng(100 + s).standard_normal(grid.n)
+        x, info = prob.solve(t(b), tol=1e-8, m=20, k=10, mode="hybrid", hybrid_switch=2, max_matvec=3000,
+                             precond_side="left", precond="subdomain")
+        xo, io = seq.solve(b)
+        xg = x.cpu().numpy()
+        assert info["mode_used"] == (1 if s < 2 else 2) and info["status"] == 0, (s, info)
+        assert np.linalg.norm(op.residual(b, xg)) <= 1e-8 * np.linalg.norm(b) * 1.0000001
+        assert np.linalg.norm(xg - xo) <= max(1e-6, 2.0 * kap * 1e-8) * np.linalg.norm(xo)
+    U, C = prob.get_recycle()
+    U, C = U.cpu().numpy().T, C.cpu().numpy().T
+    AU = np.stack([op.apply(u) for u in U.T], axis=1)
+    assert np.linalg.norm(AU - C) <= 1e-10 * np.linalg.norm(C) * np.abs(coef).max()
+
+
+def test_subdomain_invalid_combinations(ctx):
+    from paper_1501_03358_gb300.native import RKError
+    cfg = make_config(1, size=8)
+    prob = gpu_problem(ctx, cfg.grid, cfg.coef)
+    b = t(cfg.rhs(0))
+    for kw in (dict(mode="rGCROT", precond_side="right"), dict(mode="GMRES", precond_side="right"),
+               dict(mode="hybrid", precond_side="right"), dict(mode="rGCROT", precond_side="left", precision="df"),
+               dict(mode="rBiCGStab", precision="mixed")):
+        with pytest.raises(RKError):
+            prob.solve(b, precond="subdomain", check_status=True, **kw)
