@@ -52,9 +52,14 @@ WORKLOADS = {
 # in double-float; or with those products in FP32
 DTYPES = {"fp64": "f64", "df": "f64+df64-operator", "mixed": "f64+f32-operator"}
 MV_PER_SOLVE = {"channel128": 1500.0, "channel96": 1100.0, "convdiff32": 60.0, "porous192": 400.0}
-# the same with the sub-domain preconditioner (left rGCROT)
-MV_PER_SOLVE_SD = {"channel128": 150.0, "channel96": 110.0, "convdiff32": 10.0, "porous192": 60.0}
-FP64_TFLOPS = 1.25
+# the same with the sub-domain preconditioner (left rGCROT), measured likewise
+MV_PER_SOLVE_SD = {"channel128": 505.0}
+# the preconditioner each workload is defined with: the channel names the
+# paper's "Jacobi preconditioner" (the sub-domain one of Sec. 2.1), the
+# convection-diffusion case point Jacobi
+PRECOND_DEFAULT = {"channel128": "subdomain", "channel96": "subdomain"}
+FP64_TOPS = 0.625                    # nominal 1.25 TFLOP/s FP64, one DFMA = 2 flops
+FP32_TOPS = 152 * 128 * 2.07e9 / 1e12  # FP32 lanes x SMs x max SM clock
 
 
 def load_peaks():
@@ -156,13 +161,18 @@ def _oracle_prec(precond):
     return dict(left=True, prec="schwarz") if precond == "subdomain" else {}
 
 
-def subdomain_flops(grid, S):
-    """FP64 flops of one launch of the sub-domain local-sweep kernel (an FMA
-    counts 2, a multiply or add 1): per grown-box cell inside the grid, the
-    first sweep from zero is omega (dinv r) (2 flops) and each later sweep
-    s = a_0 z + sum fma(a_t, z_t), u = dinv (r - s), z += omega u (2S + 3);
-    the last sweep runs on owned cells only. Grown-box cells inside the grid
-    factor per axis, so the sums over boxes are products of per-axis sums."""
+def subdomain_ops(grid, S, df):
+    """Arithmetic of one launch of the sub-domain local-sweep kernel, per
+    grown-box cell inside the grid: the first sweep from zero is
+    omega (dinv r), each later sweep s = a_0 z + sum_t a_t z_t,
+    u = dinv (r - s), z += omega u, and the last sweep runs on owned cells
+    only. FP64 variant: FP64 pipe instructions (S + 3 per cell-sweep, 2 in the
+    first sweep). Double-float variant: FP32 pipe instructions of its
+    error-free transformations (TwoProduct 4, lazy multiply-add 12,
+    renormalisation 3, add 11, multiply 7, fused multiply-add 15: 112 per
+    cell-sweep for 7 bands, 262 for 19; 14 in the first sweep). Grown-box
+    cells inside the grid factor per axis, so the sums over boxes are
+    products of per-axis sums."""
     box, ov, sweeps = (16, 8, 8), 1, 5
     dims = (grid.nx, grid.ny, grid.nz)
     g = []
@@ -175,8 +185,11 @@ def subdomain_flops(grid, S):
             tot += w + lo + hi
         g.append(tot)
     grown = g[0] * g[1] * g[2]
-    per_cell = 2 * S + 3
-    return 2.0 * grown + (sweeps - 2) * per_cell * grown + per_cell * grid.n
+    if df:
+        first, per_cell = 14, (4 + 12 * (S - 1) + 3 * (1 if S == 7 else 3) + 11 + 7 + 15)
+    else:
+        first, per_cell = 2, S + 3
+    return float(first * grown + (sweeps - 2) * per_cell * grown + per_cell * grid.n)
 
 
 def oracle_cycle_sample(cfg, mode, m, k, cycles=2, precond="jacobi"):
@@ -202,30 +215,38 @@ def oracle_cycle_sample(cfg, mode, m, k, cycles=2, precond="jacobi"):
 def run_reference(args, ws, rank):
     if rank != 0:
         return
+    mv = (MV_PER_SOLVE_SD if args.precond == "subdomain" else MV_PER_SOLVE).get(args.workload)
+    if mv is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"no measured products per solve for "
+                          f"{args.workload} with the {args.precond} preconditioner"}), flush=True)
+        return
     from problems import make_config
     cid, edge, mode, m, k = WORKLOADS[args.workload]
     cfg = make_config(cid, size=edge)
-    # warm-up: build the recycle space with one cycle
     import oracle
     op = oracle.Stencil(cfg.grid, cfg.coef)
     b = cfg.rhs(0)
     pk = _oracle_prec(args.precond)
-    _, U, C, _ = oracle.rgcrot(op, b, tol=1e-14, m=m, k=k, max_matvec=m, **pk)
+    # each step: one cycle cut at ms Arnoldi steps (the sub-domain
+    # preconditioner costs the oracle about 0.3 s per product at 128^3)
+    ms = m if args.precond != "subdomain" else min(m, 10)
+    # warm-up: build the recycle space
+    _, U, C, _ = oracle.rgcrot(op, b, tol=1e-14, m=m, k=k, max_matvec=ms, **pk)
     for _ in range(max(args.warmup - 1, 0)):
-        _, U, C, _ = oracle.rgcrot(op, b, tol=1e-14, m=m, k=k, U=U, C=C, max_matvec=m, **pk)
+        _, U, C, _ = oracle.rgcrot(op, b, tol=1e-14, m=m, k=k, U=U, C=C, max_matvec=ms, **pk)
     times = []
     t_all = time.perf_counter()
     for s in range(args.steps):
         t0 = time.perf_counter()
-        _, U, C, info = oracle.rgcrot(op, b, tol=1e-14, m=m, k=k, U=U, C=C, max_matvec=m, **pk)
+        _, U, C, info = oracle.rgcrot(op, b, tol=1e-14, m=m, k=k, U=U, C=C, max_matvec=ms, **pk)
         times.append((time.perf_counter() - t0) / max(info["matvecs"], 1))
     total = time.perf_counter() - t_all
     per_mv = statistics.mean(times)
-    mv = (MV_PER_SOLVE_SD if args.precond == "subdomain" else MV_PER_SOLVE)[args.workload]
     value = 1.0 / (per_mv * mv)
     threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    sample = (f"each step: one rGCROT({m},{k}) cycle ({m} matvecs, recycle dim {k}) of step 0 of {args.workload}; "
-              f"solves/s = 1/(s per matvec x {mv:.0f} matvecs per solve)")
+    sample = (f"each step: one rGCROT({m},{k}) cycle cut at {ms} matvecs (recycle space carried), step 0 of "
+              f"{args.workload}, {args.precond} preconditioner; solves/s = 1/(s per matvec x {mv:.0f} matvecs "
+              f"per solve measured on the GPU arm)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -341,14 +362,20 @@ def run_ours(args, ws, rank, local):
             "peak_source": peak_src,
             "launches": d["launches"], "avg_launch_us": 1000.0 * d["ms"] / max(d["launches"], 1),
             "bytes_per_launch": d["bytes"] / max(d["launches"], 1)}
-    if dname == "subdomain_local":
-        # bound by the FP64 pipe: FP64 flops per launch over the nominal FP64
-        # rate (1.25 TFLOP/s at the 2070 MHz maximum SM clock)
-        fl = subdomain_flops(cfg.grid, cfg.S)
-        tf = fl * d["launches"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
-        roof.update({"bound": "alu", "achieved": tf, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
-                     "frac": tf / FP64_TFLOPS, "traffic": None, "traffic_source": None,
-                     "peak_source": "nominal FP64 rate", "flops_per_launch": fl})
+    if dname in ("subdomain_local", "subdomain_df"):
+        # bound by the arithmetic pipe: FP64 instructions against the nominal
+        # DFMA rate (1.25 TFLOP/s / 2 = 0.625 T instructions/s), or, for the
+        # double-float variant, FP32 instructions against 128 FP32 lanes per SM
+        # per clock (152 SMs at 2.07 GHz: 40.3 T instructions/s)
+        dfk = dname == "subdomain_df"
+        ops = subdomain_ops(cfg.grid, cfg.S, dfk)
+        peak = FP32_TOPS if dfk else FP64_TOPS
+        ach = ops * d["launches"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
+        roof.update({"bound": "alu", "achieved": ach, "peak": peak,
+                     "unit": "T FP32 instr/s" if dfk else "T FP64 instr/s", "frac": ach / peak,
+                     "traffic": None, "traffic_source": None,
+                     "peak_source": "FP32 lanes x SMs x max SM clock" if dfk else "nominal FP64 rate / 2 per DFMA",
+                     "instr_per_launch": ops})
     total_model = sum(i["model_bytes"] for i in tinfo)
     solver_gbs = total_model / (ms * 1e-3) / 1e9
     launches = int(sum(v["launches"] for v in prof.values()))
@@ -627,9 +654,10 @@ def main():
                     help="fp64: FP64 operator, double-float projections; df: double-float operator in the "
                          "recurrences; mixed: FP32 inner operator (A11). "
                          "Default fp64 for the single-sequence workloads, mixed for batch64 and serve")
-    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "subdomain"],
+    ap.add_argument("--precond", default=None, choices=["jacobi", "subdomain"],
                     help="jacobi: right point Jacobi; subdomain: Sec. 2.1's sub-domain Jacobi preconditioner "
-                         "(5 damped local sweeps on overlapping 16x8x8 boxes, one global sweep), left in rGCROT")
+                         "(5 damped local sweeps on overlapping 16x8x8 boxes, one global sweep), left in rGCROT. "
+                         "Default: subdomain for the channel workloads, jacobi otherwise")
     ap.add_argument("--nprob", type=int, default=None, help="problems (batch64: 64; serve: 12)")
     ap.add_argument("--threads", type=int, default=0, help="rk_solve_batch worker threads (0: min(n, 16))")
     ap.add_argument("--requests", type=int, default=60, help="serve: number of timed requests")
@@ -643,6 +671,8 @@ def main():
     ws, rank, local = dist_init()
     if args.nprob is None:
         args.nprob = 64 if args.workload == "batch64" else 12
+    if args.precond is None:
+        args.precond = PRECOND_DEFAULT.get(args.workload, "jacobi")
     if args.impl == "reference":
         if args.workload in ("batch64", "serve"):
             if rank == 0:

@@ -121,10 +121,13 @@ typedef struct {
                             always right-preconditioned (Sec. 2.1); a stored recycle space is
                             converted (C re-derived from U by CholQR2) when a solve uses the other
                             side. Left with RK_MIXED: RK_E_INVALID */
-  int32_t precond;       /* rk_preconditioner. RK_PC_SUBDOMAIN: precision RK_FP64 only; GMRES,
-                            rGCROT and the hybrid's rGCROT phase left-preconditioned only
-                            (precond_side = 1), rBiCGStab right-preconditioned (x <- x + M^{-1} x~);
-                            otherwise RK_E_INVALID */
+  int32_t precond;       /* rk_preconditioner. RK_PC_SUBDOMAIN: precision RK_FP64 (the operator and
+                            the preconditioner in FP64, bit-exact order) or RK_DF (the products of
+                            the recurrences with the double-float operator and a double-float
+                            evaluation of the same preconditioner; residuals, M^{-1} b and the final
+                            M^{-1} x~ in FP64); GMRES, rGCROT and the hybrid's rGCROT phase
+                            left-preconditioned only (precond_side = 1), rBiCGStab
+                            right-preconditioned (x <- x + M^{-1} x~); otherwise RK_E_INVALID */
 } rk_solve_params;
 
 typedef struct {
@@ -214,9 +217,11 @@ int rk_solve(rk_problem* p, const double* b, double* x, const rk_solve_params* p
  * the result widened to FP64; 3: the double-float operator of RK_DF,
  * y = A_df (M_df^{-1} v) with v rounded to double-float and the result
  * widened to FP64 (exact); 5: y = M^{-1} v and 6: y = M^{-1} (A v) with the
- * sub-domain preconditioner (RK_PC_SUBDOMAIN), y must not alias v. Other
- * values: RK_E_INVALID. The operator copies of modes 2 and 3 and the
- * workspace of modes 5 and 6 are made on first use (and freed by
+ * sub-domain preconditioner (RK_PC_SUBDOMAIN); 7 and 8: the same with the
+ * double-float variant of RK_DF (v rounded to double-float, the result
+ * widened to FP64); for 5-8 y must not alias v. Other
+ * values: RK_E_INVALID. The operator copies of modes 2, 3, 7 and 8 and the
+ * workspace of modes 5-8 are made on first use (and freed by
  * rk_problem_release).
  * And r = b - A x. All vectors device, N doubles.
  */
@@ -306,7 +311,7 @@ int rk_import_recycle(rk_problem* p, const void* buf, int64_t bytes, void* strea
 /*
  * Opt-in kernel timing of the solves of a problem: CUDA events on the solve's
  * stream around every launch, summed per kernel class ("spmv", "residual",
- * "dots", "update", "gemm_rows", "gram", "small", "bicg", "harmonic_ritz", "subdomain_local") with the class's
+ * "dots", "update", "gemm_rows", "gram", "small", "bicg", "harmonic_ritz", "subdomain_local", "subdomain_df") with the class's
  * algorithmic HBM bytes (the library's byte model of each launch).
  * rk_profile_enable resets the counters; rk_profile_read copies up to cap
  * entries to out (host) and sets *count to the number of classes.

@@ -78,6 +78,14 @@ int64_t subdomain_boxes(const Dims& d);
 // written); the global sweep is launch_jsweep(z, r).
 cudaError_t launch_subdomain_local(const Dims& d, int S, const double* coef, const double* dinv, const double* r,
                                    double* z, const int* skip, cudaStream_t st);
+// The double-float variant (RK_DF): bands and 1/a_pp from their double-float
+// copies, r FP64 or double-float (r_df), z double-float.
+cudaError_t launch_subdomain_local_dd(const Dims& d, int S, const float2* coefd, const float2* dinvd, const void* r,
+                                      bool r_df, float2* z, const int* skip, cudaStream_t st);
+// y = z + omega dinv (b - A z) in double-float (z, b double-float; y
+// double-float or FP64)
+cudaError_t launch_jsweep_dd(const Dims& d, int S, const float2* coefd, const float2* dinvd, const float2* z,
+                             const float2* b, void* y, bool y_df, const int* skip, cudaStream_t st);
 // x += v
 cudaError_t launch_add(int64_t n, const double* v, double* x, cudaStream_t st);
 

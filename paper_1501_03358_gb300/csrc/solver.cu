@@ -105,8 +105,9 @@ int alloc_into(rk_context* c, T** out, size_t count) {
 
 // Opt-in per-kernel-class timing: CUDA events recorded on the solve's stream
 // around every launch, reduced at the solve's synchronisation points.
-enum ProfClass { PC_SPMV = 0, PC_RESID, PC_DOTS, PC_UPDATE, PC_GEMM, PC_GRAM, PC_SMALL, PC_BICG, PC_HRITZ, PC_SUBDOMAIN, PC_COUNT };
-static const char* kProfNames[PC_COUNT] = {"spmv", "residual", "dots", "update", "gemm_rows", "gram", "small", "bicg", "harmonic_ritz", "subdomain_local"};
+enum ProfClass { PC_SPMV = 0, PC_RESID, PC_DOTS, PC_UPDATE, PC_GEMM, PC_GRAM, PC_SMALL, PC_BICG, PC_HRITZ, PC_SUBDOMAIN, PC_SUBDOMAIN_DF, PC_COUNT };
+static const char* kProfNames[PC_COUNT] = {"spmv", "residual", "dots", "update", "gemm_rows", "gram", "small", "bicg", "harmonic_ritz", "subdomain_local",
+                                             "subdomain_df"};
 
 struct Profiler {
   bool on = false;
@@ -195,7 +196,7 @@ struct rk_problem {
   float* dinv32 = nullptr;        // mixed precision: FP32 1/a_pp
   float2* coefdf = nullptr;       // RK_DF: double-float copy of the bands
   float2* dinvdf = nullptr;       // RK_DF: double-float 1/a_pp
-  double* sdw = nullptr;          // sub-domain preconditioner: 2 FP64 vectors (local result, operand)
+  double* sdw = nullptr;          // sub-domain preconditioner: 3 vectors (local result, operands)
   double* bicg = nullptr;
   // small
   double* small = nullptr;
@@ -502,11 +503,33 @@ int ensure_dfop(rk_problem* p, cudaStream_t st) {
   return RK_OK;
 }
 
-// Workspace of the sub-domain preconditioner (Sec. 2.1): two FP64 vectors.
+// Workspace of the sub-domain preconditioner (Sec. 2.1): three vectors of
+// 8-byte words (FP64 or double-float).
 int ensure_subdomain(rk_problem* p) {
   if (p->sdw) return RK_OK;
   p->drop_graphs();
-  return alloc_into(p->ctx, &p->sdw, (size_t)2 * p->ld);
+  return alloc_into(p->ctx, &p->sdw, (size_t)3 * p->ld);
+}
+
+// y = M_df^{-1} r with the double-float variant of the sub-domain
+// preconditioner (RK_DF): r FP64 (rounded to double-float into sdw[1]) or
+// double-float; y double-float or FP64. r must not alias sdw[0].
+int subdomain_df_launch(rk_problem* p, const void* r, bool r_df, void* y, bool y_df, const int* skip,
+                        cudaStream_t st) {
+  float2* z0 = (float2*)p->sdw;
+  const float2* rd = (const float2*)r;
+  if (!r_df) {
+    float2* t = (float2*)(p->sdw + p->ld);
+    RK_CUDA(launch_round_df(p->n, (const double*)r, t, st));
+    rd = t;
+  }
+  {
+    ProfScope ps(&p->prof, PC_SUBDOMAIN_DF, 8.0 * (p->S + 3) * (double)p->n, st);
+    RK_CUDA(launch_subdomain_local_dd(p->d, p->S, p->coefdf, p->dinvdf, rd, true, z0, skip, st));
+  }
+  ProfScope ps(&p->prof, PC_SPMV, 8.0 * (p->S + 4) * (double)p->n, st);
+  RK_CUDA(launch_jsweep_dd(p->d, p->S, p->coefdf, p->dinvdf, z0, rd, y, y_df, skip, st));
+  return RK_OK;
 }
 
 // y = M^{-1} r with the sub-domain preconditioner (Sec. 2.1): the local
@@ -534,6 +557,22 @@ int ensure_operator(rk_problem* p, int precision, cudaStream_t st) {
 // (RK_MIXED) or the double-float operator (RK_DF)
 int opapply_launch(rk_problem* p, int precision, const void* v, bool v_df, void* y, bool y_df, const int* skip,
                    cudaStream_t st, bool left = false, int pc = RK_PC_JACOBI) {
+  if (pc == RK_PC_SUBDOMAIN && precision == RK_DF) {
+    // the same products with the double-float operator and preconditioner
+    float2* t = (float2*)(p->sdw + p->ld);
+    if (left) {
+      {
+        ProfScope ps(&p->prof, PC_SPMV, 8.0 * (p->S + 2) * (double)p->n, st);
+        RK_CUDA(launch_stencil_dd(p->d, p->S, ST_PLAIN, p->coefdf, p->dinvdf, v, v_df, t, true, skip, st));
+      }
+      return subdomain_df_launch(p, t, true, y, y_df, skip, st);
+    }
+    float2* z = (float2*)(p->sdw + 2 * p->ld);
+    RK_TRY(subdomain_df_launch(p, v, v_df, z, true, skip, st));
+    ProfScope ps(&p->prof, PC_SPMV, 8.0 * (p->S + 2) * (double)p->n, st);
+    RK_CUDA(launch_stencil_dd(p->d, p->S, ST_PLAIN, p->coefdf, p->dinvdf, z, true, y, y_df, skip, st));
+    return RK_OK;
+  }
   if (pc == RK_PC_SUBDOMAIN) {
     // M^{-1} (A v) or A (M^{-1} v) with the sub-domain preconditioner (FP64)
     double* t = p->sdw + p->ld;
@@ -1148,18 +1187,23 @@ int rk_apply(const rk_problem* p, const double* v, double* y, int32_t precond, v
     RK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     return RK_OK;
   }
-  if (precond == 5 || precond == 6) {
+  if (precond >= 5 && precond <= 8) {
     if (v == y) return fail(RK_E_INVALID, "y must not alias v");
     rk_problem* pm = const_cast<rk_problem*>(p);
     RK_TRY(ensure_subdomain(pm));
+    if (precond >= 7) RK_TRY(ensure_dfop(pm, (cudaStream_t)stream));
     if (precond == 5)
       RK_TRY(subdomain_launch(pm, v, y, false, nullptr, nullptr, (cudaStream_t)stream));
-    else
+    else if (precond == 6)
       RK_TRY(opapply_launch(pm, RK_FP64, v, false, y, false, nullptr, (cudaStream_t)stream, true, RK_PC_SUBDOMAIN));
+    else if (precond == 7)
+      RK_TRY(subdomain_df_launch(pm, v, false, y, false, nullptr, (cudaStream_t)stream));
+    else
+      RK_TRY(opapply_launch(pm, RK_DF, v, false, y, false, nullptr, (cudaStream_t)stream, true, RK_PC_SUBDOMAIN));
     RK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     return RK_OK;
   }
-  if (precond < 0 || precond > 6) return fail(RK_E_INVALID, "precond must be 0..6");
+  if (precond < 0 || precond > 8) return fail(RK_E_INVALID, "precond must be 0..8");
   RK_CUDA(launch_stencil(p->d, p->S, precond == 4 ? ST_LEFT : (precond ? ST_PREC : ST_PLAIN), p->coef, p->dinv, v, nullptr, y, nullptr,
                          nullptr, nullptr, nullptr, (cudaStream_t)stream));
   RK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
@@ -1369,7 +1413,8 @@ int rk_solve(rk_problem* p, const double* b, double* x, const rk_solve_params* p
     return fail(RK_E_INVALID, "left preconditioning is not available with RK_MIXED");
   if (prm.precond != RK_PC_JACOBI && prm.precond != RK_PC_SUBDOMAIN) return fail(RK_E_INVALID, "unknown precond");
   if (prm.precond == RK_PC_SUBDOMAIN) {
-    if (prm.precision != RK_FP64) return fail(RK_E_INVALID, "the sub-domain preconditioner runs in RK_FP64 only");
+    if (prm.precision == RK_MIXED)
+      return fail(RK_E_INVALID, "the sub-domain preconditioner runs in RK_FP64 or RK_DF");
     if (prm.mode != RK_RBICGSTAB && prm.precond_side != 1)
       return fail(RK_E_INVALID, "the sub-domain preconditioner is applied from the left in GMRES and rGCROT");
     RK_TRY(ensure_subdomain(p));
@@ -1487,7 +1532,7 @@ int rk_problem_memory(const rk_problem* p, int64_t* device_bytes) {
   if (p->dinv32) b += 4 * ld;
   if (p->coefdf) b += 8 * S * n;
   if (p->dinvdf) b += 8 * ld;
-  if (p->sdw) b += 8 * 2 * ld;
+  if (p->sdw) b += 8 * 3 * ld;
   if (p->bicg) b += 8 * 7 * ld;
   b += 8 * (p->small_n + p->eta_n + (p->part ? p->part_n : 0));
   *device_bytes = (int64_t)b;

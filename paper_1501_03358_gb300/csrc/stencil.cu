@@ -237,7 +237,8 @@ template <int S, int MODE, typename VT, typename YT>
 __global__ void __launch_bounds__(kTX* kTY) k_stencil_dd(Dims d, const float2* __restrict__ coef,
                                                          const float2* __restrict__ dinv,
                                                          const VT* __restrict__ v, YT* __restrict__ y,
-                                                         const int* skip, int zchunk) {
+                                                         const int* skip, int zchunk,
+                                                         const float2* __restrict__ bv, float2 om) {
   if (skip != nullptr && *skip != 0) return;
   __shared__ float2 sz[3][kTY + 2][kTX + 2];
   const int tx = threadIdx.x & (kTX - 1), ty = threadIdx.x / kTX;
@@ -339,6 +340,11 @@ __global__ void __launch_bounds__(kTX* kTY) k_stencil_dd(Dims d, const float2* _
       df_renorm(s, c);
       float2 wv = make_float2(s, c);
       if (MODE == ST_LEFT) wv = df_mul(wv, __ldg(&dinv[p]));
+      if (MODE == ST_JSWEEP) {
+        // z + omega dinv (b - A z), the damped point-Jacobi sweep
+        const float2 u = df_mul(__ldg(&dinv[p]), df_sub(__ldg(&bv[p]), wv));
+        wv = df_fma(om, u, sz[sc][cy][cx]);
+      }
       st_df<YT>(y, p, wv);
     }
     __syncthreads();
@@ -478,6 +484,26 @@ cudaError_t launch_stencil_df(const Dims& d, int S, int mode, const double* coef
   return cudaGetLastError();
 }
 
+cudaError_t launch_jsweep_dd(const Dims& d, int S, const float2* coefd, const float2* dinvd, const float2* z,
+                             const float2* b, void* y, bool y_df, const int* skip, cudaStream_t st) {
+  dim3 grid;
+  int zchunk;
+  stencil_grid(d, grid, zchunk, 4);
+  const dim3 block(kTX * kTY);
+  // omega as a double-float pair
+  const float oh = (float)kSdOmega;
+  const float2 om = make_float2(oh, (float)(kSdOmega - (double)oh));
+#define RK_SJD(SS, YT)                                                                                              \
+  k_stencil_dd<SS, ST_JSWEEP, float2, YT><<<grid, block, 0, st>>>(d, coefd, dinvd, z, (YT*)y, skip, zchunk, b, om)
+  if (S == 7) {
+    if (y_df) RK_SJD(7, float2); else RK_SJD(7, double);
+  } else {
+    if (y_df) RK_SJD(19, float2); else RK_SJD(19, double);
+  }
+#undef RK_SJD
+  return cudaGetLastError();
+}
+
 cudaError_t launch_round_df(int64_t n, const double* src, float2* dst, cudaStream_t st) {
   k_round_df<<<red_blocks(n), kRedThreads, 0, st>>>(n, src, dst);
   return cudaGetLastError();
@@ -490,8 +516,9 @@ cudaError_t launch_stencil_dd(const Dims& d, int S, int mode, const float2* coef
   int zchunk;
   stencil_grid(d, grid, zchunk, 4);
   const dim3 block(kTX * kTY);
-#define RK_SDD(SS, MM, VT, YT) \
-  k_stencil_dd<SS, MM, VT, YT><<<grid, block, 0, st>>>(d, coefd, dinvd, (const VT*)v, (YT*)y, skip, zchunk)
+#define RK_SDD(SS, MM, VT, YT)                                                                                 \
+  k_stencil_dd<SS, MM, VT, YT><<<grid, block, 0, st>>>(d, coefd, dinvd, (const VT*)v, (YT*)y, skip, zchunk, nullptr, \
+                                                       make_float2(0.f, 0.f))
 #define RK_SDD_TYPES(SS, MM)                         \
   if (v_df && y_df) RK_SDD(SS, MM, float2, float2); \
   else if (v_df) RK_SDD(SS, MM, float2, double);    \

@@ -55,6 +55,47 @@ def test_subdomain_apply_full_size(ctx):
     assert np.array_equal(prob.apply(t(v), subdomain="left").cpu().numpy(), op.schwarz(op.apply(v)))
 
 
+def sd_df_bound(op, coef, S, v, y, left):
+    """Elementwise bar of the double-float variant against the FP64 oracle.
+    One sweep z' = z + omega D^-1 (r - A_loc z) in double-float errs by at
+    most (S + 12) 2^-46 (|z| + omega |D^-1| (|r| + |A| |z|)) per cell: the
+    band sum within the (S + 8) 2^-46 sum |a| |z| of the double-float
+    stencil, four more rounded operations, and the double-float rounding of
+    the bands and 1/a_pp (2^-48 each). Later sweeps multiply an error by the
+    iteration matrix I - omega D^-1 A_loc, whose infinity norm is at most
+    g = max_p |1 - omega| + omega sum_{t>0} |a_t| / |a_p| (1 for diagonally
+    dominant rows), and the left product adds the double-float A v. Six
+    sweeps (five local and the global one): the bar is
+    6 (S + 12) 2^-46 max(1, g)^6 max_p (|z| + omega |D^-1| (|r| + |A| |z|)),
+    with z the oracle's result and r its right-hand side."""
+    w = 2.0 / 3.0
+    a0 = np.abs(coef[0])
+    g = float(np.max(abs(1 - w) + w * np.abs(coef[1:]).sum(axis=0) / a0))
+    r = op.apply(v) if left else v
+    absA = oracle.Stencil(op.grid, np.abs(coef))
+    mag = np.abs(y) + w / a0 * (np.abs(r) + absA.apply(np.abs(y)))
+    if left:
+        mag = mag + w / a0 * absA.apply(np.abs(v))
+    return 6 * (S + 12) * 2.0 ** -46 * max(1.0, g) ** 6 * float(mag.max())
+
+
+@pytest.mark.parametrize("S", [7, 19])
+@pytest.mark.parametrize("dims,per", SD_GRIDS[:4])
+def test_subdomain_df_within_bound(ctx, S, dims, per):
+    """The double-float variant (precision "df") against the FP64 oracle,
+    within the derived bar of sd_df_bound."""
+    g = Grid(*dims, per)
+    coef = random_operator(g, S, np.random.default_rng(hash((S, dims, 12)) % 2**32))
+    prob = gpu_problem(ctx, g, coef)
+    op = oracle.Stencil(g, coef)
+    v = np.random.default_rng(7).standard_normal(g.n)
+    for mode, left in (("minv_df", False), ("left_df", True)):
+        yo = op.schwarz(op.apply(v) if left else v)
+        yg = prob.apply(t(v), subdomain=mode).cpu().numpy()
+        err = float(np.abs(yg - yo).max())
+        assert err <= sd_df_bound(op, coef, S, v, yo, left), (mode, err)
+
+
 def check_sd_left(op, b, xg, info, xo, io, tol, slack, kap):
     rel = np.linalg.norm(op.residual(b, xg)) / np.linalg.norm(b)
     assert rel <= tol * 1.0000001 and info["status"] == 0, (rel, info)
@@ -77,8 +118,9 @@ def test_subdomain_left_gmres_parity(ctx, cfg_id, size, m):
     check_sd_left(op, b, x.cpu().numpy(), info, xo, io, 1e-8, slack, kappa(cfg.grid, cfg.coef))
 
 
+@pytest.mark.parametrize("precision", ["fp64", "df"])
 @pytest.mark.parametrize("cfg_id,size,m,k,steps", [(1, 12, 30, 10, 3), (2, 14, 30, 10, 3)])
-def test_subdomain_left_rgcrot_sequence_parity(ctx, cfg_id, size, m, k, steps):
+def test_subdomain_left_rgcrot_sequence_parity(ctx, cfg_id, size, m, k, steps, precision):
     """Left rGCROT with the sub-domain preconditioner over a sequence: the
     solve bars, and M^{-1} A U = C, C^T C = I for the carried pair."""
     cfg = make_config(cfg_id, size=size)
@@ -90,7 +132,7 @@ def test_subdomain_left_rgcrot_sequence_parity(ctx, cfg_id, size, m, k, steps):
     for s in range(steps):
         b = cfg.rhs(s)
         x, info = prob.solve(t(b), tol=1e-8, m=m, k=k, mode="rGCROT", max_matvec=3000, precond_side="left",
-                             precond="subdomain")
+                             precond="subdomain", precision=precision)
         U0, C0 = seq.U, seq.C
         xo, io = seq.solve(b)
         run = lambda bb: oracle.rgcrot(op, bb, tol=1e-8, m=m, k=k, U=U0, C=C0, max_matvec=3000, left=True,
@@ -104,8 +146,9 @@ def test_subdomain_left_rgcrot_sequence_parity(ctx, cfg_id, size, m, k, steps):
         assert np.linalg.norm(C.T @ C - np.eye(C.shape[1])) <= 1e-11
 
 
+@pytest.mark.parametrize("precision", ["fp64", "df"])
 @pytest.mark.parametrize("with_space", [False, True])
-def test_subdomain_rbicgstab_parity(ctx, with_space):
+def test_subdomain_rbicgstab_parity(ctx, with_space, precision):
     """rBiCGStab right-preconditioned with the sub-domain preconditioner:
     v = A M^{-1} p, x <- x + M^{-1} x~ (Algorithm 4)."""
     cfg = make_config(1, size=14)
@@ -117,7 +160,7 @@ def test_subdomain_rbicgstab_parity(ctx, with_space):
         prob.set_recycle(t(U.T), t(C.T))
     b = cfg.rhs(2)
     x, info = prob.solve(t(b), tol=1e-8, k=8 if with_space else 0, mode="rBiCGStab", max_matvec=3000,
-                         precond="subdomain")
+                         precond="subdomain", precision=precision)
     xo, io = oracle.rbicgstab(op, b, tol=1e-8, U=U, C=C, max_matvec=3000, prec="schwarz")
     run = lambda bb: oracle.rbicgstab(op, bb, tol=1e-8, U=U, C=C, max_matvec=3000, prec="schwarz")[1]
     slack, _ = mv_slack(run, b, io["matvecs"])
@@ -158,7 +201,7 @@ def test_subdomain_invalid_combinations(ctx):
     prob = gpu_problem(ctx, cfg.grid, cfg.coef)
     b = t(cfg.rhs(0))
     for kw in (dict(mode="rGCROT", precond_side="right"), dict(mode="GMRES", precond_side="right"),
-               dict(mode="hybrid", precond_side="right"), dict(mode="rGCROT", precond_side="left", precision="df"),
+               dict(mode="hybrid", precond_side="right"), dict(mode="rGCROT", precond_side="left", precision="mixed"),
                dict(mode="rBiCGStab", precision="mixed")):
         with pytest.raises(RKError):
             prob.solve(b, precond="subdomain", check_status=True, **kw)
