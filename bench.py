@@ -1,10 +1,12 @@
 #!/usr/bin/env python
 """Benchmark: solves/s of a time-step sequence on the 128^3 wall-refined
 channel (7-point, periodic x/z, Neumann walls, one pinned cell), rGCROT(40,20)
-with the recycle space carried from step to step, relative tolerance 1e-8.
+with the recycle space carried from step to step, relative tolerance 1e-8 on
+the true residual, preconditioned from the left by the sub-domain Jacobi
+preconditioner of Sec. 2.1 (`--precond jacobi`: right point Jacobi).
 
 One "step" is one solve of one time step (all of the solver's phases: stencil
-products with the Jacobi preconditioner, projections onto the recycle space,
+products with the preconditioner, projections onto the recycle space,
 Arnoldi orthogonalisation, cycle updates and the harmonic Ritz recycle
 update). Before the W warm-up steps, an untimed pre-roll runs the first steps
 of the sequence with a matvec cap until one converges: the first solves of a
@@ -371,9 +373,15 @@ def run_ours(args, ws, rank, local):
         ops = subdomain_ops(cfg.grid, cfg.S, dfk)
         peak = FP32_TOPS if dfk else FP64_TOPS
         ach = ops * d["launches"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
+        # DRAM traffic per launch from one ncu capture of the FP64 kernel on
+        # the 96^3 channel (63.8 MB read + 2.8 MB written for 884,736 cells),
+        # scaled by the cells of this grid; the double-float variant reads the
+        # same bytes (63.9 + 2.7 MB)
+        traffic = (63.8 + 2.8) * 1e6 / 96 ** 3 * cfg.grid.n
         roof.update({"bound": "alu", "achieved": ach, "peak": peak,
                      "unit": "T FP32 instr/s" if dfk else "T FP64 instr/s", "frac": ach / peak,
-                     "traffic": None, "traffic_source": None,
+                     "traffic": traffic,
+                     "traffic_source": "ncu DRAM bytes of one launch on the 96^3 channel x cells of this grid",
                      "peak_source": "FP32 lanes x SMs x max SM clock" if dfk else "nominal FP64 rate / 2 per DFMA",
                      "instr_per_launch": ops})
     total_model = sum(i["model_bytes"] for i in tinfo)
