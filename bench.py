@@ -546,6 +546,59 @@ def run_batch(args, ws, rank, local):
     ctx.close()
 
 
+def run_switch_sweep(args, ws, rank, local):
+    """The hybrid's switch-step experiment (Sec. 4.3, Table 8) replayed on the
+    porous configuration: for each switch step n, a fresh problem solves the
+    first T steps of the time-step sequence with the hybrid (rGCROT(40,20)
+    for solves 1..n, then rBiCGStab with the recycle space frozen); reports
+    per n the summed solve time (CUDA events), products, and whether every
+    solve converged. Right-hand sides are generated once, resident in HBM."""
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__ as g
+    g.build()
+    from problems import make_config
+    from paper_1501_03358_gb300 import Context, Problem
+    cfg = make_config(3, size=args.sweep_edge)
+    T = args.sweep_steps
+    rhs = [torch.from_numpy(cfg.rhs(t)).cuda() for t in range(T)]
+    ctx = Context()
+    stream = torch.cuda.current_stream()
+    kw = dict(tol=1e-8, m=40, k=20, mode="hybrid", max_matvec=args.max_matvec, precision=args.precision or "fp64",
+              precond=args.precond, precond_side="left" if args.precond == "subdomain" else "right")
+    x = torch.zeros(cfg.n, dtype=torch.float64, device="cuda")
+    results = []
+    for n in range(1, args.sweep_max + 1):
+        prob = Problem(ctx, cfg.grid, torch.from_numpy(cfg.coef))
+        per = []
+        for t in range(T):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            x.zero_()
+            e0.record(stream)
+            _, info = prob.solve(rhs[t], out=x, hybrid_switch=n, **kw)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            per.append((e0.elapsed_time(e1), info))
+        results.append({"switch": n, "ms_total": sum(p[0] for p in per),
+                        "ms_rgcrot": sum(p[0] for p in per if p[1]["mode_used"] == 1),
+                        "ms_rbicgstab": sum(p[0] for p in per if p[1]["mode_used"] == 2),
+                        "matvecs": [p[1]["matvecs"] for p in per],
+                        "all_converged": all(p[1]["status"] == 0 for p in per),
+                        "relres_max": max(p[1]["relres_true"] for p in per)})
+        prob.close()
+    best = min((r for r in results if r["all_converged"]), key=lambda r: r["ms_total"], default=None)
+    line = {"metric": "hybrid switch-step sweep: summed solve time of the first T steps per switch step n",
+            "unit": "ms", "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "porous", "grid": [args.sweep_edge] * 3, "stencil": cfg.S, "steps": T,
+                       "solver": "hybrid rGCROT(40,20) -> rBiCGStab", "tol": 1e-8, "precond": args.precond,
+                       "precision": kw["precision"], "solid_fraction": getattr(cfg, "solid_fraction", None)},
+            "results": results, "best_switch": best["switch"] if best else None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_serve(args, ws, rank, local):
     """Serving loop (reduced config 5): resident problems of mixed sizes
     (channel and porous generators alternating), requests = the next
@@ -666,6 +719,11 @@ def main():
                     help="jacobi: right point Jacobi; subdomain: Sec. 2.1's sub-domain Jacobi preconditioner "
                          "(5 damped local sweeps on overlapping 16x8x8 boxes, one global sweep), left in rGCROT. "
                          "Default: subdomain for the channel workloads, jacobi otherwise")
+    ap.add_argument("--switch-sweep", action="store_true",
+                    help="replay the hybrid switch-step sweep (Table 8) on the porous configuration")
+    ap.add_argument("--sweep-edge", type=int, default=192, help="switch sweep: grid edge")
+    ap.add_argument("--sweep-steps", type=int, default=10, help="switch sweep: time steps per switch step")
+    ap.add_argument("--sweep-max", type=int, default=9, help="switch sweep: largest switch step")
     ap.add_argument("--nprob", type=int, default=None, help="problems (batch64: 64; serve: 12)")
     ap.add_argument("--threads", type=int, default=0, help="rk_solve_batch worker threads (0: min(n, 16))")
     ap.add_argument("--requests", type=int, default=60, help="serve: number of timed requests")
@@ -680,7 +738,7 @@ def main():
     if args.nprob is None:
         args.nprob = 64 if args.workload == "batch64" else 12
     if args.precond is None:
-        args.precond = PRECOND_DEFAULT.get(args.workload, "jacobi")
+        args.precond = "subdomain" if args.switch_sweep else PRECOND_DEFAULT.get(args.workload, "jacobi")
     if args.impl == "reference":
         if args.workload in ("batch64", "serve"):
             if rank == 0:
@@ -692,6 +750,8 @@ def main():
         run_batch(args, ws, rank, local)
     elif args.workload == "serve":
         run_serve(args, ws, rank, local)
+    elif args.switch_sweep:
+        run_switch_sweep(args, ws, rank, local)
     else:
         if args.precision is None:
             args.precision = "fp64"
