@@ -18,6 +18,8 @@
 // with a ring of zeros around them, so neighbour reads need no bounds tests.
 // The bands, r and 1/a_pp are read from global memory (they stay in L1/L2
 // across the sweeps); the kernel is bound by the FP64 pipe, not by HBM.
+#include <mutex>
+
 #include "rk_internal.h"
 #include "rk_device.cuh"
 #include "rk_df.cuh"
@@ -412,12 +414,13 @@ cudaError_t launch_subdomain_local_dd(const Dims& d, int S, const float2* coefd,
   const float oh = (float)kSdOmega;
   const float2 om = make_float2(oh, (float)(kSdOmega - (double)oh));
   if (S == 7) {
-    static bool attr = false;
-    if (!attr) {
+    // the 161 KB of dynamic shared memory need an opt-in, once per process
+    // (the batch executor launches from several host threads)
+    static std::once_flag attr;
+    std::call_once(attr, [] {
       cudaFuncSetAttribute(k_subdomain_local_dd7s<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSdsSmem);
       cudaFuncSetAttribute(k_subdomain_local_dd7s<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSdsSmem);
-      attr = true;
-    }
+    });
     if (r_df)
       k_subdomain_local_dd7s<float2><<<(unsigned)nb, kSdsThreads, kSdsSmem, st>>>(d, coefd, dinvd, (const float2*)r, z,
                                                                                  skip, nbx, nby, om);

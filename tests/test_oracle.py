@@ -110,12 +110,14 @@ def test_rgcrot_k0_is_gmres(name, grid, coef, b):
     assert np.array_equal(x1, x2) and i1["matvecs"] == i2["matvecs"] and U is None
 
 
+@pytest.mark.parametrize("prec", ["jacobi", "schwarz"])
 @pytest.mark.parametrize("name,grid,coef,b", PROBS, ids=[p[0] for p in PROBS])
-def test_rbicgstab_empty_is_bicgstab(name, grid, coef, b):
-    """Algorithm 4 with an empty recycle space is Algorithm 2 (note under Alg. 4)."""
+def test_rbicgstab_empty_is_bicgstab(name, grid, coef, b, prec):
+    """Algorithm 4 with an empty recycle space is Algorithm 2 (note under
+    Alg. 4), with either preconditioner."""
     op = Stencil(grid, coef)
-    x1, i1 = bicgstab(op, b, tol=1e-10)
-    x2, i2 = rbicgstab(op, b, tol=1e-10, max_restarts=0)
+    x1, i1 = bicgstab(op, b, tol=1e-10, prec=prec)
+    x2, i2 = rbicgstab(op, b, tol=1e-10, max_restarts=0, prec=prec)
     assert np.array_equal(x1, x2) and i1["matvecs"] == i2["matvecs"]
 
 
@@ -339,13 +341,14 @@ def test_left_preconditioned_solvers_reach_dense_lu(name, grid, coef, b, mode):
     assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= max(1e-9, 10 * np.linalg.cond(A) * tol)
 
 
+@pytest.mark.parametrize("prec", ["jacobi", "schwarz"])
 @pytest.mark.parametrize("name,grid,coef,b", PROBS, ids=[p[0] for p in PROBS])
-def test_left_rgcrot_k0_is_left_gmres(name, grid, coef, b):
+def test_left_rgcrot_k0_is_left_gmres(name, grid, coef, b, prec):
     """Without a recycle space, left-preconditioned Algorithm 3 is
-    left-preconditioned Algorithm 1, bit for bit."""
+    left-preconditioned Algorithm 1, bit for bit, with either preconditioner."""
     op = Stencil(grid, coef)
-    x1, i1 = gmres(op, b, tol=1e-10, m=7, left=True)
-    x2, U, C, i2 = rgcrot(op, b, tol=1e-10, m=7, k=0, left=True)
+    x1, i1 = gmres(op, b, tol=1e-10, m=7, left=True, prec=prec)
+    x2, U, C, i2 = rgcrot(op, b, tol=1e-10, m=7, k=0, left=True, prec=prec)
     assert np.array_equal(x1, x2) and i1["matvecs"] == i2["matvecs"] and U is None
 
 
@@ -472,3 +475,52 @@ def test_schwarz_preconditioner_is_linear_and_converges_to_the_inverse():
     # damped Jacobi on the whole (unsplit) problem: spectral radius 0.992 here
     zi = op.schwarz(r1, box=(g.nx, g.ny, g.nz), overlap=1, sweeps=4000, omega=2.0 / 3.0)
     assert np.linalg.norm(A @ zi - r1) <= 1e-12 * np.linalg.norm(r1)
+
+
+@pytest.mark.parametrize("name,grid,coef,b", PROBS, ids=[p[0] for p in PROBS])
+@pytest.mark.parametrize("mode", ["GMRES", "rGCROT", "rBiCGStab"])
+def test_schwarz_preconditioned_solvers_reach_dense_lu(name, grid, coef, b, mode):
+    """GMRES(m) and rGCROT(m,k) left-preconditioned and rBiCGStab
+    right-preconditioned by the sub-domain preconditioner reach the dense LU
+    solution: the true residual meets the tolerance and x is within kappa(A)
+    times it of A^{-1} b."""
+    op = Stencil(grid, coef)
+    A = dense_matrix(grid, coef)
+    xs = sla.solve(A, b)
+    tol = 1e-11
+    if mode == "GMRES":
+        x, info = gmres(op, b, tol=tol, m=12, max_matvec=4000, left=True, prec="schwarz")
+    elif mode == "rGCROT":
+        x, _, _, info = rgcrot(op, b, tol=tol, m=12, k=6, max_matvec=4000, left=True, prec="schwarz")
+    else:
+        x, info = rbicgstab(op, b, tol=tol, max_matvec=4000, prec="schwarz")
+    assert info["status"] == oracle.OK, info["status"]
+    rel = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+    rounding = 64 * 2.0 ** -53 * np.linalg.norm(np.abs(A) @ np.abs(x)) / np.linalg.norm(b)
+    assert rel <= tol + rounding
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= max(1e-9, 10 * np.linalg.cond(A) * tol)
+
+
+def test_left_stop_test_is_on_the_true_residual():
+    """Reading N12. Scaling the rows of A x = b by s leaves the point-Jacobi
+    left-preconditioned system M^-1 A x = M^-1 b unchanged (M = diag(A)
+    scales with the rows) but not ||b - A x|| / ||b||. With s spread over six
+    decades, the left solve of the unscaled system returns an x whose
+    preconditioned residual meets the tolerance while the scaled system's
+    true residual does not; the solve of the scaled system continues until
+    its true residual does (checked with dense matrices)."""
+    c = make_config(1, size=6)
+    g, coef, b = c.grid, c.coef, c.rhs(0)
+    s = 10.0 ** np.random.default_rng(0).uniform(-3.0, 3.0, g.n)
+    coef_s, b_s = coef * s[None, :], b * s
+    A, A_s = dense_matrix(g, coef), dense_matrix(g, coef_s)
+    tol = 1e-8
+    xu, iu = gmres(Stencil(g, coef), b, tol=tol, m=20, left=True, max_matvec=3000)
+    minv = 1.0 / coef[0]
+    prel = np.linalg.norm(minv * (b - A @ xu)) / np.linalg.norm(minv * b)
+    assert prel <= tol
+    assert np.linalg.norm(b_s - A_s @ xu) / np.linalg.norm(b_s) > tol
+    x, info = gmres(Stencil(g, coef_s), b_s, tol=tol, m=20, left=True, max_matvec=3000)
+    assert info["status"] == oracle.OK
+    assert np.linalg.norm(b_s - A_s @ x) / np.linalg.norm(b_s) <= tol
+    assert info["matvecs"] > iu["matvecs"]
