@@ -10,6 +10,11 @@
 // arithmetic order is fixed:
 //   w = c_0 * z_P;  w = fma(c_s, z_{nb(s)}, w) for s = 1 .. S-1
 // (out-of-domain neighbours contribute fma(0, 0, w)).
+//
+// The same kernels also evaluate the left-preconditioned forms dinv (A v)
+// and dinv (b - A v) (Sec. 2.1, left for GMRES-type solvers), and the global
+// sweep of the sub-domain Jacobi preconditioner, one damped point-Jacobi
+// sweep y = z + omega dinv (r - A z) (ST_JSWEEP), in the same band order.
 #include "rk_internal.h"
 #include "rk_device.cuh"
 #include "rk_df.cuh"
