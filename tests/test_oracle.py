@@ -524,3 +524,30 @@ def test_left_stop_test_is_on_the_true_residual():
     assert info["status"] == oracle.OK
     assert np.linalg.norm(b_s - A_s @ x) / np.linalg.norm(b_s) <= tol
     assert info["matvecs"] > iu["matvecs"]
+
+
+def test_schwarz_hybrid_sequence_sides_and_stop_test():
+    """The hybrid with the sub-domain preconditioner (Sec. 2.4 with Sec. 2.1's
+    sides): left rGCROT for the first solves (carried pair M^-1 A U = C with
+    M^-1 the dense sub-domain matrix), then right rBiCGStab after the pair is
+    re-formed as A U = C; every solve meets the true-residual tolerance."""
+    name, grid, coef, b = PROBS[2]
+    op = Stencil(grid, coef)
+    A = dense_matrix(grid, coef)
+    Md = _schwarz_dense(grid, coef, (16, 8, 8), 1, 5, 2.0 / 3.0)
+    seq = oracle.RecyclingSequence(op, mode="hybrid", m=8, k=4, tol=1e-10, hybrid_switch=2, max_matvec=3000,
+                                   left=True, prec="schwarz")
+    rng = np.random.default_rng(11)
+    modes = []
+    for s in range(4):
+        bs = b + 0.05 * s * rng.standard_normal(b.size)
+        x, info = seq.solve(bs)
+        modes.append(info["mode"])
+        assert info["status"] == oracle.OK
+        assert np.linalg.norm(bs - A @ x) <= 1e-10 * np.linalg.norm(bs) * (1 + 1e-6)
+        if s == 0:  # after a left rGCROT solve: M^-1 A U = C
+            B = Md @ A
+            assert np.linalg.norm(B @ seq.U - seq.C) <= 1e-10 * np.linalg.norm(B, 2) * np.linalg.norm(seq.U)
+    assert modes == ["rGCROT", "rGCROT", "rBiCGStab", "rBiCGStab"]
+    assert np.linalg.norm(A @ seq.U - seq.C) <= 1e-10 * np.linalg.norm(A, 2) * np.linalg.norm(seq.U)
+    assert np.linalg.norm(seq.C.T @ seq.C - np.eye(seq.C.shape[1])) <= 1e-11
