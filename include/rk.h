@@ -353,9 +353,11 @@ int rk_harmonic_ritz(rk_context* ctx, int32_t n, const double* G, const double* 
  * process exits), and calls no cudaMalloc, cudaFree or allocating routine.
  *
  * Same arguments and results as rk_dots (out[q] = Q_q^T w, q < nq, in the
- * same fixed reduction order, so the two agree bit for bit), without a
- * context. Limit: nq <= 64 columns (larger nq returns RK_E_INVALID with a
- * message); any n. The first call on a device looks up the scratch array's
+ * same fixed reduction order, so the two agree bit for bit; nq = 0 does
+ * nothing, as there), without a context. Limit: nq <= 64 columns (larger nq
+ * returns RK_E_INVALID with a message); any n. Like every entry point, the
+ * call returns after its work on `stream` has completed (it synchronises
+ * that stream). The first call on a device looks up the scratch array's
  * device address (cudaGetSymbolAddress) and clears its counter, which
  * synchronises that device: make the first call on each device before any
  * stream capture. All calls share the one scratch array, whose contents

@@ -79,7 +79,7 @@ class _Prec:
 def _stop_test(left, op, b, x, rho, tolp, toltrue):
     """The stop test of GMRES and rGCROT (Sec. 4: the L2 norm of the
     residual, ||b - A x|| <= tol ||b||). Right preconditioning: the cycle's
-    residual is the true one. Left (reading N12): the cycles work on
+    residual is the true one. Left: the cycles work on
     M^{-1}(b - A x) with the target tolp; the true residual decides, and when
     the preconditioned target is met but the true residual is not, the target
     is scaled down by the observed shortfall. Returns (converged, tolp,

@@ -789,14 +789,13 @@ int dots2_blocks(int64_t n) {
   return (int)b;
 }
 
-// one-time attribute setup (thread-safe static initialisation); also run
-// when a problem is created, so that it never happens inside a graph capture
+// one-time attribute setup per device; also run when a problem is created,
+// so that it never happens inside a graph capture
 void dfblas_prepare() {
-  static const bool attr = [] {
+  static std::atomic<uint64_t> done{0};
+  once_per_device(done, [] {
     cudaFuncSetAttribute(k_dfdots2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kD2Smem);
-    return true;
-  }();
-  (void)attr;
+  });
 }
 
 cudaError_t launch_dfdots2(const DFDots2Args& a, cudaStream_t st) {
@@ -817,12 +816,11 @@ cudaError_t launch_dfupdate2(const DFUpdate2Args& a, cudaStream_t st) {
 
 template <typename OT, int CB>
 static cudaError_t gemm2_go(const DFGemmArgs& a, int tr, int ncp, int threads, size_t smem, cudaStream_t st) {
-  // one-time attribute setup (thread-safe static initialisation)
-  static const bool attr = [] {
+  // one-time attribute setup per device
+  static std::atomic<uint64_t> done{0};
+  once_per_device(done, [] {
     cudaFuncSetAttribute(k_dfgemm2<OT, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    return true;
-  }();
-  (void)attr;
+  });
   const int64_t ntiles = (a.n + tr - 1) / tr;
   const int64_t cap = (int64_t)kNumSM * 4;
   const int blocks = (int)(ntiles < cap ? ntiles : cap);
@@ -887,12 +885,11 @@ cudaError_t launch_dfgram(const DFGramArgs& a, cudaStream_t st) {
   const int nblk = nbq * nbl;
   const int sx = ((np + 3) / 4) * 4 + 1, sy = ((a.nu + 3) / 4) * 4 + 1;
   const size_t tiles = ((size_t)kGramTR * (sx + sy) + kGramTR) * sizeof(float2);
-  // one-time attribute setup (thread-safe static initialisation)
-  static const bool attr = [] {
+  // one-time attribute setup per device
+  static std::atomic<uint64_t> done{0};
+  once_per_device(done, [] {
     cudaFuncSetAttribute(k_dfgram2, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    return true;
-  }();
-  (void)attr;
+  });
   const int blocks = gram_blocks(a.n);
   for (int ob0 = 0; ob0 < nblk; ob0 += 256) {
     const int nob = nblk - ob0 < 256 ? nblk - ob0 : 256;

@@ -375,11 +375,10 @@ bool dfgemm_tc_supported(const DFGemmArgs& a, bool out_df) {
 }
 
 void dfgemm_tc_prepare() {
-  static const bool attr = [] {
+  static std::atomic<uint64_t> done{0};
+  once_per_device(done, [] {
     cudaFuncSetAttribute(k_dfgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
-    return true;
-  }();
-  (void)attr;
+  });
 }
 
 cudaError_t launch_dfgemm_tc(const DFGemmArgs& a, void* ws, int* err, cudaStream_t st) {

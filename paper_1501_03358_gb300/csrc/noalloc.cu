@@ -59,7 +59,8 @@ int setup_device(int dev, DevScratch** out) {
 
 extern "C" int rk_dots_noalloc(int64_t n, int32_t nq, const double* Q, int64_t ld, const double* w, double* out,
                                void* stream) {
-  if (!w || !out || n <= 0 || nq < 1 || ld < n || !Q) return fail(RK_E_INVALID, "bad argument to rk_dots_noalloc");
+  if (!w || !out || n <= 0 || nq < 0 || (nq > 0 && !Q) || ld < n)
+    return fail(RK_E_INVALID, "bad argument to rk_dots_noalloc");
   if (nq > kNoAllocMaxCols)
     return fail(RK_E_INVALID, "rk_dots_noalloc: nq = " + std::to_string(nq) + " exceeds the fixed scratch limit of " +
                                   std::to_string(kNoAllocMaxCols) + " columns");

@@ -1,8 +1,10 @@
 // Internal declarations of librk (CUDA, sm_103a). Not part of the ABI.
 #pragma once
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <cstddef>
+#include <mutex>
 
 namespace rk {
 
@@ -32,6 +34,23 @@ inline int red_blocks(int64_t n) {
   if (b < 1) b = 1;
   if (b > kMaxRedBlocks) b = kMaxRedBlocks;
   return (int)b;
+}
+
+// Per-device one-time set-up (the dynamic shared-memory opt-in of
+// cudaFuncSetAttribute applies to the current device only): f runs once for
+// each device on which a call site is reached, under a lock, and later calls
+// on that device skip it; mask holds one bit per device (ordinals < 64).
+std::mutex& setup_mutex();
+template <typename F>
+inline void once_per_device(std::atomic<uint64_t>& mask, F&& f) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  const uint64_t bit = 1ull << (dev & 63);
+  if (mask.load(std::memory_order_acquire) & bit) return;
+  std::lock_guard<std::mutex> lock(setup_mutex());
+  if (mask.load(std::memory_order_acquire) & bit) return;
+  f();
+  mask.fetch_or(bit, std::memory_order_release);
 }
 
 // ---- stencil.cu
@@ -80,6 +99,7 @@ cudaError_t launch_subdomain_local(const Dims& d, int S, const double* coef, con
                                    double* z, const int* skip, cudaStream_t st);
 // The double-float variant (RK_DF): bands and 1/a_pp from their double-float
 // copies, r FP64 or double-float (r_df), z double-float.
+void subdomain_prepare();
 cudaError_t launch_subdomain_local_dd(const Dims& d, int S, const float2* coefd, const float2* dinvd, const void* r,
                                       bool r_df, float2* z, const int* skip, cudaStream_t st);
 // y = z + omega dinv (b - A z) in double-float (z, b double-float; y

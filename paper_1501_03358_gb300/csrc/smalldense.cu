@@ -1180,12 +1180,11 @@ cudaError_t launch_harmonic_ritz(SolveState* s, SmallBuffers b, int kc, int jj, 
   const int n = kc + jj;
   const size_t bytes = hr_doubles_host(n) * sizeof(double);
   const int use_smem = bytes <= kHRSmemMax ? 1 : 0;
-  // one-time attribute setup (thread-safe static initialisation)
-  static const bool attr = [] {
+  // one-time attribute setup per device
+  static std::atomic<uint64_t> done{0};
+  once_per_device(done, [] {
     cudaFuncSetAttribute(k_harmonic_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHRSmemMax);
-    return true;
-  }();
-  (void)attr;
+  });
   k_harmonic_ritz<<<1, kHRThreads, use_smem ? bytes : 0, st>>>(s, b, kc, jj, k, use_smem);
   return cudaGetLastError();
 }
@@ -1194,12 +1193,11 @@ cudaError_t launch_harmonic_ritz_small(int n, const double* G, const double* F, 
                                        int* knew, double* ws, cudaStream_t st) {
   const size_t bytes = hr_doubles_host(n) * sizeof(double);
   const int use_smem = bytes <= kHRSmemMax ? 1 : 0;
-  // one-time attribute setup (thread-safe static initialisation)
-  static const bool attr = [] {
+  // one-time attribute setup per device
+  static std::atomic<uint64_t> done{0};
+  once_per_device(done, [] {
     cudaFuncSetAttribute(k_harmonic_ritz_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHRSmemMax);
-    return true;
-  }();
-  (void)attr;
+  });
   k_harmonic_ritz_small<<<1, kHRThreads, use_smem ? bytes : 0, st>>>(n, G, F, k, QC, PU, knew, ws, use_smem);
   return cudaGetLastError();
 }

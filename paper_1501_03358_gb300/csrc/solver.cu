@@ -40,6 +40,10 @@ int fail(int code, const std::string& msg) {
 }  // namespace
 
 void rk::set_last_error(const char* msg) { g_err = msg; }
+std::mutex& rk::setup_mutex() {
+  static std::mutex mu;
+  return mu;
+}
 
 namespace {
 
@@ -982,7 +986,7 @@ int solve_bicg(rk_problem* p, const double* b, double* x, const rk_solve_params&
       }
       words += kc + 4;
     }
-    // true residual (replacement, R12)
+    // true residual b - A x; above tol, Algorithm 4 restarts from the current x (residual replacement)
     RK_TRY(stencil_launch(p, ST_RESID, x, b, v.r, p->part, p->counter, &p->st->rho2, nullptr, st));
     RK_TRY(sync_state(p, st));
     rel = std::sqrt(p->st_h->rho2) / bnorm;
@@ -1081,6 +1085,7 @@ int rk_create_problem(rk_context* ctx, const rk_grid* grid, int32_t S, const dou
   int r;
   dfblas_prepare();
   dfgemm_tc_prepare();
+  subdomain_prepare();
   if ((r = alloc_into(ctx, &p->coef, (size_t)S * p->n)) != RK_OK) return cleanup(r);
   if ((r = alloc_into(ctx, &p->dinv, (size_t)p->ld)) != RK_OK) return cleanup(r);
   if ((r = alloc_into(ctx, &p->counter, kCounters)) != RK_OK) return cleanup(r);

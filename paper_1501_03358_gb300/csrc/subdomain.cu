@@ -406,6 +406,18 @@ cudaError_t launch_subdomain_local(const Dims& d, int S, const double* coef, con
   return cudaGetLastError();
 }
 
+// The 161 KB of dynamic shared memory of the staged 7-band double-float
+// sweeps need an opt-in, once per device (the batch executor launches from
+// several host threads); also run when a problem is created, so that it
+// never happens inside a graph capture.
+void subdomain_prepare() {
+  static std::atomic<uint64_t> done{0};
+  once_per_device(done, [] {
+    cudaFuncSetAttribute(k_subdomain_local_dd7s<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSdsSmem);
+    cudaFuncSetAttribute(k_subdomain_local_dd7s<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSdsSmem);
+  });
+}
+
 cudaError_t launch_subdomain_local_dd(const Dims& d, int S, const float2* coefd, const float2* dinvd, const void* r,
                                       bool r_df, float2* z, const int* skip, cudaStream_t st) {
   const int nbx = (d.nx + kSdBX - 1) / kSdBX, nby = (d.ny + kSdBY - 1) / kSdBY;
@@ -414,13 +426,7 @@ cudaError_t launch_subdomain_local_dd(const Dims& d, int S, const float2* coefd,
   const float oh = (float)kSdOmega;
   const float2 om = make_float2(oh, (float)(kSdOmega - (double)oh));
   if (S == 7) {
-    // the 161 KB of dynamic shared memory need an opt-in, once per process
-    // (the batch executor launches from several host threads)
-    static std::once_flag attr;
-    std::call_once(attr, [] {
-      cudaFuncSetAttribute(k_subdomain_local_dd7s<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSdsSmem);
-      cudaFuncSetAttribute(k_subdomain_local_dd7s<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSdsSmem);
-    });
+    subdomain_prepare();
     if (r_df)
       k_subdomain_local_dd7s<float2><<<(unsigned)nb, kSdsThreads, kSdsSmem, st>>>(d, coefd, dinvd, (const float2*)r, z,
                                                                                  skip, nbx, nby, om);

@@ -177,6 +177,86 @@ def test_harmonic_ritz_values_dense():
     assert np.allclose(got, ref, atol=1e-9 * scale, rtol=1e-9)
 
 
+def _dense_harmonic_selection(Ahat, Y, k, largest=False):
+    """The harmonic Ritz vectors of the k smallest |theta| by definition, from
+    explicit dense matrices: eigenpairs of ((AY)^T AY, (AY)^T Y) (Y a basis of
+    the space, Ahat = A M^{-1}); the selected set is every eigenvalue with
+    |theta| <= tau for the largest tau that keeps their number <= k (a
+    conjugate pair shares |theta|, so it is in or out whole). Returns the
+    coefficient matrix P (a complex vector enters as its real and imaginary
+    parts), so the selected space is range(Y P). ``largest``: the k largest
+    instead (a deliberately wrong selection, to show the pin can tell)."""
+    AY = Ahat @ Y
+    th, vec = sla.eig(AY.T @ AY, AY.T @ Y)
+    mag = np.abs(th)
+    sel = np.zeros(mag.size, dtype=bool)
+    for t in (np.sort(mag)[::-1] if largest else np.sort(mag)):
+        s = mag >= t * (1 - 1e-9) if largest else mag <= t * (1 + 1e-9)
+        if s.sum() > k:
+            break
+        sel = s
+    cols = []
+    for i in np.nonzero(sel)[0]:
+        if th[i].imag > 0:
+            cols += [vec[:, i].real, vec[:, i].imag]
+        elif th[i].imag == 0:
+            cols.append(vec[:, i].real)
+    return np.stack(cols, axis=1)
+
+
+@pytest.mark.parametrize("which,k,expect", [
+    ("porous", 3, 3),      # real values only below the cut
+    ("porous", 6, 5),      # the 6th and 7th smallest are a conjugate pair: dropped whole
+    ("random19", 2, 1),    # the cut splits the first pair
+    ("random19", 4, 3),    # one real value and one pair kept, the next pair split
+    ("random19", 5, 5),    # one real value and two pairs
+    ("convdiff", 4, 4),
+    ("channel", 5, 5),
+    ("skew19", 3, 3),      # the third smallest |theta| is real, but a pair has a smaller real part
+    ("skew19", 5, 5),
+])
+def test_harmonic_ritz_selection_dense(which, k, expect):
+    """The subspace that the recycle update keeps (Algorithm 3, "update U and
+    C", read as GCRO-DR's harmonic Ritz vectors): range(U_new) must be
+    M^{-1} range(Y P) with Y = [M U, V_j] and P the eigenvectors of the k
+    smallest |theta| of the dense pencil ((AY)^T AY, (AY)^T Y), formed from the
+    explicit matrix A M^{-1} (not from the small G, F of the update), and
+    range(C_new) = A M^{-1} range(Y P). Cases where the k largest values span
+    a different space and where the cut splits a conjugate pair."""
+    if which == "skew19":
+        # strongly nonsymmetric bands: complex values whose real parts order
+        # differently from their moduli
+        grid = Grid(4, 5, 3, (True, False, True))
+        coef = random_operator(grid, 19, np.random.default_rng(5), 0.6)
+        b = np.random.default_rng(5).standard_normal(grid.n)
+    else:
+        name, grid, coef, b = {p[0]: p for p in PROBS}[which]
+    op = Stencil(grid, coef)
+    A = dense_matrix(grid, coef)
+    M, Minv = np.diag(coef[0]), np.diag(1.0 / coef[0])
+    Ahat = A @ Minv
+    _, U, C, _ = rgcrot(op, b, tol=1e-12, m=6, k=4, max_matvec=60)
+    b2 = b + 0.05 * np.random.default_rng(2).standard_normal(b.size)
+    _, _, _, info = rgcrot(op, b2, tol=1e-14, m=6, k=4, U=U, C=C, max_matvec=6, keep_cycle=True, update=False)
+    lc = info["last_cycle"]
+    jj = lc["jj"]
+    Hm = np.zeros((7, 6)); Hm[: jj + 1, :jj] = lc["H"]
+    Bm = np.zeros((4, 6)); Bm[:, :jj] = lc["B"]
+    Vfull = np.zeros((7, grid.n)); Vfull[: jj + 1] = lc["V"]
+    Un, Cn = harmonic_ritz_update(op, lc["U"], lc["C"], Vfull, Bm, Hm, jj, k)
+    Y = np.concatenate([M @ lc["U"], lc["V"][:jj].T], axis=1)
+    P = _dense_harmonic_selection(Ahat, Y, k)
+    assert P.shape[1] == expect
+    assert Un.shape[1] == expect and Cn.shape[1] == expect
+    assert sla.subspace_angles(Un, Minv @ Y @ P).max() <= 1e-10
+    assert sla.subspace_angles(Cn, Ahat @ Y @ P).max() <= 1e-10
+    assert np.linalg.norm(A @ Un - Cn) <= 1e-11 * np.linalg.norm(A, 2) * np.linalg.norm(Un)
+    assert np.linalg.norm(Cn.T @ Cn - np.eye(expect)) <= 1e-12
+    PL = _dense_harmonic_selection(Ahat, Y, k, largest=True)
+    if PL.shape[1] == expect:  # the pin separates the smallest from the largest values
+        assert sla.subspace_angles(Minv @ Y @ PL, Minv @ Y @ P).max() > 0.5
+
+
 def test_exact_recycling():
     """If b lies in range(C) the initial projection onto C solves the
     system: no matrix-vector products and x = U C^T b."""
@@ -502,7 +582,8 @@ def test_schwarz_preconditioned_solvers_reach_dense_lu(name, grid, coef, b, mode
 
 
 def test_left_stop_test_is_on_the_true_residual():
-    """Reading N12. Scaling the rows of A x = b by s leaves the point-Jacobi
+    """The stop test of left solves is on the true residual ||b - A x|| <=
+    tol ||b|| (Sec. 4 states the criterion on the residual norm). Scaling the rows of A x = b by s leaves the point-Jacobi
     left-preconditioned system M^-1 A x = M^-1 b unchanged (M = diag(A)
     scales with the rows) but not ||b - A x|| / ||b||. With s spread over six
     decades, the left solve of the unscaled system returns an x whose
