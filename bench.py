@@ -1,21 +1,25 @@
 #!/usr/bin/env python
-"""Benchmark: solves/s of a time-step sequence on the 128^3 wall-refined
-channel (7-point, periodic x/z, Neumann walls, one pinned cell), rGCROT(40,20)
-with the recycle space carried from step to step, relative tolerance 1e-8 on
-the true residual, preconditioned from the left by the sub-domain Jacobi
-preconditioner of Sec. 2.1 (`--precond jacobi`: right point Jacobi).
+"""Benchmark of the recycling solvers on the synthetic stand-ins of the
+paper's workloads. Default: the porous medium at 192^3 (19-point skewed
+stencil, low-conductivity spheres, Dirichlet inlet/outlet), the hybrid of
+Sec. 2.4 — rGCROT(40,20) for the first 5 time steps, then rBiCGStab reusing
+that k = 20 recycle space — right point Jacobi, relative tolerance 1e-8 on
+the true residual, FP64.
 
-One "step" is one solve of one time step (all of the solver's phases: stencil
+One "step" is one solve of one time step (every phase of the solver: stencil
 products with the preconditioner, projections onto the recycle space,
-Arnoldi orthogonalisation, cycle updates and the harmonic Ritz recycle
-update). Before the W warm-up steps, an untimed pre-roll runs the first steps
-of the sequence with a matvec cap until one converges: the first solves of a
-sequence build the recycle space and can stall until it holds the slowest
-modes of the pinned-cell operator. Then K timed steps; inputs (all right-hand
-sides) are resident in HBM before the timed region, and every step's working
-set (about 1 GB of basis vectors) exceeds the 129 MB L2. Prints one JSON line.
+Arnoldi orthogonalisation or the BiCGStab recurrences, cycle updates and the
+harmonic Ritz recycle update). A hybrid sequence is timed from its first
+step: after W warm-up solves the problem starts a new sequence
+(rk_problem_reset) and the K timed solves are steps 0 .. K-1. The timed
+region runs the production path (captured Arnoldi cycles replayed); the
+per-kernel breakdown comes from a separate untimed replay of the same steps
+with CUDA events around every launch. Inputs (all right-hand sides) are
+resident in HBM before the timed region; every step's working set exceeds
+the 129 MB L2. Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload porous192|channel128|...] [--precision fp64|df|mixed]
   --impl reference times the CPU oracle (FP64, host cores) on a bounded
   sample of the same workload.
 """
@@ -53,15 +57,34 @@ WORKLOADS = {
 # double-float basis and projections; the same with the recurrences' products
 # in double-float; or with those products in FP32
 DTYPES = {"fp64": "f64", "df": "f64+df64-operator", "mixed": "f64+f32-operator"}
-MV_PER_SOLVE = {"channel128": 1500.0, "channel96": 1100.0, "convdiff32": 60.0, "porous192": 400.0}
+MV_PER_SOLVE = {"channel128": {1: 1500.0}, "channel96": {1: 1100.0}, "convdiff32": {1: 60.0},
+                "porous192": {1: 400.0, 2: 400.0}}
 # the same with the sub-domain preconditioner (left rGCROT), measured likewise
-MV_PER_SOLVE_SD = {"channel128": 505.0}
+MV_PER_SOLVE_SD = {"channel128": {1: 505.0}, "porous192": {1: 360.0, 2: 309.0}}
 # the preconditioner each workload is defined with: the channel names the
 # paper's "Jacobi preconditioner" (the sub-domain one of Sec. 2.1), the
 # convection-diffusion case point Jacobi
 PRECOND_DEFAULT = {"channel128": "subdomain", "channel96": "subdomain"}
-FP64_TOPS = 0.625                    # nominal 1.25 TFLOP/s FP64, one DFMA = 2 flops
+FP64_TOPS = 0.625                    # nominal 1.25 TFLOP/s FP64, one DFMA = 2 flops (fallback)
+# where the basis, the recycle space and the projection arithmetic live
+BASIS = {"fp64": "f64", "df": "double-float", "mixed": "f64"}
 FP32_TOPS = 152 * 128 * 2.07e9 / 1e12  # FP32 lanes x SMs x max SM clock
+
+
+def fp64_peak_tops():
+    """The FP64 fma issue rate of this GPU in T lane operations per second,
+    measured by librk's probe (rk_fp64_fma_rate); the nominal rate if the
+    probe cannot run."""
+    try:
+        import ctypes
+        import torch
+        from paper_1501_03358_gb300 import native
+        lib = native.load()
+        v = ctypes.c_double()
+        native.check(lib.rk_fp64_fma_rate(ctypes.byref(v), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+        return v.value / 1e12, "measured (rk_fp64_fma_rate: FP64 fma chains, CUDA events)"
+    except Exception as e:  # pragma: no cover - reported, not hidden
+        return FP64_TOPS, f"nominal 1.25 TFLOP/s / 2 (probe failed: {e})"
 
 
 def load_peaks():
@@ -195,70 +218,143 @@ def subdomain_ops(grid, S, df):
     return float(first * grown + (sweeps - 2) * per_cell * grown + per_cell * grid.n)
 
 
-def oracle_cycle_sample(cfg, mode, m, k, cycles=2, precond="jacobi"):
-    """Time the CPU oracle on `cycles` rGCROT cycles of step 0 of the workload
-    (the first builds the recycle space; the last is timed). Returns
-    (seconds per matvec of a cycle at recycle dimension k, threads)."""
-    import numpy as np
+def _standin_space(n, k):
+    """k orthonormal columns (normalised indicators of k equal slabs of
+    cells) used as both U and C: a recycle space of dimension k for timing
+    the oracle's arithmetic only. A U = C does not hold for it, which the
+    operation count of a sample does not depend on."""
+    C = np.zeros((n, k))
+    sl = n // k
+    for c in range(k):
+        C[c * sl:(c + 1) * sl, c] = 1.0 / np.sqrt(sl)
+    return C.copy(), C
+
+
+def oracle_per_matvec(cfg, precond, m, k, modes, nmv):
+    """Seconds per matrix-vector product of the CPU oracle, per solver, on a
+    bounded sample of step 0 of the workload at recycle dimension k:
+    rGCROT (mode 1) one cycle of nmv Arnoldi steps (recycle update off),
+    rBiCGStab (mode 2) nmv products. Returns ({mode: s}, threads, note)."""
     import oracle
     op = oracle.Stencil(cfg.grid, cfg.coef)
     b = cfg.rhs(0)
-    U = C = None
-    per_mv = None
-    for c in range(cycles):
+    U, C = _standin_space(cfg.n, k) if k > 0 else (None, None)
+    pk = _oracle_prec(precond)
+    out = {}
+    for mode in sorted(modes):
         t0 = time.perf_counter()
-        _, U, C, info = oracle.rgcrot(op, b, tol=1e-14, m=m, k=k, U=U, C=C, max_matvec=m,
-                                      **_oracle_prec(precond))
-        dt = time.perf_counter() - t0
-        per_mv = dt / max(info["matvecs"], 1)
+        if mode == 2:
+            _, info = oracle.rbicgstab(op, b, tol=1e-14, U=U, C=C, max_matvec=nmv, max_restarts=0,
+                                       prec=pk.get("prec", "jacobi"))
+        else:
+            _, _, _, info = oracle.rgcrot(op, b, tol=1e-14, m=m, k=k if mode == 1 else 0,
+                                          U=U if mode == 1 else None, C=C if mode == 1 else None, update=False,
+                                          max_matvec=nmv, **pk)
+        out[mode] = (time.perf_counter() - t0) / max(info["matvecs"], 1)
     threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return per_mv, threads
+    note = (f"the oracle on step 0 at recycle dimension {k} (stand-in orthonormal space): "
+            + ", ".join(f"{['GMRES', 'rGCROT', 'rBiCGStab'][md]} {nmv} products "
+                        f"({1e3 * t:.0f} ms per product)" for md, t in sorted(out.items()))
+            + "; the recycle update of each rGCROT cycle is not included")
+    return out, threads, note
+
+
+def cpu_baseline(cfg, args, m, k, tinfo):
+    """The oracle as it stands, timed on the host cores on a bounded sample
+    (oracle_per_matvec), scaled to solves/s with the products per solve and
+    the solver of each timed step measured on the GPU."""
+    modes = {i["mode_used"] for i in tinfo}
+    per, threads, note = oracle_per_matvec(cfg, args.precond, m, k, modes, args.cpu_sample_matvecs)
+    secs = sum(per[i["mode_used"]] * i["matvecs"] for i in tinfo)
+    return {"value": len(tinfo) / secs, "unit": "solves/s", "cores": threads, "kind": "oracle",
+            "sample": note + f"; solves/s = {len(tinfo)} / sum over the timed steps of (products of the step x "
+                             f"seconds per product of its solver)"}
 
 
 def run_reference(args, ws, rank):
+    """The reference arm: the CPU oracle (FP64, host cores) on the same
+    workload. Each step is a bounded sample of the solve of that time step
+    (the solver the hybrid uses at that step, args.cpu_sample_matvecs
+    products at recycle dimension k), converted to solves/s with the
+    products per solve that the GPU arm measured for that solver."""
     if rank != 0:
         return
-    mv = (MV_PER_SOLVE_SD if args.precond == "subdomain" else MV_PER_SOLVE).get(args.workload)
-    if mv is None:
+    table = MV_PER_SOLVE_SD if args.precond == "subdomain" else MV_PER_SOLVE
+    mvs = table.get(args.workload)
+    if mvs is None:
         print(json.dumps({"impl": "reference", "unavailable": f"no measured products per solve for "
                           f"{args.workload} with the {args.precond} preconditioner"}), flush=True)
         return
     from problems import make_config
     cid, edge, mode, m, k = WORKLOADS[args.workload]
     cfg = make_config(cid, size=edge)
-    import oracle
-    op = oracle.Stencil(cfg.grid, cfg.coef)
-    b = cfg.rhs(0)
-    pk = _oracle_prec(args.precond)
-    # each step: one cycle cut at ms Arnoldi steps (the sub-domain
-    # preconditioner costs the oracle about 0.3 s per product at 128^3)
-    ms = m if args.precond != "subdomain" else min(m, 10)
-    # warm-up: build the recycle space
-    _, U, C, _ = oracle.rgcrot(op, b, tol=1e-14, m=m, k=k, max_matvec=ms, **pk)
-    for _ in range(max(args.warmup - 1, 0)):
-        _, U, C, _ = oracle.rgcrot(op, b, tol=1e-14, m=m, k=k, U=U, C=C, max_matvec=ms, **pk)
-    times = []
+    hybrid = mode == "hybrid"
+    step_mode = [(1 if (not hybrid or t < args.hybrid_switch) else 2) for t in range(args.steps)]
     t_all = time.perf_counter()
-    for s in range(args.steps):
-        t0 = time.perf_counter()
-        _, U, C, info = oracle.rgcrot(op, b, tol=1e-14, m=m, k=k, U=U, C=C, max_matvec=ms, **pk)
-        times.append((time.perf_counter() - t0) / max(info["matvecs"], 1))
+    # warm-up: one sample of each solver (loads the C loops, touches the operator)
+    per, threads, note = oracle_per_matvec(cfg, args.precond, m, k, set(step_mode), args.cpu_sample_matvecs)
+    times = []
+    for t in range(args.steps):
+        md = step_mode[t]
+        p1, _, _ = oracle_per_matvec(cfg, args.precond, m, k, {md}, args.cpu_sample_matvecs)
+        times.append(p1[md] * mvs[md])
     total = time.perf_counter() - t_all
-    per_mv = statistics.mean(times)
-    value = 1.0 / (per_mv * mv)
-    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    sample = (f"each step: one rGCROT({m},{k}) cycle cut at {ms} matvecs (recycle space carried), step 0 of "
-              f"{args.workload}, {args.precond} preconditioner; solves/s = 1/(s per matvec x {mv:.0f} matvecs "
-              f"per solve measured on the GPU arm)")
+    value = args.steps / sum(times)
+    sample = (note + "; each step: the same sample of its solver, solves/s = steps / sum of (seconds per product "
+              "x products per solve of that solver measured on the GPU arm: "
+              + ", ".join(f"{['GMRES', 'rGCROT', 'rBiCGStab'][md]} {v:.0f}" for md, v in sorted(mvs.items())) + ")")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "grid": [edge] * 3, "solver": f"{mode}({m},{k})", "tol": 1e-8,
+            "config": {"workload": args.workload, "grid": [edge] * 3, "stencil": cfg.S,
+                       "solver": (f"hybrid rGCROT({m},{k}) for {args.hybrid_switch} steps -> rBiCGStab(k={k})"
+                                  if hybrid else f"{mode}({m},{k})"), "tol": 1e-8,
                        "precond": args.precond, "l2": "inputs larger than L2"},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _timed_solves(prob, rhs, kw, stream, x, keep=None):
+    """Solve the right-hand sides in order on `stream` with CUDA events around
+    each solve and around the whole run. Returns (ms, [(ms, info)])."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ev, infos = [], []
+    e0.record(stream)
+    for i, b in enumerate(rhs):
+        ts = torch.cuda.Event(enable_timing=True)
+        te = torch.cuda.Event(enable_timing=True)
+        ts.record(stream)
+        x.zero_()
+        _, info = prob.solve(b, out=x, **kw)
+        te.record(stream)
+        if keep is not None:
+            keep.append(x.clone())
+        ev.append((ts, te))
+        infos.append(info)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), [(a.elapsed_time(b), inf) for (a, b), inf in zip(ev, infos)]
+
+
+def _phase_summary(per, hbm_peak):
+    """Per phase of a hybrid sequence (mode_used 1 = rGCROT, 2 = rBiCGStab):
+    solves, time, products, modelled bytes and their HBM fraction."""
+    out = {}
+    for mode, name in ((0, "GMRES"), (1, "rGCROT"), (2, "rBiCGStab")):
+        sel = [(ms, i) for ms, i in per if i["mode_used"] == mode]
+        if not sel:
+            continue
+        ms = sum(s[0] for s in sel)
+        by = sum(s[1]["model_bytes"] for s in sel)
+        gbs = by / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        out[name] = {"solves": len(sel), "ms": ms, "ms_per_solve": ms / len(sel),
+                     "matvecs_per_solve": statistics.mean(s[1]["matvecs"] for s in sel),
+                     "model_GBps": gbs, "frac_of_hbm": gbs / hbm_peak}
+    return out
 
 
 def run_ours(args, ws, rank, local):
@@ -277,64 +373,72 @@ def run_ours(args, ws, rank, local):
     ctx = Context()
     prob = Problem(ctx, cfg.grid, torch.from_numpy(cfg.coef))
     x = torch.zeros(cfg.n, dtype=torch.float64, device="cuda")
-    kw = dict(tol=1e-8, m=m, k=k, mode=mode, max_matvec=args.max_matvec, hybrid_switch=5, precision=args.precision,
-              precond=args.precond, precond_side="left" if args.precond == "subdomain" else "right")
-    # sequence pre-roll (untimed, before warm-up): the first solves of a
-    # sequence build the recycle space and may stall until it holds the
-    # slowest modes; run them with a matvec cap, stopping at the first one
-    # that converges, so that the timed steps are steady-state solves
+    side = "left" if (args.precond == "subdomain" and mode != "rBiCGStab") else "right"
+    kw = dict(tol=1e-8, m=m, k=k, mode=mode, max_matvec=args.max_matvec, hybrid_switch=args.hybrid_switch,
+              precision=args.precision, precond=args.precond, precond_side=side)
+    hybrid = mode == "hybrid"
     P = 0
-    for t in range(args.preroll):
-        x.zero_()
-        _, info = prob.solve(torch.from_numpy(cfg.rhs(t)).cuda(), out=x, **dict(kw, max_matvec=args.preroll_matvec))
-        P += 1
-        if info["status"] == 0:
-            break
-    t0s = P
+    if hybrid:
+        # a hybrid sequence is timed from its first step: steps 0 .. K-1 (the
+        # rGCROT phase builds the recycle space, the rBiCGStab phase reuses it);
+        # the warm-up runs W steps of the same sequence with the switch moved
+        # so that both phases run, then the problem starts a new sequence
+        t0s = 0
+        seq = list(range(K))
+        warm = list(range(W))
+    else:
+        # sequence pre-roll (untimed, before warm-up): the first solves of an
+        # rGCROT sequence build the recycle space and may stall until it holds
+        # the slowest modes; run them with a matvec cap, stopping at the first
+        # one that converges, so that the timed steps are steady-state solves
+        for t in range(args.preroll):
+            x.zero_()
+            _, info = prob.solve(torch.from_numpy(cfg.rhs(t)).cuda(), out=x,
+                                 **dict(kw, max_matvec=args.preroll_matvec))
+            P += 1
+            if info["status"] == 0:
+                break
+        t0s = P
+        warm = list(range(t0s, t0s + W))
+        seq = list(range(t0s + W, t0s + W + K))
+    steps_needed = sorted(set(warm) | set(seq) | set(range(seq[-1] + 1, seq[-1] + 1 + K)) if not hybrid
+                          else set(warm) | set(seq))
     # all right-hand sides resident in HBM before timing; pinned host copies for e2e
-    rhs_host = {t: torch.from_numpy(cfg.rhs(t)).pin_memory() for t in range(t0s, t0s + W + 2 * K)}
+    rhs_host = {t: torch.from_numpy(cfg.rhs(t)).pin_memory() for t in steps_needed}
     rhs_dev = {t: h.to("cuda", non_blocking=True) for t, h in rhs_host.items()}
-    for t in range(t0s, t0s + W):
+    wkw = dict(kw, hybrid_switch=max(1, min(args.hybrid_switch, W - 1))) if hybrid else kw
+    for t in warm:
         x.zero_()
-        prob.solve(rhs_dev[t], out=x, **kw)
+        prob.solve(rhs_dev[t], out=x, **wkw)
+    if hybrid:
+        prob.reset()
     torch.cuda.synchronize()
-    # ---- timed region (device events on the solve stream), profiling on
-    prob.profile(True)
+    # ---- timed region: the production path (captured cycles replayed, no
+    # per-kernel events), device events on the solve stream
     sampler = ClockSampler(local)
     sampler.start()
     barrier(ws)
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    lat = []
-    e0.record(stream)
-    tinfo = []
-    for t in range(t0s + W, t0s + W + K):
-        ts = torch.cuda.Event(enable_timing=True)
-        te = torch.cuda.Event(enable_timing=True)
-        ts.record(stream)
-        x.zero_()
-        _, info = prob.solve(rhs_dev[t], out=x, **kw)
-        te.record(stream)
-        tinfo.append(info)
-        lat.append((ts, te))
-    e1.record(stream)
-    torch.cuda.synchronize()
+    xs_keep = [] if (args.vs_fp64 and args.precision != "fp64") else None
+    ms, per = _timed_solves(prob, [rhs_dev[t] for t in seq], kw, stream, x, keep=xs_keep)
     barrier(ws)
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    lat_ms = [a.elapsed_time(b) for a, b in lat]
-    prof = prob.profile_read()
-    prob.profile(False)
+    tinfo = [p[1] for p in per]
+    lat_ms = [p[0] for p in per]
     ms_max = max_over_ranks(ws, ms)
     # ---- end to end through the public API: pinned host b -> device, solve,
     # device -> pinned host x, every step
+    if hybrid:
+        prob.reset()
+        e2e_steps = seq
+    else:
+        e2e_steps = list(range(seq[-1] + 1, seq[-1] + 1 + K))
     xh = torch.empty(cfg.n, dtype=torch.float64).pin_memory()
     bdev = torch.empty(cfg.n, dtype=torch.float64, device="cuda")
     barrier(ws)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for t in range(t0s + W + K, t0s + W + 2 * K):
+    for t in e2e_steps:
         bdev.copy_(rhs_host[t], non_blocking=True)
         x.zero_()
         prob.solve(bdev, out=x, **kw)
@@ -343,16 +447,25 @@ def run_ours(args, ws, rank, local):
     e2e_s = time.perf_counter() - t0
     barrier(ws)
     e2e_s = max_over_ranks(ws, e2e_s)
+    # ---- kernel classes: a separate, untimed replay of the same steps with
+    # CUDA events around every launch (captured cycles are not used then)
+    if hybrid:
+        prob.reset()
+    prob.profile(True)
+    prof_ms, prof_per = _timed_solves(prob, [rhs_dev[t] for t in (seq if hybrid else e2e_steps)], kw, stream, x)
+    prof = prob.profile_read()
+    prob.profile(False)
 
     peaks, peak_src = load_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    fp64_peak, fp64_src = fp64_peak_tops()
     # DRAM traffic of one launch over its algorithmic bytes, from one ncu
     # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the same
     # kernels on the 96^3 channel: dots at nq = 40 (335.2 MB for 297.3 MB),
     # update at nq = 58 (437.9 MB for 438.8 MB). Every operand is far larger
-    # than L2 at both sizes, so the ratio carries over to 128^3.
+    # than L2 at both sizes, so the ratio carries over.
     traffic_ratio = {"dots": 335.2 / 297.3, "update": 437.9 / 438.8}
-    # dominant kernel class by time
+    # dominant kernel class by time (profiled replay)
     dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
     dname, d = dom
     achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
@@ -362,28 +475,24 @@ def run_ours(args, ws, rank, local):
                         if dname in traffic_ratio else None),
             "traffic_source": "ncu DRAM bytes / algorithmic bytes on the 96^3 channel x this run's "
                               "algorithmic bytes per launch" if dname in traffic_ratio else None,
-            "peak_source": peak_src,
+            "peak_source": peak_src, "timing": "CUDA events around each launch in an untimed replay of the "
+                                               "timed steps",
             "launches": d["launches"], "avg_launch_us": 1000.0 * d["ms"] / max(d["launches"], 1),
             "bytes_per_launch": d["bytes"] / max(d["launches"], 1)}
     if dname in ("subdomain_local", "subdomain_df"):
-        # bound by the arithmetic pipe: FP64 instructions against the nominal
-        # DFMA rate (1.25 TFLOP/s / 2 = 0.625 T instructions/s), or, for the
-        # double-float variant, FP32 instructions against 128 FP32 lanes per SM
-        # per clock (152 SMs at 2.07 GHz: 40.3 T instructions/s)
+        # bound by the arithmetic pipe: FP64 instructions against the measured
+        # FP64 rate, or, for the double-float variant, FP32 instructions
+        # against 128 FP32 lanes per SM per clock (152 SMs at 2.07 GHz)
         dfk = dname == "subdomain_df"
         ops = subdomain_ops(cfg.grid, cfg.S, dfk)
-        peak = FP32_TOPS if dfk else FP64_TOPS
+        peak = FP32_TOPS if dfk else fp64_peak
         ach = ops * d["launches"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
-        # DRAM traffic per launch from one ncu capture of the FP64 kernel on
-        # the 96^3 channel (63.8 MB read + 2.8 MB written for 884,736 cells),
-        # scaled by the cells of this grid; the double-float variant reads the
-        # same bytes (63.9 + 2.7 MB)
         traffic = (63.8 + 2.8) * 1e6 / 96 ** 3 * cfg.grid.n
         roof.update({"bound": "alu", "achieved": ach, "peak": peak,
                      "unit": "T FP32 instr/s" if dfk else "T FP64 instr/s", "frac": ach / peak,
                      "traffic": traffic,
                      "traffic_source": "ncu DRAM bytes of one launch on the 96^3 channel x cells of this grid",
-                     "peak_source": "FP32 lanes x SMs x max SM clock" if dfk else "nominal FP64 rate / 2 per DFMA",
+                     "peak_source": "FP32 lanes x SMs x max SM clock" if dfk else fp64_src,
                      "instr_per_launch": ops})
     total_model = sum(i["model_bytes"] for i in tinfo)
     solver_gbs = total_model / (ms * 1e-3) / 1e9
@@ -394,32 +503,48 @@ def run_ours(args, ws, rank, local):
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": K, "warmup": W,
         "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": DTYPES[args.precision], "data": "synthetic",
-        "config": {"workload": args.workload, "grid": [edge] * 3, "stencil": cfg.S, "solver": f"{mode}({m},{k})",
-                   "precision": args.precision, "precond": args.precond,
-                   "tol": 1e-8, "preroll_steps": P, "preroll_matvec_cap": args.preroll_matvec,
-                   "sequence_steps_timed": [t0s + W, t0s + W + K - 1], "l2": "inputs larger than L2",
+        "config": {"workload": args.workload, "grid": [edge] * 3, "stencil": cfg.S,
+                   "solver": (f"hybrid rGCROT({m},{k}) for {args.hybrid_switch} steps -> rBiCGStab(k={k})"
+                              if hybrid else f"{mode}({m},{k})"),
+                   "precision": args.precision, "basis": BASIS[args.precision], "precond": args.precond,
+                   "precond_side": side, "tol": 1e-8, "preroll_steps": P,
+                   "preroll_matvec_cap": args.preroll_matvec if not hybrid else None,
+                   "sequence_steps_timed": [seq[0], seq[-1]], "l2": "inputs larger than L2",
+                   "solid_fraction": cfg.solid_fraction if hybrid else None,
                    "parallelism": "replicas" if ws > 1 else "single"},
         "solver_hbm_gbs": solver_gbs, "solver_hbm_frac": solver_gbs / hbm_peak,
+        "phases": _phase_summary(per, hbm_peak),
         "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99))},
+        "per_step": [{"step": t, "mode": ["GMRES", "rGCROT", "rBiCGStab"][i["mode_used"]], "ms": round(l, 3),
+                      "matvecs": i["matvecs"], "relres": i["relres_true"]} for t, l, i in zip(seq, lat_ms, tinfo)],
         "matvecs_per_solve": statistics.mean(mv), "relres_max": max(i["relres_true"] for i in tinfo),
         "all_converged": all(i["status"] == 0 for i in tinfo),
         "roofline": roof,
         "kernel_classes": {kname: {"ms": round(v["ms"], 3), "launches": v["launches"],
                                    "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
                            for kname, v in prof.items() if v["launches"]},
+        "kernel_classes_pass": {"ms": prof_ms, "note": "untimed replay with per-launch events"},
         "gpu_launches": launches,
-        "e2e": {"value": ws * K / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * cfg.n,
+        "gpu_launches_source": "library launches counted in the profiled replay of the same steps",
+        "e2e": {"value": ws * len(e2e_steps) / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * cfg.n,
                 "d2h_bytes_per_step": 8 * cfg.n},
         "clocks": clocks,
     }
+    if xs_keep is not None:
+        # the same sequence in FP64 (a second problem): per-step difference of
+        # the solutions, relative to the FP64 one
+        ref = Problem(ctx, cfg.grid, torch.from_numpy(cfg.coef))
+        errs = []
+        fkw = dict(kw, precision="fp64")
+        for i, t in enumerate(seq):
+            x.zero_()
+            ref.solve(rhs_dev[t], out=x, **fkw)
+            errs.append(float(torch.linalg.norm(xs_keep[i] - x) / torch.linalg.norm(x)))
+        ref.close()
+        line["error_vs_fp64"] = {"per_step": errs, "max": max(errs),
+                                 "reference": "the same sequence solved by the fp64 path of this library"}
     if rank == 0 and not args.no_cpu_baseline:
-        per_mv, threads = oracle_cycle_sample(cfg, mode, m, k, cycles=2, precond=args.precond)
-        mvs = statistics.mean(mv)
-        line["cpu_baseline"] = {"value": 1.0 / (per_mv * mvs), "unit": "solves/s", "cores": threads,
-                                "kind": "oracle",
-                                "sample": f"two rGCROT({m},{k}) cycles of step 0 (the second, at recycle dim {k}, "
-                                          f"timed: {per_mv * 1e3:.1f} ms per matvec); solves/s = 1/(that x "
-                                          f"{mvs:.0f} matvecs per solve measured above)"}
+        line["cpu_baseline"] = cpu_baseline(cfg, args, m, k, tinfo)
     if rank == 0:
         print(json.dumps(line), flush=True)
     prob.close()
@@ -706,7 +831,13 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="channel128", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="porous192", choices=sorted(WORKLOADS))
+    ap.add_argument("--hybrid-switch", type=int, default=5, help="hybrid: rGCROT solves before the switch")
+    ap.add_argument("--vs-fp64", type=int, default=1,
+                    help="precision df/mixed: also solve the timed steps with the fp64 path and report the "
+                         "per-step difference of the solutions (1 = on)")
+    ap.add_argument("--cpu-sample-matvecs", type=int, default=6,
+                    help="CPU oracle sample: products per solver")
     ap.add_argument("--max-matvec", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--preroll", type=int, default=12,

@@ -371,6 +371,24 @@ int rk_dots_noalloc(int64_t n, int32_t nq, const double* Q, int64_t ld, const do
  * recycle dimension. */
 int rk_problem_stats(const rk_problem* p, int32_t* solves, int32_t* recycle_dim, int64_t* n);
 
+/*
+ * Start a new time-step sequence on the same operator: the recycle space is
+ * dropped (as rk_set_recycle with k = 0) and RK_HYBRID's solve counter
+ * restarts, so the next solve is solve 0 of a new rGCROT phase (Sec. 2.4).
+ * Buffers, operator copies and captured cycles are kept. Returns RK_E_INVALID
+ * for a NULL problem. No counterpart in the paper (its runs are one sequence).
+ */
+int rk_problem_reset(rk_problem* p);
+
+/*
+ * Measure this GPU's FP64 fma issue rate (lane operations per second, one
+ * fma = 2 flops): 608 blocks of 256 threads, 8 independent fma chains of
+ * 4096 steps per thread, best of three timed launches (CUDA events on
+ * `stream`) after one warm-up launch. The denominator of the rooflines of
+ * kernels bound by the FP64 pipe. No counterpart in the paper.
+ */
+int rk_fp64_fma_rate(double* fma_per_s, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,7 +13,9 @@ Parity status of each function:
 * ``gmres``: pinned (dense LU, finite termination, monotone residuals).
 * ``rgcrot``: pinned (k=0 equals ``gmres`` exactly; dense LU; A U = C,
   C^T C = I, V ⟂ C, augmented Arnoldi relation; exact recycling).
-* ``harmonic_ritz_update``: pinned (independent dense harmonic Ritz values).
+* ``harmonic_ritz_update``: pinned (independent dense harmonic Ritz values,
+  and the selected subspace against the eigenvectors of the k smallest
+  |theta| of the explicit dense pencil).
 * ``bicgstab``: pinned (dense LU).
 * ``rbicgstab``: pinned (empty recycle space equals ``bicgstab`` exactly;
   dense LU; r ⟂ C; solution/residual relation).

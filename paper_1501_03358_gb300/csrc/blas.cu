@@ -67,7 +67,30 @@ __global__ void k_fill(int64_t n, double val, double* __restrict__ dst) {
     dst[i] = val;
 }
 
+// FP64 issue-rate probe: 8 independent fma chains per thread (enough to keep
+// the FP64 pipe busy), iters steps each; nothing is stored unless the sum is
+// exactly 0.5, which the chains never reach, so no work is eliminated.
+__device__ double g_probe_sink;
+__global__ void __launch_bounds__(256) k_fp64_probe(int iters, double m, double c) {
+  double a[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) a[q] = 1.0 + 0.001 * (threadIdx.x + q);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[q] = fma(a[q], m, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s += a[q];
+  if (s == 0.5) g_probe_sink = s;
+}
+
 }  // namespace
+
+cudaError_t launch_fp64_probe(int blocks, int iters, cudaStream_t st) {
+  k_fp64_probe<<<blocks, 256, 0, st>>>(iters, 0.9999999, 1e-9);
+  return cudaGetLastError();
+}
 
 int gram_blocks(int64_t n) {
   int64_t b = (n + 1023) / 1024;

@@ -131,6 +131,9 @@ cudaError_t launch_dots(const DotsArgs& a, cudaStream_t st);
 // Blocks of the double-float Gram kernel for n rows (a function of n alone).
 int gram_blocks(int64_t n);
 
+// FP64 fma-rate probe: blocks x 256 threads x 8 chains x iters fma.
+cudaError_t launch_fp64_probe(int blocks, int iters, cudaStream_t st);
+
 // Elementwise helpers for the BiCGStab recurrences (see solver.cu).
 cudaError_t launch_copy(int64_t n, const double* src, double* dst, cudaStream_t st);
 cudaError_t launch_fill(int64_t n, double val, double* dst, cudaStream_t st);

@@ -1524,6 +1524,37 @@ int rk_problem_stats(const rk_problem* p, int32_t* solves, int32_t* recycle_dim,
   return RK_OK;
 }
 
+int rk_fp64_fma_rate(double* fma_per_s, void* stream) {
+  if (!fma_per_s) return fail(RK_E_INVALID, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int blocks = 4 * kNumSM, iters = 4096;
+  const double fmas = (double)blocks * 256 * 8 * iters;
+  cudaEvent_t e0, e1;
+  RK_CUDA(cudaEventCreate(&e0));
+  RK_CUDA(cudaEventCreate(&e1));
+  float best = 0.f;
+  for (int rep = 0; rep < 4; ++rep) {  // the first launch warms the clocks up
+    RK_CUDA(cudaEventRecord(e0, st));
+    RK_CUDA(launch_fp64_probe(blocks, iters, st));
+    RK_CUDA(cudaEventRecord(e1, st));
+    RK_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    RK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (rep > 0 && (best == 0.f || ms < best)) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *fma_per_s = best > 0.f ? fmas / (best * 1e-3) : 0.0;
+  return RK_OK;
+}
+
+int rk_problem_reset(rk_problem* p) {
+  if (!p) return fail(RK_E_INVALID, "NULL problem");
+  p->kdim = 0;
+  p->kside = 0;
+  p->hyb_base = p->solves;
+  return RK_OK;
+}
 
 int rk_problem_memory(const rk_problem* p, int64_t* device_bytes) {
   if (!p || !device_bytes) return fail(RK_E_INVALID, "NULL argument");

@@ -187,6 +187,11 @@ class Problem:
         N.check(self.lib.rk_problem_stats(self._h, ctypes.byref(s), ctypes.byref(k), ctypes.byref(n)))
         return dict(solves=s.value, recycle_dim=k.value, n=n.value)
 
+    def reset(self):
+        """Start a new time-step sequence: drop the recycle space and restart
+        the hybrid's solve counter (rk_problem_reset)."""
+        N.check(self.lib.rk_problem_reset(self._h))
+
     def profile(self, on: bool = True):
         """Enable (and reset) or disable per-kernel-class timing of solves."""
         N.check(self.lib.rk_profile_enable(self._h, 1 if on else 0))

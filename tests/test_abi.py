@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_symbols():
     text = open(os.path.join(ROOT, "include", "rk.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = set(re.findall(r"\b(rk_[a-z_]+)\s*\(", text))
+    names = set(re.findall(r"\b(rk_[a-z0-9_]+)\s*\(", text))
     return sorted(n for n in names if not n.endswith("_fn"))
 
 
