@@ -56,7 +56,7 @@ WORKLOADS = {
 # arithmetic of the path per precision: FP64 operator and true residual with
 # double-float basis and projections; the same with the recurrences' products
 # in double-float; or with those products in FP32
-DTYPES = {"fp64": "f64", "df": "f64+df64-operator", "mixed": "f64+f32-operator"}
+DTYPES = {"fp64": "f64", "df": "f64+df64", "mixed": "f64+f32-operator"}
 MV_PER_SOLVE = {"channel128": {1: 1500.0}, "channel96": {1: 1100.0}, "convdiff32": {1: 60.0},
                 "porous192": {1: 400.0, 2: 400.0}}
 # the same with the sub-domain preconditioner (left rGCROT), measured likewise

@@ -28,10 +28,15 @@
  *    exactly 0 (checked by rk_create_problem).
  *  - The recycle space is stored in x-space: U, C are N x k column-major
  *    (column c at offset c*N) with A U = C and C^T C = I; the R of the QR that forms C
- *    is folded into U. Inside the library U, C and the Arnoldi basis are kept
- *    as double-float pairs (hi + lo of two FP32 numbers, about 48 significant
- *    bits) and all projection arithmetic is double-float: a recycle space set
- *    and read back agrees with the original to about 2^-46 relative.
+ *    is folded into U. Inside the library U, C and the Arnoldi basis are
+ *    stored in FP64 and every projection, orthogonalisation, Gram and
+ *    recycle-update product is FP64 arithmetic (precisions RK_FP64 and
+ *    RK_MIXED); with RK_DF they are kept as double-float pairs (hi + lo of
+ *    two FP32 numbers, about 48 significant bits) and that arithmetic runs in
+ *    double-float on the FP32 pipe. A stored space is converted in place when
+ *    a solve of the other kind comes (one rounding to double-float). A
+ *    recycle space set and read back is bit-exact in FP64 storage and agrees
+ *    to about 2^-46 relative in double-float storage.
  *  - Every pointer argument named "device" is CUDA device memory owned by
  *    the caller and only read or written during the call. Host pointers are
  *    named so. All GPU work is ordered on the stream passed to the call; the
@@ -94,13 +99,18 @@ typedef struct {
   int32_t max_matvec;    /* cap on matrix-vector products in the recurrences (<= 0: 2000) */
   int32_t hybrid_switch; /* RK_HYBRID: solves of this problem run with rGCROT before the switch */
   int32_t mode;          /* rk_mode */
-  int32_t precision;     /* rk_precision: RK_FP64, or RK_MIXED = the A M^{-1} products of the
+  int32_t precision;     /* rk_precision: RK_FP64 = FP64 storage and arithmetic throughout (the
+                            operator, the basis, U and C, the projections, orthogonalisation,
+                            Gram, recycle-update products and the Schur iteration of the
+                            harmonic Ritz problem); RK_MIXED = the A M^{-1} products of the
                             recurrences with an FP32 copy of the operator (FP32 accumulation),
                             everything else as in RK_FP64, b - A x recomputed in FP64 every
-                            cycle / on convergence (residual replacement); or RK_DF = those
+                            cycle / on convergence (residual replacement); RK_DF = those
                             products with a double-float copy of the operator (bands and
                             1/a_pp rounded to ~48 bits once, double-float accumulation in band
-                            order), everything else as in RK_FP64 */
+                            order) and the basis, U, C, projections and Schur iteration in
+                            double-float on the FP32 pipe; residuals, x and the small least
+                            squares problems in FP64 */
   int32_t update_recycle;/* rGCROT: 1 = update U, C after every cycle (Algorithm 3), 0 = keep */
   int32_t hybrid_refresh;  /* RK_HYBRID, Sec. 2.4 "intermittent solves with rGCROT": after the
                               switch, every hybrid_refresh-th solve runs rGCROT (updating U, C);
@@ -238,20 +248,41 @@ int rk_dots(rk_context* ctx, int64_t n, int32_t nq, const double* Q, int64_t ld,
             double* out, void* stream);
 
 /*
+ * The fused inner products of one Arnoldi step of GMRES / rGCROT
+ * (Algorithms 1 and 3: the projection of the new vector onto [C V_j] and its
+ * norm, by classical Gram-Schmidt with the second pass of the previous
+ * vector delayed to this step) on their own, with the kernel that solves of
+ * the given precision run: out = [Q^T p (nq), Q^T w (nq), p^T p, p^T w,
+ * w^T w] (2 nq + 3 doubles) for Q (N x nq, leading dimension ld >= N), p and
+ * w (N doubles), all device FP64. precision RK_FP64: the FP64 kernel of the
+ * RK_FP64 and RK_MIXED basis on the operands as given; RK_DF: the operands
+ * first rounded to double-float, then the double-float kernel. 0 <= nq <=
+ * 128, else RK_E_INVALID; RK_E_DEVICE_TIMEOUT if a bounded device wait
+ * gave up. Allocates temporary device memory through the context's
+ * allocator; synchronises `stream`. The reduction order is fixed by N.
+ * A test entry point.
+ */
+int rk_arnoldi_dots(rk_context* ctx, int64_t n, int32_t nq, const double* Q, int64_t ld, const double* p,
+                    const double* w, double* out, int32_t precision, void* stream);
+
+/*
  * The row-tiled product of the recycle updates of Algorithm 3 (C <- W_hat QC,
  * U <- W PU) on its own: out = [A, diag(s) B] P with A (N x na) and B
  * (N x nb) device FP64 column-major (leading dimensions lda, ldb >= N; either
  * part may be empty), s device N doubles or NULL (identity), P device FP64
  * (na + nb) x nc column-major with leading dimension na + nb, out device
- * N x nc FP64 (leading dimension ldo >= N). A and B are first rounded to
- * double-float, as the solver stores its basis. engine = 1 runs the
- * tensor-core kernel the solver uses for 2 <= nc <= 32 and na + nb <= 64
+ * N x nc FP64 (leading dimension ldo >= N). For engines 0 and 1, A and B
+ * are first rounded to double-float, as RK_DF solves store their basis;
+ * engine = 1 runs the tensor-core kernel those solves use for
+ * 2 <= nc <= 32 and na + nb <= 64
  * (7 BF16 digits per operand, exact FP32 accumulation per digit level on the
  * fifth-generation tensor cores); engine = 0 the double-float kernel on the
- * FP32 pipe. RK_E_INVALID for bad arguments or a shape the tensor-core
+ * FP32 pipe; engine = 2 the FP64 kernel of the RK_FP64 / RK_MIXED basis on
+ * A and B as given (FP64 fused multiply-adds, no rounding of the operands).
+ * RK_E_INVALID for bad arguments or a shape the tensor-core
  * engine does not take; RK_E_DEVICE_TIMEOUT if a bounded device wait gave
- * up. Allocates temporary device memory through the context's allocator;
- * synchronises `stream`. No counterpart in the paper (a test entry point).
+ * up. Engines 0 and 1 allocate temporary device memory through the
+ * context's allocator (engine 2 allocates nothing); synchronises `stream`. No counterpart in the paper (a test entry point).
  */
 int rk_row_gemm(rk_context* ctx, int64_t n, int32_t na, const double* A, int64_t lda, int32_t nb,
                 const double* B, int64_t ldb, const double* s, const double* P, int32_t nc, double* out,
@@ -335,10 +366,14 @@ int rk_profile_read(rk_problem* p, rk_prof_entry* out, int32_t cap, int32_t* cou
  * with orthonormal columns and PU (n x knew, ld n) with G PU = QC and
  * range(PU) = span of the selected vectors; *knew (host) = their number.
  * Then C <- W_hat QC and U <- W PU keep A U = C and C^T C = I.
+ * precision: RK_FP64 runs the Hessenberg reduction and the Francis
+ * iteration in FP64 (as RK_FP64 and RK_MIXED solves do), RK_DF in
+ * double-float on the FP32 pipe (as RK_DF solves do); other values:
+ * RK_E_INVALID. The QR of G and everything after the Schur form are FP64.
  * Returns RK_E_BREAKDOWN if the eigen-iteration fails to converge.
  */
 int rk_harmonic_ritz(rk_context* ctx, int32_t n, const double* G, const double* F, int32_t k, double* QC,
-                     double* PU, int32_t* knew, void* stream);
+                     double* PU, int32_t* knew, int32_t precision, void* stream);
 
 /*
  * rk_dots without any device allocation. The paper has no counterpart: this

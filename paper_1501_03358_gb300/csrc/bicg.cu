@@ -6,6 +6,7 @@
 // device flag stops the remaining kernels of a batch on convergence or
 // breakdown.
 #include <cmath>
+#include <type_traits>
 #include "rk_bicg.h"
 #include "rk_device.cuh"
 #include "rk_df.cuh"
@@ -53,8 +54,9 @@ __global__ void k_bicg_alpha(BicgScalars* s, const double* dots, int kc) {
 // v <- v - C eta1; s = r - alpha v; ||s||; on convergence the
 // half step is recorded (xi += alpha eta1 here, x~ += alpha p
 // by k_bicg_half).
+template <typename CT>
 __global__ void __launch_bounds__(kRedThreads) k_bicg_s(BicgVecs v, BicgScalars* s, int64_t n, int kc,
-                                                        const float2* C, int64_t ld, const double* eta1,
+                                                        const CT* C, int64_t ld, const double* eta1,
                                                         double* xi, double* part, unsigned* counter) {
   if (stopped(s)) return;
   __shared__ double red[32];
@@ -73,12 +75,16 @@ __global__ void __launch_bounds__(kRedThreads) k_bicg_s(BicgVecs v, BicgScalars*
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     double vi = v.v[i];
     if (kc) {
-      float sh = 0.f, sl = 0.f;  // C eta1 in double-float
-      for (int q = 0; q < kc; ++q) {
-        const float2 c = __ldg(&C[(int64_t)q * ld + i]);
-        df_mac(sh, sl, c.x, c.y, sedf[q].x, sedf[q].y);
+      if constexpr (std::is_same<CT, float2>::value) {
+        float sh = 0.f, sl = 0.f;  // C eta1 in double-float
+        for (int q = 0; q < kc; ++q) {
+          const float2 c = __ldg(&C[(int64_t)q * ld + i]);
+          df_mac(sh, sl, c.x, c.y, sedf[q].x, sedf[q].y);
+        }
+        vi = (vi - (double)sh) - (double)sl;
+      } else {
+        for (int q = 0; q < kc; ++q) vi = fma(-__ldg(&C[(int64_t)q * ld + i]), se[q], vi);  // FP64
       }
-      vi = (vi - (double)sh) - (double)sl;
       v.v[i] = vi;
     }
     const double si = fma(-alpha, vi, v.r[i]);
@@ -116,14 +122,17 @@ __global__ void __launch_bounds__(kRedThreads) k_bicg_half(BicgVecs v, BicgScala
 }
 
 // t <- t - C eta2; omega = t^T s / t^T t (last block).
+template <typename CT>
 __global__ void __launch_bounds__(kRedThreads) k_bicg_t(BicgVecs v, BicgScalars* s, int64_t n, int kc,
-                                                        const float2* C, int64_t ld, const double* eta2,
+                                                        const CT* C, int64_t ld, const double* eta2,
                                                         double* part, unsigned* counter) {
   if (stopped(s)) return;
   __shared__ double red[32];
   __shared__ int lastflag;
   __shared__ float2 sedf[256];
+  __shared__ double se[256];
   for (int q = threadIdx.x; q < kc; q += blockDim.x) {
+    se[q] = eta2[q];
     const df e = df_from_double(eta2[q]);
     sedf[q] = make_float2(e.hi, e.lo);
   }
@@ -133,12 +142,16 @@ __global__ void __launch_bounds__(kRedThreads) k_bicg_t(BicgVecs v, BicgScalars*
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     double ti = v.t[i];
     if (kc) {
-      float sh = 0.f, sl = 0.f;  // C eta2 in double-float
-      for (int q = 0; q < kc; ++q) {
-        const float2 c = __ldg(&C[(int64_t)q * ld + i]);
-        df_mac(sh, sl, c.x, c.y, sedf[q].x, sedf[q].y);
+      if constexpr (std::is_same<CT, float2>::value) {
+        float sh = 0.f, sl = 0.f;  // C eta2 in double-float
+        for (int q = 0; q < kc; ++q) {
+          const float2 c = __ldg(&C[(int64_t)q * ld + i]);
+          df_mac(sh, sl, c.x, c.y, sedf[q].x, sedf[q].y);
+        }
+        ti = (ti - (double)sh) - (double)sl;
+      } else {
+        for (int q = 0; q < kc; ++q) ti = fma(-__ldg(&C[(int64_t)q * ld + i]), se[q], ti);  // FP64
       }
-      ti = (ti - (double)sh) - (double)sl;
       v.t[i] = ti;
     }
     ts = fma(ti, v.s[i], ts);
@@ -259,18 +272,26 @@ cudaError_t launch_bicg_alpha(BicgScalars* s, const double* dots, int kc, cudaSt
   k_bicg_alpha<<<1, 32, 0, st>>>(s, dots, kc);
   return cudaGetLastError();
 }
-cudaError_t launch_bicg_s(const BicgVecs& v, BicgScalars* s, int64_t n, int kc, const float2* C, int64_t ld,
+cudaError_t launch_bicg_s(const BicgVecs& v, BicgScalars* s, int64_t n, int kc, const void* C, bool c_df, int64_t ld,
                           const double* eta1, double* xi, double* part, unsigned* counter, cudaStream_t st) {
-  k_bicg_s<<<red_blocks(n), kRedThreads, 0, st>>>(v, s, n, kc, C, ld, eta1, xi, part, counter);
+  if (c_df)
+    k_bicg_s<float2><<<red_blocks(n), kRedThreads, 0, st>>>(v, s, n, kc, (const float2*)C, ld, eta1, xi, part,
+                                                            counter);
+  else
+    k_bicg_s<double><<<red_blocks(n), kRedThreads, 0, st>>>(v, s, n, kc, (const double*)C, ld, eta1, xi, part,
+                                                            counter);
   return cudaGetLastError();
 }
 cudaError_t launch_bicg_half(const BicgVecs& v, BicgScalars* s, int64_t n, cudaStream_t st) {
   k_bicg_half<<<red_blocks(n), kRedThreads, 0, st>>>(v, s, n);
   return cudaGetLastError();
 }
-cudaError_t launch_bicg_t(const BicgVecs& v, BicgScalars* s, int64_t n, int kc, const float2* C, int64_t ld,
+cudaError_t launch_bicg_t(const BicgVecs& v, BicgScalars* s, int64_t n, int kc, const void* C, bool c_df, int64_t ld,
                           const double* eta2, double* part, unsigned* counter, cudaStream_t st) {
-  k_bicg_t<<<red_blocks(n), kRedThreads, 0, st>>>(v, s, n, kc, C, ld, eta2, part, counter);
+  if (c_df)
+    k_bicg_t<float2><<<red_blocks(n), kRedThreads, 0, st>>>(v, s, n, kc, (const float2*)C, ld, eta2, part, counter);
+  else
+    k_bicg_t<double><<<red_blocks(n), kRedThreads, 0, st>>>(v, s, n, kc, (const double*)C, ld, eta2, part, counter);
   return cudaGetLastError();
 }
 cudaError_t launch_bicg_r(const BicgVecs& v, BicgScalars* s, int64_t n, int kc, const double* eta1,

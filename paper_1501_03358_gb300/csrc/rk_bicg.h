@@ -34,10 +34,11 @@ cudaError_t launch_bicg_foldcoef(const double* xi, int kc, double* coefv, cudaSt
 cudaError_t launch_bicg_init(BicgScalars* s, const double* rho2, double tolabs, int maxmv, cudaStream_t st);
 cudaError_t launch_bicg_p(const BicgVecs& v, BicgScalars* s, int64_t n, cudaStream_t st);
 cudaError_t launch_bicg_alpha(BicgScalars* s, const double* dots, int kc, cudaStream_t st);
-cudaError_t launch_bicg_s(const BicgVecs& v, BicgScalars* s, int64_t n, int kc, const float2* C, int64_t ld,
+// C: kc columns (leading dimension ld), double-float (c_df) or FP64
+cudaError_t launch_bicg_s(const BicgVecs& v, BicgScalars* s, int64_t n, int kc, const void* C, bool c_df, int64_t ld,
                           const double* eta1, double* xi, double* part, unsigned* counter, cudaStream_t st);
 cudaError_t launch_bicg_half(const BicgVecs& v, BicgScalars* s, int64_t n, cudaStream_t st);
-cudaError_t launch_bicg_t(const BicgVecs& v, BicgScalars* s, int64_t n, int kc, const float2* C, int64_t ld,
+cudaError_t launch_bicg_t(const BicgVecs& v, BicgScalars* s, int64_t n, int kc, const void* C, bool c_df, int64_t ld,
                           const double* eta2, double* part, unsigned* counter, cudaStream_t st);
 cudaError_t launch_bicg_r(const BicgVecs& v, BicgScalars* s, int64_t n, int kc, const double* eta1,
                           const double* eta2, double* xi, double* part, unsigned* counter, cudaStream_t st);

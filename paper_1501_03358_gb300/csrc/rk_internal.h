@@ -250,6 +250,84 @@ cudaError_t launch_from_df(int64_t n, const float2* src, double* dst, int ncols,
                            cudaStream_t st);
 cudaError_t launch_axpy_scaled(int64_t n, const double* s, const double* v, double* x, cudaStream_t st);
 
+// ---- f64blas.cu: the same roles over FP64 columns (the RK_FP64 and RK_MIXED
+// precisions store the basis, U and C in FP64 and project in FP64).
+struct F64Dots2Args {
+  int64_t n;
+  int nq;
+  const double* Q;
+  int64_t ld;
+  const double* p;
+  const double* w;
+  double* part;       // dots2_f64_rows(n) * (2 nq + 3)
+  unsigned* counter;  // one per column group (ceil(nq / 8) + 1 of them)
+  double* out;        // 2 nq + 3
+  const int* skip_flag;
+};
+int dots2_f64_rows(int64_t n);
+cudaError_t launch_dots2_f64(const F64Dots2Args& a, cudaStream_t st);
+
+struct F64Update2Args {
+  int64_t n;
+  int nq;
+  const double* Q;
+  int64_t ld;
+  const double* a;     // device, nq
+  const double* b;     // device, nq
+  const double* scal;  // device, 3
+  double* p;
+  double* w;
+  const int* mode;
+};
+cudaError_t launch_update2_f64(const F64Update2Args& a, cudaStream_t st);
+
+struct F64UpdateArgs {
+  int64_t n;
+  int nq;
+  const double* Q;
+  int64_t ld;
+  const double* c;          // device, nq
+  const double* yin;
+  double* yout;             // may alias yin
+  const double* scale_ptr;  // nullable
+  int scale_rsqrt;
+  double* part;
+  unsigned* counter;
+  double* nrm2;             // nullable: ||y_out||^2
+  const int* skip_flag;
+};
+cudaError_t launch_update_f64(const F64UpdateArgs& a, cudaStream_t st);
+
+struct F64GemmArgs {
+  int64_t n;
+  int na, nb, nc;
+  const double* A; int64_t lda;
+  const double* Bm; int64_t ldb;
+  const double* bscale;  // nullable, multiplies the Bm columns
+  const double* P;       // device, (na + nb) x nc
+  double* out; int64_t ldo;
+  int accum;
+};
+cudaError_t launch_gemm_rows_f64(const F64GemmArgs& a, cudaStream_t st);
+
+struct F64GramArgs {
+  int64_t n;
+  int na, nb, nu;
+  const double* A; int64_t lda;
+  const double* Bm; int64_t ldb;
+  const double* d;       // nullable
+  const double* U; int64_t ldu;
+  double* part;
+  unsigned* counter;
+  double* out;
+};
+cudaError_t launch_gram_f64(const F64GramArgs& a, cudaStream_t st);
+cudaError_t launch_copy_scaled(int64_t n, const double* src, double* dst, const double* scale_ptr, int scale_rsqrt,
+                               int ncols, int64_t lds, int64_t ldd, cudaStream_t st);
+// change the storage of ncols columns (leading dimension ld) in place between
+// FP64 and double-float
+cudaError_t launch_convert_basis(int64_t n, int ncols, int64_t ld, void* base, bool to_df, cudaStream_t st);
+
 // Thread-local message returned by rk_last_error (solver.cu).
 void set_last_error(const char* msg);
 

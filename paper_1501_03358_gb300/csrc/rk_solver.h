@@ -51,7 +51,10 @@ struct SmallBuffers {
 
 cudaError_t launch_dcgs_coef(SolveState* s, SmallBuffers b, int kc, int j, int final_pass, cudaStream_t st);
 cudaError_t launch_cycle_solve(SolveState* s, SmallBuffers b, int kc, cudaStream_t st);
-cudaError_t launch_harmonic_ritz(SolveState* s, SmallBuffers b, int kc, int jj, int k, cudaStream_t st);
+// schur_f64: the Hessenberg reduction and the Francis iteration in FP64
+// (else in double-float on the FP32 pipe)
+cudaError_t launch_harmonic_ritz(SolveState* s, SmallBuffers b, int kc, int jj, int k, bool schur_f64,
+                                 cudaStream_t st);
 cudaError_t launch_set_scalar(SolveState* s, int which, cudaStream_t st);
 cudaError_t launch_cycle_init(SolveState* s, SmallBuffers b, cudaStream_t st);
 cudaError_t launch_set_tol(SolveState* s, double tol, cudaStream_t st);
@@ -64,6 +67,6 @@ cudaError_t launch_chol_rinv(int k, const double* G, double* Rinv, double* Rw, i
 // (n+1) x n column-major device arrays; outputs QC ((n+1) x k), PU (n x k) and
 // *knew (device int).
 cudaError_t launch_harmonic_ritz_small(int n, const double* G, const double* F, int k, double* QC,
-                                       double* PU, int* knew, double* ws, cudaStream_t st);
+                                       double* PU, int* knew, double* ws, bool schur_f64, cudaStream_t st);
 
 }  // namespace rk

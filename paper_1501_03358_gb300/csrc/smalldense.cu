@@ -644,10 +644,259 @@ __device__ void francis_df(float2* Hd, int ldh, float2* Zd, int n, double* wr, d
 #undef ZD
 }
 
+// A(r, c0 + i) -= tau * (A(r, c0:c0+len) v) v_i for rows r in [r0, r1).
+__device__ void apply_right(double* A, int ld, int r0, int r1, int c0, int len, const double* v, double tau) {
+  if (tau == 0.0) return;
+  for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    double w = 0.0;
+    for (int i = 0; i < len; ++i) w = fma(A[r + (int64_t)(c0 + i) * ld], v[i], w);
+    w *= tau;
+    for (int i = 0; i < len; ++i) A[r + (int64_t)(c0 + i) * ld] = fma(-w, v[i], A[r + (int64_t)(c0 + i) * ld]);
+  }
+}
+
+// 3- or 2-vector Householder reflector in FP64 (one thread):
+// (I - tau v v^T) [x y z]^T = [beta 0 0]^T with v = [1, v1, v2].
+__device__ void house_small_f64(double x, double y, double z, int len, double* v, double* tau) {
+  const double nrm = len == 3 ? sqrt(fma(x, x, fma(y, y, z * z))) : sqrt(fma(x, x, y * y));
+  v[0] = 1.0;
+  if (nrm == 0.0 || (y == 0.0 && (len == 2 || z == 0.0))) {
+    v[1] = v[2] = 0.0;
+    *tau = 0.0;
+    return;
+  }
+  const double beta = x <= 0.0 ? nrm : -nrm;
+  const double v0 = x - beta;
+  v[1] = y / v0;
+  v[2] = len == 3 ? z / v0 : 0.0;
+  *tau = (beta - x) / beta;
+}
+
+// Householder reduction to upper Hessenberg form H = Z^T M Z in FP64, in
+// place on M (n x n, leading dimension n), Z (n x n) accumulating the
+// reflectors; v: n + 1 scratch doubles. Block-wide.
+__device__ void hessenberg_f64(double* M, double* Z, int n, double* v, double* red, double* sh_beta, double* sh_tau) {
+  for (int c = 0; c + 2 < n; ++c) {
+    const int len = n - c - 1;
+    double* x = M + (int64_t)c * n + c + 1;
+    house(x, len, v, sh_beta, sh_tau, red);
+    const double tau = *sh_tau;
+    apply_left(M, n, c + 1, len, c, n, v, tau);
+    __syncthreads();
+    apply_right(M, n, 0, n, c + 1, len, v, tau);
+    apply_right(Z, n, 0, n, c + 1, len, v, tau);
+    __syncthreads();
+    for (int i = threadIdx.x; i < len; i += blockDim.x) x[i] = i == 0 ? *sh_beta : 0.0;
+    __syncthreads();
+  }
+}
+
+// Francis double-shift QR in FP64 (implicit, bulge chasing with 3 x 3
+// reflectors; exceptional shifts at iterations 10 and 20 of one
+// eigenvalue; deflation when |h_{l,l-1}| <= 2^-52 (|h_{l-1,l-1}| + |h_ll|)
+// or below 2^-52 max |h_ij|; 2 x 2 blocks with real eigenvalues split by a
+// rotation) on H (n x n Hessenberg, leading dimension n) with the
+// transformations accumulated into Z. hmax: max |h_ij|. Block-wide;
+// eigenvalues to wr, wi. On more than 40 n iterations *sfail is set.
+__device__ void francis_f64(double* H, double* Z, int n, double* wr, double* wi, double hmax, int* su, int* sl,
+                            int* siter, int* stotal, int* sfail) {
+  __shared__ double v3[3], tau3, fxyz[3], rot[2];
+  __shared__ int c_real;
+  const double eps = 2.220446049250313e-16;  // 2^-52
+  const double floor_abs = eps * hmax;
+  const int tid = threadIdx.x;
+#define HF(i, j) H[(i) + (int64_t)(j) * n]
+#define ZF(i, j) Z[(i) + (int64_t)(j) * n]
+  while (true) {
+    __syncthreads();
+    const int u = *su;
+    if (u < 0 || *sfail) break;
+    if (tid == 0) {
+      int l = u;
+      while (l > 0) {
+        const double h = fabs(HF(l, l - 1));
+        const double sc = fabs(HF(l - 1, l - 1)) + fabs(HF(l, l));
+        if (h <= eps * sc || h <= floor_abs) break;
+        --l;
+      }
+      if (l > 0) HF(l, l - 1) = 0.0;
+      *sl = l;
+    }
+    __syncthreads();
+    const int l = *sl;
+    if (l == u) {  // 1 x 1 block
+      if (tid == 0) {
+        wr[u] = HF(u, u);
+        wi[u] = 0.0;
+        *su = u - 1;
+        *siter = 0;
+      }
+      continue;
+    }
+    if (l == u - 1) {  // 2 x 2 block: split if real, record the pair if complex
+      if (tid == 0) {
+        const double a = HF(u - 1, u - 1), bb = HF(u - 1, u), c = HF(u, u - 1), d = HF(u, u);
+        const double p = 0.5 * (a - d);
+        const double disc = fma(p, p, bb * c);
+        if (disc >= 0.0) {
+          const double sq = sqrt(disc);
+          const double zz = p + (p >= 0.0 ? sq : -sq);
+          double cs = 1.0, sn = 0.0;
+          if (zz != 0.0 || c != 0.0) {
+            const double r = hypot(zz, c);
+            cs = zz / r;
+            sn = c / r;
+          }
+          rot[0] = cs;
+          rot[1] = sn;
+          c_real = 1;
+        } else {
+          c_real = 0;
+          wr[u - 1] = 0.5 * (a + d);
+          wr[u] = 0.5 * (a + d);
+          wi[u - 1] = sqrt(-disc);
+          wi[u] = -sqrt(-disc);
+        }
+      }
+      __syncthreads();
+      if (c_real) {
+        const double cs = rot[0], sn = rot[1];
+        for (int j = u - 1 + tid; j < n; j += blockDim.x) {
+          const double h1 = HF(u - 1, j), h2 = HF(u, j);
+          HF(u - 1, j) = cs * h1 + sn * h2;
+          HF(u, j) = -sn * h1 + cs * h2;
+        }
+        __syncthreads();
+        for (int i = tid; i <= u; i += blockDim.x) {
+          const double h1 = HF(i, u - 1), h2 = HF(i, u);
+          HF(i, u - 1) = cs * h1 + sn * h2;
+          HF(i, u) = -sn * h1 + cs * h2;
+        }
+        for (int i = tid; i < n; i += blockDim.x) {
+          const double z1 = ZF(i, u - 1), z2 = ZF(i, u);
+          ZF(i, u - 1) = cs * z1 + sn * z2;
+          ZF(i, u) = -sn * z1 + cs * z2;
+        }
+        __syncthreads();
+        if (tid == 0) {
+          HF(u, u - 1) = 0.0;
+          wr[u - 1] = HF(u - 1, u - 1);
+          wr[u] = HF(u, u);
+          wi[u - 1] = 0.0;
+          wi[u] = 0.0;
+        }
+      }
+      if (tid == 0) {
+        *su = u - 2;
+        *siter = 0;
+      }
+      continue;
+    }
+    // Francis double-shift step on the active window [l, u]
+    if (tid == 0) {
+      *siter += 1;
+      *stotal += 1;
+      if (*stotal > 40 * n) *sfail = 1;
+      double s, t;
+      if (*siter == 10 || *siter == 20) {
+        const double ww = fabs(HF(u, u - 1)) + (u >= 2 ? fabs(HF(u - 1, u - 2)) : 0.0);
+        s = 1.5 * ww;
+        t = ww * ww;
+      } else {
+        s = HF(u - 1, u - 1) + HF(u, u);
+        t = HF(u - 1, u - 1) * HF(u, u) - HF(u - 1, u) * HF(u, u - 1);
+      }
+      fxyz[0] = HF(l, l) * HF(l, l) + HF(l, l + 1) * HF(l + 1, l) - s * HF(l, l) + t;
+      fxyz[1] = HF(l + 1, l) * (HF(l, l) + HF(l + 1, l + 1) - s);
+      fxyz[2] = (l + 2 <= u) ? HF(l + 1, l) * HF(l + 2, l + 1) : 0.0;
+    }
+    __syncthreads();
+    if (*sfail) break;
+    for (int kk = l; kk <= u - 2; ++kk) {
+      if (tid == 0) house_small_f64(fxyz[0], fxyz[1], fxyz[2], 3, v3, &tau3);
+      __syncthreads();
+      const double tau = tau3;
+      const double v1 = v3[1], v2 = v3[2];
+      if (tau != 0.0) {
+        const int q = kk > l ? kk - 1 : l;
+        for (int j = q + tid; j < n; j += blockDim.x) {
+          const double h0 = HF(kk, j), h1 = HF(kk + 1, j), h2 = HF(kk + 2, j);
+          const double ww = tau * fma(v2, h2, fma(v1, h1, h0));
+          HF(kk, j) = h0 - ww;
+          HF(kk + 1, j) = fma(-ww, v1, h1);
+          HF(kk + 2, j) = fma(-ww, v2, h2);
+        }
+        __syncthreads();
+        const int rmaxi = kk + 3 < u ? kk + 3 : u;
+        for (int i = tid; i <= rmaxi; i += blockDim.x) {
+          const double h0 = HF(i, kk), h1 = HF(i, kk + 1), h2 = HF(i, kk + 2);
+          const double ww = tau * fma(v2, h2, fma(v1, h1, h0));
+          HF(i, kk) = h0 - ww;
+          HF(i, kk + 1) = fma(-ww, v1, h1);
+          HF(i, kk + 2) = fma(-ww, v2, h2);
+        }
+        for (int i = tid; i < n; i += blockDim.x) {
+          const double h0 = ZF(i, kk), h1 = ZF(i, kk + 1), h2 = ZF(i, kk + 2);
+          const double ww = tau * fma(v2, h2, fma(v1, h1, h0));
+          ZF(i, kk) = h0 - ww;
+          ZF(i, kk + 1) = fma(-ww, v1, h1);
+          ZF(i, kk + 2) = fma(-ww, v2, h2);
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        fxyz[0] = HF(kk + 1, kk);
+        fxyz[1] = HF(kk + 2, kk);
+        fxyz[2] = kk < u - 2 ? HF(kk + 3, kk) : 0.0;
+      }
+      __syncthreads();
+    }
+    // final 2-vector reflector on rows u-1, u
+    if (tid == 0) house_small_f64(fxyz[0], fxyz[1], 0.0, 2, v3, &tau3);
+    __syncthreads();
+    {
+      const double tau = tau3;
+      const double v1 = v3[1];
+      if (tau != 0.0) {
+        const int q = u - 2 >= l ? u - 2 : l;
+        for (int j = q + tid; j < n; j += blockDim.x) {
+          const double h0 = HF(u - 1, j), h1 = HF(u, j);
+          const double ww = tau * fma(v1, h1, h0);
+          HF(u - 1, j) = h0 - ww;
+          HF(u, j) = fma(-ww, v1, h1);
+        }
+        __syncthreads();
+        for (int i = tid; i <= u; i += blockDim.x) {
+          const double h0 = HF(i, u - 1), h1 = HF(i, u);
+          const double ww = tau * fma(v1, h1, h0);
+          HF(i, u - 1) = h0 - ww;
+          HF(i, u) = fma(-ww, v1, h1);
+        }
+        for (int i = tid; i < n; i += blockDim.x) {
+          const double h0 = ZF(i, u - 1), h1 = ZF(i, u);
+          const double ww = tau * fma(v1, h1, h0);
+          ZF(i, u - 1) = h0 - ww;
+          ZF(i, u) = fma(-ww, v1, h1);
+        }
+      }
+    }
+    __syncthreads();
+    // the entries below the subdiagonal that rounding leaves behind
+    if (tid == 0) {
+      for (int i = l + 2; i <= u; ++i) {
+        HF(i, i - 2) = 0.0;
+        if (i >= l + 3) HF(i, i - 3) = 0.0;
+      }
+    }
+  }
+#undef HF
+#undef ZF
+}
+
 // Core: G, F already in w.G, w.F (ld n+1). Outputs QC (ld ldqc, n+1 rows),
 // PU (ld ldpu, n rows), *knew_out, *status_out (0 ok).
 __device__ void hr_core(HRWork w, int n, int k, double* QC, int ldqc, double* PU, int ldpu, int* knew_out,
-                        int* status_out) {
+                        int* status_out, int schur_f64) {
   __shared__ double red[32];
   __shared__ double sh_beta, sh_tau;
   __shared__ int sh_u, sh_l, sh_iter, sh_total, sh_fail, sh_knew;
@@ -687,7 +936,32 @@ __device__ void hr_core(HRWork w, int n, int k, double* QC, int ldqc, double* PU
   }
   __syncthreads();
   // ---- 3./4. Hessenberg form and real Schur form (T in M, Schur vectors
-  //         in Z). Both are long chains of small dependent steps, and on this
+  //         in Z), in FP64 (schur_f64) ...
+  double hnorm = 0.0;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) hnorm = fmax(hnorm, fabs(w.M[t]));
+  hnorm = block_sum(hnorm, red);  // a bound on max |m_ij|, used for the scale and zero tests
+  if (schur_f64) {
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) w.Z[t] = (t % (n + 1)) == 0 ? 1.0 : 0.0;
+    __syncthreads();
+    hessenberg_f64(w.M, w.Z, n, w.v, red, &sh_beta, &sh_tau);
+    double hm = 0.0;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) hm = fmax(hm, fabs(w.M[t]));
+    __shared__ double sh_hm[32];
+    for (int o = 16; o > 0; o >>= 1) hm = fmax(hm, __shfl_xor_sync(0xffffffffu, hm, o));
+    if ((threadIdx.x & 31) == 0) sh_hm[threadIdx.x >> 5] = hm;
+    if (threadIdx.x == 0) {
+      sh_u = n - 1;
+      sh_iter = 0;
+      sh_total = 0;
+      sh_fail = 0;
+    }
+    __syncthreads();
+    hm = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) hm = fmax(hm, sh_hm[q]);
+    francis_f64(w.M, w.Z, n, w.wr, w.wi, hm, &sh_u, &sh_l, &sh_iter, &sh_total, &sh_fail);
+    __syncthreads();
+  } else {
+  //         ... or in double-float. Both are long chains of small dependent steps, and on this
   //         GPU an FP64 instruction costs a warp ~64 cycles even with one
   //         lane active, so they run in double-float arithmetic on the FP32
   //         pipe (about 48 significant bits): M, scaled by a power of two
@@ -696,9 +970,6 @@ __device__ void hr_core(HRWork w, int n, int k, double* QC, int ldqc, double* PU
   //         n+1, conflict-free column sweeps), Z into the M workspace; the
   //         Schur-vector updates run on other warps than the row updates of
   //         H; T (scaled back), Z and the eigenvalues return to FP64.
-  double hnorm = 0.0;
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) hnorm = fmax(hnorm, fabs(w.M[t]));
-  hnorm = block_sum(hnorm, red);  // a bound on max |m_ij|, used for the scale and zero tests
   __shared__ double sh_scale;
   if (threadIdx.x == 0) {
     int ex = 0;
@@ -747,6 +1018,7 @@ __device__ void hr_core(HRWork w, int n, int k, double* QC, int ldqc, double* PU
     w.wr[t] /= hscale;
     w.wi[t] /= hscale;
   }
+  }  // double-float Schur form
   double* H = w.M;
 #define HH(i, j) H[(i) + (int64_t)(j) * n]
   __syncthreads();
@@ -1031,7 +1303,7 @@ __device__ void hr_core(HRWork w, int n, int k, double* QC, int ldqc, double* PU
 // Solver wrapper: builds G and F from the cycle's B, H and Gram, runs the
 // core, folds the column scales of the stored V into QC and PU.
 __global__ void __launch_bounds__(kHRThreads) k_harmonic_ritz(SolveState* s, SmallBuffers b, int kc, int jj, int k,
-                                                              int use_smem) {
+                                                              int use_smem, int schur_f64) {
   extern __shared__ double dsm[];
   const int n = kc + jj;
   double* base = use_smem ? dsm : b.hrws;
@@ -1057,7 +1329,7 @@ __global__ void __launch_bounds__(kHRThreads) k_harmonic_ritz(SolveState* s, Sma
   }
   __syncthreads();
   __shared__ int knew, st;
-  hr_core(w, n, k, b.QC, n + 1, b.PU, n, &knew, &st);
+  hr_core(w, n, k, b.QC, n + 1, b.PU, n, &knew, &st, schur_f64);
   __syncthreads();
   // fold the stored-column scales (v_l = sv[l] q_l) into the coefficients
   for (int t = threadIdx.x; t < (n + 1) * knew; t += blockDim.x) {
@@ -1076,7 +1348,7 @@ __global__ void __launch_bounds__(kHRThreads) k_harmonic_ritz(SolveState* s, Sma
 
 __global__ void __launch_bounds__(kHRThreads) k_harmonic_ritz_small(int n, const double* G, const double* F, int k,
                                                                     double* QC, double* PU, int* knew_out,
-                                                                    double* ws, int use_smem) {
+                                                                    double* ws, int use_smem, int schur_f64) {
   extern __shared__ double dsm[];
   double* base = use_smem ? dsm : ws;
   HRWork w = hr_carve(base, n);
@@ -1086,7 +1358,7 @@ __global__ void __launch_bounds__(kHRThreads) k_harmonic_ritz_small(int n, const
   }
   __syncthreads();
   __shared__ int knew, st;
-  hr_core(w, n, k, QC, n + 1, PU, n, &knew, &st);
+  hr_core(w, n, k, QC, n + 1, PU, n, &knew, &st, schur_f64);
   __syncthreads();
   if (threadIdx.x == 0) *knew_out = st == 0 ? knew : -st;
 }
@@ -1176,7 +1448,8 @@ cudaError_t launch_cycle_solve(SolveState* s, SmallBuffers b, int kc, cudaStream
 
 static constexpr size_t kHRSmemMax = 200 * 1024;
 
-cudaError_t launch_harmonic_ritz(SolveState* s, SmallBuffers b, int kc, int jj, int k, cudaStream_t st) {
+cudaError_t launch_harmonic_ritz(SolveState* s, SmallBuffers b, int kc, int jj, int k, bool schur_f64,
+                                 cudaStream_t st) {
   const int n = kc + jj;
   const size_t bytes = hr_doubles_host(n) * sizeof(double);
   const int use_smem = bytes <= kHRSmemMax ? 1 : 0;
@@ -1185,12 +1458,12 @@ cudaError_t launch_harmonic_ritz(SolveState* s, SmallBuffers b, int kc, int jj, 
   once_per_device(done, [] {
     cudaFuncSetAttribute(k_harmonic_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHRSmemMax);
   });
-  k_harmonic_ritz<<<1, kHRThreads, use_smem ? bytes : 0, st>>>(s, b, kc, jj, k, use_smem);
+  k_harmonic_ritz<<<1, kHRThreads, use_smem ? bytes : 0, st>>>(s, b, kc, jj, k, use_smem, schur_f64 ? 1 : 0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_harmonic_ritz_small(int n, const double* G, const double* F, int k, double* QC, double* PU,
-                                       int* knew, double* ws, cudaStream_t st) {
+                                       int* knew, double* ws, bool schur_f64, cudaStream_t st) {
   const size_t bytes = hr_doubles_host(n) * sizeof(double);
   const int use_smem = bytes <= kHRSmemMax ? 1 : 0;
   // one-time attribute setup per device
@@ -1198,7 +1471,8 @@ cudaError_t launch_harmonic_ritz_small(int n, const double* G, const double* F, 
   once_per_device(done, [] {
     cudaFuncSetAttribute(k_harmonic_ritz_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHRSmemMax);
   });
-  k_harmonic_ritz_small<<<1, kHRThreads, use_smem ? bytes : 0, st>>>(n, G, F, k, QC, PU, knew, ws, use_smem);
+  k_harmonic_ritz_small<<<1, kHRThreads, use_smem ? bytes : 0, st>>>(n, G, F, k, QC, PU, knew, ws, use_smem,
+                                                                     schur_f64 ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -193,8 +193,9 @@ struct rk_problem {
   double* dinv = nullptr;
   double anorm_f = 0.0;  // ||A||_F
   int kmax = 0, mcap = 0, kdim = 0;
-  float2* QB = nullptr;           // double-float basis [C | V]
-  float2* Ub = nullptr;           // double-float U
+  float2* QB = nullptr;           // basis [C | V]: FP64 or double-float (bdf), 8 bytes per element
+  float2* Ub = nullptr;           // U, in the same format
+  bool bdf = false;               // the stored recycle space is double-float (RK_DF solves) rather than FP64
   double* rvec = nullptr;         // FP64 residual of the rGCROT cycle
   float* coef32 = nullptr;        // mixed precision: FP32 copy of the bands
   float* dinv32 = nullptr;        // mixed precision: FP32 1/a_pp
@@ -359,13 +360,37 @@ int norm2_into(rk_problem* p, const double* v, int slot, cudaStream_t st) {
   return RK_OK;
 }
 
-// out = [Q^T w (nq DF columns), w^T w (self), e^T w (extra, FP64)]
-int dfdots_launch(rk_problem* p, const float2* Q, int nq, const void* w, bool w_df, double* out, const int* skip,
-                  cudaStream_t st, const double* extra0 = nullptr, int self = 0) {
+// The stored basis, U and C are FP64 (RK_FP64, RK_MIXED) or double-float
+// (RK_DF): p->bdf. Each helper below takes basis columns as untyped pointers
+// and runs the kernel of the stored format; vectors named FP64 are FP64 in
+// either case.
+
+// out = [Q^T w (nq basis columns), then w^T w (self) or e^T w (extra, FP64)];
+// w is a basis column (w_basis) or an FP64 vector
+int bdots_launch(rk_problem* p, const void* Q, int nq, const void* w, bool w_basis, double* out, const int* skip,
+                 cudaStream_t st, const double* extra0 = nullptr, int self = 0) {
+  ProfScope ps(&p->prof, PC_DOTS, 8.0 * (nq + (extra0 ? 2 : 0) + 1) * (double)p->n, st);
+  if (!p->bdf) {
+    DotsArgs a{};
+    a.n = p->n;
+    a.nq = nq;
+    a.Q = (const double*)Q;
+    a.ld = p->ld;
+    a.extra[0] = extra0;
+    a.ne = extra0 ? 1 : 0;
+    a.self = self;
+    a.w = (const double*)w;
+    a.part = p->part;
+    a.counter = p->counter;
+    a.out = out;
+    a.skip_flag = skip;
+    RK_CUDA(launch_dots(a, st));
+    return RK_OK;
+  }
   DFDotsArgs a{};
   a.n = p->n;
   a.nq = nq;
-  a.Q = Q;
+  a.Q = (const float2*)Q;
   a.ld = p->ld;
   a.extra[0] = extra0;
   a.ne = extra0 ? 1 : 0;
@@ -375,19 +400,37 @@ int dfdots_launch(rk_problem* p, const float2* Q, int nq, const void* w, bool w_
   a.counter = p->counter;
   a.out = out;
   a.skip_flag = skip;
-  ProfScope ps(&p->prof, PC_DOTS, 8.0 * (nq + (extra0 ? 2 : 0) + 1) * (double)p->n, st);
-  RK_CUDA(launch_dfdots(a, w_df, st));
+  RK_CUDA(launch_dfdots(a, w_basis, st));
   return RK_OK;
 }
 
-// yout = (yin - Q c) * scale, ||yout||^2 -> nrm2
-int dfupdate_launch(rk_problem* p, const float2* Q, int nq, const double* c, const void* yin, bool in_df, void* yout,
-                    bool out_df, double* nrm2, const int* skip, cudaStream_t st, const double* scale_ptr = nullptr,
-                    int scale_rsqrt = 0) {
+// y_out = (y_in - Q c) * scale, ||y_out||^2 -> nrm2 (y FP64)
+int bupdate_launch(rk_problem* p, const void* Q, int nq, const double* c, const double* yin, double* yout,
+                   double* nrm2, const int* skip, cudaStream_t st, const double* scale_ptr = nullptr,
+                   int scale_rsqrt = 0) {
+  ProfScope ps(&p->prof, PC_UPDATE, 8.0 * (nq + 2) * (double)p->n, st);
+  if (!p->bdf) {
+    F64UpdateArgs a{};
+    a.n = p->n;
+    a.nq = nq;
+    a.Q = (const double*)Q;
+    a.ld = p->ld;
+    a.c = c;
+    a.yin = yin;
+    a.yout = yout;
+    a.scale_ptr = scale_ptr;
+    a.scale_rsqrt = scale_rsqrt;
+    a.part = p->part;
+    a.counter = p->counter;
+    a.nrm2 = nrm2;
+    a.skip_flag = skip;
+    RK_CUDA(launch_update_f64(a, st));
+    return RK_OK;
+  }
   DFUpdateArgs a{};
   a.n = p->n;
   a.nq = nq;
-  a.Q = Q;
+  a.Q = (const float2*)Q;
   a.ld = p->ld;
   a.c = c;
   a.yin = yin;
@@ -398,72 +441,196 @@ int dfupdate_launch(rk_problem* p, const float2* Q, int nq, const double* c, con
   a.counter = p->counter;
   a.nrm2 = nrm2;
   a.skip_flag = skip;
-  ProfScope ps(&p->prof, PC_UPDATE, 8.0 * (nq + 2) * (double)p->n, st);
-  RK_CUDA(launch_dfupdate(a, in_df, out_df, st));
+  RK_CUDA(launch_dfupdate(a, false, false, st));
   return RK_OK;
 }
 
-// dots = [Q^T p, Q^T w, p^T p, p^T w, w^T w] of one Arnoldi step
-int dfdots2_launch(rk_problem* p, const float2* Q, int nq, const float2* pv, const float2* w, double* out,
-                   const int* skip, cudaStream_t st) {
+// dots = [Q^T p, Q^T w, p^T p, p^T w, w^T w] of one Arnoldi step (basis columns)
+int bdots2_launch(rk_problem* p, const void* Q, int nq, const void* pv, const void* w, double* out, const int* skip,
+                  cudaStream_t st) {
+  ProfScope ps(&p->prof, PC_DOTS, 8.0 * (nq + 2) * (double)p->n, st);
+  if (!p->bdf) {
+    F64Dots2Args a{};
+    a.n = p->n;
+    a.nq = nq;
+    a.Q = (const double*)Q;
+    a.ld = p->ld;
+    a.p = (const double*)pv;
+    a.w = (const double*)w;
+    a.part = p->part;
+    a.counter = p->counter + kGroupCounters;
+    a.out = out;
+    a.skip_flag = skip;
+    RK_CUDA(launch_dots2_f64(a, st));
+    return RK_OK;
+  }
   DFDots2Args a{};
   a.n = p->n;
   a.nq = nq;
-  a.Q = Q;
+  a.Q = (const float2*)Q;
   a.ld = p->ld;
-  a.p = pv;
-  a.w = w;
+  a.p = (const float2*)pv;
+  a.w = (const float2*)w;
   a.part = p->part;
   a.counter = p->counter + kGroupCounters;
   a.out = out;
   a.skip_flag = skip;
   a.err = &p->st->dev_err;
-  ProfScope ps(&p->prof, PC_DOTS, 8.0 * (nq + 2) * (double)p->n, st);
   RK_CUDA(launch_dfdots2(a, st));
   return RK_OK;
 }
 
 // v = (p - Q a) s0 (in place), p_next = (w - Q b) s1 - v s2 (in place of w)
-int dfupdate2_launch(rk_problem* p, const float2* Q, int nq, const double* ca, const double* cb, const double* scal,
-                     float2* pv, float2* w, const int* mode, bool both, cudaStream_t st) {
+int bupdate2_launch(rk_problem* p, const void* Q, int nq, const double* ca, const double* cb, const double* scal,
+                    void* pv, void* w, const int* mode, bool both, cudaStream_t st) {
+  ProfScope ps(&p->prof, PC_UPDATE, 8.0 * (nq + (both ? 4 : 2)) * (double)p->n, st);
+  if (!p->bdf) {
+    F64Update2Args a{};
+    a.n = p->n;
+    a.nq = nq;
+    a.Q = (const double*)Q;
+    a.ld = p->ld;
+    a.a = ca;
+    a.b = cb;
+    a.scal = scal;
+    a.p = (double*)pv;
+    a.w = (double*)w;
+    a.mode = mode;
+    RK_CUDA(launch_update2_f64(a, st));
+    return RK_OK;
+  }
   DFUpdate2Args a{};
   a.n = p->n;
   a.nq = nq;
-  a.Q = Q;
+  a.Q = (const float2*)Q;
   a.ld = p->ld;
   a.a = ca;
   a.b = cb;
   a.scal = scal;
-  a.p = pv;
-  a.w = w;
+  a.p = (float2*)pv;
+  a.w = (float2*)w;
   a.mode = mode;
-  ProfScope ps(&p->prof, PC_UPDATE, 8.0 * (nq + (both ? 4 : 2)) * (double)p->n, st);
   RK_CUDA(launch_dfupdate2(a, st));
   return RK_OK;
 }
 
-// out (+)= [A cols | bscale .* B cols] P  (A, B double-float; out DF or FP64)
-int dfgemm_launch(rk_problem* p, const float2* A, int na, const float2* Bm, int nb, const double* bscale,
-                  const double* P, int nc, void* out, bool out_df, int accum, cudaStream_t st) {
+// out (+)= [A cols | bscale .* B cols] P  (A, B basis columns; out basis
+// columns (out_basis) or an FP64 vector)
+int bgemm_launch(rk_problem* p, const void* A, int na, const void* Bm, int nb, const double* bscale, const double* P,
+                 int nc, void* out, bool out_basis, int accum, cudaStream_t st) {
+  ProfScope ps(&p->prof, PC_GEMM, 8.0 * (na + nb + nc * (accum ? 2 : 1) + (bscale ? 1 : 0)) * (double)p->n, st);
+  if (!p->bdf) {
+    F64GemmArgs a{};
+    a.n = p->n;
+    a.na = na;
+    a.nb = nb;
+    a.nc = nc;
+    a.A = (const double*)A;
+    a.lda = p->ld;
+    a.Bm = (const double*)Bm;
+    a.ldb = p->ld;
+    a.bscale = bscale;
+    a.P = P;
+    a.out = (double*)out;
+    a.ldo = p->ld;
+    a.accum = accum;
+    RK_CUDA(launch_gemm_rows_f64(a, st));
+    return RK_OK;
+  }
   DFGemmArgs a{};
   a.n = p->n;
   a.na = na;
   a.nb = nb;
   a.nc = nc;
-  a.A = A;
+  a.A = (const float2*)A;
   a.lda = p->ld;
-  a.Bm = Bm;
+  a.Bm = (const float2*)Bm;
   a.ldb = p->ld;
   a.bscale = bscale;
   a.P = P;
   a.out = out;
   a.ldo = p->ld;
   a.accum = accum;
-  ProfScope ps(&p->prof, PC_GEMM, 8.0 * (na + nb + nc * (accum ? 2 : 1) + (bscale ? 1 : 0)) * (double)p->n, st);
-  if (p->sb.tcws != nullptr && dfgemm_tc_supported(a, out_df))
+  if (p->sb.tcws != nullptr && dfgemm_tc_supported(a, out_basis))
     RK_CUDA(launch_dfgemm_tc(a, p->sb.tcws, &p->st->dev_err, st));
   else
-    RK_CUDA(launch_dfgemm_rows(a, out_df, st));
+    RK_CUDA(launch_dfgemm_rows(a, out_basis, st));
+  return RK_OK;
+}
+
+// out[q + l*(na+nb)] = [A B]_q^T diag(d) U_l (basis columns; d FP64, nullable)
+int bgram_launch(rk_problem* p, const void* A, int na, const void* Bm, int nb, const double* d, const void* U, int nu,
+                 double* out, cudaStream_t st) {
+  ProfScope ps(&p->prof, PC_GRAM, 8.0 * (na + nb + nu + (d ? 1 : 0)) * (double)p->n, st);
+  if (!p->bdf) {
+    F64GramArgs g{};
+    g.n = p->n;
+    g.na = na;
+    g.nb = nb;
+    g.nu = nu;
+    g.A = (const double*)A;
+    g.lda = p->ld;
+    g.Bm = (const double*)Bm;
+    g.ldb = p->ld;
+    g.d = d;
+    g.U = (const double*)U;
+    g.ldu = p->ld;
+    g.part = p->part;
+    g.counter = p->counter;
+    g.out = out;
+    RK_CUDA(launch_gram_f64(g, st));
+    return RK_OK;
+  }
+  DFGramArgs g{};
+  g.n = p->n;
+  g.na = na;
+  g.nb = nb;
+  g.nu = nu;
+  g.A = (const float2*)A;
+  g.lda = p->ld;
+  g.Bm = (const float2*)Bm;
+  g.ldb = p->ld;
+  g.d = d;
+  g.U = (const float2*)U;
+  g.ldu = p->ld;
+  g.part = p->part;
+  g.counter = p->counter;
+  g.out = out;
+  RK_CUDA(launch_dfgram(g, st));
+  return RK_OK;
+}
+
+// ncols FP64 columns (leading dimension lds) into basis columns (ldd),
+// times scale (1, *scale_ptr or 1/sqrt(*scale_ptr))
+int to_basis(rk_problem* p, const double* src, void* dst, const double* scale_ptr, int scale_rsqrt, int ncols,
+             int64_t lds, int64_t ldd, cudaStream_t st) {
+  if (p->bdf)
+    RK_CUDA(launch_to_df(p->n, src, (float2*)dst, scale_ptr, scale_rsqrt, ncols, lds, ldd, st));
+  else
+    RK_CUDA(launch_copy_scaled(p->n, src, (double*)dst, scale_ptr, scale_rsqrt, ncols, lds, ldd, st));
+  return RK_OK;
+}
+
+// basis columns into FP64 columns
+int from_basis(const rk_problem* p, const void* src, double* dst, int ncols, int64_t lds, int64_t ldd,
+               cudaStream_t st) {
+  if (p->bdf)
+    RK_CUDA(launch_from_df(p->n, (const float2*)src, dst, ncols, lds, ldd, st));
+  else
+    RK_CUDA(launch_copy_scaled(p->n, (const double*)src, dst, nullptr, 0, ncols, lds, ldd, st));
+  return RK_OK;
+}
+
+// The storage of the recycle space for a solve of the given precision:
+// RK_DF keeps the basis, U and C in double-float, the others in FP64; a
+// stored space in the other format is converted in place.
+int ensure_basis(rk_problem* p, bool want_df, cudaStream_t st) {
+  if (p->bdf == want_df) return RK_OK;
+  if (p->kdim > 0) {
+    RK_CUDA(launch_convert_basis(p->n, p->kdim, p->ld, p->Cblk(p->kdim), want_df, st));
+    RK_CUDA(launch_convert_basis(p->n, p->kdim, p->ld, p->Ublk(p->kdim), want_df, st));
+  }
+  p->bdf = want_df;
   return RK_OK;
 }
 
@@ -618,37 +785,28 @@ int derive_c_from_u(rk_problem* p, int k, cudaStream_t st, bool left = false, in
   if (left && pc == RK_PC_SUBDOMAIN) {
     RK_TRY(ensure_subdomain(p));
     for (int c = 0; c < k; ++c)
-      RK_TRY(opapply_launch(p, RK_FP64, Ud + (int64_t)c * p->ld, true, Cd + (int64_t)c * p->ld, true, nullptr, st,
+      RK_TRY(opapply_launch(p, RK_FP64, Ud + (int64_t)c * p->ld, p->bdf, Cd + (int64_t)c * p->ld, p->bdf, nullptr, st,
                             true, pc));
   } else {
-    for (int c = 0; c < k; ++c)
-      RK_CUDA(launch_stencil_df(p->d, p->S, left ? ST_LEFT : ST_PLAIN, p->coef, p->dinv, Ud + (int64_t)c * p->ld,
-                                true, Cd + (int64_t)c * p->ld, true, nullptr, st));
+    for (int c = 0; c < k; ++c) {
+      if (p->bdf)
+        RK_CUDA(launch_stencil_df(p->d, p->S, left ? ST_LEFT : ST_PLAIN, p->coef, p->dinv, Ud + (int64_t)c * p->ld,
+                                  true, Cd + (int64_t)c * p->ld, true, nullptr, st));
+      else
+        RK_CUDA(launch_stencil(p->d, p->S, left ? ST_LEFT : ST_PLAIN, p->coef, p->dinv,
+                               (const double*)(Ud + (int64_t)c * p->ld), nullptr, (double*)(Cd + (int64_t)c * p->ld),
+                               nullptr, nullptr, nullptr, nullptr, st));
+    }
   }
   for (int pass = 0; pass < 2; ++pass) {
-    DFGramArgs g{};
-    g.n = p->n;
-    g.na = k;
-    g.nb = 0;
-    g.nu = k;
-    g.A = Cd;
-    g.lda = p->ld;
-    g.Bm = nullptr;
-    g.ldb = p->ld;
-    g.d = nullptr;
-    g.U = Cd;
-    g.ldu = p->ld;
-    g.part = p->part;
-    g.counter = p->counter;
-    g.out = G;
-    RK_CUDA(launch_dfgram(g, st));
+    RK_TRY(bgram_launch(p, Cd, k, nullptr, 0, nullptr, Cd, k, G, st));
     RK_CUDA(launch_chol_rinv(k, G, Rinv, Rw, p->istat, st));
     int hs = 0;
     RK_CUDA(cudaMemcpyAsync(&hs, p->istat, sizeof(int), cudaMemcpyDeviceToHost, st));
     RK_CUDA(cudaStreamSynchronize(st));
     if (hs != 0) return fail(RK_E_INVALID, "A U is rank deficient (Cholesky of C~^T C~ failed)");
-    RK_TRY(dfgemm_launch(p, Cd, k, nullptr, 0, nullptr, Rinv, k, Cd, true, 0, st));
-    RK_TRY(dfgemm_launch(p, Ud, k, nullptr, 0, nullptr, Rinv, k, Ud, true, 0, st));
+    RK_TRY(bgemm_launch(p, Cd, k, nullptr, 0, nullptr, Rinv, k, Cd, true, 0, st));
+    RK_TRY(bgemm_launch(p, Ud, k, nullptr, 0, nullptr, Rinv, k, Ud, true, 0, st));
   }
   return RK_OK;
 }
@@ -668,9 +826,9 @@ int ensure_side(rk_problem* p, bool left, int pc, cudaStream_t st) {
 int project_residual(rk_problem* p, int kc, double* r, double* x, cudaStream_t st) {
   if (kc == 0) return RK_OK;  // ||r||^2 already in st->rho2
   double* xi = p->eta;        // kc
-  RK_TRY(dfdots_launch(p, p->Cblk(kc), kc, r, false, xi, nullptr, st));
-  RK_TRY(dfupdate_launch(p, p->Cblk(kc), kc, xi, r, false, r, false, &p->st->rho2, nullptr, st));
-  RK_TRY(dfgemm_launch(p, p->Ublk(kc), kc, nullptr, 0, nullptr, xi, 1, x, false, 1, st));
+  RK_TRY(bdots_launch(p, p->Cblk(kc), kc, r, false, xi, nullptr, st));
+  RK_TRY(bupdate_launch(p, p->Cblk(kc), kc, xi, r, r, &p->st->rho2, nullptr, st));
+  RK_TRY(bgemm_launch(p, p->Ublk(kc), kc, nullptr, 0, nullptr, xi, 1, x, false, 1, st));
   return RK_OK;
 }
 
@@ -774,28 +932,28 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
     // a CUDA graph and replayed (not while the per-kernel profiler runs)
     const bool keep_last = update && k > 0;
     auto cycle = [&](cudaStream_t st) -> int {
-      // v_1 = r / rho, stored double-float
-      RK_CUDA(launch_to_df(p->n, r, p->Vcol(0), &p->st->rho2, 1, 1, p->ld, p->ld, st));
+      // v_1 = r / rho, in the basis format
+      RK_TRY(to_basis(p, r, p->Vcol(0), &p->st->rho2, 1, 1, p->ld, p->ld, st));
       { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_cycle_init(p->st, p->sb, st)); }
       // per step: one product, one fused inner-product pass and one update
       // pass per step (Gram-Schmidt against [C V_j] with the second pass of
       // each vector delayed to the next step)
       for (int j = 0; j < steps; ++j) {
-        RK_TRY(opapply_launch(p, opk, p->Vcol(j), true, p->Vcol(j + 1), true, done, st, left, pc));
+        RK_TRY(opapply_launch(p, opk, p->Vcol(j), p->bdf, p->Vcol(j + 1), p->bdf, done, st, left, pc));
         const int nq = kc + j;
-        RK_TRY(dfdots2_launch(p, p->Cblk(kc), nq, p->Vcol(j), p->Vcol(j + 1), p->sb.dots, done, st));
+        RK_TRY(bdots2_launch(p, p->Cblk(kc), nq, p->Vcol(j), p->Vcol(j + 1), p->sb.dots, done, st));
         { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_dcgs_coef(p->st, p->sb, kc, j, 0, st)); }
-        RK_TRY(dfupdate2_launch(p, p->Cblk(kc), nq, p->sb.dots, p->sb.dots + nq, p->st->scal, p->Vcol(j),
-                                p->Vcol(j + 1), &p->st->upd_mode, true, st));
+        RK_TRY(bupdate2_launch(p, p->Cblk(kc), nq, p->sb.dots, p->sb.dots + nq, p->st->scal, p->Vcol(j),
+                               p->Vcol(j + 1), &p->st->upd_mode, true, st));
       }
       // cycle end without convergence: second pass of the last vector
       // (completes column steps-1; v_steps is kept for the recycle update)
       const int nq = kc + steps;
-      RK_TRY(dfdots_launch(p, p->Cblk(kc), nq, p->Vcol(steps), true, p->sb.dots, done, st, nullptr, 1));
+      RK_TRY(bdots_launch(p, p->Cblk(kc), nq, p->Vcol(steps), true, p->sb.dots, done, st, nullptr, 1));
       { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_dcgs_coef(p->st, p->sb, kc, steps, 1, st)); }
       if (keep_last)
-        RK_TRY(dfupdate2_launch(p, p->Cblk(kc), nq, p->sb.dots, p->sb.dots, p->st->scal, p->Vcol(steps),
-                                p->Vcol(steps), &p->st->upd_mode, false, st));
+        RK_TRY(bupdate2_launch(p, p->Cblk(kc), nq, p->sb.dots, p->sb.dots, p->st->scal, p->Vcol(steps),
+                               p->Vcol(steps), &p->st->upd_mode, false, st));
       return RK_OK;
     };
     if (p->prof.on) {
@@ -831,38 +989,25 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
     cycles += 1;
     // y, z = -B y, x <- x + M^{-1} V_j y + U z (left: x <- x + V_j y + U z)
     { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_cycle_solve(p->st, p->sb, kc, st)); }
-    RK_TRY(dfgemm_launch(p, p->Ublk(kc), kc, p->Vcol(0), jj, left ? nullptr : p->dinv, p->sb.xcoef, 1, x, false, 1,
-                         st));
+    RK_TRY(bgemm_launch(p, p->Ublk(kc), kc, p->Vcol(0), jj, left ? nullptr : p->dinv, p->sb.xcoef, 1, x, false, 1,
+                        st));
     words += model_words_cycle(p->S, kc, jj, m);
     // recycle update (harmonic Ritz)
     if (update && k > 0) {
       if (kc > 0) {
-        DFGramArgs g{};
-        g.n = p->n;
-        g.na = kc;
-        g.nb = jj + 1;
-        g.nu = kc;
-        g.A = p->Cblk(kc);
-        g.lda = p->ld;
-        g.Bm = p->Vcol(0);
-        g.ldb = p->ld;
-        g.d = left ? nullptr : p->coef;  // M = diag(A) = band 0 (left: F = W_hat^T W)
-        g.U = p->Ublk(kc);
-        g.ldu = p->ld;
-        g.part = p->part;
-        g.counter = p->counter;
-        g.out = p->sb.gram;
-        { ProfScope ps_(&p->prof, PC_GRAM, 8.0 * (g.na + g.nb + g.nu + 1) * (double)p->n, st); RK_CUDA(launch_dfgram(g, st)); }
+        // [C V_{j+1}]^T (M U), M = diag(A) = band 0 (left: F = W_hat^T W, no M)
+        RK_TRY(bgram_launch(p, p->Cblk(kc), kc, p->Vcol(0), jj + 1, left ? nullptr : p->coef, p->Ublk(kc), kc,
+                            p->sb.gram, st));
       }
-      { ProfScope ps_(&p->prof, PC_HRITZ, 0.0, st); RK_CUDA(launch_harmonic_ritz(p->st, p->sb, kc, jj, k, st)); }
+      { ProfScope ps_(&p->prof, PC_HRITZ, 0.0, st); RK_CUDA(launch_harmonic_ritz(p->st, p->sb, kc, jj, k, !p->bdf, st)); }
       RK_TRY(sync_state(p, st));
       const int knew = p->st_h->knew;
       if (p->st_h->hr_status == 0 && knew > 0) {
         // C <- [C V_{j+1}] QC, U <- [U, M^{-1} V_j] PU (left: [U, V_j] PU), in place (row tiles)
-        RK_TRY(dfgemm_launch(p, p->Cblk(kc), kc, p->Vcol(0), jj + 1, nullptr, p->sb.QC, knew, p->Cblk(knew), true, 0,
-                             st));
-        RK_TRY(dfgemm_launch(p, p->Ublk(kc), kc, p->Vcol(0), jj, left ? nullptr : p->dinv, p->sb.PU, knew,
-                             p->Ublk(knew), true, 0, st));
+        RK_TRY(bgemm_launch(p, p->Cblk(kc), kc, p->Vcol(0), jj + 1, nullptr, p->sb.QC, knew, p->Cblk(knew), true, 0,
+                            st));
+        RK_TRY(bgemm_launch(p, p->Ublk(kc), kc, p->Vcol(0), jj, left ? nullptr : p->dinv, p->sb.PU, knew,
+                            p->Ublk(knew), true, 0, st));
         kc = knew;
         p->kdim = knew;
         words += 6.0 * kc + 3.0 * jj + 4;
@@ -939,10 +1084,10 @@ int solve_bicg(rk_problem* p, const double* b, double* x, const rk_solve_params&
     // r = b - A x; its projection: eta1 = C^T r, r -= C eta1, xi = -eta1
     RK_TRY(stencil_launch(p, ST_RESID, x, b, v.r, p->part, p->counter, &p->st->rho2, nullptr, st));
     if (kc) {
-      RK_TRY(dfdots_launch(p, p->Cblk(kc), kc, v.r, false, xi, nullptr, st));
-      RK_TRY(dfupdate_launch(p, p->Cblk(kc), kc, xi, v.r, false, v.r, false, &p->st->rho2, nullptr, st));
+      RK_TRY(bdots_launch(p, p->Cblk(kc), kc, v.r, false, xi, nullptr, st));
+      RK_TRY(bupdate_launch(p, p->Cblk(kc), kc, xi, v.r, v.r, &p->st->rho2, nullptr, st));
       // xi = -eta1 enters x at once (x <- x + U eta1); xi restarts from 0
-      RK_TRY(dfgemm_launch(p, p->Ublk(kc), kc, nullptr, 0, nullptr, xi, 1, x, false, 1, st));
+      RK_TRY(bgemm_launch(p, p->Ublk(kc), kc, nullptr, 0, nullptr, xi, 1, x, false, 1, st));
       RK_CUDA(cudaMemsetAsync(xi, 0, sizeof(double) * kc, st));
     }
     { ProfScope ps_(&p->prof, PC_BICG, 24.0 * p->n, st); RK_CUDA(launch_copy(p->n, v.r, v.rt, st)); RK_CUDA(launch_fill(p->n, 0.0, v.xt, st)); }
@@ -953,12 +1098,12 @@ int solve_bicg(rk_problem* p, const double* b, double* x, const rk_solve_params&
       for (int it = 0; it < NB; ++it) {
         { ProfScope ps_(&p->prof, PC_BICG, 32.0 * p->n, st); RK_CUDA(launch_bicg_p(v, p->bs, p->n, st)); }
         RK_TRY(opapply_launch(p, opk, v.p, false, v.v, false, &p->bs->stop, st, false, pc));
-        RK_TRY(dfdots_launch(p, p->Cblk(kc), kc, v.v, false, eta1, &p->bs->stop, st, v.rt));
+        RK_TRY(bdots_launch(p, p->Cblk(kc), kc, v.v, false, eta1, &p->bs->stop, st, v.rt));
         { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_bicg_alpha(p->bs, eta1, kc, st)); }
-        { ProfScope ps_(&p->prof, PC_BICG, 8.0 * (kc + (kc ? 5 : 3)) * (double)p->n, st); RK_CUDA(launch_bicg_s(v, p->bs, p->n, kc, p->Cblk(kc), p->ld, eta1, xi, p->part, p->counter, st)); }
+        { ProfScope ps_(&p->prof, PC_BICG, 8.0 * (kc + (kc ? 5 : 3)) * (double)p->n, st); RK_CUDA(launch_bicg_s(v, p->bs, p->n, kc, p->Cblk(kc), p->bdf, p->ld, eta1, xi, p->part, p->counter, st)); }
         RK_TRY(opapply_launch(p, opk, v.s, false, v.t, false, &p->bs->stop, st, false, pc));
-        if (kc) RK_TRY(dfdots_launch(p, p->Cblk(kc), kc, v.t, false, eta2, &p->bs->stop, st));
-        { ProfScope ps_(&p->prof, PC_BICG, 8.0 * (kc + (kc ? 3 : 2)) * (double)p->n, st); RK_CUDA(launch_bicg_t(v, p->bs, p->n, kc, p->Cblk(kc), p->ld, eta2, p->part, p->counter, st)); }
+        if (kc) RK_TRY(bdots_launch(p, p->Cblk(kc), kc, v.t, false, eta2, &p->bs->stop, st));
+        { ProfScope ps_(&p->prof, PC_BICG, 8.0 * (kc + (kc ? 3 : 2)) * (double)p->n, st); RK_CUDA(launch_bicg_t(v, p->bs, p->n, kc, p->Cblk(kc), p->bdf, p->ld, eta2, p->part, p->counter, st)); }
         { ProfScope ps_(&p->prof, PC_BICG, 56.0 * p->n, st); RK_CUDA(launch_bicg_r(v, p->bs, p->n, kc, eta1, eta2, xi, p->part, p->counter, st)); }
       }
       RK_CUDA(cudaMemcpyAsync(p->bs_h, p->bs, sizeof(BicgScalars), cudaMemcpyDeviceToHost, st));
@@ -982,7 +1127,7 @@ int solve_bicg(rk_problem* p, const double* b, double* x, const rk_solve_params&
       }
       if (kc) {
         { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_bicg_foldcoef(xi, kc, coefv, st)); }
-        RK_TRY(dfgemm_launch(p, p->Ublk(kc), kc, nullptr, 0, nullptr, coefv, 1, x, false, 1, st));
+        RK_TRY(bgemm_launch(p, p->Ublk(kc), kc, nullptr, 0, nullptr, coefv, 1, x, false, 1, st));
       }
       words += kc + 4;
     }
@@ -1252,9 +1397,29 @@ int rk_row_gemm(rk_context* ctx, int64_t n, int32_t na, const double* A, int64_t
                 int64_t ldb, const double* s, const double* P, int32_t nc, double* out, int64_t ldo, int32_t engine,
                 void* stream) {
   if (!ctx || n <= 0 || na < 0 || nb < 0 || na + nb < 1 || nc < 1 || !P || !out || ldo < n ||
-      (na > 0 && (!A || lda < n)) || (nb > 0 && (!B || ldb < n)) || (engine != 0 && engine != 1))
+      (na > 0 && (!A || lda < n)) || (nb > 0 && (!B || ldb < n)) || engine < 0 || engine > 2)
     return fail(RK_E_INVALID, "bad argument to rk_row_gemm");
   cudaStream_t st = (cudaStream_t)stream;
+  if (engine == 2) {
+    // the FP64 product of the RK_FP64 / RK_MIXED basis, on the operands as given
+    F64GemmArgs g{};
+    g.n = n;
+    g.na = na;
+    g.nb = nb;
+    g.nc = nc;
+    g.A = A;
+    g.lda = lda;
+    g.Bm = B;
+    g.ldb = ldb;
+    g.bscale = s;
+    g.P = P;
+    g.out = out;
+    g.ldo = ldo;
+    g.accum = 0;
+    RK_CUDA(launch_gemm_rows_f64(g, st));
+    RK_CUDA(cudaStreamSynchronize(st));
+    return RK_OK;
+  }
   DFGemmArgs a{};
   a.n = n;
   a.na = na;
@@ -1303,6 +1468,73 @@ int rk_row_gemm(rk_context* ctx, int64_t n, int32_t na, const double* A, int64_t
   return rc;
 }
 
+int rk_arnoldi_dots(rk_context* ctx, int64_t n, int32_t nq, const double* Q, int64_t ld, const double* pv,
+                    const double* w, double* out, int32_t precision, void* stream) {
+  if (!ctx || n <= 0 || nq < 0 || nq > 128 || (nq > 0 && (!Q || ld < n)) || !pv || !w || !out ||
+      (precision != RK_FP64 && precision != RK_DF))
+    return fail(RK_E_INVALID, "bad argument to rk_arnoldi_dots");
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool df = precision == RK_DF;
+  const int ncols = 2 * nq + 3;
+  const size_t nparts = (size_t)(df ? dots2_blocks(n) : dots2_f64_rows(n)) * ncols;
+  const int ncnt = 64;
+  const int64_t ldc = round_up(n, 32);  // column starts 256-byte aligned, as in the solver's basis
+  double* part = (double*)dev_alloc(ctx, nparts * sizeof(double));
+  unsigned* cnt = (unsigned*)dev_alloc(ctx, ncnt * sizeof(unsigned));
+  float2* cp = df ? (float2*)dev_alloc(ctx, (size_t)(nq + 2) * ldc * sizeof(float2)) : nullptr;
+  int* err = (int*)dev_alloc(ctx, sizeof(int));
+  int rc = RK_OK;
+  if (!part || !cnt || !err || (df && !cp)) {
+    rc = fail(RK_E_OOM, "rk_arnoldi_dots: workspace allocation failed");
+  } else {
+    cudaError_t e = cudaMemsetAsync(cnt, 0, ncnt * sizeof(unsigned), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (df) {
+      // the operands rounded to double-float, as RK_DF solves store them
+      if (e == cudaSuccess && nq > 0) e = launch_to_df(n, Q, cp, nullptr, 0, nq, ld, ldc, st);
+      if (e == cudaSuccess) e = launch_to_df(n, pv, cp + (int64_t)nq * ldc, nullptr, 0, 1, n, ldc, st);
+      if (e == cudaSuccess) e = launch_to_df(n, w, cp + (int64_t)(nq + 1) * ldc, nullptr, 0, 1, n, ldc, st);
+      DFDots2Args a{};
+      a.n = n;
+      a.nq = nq;
+      a.Q = cp;
+      a.ld = ldc;
+      a.p = cp + (int64_t)nq * ldc;
+      a.w = cp + (int64_t)(nq + 1) * ldc;
+      a.part = part;
+      a.counter = cnt;
+      a.out = out;
+      a.err = err;
+      if (e == cudaSuccess) e = launch_dfdots2(a, st);
+    } else {
+      F64Dots2Args a{};
+      a.n = n;
+      a.nq = nq;
+      a.Q = Q;
+      a.ld = ld;
+      a.p = pv;
+      a.w = w;
+      a.part = part;
+      a.counter = cnt;
+      a.out = out;
+      if (e == cudaSuccess) e = launch_dots2_f64(a, st);
+    }
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess)
+      rc = fail(RK_E_CUDA, std::string("rk_arnoldi_dots: ") + cudaGetErrorString(e));
+    else if (herr != 0)
+      rc = fail(RK_E_DEVICE_TIMEOUT, "rk_arnoldi_dots: a bounded device wait gave up");
+  }
+  cudaStreamSynchronize(st);
+  dev_free(ctx, part);
+  dev_free(ctx, cnt);
+  dev_free(ctx, cp);
+  dev_free(ctx, err);
+  return rc;
+}
+
 int rk_set_recycle(rk_problem* p, const double* U, const double* C, int32_t k, void* stream) {
   if (!p) return fail(RK_E_INVALID, "NULL problem");
   cudaStream_t st = (cudaStream_t)stream;
@@ -1316,36 +1548,17 @@ int rk_set_recycle(rk_problem* p, const double* U, const double* C, int32_t k, v
   p->kdim = 0;  // replaced below; on any error the problem is left without a recycle space
   float2* Ud = p->Ublk(k);
   float2* Cd = p->Cblk(k);
-  // the caller's FP64 N x k (leading dimension N) into the double-float store
-  RK_CUDA(launch_to_df(p->n, U, Ud, nullptr, 0, k, p->n, p->ld, st));
+  // the caller's FP64 N x k (leading dimension N) into the store (FP64, or
+  // double-float after RK_DF solves)
+  RK_TRY(to_basis(p, U, Ud, nullptr, 0, k, p->n, p->ld, st));
   double* G = p->eta;                     // k x k
-  double* Rinv = p->eta + (size_t)k * k;  // k x k
-  double* Rw = p->sb.hrws;                // k x k scratch
-  auto gram_cc = [&](float2* X) -> int {
-    DFGramArgs g{};
-    g.n = p->n;
-    g.na = k;
-    g.nb = 0;
-    g.nu = k;
-    g.A = X;
-    g.lda = p->ld;
-    g.Bm = nullptr;
-    g.ldb = p->ld;
-    g.d = nullptr;
-    g.U = X;
-    g.ldu = p->ld;
-    g.part = p->part;
-    g.counter = p->counter;
-    g.out = G;
-    RK_CUDA(launch_dfgram(g, st));
-    return RK_OK;
-  };
+  auto gram_cc = [&](float2* X) -> int { return bgram_launch(p, X, k, nullptr, 0, nullptr, X, k, G, st); };
   if (!C) {
     // forming C from U: C~ = A U; thin QR by CholQR2 (C~ = C R), U <- U R^{-1}
     RK_TRY(derive_c_from_u(p, k, st));
     p->kside = 0;
   } else {
-    RK_CUDA(launch_to_df(p->n, C, Cd, nullptr, 0, k, p->n, p->ld, st));
+    RK_TRY(to_basis(p, C, Cd, nullptr, 0, k, p->n, p->ld, st));
     // invariants: ||C^T C - I||_F and ||A U - C||_F
     RK_TRY(gram_cc(Cd));
     std::vector<double> hg((size_t)k * k);
@@ -1364,12 +1577,15 @@ int rk_set_recycle(rk_problem* p, const double* U, const double* C, int32_t k, v
     RK_CUDA(cudaMemcpyAsync(onev, &one, sizeof(double), cudaMemcpyHostToDevice, st));
     double eau = 0.0, un = 0.0;
     for (int c = 0; c < k; ++c) {
-      RK_CUDA(launch_stencil_df(p->d, p->S, ST_PLAIN, p->coef, nullptr, Ud + (int64_t)c * p->ld, true, tmp, false,
-                                nullptr, st));
+      if (p->bdf)
+        RK_CUDA(launch_stencil_df(p->d, p->S, ST_PLAIN, p->coef, nullptr, Ud + (int64_t)c * p->ld, true, tmp, false,
+                                  nullptr, st));
+      else
+        RK_CUDA(launch_stencil(p->d, p->S, ST_PLAIN, p->coef, nullptr, (const double*)(Ud + (int64_t)c * p->ld),
+                               nullptr, tmp, nullptr, nullptr, nullptr, nullptr, st));
       // tmp <- A u_c - c_c, ||tmp||^2 ; ||u_c||^2
-      RK_TRY(dfupdate_launch(p, Cd + (int64_t)c * p->ld, 1, onev, tmp, false, tmp, false, &p->st->nrm2[2], nullptr,
-                             st));
-      RK_TRY(dfdots_launch(p, nullptr, 0, Ud + (int64_t)c * p->ld, true, &p->st->nrm2[3], nullptr, st, nullptr, 1));
+      RK_TRY(bupdate_launch(p, Cd + (int64_t)c * p->ld, 1, onev, tmp, tmp, &p->st->nrm2[2], nullptr, st));
+      RK_TRY(bdots_launch(p, nullptr, 0, Ud + (int64_t)c * p->ld, true, &p->st->nrm2[3], nullptr, st, nullptr, 1));
       RK_TRY(sync_state(p, st));
       eau += p->st_h->nrm2[2];
       un += p->st_h->nrm2[3];
@@ -1392,8 +1608,8 @@ int rk_get_recycle(const rk_problem* p, double* U, double* C, int32_t* k, void* 
   cudaStream_t st = (cudaStream_t)stream;
   const int kd = p->kdim;
   if (kd > 0) {
-    if (U) RK_CUDA(launch_from_df(p->n, p->Ublk(kd), U, kd, p->ld, p->n, st));
-    if (C) RK_CUDA(launch_from_df(p->n, p->Cblk(kd), C, kd, p->ld, p->n, st));
+    if (U) RK_TRY(from_basis(p, p->Ublk(kd), U, kd, p->ld, p->n, st));
+    if (C) RK_TRY(from_basis(p, p->Cblk(kd), C, kd, p->ld, p->n, st));
     RK_CUDA(cudaStreamSynchronize(st));
   }
   *k = kd;
@@ -1424,6 +1640,8 @@ int rk_solve(rk_problem* p, const double* b, double* x, const rk_solve_params* p
       return fail(RK_E_INVALID, "the sub-domain preconditioner is applied from the left in GMRES and rGCROT");
     RK_TRY(ensure_subdomain(p));
   }
+  // the stored recycle space in the format of this solve's precision
+  RK_TRY(ensure_basis(p, prm.precision == RK_DF, st));
   int mode = prm.mode;
   const bool hybrid = mode == RK_HYBRID;
   if (hybrid) {
@@ -1495,8 +1713,9 @@ int rk_profile_read(rk_problem* p, rk_prof_entry* out, int32_t cap, int32_t* cou
 }
 
 int rk_harmonic_ritz(rk_context* ctx, int32_t n, const double* G, const double* F, int32_t k, double* QC,
-                     double* PU, int32_t* knew, void* stream) {
-  if (!ctx || !G || !F || !QC || !PU || !knew || n <= 0 || k <= 0 || k > n || n > 511)
+                     double* PU, int32_t* knew, int32_t precision, void* stream) {
+  if (!ctx || !G || !F || !QC || !PU || !knew || n <= 0 || k <= 0 || k > n || n > 511 ||
+      (precision != RK_FP64 && precision != RK_DF))
     return fail(RK_E_INVALID, "bad argument to rk_harmonic_ritz");
   cudaStream_t st = (cudaStream_t)stream;
   const size_t ws = harmonic_ritz_ws_doubles(n) + 8;
@@ -1507,7 +1726,7 @@ int rk_harmonic_ritz(rk_context* ctx, int32_t n, const double* G, const double* 
     if (!ctx->part) return fail(RK_E_OOM, "workspace allocation failed");
   }
   int* dk = (int*)(ctx->counter + 32);
-  RK_CUDA(launch_harmonic_ritz_small(n, G, F, k, QC, PU, dk, ctx->part, st));
+  RK_CUDA(launch_harmonic_ritz_small(n, G, F, k, QC, PU, dk, ctx->part, precision == RK_FP64, st));
   int h = 0;
   RK_CUDA(cudaMemcpyAsync(&h, dk, sizeof(int), cudaMemcpyDeviceToHost, st));
   RK_CUDA(cudaStreamSynchronize(st));
@@ -1677,8 +1896,9 @@ int rk_solve_batch(rk_problem* const* problems, const double* const* b, double* 
 
 
 // Opaque recycle-space blob: 4 int64 (magic, n, k, side of the pair: 0
-// A U = C, 1 M^{-1} A U = C), then U and C as stored (k double-float
-// columns of n each).
+// A U = C, 1 M^{-1} A U = C with point Jacobi, 2 with the sub-domain
+// preconditioner; plus 256 when the columns are double-float), then U and C
+// as stored (k columns of n 8-byte elements each).
 static const int64_t kRecycleMagic = 0x524b524543594331LL;  // "RKRECYC1"
 
 int rk_recycle_bytes(const rk_problem* p, int64_t* bytes) {
@@ -1693,7 +1913,7 @@ int rk_export_recycle(const rk_problem* p, void* buf, int64_t cap, void* stream)
   RK_TRY(rk_recycle_bytes(p, &need));
   if (cap < need) return fail(RK_E_INVALID, "export buffer too small");
   cudaStream_t st = (cudaStream_t)stream;
-  const int64_t hdr[4] = {kRecycleMagic, p->n, p->kdim, p->kside};
+  const int64_t hdr[4] = {kRecycleMagic, p->n, p->kdim, p->kside + (p->bdf ? 256 : 0)};
   char* b = (char*)buf;
   RK_CUDA(cudaMemcpyAsync(b, hdr, sizeof(hdr), cudaMemcpyHostToDevice, st));
   const int k = p->kdim;
@@ -1718,7 +1938,9 @@ int rk_import_recycle(rk_problem* p, const void* buf, int64_t bytes, void* strea
   if (hdr[1] != p->n) return fail(RK_E_INVALID, "recycle blob is for another problem size");
   const int64_t k = hdr[2];
   if (k < 0 || k > 256) return fail(RK_E_INVALID, "bad recycle dimension in blob");
-  if (hdr[3] < 0 || hdr[3] > 2) return fail(RK_E_INVALID, "bad recycle side in blob");
+  const int64_t side = hdr[3] & 255;
+  const bool blob_df = (hdr[3] & 256) != 0;
+  if (hdr[3] < 0 || hdr[3] > 511 || side > 2) return fail(RK_E_INVALID, "bad recycle side in blob");
   const size_t col = sizeof(float2) * (size_t)p->n;
   if (bytes < 32 + 2 * (int64_t)col * k) return fail(RK_E_INVALID, "recycle blob too short");
   p->kdim = 0;
@@ -1731,7 +1953,8 @@ int rk_import_recycle(rk_problem* p, const void* buf, int64_t bytes, void* strea
                             cudaMemcpyDeviceToDevice, st));
   RK_CUDA(cudaStreamSynchronize(st));
   p->kdim = (int)k;
-  p->kside = (int)hdr[3];
+  p->kside = (int)side;
+  p->bdf = blob_df;
   return RK_OK;
 }
 

@@ -79,10 +79,26 @@ class Context:
         N.check(self.lib.rk_dots(self._h, n, nq, _dptr(Q), ld, _dptr(w), _dptr(out), _stream_ptr(stream)))
         return out[:nq]
 
+    def arnoldi_dots(self, Q, p, w, precision="fp64", stream=None):
+        """[Q^T p, Q^T w, p^T p, p^T w, w^T w] for Q (nq, N) row-contiguous and
+        p, w (N,), by the fused inner-product kernel of one Arnoldi step that
+        solves of ``precision`` ("fp64" or "df") run (rk_arnoldi_dots)."""
+        p = _f64_cuda(p)
+        w = _f64_cuda(w)
+        n = p.numel()
+        Q = _f64_cuda(Q) if Q is not None else None
+        nq = Q.shape[0] if Q is not None else 0
+        out = torch.empty(2 * nq + 3, dtype=torch.float64, device="cuda")
+        N.check(self.lib.rk_arnoldi_dots(self._h, n, nq, _dptr(Q) if nq else None, Q.stride(0) if nq else n,
+                                         _dptr(p), _dptr(w), _dptr(out),
+                                         {"fp64": N.RK_FP64, "df": N.RK_DF}[precision], _stream_ptr(stream)))
+        return out
+
     def row_gemm(self, A, B, s, P, engine=1, stream=None):
         """[A, diag(s) B] P for A (na, N), B (nb, N) row-contiguous (either may
         be None), s (N,) or None, P (na + nb, nc): the recycle-update product
-        through rk_row_gemm (engine 1: tensor cores, 0: FP32 pipe). Returns
+        through rk_row_gemm (engine 1: tensor cores, 0: FP32 pipe, both on
+        double-float copies of A and B; 2: FP64 on the operands as given). Returns
         (nc, N)."""
         n = (A if A is not None else B).shape[1]
         A = _f64_cuda(A) if A is not None else None
@@ -99,9 +115,10 @@ class Context:
                                      _dptr(Pc), nc, _dptr(out), n, engine, _stream_ptr(stream)))
         return out
 
-    def harmonic_ritz(self, G, F, k, stream=None):
+    def harmonic_ritz(self, G, F, k, stream=None, precision="fp64"):
         """Device harmonic Ritz selection of the recycle update (Algorithm 3): returns (QC, PU) as
-        ((n+1) x knew, n x knew) tensors (see include/rk.h)."""
+        ((n+1) x knew, n x knew) tensors (see include/rk.h). precision "fp64": the
+        Schur iteration in FP64; "df": in double-float."""
         G = _f64_cuda(G)
         F = _f64_cuda(F)
         n = G.shape[1]
@@ -112,7 +129,8 @@ class Context:
         PU = torch.zeros((k, n), dtype=torch.float64, device="cuda")
         kn = ctypes.c_int32()
         N.check(self.lib.rk_harmonic_ritz(self._h, n, _dptr(Gc), _dptr(Fc), k, _dptr(QC), _dptr(PU),
-                                          ctypes.byref(kn), _stream_ptr(stream)))
+                                          ctypes.byref(kn), {"fp64": N.RK_FP64, "df": N.RK_DF}[precision],
+                                          _stream_ptr(stream)))
         return QC[: kn.value].t(), PU[: kn.value].t()
 
     def close(self):

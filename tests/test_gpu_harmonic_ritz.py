@@ -67,13 +67,16 @@ def gap(A, B):
     return float(np.linalg.norm(qb - qa @ (qa.T @ qb), 2))
 
 
+@pytest.mark.parametrize("precision", ["fp64", "df"])
 @pytest.mark.parametrize("kc,jj,k,seed", [(0, 10, 4, 1), (0, 40, 20, 2), (8, 12, 6, 3), (20, 40, 20, 4),
                                          (10, 30, 10, 5), (20, 40, 20, 6), (5, 3, 8, 7)])
-def test_harmonic_ritz_matches_scipy(ctx, kc, jj, k, seed):
+def test_harmonic_ritz_matches_scipy(ctx, kc, jj, k, seed, precision):
+    """The Schur iteration in FP64 (RK_FP64 / RK_MIXED solves) and in
+    double-float (RK_DF solves) select SciPy's subspace."""
     G, F = pencil(kc, jj, seed)
     n = kc + jj
     k = min(k, n)
-    QC, PU = ctx.harmonic_ritz(torch.from_numpy(G), torch.from_numpy(F), k)
+    QC, PU = ctx.harmonic_ritz(torch.from_numpy(G), torch.from_numpy(F), k, precision=precision)
     QC, PU = QC.cpu().numpy(), PU.cpu().numpy()
     P, mags = reference_basis(G, F, k)
     assert PU.shape[1] == P.shape[1]
@@ -93,7 +96,8 @@ def test_harmonic_ritz_matches_scipy(ctx, kc, jj, k, seed):
     assert gap(PU, P) <= 100.0 * sens + 1e-10, (gap(PU, P), sens)
 
 
-def test_pencil_with_near_zero_eigenvalues(ctx):
+@pytest.mark.parametrize("precision", ["fp64", "df"])
+def test_pencil_with_near_zero_eigenvalues(ctx, precision):
     """The second-cycle pencil of rGCROT(20,10) on a small skewed porous
     problem: M'' has eigenvalues near zero, whose neighbouring diagonal
     entries are tiny, so a purely relative deflation test never fires at the
@@ -133,7 +137,7 @@ def test_pencil_with_near_zero_eigenvalues(ctx):
     finally:
         K.harmonic_ritz_update = orig
     G, F = pens[1]
-    QC, PU = ctx.harmonic_ritz(torch.from_numpy(G), torch.from_numpy(F), 10)
+    QC, PU = ctx.harmonic_ritz(torch.from_numpy(G), torch.from_numpy(F), 10, precision=precision)
     PU = PU.cpu().numpy()
     P, _ = reference_basis(G, F, 10)
     assert PU.shape[1] == P.shape[1] == 9  # the third complex pair is split by the cut and dropped

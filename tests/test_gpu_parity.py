@@ -136,7 +136,30 @@ def test_block_dots(ctx, n, nq):
     assert np.all(np.abs(got - ref) <= bound)
 
 
-@pytest.mark.parametrize("engine", [1, 0])
+@pytest.mark.parametrize("precision", ["fp64", "df"])
+@pytest.mark.parametrize("n,nq", [(1, 1), (1000, 3), (4099, 17), (100003, 40), (262144, 61), (2 ** 21, 61),
+                                  (3001, 0), (777, 128)])
+def test_arnoldi_dots_against_exact_sums(ctx, n, nq, precision):
+    """The hot path's fused Arnoldi inner products [Q^T p, Q^T w, p^T p,
+    p^T w, w^T w] (the kernel the solvers run at every step: FP64 for the
+    fp64 and mixed precisions, double-float for df) against sums of the
+    exactly rounded products (math.fsum), element by element, at the
+    normwise bar of single dot products: |d - d_ref| <= 1e-13 ||a|| ||b||.
+    Sizes from one row to 2^21 rows (the row ranges of 152 blocks), 0 to
+    128 columns, a ragged tail, and columns scaled over six decades."""
+    rng = np.random.default_rng(n + 7 * nq)
+    Q = rng.standard_normal((nq, n)) * np.exp2(rng.integers(-10, 10, size=(nq, 1)))
+    pv = rng.standard_normal(n)
+    w = rng.standard_normal(n) * 1e3
+    got = ctx.arnoldi_dots(t(Q) if nq else None, t(pv), t(w), precision=precision).cpu().numpy()
+    pairs = [(Q[q], pv) for q in range(nq)] + [(Q[q], w) for q in range(nq)] + [(pv, pv), (pv, w), (w, w)]
+    ref = np.array([math.fsum(a * b) for a, b in pairs])
+    bound = np.array([1e-13 * np.linalg.norm(a) * np.linalg.norm(b) for a, b in pairs])
+    assert got.shape == ref.shape
+    assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) / bound))
+
+
+@pytest.mark.parametrize("engine", [1, 0, 2])
 @pytest.mark.parametrize("n,na,nb,nc,scaled", [
     (1, 3, 2, 2, False), (127, 20, 41, 20, True), (129, 61, 0, 20, False), (1000, 20, 40, 20, True),
     (5003, 0, 64, 32, True), (4099, 32, 32, 7, False), (300, 1, 0, 2, False), (70000, 20, 41, 20, True),
@@ -149,6 +172,9 @@ def test_row_gemm_recycle_update(ctx, engine, n, na, nb, nc, scaled):
     double-float epilogue, and the fixed-point digits, which truncate each
     element below 2^-56 of its row's (X) or column's (P) largest:
     |out - X P| <= 2^-45 (|X| |P|) + 2^-52 K max_row|X| max_col|P|.
+    FP64 engine (the fp64 and mixed basis): K fused multiply-adds per
+    output and one rounded product s_i b_iq: |out - X P| <= (K + 2) 2^-53
+    (|X| |P|).
     Scales within a row and within a column of P span 2^8. 70000 rows
     span hundreds of tiles per block (bulk-copied tiles prefetched one
     ahead, then a ragged last tile); 70001 rows give operands the bulk copy
@@ -172,6 +198,8 @@ def test_row_gemm_recycle_update(ctx, engine, n, na, nb, nc, scaled):
     if engine == 1:
         K = na + nb
         bound = 2.0 ** -45 * comp + 2.0 ** -52 * K * np.abs(P).max(axis=0)[:, None] * np.abs(X).max(axis=0)[None, :]
+    elif engine == 2:
+        bound = (na + nb + 2) * 2.0 ** -53 * comp
     else:
         bound = 2.0 ** -44 * comp
     err = np.abs((got.astype(np.longdouble) - ref).astype(np.float64))
@@ -275,8 +303,9 @@ def test_rgcrot_sequence_parity(ctx, cfg_id, size, m, k, steps):
         assert np.linalg.norm(C.T @ C - np.eye(C.shape[1])) <= 1e-11
 
 
+@pytest.mark.parametrize("precision", ["fp64", "df"])
 @pytest.mark.parametrize("cfg_id,size,m,k", [(1, 10, 12, 6), (2, 10, 20, 8), (1, 8, 30, 10)])
-def test_harmonic_ritz_cycles_match_oracle(ctx, cfg_id, size, m, k):
+def test_harmonic_ritz_cycles_match_oracle(ctx, cfg_id, size, m, k, precision):
     """Recycle space after one and after two cycles (updated by harmonic Ritz
     vectors, computed on the device) spans the oracle's (SciPy eig of the
     pencil) to within rounding-level principal angles."""
@@ -286,7 +315,7 @@ def test_harmonic_ritz_cycles_match_oracle(ctx, cfg_id, size, m, k):
     b = cfg.rhs(0)
     U = C = None
     for cyc in range(2):
-        prob.solve(t(b), tol=1e-14, m=m, k=k, mode="rGCROT", max_matvec=m)
+        prob.solve(t(b), tol=1e-14, m=m, k=k, mode="rGCROT", max_matvec=m, precision=precision)
         _, U, C, _ = oracle.rgcrot(op, b, tol=1e-14, m=m, k=k, U=U, C=C, max_matvec=m)
         Ug, Cg = prob.get_recycle()
         Cg = Cg.cpu().numpy().T
@@ -300,11 +329,20 @@ def test_recycle_set_get_roundtrip_and_forming_c(ctx):
     op = oracle.Stencil(cfg.grid, cfg.coef)
     _, U, C, _ = oracle.rgcrot(op, cfg.rhs(0), tol=1e-10, m=10, k=6)
     kk = U.shape[1]  # 6, or 5 when the cut falls inside a conjugate pair
-    # C given: stored as is (in double-float, so to ~48 significant bits)
+    # C given: stored as is (FP64 store: bit for bit)
     prob.set_recycle(t(U.T), t(C.T))
+    U2, C2 = prob.get_recycle()
+    assert np.array_equal(U2.cpu().numpy(), U.T) and np.array_equal(C2.cpu().numpy(), C.T)
+    # after a df solve the store is double-float (to ~48 significant bits)
+    prob.solve(t(cfg.rhs(1)), tol=1e-8, m=10, k=6, mode="rGCROT", update_recycle=False, precision="df")
     U2, C2 = prob.get_recycle()
     assert np.all(np.abs(U2.cpu().numpy() - U.T) <= 2.0 ** -46 * np.abs(U.T))
     assert np.all(np.abs(C2.cpu().numpy() - C.T) <= 2.0 ** -46 * np.abs(C.T))
+    # and back to FP64 by the next fp64 solve (the conversion rounds once)
+    prob.solve(t(cfg.rhs(1)), tol=1e-8, m=10, k=6, mode="rGCROT", update_recycle=False)
+    U3, C3 = prob.get_recycle()
+    assert np.array_equal(U3.cpu().numpy(), U2.cpu().numpy()) and np.array_equal(C3.cpu().numpy(), C2.cpu().numpy())
+    prob.set_recycle(t(U.T), t(C.T))
     # C omitted: the library forms C = orth(A U) and rescales U so that A U = C
     Uraw = U @ np.diag([1.0, 2.0, -3.0, 0.5, 4.0, 1.5][:kk])
     prob.set_recycle(t(Uraw.T))
