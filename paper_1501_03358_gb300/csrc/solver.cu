@@ -250,42 +250,21 @@ void free_small(rk_problem* p) {
 }
 
 // (Re)allocate the recycle/Arnoldi storage for capacity (kmax, mcap), keeping
-// the stored recycle space.
+// the stored recycle space. Transactional: every new buffer is allocated
+// before the old ones are touched, so when the allocator returns NULL the
+// problem keeps its previous buffers, capacity and recycle space unchanged
+// (RK_E_OOM) and stays usable.
 int ensure_capacity(rk_problem* p, int kneed, int mneed, cudaStream_t st) {
-  if (kneed <= p->kmax && mneed <= p->mcap && p->QB) return RK_OK;
-  p->drop_graphs();
+  if (kneed <= p->kmax && mneed <= p->mcap && p->QB && (p->kmax == 0 || p->Ub) && p->rvec && p->small && p->eta &&
+      p->part)
+    return RK_OK;
   const int kmax = std::max(kneed, p->kmax);
   const int mcap = std::max(mneed, p->mcap);
   if (kmax > 256) return fail(RK_E_INVALID, "recycle dimension above 256 is not supported");
   if (kmax + mcap + 1 > 512) return fail(RK_E_INVALID, "k + m above 511 is not supported");
-  float2* QB = nullptr;
-  float2* Ub = nullptr;
-  RK_TRY(alloc_into(p->ctx, &QB, (size_t)(kmax + mcap + 1) * p->ld));
-  if (kmax > 0) {
-    int r = alloc_into(p->ctx, &Ub, (size_t)kmax * p->ld);
-    if (r != RK_OK) {
-      dev_free(p->ctx, QB);
-      return r;
-    }
-  }
-  if (p->kdim > 0) {
-    RK_CUDA(cudaMemcpyAsync(QB + (int64_t)(kmax - p->kdim) * p->ld, p->Cblk(p->kdim),
-                            sizeof(float2) * p->ld * p->kdim, cudaMemcpyDeviceToDevice, st));
-    RK_CUDA(cudaMemcpyAsync(Ub + (int64_t)(kmax - p->kdim) * p->ld, p->Ublk(p->kdim),
-                            sizeof(float2) * p->ld * p->kdim, cudaMemcpyDeviceToDevice, st));
-    RK_CUDA(cudaStreamSynchronize(st));
-  }
-  dev_free(p->ctx, p->QB);
-  dev_free(p->ctx, p->Ub);
-  p->QB = QB;
-  p->Ub = Ub;
-  p->kmax = kmax;
-  p->mcap = mcap;
-  if (!p->rvec) RK_TRY(alloc_into(p->ctx, &p->rvec, (size_t)p->ld));
-  // small buffers
-  free_small(p);
+  // sizes of the small buffers
+  SmallBuffers b{};
   const int m = mcap, nq = kmax + mcap + 2;
-  SmallBuffers& b = p->sb;
   b.m = m;
   b.kmax = std::max(kmax, 1);
   b.nqmax = nq;
@@ -303,30 +282,68 @@ int ensure_capacity(rk_problem* p, int kneed, int mneed, cudaStream_t st) {
                ogram = take((size_t)(kmax + m + 1) * b.kmax), oQC = take((size_t)(kmax + m + 1) * b.kmax),
                oPU = take((size_t)(kmax + m) * b.kmax), ows = take(b.hrws_doubles),
                otc = take((dfgemm_tc_ws_bytes() + 7) / 8);
-  RK_TRY(alloc_into(p->ctx, &p->small, total));
+  const size_t eta_n = (size_t)4 * (kmax + 4) + (size_t)kmax * kmax * 2 + 16;
+  const size_t part_n = partials_needed(p, kmax, mcap);
+  // allocate everything new first
+  float2* QB = nullptr;
+  float2* Ub = nullptr;
+  double *rvec = nullptr, *small = nullptr, *eta = nullptr, *part = nullptr;
+  int r = alloc_into(p->ctx, &QB, (size_t)(kmax + mcap + 1) * p->ld);
+  if (r == RK_OK && kmax > 0) r = alloc_into(p->ctx, &Ub, (size_t)kmax * p->ld);
+  if (r == RK_OK && !p->rvec) r = alloc_into(p->ctx, &rvec, (size_t)p->ld);
+  if (r == RK_OK) r = alloc_into(p->ctx, &small, total);
+  if (r == RK_OK) r = alloc_into(p->ctx, &eta, eta_n);
+  if (r == RK_OK) r = alloc_into(p->ctx, &part, part_n);
+  if (r != RK_OK) {
+    dev_free(p->ctx, QB);
+    dev_free(p->ctx, Ub);
+    dev_free(p->ctx, rvec);
+    dev_free(p->ctx, small);
+    dev_free(p->ctx, eta);
+    dev_free(p->ctx, part);
+    return r;
+  }
+  p->drop_graphs();
+  if (p->kdim > 0) {
+    RK_CUDA(cudaMemcpyAsync(QB + (int64_t)(kmax - p->kdim) * p->ld, p->Cblk(p->kdim),
+                            sizeof(float2) * p->ld * p->kdim, cudaMemcpyDeviceToDevice, st));
+    RK_CUDA(cudaMemcpyAsync(Ub + (int64_t)(kmax - p->kdim) * p->ld, p->Ublk(p->kdim),
+                            sizeof(float2) * p->ld * p->kdim, cudaMemcpyDeviceToDevice, st));
+  }
+  RK_CUDA(cudaStreamSynchronize(st));
+  dev_free(p->ctx, p->QB);
+  dev_free(p->ctx, p->Ub);
+  p->QB = QB;
+  p->Ub = Ub;
+  p->kmax = kmax;
+  p->mcap = mcap;
+  if (rvec) p->rvec = rvec;
+  free_small(p);
+  p->small = small;
   p->small_n = total;
-  b.H = p->small + oH;
-  b.R = p->small + oR;
-  b.B = p->small + oB;
-  b.g = p->small + og;
-  b.cs = p->small + ocs;
-  b.sn = p->small + osn;
-  b.sv = p->small + osv;
-  b.hacc = p->small + ohacc;
-  b.dots = p->small + odots;
-  b.coef = p->small + ocoef;
-  b.y = p->small + oy;
-  b.xcoef = p->small + ox;
-  b.gram = p->small + ogram;
-  b.QC = p->small + oQC;
-  b.PU = p->small + oPU;
-  b.hrws = p->small + ows;
-  b.tcws = p->small + otc;
+  b.H = small + oH;
+  b.R = small + oR;
+  b.B = small + oB;
+  b.g = small + og;
+  b.cs = small + ocs;
+  b.sn = small + osn;
+  b.sv = small + osv;
+  b.hacc = small + ohacc;
+  b.dots = small + odots;
+  b.coef = small + ocoef;
+  b.y = small + oy;
+  b.xcoef = small + ox;
+  b.gram = small + ogram;
+  b.QC = small + oQC;
+  b.PU = small + oPU;
+  b.hrws = small + ows;
+  b.tcws = small + otc;
+  p->sb = b;
   RK_CUDA(cudaMemsetAsync(p->small, 0, total * sizeof(double), st));
-  p->eta_n = (size_t)4 * (kmax + 4) + (size_t)kmax * kmax * 2 + 16;
-  RK_TRY(alloc_into(p->ctx, &p->eta, p->eta_n));
-  p->part_n = partials_needed(p, kmax, mcap);
-  RK_TRY(alloc_into(p->ctx, &p->part, p->part_n));
+  p->eta = eta;
+  p->eta_n = eta_n;
+  p->part = part;
+  p->part_n = part_n;
   return RK_OK;
 }
 
@@ -653,10 +670,21 @@ int stencil_df_launch(rk_problem* p, int mode, const void* v, bool v_df, void* y
 // FP32 copy of the operator for the mixed-precision inner products (A11):
 // coefficients and 1/a_pp rounded to nearest once.
 int ensure_mixed(rk_problem* p, cudaStream_t st) {
-  if (p->coef32) return RK_OK;
+  if (p->coef32 && p->dinv32) return RK_OK;
+  float* c32 = nullptr;
+  float* d32 = nullptr;
+  int r = alloc_into(p->ctx, &c32, (size_t)p->S * p->n);
+  if (r == RK_OK) r = alloc_into(p->ctx, &d32, (size_t)p->ld);
+  if (r != RK_OK) {  // nothing installed: the problem is unchanged
+    dev_free(p->ctx, c32);
+    dev_free(p->ctx, d32);
+    return r;
+  }
   p->drop_graphs();
-  RK_TRY(alloc_into(p->ctx, &p->coef32, (size_t)p->S * p->n));
-  RK_TRY(alloc_into(p->ctx, &p->dinv32, (size_t)p->ld));
+  dev_free(p->ctx, p->coef32);
+  dev_free(p->ctx, p->dinv32);
+  p->coef32 = c32;
+  p->dinv32 = d32;
   RK_CUDA(launch_round_f32((int64_t)p->S * p->n, p->coef, p->coef32, st));
   RK_CUDA(launch_round_f32(p->n, p->dinv, p->dinv32, st));
   return RK_OK;
@@ -665,10 +693,21 @@ int ensure_mixed(rk_problem* p, cudaStream_t st) {
 // Double-float copy of the operator for RK_DF: bands and 1/a_pp rounded to
 // double-float once.
 int ensure_dfop(rk_problem* p, cudaStream_t st) {
-  if (p->coefdf) return RK_OK;
+  if (p->coefdf && p->dinvdf) return RK_OK;
+  float2* cdf = nullptr;
+  float2* ddf = nullptr;
+  int r = alloc_into(p->ctx, &cdf, (size_t)p->S * p->n);
+  if (r == RK_OK) r = alloc_into(p->ctx, &ddf, (size_t)p->ld);
+  if (r != RK_OK) {  // nothing installed: the problem is unchanged
+    dev_free(p->ctx, cdf);
+    dev_free(p->ctx, ddf);
+    return r;
+  }
   p->drop_graphs();
-  RK_TRY(alloc_into(p->ctx, &p->coefdf, (size_t)p->S * p->n));
-  RK_TRY(alloc_into(p->ctx, &p->dinvdf, (size_t)p->ld));
+  dev_free(p->ctx, p->coefdf);
+  dev_free(p->ctx, p->dinvdf);
+  p->coefdf = cdf;
+  p->dinvdf = ddf;
   RK_CUDA(launch_round_df((int64_t)p->S * p->n, p->coef, p->coefdf, st));
   RK_CUDA(launch_round_df(p->n, p->dinv, p->dinvdf, st));
   return RK_OK;
