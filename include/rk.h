@@ -316,6 +316,18 @@ int rk_solve_batch(rk_problem* const* problems, const double* const* b, double* 
 int rk_problem_memory(const rk_problem* p, int64_t* device_bytes);
 
 /*
+ * Device bytes the problem will hold during and after a solve with the
+ * given parameters: rk_problem_memory plus every buffer that solve would
+ * make (basis and recycle storage for capacity max(k, stored dimension) and
+ * m, the small buffers, operator copies of RK_MIXED / RK_DF, the
+ * preconditioner's workspace, the rBiCGStab vectors), counting the old and
+ * new basis once each where a growing capacity copies the recycle space
+ * over. A bound for admission under a memory budget, before a problem's
+ * first solve. No counterpart in the paper.
+ */
+int rk_problem_footprint(const rk_problem* p, const rk_solve_params* params, int64_t* device_bytes);
+
+/*
  * Free a problem's basis, recycle and solver workspace, keeping the operator
  * (memory pressure: a serving process evicting an idle problem). The recycle
  * space is dropped: save it first with rk_get_recycle and restore it with
@@ -414,6 +426,19 @@ int rk_problem_stats(const rk_problem* p, int32_t* solves, int32_t* recycle_dim,
  * for a NULL problem. No counterpart in the paper (its runs are one sequence).
  */
 int rk_problem_reset(rk_problem* p);
+
+/*
+ * Test hook for the failure path of the bounded device waits: with
+ * polls > 0, the bulk-copy producer of the double-float Arnoldi inner
+ * products (RK_DF solves) gives up after that many polls of a stage-release
+ * barrier, issues no further copies, lets the consumers stop at the first
+ * stage it did not issue (so no copy into shared memory is in flight when
+ * the block exits) and flags the failure; the solve then returns
+ * RK_E_DEVICE_TIMEOUT and the problem stays usable. polls = 0 restores the
+ * default limit (2^22 polls). Synchronises `stream`. No counterpart in the
+ * paper.
+ */
+int rk_problem_wait_limit(rk_problem* p, int32_t polls, void* stream);
 
 /*
  * Measure this GPU's FP64 fma issue rate (lane operations per second, one

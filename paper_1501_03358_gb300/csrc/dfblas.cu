@@ -251,6 +251,7 @@ __global__ void __launch_bounds__(kD2Threads) k_dfdots2(DFDots2Args a, int64_t r
   __shared__ __align__(8) uint64_t empty[kD2Stages];
   __shared__ float2 red[kWarps][kDFCols];
   __shared__ int lastflag;
+  __shared__ int abort_at;  // first stage the producer did not issue (it gave up waiting)
   const int ncols = 2 * a.nq + 3;
   const int ngroups = (a.nq + kDotGroup - 1) / kDotGroup;
   const bool scal = (int)blockIdx.y >= ngroups;
@@ -271,16 +272,23 @@ __global__ void __launch_bounds__(kD2Threads) k_dfdots2(DFDots2Args a, int64_t r
       mbar_init(&empty[s], kWarps);
     }
     mbar_init_fence();
+    abort_at = 0x7fffffff;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (wid == kWarps) {
-    // producer: refill a stage once every consumer warp has released it
+    // producer: refill a stage once every consumer warp has released it;
+    // if that wait gives up, no copy is issued for stage s or later and the
+    // consumers stop at stage s (every copy they wait for was issued)
     if (lane == 0) {
+      const int lim = a.wait_limit != nullptr ? *a.wait_limit : 0;
+      const int polls = lim > 0 ? lim : kMbarPolls;
       for (int s = 0; s < nst; ++s) {
         const int slot = s % kD2Stages;
-        if (s >= kD2Stages && !mbar_wait_bounded(&empty[slot], (unsigned)((s / kD2Stages - 1) & 1))) {
+        if (s >= kD2Stages && !mbar_wait_polls(&empty[slot], (unsigned)((s / kD2Stages - 1) & 1), polls)) {
           if (a.err) atomicExch(a.err, 2);
+          abort_at = s;
+          __threadfence_block();
           break;
         }
         const int64_t r0 = begin + (int64_t)s * kD2Rows;
@@ -300,8 +308,20 @@ __global__ void __launch_bounds__(kD2Threads) k_dfdots2(DFDots2Args a, int64_t r
   float s0h = 0.f, s0l = 0.f, s1h = 0.f, s1l = 0.f, s2h = 0.f, s2l = 0.f;
   for (int s = 0; s < nst; ++s) {
     const int slot = s % kD2Stages;
-    if (!mbar_wait_bounded(&full[slot], (unsigned)((s / kD2Stages) & 1))) {
-      if (a.err) atomicExch(a.err, 1);
+    // wait for stage s, unless the producer gave up before issuing it
+    bool got = false, stopped = false;
+    for (int it = 0; it < kMbarPolls; ++it) {
+      if (mbar_try_wait(&full[slot], (unsigned)((s / kD2Stages) & 1))) {
+        got = true;
+        break;
+      }
+      if (*(volatile int*)&abort_at <= s) {
+        stopped = true;
+        break;
+      }
+    }
+    if (!got) {
+      if (!stopped && a.err) atomicExch(a.err, 1);
       break;
     }
     const int64_t r0 = begin + (int64_t)s * kD2Rows;

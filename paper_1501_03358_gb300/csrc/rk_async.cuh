@@ -40,6 +40,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
   return false;
 }
 
+// the same with a given number of polls
+__device__ __forceinline__ bool mbar_wait_polls(uint64_t* bar, unsigned parity, int polls) {
+  for (int it = 0; it < polls; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
 // plain arrival (no transaction bytes)
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");

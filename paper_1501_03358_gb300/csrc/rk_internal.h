@@ -187,6 +187,7 @@ struct DFDots2Args {
   double* out;        // 2 nq + 3
   const int* skip_flag;
   int* err;           // set nonzero if a bounded wait gives up
+  const int* wait_limit;  // nullable; *wait_limit > 0: polls of the producer's stage-release waits
 };
 cudaError_t launch_dfdots2(const DFDots2Args& a, cudaStream_t st);
 // one-time kernel attribute setup of the streaming kernels (idempotent)

@@ -24,7 +24,7 @@ struct SolveState {
   int upd_mode;      // Arnoldi update pass: 0 v_j and p_{j+1}, 1 v_j only, 2 none
   int nspmv;         // products A M^{-1} p taken in the current cycle
   int dev_err;       // nonzero: a bounded device wait gave up (kernel id)
-  int pad_;
+  int wait_limit;    // > 0: polls before the Arnoldi inner products' copy producer gives up (test hook)
 };
 
 struct SmallBuffers {

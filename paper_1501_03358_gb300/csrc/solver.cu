@@ -493,6 +493,7 @@ int bdots2_launch(rk_problem* p, const void* Q, int nq, const void* pv, const vo
   a.out = out;
   a.skip_flag = skip;
   a.err = &p->st->dev_err;
+  a.wait_limit = &p->st->wait_limit;
   RK_CUDA(launch_dfdots2(a, st));
   return RK_OK;
 }
@@ -1806,11 +1807,52 @@ int rk_fp64_fma_rate(double* fma_per_s, void* stream) {
   return RK_OK;
 }
 
+int rk_problem_wait_limit(rk_problem* p, int32_t polls, void* stream) {
+  if (!p || polls < 0) return fail(RK_E_INVALID, "bad argument to rk_problem_wait_limit");
+  cudaStream_t st = (cudaStream_t)stream;
+  RK_CUDA(cudaMemcpyAsync(&p->st->wait_limit, &polls, sizeof(int), cudaMemcpyHostToDevice, st));
+  RK_CUDA(cudaStreamSynchronize(st));
+  return RK_OK;
+}
+
 int rk_problem_reset(rk_problem* p) {
   if (!p) return fail(RK_E_INVALID, "NULL problem");
   p->kdim = 0;
   p->kside = 0;
   p->hyb_base = p->solves;
+  return RK_OK;
+}
+
+int rk_problem_footprint(const rk_problem* p, const rk_solve_params* prm, int64_t* device_bytes) {
+  if (!p || !prm || !device_bytes) return fail(RK_E_INVALID, "NULL argument");
+  int64_t now = 0;
+  RK_TRY(rk_problem_memory(p, &now));
+  const size_t ld = (size_t)p->ld, n = (size_t)p->n, S = (size_t)p->S;
+  // buffers a solve with these parameters makes that the problem lacks
+  const bool gcr = prm->mode != RK_RBICGSTAB;
+  const bool bicg = prm->mode == RK_RBICGSTAB || prm->mode == RK_HYBRID;
+  const int kneed = std::max(std::max(prm->k, 0), p->kdim);
+  const int kmax = std::max(kneed, p->kmax);
+  const int mcap = std::max(gcr ? std::max(prm->m, 1) : 1, p->mcap);
+  size_t add = 0;
+  if (kmax > p->kmax || mcap > p->mcap || !p->QB) {
+    // ensure_capacity: the new basis and small buffers replace the old ones
+    // (both are held while the recycle space is copied over)
+    size_t total = 0;
+    auto take = [&](size_t cnt) { total += (size_t)round_up((int64_t)cnt, 32); };
+    const int m = mcap, nq = kmax + mcap + 2, kk = std::max(kmax, 1);
+    take((size_t)(m + 1) * m); take((size_t)(m + 1) * m); take((size_t)kk * m); take(m + 1); take(m); take(m);
+    take(m + 2); take(nq); take(2 * (size_t)nq + 8); take(nq); take(m); take(nq);
+    take((size_t)(kmax + m + 1) * kk); take((size_t)(kmax + m + 1) * kk); take((size_t)(kmax + m) * kk);
+    take(harmonic_ritz_ws_doubles(std::max(kmax + mcap, 1))); take((dfgemm_tc_ws_bytes() + 7) / 8);
+    add += 8 * (size_t)(kmax + mcap + 1) * ld + 8 * (size_t)kmax * ld + (p->rvec ? 0 : 8 * ld) +
+           8 * (total + (size_t)4 * (kmax + 4) + (size_t)kmax * kmax * 2 + 16 + partials_needed(p, kmax, mcap));
+  }
+  if (prm->precision == RK_MIXED && !p->coef32) add += 4 * S * n + 4 * ld;
+  if (prm->precision == RK_DF && !p->coefdf) add += 8 * S * n + 8 * ld;
+  if ((prm->precond == RK_PC_SUBDOMAIN || prm->precond_side == 1) && !p->sdw) add += 8 * 3 * ld;
+  if (bicg && !p->bicg) add += 8 * 7 * ld;
+  *device_bytes = now + (int64_t)add;
   return RK_OK;
 }
 

@@ -30,7 +30,8 @@ EXPORTS = ("rk_last_error", "rk_version", "rk_context_create", "rk_context_destr
            "rk_problem_destroy", "rk_set_recycle", "rk_get_recycle", "rk_solve", "rk_apply", "rk_residual",
            "rk_dots", "rk_problem_stats", "rk_profile_enable", "rk_profile_read", "rk_harmonic_ritz",
            "rk_dots_noalloc", "rk_row_gemm", "rk_solve_batch", "rk_problem_memory", "rk_problem_release",
-           "rk_problem_reset", "rk_fp64_fma_rate", "rk_arnoldi_dots",
+           "rk_problem_reset", "rk_fp64_fma_rate", "rk_arnoldi_dots", "rk_problem_wait_limit",
+           "rk_problem_footprint",
            "rk_recycle_bytes", "rk_export_recycle", "rk_import_recycle")
 
 
@@ -99,6 +100,8 @@ def load(path: str = LIB_PATH):
     L.rk_dots.argtypes = [vp, i64, i32, vp, i64, vp, vp, vp]
     L.rk_problem_stats.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i64)]
     L.rk_problem_reset.argtypes = [vp]
+    L.rk_problem_footprint.argtypes = [vp, ctypes.POINTER(rk_solve_params), ctypes.POINTER(i64)]
+    L.rk_problem_wait_limit.argtypes = [vp, i32, vp]
     L.rk_fp64_fma_rate.argtypes = [ctypes.POINTER(ctypes.c_double), vp]
     L.rk_arnoldi_dots.argtypes = [vp, i64, i32, vp, i64, vp, vp, vp, i32, vp]
     L.rk_profile_enable.argtypes = [vp, i32]

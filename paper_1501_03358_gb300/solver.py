@@ -254,6 +254,18 @@ class Problem:
             out.copy_(_f64_cuda(x0, (self.n,)))
         return b, out
 
+    def footprint(self, tol=1e-8, m=40, k=20, mode="rGCROT", max_matvec=2000, hybrid_switch=5,
+                  update_recycle=True, precision="fp64", hybrid_refresh=0, hybrid_fallback=0,
+                  precond_side="right", precond="jacobi", **_):
+        """Device bytes this problem will hold during and after a solve with
+        these parameters (rk_problem_footprint): for admission under a memory
+        budget before the first solve."""
+        prm = _params(tol, m, k, mode, max_matvec, hybrid_switch, update_recycle, precision, hybrid_refresh,
+                      hybrid_fallback, precond_side, precond)
+        v = ctypes.c_int64()
+        N.check(self.lib.rk_problem_footprint(self._h, ctypes.byref(prm), ctypes.byref(v)))
+        return int(v.value)
+
     def memory(self) -> int:
         """Device bytes held by this problem."""
         v = ctypes.c_int64()

@@ -97,38 +97,69 @@ def test_release_and_restore_is_exact(ctx):
     b.close()
 
 
-def test_serving_with_eviction_matches_direct_sequences(ctx):
-    """Requests for several problems under a budget that holds only part of
-    their workspaces: every request is solved, problems are evicted and
-    restored, and each problem's results equal its sequence solved directly."""
+def test_continuous_serving_with_eviction_matches_direct_sequences(ctx):
+    """Continuous admission: requests for four problems arrive while others
+    are being solved (three slots, each its own stream), under a budget that
+    holds the operators and only about two problems' solve footprints, so
+    problems are evicted (recycle space spilled to host memory) and restored
+    while other slots run. Each request's x equals, bit for bit, the same
+    problem's sequence solved alone, in both phases of the hybrid."""
     from paper_1501_03358_gb300 import Problem
     from paper_1501_03358_gb300.serving import Server
     cfgs = small_set(4, max_edge=36)
-    kw = dict(KW, mode="rGCROT")
-    direct = {}
+    kw = dict(KW)  # hybrid: steps 0-1 rGCROT, 2-3 rBiCGStab
+    steps = 4
+    direct, base, foot = {}, [], []
     for i, c in enumerate(cfgs):
         p = Problem(ctx, c.grid, torch.from_numpy(c.coef))
-        direct[i] = [p.solve(torch.from_numpy(c.rhs(t)).cuda(), **kw) for t in range(3)]
-        full = p.memory()
+        base.append(p.memory())
+        foot.append(p.footprint(**kw))
+        direct[i] = [p.solve(torch.from_numpy(c.rhs(t)).cuda(), **kw) for t in range(steps)]
         p.close()
-    # operators plus about two problems' workspace
-    op_bytes = sum(8 * (c.S + 2) * c.n for c in cfgs)
-    budget = op_bytes + 2 * max(8 * (kw["k"] * 2 + kw["m"] + 12) * c.n for c in cfgs)
-    srv = Server(ctx, budget, kw, max_batch=2)
+    budget = sum(base) + 2 * max(f - b for f, b in zip(foot, base))
+    srv = Server(ctx, budget, kw, slots=3)
     for i, c in enumerate(cfgs):
         srv.add(i, c.grid, torch.from_numpy(c.coef))
-    for t in range(3):
-        for i, c in enumerate(cfgs):
-            srv.submit(i, torch.from_numpy(c.rhs(t)).cuda())
+    rhs = {(i, t): torch.from_numpy(c.rhs(t)).cuda() for i, c in enumerate(cfgs) for t in range(steps)}
+    torch.cuda.synchronize()
+    # staggered arrivals: the next step of every problem is submitted while
+    # the slots are still busy with the previous ones
+    order = [(i, t) for t in range(steps) for i in range(len(cfgs))]
+    k = 0
+    while k < len(order) or srv.queue or srv.in_flight():
+        if k < len(order):
+            srv.submit(order[k][0], rhs[order[k]])
+            k += 1
+        srv.poll()
+        if k >= len(order) or srv.in_flight() >= 3:
+            srv.wait_any(timeout=5.0)
     srv.drain()
-    assert len(srv.done) == 12
+    assert len(srv.done) == len(order)
     assert srv.evictions > 0 and srv.restores > 0
-    seen = {i: 0 for i in range(4)}
+    assert srv.max_in_flight >= 2
+    seen = {i: 0 for i in range(len(cfgs))}
     for r in sorted(srv.done, key=lambda r: r.rid):
         t = seen[r.name]
         seen[r.name] += 1
         xd, idd = direct[r.name][t]
         assert r.info["status"] == 0
+        assert r.info["mode_used"] == idd["mode_used"]
         assert r.info["matvecs"] == idd["matvecs"], (r.name, t)
         assert torch.equal(r.x, xd), (r.name, t)
     srv.close()
+
+
+def test_footprint_bounds_the_memory_of_a_first_solve(ctx):
+    """rk_problem_footprint before any solve bounds the bytes the problem
+    holds after it (the admission figure of the serving loop), for every
+    mode and precision."""
+    from paper_1501_03358_gb300 import Problem
+    c = small_set(1, max_edge=30)[0]
+    for kw in (dict(KW), dict(KW, mode="rGCROT", precision="mixed"), dict(KW, mode="rBiCGStab", precision="df"),
+               dict(KW, mode="rGCROT", precond="subdomain", precond_side="left")):
+        p = Problem(ctx, c.grid, torch.from_numpy(c.coef))
+        f = p.footprint(**kw)
+        for t in range(3):
+            p.solve(torch.from_numpy(c.rhs(t)).cuda(), **kw)
+            assert p.memory() <= f, kw
+        p.close()

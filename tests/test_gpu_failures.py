@@ -3,7 +3,8 @@ hang): an allocator that returns NULL gives RK_E_OOM and leaves the problem
 usable, with the next solve equal bit for bit to the same solve on a problem
 that never saw a failure; a constructed rBiCGStab breakdown (Algorithm 4's
 "exit gracefully" branch) gives RK_E_BREAKDOWN after the restarts, as the
-oracle does."""
+oracle does; a bounded device wait made to run out from the host gives
+RK_E_DEVICE_TIMEOUT with no copy in flight, and the problem stays usable."""
 import ctypes
 
 import numpy as np
@@ -192,9 +193,44 @@ def test_rbicgstab_breakdown_matches_oracle(lib):
     assert info["matvecs"] == io["matvecs"] and info["restarts"] == io["restarts"]
     assert np.array_equal(x.cpu().numpy(), np.zeros(2))
     # the problem is still usable: a well-posed right-hand side for the same A
-    # (r~^T A M^{-1} r_0 = 1 + 4 != 0 for b = [1, 0]) converges
+    # (r~^T A M^{-1} r_0 = 1 for b = [1, 0]) converges
     x, info = p.solve(torch.tensor([1.0, 0.0], dtype=torch.float64).cuda(), tol=1e-12, mode="rBiCGStab", k=0)
     assert info["status"] == 0
     assert np.allclose(oracle.dense_matrix(g, coef) @ x.cpu().numpy(), [1.0, 0.0], rtol=0, atol=1e-12)
     p.close()
+    ctx.close()
+
+
+def test_bounded_wait_gives_device_timeout_and_problem_stays_usable(lib):
+    """The bounded waits of the bulk-copy pipeline, made to run out from the
+    host (rk_problem_wait_limit, one poll): the copy producer of the
+    double-float Arnoldi inner products gives up at a stage-release barrier,
+    issues nothing more, and the consumers stop at the first stage it did not
+    issue, so every copy they waited for had been issued and no copy is in
+    flight when a block exits. The solve returns RK_E_DEVICE_TIMEOUT; with
+    the limit restored the same problem solves the same system bit for bit
+    like a problem that never timed out."""
+    from paper_1501_03358_gb300 import Context, Problem, native
+    from paper_1501_03358_gb300.native import RKError, RK_E_DEVICE_TIMEOUT
+    cfg = make_config(1, size=32)  # 32^3 cells: 16 copy stages per block, so the producer waits
+    b = torch.from_numpy(cfg.rhs(0)).cuda()
+    kw = dict(tol=1e-8, mode="rGCROT", m=20, k=10, precision="df", max_matvec=3000)
+    ctx = Context()
+    ref = Problem(ctx, cfg.grid, torch.from_numpy(cfg.coef))
+    x_ref, info_ref = ref.solve(b, **kw)
+    assert info_ref["status"] == 0
+    p = Problem(ctx, cfg.grid, torch.from_numpy(cfg.coef))
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    native.check(lib.rk_problem_wait_limit(p._h, 1, stream))
+    with pytest.raises(RKError) as ei:
+        p.solve(b, **kw)
+    assert ei.value.code == RK_E_DEVICE_TIMEOUT
+    assert p.stats()["solves"] == 0 and p.stats()["recycle_dim"] == 0
+    native.check(lib.rk_problem_wait_limit(p._h, 0, stream))
+    x, info = p.solve(b, **kw)
+    assert info["status"] == 0
+    assert np.array_equal(x.cpu().numpy(), x_ref.cpu().numpy())
+    assert info["matvecs"] == info_ref["matvecs"]
+    p.close()
+    ref.close()
     ctx.close()
