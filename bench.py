@@ -726,98 +726,133 @@ def run_switch_sweep(args, ws, rank, local):
 
 
 def run_serve(args, ws, rank, local):
-    """Serving loop (reduced config 5): resident problems of mixed sizes
-    (channel and porous generators alternating), requests = the next
+    """Serving loop (config 5): resident problems of mixed sizes (channel and
+    porous generators alternating over --serve-edges), each request the next
     right-hand side of one problem, arriving as a Poisson process at
-    ``--rate-frac`` of the measured burst capacity; admission by a device
-    memory budget with LRU eviction of recycle spaces (exact spill to pinned
-    host memory). Reports solves/s and p50/p99 latency (completion - arrival),
-    and the same arrivals served by plain FP64 GMRES(40) without recycling."""
+    --rate-frac times the measured single-stream capacity; continuous
+    admission (serving.Server: --slots worker streams, requests start as
+    slots and memory free up) under a device-memory budget with LRU eviction
+    of recycle spaces (exact spill to pinned host memory). Reports solves/s
+    and p50/p99 latency (completion - arrival) for the hybrid recycling
+    solver (mixed precision) and for plain FP64 GMRES(40) without recycling
+    on the same arrivals. Problems of one edge and generator share their
+    coefficients (generated once); right-hand sides are b_t = F_a + 0.05 t F_b
+    from a pool of smoothed divergence fields per edge."""
     import torch
     torch.cuda.set_device(local)
     import __graft_entry__ as g
     g.build()
     from problems import make_config
-    from problems.configs import porous_problem, ConfigProblem
+    from problems.configs import porous_problem
+    from problems.fields import rng_for, face_velocity, divergence, normalise_div
     from paper_1501_03358_gb300 import Context
     from paper_1501_03358_gb300.serving import Server
     edges = [int(e) for e in args.serve_edges.split(",")]
-    cfgs = []
+    ops = {}
     for i in range(args.nprob):
         e = edges[i % len(edges)]
-        if i % 2 == 0:
-            cfgs.append(make_config(2, size=e, seed=20150113 + 5 + 1000 * rank + i))
+        kind = "channel" if (i // len(edges)) % 2 == 0 else "porous"
+        if (e, kind) in ops:
+            continue
+        if kind == "channel":
+            c = make_config(2, size=e)
+            ops[(e, kind)] = (c.grid, c.coef, c)
         else:
-            gr, coef, got = porous_problem((e, e, e), 0.25, 10.0, 20150113 + 5 + 1000 * rank + i,
-                                           max_attempts=200_000)
-            ones = np.ones(e)
-            cfgs.append(ConfigProblem(f"serve{i}", gr, 19, coef, {}, 20, 20150113 + 5 + i, "div",
-                                      dict(sigma=4.0, hx=ones, hy=ones, hz=ones, walls=(False, True, True))))
+            gr, coef, _ = porous_problem((e, e, e), 0.25, 10.0, 20150113 + 5 + e, max_attempts=200_000)
+            ops[(e, kind)] = (gr, coef, None)
+    fields = {}
+    for (e, kind), (gr, coef, c) in ops.items():
+        if e in fields:
+            continue
+        ones = np.ones(e)
+        vol = np.ones((e, e, e))
+        fl = []
+        for j in range(3):
+            u = face_velocity(gr, 4.0, rng_for(20150113 + 5, 7, 1000 * e + j), walls=(False, True, True))
+            fl.append(np.ascontiguousarray(normalise_div(divergence(gr, ones, ones, ones, *u), vol).reshape(-1)))
+        fields[e] = fl
+    probs = []
+    for i in range(args.nprob):
+        e = edges[i % len(edges)]
+        kind = "channel" if (i // len(edges)) % 2 == 0 else "porous"
+        probs.append((e, kind))
     nreq = args.requests
     rng = np.random.default_rng(20150113 + 55 + rank)
-    order = [int(i) for i in rng.integers(0, len(cfgs), nreq)]
-    seen = [0] * len(cfgs)
-    reqs = []
-    for i in order:
-        reqs.append((i, torch.from_numpy(cfgs[i].rhs(seen[i] + 1)).cuda()))
-        seen[i] += 1
+    order = [int(i) for i in rng.integers(0, len(probs), nreq)]
     ctx = Context()
-    footprint = sum(8 * (c.S + 2) * c.n + 8 * (2 * 20 + 40 + 12) * c.n for c in cfgs)
-    budget = int(args.budget_frac * footprint)
 
-    def serve(kw, rate):
-        srv = Server(ctx, budget, kw, max_batch=args.max_batch, nthreads=args.threads)
-        for i, c in enumerate(cfgs):
-            srv.add(i, c.grid, torch.from_numpy(c.coef))
-        # warm-up: one request per problem (builds recycle spaces), untimed
-        for i, c in enumerate(cfgs):
-            srv.submit(i, torch.from_numpy(c.rhs(0)).cuda())
+    def rhs(i, t):
+        fl = fields[probs[i][0]]
+        b = fl[i % 3] + 0.05 * t * fl[(i + 1) % 3]
+        if probs[i][1] == "channel":
+            b = b.copy()
+            b[0] = 0.0  # the pinned cell of the channel operator
+        return torch.from_numpy(b)
+
+    budget = int(args.budget_gb * 1e9)
+
+    def serve(kw, rate, nwarm=1):
+        srv = Server(ctx, budget, kw, slots=args.slots)
+        for i, (e, kind) in enumerate(probs):
+            gr, coef, _ = ops[(e, kind)]
+            srv.add(i, gr, torch.from_numpy(coef))
+        # warm-up (untimed): the first steps of every problem's sequence
+        for t in range(nwarm):
+            for i in range(len(probs)):
+                srv.submit(i, rhs(i, t).cuda())
         srv.drain()
         srv.done.clear()
+        seen = [nwarm] * len(probs)
+        reqs = []
+        for i in order:
+            reqs.append((i, rhs(i, seen[i]).pin_memory()))
+            seen[i] += 1
         arr = np.cumsum(rng.exponential(1.0 / rate, nreq)) if rate else np.zeros(nreq)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         nxt = 0
-        while nxt < nreq or srv.queue:
+        while nxt < nreq or srv.queue or srv.in_flight():
             now = time.perf_counter() - t0
             while nxt < nreq and arr[nxt] <= now:
-                srv.submit(reqs[nxt][0], reqs[nxt][1], arrival=t0 + arr[nxt])
+                srv.submit(reqs[nxt][0], reqs[nxt][1].to("cuda", non_blocking=True), arrival=t0 + arr[nxt])
                 nxt += 1
-            if srv.queue:
-                srv.step()
-            elif nxt < nreq:
-                time.sleep(max(0.0, min(arr[nxt] - now, 0.01)))
+            srv.poll()
+            wait = (arr[nxt] - (time.perf_counter() - t0)) if nxt < nreq else 1.0
+            if wait > 0:
+                srv.wait_any(timeout=min(max(wait, 0.0005), 1.0))
         wall = time.perf_counter() - t0
         lat = [1e3 * (r.finish - r.arrival) for r in srv.done]
         res = {"solves_per_s": len(srv.done) / wall, "latency_ms": _percentiles(lat),
                "converged": sum(1 for r in srv.done if r.info["status"] == 0), "requests": len(srv.done),
-               "evictions": srv.evictions, "restores": srv.restores,
-               "matvecs_per_solve": statistics.mean(r.info["matvecs"] for r in srv.done)}
+               "evictions": srv.evictions, "restores": srv.restores, "max_in_flight": srv.max_in_flight,
+               "matvecs_per_solve": statistics.mean(r.info["matvecs"] for r in srv.done),
+               "relres_max": max(r.info["relres_true"] for r in srv.done)}
         srv.close()
         return res
 
-    cap_mv = min(args.max_matvec, 4000)
+    cap_mv = args.max_matvec
     rkw = dict(tol=1e-8, m=40, k=20, mode="hybrid", hybrid_switch=5, max_matvec=cap_mv,
                precision=args.precision or "mixed")
     gkw = dict(tol=1e-8, m=40, k=0, mode="GMRES", max_matvec=cap_mv, precision="fp64")
-    cap = serve(rkw, None)                      # burst: all requests at t = 0
-    rate = args.rate_frac * cap["solves_per_s"]
-    live = serve(rkw, rate)
-    gm = serve(gkw, rate)
-    peaks, peak_src = load_peaks()
+    cap = serve(rkw, None)                      # burst: every request at t = 0
+    rates = [float(r) for r in args.rate_fracs.split(",")]
+    sweep = {}
+    for rf in rates:
+        sweep[str(rf)] = {"hybrid_recycling": serve(rkw, rf * cap["solves_per_s"])}
+        if not args.no_gmres:
+            sweep[str(rf)]["gmres40_fp64"] = serve(gkw, rf * cap["solves_per_s"])
+    head = sweep[str(rates[0])]["hybrid_recycling"]
     line = {
-        "metric": METRIC, "value": live["solves_per_s"], "unit": "solves/s", "n_gpus": ws, "steps": nreq,
-        "warmup": len(cfgs), "ms_per_step": 1e3 / max(live["solves_per_s"], 1e-9), "higher_is_better": True,
+        "metric": METRIC, "value": head["solves_per_s"], "unit": "solves/s", "n_gpus": ws, "steps": nreq,
+        "warmup": len(probs), "ms_per_step": 1e3 / max(head["solves_per_s"], 1e-9), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32-operator", "data": "synthetic",
-        "config": {"workload": "serve", "problems": len(cfgs), "edges": edges, "requests": nreq,
-                   "budget_bytes": budget, "budget_frac_of_footprint": args.budget_frac,
-                   "rate_per_s": rate, "rate_frac_of_capacity": args.rate_frac, "max_batch": args.max_batch,
+        "config": {"workload": "serve", "problems": len(probs), "edges": edges, "requests": nreq,
+                   "budget_bytes": budget, "slots": args.slots, "rate_fracs_of_capacity": rates,
                    "solver": "hybrid rGCROT(40,20)->rBiCGStab, mixed", "tol": 1e-8, "max_matvec": cap_mv,
-                   "reduced": "edges and problem count reduced from the 32 x {64..256}^3 / 120 GB serving set"},
-        "latency_ms": live["latency_ms"], "serving": live, "burst_capacity": cap,
-        "gmres40_no_recycling_same_arrivals": gm,
+                   "admission": "continuous (slots x streams), footprint reservation, LRU eviction"},
+        "latency_ms": head["latency_ms"], "burst_capacity": cap, "sweep": sweep,
         "roofline": None, "gpu_launches": None,
-        "e2e": {"value": live["solves_per_s"], "unit": "solves/s", "h2d_bytes_per_step": 0,
+        "e2e": {"value": head["solves_per_s"], "unit": "solves/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     if rank == 0:
@@ -858,17 +893,18 @@ def main():
     ap.add_argument("--sweep-max", type=int, default=9, help="switch sweep: largest switch step")
     ap.add_argument("--nprob", type=int, default=None, help="problems (batch64: 64; serve: 12)")
     ap.add_argument("--threads", type=int, default=0, help="rk_solve_batch worker threads (0: min(n, 16))")
-    ap.add_argument("--requests", type=int, default=60, help="serve: number of timed requests")
-    ap.add_argument("--serve-edges", default="32,48,64,96", help="serve: grid edges, cycled over problems")
-    ap.add_argument("--budget-frac", type=float, default=0.6, help="serve: memory budget / full footprint")
-    ap.add_argument("--rate-frac", type=float, default=0.7, help="serve: arrival rate / burst capacity")
-    ap.add_argument("--max-batch", type=int, default=8, help="serve: requests per batch")
+    ap.add_argument("--requests", type=int, default=64, help="serve: number of timed requests")
+    ap.add_argument("--serve-edges", default="64,96,128,192,256", help="serve: grid edges, cycled over problems")
+    ap.add_argument("--budget-gb", type=float, default=120.0, help="serve: device memory budget (GB)")
+    ap.add_argument("--rate-fracs", default="0.25,0.5,1,2", help="serve: arrival rates / burst capacity")
+    ap.add_argument("--slots", type=int, default=4, help="serve: concurrent solve slots (streams)")
+    ap.add_argument("--no-gmres", action="store_true", help="serve: skip the GMRES(40) arm")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     ws, rank, local = dist_init()
     if args.nprob is None:
-        args.nprob = 64 if args.workload == "batch64" else 12
+        args.nprob = 64 if args.workload == "batch64" else 32
     if args.precond is None:
         args.precond = "subdomain" if args.switch_sweep else PRECOND_DEFAULT.get(args.workload, "jacobi")
     if args.impl == "reference":
