@@ -277,11 +277,17 @@ int rk_arnoldi_dots(rk_context* ctx, int64_t n, int32_t nq, const double* Q, int
  * 2 <= nc <= 32 and na + nb <= 64
  * (7 BF16 digits per operand, exact FP32 accumulation per digit level on the
  * fifth-generation tensor cores); engine = 0 the double-float kernel on the
- * FP32 pipe; engine = 2 the FP64 kernel of the RK_FP64 / RK_MIXED basis on
- * A and B as given (FP64 fused multiply-adds, no rounding of the operands).
+ * FP32 pipe; engine = 2 the FP64 fused multiply-add kernel on A and B as
+ * given; engine = 3 the tensor-core kernel on A and B as given (the RK_FP64 /
+ * RK_MIXED recycle update, 2 <= nc <= 32, na + nb <= 64): each FP64 row of X
+ * cut exactly into a 56-bit fixed-point integer against its largest entry
+ * (bits below 2^-56 of it truncated) and seven balanced base-256 digits,
+ * exact digit products summed per level in FP32 on the tensor cores, the
+ * levels combined exactly in integers and rounded once to FP64 (out 16-byte
+ * aligned, ldo even).
  * RK_E_INVALID for bad arguments or a shape the tensor-core
  * engine does not take; RK_E_DEVICE_TIMEOUT if a bounded device wait gave
- * up. Engines 0 and 1 allocate temporary device memory through the
+ * up. Engines 0, 1 and 3 allocate temporary device memory through the
  * context's allocator (engine 2 allocates nothing); synchronises `stream`. No counterpart in the paper (a test entry point).
  */
 int rk_row_gemm(rk_context* ctx, int64_t n, int32_t na, const double* A, int64_t lda, int32_t nb,

@@ -282,10 +282,11 @@ __global__ void __launch_bounds__(kD2Threads) k_dfdots2(DFDots2Args a, int64_t r
     // consumers stop at stage s (every copy they wait for was issued)
     if (lane == 0) {
       const int lim = a.wait_limit != nullptr ? *a.wait_limit : 0;
-      const int polls = lim > 0 ? lim : kMbarPolls;
       for (int s = 0; s < nst; ++s) {
         const int slot = s % kD2Stages;
-        if (s >= kD2Stages && !mbar_wait_polls(&empty[slot], (unsigned)((s / kD2Stages - 1) & 1), polls)) {
+        const unsigned par = (unsigned)((s / kD2Stages - 1) & 1);
+        if (s >= kD2Stages &&
+            !(lim > 0 ? mbar_wait_polls(&empty[slot], par, lim) : mbar_wait_bounded(&empty[slot], par))) {
           if (a.err) atomicExch(a.err, 2);
           abort_at = s;
           __threadfence_block();

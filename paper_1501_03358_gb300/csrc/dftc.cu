@@ -110,6 +110,62 @@ __device__ __forceinline__ float scale_pow2(float x, int ex) {
   return ldexpf(x, ex);
 }
 
+// ---- FP64 operands (the RK_FP64 / RK_MIXED basis). A row's values are cut
+// against 2^E (|x| < 2^E over the row) into the signed fixed-point integer
+// F = trunc(x 2^(56 - E)) (|F| < 2^56: every bit of x within 2^3 of the
+// row's largest, the rest truncated below 2^(E - 56)), taken from the
+// IEEE-754 bits with integer operations, and F into seven balanced base-256
+// digits by rounding shifts from the top: d_1 = round(F / 2^48) (|d_1| <=
+// 256), each next digit the rounded remainder (|d_i| <= 128), so
+// F = sum_i d_i 2^(56 - 8i) exactly. The level sums S_L (exact integers
+// below 2^24 in FP32) are combined exactly in 64-bit integers
+// (hi = S_2 2^24 + S_3 2^16 + S_4 2^8 + S_5, lo = S_6 2^16 + S_7 2^8 + S_8)
+// and rounded once, fma(hi, 2^24, lo), in FP64.
+
+// the biased exponent field of x (0 for zeros and subnormals, which count as 0)
+__device__ __forceinline__ int f64_expbits(double x) {
+  return (int)((unsigned)(__double_as_longlong(x) >> 52) & 0x7ffu);
+}
+
+// F = trunc(x 2^(56 - E)) with E = emax - 1022 (emax the row's largest
+// exponent field), from the bits of x
+__device__ __forceinline__ long long f64_fixed56(double x, int emax) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int eb = (int)((b >> 52) & 0x7ffu);
+  if (eb == 0) return 0;
+  const unsigned long long m = (b & 0xfffffffffffffull) | 0x10000000000000ull;
+  const int sh = eb - emax + 3;  // <= 3
+  unsigned long long f;
+  if (sh >= 0)
+    f = m << sh;
+  else
+    f = sh > -60 ? (m >> (-sh)) : 0ull;
+  return (b >> 63) ? -(long long)f : (long long)f;
+}
+
+// exact FP32 integer value (|v| < 2^25) to int, from the bits
+__device__ __forceinline__ int f32_int_exact(float v) {
+  const unsigned u = __float_as_uint(v);
+  const int e = (int)((u >> 23) & 0xffu);
+  if (e < 127) return 0;  // |v| < 1: 0 (level sums are integers)
+  const int m = (int)((u & 0x7fffffu) | 0x800000u);
+  const int r = e >= 150 ? (m << (e - 150)) : (m >> (150 - e));
+  return (u >> 31) ? -r : r;
+}
+
+// exact int64 (|v| < 2^53) to FP64, from the bits
+__device__ __forceinline__ double i64_to_f64_exact(long long v) {
+  if (v == 0) return 0.0;
+  const unsigned long long neg = v < 0 ? 1ull : 0ull;
+  unsigned long long a = neg ? (unsigned long long)(-v) : (unsigned long long)v;
+  const int lz = __clzll((long long)a);   // a < 2^53: lz >= 11
+  const int e = 63 - lz;                  // a in [2^e, 2^(e+1))
+  a <<= (52 - e);                         // 53 significant bits, leading bit at 52
+  const unsigned long long bits = (neg << 63) | ((unsigned long long)(e + 1023) << 52) | (a & 0xfffffffffffffull);
+  return __longlong_as_double((long long)bits);
+}
+
+template <bool F64>
 __global__ void __launch_bounds__(kTcThreads, 1) k_dfgemm_tc(DFGemmArgs a, const __nv_bfloat16* __restrict__ bdig,
                                                                 const int* __restrict__ fexp, int kp, int bulk_ok,
                                                                 int* err) {
@@ -236,33 +292,85 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dfgemm_tc(DFGemmArgs a, const
           }
         if (a.bscale) bs[rl] = valid ? __ldg(&a.bscale[row]) : 0.0;
       }
-      const float2 sc = a.bscale ? df_from_double_i(bs[rl]) : make_float2(1.f, 0.f);
-      // half-row maximum of the high words; for the B part max |b| |s| with
-      // 2^-20 of headroom, which bounds the double-float products taken
-      // with the digits (their high words differ from b_hi s_hi by < 2^-22)
-      float mxa = 0.f, mxb = 0.f;
-      for (int ks = 0; ks < nks; ++ks)
-        for (int e = 0; e < 8; ++e) {
-          const int q = ks * 16 + half * 8 + e;
-          if (q >= np) break;
-          const float xh = fabsf(X[q * kTcRows + rl].x);
-          if (q < a.na)
-            mxa = fmaxf(mxa, xh);
-          else
-            mxb = fmaxf(mxb, xh);
-        }
-      float mx = fmaxf(mxa, mxb * fabsf(sc.x) * 1.00000095367431640625f);
-      rmax[it & 1][half][rl] = mx;
-      named_barrier_sync(pairbar, 64);
-      mx = fmaxf(rmax[it & 1][0][rl], rmax[it & 1][1][rl]);
-      int E = mx > 0.f ? ilogbf(mx) + 1 : 0;
-      E = E < -125 ? -125 : (E > 126 ? 126 : E);  // keep 2^-E a normal FP32 number
-      const float scale = __int_as_float((127 - E) << 23);
+      float2 sc = make_float2(1.f, 0.f);
+      float scale = 1.f;
+      int E = 0, emax = 0;
+      double* Xd = reinterpret_cast<double*>(X);
+      if constexpr (F64) {
+        // the B columns scaled in place (one FP64 product each), then the
+        // largest exponent field of the half-row, traded with the partner warp
+        const double scd = a.bscale ? bs[rl] : 1.0;
+        int em = 0;
+        for (int ks = 0; ks < nks; ++ks)
+          for (int e = 0; e < 8; ++e) {
+            const int q = ks * 16 + half * 8 + e;
+            if (q >= np) break;
+            double x = Xd[q * kTcRows + rl];
+            if (q >= a.na && a.bscale) {
+              x *= scd;
+              Xd[q * kTcRows + rl] = x;
+            }
+            em = max(em, f64_expbits(x));
+          }
+        rmax[it & 1][half][rl] = __int_as_float(em);
+        named_barrier_sync(pairbar, 64);
+        emax = max(__float_as_int(rmax[it & 1][0][rl]), __float_as_int(rmax[it & 1][1][rl]));
+        E = emax > 0 ? emax - 1022 : 0;  // |x| < 2^E over the row
+      } else {
+        sc = a.bscale ? df_from_double_i(bs[rl]) : make_float2(1.f, 0.f);
+        // half-row maximum of the high words; for the B part max |b| |s| with
+        // 2^-20 of headroom, which bounds the double-float products taken
+        // with the digits (their high words differ from b_hi s_hi by < 2^-22)
+        float mxa = 0.f, mxb = 0.f;
+        for (int ks = 0; ks < nks; ++ks)
+          for (int e = 0; e < 8; ++e) {
+            const int q = ks * 16 + half * 8 + e;
+            if (q >= np) break;
+            const float xh = fabsf(X[q * kTcRows + rl].x);
+            if (q < a.na)
+              mxa = fmaxf(mxa, xh);
+            else
+              mxb = fmaxf(mxb, xh);
+          }
+        float mx = fmaxf(mxa, mxb * fabsf(sc.x) * 1.00000095367431640625f);
+        rmax[it & 1][half][rl] = mx;
+        named_barrier_sync(pairbar, 64);
+        mx = fmaxf(rmax[it & 1][0][rl], rmax[it & 1][1][rl]);
+        E = mx > 0.f ? ilogbf(mx) + 1 : 0;
+        E = E < -125 ? -125 : (E > 126 ? 126 : E);  // keep 2^-E a normal FP32 number
+        scale = __int_as_float((127 - E) << 23);
+      }
       for (int ks = 0; ks < nks; ++ks, ++cc) {
         const int b = cc & 1;
         if (cc >= 2) wait(&dfree[b], (unsigned)(((cc >> 1) - 1) & 1));  // the MMAs that read it last
         // this warp's lanes, this K half's 4 columns of each digit plane
         const uint32_t ta = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + kTcADig + b * kTcADigCols + 4 * half;
+        if constexpr (F64) {
+          // the 8 elements of this thread's row and K half: fixed-point
+          // integers, then balanced base-256 digits top down
+          long long rem[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int q = ks * 16 + half * 8 + e;
+            rem[e] = q < np ? f64_fixed56(Xd[q * kTcRows + rl], emax) : 0ll;
+          }
+#pragma unroll
+          for (int i = 0; i < kTcDigits; ++i) {
+            const int sh = 48 - 8 * i;
+            float d[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              long long t = rem[e];
+              if (i < kTcDigits - 1) {
+                t = (rem[e] + (1ll << (sh - 1))) >> sh;  // rounded (arithmetic shift)
+                rem[e] -= t << sh;
+              }
+              d[e] = (float)(int)t;  // |t| <= 256: exact
+            }
+            tc_store4(ta + 8 * i, pack_bf16(d[0], d[1]), pack_bf16(d[2], d[3]), pack_bf16(d[4], d[5]),
+                      pack_bf16(d[6], d[7]));
+          }
+        } else {
         // The 8 elements of this thread's row and K half, digit by digit
         // (ILP 8). Digit i is yh rounded to a multiple of 256^-i, taken as
         // (yh + 1.5 2^(23-8i)) - 1.5 2^(23-8i) (the sum's ulp is 256^-i),
@@ -306,6 +414,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dfgemm_tc(DFGemmArgs a, const
 #pragma unroll
         for (int e = 0; e < 8; ++e) yh[e] = __fadd_rn(yh[e], yl[e]);
         digit(6, false);
+        }
         tc_wait_store();
         tc_fence_before_sync();
         __syncwarp();
@@ -328,7 +437,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dfgemm_tc(DFGemmArgs a, const
         for (int L = 2; L <= kTcDigits + 1; ++L) tc_load8_async(tl + kTcCols * (L - 2), lv[L - 2]);
         tc_wait_load();
 #pragma unroll
-        for (int L = kTcDigits + 1; L >= 2; --L) {
+        for (int L = kTcDigits + 1; L >= 2 && !F64; --L) {
           const float w = __int_as_float((127 - 8 * L) << 23);  // 256^-L
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
@@ -339,7 +448,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dfgemm_tc(DFGemmArgs a, const
             sh[u] = s2;
           }
         }
-        if (valid) {
+        if constexpr (F64) {
+          if (valid) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int c = c0 + u;
+              if (c < a.nc) {
+                // sum_L S_L 256^(8-L) exactly in 64-bit integers, one rounding
+                long long hi = 0, lo = 0;
+#pragma unroll
+                for (int L = 2; L <= 5; ++L) hi = (hi << 8) + f32_int_exact(__uint_as_float(lv[L - 2][u]));
+#pragma unroll
+                for (int L = 6; L <= kTcDigits + 1; ++L) lo = (lo << 8) + f32_int_exact(__uint_as_float(lv[L - 2][u]));
+                const double v = fma(i64_to_f64_exact(hi), 16777216.0, i64_to_f64_exact(lo));
+                reinterpret_cast<double*>(a.out)[(int64_t)c * a.ldo + row] = ldexp(v, E + fs[c] - 64);
+              }
+            }
+          }
+        } else if (valid) {
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
             const int c = c0 + u;
@@ -374,14 +500,19 @@ bool dfgemm_tc_supported(const DFGemmArgs& a, bool out_df) {
   return out_df && a.accum == 0 && a.nc >= 2 && a.nc <= kTcCols && np >= 1 && np <= kTcKMax;
 }
 
+bool gemm_tc_f64_supported(int np, int nc, int accum) {
+  return accum == 0 && nc >= 2 && nc <= kTcCols && np >= 1 && np <= kTcKMax;
+}
+
 void dfgemm_tc_prepare() {
   static std::atomic<uint64_t> done{0};
   once_per_device(done, [] {
-    cudaFuncSetAttribute(k_dfgemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    cudaFuncSetAttribute(k_dfgemm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    cudaFuncSetAttribute(k_dfgemm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
   });
 }
 
-cudaError_t launch_dfgemm_tc(const DFGemmArgs& a, void* ws, int* err, cudaStream_t st) {
+cudaError_t launch_dfgemm_tc(const DFGemmArgs& a, void* ws, int* err, cudaStream_t st, bool f64) {
   const int np = a.na + a.nb;
   const int kp = (np + 15) & ~15;
   __nv_bfloat16* bdig = reinterpret_cast<__nv_bfloat16*>(ws);
@@ -397,7 +528,10 @@ cudaError_t launch_dfgemm_tc(const DFGemmArgs& a, void* ws, int* err, cudaStream
   auto al16 = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
   const int bulk_ok = (a.na == 0 || (al16(a.A) && (a.lda & 1) == 0)) && (a.nb == 0 || (al16(a.Bm) && (a.ldb & 1) == 0)) &&
                       (a.bscale == nullptr || al16(a.bscale));
-  k_dfgemm_tc<<<blocks, kTcThreads, kTcSmem, st>>>(a, bdig, fexp, kp, bulk_ok, err);
+  if (f64)
+    k_dfgemm_tc<true><<<blocks, kTcThreads, kTcSmem, st>>>(a, bdig, fexp, kp, bulk_ok, err);
+  else
+    k_dfgemm_tc<false><<<blocks, kTcThreads, kTcSmem, st>>>(a, bdig, fexp, kp, bulk_ok, err);
   return cudaGetLastError();
 }
 

@@ -40,10 +40,22 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
   return false;
 }
 
-// the same with a given number of polls
+// non-blocking test of the phase with the given parity
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// the same with a given number of non-blocking polls (a try_wait may itself
+// wait for a while; a test_wait returns at once)
 __device__ __forceinline__ bool mbar_wait_polls(uint64_t* bar, unsigned parity, int polls) {
   for (int it = 0; it < polls; ++it)
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_test_wait(bar, parity)) return true;
   return false;
 }
 

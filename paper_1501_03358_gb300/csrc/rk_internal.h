@@ -227,10 +227,12 @@ cudaError_t launch_dfgemm_rows(const DFGemmArgs& a, bool out_df, cudaStream_t st
 // The same product on the tensor cores (digit-sliced, exact FP32
 // accumulation; dftc.cu): DF output, 2 <= nc <= 32, na + nb <= 64. ws holds
 // dfgemm_tc_ws_bytes() (16-byte aligned); err receives 3 if a bounded wait
-// gave up.
+// gave up. f64: A, Bm and out are FP64 columns (the pointers of a carry FP64
+// data; the FP64 basis), the result rounded once in FP64.
 size_t dfgemm_tc_ws_bytes();
 bool dfgemm_tc_supported(const DFGemmArgs& a, bool out_df);
-cudaError_t launch_dfgemm_tc(const DFGemmArgs& a, void* ws, int* err, cudaStream_t st);
+bool gemm_tc_f64_supported(int np, int nc, int accum);
+cudaError_t launch_dfgemm_tc(const DFGemmArgs& a, void* ws, int* err, cudaStream_t st, bool f64 = false);
 void dfgemm_tc_prepare();
 
 struct DFGramArgs {

@@ -552,6 +552,25 @@ int bgemm_launch(rk_problem* p, const void* A, int na, const void* Bm, int nb, c
     a.out = (double*)out;
     a.ldo = p->ld;
     a.accum = accum;
+    if (p->sb.tcws != nullptr && out_basis && gemm_tc_f64_supported(na + nb, nc, accum)) {
+      // FP64 operands on the tensor cores: exact digit products, one rounding
+      DFGemmArgs t{};
+      t.n = p->n;
+      t.na = na;
+      t.nb = nb;
+      t.nc = nc;
+      t.A = (const float2*)A;
+      t.lda = p->ld;
+      t.Bm = (const float2*)Bm;
+      t.ldb = p->ld;
+      t.bscale = bscale;
+      t.P = P;
+      t.out = out;
+      t.ldo = p->ld;
+      t.accum = 0;
+      RK_CUDA(launch_dfgemm_tc(t, p->sb.tcws, &p->st->dev_err, st, true));
+      return RK_OK;
+    }
     RK_CUDA(launch_gemm_rows_f64(a, st));
     return RK_OK;
   }
@@ -1437,9 +1456,49 @@ int rk_row_gemm(rk_context* ctx, int64_t n, int32_t na, const double* A, int64_t
                 int64_t ldb, const double* s, const double* P, int32_t nc, double* out, int64_t ldo, int32_t engine,
                 void* stream) {
   if (!ctx || n <= 0 || na < 0 || nb < 0 || na + nb < 1 || nc < 1 || !P || !out || ldo < n ||
-      (na > 0 && (!A || lda < n)) || (nb > 0 && (!B || ldb < n)) || engine < 0 || engine > 2)
+      (na > 0 && (!A || lda < n)) || (nb > 0 && (!B || ldb < n)) || engine < 0 || engine > 3)
     return fail(RK_E_INVALID, "bad argument to rk_row_gemm");
   cudaStream_t st = (cudaStream_t)stream;
+  if (engine == 3) {
+    // the tensor-core product on FP64 operands as given (the RK_FP64 /
+    // RK_MIXED recycle update)
+    if (!gemm_tc_f64_supported(na + nb, nc, 0) || ((uintptr_t)out & 15u) != 0 || (ldo & 1) != 0)
+      return fail(RK_E_INVALID, "rk_row_gemm: the tensor-core engine needs 2 <= nc <= 32 and na + nb <= 64");
+    void* ws = dev_alloc(ctx, dfgemm_tc_ws_bytes());
+    int* err = (int*)dev_alloc(ctx, sizeof(int));
+    int rc = RK_OK;
+    if (!ws || !err) {
+      rc = fail(RK_E_OOM, "rk_row_gemm: workspace allocation failed");
+    } else {
+      DFGemmArgs t{};
+      t.n = n;
+      t.na = na;
+      t.nb = nb;
+      t.nc = nc;
+      t.A = (const float2*)A;
+      t.lda = lda;
+      t.Bm = (const float2*)B;
+      t.ldb = ldb;
+      t.bscale = s;
+      t.P = P;
+      t.out = out;
+      t.ldo = ldo;
+      t.accum = 0;
+      cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+      if (e == cudaSuccess) e = launch_dfgemm_tc(t, ws, err, st, true);
+      int herr = 0;
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess)
+        rc = fail(RK_E_CUDA, std::string("rk_row_gemm: ") + cudaGetErrorString(e));
+      else if (herr != 0)
+        rc = fail(RK_E_DEVICE_TIMEOUT, "rk_row_gemm: a bounded device wait gave up");
+    }
+    cudaStreamSynchronize(st);
+    dev_free(ctx, ws);
+    dev_free(ctx, err);
+    return rc;
+  }
   if (engine == 2) {
     // the FP64 product of the RK_FP64 / RK_MIXED basis, on the operands as given
     F64GemmArgs g{};

@@ -159,7 +159,7 @@ def test_arnoldi_dots_against_exact_sums(ctx, n, nq, precision):
     assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) / bound))
 
 
-@pytest.mark.parametrize("engine", [1, 0, 2])
+@pytest.mark.parametrize("engine", [1, 0, 2, 3])
 @pytest.mark.parametrize("n,na,nb,nc,scaled", [
     (1, 3, 2, 2, False), (127, 20, 41, 20, True), (129, 61, 0, 20, False), (1000, 20, 40, 20, True),
     (5003, 0, 64, 32, True), (4099, 32, 32, 7, False), (300, 1, 0, 2, False), (70000, 20, 41, 20, True),
@@ -172,9 +172,13 @@ def test_row_gemm_recycle_update(ctx, engine, n, na, nb, nc, scaled):
     double-float epilogue, and the fixed-point digits, which truncate each
     element below 2^-56 of its row's (X) or column's (P) largest:
     |out - X P| <= 2^-45 (|X| |P|) + 2^-52 K max_row|X| max_col|P|.
-    FP64 engine (the fp64 and mixed basis): K fused multiply-adds per
-    output and one rounded product s_i b_iq: |out - X P| <= (K + 2) 2^-53
-    (|X| |P|).
+    FP64 engine: K fused multiply-adds per output and one rounded product
+    s_i b_iq: |out - X P| <= (K + 2) 2^-53 (|X| |P|). Tensor-core engine on
+    FP64 operands (the fp64 and mixed recycle update): s_i b_iq rounded
+    once, each element truncated below 2^-56 of 2^E_r (< 2^-55 of its row's
+    largest), P's seven digits to 2^-57 of 2^F_c, digit levels above 8
+    dropped, one final rounding: |out - X P| <= 2^-51 (|X| |P|) +
+    2^-50 K max_row|X| max_col|P|.
     Scales within a row and within a column of P span 2^8. 70000 rows
     span hundreds of tiles per block (bulk-copied tiles prefetched one
     ahead, then a ragged last tile); 70001 rows give operands the bulk copy
@@ -200,19 +204,23 @@ def test_row_gemm_recycle_update(ctx, engine, n, na, nb, nc, scaled):
         bound = 2.0 ** -45 * comp + 2.0 ** -52 * K * np.abs(P).max(axis=0)[:, None] * np.abs(X).max(axis=0)[None, :]
     elif engine == 2:
         bound = (na + nb + 2) * 2.0 ** -53 * comp
+    elif engine == 3:
+        K = na + nb
+        bound = 2.0 ** -51 * comp + 2.0 ** -50 * K * np.abs(P).max(axis=0)[:, None] * np.abs(X).max(axis=0)[None, :]
     else:
         bound = 2.0 ** -44 * comp
     err = np.abs((got.astype(np.longdouble) - ref).astype(np.float64))
     assert np.all(err <= bound), float(np.max(err / np.maximum(bound, 1e-300)))
 
 
-def test_row_gemm_tensor_engine_limits(ctx):
+@pytest.mark.parametrize("engine", [1, 3])
+def test_row_gemm_tensor_engine_limits(ctx, engine):
     from paper_1501_03358_gb300.native import RKError
     A = t(np.ones((65, 64)))
     with pytest.raises(RKError):
-        ctx.row_gemm(A, None, None, t(np.ones((65, 4))), engine=1)
+        ctx.row_gemm(A, None, None, t(np.ones((65, 4))), engine=engine)
     with pytest.raises(RKError):
-        ctx.row_gemm(t(np.ones((4, 64))), None, None, t(np.ones((4, 33))), engine=1)
+        ctx.row_gemm(t(np.ones((4, 64))), None, None, t(np.ones((4, 33))), engine=engine)
 
 
 _KAPPA = {}
