@@ -283,8 +283,7 @@ int rk_arnoldi_dots(rk_context* ctx, int64_t n, int32_t nq, const double* Q, int
  * cut exactly into a 56-bit fixed-point integer against its largest entry
  * (bits below 2^-56 of it truncated) and seven balanced base-256 digits,
  * exact digit products summed per level in FP32 on the tensor cores, the
- * levels combined exactly in integers and rounded once to FP64 (out 16-byte
- * aligned, ldo even).
+ * levels combined exactly in integers and rounded once to FP64.
  * RK_E_INVALID for bad arguments or a shape the tensor-core
  * engine does not take; RK_E_DEVICE_TIMEOUT if a bounded device wait gave
  * up. Engines 0, 1 and 3 allocate temporary device memory through the

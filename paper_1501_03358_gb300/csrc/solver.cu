@@ -1462,7 +1462,7 @@ int rk_row_gemm(rk_context* ctx, int64_t n, int32_t na, const double* A, int64_t
   if (engine == 3) {
     // the tensor-core product on FP64 operands as given (the RK_FP64 /
     // RK_MIXED recycle update)
-    if (!gemm_tc_f64_supported(na + nb, nc, 0) || ((uintptr_t)out & 15u) != 0 || (ldo & 1) != 0)
+    if (!gemm_tc_f64_supported(na + nb, nc, 0))
       return fail(RK_E_INVALID, "rk_row_gemm: the tensor-core engine needs 2 <= nc <= 32 and na + nb <= 64");
     void* ws = dev_alloc(ctx, dfgemm_tc_ws_bytes());
     int* err = (int*)dev_alloc(ctx, sizeof(int));
