@@ -130,12 +130,16 @@ typedef struct {
                             tol ||b|| / ||b - A x||). rBiCGStab is
                             always right-preconditioned (Sec. 2.1); a stored recycle space is
                             converted (C re-derived from U by CholQR2) when a solve uses the other
-                            side. Left with RK_MIXED: RK_E_INVALID */
+                            side. With RK_MIXED the left product is M32^{-1} (A32 v) (FP32 bands,
+                            1/a_pp and preconditioner) */
   int32_t precond;       /* rk_preconditioner. RK_PC_SUBDOMAIN: precision RK_FP64 (the operator and
-                            the preconditioner in FP64, bit-exact order) or RK_DF (the products of
+                            the preconditioner in FP64, bit-exact order), RK_DF (the products of
                             the recurrences with the double-float operator and a double-float
-                            evaluation of the same preconditioner; residuals, M^{-1} b and the final
-                            M^{-1} x~ in FP64); GMRES, rGCROT and the hybrid's rGCROT phase
+                            evaluation of the same preconditioner) or RK_MIXED (those products with
+                            the FP32 operator and the same sweeps in FP32: bands, 1/a_pp, r and
+                            omega rounded to FP32 once, every step one FP32 rounding in the FP64
+                            order); residuals, M^{-1} b and the final M^{-1} x~ in FP64 in every
+                            precision; GMRES, rGCROT and the hybrid's rGCROT phase
                             left-preconditioned only (precond_side = 1), rBiCGStab
                             right-preconditioned (x <- x + M^{-1} x~); otherwise RK_E_INVALID */
 } rk_solve_params;
@@ -229,7 +233,9 @@ int rk_solve(rk_problem* p, const double* b, double* x, const rk_solve_params* p
  * widened to FP64 (exact); 5: y = M^{-1} v and 6: y = M^{-1} (A v) with the
  * sub-domain preconditioner (RK_PC_SUBDOMAIN); 7 and 8: the same with the
  * double-float variant of RK_DF (v rounded to double-float, the result
- * widened to FP64); for 5-8 y must not alias v. Other
+ * widened to FP64); 9 and 10: y = M32^{-1} v and y = M32^{-1} (A32 v) with
+ * the FP32 variant of RK_MIXED; 11: y = d32 .* (A32 v), the FP32 left
+ * point-Jacobi product of RK_MIXED; for 5-11 y must not alias v. Other
  * values: RK_E_INVALID. The operator copies of modes 2, 3, 7 and 8 and the
  * workspace of modes 5-8 are made on first use (and freed by
  * rk_problem_release).

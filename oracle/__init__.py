@@ -19,6 +19,8 @@ Parity status of each function:
 * ``bicgstab``: pinned (dense LU).
 * ``rbicgstab``: pinned (empty recycle space equals ``bicgstab`` exactly;
   dense LU; r ⟂ C; solution/residual relation).
+* ``Stencil.apply_f32/schwarz_f32`` (the FP32 restatements of the mixed
+  precision): pinned within FP32 rounding of the pinned FP64 forms.
 * Iteration counts of the paper's Tables 2-8: parity unpinned (the paper's
   matrices are not available).
 """

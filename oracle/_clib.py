@@ -45,6 +45,11 @@ def lib():
             L.oracle_apply_prec_f32.argtypes = [i64, i64, i64, p, ctypes.c_int, p, p, p, p]
             L.oracle_jacobi_inverse.restype = None
             L.oracle_jacobi_inverse.argtypes = [i64, p, p]
+            L.oracle_apply_f32.restype = None
+            L.oracle_apply_f32.argtypes = [i64, i64, i64, p, ctypes.c_int, p, p, ctypes.c_int, p, p]
+            L.oracle_schwarz_jacobi_f32.restype = None
+            L.oracle_schwarz_jacobi_f32.argtypes = [i64, i64, i64, p, ctypes.c_int, p, p, ctypes.c_int, ctypes.c_int,
+                                                    ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, p, p]
             L.oracle_schwarz_jacobi.restype = None
             L.oracle_schwarz_jacobi.argtypes = [i64, i64, i64, p, ctypes.c_int, p, p, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, p, p]
@@ -125,6 +130,32 @@ class Stencil:
                                     self.SCHWARZ_SWEEPS if sweeps is None else sweeps,
                                     self.SCHWARZ_OMEGA if omega is None else omega, _ptr(r), _ptr(z))
         return z
+
+    def apply_f32(self, v, left=False):
+        """The FP32 operator of the mixed precision: A32 v32, or with ``left``
+        d32 .* (A32 v32) (oracle_apply_f32)."""
+        v = _c64(v)
+        y = np.empty(self.n)
+        lib().oracle_apply_f32(*self._dims()[:6], _ptr(self.dinv), 3 if left else 1, _ptr(v), _ptr(y))
+        return y
+
+    def schwarz_f32(self, r):
+        """z = M32^{-1} r: the sub-domain preconditioner restated in FP32
+        (oracle_schwarz_jacobi_f32), the class constants as parameters."""
+        r = _c64(r)
+        z = np.empty(self.n)
+        bx, by, bz = self.SCHWARZ_BOX
+        lib().oracle_schwarz_jacobi_f32(*self._dims()[:6], _ptr(self.dinv), bx, by, bz, self.SCHWARZ_OVERLAP,
+                                        self.SCHWARZ_SWEEPS, self.SCHWARZ_OMEGA, _ptr(r), _ptr(z))
+        return z
+
+    def left_schwarz_f32(self, v):
+        """M32^{-1} (A32 v): the left-preconditioned FP32 product of the mixed precision."""
+        return self.schwarz_f32(self.apply_f32(v))
+
+    def right_schwarz_f32(self, v):
+        """A32 (M32^{-1} v): the right-preconditioned FP32 product of the mixed precision."""
+        return self.apply_f32(self.schwarz_f32(v))
 
     def apply_left(self, v):
         """M^{-1} (A v) (left preconditioning): the product, then one rounding per element."""

@@ -77,6 +77,12 @@ cudaError_t launch_round_df(int64_t n, const double* src, float2* dst, cudaStrea
 cudaError_t launch_stencil_dd(const Dims& d, int S, int mode, const float2* coefd, const float2* dinvd,
                               const void* v, bool v_df, void* y, bool y_df, const int* skip, cudaStream_t st);
 cudaError_t launch_round_f32(int64_t n, const double* src, float* dst, cudaStream_t st);
+// The FP32 operator in the modes ST_PREC, ST_PLAIN, ST_LEFT and ST_JSWEEP
+// (y = fmaf(omega32, d32 .* (r32 - A32 v), v) with r32 FP32): v and y FP64
+// (kind 0) or FP32 (kind 1); FP32 rounding of every step in band order.
+cudaError_t launch_stencil32_ex(const Dims& d, int S, int mode, const float* coef32, const float* dinv32,
+                                const void* v, int v_kind, void* y, int y_kind, const float* r32, const int* skip,
+                                cudaStream_t st);
 cudaError_t launch_stencil_df(const Dims& d, int S, int mode, const double* coef, const double* dinv,
                               const void* v, bool v_df, void* y, bool y_df, const int* skip_flag, cudaStream_t st);
 int stencil_blocks(const Dims& d);
@@ -99,6 +105,11 @@ cudaError_t launch_subdomain_local(const Dims& d, int S, const double* coef, con
                                    double* z, const int* skip, cudaStream_t st);
 // The double-float variant (RK_DF): bands and 1/a_pp from their double-float
 // copies, r FP64 or double-float (r_df), z double-float.
+// The FP32 variant (RK_MIXED): bands and 1/a_pp from their FP32 copies, r
+// FP64 (rounded on load) or FP32 (r_f32), z FP32, every step in FP32 in the
+// order of the FP64 kernel.
+cudaError_t launch_subdomain_local32(const Dims& d, int S, const float* coef32, const float* dinv32, const void* r,
+                                     bool r_f32, float* z, const int* skip, cudaStream_t st);
 void subdomain_prepare();
 cudaError_t launch_subdomain_local_dd(const Dims& d, int S, const float2* coefd, const float2* dinvd, const void* r,
                                       bool r_df, float2* z, const int* skip, cudaStream_t st);

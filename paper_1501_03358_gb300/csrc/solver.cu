@@ -109,9 +109,9 @@ int alloc_into(rk_context* c, T** out, size_t count) {
 
 // Opt-in per-kernel-class timing: CUDA events recorded on the solve's stream
 // around every launch, reduced at the solve's synchronisation points.
-enum ProfClass { PC_SPMV = 0, PC_RESID, PC_DOTS, PC_UPDATE, PC_GEMM, PC_GRAM, PC_SMALL, PC_BICG, PC_HRITZ, PC_SUBDOMAIN, PC_SUBDOMAIN_DF, PC_COUNT };
+enum ProfClass { PC_SPMV = 0, PC_RESID, PC_DOTS, PC_UPDATE, PC_GEMM, PC_GRAM, PC_SMALL, PC_BICG, PC_HRITZ, PC_SUBDOMAIN, PC_SUBDOMAIN_DF, PC_SUBDOMAIN32, PC_COUNT };
 static const char* kProfNames[PC_COUNT] = {"spmv", "residual", "dots", "update", "gemm_rows", "gram", "small", "bicg", "harmonic_ritz", "subdomain_local",
-                                             "subdomain_df"};
+                                             "subdomain_df", "subdomain32"};
 
 struct Profiler {
   bool on = false;
@@ -777,6 +777,29 @@ int subdomain_launch(rk_problem* p, const double* r, void* y, bool y_df, double*
   return RK_OK;
 }
 
+// y = M32^{-1} r with the FP32 variant of the sub-domain preconditioner
+// (RK_MIXED): r FP64 (rounded to FP32 into the scratch) or FP32 (r_f32,
+// which must not lie in the first two FP32 vectors of the scratch); y FP64
+// (y_kind 0) or FP32 (y_kind 1). Scratch: the preconditioner workspace as
+// FP32 vectors [r32 | z32 | ...].
+int subdomain32_launch(rk_problem* p, const void* r, bool r_f32, void* y, int y_kind, const int* skip,
+                       cudaStream_t st) {
+  float* f0 = reinterpret_cast<float*>(p->sdw);
+  float* z32 = f0 + p->ld;
+  const float* r32 = (const float*)r;
+  if (!r_f32) {
+    RK_CUDA(launch_round_f32(p->n, (const double*)r, f0, st));
+    r32 = f0;
+  }
+  {
+    ProfScope ps(&p->prof, PC_SUBDOMAIN32, 4.0 * (p->S + 3) * (double)p->n, st);
+    RK_CUDA(launch_subdomain_local32(p->d, p->S, p->coef32, p->dinv32, r32, true, z32, skip, st));
+  }
+  ProfScope ps(&p->prof, PC_SPMV, 4.0 * (p->S + 4) * (double)p->n, st);
+  RK_CUDA(launch_stencil32_ex(p->d, p->S, ST_JSWEEP, p->coef32, p->dinv32, z32, 1, y, y_kind, r32, skip, st));
+  return RK_OK;
+}
+
 int ensure_operator(rk_problem* p, int precision, cudaStream_t st) {
   if (precision == RK_MIXED) return ensure_mixed(p, st);
   if (precision == RK_DF) return ensure_dfop(p, st);
@@ -787,6 +810,30 @@ int ensure_operator(rk_problem* p, int precision, cudaStream_t st) {
 // (RK_MIXED) or the double-float operator (RK_DF)
 int opapply_launch(rk_problem* p, int precision, const void* v, bool v_df, void* y, bool y_df, const int* skip,
                    cudaStream_t st, bool left = false, int pc = RK_PC_JACOBI) {
+  if (precision == RK_MIXED && (left || pc == RK_PC_SUBDOMAIN)) {
+    // the FP32 operator with the preconditioner from the left (point Jacobi
+    // or the FP32 sub-domain sweeps), or the FP32 sub-domain preconditioner
+    // from the right; FP64 vectors in and out (the mixed basis is FP64)
+    if (v_df || y_df) return fail(RK_E_INVALID, "the FP32 products take FP64 vectors");
+    float* f = reinterpret_cast<float*>(p->sdw);
+    if (pc != RK_PC_SUBDOMAIN) {
+      ProfScope ps(&p->prof, PC_SPMV, 8.0 * (0.5 * p->S + 2.5) * (double)p->n, st);
+      RK_CUDA(launch_stencil32_ex(p->d, p->S, ST_LEFT, p->coef32, p->dinv32, v, 0, y, 0, nullptr, skip, st));
+      return RK_OK;
+    }
+    float* t32 = f + 2 * p->ld;  // A32 v (left) or M32^{-1} v (right)
+    if (left) {
+      {
+        ProfScope ps(&p->prof, PC_SPMV, 8.0 * (0.5 * p->S + 1.5) * (double)p->n, st);
+        RK_CUDA(launch_stencil32_ex(p->d, p->S, ST_PLAIN, p->coef32, p->dinv32, v, 0, t32, 1, nullptr, skip, st));
+      }
+      return subdomain32_launch(p, t32, true, y, 0, skip, st);
+    }
+    RK_TRY(subdomain32_launch(p, v, false, t32, 1, skip, st));
+    ProfScope ps(&p->prof, PC_SPMV, 8.0 * (0.5 * p->S + 1.5) * (double)p->n, st);
+    RK_CUDA(launch_stencil32_ex(p->d, p->S, ST_PLAIN, p->coef32, p->dinv32, t32, 1, y, 0, nullptr, skip, st));
+    return RK_OK;
+  }
   if (pc == RK_PC_SUBDOMAIN && precision == RK_DF) {
     // the same products with the double-float operator and preconditioner
     float2* t = (float2*)(p->sdw + p->ld);
@@ -1082,9 +1129,10 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
     conv = converged();
   }
   if (mixed && update && p->kdim > 0) {
-    // the FP32 operator leaves A U = C only to FP32 accuracy: re-derive C from
-    // U in FP64 so the space carried to the next solve keeps A U = C exactly
-    RK_TRY(derive_c_from_u(p, p->kdim, st));
+    // the FP32 operator leaves A U = C (left: M^{-1} A U = C) only to FP32
+    // accuracy: re-derive C from U with the FP64 operator and preconditioner
+    // so the space carried to the next solve keeps the pair exact
+    RK_TRY(derive_c_from_u(p, p->kdim, st, left, pc));
   }
   info.matvecs = matvecs;
   info.cycles_or_iters = cycles;
@@ -1412,7 +1460,21 @@ int rk_apply(const rk_problem* p, const double* v, double* y, int32_t precond, v
     RK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     return RK_OK;
   }
-  if (precond < 0 || precond > 8) return fail(RK_E_INVALID, "precond must be 0..8");
+  if (precond >= 9 && precond <= 11) {
+    if (v == y) return fail(RK_E_INVALID, "y must not alias v");
+    rk_problem* pm = const_cast<rk_problem*>(p);
+    cudaStream_t st = (cudaStream_t)stream;
+    RK_TRY(ensure_mixed(pm, st));
+    RK_TRY(ensure_subdomain(pm));
+    if (precond == 9)
+      RK_TRY(subdomain32_launch(pm, v, false, y, 0, nullptr, st));
+    else
+      RK_TRY(opapply_launch(pm, RK_MIXED, v, false, y, false, nullptr, st, true,
+                            precond == 10 ? RK_PC_SUBDOMAIN : RK_PC_JACOBI));
+    RK_CUDA(cudaStreamSynchronize(st));
+    return RK_OK;
+  }
+  if (precond < 0 || precond > 11) return fail(RK_E_INVALID, "precond must be 0..11");
   RK_CUDA(launch_stencil(p->d, p->S, precond == 4 ? ST_LEFT : (precond ? ST_PREC : ST_PLAIN), p->coef, p->dinv, v, nullptr, y, nullptr,
                          nullptr, nullptr, nullptr, (cudaStream_t)stream));
   RK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
@@ -1729,12 +1791,8 @@ int rk_solve(rk_problem* p, const double* b, double* x, const rk_solve_params* p
   cudaStream_t st = (cudaStream_t)stream;
   if (prm.hybrid_refresh < 0 || prm.hybrid_fallback < 0) return fail(RK_E_INVALID, "negative hybrid parameter");
   if (prm.precond_side != 0 && prm.precond_side != 1) return fail(RK_E_INVALID, "precond_side must be 0 or 1");
-  if (prm.precond_side == 1 && prm.precision == RK_MIXED)
-    return fail(RK_E_INVALID, "left preconditioning is not available with RK_MIXED");
   if (prm.precond != RK_PC_JACOBI && prm.precond != RK_PC_SUBDOMAIN) return fail(RK_E_INVALID, "unknown precond");
   if (prm.precond == RK_PC_SUBDOMAIN) {
-    if (prm.precision == RK_MIXED)
-      return fail(RK_E_INVALID, "the sub-domain preconditioner runs in RK_FP64 or RK_DF");
     if (prm.mode != RK_RBICGSTAB && prm.precond_side != 1)
       return fail(RK_E_INVALID, "the sub-domain preconditioner is applied from the left in GMRES and rGCROT");
     RK_TRY(ensure_subdomain(p));

@@ -143,6 +143,8 @@ template <>
 __device__ __forceinline__ float ld_f32<double>(const double* p, int64_t q) { return __double2float_rn(__ldg(&p[q])); }
 template <>
 __device__ __forceinline__ float ld_f32<float2>(const float2* p, int64_t q) { return __ldg(&p[q]).x; }
+template <>
+__device__ __forceinline__ float ld_f32<float>(const float* p, int64_t q) { return __ldg(&p[q]); }
 
 template <typename YT>
 __device__ __forceinline__ void st_f32(YT* p, int64_t q, float w);
@@ -150,11 +152,19 @@ template <>
 __device__ __forceinline__ void st_f32<double>(double* p, int64_t q, float w) { p[q] = (double)w; }
 template <>
 __device__ __forceinline__ void st_f32<float2>(float2* p, int64_t q, float w) { p[q] = make_float2(w, 0.f); }
+template <>
+__device__ __forceinline__ void st_f32<float>(float* p, int64_t q, float w) { p[q] = w; }
 
-template <int S, typename VT, typename YT>
+// MODE: ST_PREC y = A32 (d32 .* v32); ST_PLAIN y = A32 v32; ST_LEFT
+// y = d32 .* (A32 v32) (the product, then one rounded multiplication);
+// ST_JSWEEP y = fmaf(omega32, d32 .* (r32 - A32 v32), v32) (the global damped
+// sweep of the FP32 sub-domain preconditioner), every step one FP32 rounding
+// in the band order of the FP64 kernels.
+template <int S, int MODE, typename VT, typename YT, typename RT>
 __global__ void __launch_bounds__(kTX* kTY) k_stencil32(Dims d, const float* __restrict__ coef,
                                                         const float* __restrict__ dinv, const VT* __restrict__ v,
-                                                        YT* __restrict__ y, const int* skip, int zchunk) {
+                                                        YT* __restrict__ y, const int* skip, int zchunk,
+                                                        const RT* __restrict__ r, float om) {
   if (skip != nullptr && *skip != 0) return;
   __shared__ float sz[3][kTY + 2][kTX + 2];
   const int tx = threadIdx.x & (kTX - 1), ty = threadIdx.x / kTX;
@@ -174,7 +184,8 @@ __global__ void __launch_bounds__(kTX* kTY) k_stencil32(Dims d, const float* __r
       float val = 0.f;
       if (kw >= 0 && xw >= 0 && yw >= 0) {
         const int64_t q = (int64_t)xw + (int64_t)d.nx * yw + plane * kw;
-        val = __fmul_rn(ld_f32<VT>(v, q), __ldg(&dinv[q]));
+        val = ld_f32<VT>(v, q);
+        if (MODE == ST_PREC) val = __fmul_rn(val, __ldg(&dinv[q]));
       }
       sz[slot][ly][lx] = val;
     }
@@ -210,6 +221,9 @@ __global__ void __launch_bounds__(kTX* kTY) k_stencil32(Dims d, const float* __r
         w = fmaf(__ldg(&coef[17 * N + p]), sz[sp][cy - 1][cx], w);
         w = fmaf(__ldg(&coef[18 * N + p]), sz[sp][cy + 1][cx], w);
       }
+      if (MODE == ST_JSWEEP) w = __fsub_rn(ld_f32<RT>(r, p), w);
+      if (MODE == ST_LEFT || MODE == ST_JSWEEP) w = __fmul_rn(w, __ldg(&dinv[p]));
+      if (MODE == ST_JSWEEP) w = fmaf(om, w, sz[sc][cy][cx]);
       st_f32<YT>(y, p, w);
     }
     __syncthreads();
@@ -442,8 +456,9 @@ cudaError_t launch_stencil32(const Dims& d, int S, const float* coef32, const fl
   int zchunk;
   stencil_grid(d, grid, zchunk);
   const dim3 block(kTX * kTY);
-#define RK_S32(SS, VT, YT) \
-  k_stencil32<SS, VT, YT><<<grid, block, 0, st>>>(d, coef32, dinv32, (const VT*)v, (YT*)y, skip, zchunk)
+#define RK_S32(SS, VT, YT)                                                                                   \
+  k_stencil32<SS, ST_PREC, VT, YT, float><<<grid, block, 0, st>>>(d, coef32, dinv32, (const VT*)v, (YT*)y, skip, \
+                                                                  zchunk, nullptr, 0.f)
 #define RK_S32_T(SS)                            \
   if (v_df && y_df) RK_S32(SS, float2, float2); \
   else if (v_df) RK_S32(SS, float2, double);    \
@@ -456,6 +471,39 @@ cudaError_t launch_stencil32(const Dims& d, int S, const float* coef32, const fl
   }
 #undef RK_S32_T
 #undef RK_S32
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stencil32_ex(const Dims& d, int S, int mode, const float* coef32, const float* dinv32,
+                                const void* v, int v_kind, void* y, int y_kind, const float* r32, const int* skip,
+                                cudaStream_t st) {
+  dim3 grid;
+  int zchunk;
+  stencil_grid(d, grid, zchunk);
+  const dim3 block(kTX * kTY);
+  const float om = (float)kSdOmega;
+  // kinds: 0 FP64, 1 FP32 (the FP32 scratch vectors of the sub-domain preconditioner)
+#define RK_S32X(SS, MM, VT, YT) \
+  k_stencil32<SS, MM, VT, YT, float><<<grid, block, 0, st>>>(d, coef32, dinv32, (const VT*)v, (YT*)y, skip, zchunk, r32, om)
+#define RK_S32X_T(SS, MM)                                 \
+  if (v_kind == 1 && y_kind == 1) RK_S32X(SS, MM, float, float); \
+  else if (v_kind == 1) RK_S32X(SS, MM, float, double);       \
+  else if (y_kind == 1) RK_S32X(SS, MM, double, float);       \
+  else RK_S32X(SS, MM, double, double);
+#define RK_S32X_M(SS)                                                  \
+  if (mode == ST_PLAIN) { RK_S32X_T(SS, ST_PLAIN) }                     \
+  else if (mode == ST_LEFT) { RK_S32X_T(SS, ST_LEFT) }                  \
+  else if (mode == ST_JSWEEP) { RK_S32X_T(SS, ST_JSWEEP) }              \
+  else { RK_S32X_T(SS, ST_PREC) }
+  if (mode == ST_JSWEEP && r32 == nullptr) return cudaErrorInvalidValue;
+  if (S == 7) {
+    RK_S32X_M(7)
+  } else {
+    RK_S32X_M(19)
+  }
+#undef RK_S32X_M
+#undef RK_S32X_T
+#undef RK_S32X
   return cudaGetLastError();
 }
 

@@ -150,6 +150,115 @@ __global__ void __launch_bounds__(kSdThreads, 2)
   }
 }
 
+// ---- the FP32 variant (the mixed precision, RK_MIXED): the same sweeps with
+// the FP32 copies of the bands and of 1/a_pp (each rounded once from FP64),
+// r rounded to FP32, omega = RN32(2/3), the sweep buffers in FP32 and every
+// operation an FP32 one in the order of the FP64 kernel:
+//   s = a_0 z_e; s = fmaf(a_t, z_nb, s); u = d (r - s); z_e <- fmaf(omega, u, z_e)
+// (the first sweep omega (d r)). Half the shared memory of the FP64 kernel,
+// so 4 CTAs of 256 threads fit an SM.
+template <typename RT>
+__device__ __forceinline__ float sd_ld32(const RT* p, int64_t q);
+template <>
+__device__ __forceinline__ float sd_ld32<double>(const double* p, int64_t q) { return __double2float_rn(__ldg(&p[q])); }
+template <>
+__device__ __forceinline__ float sd_ld32<float>(const float* p, int64_t q) { return __ldg(&p[q]); }
+
+template <int S>
+__device__ __forceinline__ float sd_row32(const float* __restrict__ coef, int64_t N, int64_t p, const float* z, int q) {
+  float s = __fmul_rn(__ldg(&coef[p]), z[q]);
+  s = fmaf(__ldg(&coef[1 * N + p]), z[q - 1], s);
+  s = fmaf(__ldg(&coef[2 * N + p]), z[q + 1], s);
+  s = fmaf(__ldg(&coef[3 * N + p]), z[q - kPX], s);
+  s = fmaf(__ldg(&coef[4 * N + p]), z[q + kPX], s);
+  s = fmaf(__ldg(&coef[5 * N + p]), z[q - kPXY], s);
+  s = fmaf(__ldg(&coef[6 * N + p]), z[q + kPXY], s);
+  if (S == 19) {
+    s = fmaf(__ldg(&coef[7 * N + p]), z[q - 1 - kPX], s);
+    s = fmaf(__ldg(&coef[8 * N + p]), z[q + 1 - kPX], s);
+    s = fmaf(__ldg(&coef[9 * N + p]), z[q - 1 + kPX], s);
+    s = fmaf(__ldg(&coef[10 * N + p]), z[q + 1 + kPX], s);
+    s = fmaf(__ldg(&coef[11 * N + p]), z[q - 1 - kPXY], s);
+    s = fmaf(__ldg(&coef[12 * N + p]), z[q + 1 - kPXY], s);
+    s = fmaf(__ldg(&coef[13 * N + p]), z[q - 1 + kPXY], s);
+    s = fmaf(__ldg(&coef[14 * N + p]), z[q + 1 + kPXY], s);
+    s = fmaf(__ldg(&coef[15 * N + p]), z[q - kPX - kPXY], s);
+    s = fmaf(__ldg(&coef[16 * N + p]), z[q + kPX - kPXY], s);
+    s = fmaf(__ldg(&coef[17 * N + p]), z[q - kPX + kPXY], s);
+    s = fmaf(__ldg(&coef[18 * N + p]), z[q + kPX + kPXY], s);
+  }
+  return s;
+}
+
+template <int S, typename RT>
+__global__ void __launch_bounds__(kSdThreads, 4)
+    k_subdomain_local32(Dims d, const float* __restrict__ coef, const float* __restrict__ dinv,
+                        const RT* __restrict__ r, float* __restrict__ z, const int* skip, int nbx, int nby) {
+  if (skip != nullptr && *skip != 0) return;
+  __shared__ float buf[2][kPad];
+  const float om = (float)kSdOmega;
+  const int box = blockIdx.x;
+  const int x0 = (box % nbx) * kSdBX, y0 = ((box / nbx) % nby) * kSdBY, z0 = (box / (nbx * nby)) * kSdBZ;
+  const int wx = min(kSdBX, d.nx - x0), wy = min(kSdBY, d.ny - y0), wz = min(kSdBZ, d.nz - z0);
+  const int ex = wx + 2 * kSdOverlap, ey = wy + 2 * kSdOverlap, ez = wz + 2 * kSdOverlap;
+  const int ne = ex * ey * ez;
+  const int64_t N = d.n;
+  const int64_t plane = (int64_t)d.nx * d.ny;
+  for (int t = threadIdx.x; t < 2 * kPad; t += kSdThreads) (&buf[0][0])[t] = 0.f;
+  int64_t gp[kCellsPer];
+  int pe[kCellsPer];
+  float rv[kCellsPer], dv[kCellsPer];
+#pragma unroll
+  for (int i = 0; i < kCellsPer; ++i) {
+    const int e = threadIdx.x + i * kSdThreads;
+    gp[i] = -1;
+    pe[i] = 0;
+    rv[i] = 0.f;
+    dv[i] = 0.f;
+    if (e < ne) {
+      const int a = e % ex, b = (e / ex) % ey, c = e / (ex * ey);
+      pe[i] = (a + 1) + kPX * ((b + 1) + kPY * (c + 1));
+      const int gi = sd_wrap(x0 - kSdOverlap + a, d.nx, d.px);
+      const int gj = sd_wrap(y0 - kSdOverlap + b, d.ny, d.py);
+      const int gk = sd_wrap(z0 - kSdOverlap + c, d.nz, d.pz);
+      if (gi >= 0 && gj >= 0 && gk >= 0) {
+        gp[i] = (int64_t)gi + (int64_t)d.nx * gj + plane * gk;
+        rv[i] = sd_ld32<RT>(r, gp[i]);
+        dv[i] = __ldg(&dinv[gp[i]]);
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kCellsPer; ++i)
+    if (gp[i] >= 0) buf[0][pe[i]] = __fmul_rn(om, __fmul_rn(dv[i], rv[i]));
+  __syncthreads();
+  int cur = 0;
+  for (int sw = 1; sw < kSdSweeps - 1; ++sw) {
+    const float* za = buf[cur];
+    float* zb = buf[cur ^ 1];
+#pragma unroll
+    for (int i = 0; i < kCellsPer; ++i) {
+      if (gp[i] < 0) continue;
+      const float sv = sd_row32<S>(coef, N, gp[i], za, pe[i]);
+      const float u = __fmul_rn(dv[i], __fsub_rn(rv[i], sv));
+      zb[pe[i]] = fmaf(om, u, za[pe[i]]);
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  const float* za = buf[cur];
+  const int nown = wx * wy * wz;
+  for (int e = threadIdx.x; e < nown; e += kSdThreads) {
+    const int a = e % wx, b = (e / wx) % wy, c = e / (wx * wy);
+    const int64_t p = (int64_t)(x0 + a) + (int64_t)d.nx * (y0 + b) + plane * (z0 + c);
+    const int q = (a + 1 + kSdOverlap) + kPX * ((b + 1 + kSdOverlap) + kPY * (c + 1 + kSdOverlap));
+    const float sv = sd_row32<S>(coef, N, p, za, q);
+    const float u = __fmul_rn(__ldg(&dinv[p]), __fsub_rn(sd_ld32<RT>(r, p), sv));
+    z[p] = fmaf(om, u, za[q]);
+  }
+}
+
 // ---- the double-float variant (the `df` precision): the same sweeps with the
 // double-float copies of the bands and of 1/a_pp, the sweep buffers in
 // double-float and every operation a double-float one on the FP32 pipe
@@ -403,6 +512,22 @@ cudaError_t launch_subdomain_local(const Dims& d, int S, const double* coef, con
     k_subdomain_local<7><<<(unsigned)nb, kSdThreads, 0, st>>>(d, coef, dinv, r, z, skip, nbx, nby);
   else
     k_subdomain_local<19><<<(unsigned)nb, kSdThreads, 0, st>>>(d, coef, dinv, r, z, skip, nbx, nby);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_subdomain_local32(const Dims& d, int S, const float* coef32, const float* dinv32, const void* r,
+                                     bool r_f32, float* z, const int* skip, cudaStream_t st) {
+  const int nbx = (d.nx + kSdBX - 1) / kSdBX, nby = (d.ny + kSdBY - 1) / kSdBY;
+  const int64_t nb = subdomain_boxes(d);
+  if (nb <= 0 || nb > 0x7fffffff) return cudaErrorInvalidValue;
+#define RK_SL32(SS, RT) \
+  k_subdomain_local32<SS, RT><<<(unsigned)nb, kSdThreads, 0, st>>>(d, coef32, dinv32, (const RT*)r, z, skip, nbx, nby)
+  if (S == 7) {
+    if (r_f32) RK_SL32(7, float); else RK_SL32(7, double);
+  } else {
+    if (r_f32) RK_SL32(19, float); else RK_SL32(19, double);
+  }
+#undef RK_SL32
   return cudaGetLastError();
 }
 

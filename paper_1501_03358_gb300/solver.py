@@ -167,13 +167,16 @@ class Problem:
     def apply(self, v, precond=True, stream=None, fp32=False, df=False, left=False, subdomain=None):
         """A M^{-1} v (precond), A v, M^{-1} A v (left), or with fp32 / df the
         FP32 / double-float operator (with the preconditioner) of the "mixed"
-        / "df" precisions. subdomain="minv": M^{-1} v, "left": M^{-1} A v with
-        the sub-domain preconditioner ("minv_df", "left_df": its double-float
-        variant with the double-float operator)."""
+        / "df" precisions (fp32 with left: d32 .* (A32 v)). subdomain="minv":
+        M^{-1} v, "left": M^{-1} A v with the sub-domain preconditioner
+        ("minv_df", "left_df": its double-float variant with the double-float
+        operator; "minv32", "left32": its FP32 variant with the FP32 operator)."""
         v = _f64_cuda(v, (self.n,))
         y = torch.empty_like(v)
         if subdomain is not None:
-            mode = {"minv": 5, "left": 6, "minv_df": 7, "left_df": 8}[subdomain]
+            mode = {"minv": 5, "left": 6, "minv_df": 7, "left_df": 8, "minv32": 9, "left32": 10}[subdomain]
+        elif fp32 and left:
+            mode = 11
         else:
             mode = 2 if fp32 else (3 if df else (4 if left else (1 if precond else 0)))
         N.check(self.lib.rk_apply(self._h, _dptr(v), _dptr(y), mode, _stream_ptr(stream)))

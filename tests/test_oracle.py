@@ -632,3 +632,34 @@ def test_schwarz_hybrid_sequence_sides_and_stop_test():
     assert modes == ["rGCROT", "rGCROT", "rBiCGStab", "rBiCGStab"]
     assert np.linalg.norm(A @ seq.U - seq.C) <= 1e-10 * np.linalg.norm(A, 2) * np.linalg.norm(seq.U)
     assert np.linalg.norm(seq.C.T @ seq.C - np.eye(seq.C.shape[1])) <= 1e-11
+
+
+@pytest.mark.parametrize("per", [(False, False, False), (True, False, True)])
+@pytest.mark.parametrize("S", [7, 19])
+def test_fp32_subdomain_preconditioner_near_its_fp64_form(S, per):
+    """The FP32 restatement of the sub-domain preconditioner (the mixed
+    precision's M^{-1}: bands, 1/a_pp, r and omega rounded to FP32 once,
+    every sweep in FP32 in the FP64 order) stays within FP32 rounding of the
+    FP64 preconditioner, which is pinned against its dense definition
+    (test_schwarz_preconditioner_matches_its_dense_definition); a dropped
+    band, a wrong sign or omega, or a skipped sweep moves it by O(1). The
+    same for the FP32 operator with and without left point Jacobi, and for
+    the left and right preconditioned products."""
+    g = Grid(37, 11, 9, per)
+    coef = random_operator(g, S, np.random.default_rng(S + 3))
+    op = Stencil(g, coef)
+    A = dense_matrix(g, coef)
+    r = np.random.default_rng(9).standard_normal(g.n)
+    z64 = op.schwarz(r)
+    z32 = op.schwarz_f32(r)
+    assert np.linalg.norm(z32 - z64) <= 1e-5 * np.linalg.norm(z64)
+    assert np.any(z32 != z64)
+    # the FP32 operator: elementwise FP32 rounding bound of A v
+    w32 = op.apply_f32(r)
+    assert np.all(np.abs(w32 - A @ r) <= (S + 2) * 2.0 ** -24 * (np.abs(A) @ np.abs(r)))
+    wl = op.apply_f32(r, left=True)
+    assert np.all(np.abs(wl - (A @ r) / coef[0]) <= (S + 4) * 2.0 ** -24 * (np.abs(A) @ np.abs(r)) / np.abs(coef[0]))
+    left = op.left_schwarz_f32(r)
+    assert np.linalg.norm(left - op.schwarz(op.apply(r))) <= 1e-5 * np.linalg.norm(left)
+    right = op.right_schwarz_f32(r)
+    assert np.linalg.norm(right - op.apply(op.schwarz(r))) <= 1e-5 * np.linalg.norm(right)
