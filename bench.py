@@ -479,6 +479,18 @@ def run_ours(args, ws, rank, local):
                                                "timed steps",
             "launches": d["launches"], "avg_launch_us": 1000.0 * d["ms"] / max(d["launches"], 1),
             "bytes_per_launch": d["bytes"] / max(d["launches"], 1)}
+    if d.get("fma", 0.0) > 0 and d["ms"] > 0 and dname not in ("subdomain_local", "subdomain_df"):
+        # the FP64 kernels of the class issue their fused multiply-adds on the
+        # FP64 pipe: report that bound beside the HBM one, and the tighter as
+        # the class's roofline
+        alu = d["fma"] / (d["ms"] * 1e-3) / 1e12
+        hbm = dict(roof)
+        if alu / fp64_peak > roof["frac"]:
+            roof.update({"bound": "alu", "achieved": alu, "peak": fp64_peak, "unit": "T FP64 fma/s",
+                         "frac": alu / fp64_peak, "peak_source": fp64_src, "fma_per_launch": d["fma"] / d["launches"]})
+            roof["hbm"] = {k: hbm[k] for k in ("achieved", "peak", "unit", "frac", "traffic")}
+        else:
+            roof["alu"] = {"achieved": alu, "peak": fp64_peak, "unit": "T FP64 fma/s", "frac": alu / fp64_peak}
     if dname in ("subdomain_local", "subdomain_df"):
         # bound by the arithmetic pipe: FP64 instructions against the measured
         # FP64 rate, or, for the double-float variant, FP32 instructions
@@ -521,8 +533,12 @@ def run_ours(args, ws, rank, local):
         "all_converged": all(i["status"] == 0 for i in tinfo),
         "roofline": roof,
         "kernel_classes": {kname: {"ms": round(v["ms"], 3), "launches": v["launches"],
-                                   "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
+                                   "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None,
+                                   "hbm_frac": (v["bytes"] / (v["ms"] * 1e-3) / 1e9 / hbm_peak) if v["ms"] > 0 else None,
+                                   "fp64_frac": (v.get("fma", 0.0) / (v["ms"] * 1e-3) / 1e12 / fp64_peak)
+                                   if v["ms"] > 0 and v.get("fma", 0.0) > 0 else None}
                            for kname, v in prof.items() if v["launches"]},
+        "fp64_fma_peak_tops": fp64_peak, "fp64_fma_peak_source": fp64_src,
         "kernel_classes_pass": {"ms": prof_ms, "note": "untimed replay with per-launch events"},
         "gpu_launches": launches,
         "gpu_launches_source": "library launches counted in the profiled replay of the same steps",

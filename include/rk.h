@@ -365,8 +365,11 @@ int rk_import_recycle(rk_problem* p, const void* buf, int64_t bytes, void* strea
 /*
  * Opt-in kernel timing of the solves of a problem: CUDA events on the solve's
  * stream around every launch, summed per kernel class ("spmv", "residual",
- * "dots", "update", "gemm_rows", "gram", "small", "bicg", "harmonic_ritz", "subdomain_local", "subdomain_df") with the class's
- * algorithmic HBM bytes (the library's byte model of each launch).
+ * "dots", "update", "gemm_rows", "gram", "small", "bicg", "harmonic_ritz", "subdomain_local", "subdomain_df",
+ * "subdomain32") with the class's algorithmic HBM bytes (the library's byte
+ * model of each launch) and the FP64 fused multiply-adds of its launches that
+ * run on the FP64 pipe (the FP64 basis kernels, the FP64 stencil and the
+ * rBiCGStab vector updates; the roofline of kernels bound by that pipe).
  * rk_profile_enable resets the counters; rk_profile_read copies up to cap
  * entries to out (host) and sets *count to the number of classes.
  */
@@ -375,6 +378,7 @@ typedef struct {
   int64_t launches;
   double ms;
   double bytes;
+  double fma;
 } rk_prof_entry;
 int rk_profile_enable(rk_problem* p, int32_t on);
 int rk_profile_read(rk_problem* p, rk_prof_entry* out, int32_t cap, int32_t* count);

@@ -206,9 +206,9 @@ __global__ void __launch_bounds__(kRedThreads) k_dfupdate(DFUpdateArgs a) {
 }
 
 // Delayed-reorthogonalisation inner products: [Q^T p, Q^T w, p^T p, p^T w,
-// w^T w]. Grid: x = contiguous row ranges of rpb rows (dots2_blocks(n)),
-// y = groups of kDotGroup columns of Q plus one slice for the three
-// scalars. A block streams its vectors (p, w and its kDotGroup columns)
+// w^T w]. Grid: x = groups of kDotGroup columns of Q plus one slice for the
+// three scalars, y = contiguous row ranges of rpb rows (dots2_blocks(n)).
+// A block streams its vectors (p, w and its kDotGroup columns)
 // through a kD2Stages-deep ring of shared-memory stages of kD2Rows rows,
 // filled by bulk asynchronous copies: a producer warp refills a stage as soon
 // as every consumer warp has released it ("empty" mbarrier) and the copies
@@ -254,11 +254,11 @@ __global__ void __launch_bounds__(kD2Threads) k_dfdots2(DFDots2Args a, int64_t r
   __shared__ int abort_at;  // first stage the producer did not issue (it gave up waiting)
   const int ncols = 2 * a.nq + 3;
   const int ngroups = (a.nq + kDotGroup - 1) / kDotGroup;
-  const bool scal = (int)blockIdx.y >= ngroups;
-  const int c0 = blockIdx.y * kDotGroup;
+  const bool scal = (int)blockIdx.x >= ngroups;
+  const int c0 = blockIdx.x * kDotGroup;
   const int nc = scal ? 0 : min(kDotGroup, a.nq - c0);
   const int nvec = 2 + nc;  // only this group's columns are copied
-  const int64_t begin = (int64_t)blockIdx.x * rpb;
+  const int64_t begin = (int64_t)blockIdx.y * rpb;
   const int64_t end = min(a.n, begin + rpb);
   const int nst = end > begin ? (int)((end - begin + kD2Rows - 1) / kD2Rows) : 0;
   const float2* src[kD2Vecs];
@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(kD2Threads) k_dfdots2(DFDots2Args a, int64_t r
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[slot]);  // this warp has read the stage
   }
-  double* prow = a.part + (int64_t)blockIdx.x * ncols;
+  double* prow = a.part + (int64_t)blockIdx.y * ncols;
   float2 vals[kDFCols];
   int cA, nA, cB = 0, nB = 0;  // this group's partial columns
   if (!scal) {
@@ -407,17 +407,17 @@ __global__ void __launch_bounds__(kD2Threads) k_dfdots2(DFDots2Args a, int64_t r
   __threadfence();
   named_sync(kRedThreads);
   if (threadIdx.x == 0) {
-    const unsigned t = atomicAdd(a.counter + blockIdx.y, 1u);
-    lastflag = (t == gridDim.x - 1) ? 1 : 0;
+    const unsigned t = atomicAdd(a.counter + blockIdx.x, 1u);
+    lastflag = (t == gridDim.y - 1) ? 1 : 0;
   }
   named_sync(kRedThreads);
   if (lastflag) {
     __threadfence();
-    if (threadIdx.x == 0) a.counter[blockIdx.y] = 0u;
+    if (threadIdx.x == 0) a.counter[blockIdx.x] = 0u;
     for (int t = wid; t < nA + nB; t += kWarps) {
       const int c = t < nA ? cA + t : cB + (t - nA);
       double sum = 0.0;
-      for (int bx = lane; bx < (int)gridDim.x; bx += 32) sum += __ldcg(&a.part[(int64_t)bx * ncols + c]);
+      for (int by = lane; by < (int)gridDim.y; by += 32) sum += __ldcg(&a.part[(int64_t)by * ncols + c]);
       sum = warp_sum(sum);
       if (lane == 0) a.out[c] = sum;
     }
@@ -824,7 +824,10 @@ cudaError_t launch_dfdots2(const DFDots2Args& a, cudaStream_t st) {
   const int xb = dots2_blocks(a.n);
   const int64_t per = (a.n + xb - 1) / xb;
   const int64_t rpb = (per + kD2Rows - 1) / kD2Rows * kD2Rows;  // even: 16-byte aligned stages
-  const dim3 grid(xb, (a.nq + kDotGroup - 1) / kDotGroup + 1);
+  // x = column groups, y = row ranges: the groups of one row range are
+  // adjacent in launch order, so p and w come from HBM once and from L2 for
+  // the other groups
+  const dim3 grid((a.nq + kDotGroup - 1) / kDotGroup + 1, xb);
   k_dfdots2<<<grid, kD2Threads, kD2Smem, st>>>(a, rpb);
   return cudaGetLastError();
 }

@@ -116,10 +116,11 @@ static const char* kProfNames[PC_COUNT] = {"spmv", "residual", "dots", "update",
 struct Profiler {
   bool on = false;
   std::vector<cudaEvent_t> pool;
-  struct Pending { cudaEvent_t a, b; int cls; double bytes; };
+  struct Pending { cudaEvent_t a, b; int cls; double bytes, fma; };
   std::vector<Pending> pending;
   double ms[PC_COUNT] = {0};
   double bytes[PC_COUNT] = {0};
+  double fma[PC_COUNT] = {0};
   int64_t launches[PC_COUNT] = {0};
   cudaEvent_t get() {
     if (pool.empty()) {
@@ -137,6 +138,7 @@ struct Profiler {
       if (cudaEventElapsedTime(&t, q.a, q.b) == cudaSuccess) {
         ms[q.cls] += t;
         bytes[q.cls] += q.bytes;
+        fma[q.cls] += q.fma;
         launches[q.cls] += 1;
       }
       pool.push_back(q.a);
@@ -146,7 +148,7 @@ struct Profiler {
   }
   void reset() {
     flush();
-    for (int i = 0; i < PC_COUNT; ++i) ms[i] = bytes[i] = 0.0, launches[i] = 0;
+    for (int i = 0; i < PC_COUNT; ++i) ms[i] = bytes[i] = fma[i] = 0.0, launches[i] = 0;
   }
   ~Profiler() {
     for (auto& q : pending) { cudaEventDestroy(q.a); cudaEventDestroy(q.b); }
@@ -159,8 +161,10 @@ struct ProfScope {
   cudaStream_t st;
   cudaEvent_t a = nullptr;
   int cls;
-  double bytes;
-  ProfScope(Profiler* p, int c, double b, cudaStream_t s) : pr(p), st(s), cls(c), bytes(b) {
+  double bytes, fma;
+  // b: algorithmic HBM bytes of the launch; f: its FP64 fused multiply-adds
+  // (kernels on the FP64 pipe; 0 elsewhere)
+  ProfScope(Profiler* p, int c, double b, cudaStream_t s, double f = 0.0) : pr(p), st(s), cls(c), bytes(b), fma(f) {
     if (pr->on) {
       a = pr->get();
       cudaEventRecord(a, st);
@@ -170,7 +174,7 @@ struct ProfScope {
     if (pr->on && a) {
       cudaEvent_t bev = pr->get();
       cudaEventRecord(bev, st);
-      pr->pending.push_back({a, bev, cls, bytes});
+      pr->pending.push_back({a, bev, cls, bytes, fma});
     }
   }
 };
@@ -386,7 +390,8 @@ int norm2_into(rk_problem* p, const double* v, int slot, cudaStream_t st) {
 // w is a basis column (w_basis) or an FP64 vector
 int bdots_launch(rk_problem* p, const void* Q, int nq, const void* w, bool w_basis, double* out, const int* skip,
                  cudaStream_t st, const double* extra0 = nullptr, int self = 0) {
-  ProfScope ps(&p->prof, PC_DOTS, 8.0 * (nq + (extra0 ? 2 : 0) + 1) * (double)p->n, st);
+  ProfScope ps(&p->prof, PC_DOTS, 8.0 * (nq + (extra0 ? 2 : 0) + 1) * (double)p->n, st,
+               p->bdf ? 0.0 : (double)(nq + (extra0 ? 1 : 0) + self) * (double)p->n);
   if (!p->bdf) {
     DotsArgs a{};
     a.n = p->n;
@@ -425,7 +430,8 @@ int bdots_launch(rk_problem* p, const void* Q, int nq, const void* w, bool w_bas
 int bupdate_launch(rk_problem* p, const void* Q, int nq, const double* c, const double* yin, double* yout,
                    double* nrm2, const int* skip, cudaStream_t st, const double* scale_ptr = nullptr,
                    int scale_rsqrt = 0) {
-  ProfScope ps(&p->prof, PC_UPDATE, 8.0 * (nq + 2) * (double)p->n, st);
+  ProfScope ps(&p->prof, PC_UPDATE, 8.0 * (nq + 2) * (double)p->n, st,
+               p->bdf ? 0.0 : (double)(nq + (nrm2 ? 1 : 0)) * (double)p->n);
   if (!p->bdf) {
     F64UpdateArgs a{};
     a.n = p->n;
@@ -465,7 +471,8 @@ int bupdate_launch(rk_problem* p, const void* Q, int nq, const double* c, const 
 // dots = [Q^T p, Q^T w, p^T p, p^T w, w^T w] of one Arnoldi step (basis columns)
 int bdots2_launch(rk_problem* p, const void* Q, int nq, const void* pv, const void* w, double* out, const int* skip,
                   cudaStream_t st) {
-  ProfScope ps(&p->prof, PC_DOTS, 8.0 * (nq + 2) * (double)p->n, st);
+  ProfScope ps(&p->prof, PC_DOTS, 8.0 * (nq + 2) * (double)p->n, st,
+               p->bdf ? 0.0 : (double)(2 * nq + 3) * (double)p->n);
   if (!p->bdf) {
     F64Dots2Args a{};
     a.n = p->n;
@@ -501,7 +508,8 @@ int bdots2_launch(rk_problem* p, const void* Q, int nq, const void* pv, const vo
 // v = (p - Q a) s0 (in place), p_next = (w - Q b) s1 - v s2 (in place of w)
 int bupdate2_launch(rk_problem* p, const void* Q, int nq, const double* ca, const double* cb, const double* scal,
                     void* pv, void* w, const int* mode, bool both, cudaStream_t st) {
-  ProfScope ps(&p->prof, PC_UPDATE, 8.0 * (nq + (both ? 4 : 2)) * (double)p->n, st);
+  ProfScope ps(&p->prof, PC_UPDATE, 8.0 * (nq + (both ? 4 : 2)) * (double)p->n, st,
+               p->bdf ? 0.0 : (double)(both ? 2 * nq + 1 : nq) * (double)p->n);
   if (!p->bdf) {
     F64Update2Args a{};
     a.n = p->n;
@@ -536,7 +544,9 @@ int bupdate2_launch(rk_problem* p, const void* Q, int nq, const double* ca, cons
 // columns (out_basis) or an FP64 vector)
 int bgemm_launch(rk_problem* p, const void* A, int na, const void* Bm, int nb, const double* bscale, const double* P,
                  int nc, void* out, bool out_basis, int accum, cudaStream_t st) {
-  ProfScope ps(&p->prof, PC_GEMM, 8.0 * (na + nb + nc * (accum ? 2 : 1) + (bscale ? 1 : 0)) * (double)p->n, st);
+  const bool tc64 = !p->bdf && p->sb.tcws != nullptr && out_basis && gemm_tc_f64_supported(na + nb, nc, accum);
+  ProfScope ps(&p->prof, PC_GEMM, 8.0 * (na + nb + nc * (accum ? 2 : 1) + (bscale ? 1 : 0)) * (double)p->n, st,
+               p->bdf ? 0.0 : (tc64 ? (double)(nb + 7 * nc) : (double)(na + nb) * nc) * (double)p->n);
   if (!p->bdf) {
     F64GemmArgs a{};
     a.n = p->n;
@@ -552,7 +562,7 @@ int bgemm_launch(rk_problem* p, const void* A, int na, const void* Bm, int nb, c
     a.out = (double*)out;
     a.ldo = p->ld;
     a.accum = accum;
-    if (p->sb.tcws != nullptr && out_basis && gemm_tc_f64_supported(na + nb, nc, accum)) {
+    if (tc64) {
       // FP64 operands on the tensor cores: exact digit products, one rounding
       DFGemmArgs t{};
       t.n = p->n;
@@ -598,7 +608,8 @@ int bgemm_launch(rk_problem* p, const void* A, int na, const void* Bm, int nb, c
 // out[q + l*(na+nb)] = [A B]_q^T diag(d) U_l (basis columns; d FP64, nullable)
 int bgram_launch(rk_problem* p, const void* A, int na, const void* Bm, int nb, const double* d, const void* U, int nu,
                  double* out, cudaStream_t st) {
-  ProfScope ps(&p->prof, PC_GRAM, 8.0 * (na + nb + nu + (d ? 1 : 0)) * (double)p->n, st);
+  ProfScope ps(&p->prof, PC_GRAM, 8.0 * (na + nb + nu + (d ? 1 : 0)) * (double)p->n, st,
+               p->bdf ? 0.0 : (double)((na + nb) * nu + (d ? nu : 0)) * (double)p->n);
   if (!p->bdf) {
     F64GramArgs g{};
     g.n = p->n;
@@ -675,7 +686,8 @@ int ensure_basis(rk_problem* p, bool want_df, cudaStream_t st) {
 int stencil_launch(rk_problem* p, int mode, const double* v, const double* b, double* y, double* part,
                    unsigned* counter, double* nrm2, const int* skip, cudaStream_t st) {
   const bool resid = mode == ST_RESID;
-  ProfScope ps(&p->prof, resid ? PC_RESID : PC_SPMV, 8.0 * (p->S + (resid ? 3 : 2)) * (double)p->n, st);
+  ProfScope ps(&p->prof, resid ? PC_RESID : PC_SPMV, 8.0 * (p->S + (resid ? 3 : 2)) * (double)p->n, st,
+               (double)(p->S + (mode == ST_PLAIN ? 0 : 1)) * (double)p->n);
   RK_CUDA(launch_stencil(p->d, p->S, mode, p->coef, p->dinv, v, b, y, part, counter, nrm2, skip, st));
   return RK_OK;
 }
@@ -1203,15 +1215,15 @@ int solve_bicg(rk_problem* p, const double* b, double* x, const rk_solve_params&
     bool running = true;
     while (running) {
       for (int it = 0; it < NB; ++it) {
-        { ProfScope ps_(&p->prof, PC_BICG, 32.0 * p->n, st); RK_CUDA(launch_bicg_p(v, p->bs, p->n, st)); }
+        { ProfScope ps_(&p->prof, PC_BICG, 32.0 * p->n, st, 2.0 * p->n); RK_CUDA(launch_bicg_p(v, p->bs, p->n, st)); }
         RK_TRY(opapply_launch(p, opk, v.p, false, v.v, false, &p->bs->stop, st, false, pc));
         RK_TRY(bdots_launch(p, p->Cblk(kc), kc, v.v, false, eta1, &p->bs->stop, st, v.rt));
         { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_bicg_alpha(p->bs, eta1, kc, st)); }
-        { ProfScope ps_(&p->prof, PC_BICG, 8.0 * (kc + (kc ? 5 : 3)) * (double)p->n, st); RK_CUDA(launch_bicg_s(v, p->bs, p->n, kc, p->Cblk(kc), p->bdf, p->ld, eta1, xi, p->part, p->counter, st)); }
+        { ProfScope ps_(&p->prof, PC_BICG, 8.0 * (kc + (kc ? 5 : 3)) * (double)p->n, st, (p->bdf ? 2.0 : kc + 2.0) * p->n); RK_CUDA(launch_bicg_s(v, p->bs, p->n, kc, p->Cblk(kc), p->bdf, p->ld, eta1, xi, p->part, p->counter, st)); }
         RK_TRY(opapply_launch(p, opk, v.s, false, v.t, false, &p->bs->stop, st, false, pc));
         if (kc) RK_TRY(bdots_launch(p, p->Cblk(kc), kc, v.t, false, eta2, &p->bs->stop, st));
-        { ProfScope ps_(&p->prof, PC_BICG, 8.0 * (kc + (kc ? 3 : 2)) * (double)p->n, st); RK_CUDA(launch_bicg_t(v, p->bs, p->n, kc, p->Cblk(kc), p->bdf, p->ld, eta2, p->part, p->counter, st)); }
-        { ProfScope ps_(&p->prof, PC_BICG, 56.0 * p->n, st); RK_CUDA(launch_bicg_r(v, p->bs, p->n, kc, eta1, eta2, xi, p->part, p->counter, st)); }
+        { ProfScope ps_(&p->prof, PC_BICG, 8.0 * (kc + (kc ? 3 : 2)) * (double)p->n, st, (p->bdf ? 2.0 : kc + 2.0) * p->n); RK_CUDA(launch_bicg_t(v, p->bs, p->n, kc, p->Cblk(kc), p->bdf, p->ld, eta2, p->part, p->counter, st)); }
+        { ProfScope ps_(&p->prof, PC_BICG, 56.0 * p->n, st, 5.0 * p->n); RK_CUDA(launch_bicg_r(v, p->bs, p->n, kc, eta1, eta2, xi, p->part, p->counter, st)); }
       }
       RK_CUDA(cudaMemcpyAsync(p->bs_h, p->bs, sizeof(BicgScalars), cudaMemcpyDeviceToHost, st));
       RK_CUDA(cudaStreamSynchronize(st));
@@ -1862,6 +1874,7 @@ int rk_profile_read(rk_problem* p, rk_prof_entry* out, int32_t cap, int32_t* cou
       out[nout].launches = p->prof.launches[c];
       out[nout].ms = p->prof.ms[c];
       out[nout].bytes = p->prof.bytes[c];
+      out[nout].fma = p->prof.fma[c];
     }
     ++nout;
   }

@@ -59,7 +59,7 @@ class rk_solve_info(ctypes.Structure):
 
 class rk_prof_entry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 16), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
-                ("bytes", ctypes.c_double)]
+                ("bytes", ctypes.c_double), ("fma", ctypes.c_double)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)

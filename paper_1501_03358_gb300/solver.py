@@ -218,11 +218,11 @@ class Problem:
         N.check(self.lib.rk_profile_enable(self._h, 1 if on else 0))
 
     def profile_read(self):
-        """{class: {"launches", "ms", "bytes"}} accumulated since profile(True)."""
+        """{class: {"launches", "ms", "bytes", "fma"}} accumulated since profile(True)."""
         arr = (N.rk_prof_entry * 16)()
         cnt = ctypes.c_int32()
         N.check(self.lib.rk_profile_read(self._h, arr, 16, ctypes.byref(cnt)))
-        return {arr[i].name.decode(): dict(launches=arr[i].launches, ms=arr[i].ms, bytes=arr[i].bytes)
+        return {arr[i].name.decode(): dict(launches=arr[i].launches, ms=arr[i].ms, bytes=arr[i].bytes, fma=arr[i].fma)
                 for i in range(min(cnt.value, 16))}
 
     def get_recycle(self, stream=None):

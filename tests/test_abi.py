@@ -54,7 +54,7 @@ def test_struct_layouts_match_header(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     structs = {"rk_grid": native.rk_grid, "rk_solve_params": native.rk_solve_params,
-               "rk_solve_info": native.rk_solve_info}
+               "rk_solve_info": native.rk_solve_info, "rk_prof_entry": native.rk_prof_entry}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "rk.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
