@@ -58,9 +58,9 @@ WORKLOADS = {
 # in double-float; or with those products in FP32
 DTYPES = {"fp64": "f64", "df": "f64+df64", "mixed": "f64+f32-operator"}
 MV_PER_SOLVE = {"channel128": {1: 1500.0}, "channel96": {1: 1100.0}, "convdiff32": {1: 60.0},
-                "porous192": {1: 400.0, 2: 400.0}}
+                "porous192": {1: 1311.0, 2: 911.0}}
 # the same with the sub-domain preconditioner (left rGCROT), measured likewise
-MV_PER_SOLVE_SD = {"channel128": {1: 505.0}, "porous192": {1: 360.0, 2: 309.0}}
+MV_PER_SOLVE_SD = {"channel128": {1: 513.0}, "porous192": {1: 360.0, 2: 309.0}}
 # the preconditioner each workload is defined with: the channel names the
 # paper's "Jacobi preconditioner" (the sub-domain one of Sec. 2.1), the
 # convection-diffusion case point Jacobi
@@ -546,6 +546,25 @@ def run_ours(args, ws, rank, local):
                 "d2h_bytes_per_step": 8 * cfg.n},
         "clocks": clocks,
     }
+    if args.variants and hybrid:
+        # the same timed steps with the other precisions (side by side with the
+        # headline; timed pass only, fresh problem each)
+        var = {}
+        for vp in [v for v in args.variants.split(",") if v and v != args.precision]:
+            vprob = Problem(ctx, cfg.grid, torch.from_numpy(cfg.coef))
+            vkw = dict(kw, precision=vp)
+            for t in warm:
+                x.zero_()
+                vprob.solve(rhs_dev[t], out=x, **dict(vkw, hybrid_switch=wkw["hybrid_switch"]))
+            vprob.reset()
+            torch.cuda.synchronize()
+            vms, vper = _timed_solves(vprob, [rhs_dev[t] for t in seq], vkw, stream, x)
+            var[vp] = {"value": len(seq) / (vms * 1e-3), "ms_per_step": vms / len(seq), "dtype": DTYPES[vp],
+                       "basis": BASIS[vp], "phases": _phase_summary(vper, hbm_peak),
+                       "relres_max": max(i["relres_true"] for _, i in vper),
+                       "all_converged": all(i["status"] == 0 for _, i in vper)}
+            vprob.close()
+        line["variants"] = var
     if xs_keep is not None:
         # the same sequence in FP64 (a second problem): per-step difference of
         # the solutions, relative to the FP64 one
@@ -884,6 +903,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="porous192", choices=sorted(WORKLOADS))
     ap.add_argument("--hybrid-switch", type=int, default=5, help="hybrid: rGCROT solves before the switch")
+    ap.add_argument("--variants", default="df",
+                    help="hybrid workloads: other precisions timed on the same steps, reported beside the headline")
     ap.add_argument("--vs-fp64", type=int, default=1,
                     help="precision df/mixed: also solve the timed steps with the fp64 path and report the "
                          "per-step difference of the solutions (1 = on)")
