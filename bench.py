@@ -550,7 +550,7 @@ def run_ours(args, ws, rank, local):
         # the same timed steps with the other precisions (side by side with the
         # headline; timed pass only, fresh problem each)
         var = {}
-        for vp in [v for v in args.variants.split(",") if v and v != args.precision]:
+        for vp in [v for v in args.variants.split(",") if v in DTYPES and v != args.precision]:
             vprob = Problem(ctx, cfg.grid, torch.from_numpy(cfg.coef))
             vkw = dict(kw, precision=vp)
             for t in warm:
@@ -672,7 +672,10 @@ def run_batch(args, ws, rank, local):
                    "hybrid_switch": 5, "precision": prec, "tol": 1e-8, "threads": args.threads or min(len(cfgs), 16),
                    "sequence_steps_timed": [W, W + K - 1], "l2": "inputs larger than L2",
                    "parallelism": "replicas" if ws > 1 else "single",
-                   "executor": "rk_solve_batch: host worker threads, one CUDA stream each"},
+                   "executor": "rk_solve_batch: rBiCGStab iterations of all problems in one launch per phase "
+                               "(persistent grid over a (problem, block) work list, NB = 8 iterations per "
+                               "captured graph, shapes from the autotuner); rGCROT solves on host worker "
+                               "threads, one CUDA stream each"},
         "solver_hbm_gbs": achieved, "solver_hbm_frac": achieved / hbm_peak,
         "latency_ms": dict(_percentiles(lat_ms), unit="one time step of all problems"),
         "matvecs_per_solve": statistics.mean(i["matvecs"] for i in infos),
@@ -686,6 +689,35 @@ def run_batch(args, ws, rank, local):
                 "d2h_bytes_per_step": 8 * ntot},
         "clocks": clocks,
     }
+    # the same steps on fresh problems with every solve on the thread-pool
+    # executor (one stream per problem, no batched phase): the comparison
+    os.environ["RK_BATCHED_BICG"] = "0"
+    try:
+        probs2 = [Problem(ctx, c.grid, torch.from_numpy(c.coef)) for c in cfgs]
+        for t in range(W):
+            for xx in xs:
+                xx.zero_()
+            solve_batch(probs2, rhs_dev[t], outs=xs, nthreads=args.threads, **kw)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        pinf = []
+        for t in range(W, W + K):
+            for xx in xs:
+                xx.zero_()
+            _, inf2 = solve_batch(probs2, rhs_dev[t], outs=xs, nthreads=args.threads, **kw)
+            pinf.extend(inf2)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        pms = f0.elapsed_time(f1)
+        line["thread_pool_executor"] = {
+            "solves_per_s": nsol / (pms * 1e-3), "ms_per_step": pms / K,
+            "same_products": [i["matvecs"] for i in pinf] == [i["matvecs"] for i in infos]}
+        for pp in probs2:
+            pp.close()
+    finally:
+        os.environ.pop("RK_BATCHED_BICG", None)
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         c0 = cfgs[0]

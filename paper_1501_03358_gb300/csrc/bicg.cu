@@ -8,6 +8,7 @@
 #include <cmath>
 #include <type_traits>
 #include "rk_bicg.h"
+#include "rk_batch.h"
 #include "rk_device.cuh"
 #include "rk_df.cuh"
 
@@ -18,7 +19,7 @@ namespace {
 __device__ __forceinline__ bool stopped(const BicgScalars* s) { return s->stop != 0; }
 
 // p = r (first iteration) or p = r + beta (p - omega v)
-__global__ void __launch_bounds__(kRedThreads) k_bicg_p(BicgVecs v, BicgScalars* s, int64_t n) {
+__device__ __forceinline__ void bicg_p_body(BicgVecs v, BicgScalars* s, int64_t n, int bid, int nblk) {
   if (stopped(s)) return;
   if (s->matvecs >= s->maxmv) {  // the iteration cap (i <= max_itn)
     __syncthreads();
@@ -30,11 +31,14 @@ __global__ void __launch_bounds__(kRedThreads) k_bicg_p(BicgVecs v, BicgScalars*
   }
   const bool first = s->it == 0;
   const double beta = s->beta, omega = s->omega;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+  const int64_t stride = (int64_t)nblk * blockDim.x;
+  for (int64_t i = (int64_t)bid * blockDim.x + threadIdx.x; i < n; i += stride) {
     const double ri = v.r[i];
     v.p[i] = first ? ri : fma(beta, v.p[i] - omega * v.v[i], ri);
   }
+}
+__global__ void __launch_bounds__(kRedThreads) k_bicg_p(BicgVecs v, BicgScalars* s, int64_t n) {
+  bicg_p_body(v, s, n, blockIdx.x, gridDim.x);
 }
 
 // alpha = rho / (r~^T v) after the C projection of v; r~ is orthogonal to C, so r~^T v
@@ -55,9 +59,9 @@ __global__ void k_bicg_alpha(BicgScalars* s, const double* dots, int kc) {
 // half step is recorded (xi += alpha eta1 here, x~ += alpha p
 // by k_bicg_half).
 template <typename CT>
-__global__ void __launch_bounds__(kRedThreads) k_bicg_s(BicgVecs v, BicgScalars* s, int64_t n, int kc,
+__device__ __forceinline__ void bicg_s_body(BicgVecs v, BicgScalars* s, int64_t n, int kc,
                                                         const CT* C, int64_t ld, const double* eta1,
-                                                        double* xi, double* part, unsigned* counter) {
+                                                        double* xi, double* part, unsigned* counter, int bid, int nblk) {
   if (stopped(s)) return;
   __shared__ double red[32];
   __shared__ int lastflag;
@@ -70,9 +74,9 @@ __global__ void __launch_bounds__(kRedThreads) k_bicg_s(BicgVecs v, BicgScalars*
   }
   __syncthreads();
   const double alpha = s->alpha;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t stride = (int64_t)nblk * blockDim.x;
   double acc = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+  for (int64_t i = (int64_t)bid * blockDim.x + threadIdx.x; i < n; i += stride) {
     double vi = v.v[i];
     if (kc) {
       if constexpr (std::is_same<CT, float2>::value) {
@@ -92,9 +96,9 @@ __global__ void __launch_bounds__(kRedThreads) k_bicg_s(BicgVecs v, BicgScalars*
     acc = fma(si, si, acc);
   }
   const double b = block_sum(acc, red);
-  if (threadIdx.x == 0) part[blockIdx.x] = b;
-  if (arrive_last(counter, &lastflag)) {
-    reduce_partials(part, gridDim.x, 1, &s->s2);
+  if (threadIdx.x == 0) part[bid] = b;
+  if (arrive_last_n(counter, &lastflag, nblk)) {
+    reduce_partials(part, nblk, 1, &s->s2);
     __syncthreads();
     if (threadIdx.x == 0) {
       if (sqrt(s->s2) <= s->tolabs) {
@@ -107,6 +111,12 @@ __global__ void __launch_bounds__(kRedThreads) k_bicg_s(BicgVecs v, BicgScalars*
       }
     }
   }
+}
+template <typename CT>
+__global__ void __launch_bounds__(kRedThreads) k_bicg_s(BicgVecs v, BicgScalars* s, int64_t n, int kc,
+                                                        const CT* C, int64_t ld, const double* eta1,
+                                                        double* xi, double* part, unsigned* counter) {
+  bicg_s_body(v, s, n, kc, C, ld, eta1, xi, part, counter, blockIdx.x, gridDim.x);
 }
 
 // on convergence at the half step: x~ += alpha p
@@ -123,9 +133,9 @@ __global__ void __launch_bounds__(kRedThreads) k_bicg_half(BicgVecs v, BicgScala
 
 // t <- t - C eta2; omega = t^T s / t^T t (last block).
 template <typename CT>
-__global__ void __launch_bounds__(kRedThreads) k_bicg_t(BicgVecs v, BicgScalars* s, int64_t n, int kc,
+__device__ __forceinline__ void bicg_t_body(BicgVecs v, BicgScalars* s, int64_t n, int kc,
                                                         const CT* C, int64_t ld, const double* eta2,
-                                                        double* part, unsigned* counter) {
+                                                        double* part, unsigned* counter, int bid, int nblk) {
   if (stopped(s)) return;
   __shared__ double red[32];
   __shared__ int lastflag;
@@ -137,9 +147,9 @@ __global__ void __launch_bounds__(kRedThreads) k_bicg_t(BicgVecs v, BicgScalars*
     sedf[q] = make_float2(e.hi, e.lo);
   }
   __syncthreads();
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t stride = (int64_t)nblk * blockDim.x;
   double ts = 0.0, tt = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+  for (int64_t i = (int64_t)bid * blockDim.x + threadIdx.x; i < n; i += stride) {
     double ti = v.t[i];
     if (kc) {
       if constexpr (std::is_same<CT, float2>::value) {
@@ -161,11 +171,11 @@ __global__ void __launch_bounds__(kRedThreads) k_bicg_t(BicgVecs v, BicgScalars*
   __syncthreads();
   const double b1 = block_sum(tt, red);
   if (threadIdx.x == 0) {
-    part[2 * blockIdx.x] = b0;
-    part[2 * blockIdx.x + 1] = b1;
+    part[2 * bid] = b0;
+    part[2 * bid + 1] = b1;
   }
-  if (arrive_last(counter, &lastflag)) {
-    reduce_partials(part, gridDim.x, 2, s->tmp);
+  if (arrive_last_n(counter, &lastflag, nblk)) {
+    reduce_partials(part, nblk, 2, s->tmp);
     __syncthreads();
     if (threadIdx.x == 0) {
       s->matvecs += 1;
@@ -179,20 +189,26 @@ __global__ void __launch_bounds__(kRedThreads) k_bicg_t(BicgVecs v, BicgScalars*
     }
   }
 }
+template <typename CT>
+__global__ void __launch_bounds__(kRedThreads) k_bicg_t(BicgVecs v, BicgScalars* s, int64_t n, int kc,
+                                                        const CT* C, int64_t ld, const double* eta2,
+                                                        double* part, unsigned* counter) {
+  bicg_t_body(v, s, n, kc, C, ld, eta2, part, counter, blockIdx.x, gridDim.x);
+}
 
 // xi += alpha eta1 + omega eta2; x~ += alpha p + omega s;
 // r = s - omega t; rho = r~^T r, beta = (rho/rho_old)(alpha/omega); the
 // convergence and breakdown tests of the next iteration.
-__global__ void __launch_bounds__(kRedThreads) k_bicg_r(BicgVecs v, BicgScalars* s, int64_t n, int kc,
+__device__ __forceinline__ void bicg_r_body(BicgVecs v, BicgScalars* s, int64_t n, int kc,
                                                         const double* eta1, const double* eta2, double* xi,
-                                                        double* part, unsigned* counter) {
+                                                        double* part, unsigned* counter, int bid, int nblk) {
   if (stopped(s)) return;
   __shared__ double red[32];
   __shared__ int lastflag;
   const double alpha = s->alpha, omega = s->omega;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t stride = (int64_t)nblk * blockDim.x;
   double rr = 0.0, rtr = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+  for (int64_t i = (int64_t)bid * blockDim.x + threadIdx.x; i < n; i += stride) {
     const double si = v.s[i];
     v.xt[i] = fma(omega, si, fma(alpha, v.p[i], v.xt[i]));
     const double ri = fma(-omega, v.t[i], si);
@@ -204,11 +220,11 @@ __global__ void __launch_bounds__(kRedThreads) k_bicg_r(BicgVecs v, BicgScalars*
   __syncthreads();
   const double b1 = block_sum(rr, red);
   if (threadIdx.x == 0) {
-    part[2 * blockIdx.x] = b0;
-    part[2 * blockIdx.x + 1] = b1;
+    part[2 * bid] = b0;
+    part[2 * bid + 1] = b1;
   }
-  if (arrive_last(counter, &lastflag)) {
-    reduce_partials(part, gridDim.x, 2, s->tmp);
+  if (arrive_last_n(counter, &lastflag, nblk)) {
+    reduce_partials(part, nblk, 2, s->tmp);
     __syncthreads();
     if (threadIdx.x == 0) {
       for (int q = 0; q < kc; ++q) xi[q] = fma(omega, eta2[q], fma(alpha, eta1[q], xi[q]));
@@ -228,6 +244,11 @@ __global__ void __launch_bounds__(kRedThreads) k_bicg_r(BicgVecs v, BicgScalars*
       }
     }
   }
+}
+__global__ void __launch_bounds__(kRedThreads) k_bicg_r(BicgVecs v, BicgScalars* s, int64_t n, int kc,
+                                                        const double* eta1, const double* eta2, double* xi,
+                                                        double* part, unsigned* counter) {
+  bicg_r_body(v, s, n, kc, eta1, eta2, xi, part, counter, blockIdx.x, gridDim.x);
 }
 
 // Start of a pass of Algorithm 4 (after the initial C projection): r~ = r_0, rho = r~^T r_0.
@@ -252,7 +273,90 @@ __global__ void k_bicg_foldcoef(const double* xi, int kc, double* coefv) {
   for (int q = threadIdx.x; q <= kc; q += blockDim.x) coefv[q] = q < kc ? -xi[q] : 1.0;
 }
 
+// ---- batched launches: item (i, b) runs block b of problem i's kernel
+__global__ void __launch_bounds__(kRedThreads) k_batch_bicg_p(const BatchProb* __restrict__ P,
+                                                              const int2* __restrict__ items, int nitems) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int2 w = items[it];
+    const BatchProb& q = P[w.x];
+    bicg_p_body(q.v, q.bs, q.d.n, w.y, q.nblk);
+    __syncthreads();
+  }
+}
+
+__global__ void k_batch_bicg_alpha(const BatchProb* __restrict__ P, int nprob) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nprob) return;
+  BicgScalars* s = P[i].bs;
+  if (stopped(s)) return;
+  // the single-problem k_bicg_alpha, for problem i
+  s->matvecs += 1;
+  const double rtv = P[i].eta1[P[i].kc];
+  if (rtv == 0.0 || !isfinite(rtv)) {
+    s->flag = 2;
+    s->stop = 1;
+    return;
+  }
+  s->alpha = s->rho / rtv;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_batch_bicg_s(const BatchProb* __restrict__ P,
+                                                              const int2* __restrict__ items, int nitems) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int2 w = items[it];
+    const BatchProb& q = P[w.x];
+    bicg_s_body<double>(q.v, q.bs, q.d.n, q.kc, q.C, q.ld, q.eta1, q.xi, q.part, q.counter, w.y, q.nblk);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_batch_bicg_t(const BatchProb* __restrict__ P,
+                                                              const int2* __restrict__ items, int nitems) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int2 w = items[it];
+    const BatchProb& q = P[w.x];
+    bicg_t_body<double>(q.v, q.bs, q.d.n, q.kc, q.C, q.ld, q.eta2, q.part, q.counter, w.y, q.nblk);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_batch_bicg_r(const BatchProb* __restrict__ P,
+                                                              const int2* __restrict__ items, int nitems) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int2 w = items[it];
+    const BatchProb& q = P[w.x];
+    bicg_r_body(q.v, q.bs, q.d.n, q.kc, q.eta1, q.eta2, q.xi, q.part, q.counter, w.y, q.nblk);
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_batch_bicg_p(const BatchProb* P, const int2* items, int nitems, int grid, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  k_batch_bicg_p<<<grid < nitems ? grid : nitems, kRedThreads, 0, st>>>(P, items, nitems);
+  return cudaGetLastError();
+}
+cudaError_t launch_batch_bicg_alpha(const BatchProb* P, int nprob, cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  k_batch_bicg_alpha<<<(nprob + 127) / 128, 128, 0, st>>>(P, nprob);
+  return cudaGetLastError();
+}
+cudaError_t launch_batch_bicg_s(const BatchProb* P, const int2* items, int nitems, int grid, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  k_batch_bicg_s<<<grid < nitems ? grid : nitems, kRedThreads, 0, st>>>(P, items, nitems);
+  return cudaGetLastError();
+}
+cudaError_t launch_batch_bicg_t(const BatchProb* P, const int2* items, int nitems, int grid, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  k_batch_bicg_t<<<grid < nitems ? grid : nitems, kRedThreads, 0, st>>>(P, items, nitems);
+  return cudaGetLastError();
+}
+cudaError_t launch_batch_bicg_r(const BatchProb* P, const int2* items, int nitems, int grid, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  k_batch_bicg_r<<<grid < nitems ? grid : nitems, kRedThreads, 0, st>>>(P, items, nitems);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_bicg_foldcoef(const double* xi, int kc, double* coefv, cudaStream_t st) {
   k_bicg_foldcoef<<<1, 256, 0, st>>>(xi, kc, coefv);

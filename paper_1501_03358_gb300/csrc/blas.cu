@@ -5,6 +5,7 @@
 // double-float basis live in dfblas.cu.
 #include "rk_internal.h"
 #include "rk_device.cuh"
+#include "rk_batch.h"
 
 namespace rk {
 
@@ -12,13 +13,13 @@ namespace {
 
 constexpr int kDotCols = 16;
 
-__global__ void __launch_bounds__(kRedThreads) k_dots(DotsArgs a) {
+__device__ __forceinline__ void dots_body(const DotsArgs& a, int bid, int nblk) {
   if (a.skip_flag != nullptr && *a.skip_flag != 0) return;
   __shared__ double red[kRedThreads / 32][kDotCols];
   __shared__ int lastflag;
   const int ncols = a.nq + a.ne + a.self;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t stride = (int64_t)nblk * blockDim.x;
   for (int c0 = 0; c0 < ncols; c0 += kDotCols) {
     const double* ptr[kDotCols];
 #pragma unroll
@@ -35,7 +36,7 @@ __global__ void __launch_bounds__(kRedThreads) k_dots(DotsArgs a) {
     double acc[kDotCols];
 #pragma unroll
     for (int q = 0; q < kDotCols; ++q) acc[q] = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    for (int64_t i = (int64_t)bid * blockDim.x + threadIdx.x; i < a.n; i += stride) {
       const double wi = __ldg(&a.w[i]);
 #pragma unroll
       for (int q = 0; q < kDotCols; ++q)
@@ -50,11 +51,39 @@ __global__ void __launch_bounds__(kRedThreads) k_dots(DotsArgs a) {
     if (threadIdx.x < nc) {
       double s = 0.0;
       for (int w = 0; w < kRedThreads / 32; ++w) s += red[w][threadIdx.x];
-      a.part[(int64_t)blockIdx.x * ncols + c0 + threadIdx.x] = s;
+      a.part[(int64_t)bid * ncols + c0 + threadIdx.x] = s;
     }
     __syncthreads();
   }
-  if (arrive_last(a.counter, &lastflag)) reduce_partials(a.part, gridDim.x, ncols, a.out);
+  if (arrive_last_n(a.counter, &lastflag, nblk)) reduce_partials(a.part, nblk, ncols, a.out);
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_dots(DotsArgs a) { dots_body(a, blockIdx.x, gridDim.x); }
+
+// batched projections of rBiCGStab: which = 0 [C^T v, r~^T v] -> eta1 (the
+// single-problem call with the extra vector r~), 1: C^T t -> eta2 (only
+// problems with kc > 0 are on the work list); the problem's stop flag skips it
+__global__ void __launch_bounds__(kRedThreads) k_batch_dots(const BatchProb* __restrict__ P,
+                                                            const int2* __restrict__ items, int nitems, int which) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int2 w = items[it];
+    const BatchProb& q = P[w.x];
+    if (q.bs->stop != 0) continue;
+    DotsArgs a{};
+    a.n = q.d.n;
+    a.nq = q.kc;
+    a.Q = q.C;
+    a.ld = q.ld;
+    a.extra[0] = which == 0 ? q.v.rt : nullptr;
+    a.ne = which == 0 ? 1 : 0;
+    a.self = 0;
+    a.w = which == 0 ? q.v.v : q.v.t;
+    a.part = q.part;
+    a.counter = q.counter;
+    a.out = which == 0 ? q.eta1 : q.eta2;
+    dots_body(a, w.y, q.nblk);
+    __syncthreads();
+  }
 }
 
 __global__ void k_copy(int64_t n, const double* __restrict__ src, double* __restrict__ dst) {
@@ -101,6 +130,13 @@ int gram_blocks(int64_t n) {
 
 cudaError_t launch_dots(const DotsArgs& a, cudaStream_t st) {
   k_dots<<<red_blocks(a.n), kRedThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_dots(const BatchProb* P, const int2* items, int nitems, int which, int grid,
+                              cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  k_batch_dots<<<grid < nitems ? grid : nitems, kRedThreads, 0, st>>>(P, items, nitems, which);
   return cudaGetLastError();
 }
 

@@ -45,6 +45,24 @@ __device__ __forceinline__ bool arrive_last(unsigned* counter, int* flag_smem) {
   return last;
 }
 
+// The same for a reduction over nblocks blocks that need not be the whole
+// grid (the batched launches, where one launch serves many problems).
+__device__ __forceinline__ bool arrive_last_n(unsigned* counter, int* flag_smem, int nblocks) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = atomicAdd(counter, 1u);
+    *flag_smem = (t == (unsigned)nblocks - 1u) ? 1 : 0;
+  }
+  __syncthreads();
+  bool last = *flag_smem != 0;
+  if (last) {
+    __threadfence();
+    if (threadIdx.x == 0) *counter = 0u;
+  }
+  return last;
+}
+
 // Reduce part[b * ncols + c] over b < nblocks for every column c, one warp
 // per column, lane-strided then a fixed shuffle tree. Results to out[c].
 __device__ __forceinline__ void reduce_partials(const double* part, int nblocks, int ncols, double* out) {

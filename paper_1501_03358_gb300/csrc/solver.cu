@@ -27,6 +27,12 @@
 #include "rk_internal.h"
 #include "rk_solver.h"
 #include "rk_bicg.h"
+#include "rk_batch.h"
+#include <chrono>
+#include <cstdlib>
+#include <fstream>
+#include <mutex>
+#include <sstream>
 
 using namespace rk;
 
@@ -1158,17 +1164,40 @@ int solve_gcr(rk_problem* p, const double* b, double* x, const rk_solve_params& 
 }
 
 // ---------------------------------------------------------------- rBiCGStab
-int solve_bicg(rk_problem* p, const double* b, double* x, const rk_solve_params& prm, rk_solve_info& info,
-               bool recycle, cudaStream_t st) {
-  const int maxmv = prm.max_matvec > 0 ? prm.max_matvec : 2000;
-  const int opk = prm.precision;
+// One rBiCGStab solve (Algorithm 4) as a sequence of stages, so that the
+// batched executor can run the iterations of many solves in shared launches
+// while every other stage stays the single-problem code:
+//   bicg_setup -> { bicg_pass_start -> iterations -> bicg_pass_end }* -> bicg_finish
+struct BicgRun {
+  rk_problem* p = nullptr;
+  const double* b = nullptr;
+  double* x = nullptr;
+  rk_solve_params prm{};
+  rk_solve_info* info = nullptr;
+  int maxmv = 2000, opk = RK_FP64, pc = RK_PC_JACOBI, kc = 0;
+  BicgVecs v{};
+  double *eta1 = nullptr, *eta2 = nullptr, *xi = nullptr, *coefv = nullptr;
+  double bnorm = 0.0, tolabs = 0.0, words = 0.0, rel = 0.0, upd = 0.0;
+  int matvecs = 0, its = 0, restarts = 0, status = RK_E_NOT_CONVERGED;
+  bool done = false;
+};
+
+int bicg_setup(BicgRun& R, rk_problem* p, const double* b, double* x, const rk_solve_params& prm,
+               rk_solve_info& info, bool recycle, cudaStream_t st) {
+  R.p = p;
+  R.b = b;
+  R.x = x;
+  R.prm = prm;
+  R.info = &info;
+  R.maxmv = prm.max_matvec > 0 ? prm.max_matvec : 2000;
+  R.opk = prm.precision;
   RK_TRY(ensure_capacity(p, p->kdim, std::max(p->mcap, 1), st));
-  RK_TRY(ensure_operator(p, opk, st));
+  RK_TRY(ensure_operator(p, R.opk, st));
   if (!p->bicg) RK_TRY(alloc_into(p->ctx, &p->bicg, (size_t)7 * p->ld));
   if (recycle) RK_TRY(ensure_side(p, false, prm.precond, st));  // Sec. 2.1: BiCGStab is right-preconditioned
-  const int pc = prm.precond;
-  const int kc = recycle ? p->kdim : 0;
-  BicgVecs v{};
+  R.pc = prm.precond;
+  R.kc = recycle ? p->kdim : 0;
+  BicgVecs& v = R.v;
   v.r = p->bicg;
   v.rt = p->bicg + p->ld;
   v.p = p->bicg + 2 * p->ld;
@@ -1176,107 +1205,142 @@ int solve_bicg(rk_problem* p, const double* b, double* x, const rk_solve_params&
   v.s = p->bicg + 4 * p->ld;
   v.t = p->bicg + 5 * p->ld;
   v.xt = p->bicg + 6 * p->ld;
-  double* eta1 = p->eta;
-  double* eta2 = p->eta + (p->kmax + 4);
-  double* xi = p->eta + 2 * (p->kmax + 4);
-  double* coefv = p->eta + 3 * (p->kmax + 4);
+  R.eta1 = p->eta;
+  R.eta2 = p->eta + (p->kmax + 4);
+  R.xi = p->eta + 2 * (p->kmax + 4);
+  R.coefv = p->eta + 3 * (p->kmax + 4);
   RK_TRY(norm2_into(p, b, 0, st));
   { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_set_tol(p->st, prm.tol, st)); }
   RK_TRY(sync_state(p, st));
-  const double bnorm = p->st_h->bnorm;
-  if (!std::isfinite(bnorm)) return fail(RK_E_INVALID, "b contains NaN or Inf");
-  if (bnorm == 0.0) {
+  R.bnorm = p->st_h->bnorm;
+  if (!std::isfinite(R.bnorm)) return fail(RK_E_INVALID, "b contains NaN or Inf");
+  if (R.bnorm == 0.0) {
     RK_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * p->n, st));
     RK_CUDA(cudaStreamSynchronize(st));
     info.status = RK_OK;
     info.recycle_dim = p->kdim;
+    R.status = RK_OK;
+    R.done = true;
     return RK_OK;
   }
-  const double tolabs = prm.tol * bnorm;
-  const double S = p->S;
-  double words = 0.0;
-  int matvecs = 0, its = 0, restarts = 0;
-  double rel = 0.0, upd = 0.0;
-  int status = RK_E_NOT_CONVERGED;
+  R.tolabs = prm.tol * R.bnorm;
+  return RK_OK;
+}
+
+// r = b - A x; its projection: eta1 = C^T r, r -= C eta1, xi = -eta1; r~ = r,
+// x~ = 0, the scalars of a new pass
+int bicg_pass_start(BicgRun& R, cudaStream_t st) {
+  rk_problem* p = R.p;
+  const BicgVecs& v = R.v;
+  const int kc = R.kc;
+  RK_TRY(stencil_launch(p, ST_RESID, R.x, R.b, v.r, p->part, p->counter, &p->st->rho2, nullptr, st));
+  if (kc) {
+    RK_TRY(bdots_launch(p, p->Cblk(kc), kc, v.r, false, R.xi, nullptr, st));
+    RK_TRY(bupdate_launch(p, p->Cblk(kc), kc, R.xi, v.r, v.r, &p->st->rho2, nullptr, st));
+    // xi = -eta1 enters x at once (x <- x + U eta1); xi restarts from 0
+    RK_TRY(bgemm_launch(p, p->Ublk(kc), kc, nullptr, 0, nullptr, R.xi, 1, R.x, false, 1, st));
+    RK_CUDA(cudaMemsetAsync(R.xi, 0, sizeof(double) * kc, st));
+  }
+  { ProfScope ps_(&p->prof, PC_BICG, 24.0 * p->n, st); RK_CUDA(launch_copy(p->n, v.r, v.rt, st)); RK_CUDA(launch_fill(p->n, 0.0, v.xt, st)); }
+  { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_bicg_init(p->bs, &p->st->rho2, R.tolabs, R.maxmv - R.matvecs, st)); }
+  R.words += (p->S + 3) + 2.0 * kc + 4;
+  return RK_OK;
+}
+
+// one iteration of Algorithm 4 on one problem (the kernels skip themselves
+// once the scalars say the pass has stopped)
+int bicg_iteration(BicgRun& R, cudaStream_t st) {
+  rk_problem* p = R.p;
+  const BicgVecs& v = R.v;
+  const int kc = R.kc;
+  { ProfScope ps_(&p->prof, PC_BICG, 32.0 * p->n, st, 2.0 * p->n); RK_CUDA(launch_bicg_p(v, p->bs, p->n, st)); }
+  RK_TRY(opapply_launch(p, R.opk, v.p, false, v.v, false, &p->bs->stop, st, false, R.pc));
+  RK_TRY(bdots_launch(p, p->Cblk(kc), kc, v.v, false, R.eta1, &p->bs->stop, st, v.rt));
+  { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_bicg_alpha(p->bs, R.eta1, kc, st)); }
+  { ProfScope ps_(&p->prof, PC_BICG, 8.0 * (kc + (kc ? 5 : 3)) * (double)p->n, st, (p->bdf ? 2.0 : kc + 2.0) * p->n); RK_CUDA(launch_bicg_s(v, p->bs, p->n, kc, p->Cblk(kc), p->bdf, p->ld, R.eta1, R.xi, p->part, p->counter, st)); }
+  RK_TRY(opapply_launch(p, R.opk, v.s, false, v.t, false, &p->bs->stop, st, false, R.pc));
+  if (kc) RK_TRY(bdots_launch(p, p->Cblk(kc), kc, v.t, false, R.eta2, &p->bs->stop, st));
+  { ProfScope ps_(&p->prof, PC_BICG, 8.0 * (kc + (kc ? 3 : 2)) * (double)p->n, st, (p->bdf ? 2.0 : kc + 2.0) * p->n); RK_CUDA(launch_bicg_t(v, p->bs, p->n, kc, p->Cblk(kc), p->bdf, p->ld, R.eta2, p->part, p->counter, st)); }
+  { ProfScope ps_(&p->prof, PC_BICG, 56.0 * p->n, st, 5.0 * p->n); RK_CUDA(launch_bicg_r(v, p->bs, p->n, kc, R.eta1, R.eta2, R.xi, p->part, p->counter, st)); }
+  return RK_OK;
+}
+
+// after the pass stopped: the half step, the fold x <- x + M^{-1} x~ - U xi,
+// the true residual (residual replacement, R12), and the decision
+int bicg_pass_end(BicgRun& R, cudaStream_t st) {
+  rk_problem* p = R.p;
+  const BicgVecs& v = R.v;
+  const int kc = R.kc;
+  if (p->bs_h->half == 1) { ProfScope ps_(&p->prof, PC_BICG, 24.0 * p->n, st); RK_CUDA(launch_bicg_half(v, p->bs, p->n, st)); }
+  R.matvecs += p->bs_h->matvecs;
+  R.its += p->bs_h->it;
+  R.upd = p->bs_h->upd;
+  R.words += (double)p->bs_h->it * (2 * p->S + 4.0 * kc + 22);
+  const int flag = p->bs_h->flag;
+  if (R.pc == RK_PC_SUBDOMAIN) {
+    RK_TRY(subdomain_launch(p, v.xt, p->sdw + p->ld, false, nullptr, nullptr, st));
+    RK_CUDA(launch_add(p->n, p->sdw + p->ld, R.x, st));
+  } else {
+    RK_CUDA(launch_axpy_scaled(p->n, p->dinv, v.xt, R.x, st));
+  }
+  if (kc) {
+    { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_bicg_foldcoef(R.xi, kc, R.coefv, st)); }
+    RK_TRY(bgemm_launch(p, p->Ublk(kc), kc, nullptr, 0, nullptr, R.coefv, 1, R.x, false, 1, st));
+  }
+  R.words += kc + 4;
+  // true residual b - A x; above tol, Algorithm 4 restarts from the current x (residual replacement)
+  RK_TRY(stencil_launch(p, ST_RESID, R.x, R.b, v.r, p->part, p->counter, &p->st->rho2, nullptr, st));
+  RK_TRY(sync_state(p, st));
+  R.rel = std::sqrt(p->st_h->rho2) / R.bnorm;
+  if (R.rel <= R.prm.tol) {
+    R.status = RK_OK;
+    R.done = true;
+  } else if (R.matvecs >= R.maxmv || flag == 3) {
+    R.status = RK_E_NOT_CONVERGED;
+    R.done = true;
+  } else if (R.restarts >= 3) {
+    R.status = flag == 2 ? RK_E_BREAKDOWN : RK_E_NOT_CONVERGED;
+    R.done = true;
+  } else {
+    R.restarts += 1;
+  }
+  return RK_OK;
+}
+
+int bicg_finish(BicgRun& R) {
+  rk_solve_info& info = *R.info;
+  if (R.bnorm == 0.0) return RK_OK;
+  info.matvecs = R.matvecs;
+  info.cycles_or_iters = R.its;
+  info.restarts = R.restarts;
+  info.relres_true = R.rel;
+  info.relres_est = R.upd / R.bnorm;
+  info.recycle_dim = R.p->kdim;
+  info.model_bytes = 8.0 * R.words * (double)R.p->n;
+  info.status = R.status;
+  return R.status;
+}
+
+// ---------------------------------------------------------------- rBiCGStab
+int solve_bicg(rk_problem* p, const double* b, double* x, const rk_solve_params& prm, rk_solve_info& info,
+               bool recycle, cudaStream_t st) {
+  BicgRun R;
+  RK_TRY(bicg_setup(R, p, b, x, prm, info, recycle, st));
+  if (R.done) return RK_OK;
   const int NB = 8;
-  while (true) {
-    // r = b - A x; its projection: eta1 = C^T r, r -= C eta1, xi = -eta1
-    RK_TRY(stencil_launch(p, ST_RESID, x, b, v.r, p->part, p->counter, &p->st->rho2, nullptr, st));
-    if (kc) {
-      RK_TRY(bdots_launch(p, p->Cblk(kc), kc, v.r, false, xi, nullptr, st));
-      RK_TRY(bupdate_launch(p, p->Cblk(kc), kc, xi, v.r, v.r, &p->st->rho2, nullptr, st));
-      // xi = -eta1 enters x at once (x <- x + U eta1); xi restarts from 0
-      RK_TRY(bgemm_launch(p, p->Ublk(kc), kc, nullptr, 0, nullptr, xi, 1, x, false, 1, st));
-      RK_CUDA(cudaMemsetAsync(xi, 0, sizeof(double) * kc, st));
-    }
-    { ProfScope ps_(&p->prof, PC_BICG, 24.0 * p->n, st); RK_CUDA(launch_copy(p->n, v.r, v.rt, st)); RK_CUDA(launch_fill(p->n, 0.0, v.xt, st)); }
-    { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_bicg_init(p->bs, &p->st->rho2, tolabs, maxmv - matvecs, st)); }
-    words += (S + 3) + 2.0 * kc + 4;
+  while (!R.done) {
+    RK_TRY(bicg_pass_start(R, st));
     bool running = true;
     while (running) {
-      for (int it = 0; it < NB; ++it) {
-        { ProfScope ps_(&p->prof, PC_BICG, 32.0 * p->n, st, 2.0 * p->n); RK_CUDA(launch_bicg_p(v, p->bs, p->n, st)); }
-        RK_TRY(opapply_launch(p, opk, v.p, false, v.v, false, &p->bs->stop, st, false, pc));
-        RK_TRY(bdots_launch(p, p->Cblk(kc), kc, v.v, false, eta1, &p->bs->stop, st, v.rt));
-        { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_bicg_alpha(p->bs, eta1, kc, st)); }
-        { ProfScope ps_(&p->prof, PC_BICG, 8.0 * (kc + (kc ? 5 : 3)) * (double)p->n, st, (p->bdf ? 2.0 : kc + 2.0) * p->n); RK_CUDA(launch_bicg_s(v, p->bs, p->n, kc, p->Cblk(kc), p->bdf, p->ld, eta1, xi, p->part, p->counter, st)); }
-        RK_TRY(opapply_launch(p, opk, v.s, false, v.t, false, &p->bs->stop, st, false, pc));
-        if (kc) RK_TRY(bdots_launch(p, p->Cblk(kc), kc, v.t, false, eta2, &p->bs->stop, st));
-        { ProfScope ps_(&p->prof, PC_BICG, 8.0 * (kc + (kc ? 3 : 2)) * (double)p->n, st, (p->bdf ? 2.0 : kc + 2.0) * p->n); RK_CUDA(launch_bicg_t(v, p->bs, p->n, kc, p->Cblk(kc), p->bdf, p->ld, eta2, p->part, p->counter, st)); }
-        { ProfScope ps_(&p->prof, PC_BICG, 56.0 * p->n, st, 5.0 * p->n); RK_CUDA(launch_bicg_r(v, p->bs, p->n, kc, eta1, eta2, xi, p->part, p->counter, st)); }
-      }
+      for (int it = 0; it < NB; ++it) RK_TRY(bicg_iteration(R, st));
       RK_CUDA(cudaMemcpyAsync(p->bs_h, p->bs, sizeof(BicgScalars), cudaMemcpyDeviceToHost, st));
       RK_CUDA(cudaStreamSynchronize(st));
       p->prof.flush();
       if (p->bs_h->stop) running = false;
     }
-    if (p->bs_h->half == 1) { ProfScope ps_(&p->prof, PC_BICG, 24.0 * p->n, st); RK_CUDA(launch_bicg_half(v, p->bs, p->n, st)); }
-    matvecs += p->bs_h->matvecs;
-    its += p->bs_h->it;
-    upd = p->bs_h->upd;
-    words += (double)p->bs_h->it * (2 * S + 4.0 * kc + 22);
-    const int flag = p->bs_h->flag;
-    // final fold: x <- x + M^{-1} x~ - U xi
-    {
-      if (pc == RK_PC_SUBDOMAIN) {
-        RK_TRY(subdomain_launch(p, v.xt, p->sdw + p->ld, false, nullptr, nullptr, st));
-        RK_CUDA(launch_add(p->n, p->sdw + p->ld, x, st));
-      } else {
-        RK_CUDA(launch_axpy_scaled(p->n, p->dinv, v.xt, x, st));
-      }
-      if (kc) {
-        { ProfScope ps_(&p->prof, PC_SMALL, 0.0, st); RK_CUDA(launch_bicg_foldcoef(xi, kc, coefv, st)); }
-        RK_TRY(bgemm_launch(p, p->Ublk(kc), kc, nullptr, 0, nullptr, coefv, 1, x, false, 1, st));
-      }
-      words += kc + 4;
-    }
-    // true residual b - A x; above tol, Algorithm 4 restarts from the current x (residual replacement)
-    RK_TRY(stencil_launch(p, ST_RESID, x, b, v.r, p->part, p->counter, &p->st->rho2, nullptr, st));
-    RK_TRY(sync_state(p, st));
-    rel = std::sqrt(p->st_h->rho2) / bnorm;
-    if (rel <= prm.tol) {
-      status = RK_OK;
-      break;
-    }
-    if (matvecs >= maxmv || flag == 3) {
-      status = RK_E_NOT_CONVERGED;
-      break;
-    }
-    if (restarts >= 3) {
-      status = flag == 2 ? RK_E_BREAKDOWN : RK_E_NOT_CONVERGED;
-      break;
-    }
-    restarts += 1;
+    RK_TRY(bicg_pass_end(R, st));
   }
-  info.matvecs = matvecs;
-  info.cycles_or_iters = its;
-  info.restarts = restarts;
-  info.relres_true = rel;
-  info.relres_est = upd / bnorm;
-  info.recycle_dim = p->kdim;
-  info.model_bytes = 8.0 * words * (double)p->n;
-  info.status = status;
-  return status;
+  return bicg_finish(R);
 }
 
 void context_free(rk_context* c) {
@@ -1789,39 +1853,47 @@ int rk_get_recycle(const rk_problem* p, double* U, double* C, int32_t* k, void* 
   return RK_OK;
 }
 
-int rk_solve(rk_problem* p, const double* b, double* x, const rk_solve_params* params, rk_solve_info* info,
-             void* stream) {
-  if (!p || !b || !x || !params) return fail(RK_E_INVALID, "NULL argument");
-  rk_solve_params prm = *params;
+// The checks of a solve's parameters (RK_E_INVALID with a message).
+int check_params(const rk_solve_params& prm) {
   if (!(prm.tol > 0.0)) return fail(RK_E_INVALID, "tol must be positive");
   if (prm.precision != RK_FP64 && prm.precision != RK_MIXED && prm.precision != RK_DF)
     return fail(RK_E_INVALID, "unknown precision");
   if (prm.k < 0) return fail(RK_E_INVALID, "k < 0");
+  if (prm.hybrid_refresh < 0 || prm.hybrid_fallback < 0) return fail(RK_E_INVALID, "negative hybrid parameter");
+  if (prm.precond_side != 0 && prm.precond_side != 1) return fail(RK_E_INVALID, "precond_side must be 0 or 1");
+  if (prm.precond != RK_PC_JACOBI && prm.precond != RK_PC_SUBDOMAIN) return fail(RK_E_INVALID, "unknown precond");
+  if (prm.precond == RK_PC_SUBDOMAIN && prm.mode != RK_RBICGSTAB && prm.precond_side != 1)
+    return fail(RK_E_INVALID, "the sub-domain preconditioner is applied from the left in GMRES and rGCROT");
+  if (prm.mode < RK_GMRES || prm.mode > RK_HYBRID) return fail(RK_E_INVALID, "unknown mode");
+  return RK_OK;
+}
+
+// The solver a solve of this problem runs: RK_HYBRID resolves by the
+// problem's solve counter (Sec. 2.4: rGCROT for the first hybrid_switch
+// solves of a phase, then rBiCGStab with U, C frozen; every
+// hybrid_refresh-th solve after the switch runs rGCROT to update the space).
+int resolved_mode(const rk_problem* p, const rk_solve_params& prm) {
+  if (prm.mode != RK_HYBRID) return prm.mode;
+  const int t = p->solves - p->hyb_base;
+  const bool refresh = prm.hybrid_refresh > 0 && t >= prm.hybrid_switch &&
+                       (t - prm.hybrid_switch + 1) % prm.hybrid_refresh == 0;
+  return (t < prm.hybrid_switch || refresh) ? RK_RGCROT : RK_RBICGSTAB;
+}
+
+int rk_solve(rk_problem* p, const double* b, double* x, const rk_solve_params* params, rk_solve_info* info,
+             void* stream) {
+  if (!p || !b || !x || !params) return fail(RK_E_INVALID, "NULL argument");
+  rk_solve_params prm = *params;
+  RK_TRY(check_params(prm));
   rk_solve_info loc{};
   rk_solve_info& inf = info ? *info : loc;
   std::memset(&inf, 0, sizeof(inf));
   cudaStream_t st = (cudaStream_t)stream;
-  if (prm.hybrid_refresh < 0 || prm.hybrid_fallback < 0) return fail(RK_E_INVALID, "negative hybrid parameter");
-  if (prm.precond_side != 0 && prm.precond_side != 1) return fail(RK_E_INVALID, "precond_side must be 0 or 1");
-  if (prm.precond != RK_PC_JACOBI && prm.precond != RK_PC_SUBDOMAIN) return fail(RK_E_INVALID, "unknown precond");
-  if (prm.precond == RK_PC_SUBDOMAIN) {
-    if (prm.mode != RK_RBICGSTAB && prm.precond_side != 1)
-      return fail(RK_E_INVALID, "the sub-domain preconditioner is applied from the left in GMRES and rGCROT");
-    RK_TRY(ensure_subdomain(p));
-  }
+  if (prm.precond == RK_PC_SUBDOMAIN) RK_TRY(ensure_subdomain(p));
   // the stored recycle space in the format of this solve's precision
   RK_TRY(ensure_basis(p, prm.precision == RK_DF, st));
-  int mode = prm.mode;
-  const bool hybrid = mode == RK_HYBRID;
-  if (hybrid) {
-    // Sec. 2.4: rGCROT for the first hybrid_switch solves of a phase, then
-    // rBiCGStab with U, C frozen; every hybrid_refresh-th solve after the
-    // switch runs rGCROT to update the space
-    const int t = p->solves - p->hyb_base;
-    const bool refresh = prm.hybrid_refresh > 0 && t >= prm.hybrid_switch &&
-                         (t - prm.hybrid_switch + 1) % prm.hybrid_refresh == 0;
-    mode = (t < prm.hybrid_switch || refresh) ? RK_RGCROT : RK_RBICGSTAB;
-  }
+  const bool hybrid = prm.mode == RK_HYBRID;
+  int mode = resolved_mode(p, prm);
   inf.mode_used = mode;
   int rc;
   if (mode == RK_GMRES || mode == RK_RGCROT) {
@@ -2036,6 +2108,287 @@ int rk_problem_release(rk_problem* p, void* stream) {
   return RK_OK;
 }
 
+// ====================================================== batched rBiCGStab phase
+// The iterations of the rBiCGStab solves of a batch run as one launch per
+// iteration phase over a work list of (problem, block) items (rk_batch.h);
+// every other stage of those solves is the single-problem code, so each
+// solve gives what it gives alone. The NB iterations between host checks are
+// captured once per round into a CUDA graph and replayed.
+
+namespace {
+
+// Launch shapes of the batched phase, chosen per workload shape by timing
+// candidates on the first replays (the results do not depend on them) and
+// cached in memory and, when RK_TUNE_CACHE names a file, in that JSON file.
+struct BatchShape {
+  int bps;     // blocks per SM of the streaming kernels' persistent grid
+  int sbps;    // blocks per SM of the stencil's persistent grid
+  int zchunk;  // z planes per stencil tile
+};
+const BatchShape kShapes[] = {{4, 4, 8}, {2, 2, 8}, {8, 8, 8}, {4, 4, 4}, {4, 4, 16}, {8, 8, 16}};
+constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;  // shape key -> index into kShapes
+bool g_tune_loaded = false;
+
+const char* tune_path() { return std::getenv("RK_TUNE_CACHE"); }
+
+void tune_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = tune_path();
+  if (!path) return;
+  std::ifstream f(path);
+  if (!f) return;
+  std::stringstream ss;
+  ss << f.rdbuf();
+  const std::string t = ss.str();
+  // {"key": index, ...}: keys have no quotes or colons inside
+  size_t pos = 0;
+  while ((pos = t.find('"', pos)) != std::string::npos) {
+    const size_t e = t.find('"', pos + 1);
+    if (e == std::string::npos) break;
+    const std::string key = t.substr(pos + 1, e - pos - 1);
+    const size_t c = t.find(':', e);
+    if (c == std::string::npos) break;
+    const int v = std::atoi(t.c_str() + c + 1);
+    if (v >= 0 && v < kNumShapes) g_tune[key] = v;
+    pos = t.find_first_of(",}", c);
+    if (pos == std::string::npos) break;
+  }
+}
+
+void tune_save() {
+  const char* path = tune_path();
+  if (!path) return;
+  std::ofstream f(path);
+  if (!f) return;
+  f << "{";
+  bool first = true;
+  for (auto& kv : g_tune) {
+    f << (first ? "" : ", ") << "\"" << kv.first << "\": " << kv.second;
+    first = false;
+  }
+  f << "}\n";
+}
+
+// the workload shape: problems, total cells (log2 bucket), bands, operator precision
+std::string tune_key(const std::vector<BatchProb>& P) {
+  int64_t cells = 0;
+  int s19 = 0, f32 = 0;
+  for (auto& q : P) {
+    cells += q.d.n;
+    s19 += q.S == 19;
+    f32 += q.f32;
+  }
+  int lg = 0;
+  while ((int64_t(1) << (lg + 1)) <= cells) ++lg;
+  std::ostringstream k;
+  k << "bicg-n" << P.size() << "-c" << lg << "-s" << (s19 * 2 >= (int)P.size() ? 19 : 7) << "-f" << (f32 ? 32 : 64);
+  return k.str();
+}
+
+struct BatchDevice {
+  rk_context* ctx = nullptr;
+  BatchProb* P = nullptr;
+  int2* red = nullptr;     // (problem, block) items of the streaming kernels
+  int2* red2 = nullptr;    // the same for the problems with kc > 0 (the C^T t projection)
+  int2* tiles[2] = {nullptr, nullptr};  // stencil tiles of the 7- and 19-band problems
+  int nprob = 0, nred = 0, nred2 = 0, ntiles[2] = {0, 0};
+  void release() {
+    dev_free(ctx, P);
+    dev_free(ctx, red);
+    dev_free(ctx, red2);
+    dev_free(ctx, tiles[0]);
+    dev_free(ctx, tiles[1]);
+    P = nullptr;
+    red = red2 = tiles[0] = tiles[1] = nullptr;
+  }
+};
+
+int upload(rk_context* ctx, const void* host, size_t bytes, void** dev, cudaStream_t st) {
+  *dev = dev_alloc(ctx, bytes);
+  if (!*dev) return fail(RK_E_OOM, "batched phase: device allocation failed");
+  RK_CUDA(cudaMemcpyAsync(*dev, host, bytes, cudaMemcpyHostToDevice, st));
+  return RK_OK;
+}
+
+// descriptors and work lists of the active runs for a tiling of zchunk planes
+int batch_build(BatchDevice& D, std::vector<BatchProb>& P, int zchunk, cudaStream_t st) {
+  std::vector<int2> red, red2, tl[2];
+  for (int i = 0; i < (int)P.size(); ++i) {
+    BatchProb& q = P[i];
+    q.gx = (q.d.nx + kTX - 1) / kTX;
+    q.gy = (q.d.ny + kTY - 1) / kTY;
+    q.zchunk = std::min(zchunk, q.d.nz);
+    q.gz = (q.d.nz + q.zchunk - 1) / q.zchunk;
+    for (int b = 0; b < q.nblk; ++b) {
+      red.push_back(make_int2(i, b));
+      if (q.kc > 0) red2.push_back(make_int2(i, b));
+    }
+    const int nt = q.gx * q.gy * q.gz;
+    for (int t = 0; t < nt; ++t) tl[q.S == 19].push_back(make_int2(i, t));
+  }
+  D.release();
+  D.nprob = (int)P.size();
+  D.nred = (int)red.size();
+  D.nred2 = (int)red2.size();
+  D.ntiles[0] = (int)tl[0].size();
+  D.ntiles[1] = (int)tl[1].size();
+  RK_TRY(upload(D.ctx, P.data(), sizeof(BatchProb) * P.size(), (void**)&D.P, st));
+  RK_TRY(upload(D.ctx, red.data(), sizeof(int2) * std::max<size_t>(red.size(), 1), (void**)&D.red, st));
+  RK_TRY(upload(D.ctx, red2.data(), sizeof(int2) * std::max<size_t>(red2.size(), 1), (void**)&D.red2, st));
+  for (int s = 0; s < 2; ++s)
+    RK_TRY(upload(D.ctx, tl[s].data(), sizeof(int2) * std::max<size_t>(tl[s].size(), 1), (void**)&D.tiles[s], st));
+  RK_CUDA(cudaStreamSynchronize(st));
+  return RK_OK;
+}
+
+// NB iterations of Algorithm 4 for every active problem, one launch per phase
+cudaError_t batch_iterations(const BatchDevice& D, const BatchShape& sh, int NB, cudaStream_t st) {
+  const int g = sh.bps * kNumSM, gs = sh.sbps * kNumSM;
+  cudaError_t e = cudaSuccess;
+  for (int it = 0; it < NB && e == cudaSuccess; ++it) {
+    e = launch_batch_bicg_p(D.P, D.red, D.nred, g, st);
+    for (int s = 0; s < 2 && e == cudaSuccess; ++s)
+      e = launch_batch_stencil(D.P, D.tiles[s], D.ntiles[s], s ? 19 : 7, 0, gs, st);
+    if (e == cudaSuccess) e = launch_batch_dots(D.P, D.red, D.nred, 0, g, st);
+    if (e == cudaSuccess) e = launch_batch_bicg_alpha(D.P, D.nprob, st);
+    if (e == cudaSuccess) e = launch_batch_bicg_s(D.P, D.red, D.nred, g, st);
+    for (int s = 0; s < 2 && e == cudaSuccess; ++s)
+      e = launch_batch_stencil(D.P, D.tiles[s], D.ntiles[s], s ? 19 : 7, 1, gs, st);
+    if (e == cudaSuccess) e = launch_batch_dots(D.P, D.red2, D.nred2, 1, g, st);
+    if (e == cudaSuccess) e = launch_batch_bicg_t(D.P, D.red, D.nred, g, st);
+    if (e == cudaSuccess) e = launch_batch_bicg_r(D.P, D.red, D.nred, g, st);
+  }
+  return e;
+}
+
+int batch_graph(const BatchDevice& D, const BatchShape& sh, int NB, cudaStream_t cap, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  RK_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+  const cudaError_t e = batch_iterations(D, sh, NB, cap);
+  const cudaError_t ce = cudaStreamEndCapture(cap, &g);
+  if (e != cudaSuccess || ce != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(RK_E_CUDA, std::string("batched phase capture: ") + cudaGetErrorString(e != cudaSuccess ? e : ce));
+  }
+  const cudaError_t ie = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) return fail(RK_E_CUDA, std::string("batched phase instantiation: ") + cudaGetErrorString(ie));
+  return RK_OK;
+}
+
+// The passes of the runs in R (set up by bicg_setup) with their iterations
+// batched; on return every run is done (or *failed_at holds a failing run).
+int run_bicg_batched(std::vector<BicgRun*>& R, rk_context* ctx, cudaStream_t st) {
+  const int NB = 8;
+  cudaStream_t cap = nullptr;
+  RK_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  BatchDevice D;
+  D.ctx = ctx;
+  cudaGraphExec_t ge = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = RK_OK;
+  auto cleanup = [&](int r) {
+    if (ge) cudaGraphExecDestroy(ge);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    D.release();
+    cudaStreamDestroy(cap);
+    return r;
+  };
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return cleanup(fail(RK_E_CUDA, "batched phase: event creation failed"));
+  while (rc == RK_OK) {
+    std::vector<BicgRun*> act;
+    for (auto* r : R)
+      if (!r->done) act.push_back(r);
+    if (act.empty()) break;
+    for (auto* r : act)
+      if ((rc = bicg_pass_start(*r, st)) != RK_OK) return cleanup(rc);
+    std::vector<BatchProb> P(act.size());
+    for (size_t i = 0; i < act.size(); ++i) {
+      BicgRun& r = *act[i];
+      rk_problem* p = r.p;
+      BatchProb& q = P[i];
+      q = BatchProb{};
+      q.d = p->d;
+      q.S = p->S;
+      q.kc = r.kc;
+      q.nblk = red_blocks(p->n);
+      q.f32 = r.opk == RK_MIXED ? 1 : 0;
+      q.ld = p->ld;
+      q.coef = p->coef;
+      q.dinv = p->dinv;
+      q.coef32 = p->coef32;
+      q.dinv32 = p->dinv32;
+      q.v = r.v;
+      q.bs = p->bs;
+      q.C = reinterpret_cast<const double*>(p->Cblk(r.kc));
+      q.eta1 = r.eta1;
+      q.eta2 = r.eta2;
+      q.xi = r.xi;
+      q.part = p->part;
+      q.counter = p->counter;
+    }
+    // the launch shape: cached, or tuned on this round's first replays
+    const std::string key = tune_key(P);
+    int shape = -1;
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      tune_load();
+      auto it = g_tune.find(key);
+      if (it != g_tune.end()) shape = it->second;
+    }
+    const bool tuning = shape < 0;
+    std::vector<float> times;
+    int cur = -1;
+    bool running = true;
+    while (running) {
+      const int want = tuning ? ((int)times.size() < kNumShapes ? (int)times.size() : shape) : shape;
+      if (want != cur) {
+        if (ge) {
+          cudaGraphExecDestroy(ge);
+          ge = nullptr;
+        }
+        if ((rc = batch_build(D, P, kShapes[want].zchunk, st)) != RK_OK) return cleanup(rc);
+        if ((rc = batch_graph(D, kShapes[want], NB, cap, &ge)) != RK_OK) return cleanup(rc);
+        cur = want;
+      }
+      const bool timed = tuning && (int)times.size() < kNumShapes;
+      if (timed) RK_CUDA(cudaEventRecord(e0, st));
+      RK_CUDA(cudaGraphLaunch(ge, st));
+      if (timed) RK_CUDA(cudaEventRecord(e1, st));
+      for (auto* r : act)
+        RK_CUDA(cudaMemcpyAsync(r->p->bs_h, r->p->bs, sizeof(BicgScalars), cudaMemcpyDeviceToHost, st));
+      RK_CUDA(cudaStreamSynchronize(st));
+      running = false;
+      for (auto* r : act)
+        if (!r->p->bs_h->stop) running = true;
+      if (timed) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        times.push_back(running ? ms : 1e30f);  // a replay in which every pass stopped is not comparable
+        if ((int)times.size() == kNumShapes || !running) {
+          shape = (int)(std::min_element(times.begin(), times.end()) - times.begin());
+          if (times[shape] < 1e29f) {
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            g_tune[key] = shape;
+            tune_save();
+          }
+        }
+      }
+    }
+    for (auto* r : act)
+      if ((rc = bicg_pass_end(*r, st)) != RK_OK) return cleanup(rc);
+  }
+  return cleanup(rc);
+}
+
+}  // namespace
+
 int rk_solve_batch(rk_problem* const* problems, const double* const* b, double* const* x, int32_t n,
                    const rk_solve_params* params, rk_solve_info* infos, int32_t nthreads, void* stream) {
   if (n < 0) return fail(RK_E_INVALID, "n < 0");
@@ -2066,17 +2419,29 @@ int rk_solve_batch(rk_problem* const* problems, const double* const* b, double* 
   }
   std::vector<int> rc(n, RK_OK);
   std::vector<std::string> msg(n);
+  // rBiCGStab solves (also the hybrid's after its switch) with right point
+  // Jacobi and the FP64 basis run their iterations in the batched phase
+  // launches (unless RK_BATCHED_BICG=0); every other solve goes to the pool
+  const char* bb = std::getenv("RK_BATCHED_BICG");
+  const bool batched_on = !(bb && bb[0] == '0');
+  std::vector<int> grp, rest;
+  for (int i = 0; i < n; ++i) {
+    const rk_solve_params& pr = params[i];
+    const bool ok = batched_on && check_params(pr) == RK_OK && resolved_mode(problems[i], pr) == RK_RBICGSTAB &&
+                    pr.precond == RK_PC_JACOBI && (pr.precision == RK_FP64 || pr.precision == RK_MIXED) &&
+                    !(pr.mode == RK_HYBRID && pr.hybrid_fallback > 0) && !problems[i]->prof.on;
+    (ok ? grp : rest).push_back(i);
+  }
   // largest problems first (longest-processing-time order), so that the
   // batch does not end with one large solve running alone
-  std::vector<int> order(n);
-  for (int i = 0; i < n; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b2) { return problems[a]->n > problems[b2]->n; });
+  std::stable_sort(rest.begin(), rest.end(), [&](int a, int b2) { return problems[a]->n > problems[b2]->n; });
   if (rc_setup == RK_OK) {
     std::atomic<int> next{0};
+    const int nrest = (int)rest.size();
     auto worker = [&](int t) {
       cudaSetDevice(dev);
-      for (int q = next.fetch_add(1); q < n; q = next.fetch_add(1)) {
-        const int i = order[q];
+      for (int q = next.fetch_add(1); q < nrest; q = next.fetch_add(1)) {
+        const int i = rest[q];
         rc[i] = rk_solve(problems[i], b[i], x[i], &params[i], &infos[i], ws[t]);
         if (rc[i] != RK_OK) msg[i] = rk_last_error();
         infos[i].status = rc[i];
@@ -2084,7 +2449,50 @@ int rk_solve_batch(rk_problem* const* problems, const double* const* b, double* 
     };
     std::vector<std::thread> pool;
     for (int t = 1; t < T; ++t) pool.emplace_back(worker, t);
-    worker(0);
+    if (!grp.empty()) {
+      // the batched group on stream ws[0] in this thread, beside the pool
+      cudaStream_t gs = ws[0];
+      std::vector<BicgRun> runs(grp.size());
+      std::vector<BicgRun*> live;
+      for (size_t g = 0; g < grp.size(); ++g) {
+        const int i = grp[g];
+        rk_problem* p = problems[i];
+        rk_solve_info& inf = infos[i];
+        std::memset(&inf, 0, sizeof(inf));
+        inf.mode_used = RK_RBICGSTAB;
+        int r = ensure_basis(p, false, gs);
+        if (r == RK_OK) r = bicg_setup(runs[g], p, b[i], x[i], params[i], inf, params[i].k > 0, gs);
+        if (r != RK_OK) {
+          rc[i] = r;
+          msg[i] = rk_last_error();
+          runs[g].done = true;
+          runs[g].status = r;
+        } else if (!runs[g].done) {
+          live.push_back(&runs[g]);
+        }
+      }
+      int rb = run_bicg_batched(live, problems[grp[0]]->ctx, gs);
+      for (size_t g = 0; g < grp.size(); ++g) {
+        const int i = grp[g];
+        if (rc[i] != RK_OK) {
+          infos[i].status = rc[i];
+          continue;
+        }
+        if (rb != RK_OK && !runs[g].done) {
+          rc[i] = rb;
+          msg[i] = rk_last_error();
+          infos[i].status = rb;
+          continue;
+        }
+        rc[i] = bicg_finish(runs[g]);
+        if (rc[i] == RK_OK || rc[i] == RK_E_NOT_CONVERGED || rc[i] == RK_E_BREAKDOWN) problems[i]->solves += 1;
+        if (rc[i] != RK_OK) msg[i] = "rBiCGStab solve status " + std::to_string(rc[i]);
+        infos[i].status = rc[i];
+      }
+      if (T == 1) worker(0);  // one stream: the pool's share runs after the group
+    } else {
+      worker(0);
+    }
     for (auto& th : pool) th.join();
   }
   // work queued on `stream` afterwards runs after the whole batch

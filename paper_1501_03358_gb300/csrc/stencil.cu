@@ -16,6 +16,7 @@
 // sweep of the sub-domain Jacobi preconditioner, one damped point-Jacobi
 // sweep y = z + omega dinv (r - A z) (ST_JSWEEP), in the same band order.
 #include "rk_internal.h"
+#include "rk_batch.h"
 #include "rk_device.cuh"
 #include "rk_df.cuh"
 
@@ -46,20 +47,17 @@ __device__ __forceinline__ void st_val<double>(double* p, int64_t q, double w) {
 template <>
 __device__ __forceinline__ void st_val<float2>(float2* p, int64_t q, double w) { p[q] = df_from_double_i(w); }
 
-template <int S, int MODE, typename VT = double, typename YT = double>
-__global__ void __launch_bounds__(kTX* kTY) k_stencil(Dims d, const double* __restrict__ coef,
-                                                      const double* __restrict__ dinv,
-                                                      const VT* __restrict__ v,
-                                                      const double* __restrict__ b, YT* __restrict__ y,
-                                                      double* part, unsigned* counter, double* nrm2,
-                                                      const int* skip, int zchunk) {
-  if (skip != nullptr && *skip != 0) return;
+// One tile of the product (block coordinates bx, by, bz of the 2.5-D grid);
+// returns the thread's sum of squares of its outputs when want_norm.
+template <int S, int MODE, typename VT, typename YT>
+__device__ __forceinline__ double stencil_tile(const Dims& d, const double* __restrict__ coef,
+                                               const double* __restrict__ dinv, const VT* __restrict__ v,
+                                               const double* __restrict__ b, YT* __restrict__ y, int bx, int by,
+                                               int bz, int zchunk, bool want_norm) {
   __shared__ double sz[3][kTY + 2][kTX + 2];
-  __shared__ double red[32];
-  __shared__ int lastflag;
   const int tx = threadIdx.x & (kTX - 1), ty = threadIdx.x / kTX;
-  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
-  const int k0 = blockIdx.z * zchunk;
+  const int x0 = bx * kTX, y0 = by * kTY;
+  const int k0 = bz * zchunk;
   const int k1 = min(k0 + zchunk, d.nz);
   const int gi = x0 + tx, gj = y0 + ty;
   const bool active = gi < d.nx && gj < d.ny;
@@ -120,11 +118,26 @@ __global__ void __launch_bounds__(kTX* kTY) k_stencil(Dims d, const double* __re
         if (MODE == ST_LEFT || MODE == ST_LRESID || MODE == ST_JSWEEP) w = __dmul_rn(w, __ldg(&dinv[p]));
         if (MODE == ST_JSWEEP) w = fma(kSdOmega, w, sz[sc][cy][cx]);
         st_val<YT>(y, p, w);
-        if (part != nullptr) acc2 = fma(w, w, acc2);
+        if (want_norm) acc2 = fma(w, w, acc2);
       }
       __syncthreads();
     }
   }
+  return acc2;
+}
+
+template <int S, int MODE, typename VT = double, typename YT = double>
+__global__ void __launch_bounds__(kTX* kTY) k_stencil(Dims d, const double* __restrict__ coef,
+                                                      const double* __restrict__ dinv,
+                                                      const VT* __restrict__ v,
+                                                      const double* __restrict__ b, YT* __restrict__ y,
+                                                      double* part, unsigned* counter, double* nrm2,
+                                                      const int* skip, int zchunk) {
+  if (skip != nullptr && *skip != 0) return;
+  __shared__ double red[32];
+  __shared__ int lastflag;
+  const double acc2 = stencil_tile<S, MODE, VT, YT>(d, coef, dinv, v, b, y, blockIdx.x, blockIdx.y, blockIdx.z,
+                                                    zchunk, part != nullptr);
   if (part == nullptr) return;
   const double s = block_sum(acc2, red);
   const int nb = gridDim.x * gridDim.y * gridDim.z;
@@ -161,15 +174,14 @@ __device__ __forceinline__ void st_f32<float>(float* p, int64_t q, float w) { p[
 // sweep of the FP32 sub-domain preconditioner), every step one FP32 rounding
 // in the band order of the FP64 kernels.
 template <int S, int MODE, typename VT, typename YT, typename RT>
-__global__ void __launch_bounds__(kTX* kTY) k_stencil32(Dims d, const float* __restrict__ coef,
-                                                        const float* __restrict__ dinv, const VT* __restrict__ v,
-                                                        YT* __restrict__ y, const int* skip, int zchunk,
-                                                        const RT* __restrict__ r, float om) {
-  if (skip != nullptr && *skip != 0) return;
+__device__ __forceinline__ void stencil32_tile(const Dims& d, const float* __restrict__ coef,
+                                               const float* __restrict__ dinv, const VT* __restrict__ v,
+                                               YT* __restrict__ y, int bx, int by, int bz, int zchunk,
+                                               const RT* __restrict__ r, float om) {
   __shared__ float sz[3][kTY + 2][kTX + 2];
   const int tx = threadIdx.x & (kTX - 1), ty = threadIdx.x / kTX;
-  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
-  const int k0 = blockIdx.z * zchunk;
+  const int x0 = bx * kTX, y0 = by * kTY;
+  const int k0 = bz * zchunk;
   const int k1 = min(k0 + zchunk, d.nz);
   const int gi = x0 + tx, gj = y0 + ty;
   const bool active = gi < d.nx && gj < d.ny;
@@ -228,6 +240,15 @@ __global__ void __launch_bounds__(kTX* kTY) k_stencil32(Dims d, const float* __r
     }
     __syncthreads();
   }
+}
+
+template <int S, int MODE, typename VT, typename YT, typename RT>
+__global__ void __launch_bounds__(kTX* kTY) k_stencil32(Dims d, const float* __restrict__ coef,
+                                                        const float* __restrict__ dinv, const VT* __restrict__ v,
+                                                        YT* __restrict__ y, const int* skip, int zchunk,
+                                                        const RT* __restrict__ r, float om) {
+  if (skip != nullptr && *skip != 0) return;
+  stencil32_tile<S, MODE, VT, YT, RT>(d, coef, dinv, v, y, blockIdx.x, blockIdx.y, blockIdx.z, zchunk, r, om);
 }
 
 // Double-float operator (the recurrences' products in RK_DF): the bands and
@@ -398,7 +419,41 @@ void stencil_grid(const Dims& d, dim3& grid, int& zchunk, int per_sm = 3) {
   grid = dim3(tx, ty, nzc);
 }
 
+// batched A M^{-1} products of rBiCGStab (right point Jacobi): item (i, t)
+// is tile t of problem i in that problem's batched tiling; the FP64 or FP32
+// operator per problem; the problem's stop flag skips it. Elementwise, so the
+// tiling does not change any value.
+template <int S>
+__global__ void __launch_bounds__(kTX* kTY) k_batch_stencil(const BatchProb* __restrict__ P,
+                                                            const int2* __restrict__ tiles, int ntiles, int which) {
+  for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
+    const int2 w = tiles[it];
+    const BatchProb& q = P[w.x];
+    if (q.bs->stop != 0) continue;
+    const int bx = w.y % q.gx, by = (w.y / q.gx) % q.gy, bz = w.y / (q.gx * q.gy);
+    const double* vin = which == 0 ? q.v.p : q.v.s;
+    double* yout = which == 0 ? q.v.v : q.v.t;
+    if (q.f32)
+      stencil32_tile<S, ST_PREC, double, double, float>(q.d, q.coef32, q.dinv32, vin, yout, bx, by, bz, q.zchunk,
+                                                        nullptr, 0.f);
+    else
+      stencil_tile<S, ST_PREC, double, double>(q.d, q.coef, q.dinv, vin, nullptr, yout, bx, by, bz, q.zchunk, false);
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_batch_stencil(const BatchProb* P, const int2* tiles, int ntiles, int S, int which, int grid,
+                                 cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  const int g = grid < ntiles ? grid : ntiles;
+  if (S == 7)
+    k_batch_stencil<7><<<g, kTX * kTY, 0, st>>>(P, tiles, ntiles, which);
+  else
+    k_batch_stencil<19><<<g, kTX * kTY, 0, st>>>(P, tiles, ntiles, which);
+  return cudaGetLastError();
+}
 
 int stencil_blocks(const Dims& d) {
   dim3 g;

@@ -97,6 +97,55 @@ def test_release_and_restore_is_exact(ctx):
     b.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batched_phase_equals_alone_and_thread_pool(ctx, precision, tmp_path, monkeypatch):
+    """The batched rBiCGStab phase: twelve uneven problems (7- and 19-band),
+    each with its own recycle space, advance together in one launch per
+    iteration phase over a (problem, block) work list, with launch shapes
+    picked by the autotuner (cached to the RK_TUNE_CACHE file); every solve
+    equals, bit for bit, the same solve alone and the same batch on the
+    thread-pool executor (RK_BATCHED_BICG=0), in matrix-vector products,
+    restarts and x."""
+    import json
+    import oracle
+    from paper_1501_03358_gb300 import Problem, solve_batch
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("RK_TUNE_CACHE", str(cache))
+    cfgs = small_set(10, max_edge=40)
+    from problems import make_config
+    cfgs += [make_config(1, size=14), make_config(1, size=9)]  # 7-band problems in the same batch
+    kw = dict(tol=1e-8, k=8, mode="rBiCGStab", max_matvec=3000, precision=precision)
+    sets = []
+    for c in cfgs:
+        op = oracle.Stencil(c.grid, c.coef)
+        _, U, C, _ = oracle.rgcrot(op, c.rhs(0), tol=1e-9, m=20, k=8, max_matvec=400)
+        sets.append((torch.from_numpy(U.T.copy()).cuda(), torch.from_numpy(C.T.copy()).cuda()))
+    def fresh():
+        ps = [Problem(ctx, c.grid, torch.from_numpy(c.coef)) for c in cfgs]
+        for p, (U, C) in zip(ps, sets):
+            p.set_recycle(U, C)
+        return ps
+    alone, batch, pool = fresh(), fresh(), fresh()
+    for t in (1, 2):
+        bs = [torch.from_numpy(c.rhs(t)).cuda() for c in cfgs]
+        ref = [p.solve(b, **kw) for p, b in zip(alone, bs)]
+        monkeypatch.delenv("RK_BATCHED_BICG", raising=False)
+        xs, infos = solve_batch(batch, bs, nthreads=4, **kw)
+        monkeypatch.setenv("RK_BATCHED_BICG", "0")
+        xp, ip = solve_batch(pool, bs, nthreads=4, **kw)
+        for i in range(len(cfgs)):
+            xa, ia = ref[i]
+            assert ia["status"] == 0 and infos[i]["status"] == 0 and ip[i]["status"] == 0, (i, t)
+            for inf in (infos[i], ip[i]):
+                assert inf["matvecs"] == ia["matvecs"] and inf["restarts"] == ia["restarts"], (i, t)
+                assert inf["mode_used"] == ia["mode_used"] == 2
+            assert torch.equal(xs[i], xa) and torch.equal(xp[i], xa), (i, t)
+    tuned = json.loads(cache.read_text())
+    assert any(k.startswith("bicg-n12") for k in tuned)
+    for p in alone + batch + pool:
+        p.close()
+
+
 def test_continuous_serving_with_eviction_matches_direct_sequences(ctx):
     """Continuous admission: requests for four problems arrive while others
     are being solved (three slots, each its own stream), under a budget that
