@@ -1266,7 +1266,8 @@ int bicg_iteration(BicgRun& R, cudaStream_t st) {
 }
 
 // after the pass stopped: the half step, the fold x <- x + M^{-1} x~ - U xi,
-// the true residual (residual replacement, R12), and the decision
+// the true residual b - A x in FP64 (residual replacement: the decision is
+// taken on it, never on the recurrence's residual), and the decision
 int bicg_pass_end(BicgRun& R, cudaStream_t st) {
   rk_problem* p = R.p;
   const BicgVecs& v = R.v;

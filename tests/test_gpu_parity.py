@@ -331,6 +331,42 @@ def test_harmonic_ritz_cycles_match_oracle(ctx, cfg_id, size, m, k, precision):
         assert subspace_gap(Cg, C) <= 1e-6, (cyc, subspace_gap(Cg, C))
 
 
+def test_full_size_first_cycles_lock_step(ctx):
+    """At the 128^3 channel size, in the benchmark's launch configuration
+    (2,097,152 rows: 1188-block inner products, the 152-block persistent
+    tensor-core recycle update over 16,384 row tiles): rGCROT(40,20) with
+    point Jacobi, one cycle from an empty recycle space (a GMRES(40) cycle,
+    then the harmonic Ritz update) and one cycle with the 20-column space it
+    built, GPU against the oracle.
+
+    Bound for x: both sides minimise the same residual over Krylov bases that
+    differ by orthogonalisation rounding (CGS2 against MGS), a relative
+    perturbation of about m sqrt(N) u ~ 1e-11 (u = 2^-53), amplified by the
+    condition of the small least-squares problem of one cycle (about 10 here:
+    the first cycle cuts the residual by less than 10x), so 1e-9 relative
+    holds with margin. The recycle spaces are compared as subspaces; the
+    second cycle's x depends only on span(C) (A U = C fixes U from it), so
+    its bar is 1e-9 plus the subspace gap."""
+    cfg = make_config(2)
+    prob = gpu_problem(ctx, cfg.grid, cfg.coef)
+    op = oracle.Stencil(cfg.grid, cfg.coef)
+    b = cfg.rhs(0)
+    U = C = None
+    gap = 0.0
+    for cyc in range(2):
+        x, info = prob.solve(t(b), tol=1e-14, m=40, k=20, mode="rGCROT", max_matvec=40, precision="fp64")
+        xo, U, C, io = oracle.rgcrot(op, b, tol=1e-14, m=40, k=20, U=U, C=C, max_matvec=40)
+        assert info["matvecs"] == io["matvecs"] == 40
+        xg = x.cpu().numpy()
+        assert np.linalg.norm(xg - xo) <= (1e-9 + 10 * gap) * np.linalg.norm(xo), cyc
+        assert abs(info["relres_true"] - io["relres_true"]) <= 1e-8 * io["relres_true"], cyc
+        Ug, Cg = prob.get_recycle()
+        Cg = Cg.cpu().numpy().T
+        assert Cg.shape == C.shape == (cfg.n, 20)
+        gap = subspace_gap(Cg, C)
+        assert gap <= 1e-6, (cyc, gap)
+
+
 def test_recycle_set_get_roundtrip_and_forming_c(ctx):
     cfg = make_config(1, size=10)
     prob = gpu_problem(ctx, cfg.grid, cfg.coef)
