@@ -100,8 +100,10 @@ void dev_free(rk_context* c, void* p) {
   if (!p) return;
   if (c->free_fn)
     c->free_fn(p, c->user);
-  else
-    cudaFree(p);
+  else if (cudaFree(p) != cudaSuccess) {
+    const cudaError_t e = cudaGetLastError();
+    if (std::getenv("RK_DEBUG")) std::fprintf(stderr, "librk: cudaFree failed: %s\n", cudaGetErrorName(e));
+  }
 }
 
 template <typename T>
@@ -2211,7 +2213,8 @@ struct BatchDevice {
 int upload(rk_context* ctx, const void* host, size_t bytes, void** dev, cudaStream_t st) {
   *dev = dev_alloc(ctx, bytes);
   if (!*dev) return fail(RK_E_OOM, "batched phase: device allocation failed");
-  RK_CUDA(cudaMemcpyAsync(*dev, host, bytes, cudaMemcpyHostToDevice, st));
+  // an empty list has no host array (its device array is dev_alloc's minimum)
+  if (bytes > 0) RK_CUDA(cudaMemcpyAsync(*dev, host, bytes, cudaMemcpyHostToDevice, st));
   return RK_OK;
 }
 
@@ -2238,10 +2241,10 @@ int batch_build(BatchDevice& D, std::vector<BatchProb>& P, int zchunk, cudaStrea
   D.ntiles[0] = (int)tl[0].size();
   D.ntiles[1] = (int)tl[1].size();
   RK_TRY(upload(D.ctx, P.data(), sizeof(BatchProb) * P.size(), (void**)&D.P, st));
-  RK_TRY(upload(D.ctx, red.data(), sizeof(int2) * std::max<size_t>(red.size(), 1), (void**)&D.red, st));
-  RK_TRY(upload(D.ctx, red2.data(), sizeof(int2) * std::max<size_t>(red2.size(), 1), (void**)&D.red2, st));
+  RK_TRY(upload(D.ctx, red.data(), sizeof(int2) * red.size(), (void**)&D.red, st));
+  RK_TRY(upload(D.ctx, red2.data(), sizeof(int2) * red2.size(), (void**)&D.red2, st));
   for (int s = 0; s < 2; ++s)
-    RK_TRY(upload(D.ctx, tl[s].data(), sizeof(int2) * std::max<size_t>(tl[s].size(), 1), (void**)&D.tiles[s], st));
+    RK_TRY(upload(D.ctx, tl[s].data(), sizeof(int2) * tl[s].size(), (void**)&D.tiles[s], st));
   RK_CUDA(cudaStreamSynchronize(st));
   return RK_OK;
 }
@@ -2390,6 +2393,12 @@ int run_bicg_batched(std::vector<BicgRun*>& R, rk_context* ctx, cudaStream_t st)
 
 }  // namespace
 
+// the batch's teardown calls are not checked (nothing can be undone there);
+// with RK_DEBUG set, a failing one is named on stderr
+static void batch_dbg(cudaError_t e, const char* what) {
+  if (e != cudaSuccess && std::getenv("RK_DEBUG")) std::fprintf(stderr, "librk: %s: %s\n", what, cudaGetErrorName(e));
+}
+
 int rk_solve_batch(rk_problem* const* problems, const double* const* b, double* const* x, int32_t n,
                    const rk_solve_params* params, rk_solve_info* infos, int32_t nthreads, void* stream) {
   if (n < 0) return fail(RK_E_INVALID, "n < 0");
@@ -2444,6 +2453,11 @@ int rk_solve_batch(rk_problem* const* problems, const double* const* b, double* 
       for (int q = next.fetch_add(1); q < nrest; q = next.fetch_add(1)) {
         const int i = rest[q];
         rc[i] = rk_solve(problems[i], b[i], x[i], &params[i], &infos[i], ws[t]);
+        if (std::getenv("RK_DEBUG")) {
+          const cudaError_t e = cudaPeekAtLastError();
+          if (e != cudaSuccess)
+            std::fprintf(stderr, "librk: after the solve of problem %d (worker %d): %s\n", i, t, cudaGetErrorName(e));
+        }
         if (rc[i] != RK_OK) msg[i] = rk_last_error();
         infos[i].status = rc[i];
       }
@@ -2495,19 +2509,31 @@ int rk_solve_batch(rk_problem* const* problems, const double* const* b, double* 
       worker(0);
     }
     for (auto& th : pool) th.join();
+    if (std::getenv("RK_DEBUG")) {
+      const cudaError_t e = cudaPeekAtLastError();
+      if (e != cudaSuccess) std::fprintf(stderr, "librk: before the batch teardown: %s\n", cudaGetErrorName(e));
+    }
   }
   // work queued on `stream` afterwards runs after the whole batch
   for (int t = 0; t < T; ++t) {
     if (!ws[t]) continue;
     cudaEvent_t e;
     if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) {
-      cudaEventRecord(e, ws[t]);
-      cudaStreamWaitEvent(st, e, 0);
-      cudaEventDestroy(e);
+      batch_dbg(cudaEventRecord(e, ws[t]), "cudaEventRecord(ws)");
+      batch_dbg(cudaStreamWaitEvent(st, e, 0), "cudaStreamWaitEvent(caller)");
+      batch_dbg(cudaEventDestroy(e), "cudaEventDestroy");
     }
-    cudaStreamDestroy(ws[t]);
+    batch_dbg(cudaStreamDestroy(ws[t]), "cudaStreamDestroy(ws)");
   }
-  cudaEventDestroy(start);
+  batch_dbg(cudaEventDestroy(start), "cudaEventDestroy(start)");
+  // every call above whose failure matters has been checked; drop what a
+  // handled failure left in this thread's last-error slot, so that it is not
+  // reported later against the caller's own next CUDA call
+  {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess && std::getenv("RK_DEBUG"))
+      std::fprintf(stderr, "librk: rk_solve_batch cleared %s\n", cudaGetErrorName(e));
+  }
   if (rc_setup != RK_OK) return fail(rc_setup, "creating the batch streams failed");
   for (int i = 0; i < n; ++i)
     if (rc[i] != RK_OK) return fail(rc[i], "problem " + std::to_string(i) + ": " + msg[i]);
