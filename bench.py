@@ -793,6 +793,41 @@ def run_switch_sweep(args, ws, rank, local):
     ctx.close()
 
 
+def run_kernel_probe(args, local):
+    """One kernel of the path alone, for profilers: `dots2` = the fused
+    Arnoldi inner products [Q^T p, Q^T w, p^T p, p^T w, w^T w] of one step
+    (rk_arnoldi_dots, FP64, the tensor-core engine) on a row-contiguous N(0, 1) basis of probe-nq
+    columns and probe-n rows; prints the largest normwise difference from
+    the FP64-pipe kernel on the same operands (the tensor-core engine is
+    selected by RK_TC_DOTS=1)."""
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__ as g
+    g.build()
+    from paper_1501_03358_gb300 import Context
+    ctx = Context()
+    gen = torch.Generator(device="cuda").manual_seed(1501)
+    n, nq = args.probe_n, args.probe_nq
+    Q = torch.randn(nq, n, dtype=torch.float64, device="cuda", generator=gen)
+    p = torch.randn(n, dtype=torch.float64, device="cuda", generator=gen)
+    w = torch.randn(n, dtype=torch.float64, device="cuda", generator=gen)
+    out = None
+    os.environ["RK_TC_DOTS"] = "1"
+    for _ in range(args.probe_reps):
+        out = ctx.arnoldi_dots(Q, p, w)
+    torch.cuda.synchronize()
+    os.environ["RK_TC_DOTS"] = "0"
+    ref = ctx.arnoldi_dots(Q, p, w)
+    os.environ.pop("RK_TC_DOTS", None)
+    qn = torch.linalg.norm(Q, dim=1)
+    pn, wn = torch.linalg.norm(p), torch.linalg.norm(w)
+    scale = torch.cat([qn * pn, qn * wn, torch.stack([pn * pn, pn * wn, wn * wn])])
+    diff = float(torch.max(torch.abs(out - ref) / scale))
+    print(json.dumps({"kernel_probe": "dots2", "n": n, "nq": nq, "reps": args.probe_reps,
+                      "max_normwise_diff_vs_fp64_pipe": diff}), flush=True)
+    ctx.close()
+
+
 def run_serve(args, ws, rank, local):
     """Serving loop (config 5): resident problems of mixed sizes (channel and
     porous generators alternating over --serve-edges), each request the next
@@ -935,6 +970,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="porous192", choices=sorted(WORKLOADS))
+    ap.add_argument("--kernel-probe", choices=["dots2"], default=None,
+                    help="run one kernel of the path alone on synthetic operands (a small case for profilers)")
+    ap.add_argument("--probe-n", type=int, default=1 << 22, help="kernel probe: rows")
+    ap.add_argument("--probe-nq", type=int, default=40, help="kernel probe: basis columns")
+    ap.add_argument("--probe-reps", type=int, default=4, help="kernel probe: calls")
     ap.add_argument("--hybrid-switch", type=int, default=5, help="hybrid: rGCROT solves before the switch")
     ap.add_argument("--variants", default="df",
                     help="hybrid workloads: other precisions timed on the same steps, reported beside the headline")
@@ -990,6 +1030,8 @@ def main():
         run_serve(args, ws, rank, local)
     elif args.switch_sweep:
         run_switch_sweep(args, ws, rank, local)
+    elif args.kernel_probe:
+        run_kernel_probe(args, local)
     else:
         if args.precision is None:
             args.precision = "fp64"

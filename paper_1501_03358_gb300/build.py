@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "librk.so")
 SOURCES = ["stencil.cu", "blas.cu", "dfblas.cu", "smalldense.cu", "bicg.cu", "solver.cu", "noalloc.cu", "dftc.cu", "subdomain.cu",
-           "f64blas.cu"]
+           "f64blas.cu", "tcdots.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),
          "-I" + CSRC]

@@ -478,6 +478,7 @@ int dots2_f64_rows(int64_t n) {
 }
 
 cudaError_t launch_dots2_f64(const F64Dots2Args& a, cudaStream_t st) {
+  if (dots2_tc_supported(a)) return launch_dots2_tc(a, st);
   const int yb = dots2_f64_rows(a.n);
   const int64_t rpb = (a.n + yb - 1) / yb;
   const dim3 grid((a.nq + kF64Group - 1) / kF64Group + 1, yb);

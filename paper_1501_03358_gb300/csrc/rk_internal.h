@@ -277,9 +277,14 @@ struct F64Dots2Args {
   unsigned* counter;  // one per column group (ceil(nq / 8) + 1 of them)
   double* out;        // 2 nq + 3
   const int* skip_flag;
+  int* err;           // set when a bounded wait of the tensor-core path gave up (may be NULL)
 };
 int dots2_f64_rows(int64_t n);
 cudaError_t launch_dots2_f64(const F64Dots2Args& a, cudaStream_t st);
+// ---- tcdots.cu: the same products on the tensor cores (exact digit
+// products, FP64 accumulation); launch_dots2_f64 routes here when supported
+bool dots2_tc_supported(const F64Dots2Args& a);
+cudaError_t launch_dots2_tc(const F64Dots2Args& a, cudaStream_t st);
 
 struct F64Update2Args {
   int64_t n;

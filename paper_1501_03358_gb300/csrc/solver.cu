@@ -493,6 +493,7 @@ int bdots2_launch(rk_problem* p, const void* Q, int nq, const void* pv, const vo
     a.counter = p->counter + kGroupCounters;
     a.out = out;
     a.skip_flag = skip;
+    a.err = &p->st->dev_err;
     RK_CUDA(launch_dots2_f64(a, st));
     return RK_OK;
   }
@@ -1757,6 +1758,7 @@ int rk_arnoldi_dots(rk_context* ctx, int64_t n, int32_t nq, const double* Q, int
       a.part = part;
       a.counter = cnt;
       a.out = out;
+      a.err = err;
       if (e == cudaSuccess) e = launch_dots2_f64(a, st);
     }
     int herr = 0;

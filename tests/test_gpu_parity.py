@@ -159,6 +159,38 @@ def test_arnoldi_dots_against_exact_sums(ctx, n, nq, precision):
     assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) / bound))
 
 
+@pytest.mark.parametrize("n,nq", [(2, 1), (64, 5), (130, 62), (4096, 20), (100002, 41), (262144, 61),
+                                  (2 ** 21, 62), (1000000, 33)])
+def test_arnoldi_dots_tensor_core_engine(ctx, n, nq, monkeypatch):
+    """The FP64 fused Arnoldi inner products on the tensor cores (exact
+    digit products of 56-bit truncations per 64-row block, FP64 running
+    sums) against sums of exactly rounded products: within 1e-14 ||a|| ||b||
+    (tighter than the FP64-pipe kernel's bar; the engine is selected by
+    RK_TC_DOTS=1), with the FP64-pipe kernel (RK_TC_DOTS=0, the default) on
+    the same operands within its own bar. Operands: column
+    scales over six decades, a zero column, a column of mixed-sign values
+    spanning 2^-40..2^40 within each block, and a ragged tail."""
+    rng = np.random.default_rng(n + 11 * nq)
+    Q = rng.standard_normal((nq, n)) * np.exp2(rng.integers(-10, 10, size=(nq, 1)))
+    if nq >= 3:
+        Q[1] = 0.0
+        Q[2] = rng.standard_normal(n) * np.exp2(rng.integers(-40, 40, size=n))
+    pv = rng.standard_normal(n)
+    w = rng.standard_normal(n) * 1e3
+    pairs = [(Q[q], pv) for q in range(nq)] + [(Q[q], w) for q in range(nq)] + [(pv, pv), (pv, w), (w, w)]
+    ref = np.array([math.fsum(a * b) for a, b in pairs])
+    scale = np.array([np.linalg.norm(a) * np.linalg.norm(b) for a, b in pairs])
+    monkeypatch.setenv("RK_TC_DOTS", "1")
+    got = ctx.arnoldi_dots(t(Q), t(pv), t(w), precision="fp64").cpu().numpy()
+    err = np.abs(got - ref)
+    assert np.all(err <= 1e-14 * scale), float(np.max(err / np.maximum(scale, 1e-300)))
+    if nq >= 3:
+        assert got[1] == 0.0 and got[nq + 1] == 0.0
+    monkeypatch.setenv("RK_TC_DOTS", "0")
+    got64 = ctx.arnoldi_dots(t(Q), t(pv), t(w), precision="fp64").cpu().numpy()
+    assert np.all(np.abs(got64 - ref) <= 1e-13 * scale)
+
+
 @pytest.mark.parametrize("engine", [1, 0, 2, 3])
 @pytest.mark.parametrize("n,na,nb,nc,scaled", [
     (1, 3, 2, 2, False), (127, 20, 41, 20, True), (129, 61, 0, 20, False), (1000, 20, 40, 20, True),
