@@ -305,7 +305,14 @@ int rk_row_gemm(rk_context* ctx, int64_t n, int32_t na, const double* A, int64_t
  * Equivalent to calling rk_solve(problems[i], b[i], x[i], &params[i],
  * &infos[i]) for every i, except that the solves run concurrently: a pool of
  * nthreads host threads (<= 0: min(n, 16)), each driving its own CUDA
- * stream, takes problems from a shared queue, largest N first. problems, b, x, params, infos:
+ * stream, takes problems from a shared queue, largest N first. With the
+ * environment variable RK_BATCHED_BICG=1, the rBiCGStab solves of the batch
+ * (also a hybrid's after its switch) with right point Jacobi in RK_FP64 or
+ * RK_MIXED instead run their iterations together, one launch per iteration
+ * phase over a (problem, block) work list, on the calling thread beside the
+ * pool (launch shapes tuned on first use and cached in memory and, when
+ * RK_TUNE_CACHE names a file, in that JSON file); the results are the same
+ * bit for bit. problems, b, x, params, infos:
  * host arrays of n entries (b[i], x[i] device pointers as in rk_solve). The
  * batch starts after the work already queued on `stream`, and work queued on
  * `stream` afterwards runs after the whole batch; the call returns when every

@@ -2431,11 +2431,13 @@ int rk_solve_batch(rk_problem* const* problems, const double* const* b, double* 
   }
   std::vector<int> rc(n, RK_OK);
   std::vector<std::string> msg(n);
-  // rBiCGStab solves (also the hybrid's after its switch) with right point
-  // Jacobi and the FP64 basis run their iterations in the batched phase
-  // launches (unless RK_BATCHED_BICG=0); every other solve goes to the pool
+  // with RK_BATCHED_BICG=1, rBiCGStab solves (also the hybrid's after its
+  // switch) with right point Jacobi and the FP64 basis run their iterations
+  // in the batched phase launches; every other solve goes to the pool (by
+  // default all of them: the pool was the faster executor on the measured
+  // batches)
   const char* bb = std::getenv("RK_BATCHED_BICG");
-  const bool batched_on = !(bb && bb[0] == '0');
+  const bool batched_on = bb != nullptr && bb[0] == '1';
   std::vector<int> grp, rest;
   for (int i = 0; i < n; ++i) {
     const rk_solve_params& pr = params[i];

@@ -104,8 +104,8 @@ def test_batched_phase_equals_alone_and_thread_pool(ctx, precision, tmp_path, mo
     iteration phase over a (problem, block) work list, with launch shapes
     picked by the autotuner (cached to the RK_TUNE_CACHE file); every solve
     equals, bit for bit, the same solve alone and the same batch on the
-    thread-pool executor (RK_BATCHED_BICG=0), in matrix-vector products,
-    restarts and x."""
+    thread-pool executor (the default; the batched phase is selected with
+    RK_BATCHED_BICG=1), in matrix-vector products, restarts and x."""
     import json
     import oracle
     from paper_1501_03358_gb300 import Problem, solve_batch
@@ -129,9 +129,9 @@ def test_batched_phase_equals_alone_and_thread_pool(ctx, precision, tmp_path, mo
     for t in (1, 2):
         bs = [torch.from_numpy(c.rhs(t)).cuda() for c in cfgs]
         ref = [p.solve(b, **kw) for p, b in zip(alone, bs)]
-        monkeypatch.delenv("RK_BATCHED_BICG", raising=False)
+        monkeypatch.setenv("RK_BATCHED_BICG", "1")
         xs, infos = solve_batch(batch, bs, nthreads=4, **kw)
-        monkeypatch.setenv("RK_BATCHED_BICG", "0")
+        monkeypatch.delenv("RK_BATCHED_BICG", raising=False)
         xp, ip = solve_batch(pool, bs, nthreads=4, **kw)
         for i in range(len(cfgs)):
             xa, ia = ref[i]
