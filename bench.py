@@ -433,16 +433,19 @@ def run_ours(args, ws, rank, local):
         e2e_steps = seq
     else:
         e2e_steps = list(range(seq[-1] + 1, seq[-1] + 1 + K))
-    xh = torch.empty(cfg.n, dtype=torch.float64).pin_memory()
+    # one pinned host buffer per step (the same bytes as reusing one): with
+    # variants they hold the headline precision's solutions for comparison
+    keep_host = bool(args.variants) and hybrid
+    xhs = [torch.empty(cfg.n, dtype=torch.float64).pin_memory() for _ in (e2e_steps if keep_host else [0])]
     bdev = torch.empty(cfg.n, dtype=torch.float64, device="cuda")
     barrier(ws)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for t in e2e_steps:
+    for si, t in enumerate(e2e_steps):
         bdev.copy_(rhs_host[t], non_blocking=True)
         x.zero_()
         prob.solve(bdev, out=x, **kw)
-        xh.copy_(x, non_blocking=True)
+        xhs[si if keep_host else 0].copy_(x, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     barrier(ws)
@@ -558,11 +561,22 @@ def run_ours(args, ws, rank, local):
                 vprob.solve(rhs_dev[t], out=x, **dict(vkw, hybrid_switch=wkw["hybrid_switch"]))
             vprob.reset()
             torch.cuda.synchronize()
-            vms, vper = _timed_solves(vprob, [rhs_dev[t] for t in seq], vkw, stream, x)
+            vkeep = []
+            vms, vper = _timed_solves(vprob, [rhs_dev[t] for t in seq], vkw, stream, x, keep=vkeep)
+            # per step ||x_variant - x|| / ||x|| against the headline
+            # precision's solution of the same step (the end-to-end pass's
+            # host copies; with the fp64 headline that is the FP64 path the
+            # parity tests hold to the oracle)
+            diffs = []
+            for si, xv in enumerate(vkeep):
+                xr = xhs[si]
+                diffs.append(float(torch.linalg.norm(xv.cpu() - xr) / torch.linalg.norm(xr)))
+            del vkeep
             var[vp] = {"value": len(seq) / (vms * 1e-3), "ms_per_step": vms / len(seq), "dtype": DTYPES[vp],
                        "basis": BASIS[vp], "phases": _phase_summary(vper, hbm_peak),
                        "relres_max": max(i["relres_true"] for _, i in vper),
-                       "all_converged": all(i["status"] == 0 for _, i in vper)}
+                       "all_converged": all(i["status"] == 0 for _, i in vper),
+                       "x_rel_diff_vs_" + args.precision: {"per_step": diffs, "max": max(diffs)}}
             vprob.close()
         line["variants"] = var
     if xs_keep is not None:
@@ -979,8 +993,9 @@ def main():
     ap.add_argument("--probe-nq", type=int, default=40, help="kernel probe: basis columns")
     ap.add_argument("--probe-reps", type=int, default=4, help="kernel probe: calls")
     ap.add_argument("--hybrid-switch", type=int, default=5, help="hybrid: rGCROT solves before the switch")
-    ap.add_argument("--variants", default="df",
-                    help="hybrid workloads: other precisions timed on the same steps, reported beside the headline")
+    ap.add_argument("--variants", default="df,mixed",
+                    help="hybrid workloads: other precisions timed on the same steps, reported beside the headline "
+                         "with their per-step solution difference from it")
     ap.add_argument("--vs-fp64", type=int, default=1,
                     help="precision df/mixed: also solve the timed steps with the fp64 path and report the "
                          "per-step difference of the solutions (1 = on)")
