@@ -163,13 +163,15 @@ def test_arnoldi_dots_against_exact_sums(ctx, n, nq, precision):
                                   (2 ** 21, 62), (1000000, 33)])
 def test_arnoldi_dots_tensor_core_engine(ctx, n, nq, monkeypatch):
     """The FP64 fused Arnoldi inner products on the tensor cores (exact
-    digit products of 56-bit truncations per 64-row block, FP64 running
-    sums) against sums of exactly rounded products: within 1e-14 ||a|| ||b||
-    (tighter than the FP64-pipe kernel's bar; the engine is selected by
-    RK_TC_DOTS=1), with the FP64-pipe kernel (RK_TC_DOTS=0, the default) on
-    the same operands within its own bar. Operands: column
-    scales over six decades, a zero column, a column of mixed-sign values
-    spanning 2^-40..2^40 within each block, and a ragged tail."""
+    digit products of 56-bit truncations per 32-row block, 128-bit integer
+    running sums) against sums of exactly rounded products: within
+    1e-14 ||a|| ||b|| (tighter than the FP64-pipe kernel's bar; the engine is
+    selected by RK_TC_DOTS=1; below 32 rows the FP64-pipe kernel serves),
+    with the FP64-pipe kernel (RK_TC_DOTS=0, the default) on the same
+    operands within its own bar. Sizes from one 32-row block (a single
+    block, a ragged tail) to hundreds of blocks per SM (every buffer reused
+    many times); operands: column scales over six decades, a zero column, a
+    column of mixed-sign values spanning 2^-40..2^40 within each block."""
     rng = np.random.default_rng(n + 11 * nq)
     Q = rng.standard_normal((nq, n)) * np.exp2(rng.integers(-10, 10, size=(nq, 1)))
     if nq >= 3:
