@@ -46,6 +46,24 @@ __device__ __forceinline__ void block_reduce_cols(const double* vals, int ncol, 
 // A thread keeps 2 x kF64Group FP64 sums; every block writes its partials and
 // the last row range of a group to finish sums that group's columns over the
 // row ranges (a completion counter per group, fixed order).
+// rows [begin, end) of this thread: NC columns' sums with p (vals[q]) and
+// with w (vals[kF64Group + q]), one fma each per element, in row order
+template <int NC>
+__device__ __forceinline__ void dots2_rows(const double* const* col, const double* __restrict__ p,
+                                           const double* __restrict__ w, int64_t begin, int64_t end, double* vals) {
+  for (int64_t i = begin + threadIdx.x; i < end; i += kRedThreads) {
+    const double pv = __ldg(&p[i]), wv = __ldg(&w[i]);
+    double v[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) v[q] = __ldg(&col[q][i]);
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      vals[q] = fma(v[q], pv, vals[q]);
+      vals[kF64Group + q] = fma(v[q], wv, vals[kF64Group + q]);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kRedThreads) k_dots2_f64(F64Dots2Args a, int64_t rpb) {
   if (a.skip_flag != nullptr && *a.skip_flag != 0) return;
   __shared__ double red[kWarps][2 * kF64Group];
@@ -75,16 +93,17 @@ __global__ void __launch_bounds__(kRedThreads) k_dots2_f64(F64Dots2Args a, int64
     const double* col[kF64Group];
 #pragma unroll
     for (int q = 0; q < kF64Group; ++q) col[q] = a.Q + (int64_t)(c0 + (q < nc ? q : 0)) * a.ld;
-    for (int64_t i = begin + threadIdx.x; i < end; i += kRedThreads) {
-      const double pv = __ldg(&a.p[i]), wv = __ldg(&a.w[i]);
-      double v[kF64Group];
-#pragma unroll
-      for (int q = 0; q < kF64Group; ++q) v[q] = q < nc ? __ldg(&col[q][i]) : 0.0;
-#pragma unroll
-      for (int q = 0; q < kF64Group; ++q) {
-        vals[q] = fma(v[q], pv, vals[q]);
-        vals[kF64Group + q] = fma(v[q], wv, vals[kF64Group + q]);
-      }
+    // the group's nc columns as a compile-time count: a last group of fewer
+    // than kF64Group columns spends no FP64 fmas on padding
+    switch (nc) {
+      case 8: dots2_rows<8>(col, a.p, a.w, begin, end, vals); break;
+      case 7: dots2_rows<7>(col, a.p, a.w, begin, end, vals); break;
+      case 6: dots2_rows<6>(col, a.p, a.w, begin, end, vals); break;
+      case 5: dots2_rows<5>(col, a.p, a.w, begin, end, vals); break;
+      case 4: dots2_rows<4>(col, a.p, a.w, begin, end, vals); break;
+      case 3: dots2_rows<3>(col, a.p, a.w, begin, end, vals); break;
+      case 2: dots2_rows<2>(col, a.p, a.w, begin, end, vals); break;
+      default: dots2_rows<1>(col, a.p, a.w, begin, end, vals); break;
     }
   }
   // block partials: [Q^T p of the group | Q^T w of the group] or the scalars
@@ -142,6 +161,22 @@ __global__ void __launch_bounds__(kRedThreads) k_dots2_f64(F64Dots2Args a, int64
   }
 }
 
+// R columns q .. q + R - 1 of one row: av += sum Q_qu ca_u, and bv likewise
+// with cb when `both`, in column order
+template <int R>
+__device__ __forceinline__ void upd2_chunk(const double* col, int64_t ld, int q, const double* ca, const double* cb,
+                                           bool both, double& av, double& bv) {
+  double v[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) v[u] = __ldg(col + (int64_t)(q + u) * ld);
+#pragma unroll
+  for (int u = 0; u < R; ++u) av = fma(v[u], ca[q + u], av);
+  if (both) {
+#pragma unroll
+    for (int u = 0; u < R; ++u) bv = fma(v[u], cb[q + u], bv);
+  }
+}
+
 // v = (p - Q a) s0 into p; p_next = (w - Q b) s1 - v s2 into w (mode 0), or
 // only v (mode 1); anything else: nothing. One read of Q feeds both sums.
 __global__ void __launch_bounds__(kRedThreads) k_update2_f64(F64Update2Args a) {
@@ -164,18 +199,20 @@ __global__ void __launch_bounds__(kRedThreads) k_update2_f64(F64Update2Args a) {
     double av = a.p[i];
     double bv = mode == 0 ? a.w[i] : 0.0;
     const double* col = a.Q + i;
-    // chunks of 8 columns, the last one predicated: every load of a chunk
-    // is issued before its multiply-adds
-    for (int q = 0; q < a.nq; q += 8) {
-      double v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = q + u < a.nq ? __ldg(col + (int64_t)(q + u) * a.ld) : 0.0;
-#pragma unroll
-      for (int u = 0; u < 8; ++u) av = fma(v[u], ca[q + u], av);
-      if (mode == 0) {
-#pragma unroll
-        for (int u = 0; u < 8; ++u) bv = fma(v[u], cb[q + u], bv);
-      }
+    // chunks of 8 columns (every load of a chunk issued before its
+    // multiply-adds), then the remaining 1-7 columns as a compile-time count,
+    // so no FP64 fma is spent on padding
+    int q = 0;
+    for (; q + 8 <= a.nq; q += 8) upd2_chunk<8>(col, a.ld, q, ca, cb, mode == 0, av, bv);
+    switch (a.nq - q) {
+      case 7: upd2_chunk<7>(col, a.ld, q, ca, cb, mode == 0, av, bv); break;
+      case 6: upd2_chunk<6>(col, a.ld, q, ca, cb, mode == 0, av, bv); break;
+      case 5: upd2_chunk<5>(col, a.ld, q, ca, cb, mode == 0, av, bv); break;
+      case 4: upd2_chunk<4>(col, a.ld, q, ca, cb, mode == 0, av, bv); break;
+      case 3: upd2_chunk<3>(col, a.ld, q, ca, cb, mode == 0, av, bv); break;
+      case 2: upd2_chunk<2>(col, a.ld, q, ca, cb, mode == 0, av, bv); break;
+      case 1: upd2_chunk<1>(col, a.ld, q, ca, cb, mode == 0, av, bv); break;
+      default: break;
     }
     const double vf = av * s0;
     a.p[i] = vf;
